@@ -1,0 +1,157 @@
+"""Loss, gradients, meta network and optimiser for neural-solver training (oracle; test only).
+
+Algorithm 1 of the paper: weights w = Meta(theta; mu); unroll K iterations of the
+Table 1 method from u0; loss L2 of eq. 15; backpropagate. Readings used here:
+  * the loss is the mean *log* relative residual (1/B) sum_b ln(||f_b - A_b u_b^K|| / ||f_b||)
+    (a monotone transform of eq. 15 per instance; natural log);
+  * the meta network is an MLP 2 -> 64 -> 64 -> (m+1) with ReLU, inputs (log10 eps, theta)
+    (Sec. 2.4 feeds lg eps); outputs o map to w_i = exp(o_i) / G (G the Gershgorin bound
+    of the instance, so the net predicts scale-free log-weights, cf. the log-w
+    parametrisation of Sec. 3.2) and a momentum a = sigmoid(o_m) shared by all m steps;
+  * the NAG form (at = a), zero initial velocity.
+Gradients are taken by PyTorch autograd (FP64, CPU) through a plain forward that
+multiplies by the element-assembled sparse matrix; they are pinned by central finite
+differences of the same forward (tests).
+"""
+from __future__ import annotations
+
+import warnings
+
+import numpy as np
+import torch
+
+warnings.filterwarnings("ignore", message="Sparse CSR tensor support is in beta state")
+warnings.filterwarnings("ignore", message="Sparse invariant checks are implicitly disabled")
+
+
+def to_torch_sparse(A):
+    """scipy CSR -> torch CSR (float64 or complex128), CPU."""
+    A = A.tocsr()
+    return torch.sparse_csr_tensor(torch.from_numpy(A.indptr.astype(np.int64)),
+                                   torch.from_numpy(A.indices.astype(np.int64)),
+                                   torch.from_numpy(A.data), size=A.shape)
+
+
+def unrolled_nag(At, f, u0, w, a, K, Dinv=None):
+    """K inner NAG steps (Table 1, at = a) in torch; u^{-1} = u0 (zero velocity).
+
+    w, a: tensors of length m (a may be a length-m tensor or a scalar tensor).
+    Dinv: optional tensor, elementwise B^{-1} = D^{-1} (eq. 17).
+    """
+    m = w.shape[0]
+    u = u0
+    v = torch.zeros_like(u0)
+    for k in range(K):
+        i = k % m
+        ai = a[i] if a.dim() > 0 else a
+        ut = u + ai * v
+        r = f - At @ ut
+        if Dinv is not None:
+            r = Dinv * r
+        v = ai * v + w[i] * r
+        u = u + v
+    return u
+
+
+def log_rel_residual(At, f, u):
+    """ln(||f - A u|| / ||f||)."""
+    return torch.log(torch.linalg.vector_norm(f - At @ u) / torch.linalg.vector_norm(f))
+
+
+def loss_and_grads(As, fs, u0s, ws, alphas, K, Dinvs=None):
+    """Mean log relative residual after K NAG steps and its gradient.
+
+    As: list of scipy matrices; fs, u0s: lists of flat numpy arrays; ws: (B, m);
+    alphas: (B, m) per-step momentum or (B,) one momentum per instance.
+    Returns (L, dL/dw (B, m), dL/dalpha (same shape as alphas), [dL/du0_b]).
+    Pinned by: central finite differences (tests).
+    """
+    B = len(As)
+    w_t = torch.tensor(np.asarray(ws, dtype=np.float64), requires_grad=True)
+    a_t = torch.tensor(np.asarray(alphas, dtype=np.float64), requires_grad=True)
+    u0_t = [torch.tensor(np.asarray(u, dtype=np.float64), requires_grad=True) for u in u0s]
+    total = 0.0
+    for b in range(B):
+        At = to_torch_sparse(As[b])
+        f = torch.from_numpy(np.asarray(fs[b], dtype=np.float64))
+        Dinv = None if Dinvs is None else torch.from_numpy(np.asarray(Dinvs[b]))
+        uK = unrolled_nag(At, f, u0_t[b], w_t[b], a_t[b], K, Dinv)
+        total = total + log_rel_residual(At, f, uK)
+    L = total / B
+    L.backward()
+    return float(L.detach()), w_t.grad.numpy(), a_t.grad.numpy(), [u.grad.numpy() for u in u0_t]
+
+
+def loss_only(As, fs, u0s, ws, alphas, K):
+    """The same loss in numpy (used for finite differences)."""
+    with torch.no_grad():
+        tot = 0.0
+        for b in range(len(As)):
+            At = to_torch_sparse(As[b])
+            f = torch.from_numpy(np.asarray(fs[b], dtype=np.float64))
+            uK = unrolled_nag(At, f, torch.tensor(np.asarray(u0s[b], dtype=np.float64)),
+                              torch.tensor(np.asarray(ws[b], dtype=np.float64)),
+                              torch.tensor(np.asarray(alphas[b], dtype=np.float64)), K)
+            tot += float(log_rel_residual(At, f, uK))
+    return tot / len(As)
+
+
+# ---------------------------------------------------------------- meta network
+
+def mlp_forward(params, X):
+    """o = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for each row x of X (numpy, FP64).
+
+    params: [(W1, b1), (W2, b2), (W3, b3)], W[out][in]. Pinned by: a hand-evaluated
+    2-2-2-1 network (tests).
+    """
+    h = np.asarray(X, dtype=np.float64)
+    for li, (W, b) in enumerate(params):
+        h = h @ np.asarray(W).T + np.asarray(b)
+        if li < len(params) - 1:
+            h = np.maximum(h, 0.0)
+    return h
+
+
+def meta_output_map(o, G, m):
+    """w_i = exp(o_i) / G (i < m), a = sigmoid(o_m) (reading; see module docstring)."""
+    o = np.asarray(o, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64).reshape(-1, 1)
+    w = np.exp(o[:, :m]) / G
+    a = 1.0 / (1.0 + np.exp(-o[:, m]))
+    return w, a
+
+
+def mlp_loss_and_grads(params, X, G, m, As, fs, K):
+    """Training loss of Algorithm 1 (x0 = 0, NAG, K steps) and its gradient wrt the MLP.
+
+    Returns (L, [(dW, db) per layer], w (B, m), a (B,)). Pinned by: finite differences.
+    """
+    tp = [(torch.tensor(np.asarray(W, dtype=np.float64), requires_grad=True),
+           torch.tensor(np.asarray(b, dtype=np.float64), requires_grad=True)) for W, b in params]
+    h = torch.from_numpy(np.asarray(X, dtype=np.float64))
+    for li, (W, b) in enumerate(tp):
+        h = h @ W.T + b
+        if li < len(tp) - 1:
+            h = torch.relu(h)
+    Gt = torch.from_numpy(np.asarray(G, dtype=np.float64)).reshape(-1, 1)
+    w = torch.exp(h[:, :m]) / Gt
+    a = torch.sigmoid(h[:, m])
+    total = 0.0
+    for b in range(len(As)):
+        At = to_torch_sparse(As[b])
+        f = torch.from_numpy(np.asarray(fs[b], dtype=np.float64))
+        uK = unrolled_nag(At, f, torch.zeros_like(f), w[b], a[b], K)
+        total = total + log_rel_residual(At, f, uK)
+    L = total / len(As)
+    L.backward()
+    grads = [(W.grad.numpy(), b.grad.numpy()) for W, b in tp]
+    return float(L.detach()), grads, w.detach().numpy(), a.detach().numpy()
+
+
+def adam_step(p, g, m1, m2, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, 2015) on arrays; returns (p, m1, m2). t is 1-based."""
+    m1 = b1 * m1 + (1.0 - b1) * g
+    m2 = b2 * m2 + (1.0 - b2) * g * g
+    mh = m1 / (1.0 - b1 ** t)
+    vh = m2 / (1.0 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m1, m2

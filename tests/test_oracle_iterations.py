@@ -1,0 +1,174 @@
+"""Pins of the oracle's iterations: closed forms, exact solves, the paper's Table 2."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import richm_synth as synth
+from oracle.iterations import (chebyshev_weights, inner_steps, jacobi_binv,
+                               outer_iterations_to_tol, refined_steps, rel_residual,
+                               semi_iteration_weights)
+from oracle.operators import assemble_q1, diffusion_tensor
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _theta0_modes(n, eps):
+    """Sine modes and eigenvalues of the theta = 0 operator (separable closed form)."""
+    h = 1.0 / (n + 1)
+    C = diffusion_tensor(eps, 0.0)
+    s = np.sin(np.arange(1, n + 1) * math.pi * h / 2) ** 2
+    kap, mu = 4 * s, 1 - 2 * s / 3
+    # eigenvalue for mode (p along y/rows, q along x/columns)
+    lam = C[0, 0] * np.outer(mu, kap) + C[1, 1] * np.outer(kap, mu)
+    grid = np.arange(1, n + 1) * h
+
+    def mode(p, q):
+        return np.outer(np.sin(p * math.pi * grid), np.sin(q * math.pi * grid)).ravel()
+    return lam, mode
+
+
+@pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-5])
+def test_sine_mode_contraction(eps):
+    # b = 0, x0 = sine mode: x_K = prod_s (1 - w_{s mod m} lam) x0 (eqs. 3-5)
+    n, m, K = 15, 8, 21
+    A = assemble_q1(n, eps, 0.0)
+    lam, mode = _theta0_modes(n, eps)
+    w = semi_iteration_weights(lam.max() * 1.01, m)
+    for p, q in [(1, 1), (3, 10), (15, 15), (7, 2)]:
+        x0 = mode(p, q)
+        x, _ = inner_steps(A, np.zeros_like(x0), x0, None, w, K=K, k_start=5)
+        fac = np.prod([1 - w[(5 + s) % m] * lam[p - 1, q - 1] for s in range(K)])
+        np.testing.assert_allclose(x, fac * x0, rtol=1e-11, atol=1e-13 * np.abs(x0).max())
+
+
+def test_nag_mode_recurrence():
+    # NAG (Table 1) on an eigenvector: x_{k+1} = (1 - w lam)((1 + a) x_k - a x_{k-1})
+    n, m, K = 11, 4, 13
+    A = assemble_q1(n, 1e-2, 0.0)
+    lam, mode = _theta0_modes(n, 1e-2)
+    w = np.array([0.3, 0.5, 0.2, 0.45])
+    a = np.array([0.3, 0.1, 0.5, 0.2])
+    for p, q in [(1, 2), (6, 6), (11, 3)]:
+        x0 = mode(p, q)
+        x, _ = inner_steps(A, np.zeros_like(x0), x0, None, w, a, K=K)
+        L = lam[p - 1, q - 1]
+        s_prev, s = 1.0, 1.0
+        for k in range(K):
+            s_prev, s = s, (1 - w[k % m] * L) * ((1 + a[k % m]) * s - a[k % m] * s_prev)
+        np.testing.assert_allclose(x, s * x0, rtol=1e-11, atol=1e-13)
+
+
+def test_momentum_zero_is_richardson_and_nagex_reductions():
+    n = 9
+    A = assemble_q1(n, 0.05, 0.7)
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal(n * n)
+    w = rng.uniform(0.05, 0.3, 5)
+    x1, _ = inner_steps(A, f, np.zeros(n * n), None, w, K=17)
+    x2, _ = inner_steps(A, f, np.zeros(n * n), None, w, np.zeros(5), K=17)
+    np.testing.assert_array_equal(x1, x2)
+    # NAGex with at = a is NAG
+    a = rng.uniform(0.0, 0.5, 5)
+    x3, _ = inner_steps(A, f, np.zeros(n * n), None, w, a, K=17)
+    x4, _ = inner_steps(A, f, np.zeros(n * n), None, w, a, a.copy(), K=17)
+    np.testing.assert_array_equal(x3, x4)
+
+
+def test_chebyshev_closed_form_reduction():
+    # One period with exact lmin/lmax scales the extreme eigenvectors by
+    # +1/T_m(s) (lmin) and (-1)^m/T_m(s) (lmax), s = (lmax+lmin)/(lmax-lmin),
+    # T_m(s) = cosh(m arccosh s); every other eigenvalue is reduced at least as much.
+    n, eps = 15, 1e-2
+    A = assemble_q1(n, eps, 0.0)
+    lam, mode = _theta0_modes(n, eps)
+    lmin, lmax = lam.min(), lam.max()
+    pmin = np.unravel_index(lam.argmin(), lam.shape)
+    pmax = np.unravel_index(lam.argmax(), lam.shape)
+    for m in [3, 8, 16]:
+        w = chebyshev_weights(lmax, lmin, m)
+        Tm = math.cosh(m * math.acosh((lmax + lmin) / (lmax - lmin)))
+        for (p, q), sign in [(pmin, 1.0), (pmax, (-1.0) ** m)]:
+            x0 = mode(p + 1, q + 1)
+            x, _ = inner_steps(A, np.zeros_like(x0), x0, None, w, K=m)
+            # rounding inside a period is amplified by the large intermediate factors
+            np.testing.assert_allclose(x, sign / Tm * x0, rtol=1e-7, atol=1e-8)
+        rng = np.random.default_rng(m)
+        for _ in range(5):
+            p, q = rng.integers(1, n + 1, 2)
+            x0 = mode(p, q)
+            x, _ = inner_steps(A, np.zeros_like(x0), x0, None, w, K=m)
+            assert np.linalg.norm(x) <= (1 / Tm) * np.linalg.norm(x0) * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("eps,theta", [(1.0, 0.0), (1e-2, math.pi / 6), (1e-4, 2.0)])
+def test_direct_solve_small_grids(n, eps, theta):
+    A = assemble_q1(n, eps, theta)
+    f = synth.rhs_uniform(0, n, n).ravel()
+    ev = np.linalg.eigvalsh(A.toarray())
+    u_direct = np.linalg.solve(A.toarray(), f)
+    w = chebyshev_weights(ev.max(), ev.min(), 8)
+    k, u = outer_iterations_to_tol(A, f, w, tol=1e-13, max_outer=20000)
+    assert k <= 20000
+    np.testing.assert_allclose(u, u_direct, rtol=1e-11, atol=1e-11 * np.abs(u_direct).max())
+    # NAG with a small momentum converges to the same solution
+    k2, u2 = outer_iterations_to_tol(A, f, 0.6 * w, tol=1e-13, max_outer=40000, a=np.full(8, 0.2))
+    assert k2 <= 40000
+    np.testing.assert_allclose(u2, u_direct, rtol=1e-10, atol=1e-10 * np.abs(u_direct).max())
+
+
+def test_jacobi_preconditioner_is_rescaled_weight():
+    # Q1 with constant coefficients has a constant diagonal d, so D^{-1} = w/d.
+    n = 10
+    A = assemble_q1(n, 0.1, 1.2)
+    f = synth.rhs_uniform(3, 0, n).ravel()
+    d = A.diagonal()[0]
+    assert np.all(A.diagonal() == d)
+    w = np.array([0.5, 0.9, 0.7])
+    a = np.array([0.2, 0.2, 0.2])
+    x1, _ = inner_steps(A, f, np.zeros(n * n), None, w, a, K=11, Binv=jacobi_binv(A))
+    x2, _ = inner_steps(A, f, np.zeros(n * n), None, w / d, a, K=11)
+    np.testing.assert_allclose(x1, x2, rtol=1e-13, atol=1e-15)
+
+
+def test_refinement_split_is_the_same_iteration():
+    n = 17
+    A = assemble_q1(n, 3e-2, 0.9)
+    b = synth.rhs_uniform(2, 1, n).ravel()
+    G = 4.0
+    w = semi_iteration_weights(G, 16) * 0.6
+    a = np.full(16, 0.3)
+    for R in (64, 16, 7):
+        x_split = refined_steps(A, b, np.zeros(n * n), 200, w, a, refine_every=R)
+        x_plain, _ = inner_steps(A, b, np.zeros(n * n), None, w, a, K=200)
+        np.testing.assert_allclose(x_split, x_plain, rtol=1e-12, atol=1e-12 * np.abs(x_plain).max())
+
+
+def _golden_table2():
+    rows = []
+    with open(os.path.join(GOLDEN, "table2_chebyshev.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                meth, eps, it, band = line.split()
+                rows.append((meth, float(eps), int(it), float(band)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_table2(), ids=lambda r: f"{r[0]}-{r[1]:g}")
+def test_table2_chebyshev_rows(row):
+    meth, eps, paper_it, band = row
+    n = 63
+    A = assemble_q1(n, eps, 0.0)
+    lam, _ = _theta0_modes(n, eps)
+    if meth == "cheb3":
+        w = chebyshev_weights(lam.max(), lam.min(), 3)
+    else:
+        w = semi_iteration_weights(lam.max(), 3, 1.0 / 30.0)
+    for seed in range(2):
+        f = synth.rhs_normal(11, seed, n).ravel()
+        k, u = outer_iterations_to_tol(A, f, w, tol=1e-6)
+        assert rel_residual(A, f, u) < 1e-6
+        assert abs(k - paper_it) <= band * paper_it, (meth, eps, seed, k, paper_it)

@@ -1,0 +1,131 @@
+"""Pins of the oracle's gradients, meta network, optimiser and Fourier correction."""
+import math
+
+import numpy as np
+
+import richm_synth as synth
+from oracle.fourier import fourier_correction, two_level_cycle
+from oracle.iterations import inner_steps, semi_iteration_weights
+from oracle.operators import assemble_q1, gershgorin_max
+from oracle.training import (adam_step, loss_and_grads, loss_only, meta_output_map,
+                             mlp_forward, mlp_loss_and_grads)
+
+
+def _problem(B=2, n=7, K=12, m=4):
+    As, fs, u0s = [], [], []
+    for b in range(B):
+        A = assemble_q1(n, [1e-2, 0.3, 1.0][b % 3], [0.4, 2.0, 1.1][b % 3])
+        As.append(A)
+        fs.append(synth.rhs_uniform(21, b, n).ravel())
+        u0s.append(0.1 * synth.rhs_uniform(22, b, n).ravel())
+    w = np.stack([semi_iteration_weights(gershgorin_max(A), m) * 0.5 for A in As])
+    a = np.full((B, m), 0.3) + 0.05 * np.arange(m)
+    return As, fs, u0s, w, a, K
+
+
+def test_loss_gradient_matches_central_differences():
+    As, fs, u0s, w, a, K = _problem()
+    L, gw, ga, gu = loss_and_grads(As, fs, u0s, w, a, K)
+    h = 1e-4
+    for b in range(2):
+        for i in range(w.shape[1]):
+            wp, wm = w.copy(), w.copy()
+            wp[b, i] += h
+            wm[b, i] -= h
+            fd = (loss_only(As, fs, u0s, wp, a, K) - loss_only(As, fs, u0s, wm, a, K)) / (2 * h)
+            assert abs(fd - gw[b, i]) <= 1e-6 * max(1.0, abs(fd)), (b, i, fd, gw[b, i])
+            ap, am = a.copy(), a.copy()
+            ap[b, i] += h
+            am[b, i] -= h
+            fd = (loss_only(As, fs, u0s, w, ap, K) - loss_only(As, fs, u0s, w, am, K)) / (2 * h)
+            assert abs(fd - ga[b, i]) <= 1e-6 * max(1.0, abs(fd))
+        for idx in [0, 11, 24, 48]:
+            up = [u.copy() for u in u0s]
+            um = [u.copy() for u in u0s]
+            up[b][idx] += h
+            um[b][idx] -= h
+            fd = (loss_only(As, fs, up, w, a, K) - loss_only(As, fs, um, w, a, K)) / (2 * h)
+            assert abs(fd - gu[b][idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_loss_value_is_mean_log_relative_residual():
+    As, fs, u0s, w, a, K = _problem()
+    L = loss_only(As, fs, u0s, w, a, K)
+    ref = 0.0
+    for b in range(2):
+        u, _ = inner_steps(As[b], fs[b], u0s[b], None, w[b], a[b], K=K)
+        ref += math.log(np.linalg.norm(fs[b] - As[b] @ u) / np.linalg.norm(fs[b]))
+    assert abs(L - ref / 2) < 1e-12
+
+
+def test_mlp_forward_hand_evaluated():
+    # 2-2-2-1 network evaluated by hand
+    params = [(np.array([[1.0, -1.0], [0.5, 2.0]]), np.array([0.0, -1.0])),
+              (np.array([[1.0, 1.0], [-1.0, 3.0]]), np.array([0.5, 0.0])),
+              (np.array([[2.0, -1.0]]), np.array([0.25]))]
+    X = np.array([[1.0, 2.0], [3.0, -1.0]])
+    # x=(1,2): h1=relu(-1, 3.5)=(0,3.5); h2=relu(4, 10.5)=(4,10.5); o=8-10.5+0.25=-2.25
+    # x=(3,-1): h1=relu(4,-1.5)=(4,0); h2=relu(4.5,-4)=(4.5,0); o=9+0.25=9.25
+    np.testing.assert_allclose(mlp_forward(params, X), [[-2.25], [9.25]])
+    w, a = meta_output_map(np.array([[0.0, math.log(2.0), 0.0]]), [4.0], 2)
+    np.testing.assert_allclose(w, [[0.25, 0.5]])
+    np.testing.assert_allclose(a, [0.5])
+
+
+def test_mlp_training_gradient_matches_central_differences():
+    m, K, n = 4, 10, 6
+    params = synth.mlp_init((2, 8, 8, m + 1), seed=3)
+    params = [(W * 0.3, b * 0.3) for W, b in params]
+    insts = [synth.AnisoInstance(1e-2, 0.5, n), synth.AnisoInstance(0.5, 2.0, n)]
+    As = [assemble_q1(n, t.eps, t.theta) for t in insts]
+    G = np.array([gershgorin_max(A) for A in As])
+    fs = [synth.rhs_uniform(5, b, n).ravel() for b in range(2)]
+    X = synth.meta_inputs(insts)
+    L, grads, _, _ = mlp_loss_and_grads(params, X, G, m, As, fs, K)
+    h = 1e-5
+    rng = np.random.default_rng(0)
+    for li in range(3):
+        W, b = params[li]
+        for _ in range(3):
+            r, c = rng.integers(0, W.shape[0]), rng.integers(0, W.shape[1])
+            vals = []
+            for sgn in (1, -1):
+                P = [(Wk.copy(), bk.copy()) for Wk, bk in params]
+                P[li][0][r, c] += sgn * h
+                vals.append(mlp_loss_and_grads(P, X, G, m, As, fs, K)[0])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - grads[li][0][r, c]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_adam_first_step_is_signed_lr():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    p1, m1, m2 = adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
+    np.testing.assert_allclose(p1, p - 0.01 * np.sign(g), rtol=1e-14)
+    np.testing.assert_allclose(m1, 0.1 * g)
+    np.testing.assert_allclose(m2, 0.001 * g * g)
+
+
+def test_fft_matches_explicit_dft_and_zero_symbol():
+    for n in [5, 12, 33]:
+        A = assemble_q1(n, 1e-2, 1.0)
+        f = synth.rhs_uniform(9, n, n).ravel()
+        u = 0.3 * synth.rhs_uniform(8, n, n).ravel()
+        S = synth.fourier_symbol(n, seed=3)
+        jj = np.arange(n)
+        F = np.exp(-2j * math.pi * np.outer(jj, jj) / n)
+        r = (f - A @ u).reshape(n, n)
+        c = (F.conj() @ (S * (F @ r @ F.T)) @ F.conj().T) / (n * n)
+        np.testing.assert_allclose(fourier_correction(A, f, u, S), u + c.real.ravel(), atol=1e-12)
+        np.testing.assert_array_equal(fourier_correction(A, f, u, np.zeros((n, n))), u)
+
+
+def test_two_level_exact_inverse_symbol_on_periodic_free_case():
+    # With S = 0 a cycle is plain Richardson(m).
+    n = 9
+    A = assemble_q1(n, 1e-2, 0.3)
+    f = synth.rhs_uniform(1, 0, n).ravel()
+    w = semi_iteration_weights(gershgorin_max(A), 8)
+    u1 = two_level_cycle(A, f, np.zeros(n * n), w, np.zeros((n, n)))
+    u2, _ = inner_steps(A, f, np.zeros(n * n), None, w, K=8)
+    np.testing.assert_array_equal(u1, u2)
