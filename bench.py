@@ -1,0 +1,469 @@
+"""Benchmark: batched NAG-Richardson(m) with FP64 refinement on synthetic anisotropic Q1 instances.
+
+Workload (one step = one refinement cycle over the whole batch): 256 instances of
+-div(C grad u) = f (bilinear elements), eps = 10^U[-3, 0], theta ~ U[0, pi), n drawn
+from {127, 255, 511}, right-hand sides U[-1, 1]; NAG-Richardson(16) whose 16 weights
+and momentum come from the meta network; 64 FP32 sweeps, then the FP64 update,
+FP64 residual and per-instance convergence test. The full solve to 1e-10 is timed
+once after the steps (time to tolerance).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0). Under torchrun each rank solves its own batch of the
+same shape (weak scaling); no collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched Richardson(m) Gdof-sweeps/s, time to 1e-10 rel residual, % HBM peak"
+UNIT = "Gdof-sweeps/s"
+M, BETA, REFINE, TOL = 16, 0.3, 64, 1e-10
+SIZES = (127, 255, 511)
+BATCH = 256
+
+
+def workload_config(batch=BATCH):
+    return {
+        "workload": f"{batch} anisotropic Q1 (bilinear FEM) instances, n in {{127,255,511}}, "
+                    "eps=10^U[-3,0], theta~U[0,pi), b~U[-1,1]; NAG-Richardson(16), weights and momentum "
+                    "from the meta MLP 2-64-64-17; FP32 sweeps, FP64 refinement every 64 sweeps, tol 1e-10",
+        "instances": batch,
+        "m": M,
+        "refine_every": REFINE,
+        "sweeps_per_step": REFINE,
+        "l2": "inputs larger than L2 (state ~0.47 GB FP32 + 0.47 GB FP64 > 129 MB): no flush",
+    }
+
+
+# ---------------------------------------------------------------- distributed helpers
+
+def dist_env():
+    """(rank, world) from torchrun's environment, (0, 1) otherwise."""
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def shard_seed(rank: int) -> int:
+    """Instance-parameter seed of a rank's batch (rank 0 = the canonical batch)."""
+    return 1 + rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over the process group (timing only)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle legs
+
+def oracle_sample_rate(instances, seconds: float = 12.0, sweeps_per_chunk: int = 4):
+    """FP64 oracle NAG sweeps on one instance of each grid size, until `seconds` pass.
+
+    Returns (Gdof-sweeps/s, description). The oracle is timed as it stands
+    (scipy sparse mat-vec per sweep, one host thread)."""
+    import numpy as np
+
+    import richm_synth as synth
+    from oracle.iterations import inner_steps, semi_iteration_weights
+    from oracle.operators import assemble_q1, gershgorin_max
+    picked = {}
+    for i, t in enumerate(instances):
+        if t.n not in picked:
+            picked[t.n] = (i, t)
+    cases = []
+    for n, (i, t) in sorted(picked.items()):
+        A = assemble_q1(t.n, t.eps, t.theta)
+        G = gershgorin_max(A)
+        w = semi_iteration_weights(1.6 * G, M)
+        a = np.full(M, BETA)
+        cases.append((A, synth.rhs_uniform(2, i, t.n).ravel(), w, a, t.n))
+    dofs = 0
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        for A, f, w, a, n in cases:
+            inner_steps(A, f, np.zeros(n * n), None, w, a, K=sweeps_per_chunk, k_start=done)
+            dofs += n * n * sweeps_per_chunk
+        done += sweeps_per_chunk
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    desc = (f"{done} NAG sweeps on one instance of each n in {sorted(picked)} "
+            f"({sum(c[4] ** 2 for c in cases)} dofs), FP64 scipy CSR mat-vec, {el:.1f} s")
+    return dofs / el / 1e9, desc
+
+
+def run_reference(args):
+    """The oracle as the reference arm: same metric and workload, bounded samples."""
+    rank, world = dist_env()
+    if rank != 0:
+        return 0
+    import richm_synth as synth
+    insts = synth.batched_aniso(BATCH, SIZES, param_seed=shard_seed(0))
+    per_step = min(5.0, max(1.0, 90.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample_rate(insts, seconds=per_step)
+    rates = []
+    t0 = time.perf_counter()
+    desc = ""
+    for _ in range(args.steps):
+        r, desc = oracle_sample_rate(insts, seconds=per_step)
+        rates.append(r)
+    el = time.perf_counter() - t0
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: " + desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def build_batch(seed: int):
+    import numpy as np
+    import torch
+
+    import richm_synth as synth
+    from paper_2412_08076_gb300 import richm
+    insts = synth.batched_aniso(BATCH, SIZES, param_seed=seed)
+    op = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0) for t in insts])
+    rhs = synth.batched_rhs(insts, seed=2 if seed == 1 else 100 + seed)
+    dense = torch.tensor(np.concatenate([r.ravel() for r in rhs]), dtype=torch.float64)
+    return insts, op, rhs, dense
+
+
+def meta_inputs(op, insts, params):
+    """Device inputs of the meta network: (log10 eps, theta), Gershgorin bounds, parameters."""
+    import numpy as np
+    import torch
+
+    import richm_synth as synth
+    from paper_2412_08076_gb300 import richm
+    X = torch.tensor(synth.meta_inputs(insts), dtype=torch.float32, device="cuda")
+    G = torch.tensor(op.gershgorin(), dtype=torch.float32, device="cuda")
+    P = torch.tensor(params, dtype=torch.float32, device="cuda")
+    return X, G, P
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2412_08076_gb300 import meta as meta_mod
+    from paper_2412_08076_gb300 import richm
+
+    rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    insts, op, rhs, dense_b = build_batch(shard_seed(rank))
+    dofs = sum(t.n * t.n for t in insts)
+    params, psrc = meta_mod.load_params(M)
+    X, G, P = meta_inputs(op, insts, params)
+    B64 = op.pack(dense_b.to(dev), richm.F64)
+    X64 = op.zeros(richm.F64)
+    w, a = richm.meta_forward(P, X, G, M)
+    opts = op.solve_opts(M, tol=TOL, max_sweeps=10**8, refine_every=REFINE, inner=richm.F32, use_graph=1)
+    S = richm.Solver(op, opts, w, a)
+    S.start(B64, X64)
+    stream = torch.cuda.current_stream()
+
+    # the weight supply writes into the solver's weight buffers directly
+    def weight_supply():
+        lib = richm.load()
+        richm._check(lib.richm_meta_forward(richm._ptr(P), richm._ptr(X), richm._ptr(G), len(insts), M,
+                                            richm._ptr(w), richm._ptr(a), None, richm._stream(stream)),
+                     "richm_meta_forward")
+
+    for _ in range(args.warmup):
+        weight_supply()
+        S.step(1, sync=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        weight_supply()
+        S.step(1, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    active = S.step(0, sync=True)
+    clk = clocks.stop()
+    t_max_ms = max_over_ranks(ms, world, dev)
+    total_dofs = sum_over_ranks(float(dofs), world, dev)
+    value = total_dofs * REFINE * args.steps / (t_max_ms / 1e3) / 1e9
+    launches_per_step = 1 + REFINE + 3  # meta forward, sweeps, update, residual, reduce
+
+    # -- dominant kernel (the FP32 NAG sweep): launch duration by CUDA events on its stream
+    K = 192
+    xs = op.zeros(richm.F32)
+    xps = op.zeros(richm.F32)
+    b32 = op.zeros(richm.F32)
+    b32.copy_(B64.to(torch.float32))
+    ws = op.workspace(op._ws("richm_sweeps_workspace", richm.F32))
+    op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, work=ws)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    k0.record(stream)
+    for _ in range(reps):
+        op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, work=ws)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = k0.elapsed_time(k1) / (reps * K)
+    alg_bytes = 16.0 * dofs  # read x_k, x_{k-1}, b; write x_{k+1} (FP32)
+    achieved = alg_bytes / (sweep_ms / 1e3) / 1e9
+
+    # -- e2e: host buffers through the public API (pinned H2D of b, one cycle, D2H of x)
+    hb = dense_b.pin_memory()
+    hx = torch.empty(op.dense_elems(), dtype=torch.float64).pin_memory()
+    dB = torch.empty(op.dense_elems(), dtype=torch.float64, device=dev)
+    S2 = richm.Solver(op, opts, w, a)
+    Bp = op.zeros(richm.F64)
+    Xp = op.zeros(richm.F64)
+
+    def e2e_step():
+        dB.copy_(hb, non_blocking=True)
+        op.pack(dB, richm.F64, out=Bp)
+        Xp.zero_()
+        S2.start(Bp, Xp)
+        weight_supply()
+        S2.step(1, sync=False)
+        hx.copy_(op.unpack(Xp, richm.F64), non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    n_e2e = max(3, min(args.steps, 10))
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    q1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = q0.elapsed_time(q1) / n_e2e
+    e2e_val = dofs * REFINE / (e2e_ms / 1e3) / 1e9
+    S2.close()
+
+    # -- time to tolerance: full solve from x0 = 0 (timed once)
+    ttt = None
+    if not args.no_solve:
+        Xs = op.zeros(richm.F64)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        st, info = op.solve(B64, Xs, w, a, None, opts)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        solve_s = t0.elapsed_time(t1) / 1e3
+        sweeps = [s for s, _, _ in info]
+        ok = sum(1 for _, _, s in info if s == richm.OK)
+        # oracle verification of a sample of instances (4 of each size)
+        from oracle.operators import assemble_q1
+        xs_h = op.unpack(Xs, richm.F64).cpu().numpy()
+        offs = np.cumsum([0] + [t.n * t.n for t in insts])
+        checked, worst = 0, 0.0
+        per_n = {}
+        for i, t in enumerate(insts):
+            if per_n.get(t.n, 0) >= 4:
+                continue
+            per_n[t.n] = per_n.get(t.n, 0) + 1
+            A = assemble_q1(t.n, t.eps, t.theta)
+            u = xs_h[offs[i]:offs[i + 1]]
+            r = np.linalg.norm(rhs[i].ravel() - A @ u) / np.linalg.norm(rhs[i])
+            worst = max(worst, r)
+            checked += 1
+        ttt = {"seconds": solve_s, "status": int(st), "converged": ok, "instances": len(insts),
+               "max_sweeps": int(max(sweeps)), "total_dof_sweeps": float(sum(s * t.n * t.n for s, t in zip(sweeps, insts))),
+               "oracle_checked": checked, "oracle_worst_rel_res": worst}
+        ttt["gdof_sweeps_per_s"] = ttt["total_dof_sweeps"] / solve_s / 1e9
+        # plain FP64 GPU sweep (one instance per call, one sweep per launch): time per sweep
+        # on one instance of each size, extrapolated to the sweep counts above
+        per_sweep = {}
+        seen = {}
+        for i, t in enumerate(insts):
+            if t.n in seen:
+                continue
+            seen[t.n] = i
+            op1 = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0)])
+            b1 = op1.pack(torch.tensor(rhs[i].ravel(), device=dev), richm.F64)
+            x1 = op1.zeros(richm.F64)
+            w1 = w[i:i + 1].double().contiguous()
+            a1 = a[i:i + 1].double().contiguous()
+            o1 = op1.solve_opts(M, tol=0.0, max_sweeps=64 * 8, refine_every=64, inner=richm.F64, use_graph=0)
+            op1.solve(b1, x1, w1, a1, None, o1)
+            torch.cuda.synchronize()
+            c0 = time.perf_counter()
+            op1.solve(b1, x1, w1, a1, None, o1)
+            torch.cuda.synchronize()
+            per_sweep[t.n] = (time.perf_counter() - c0) / (64 * 8)
+            op1.close()
+        fp64_est = sum(per_sweep[t.n] * s for s, t in zip(sweeps, insts))
+        ttt["plain_fp64_seconds_extrapolated"] = fp64_est
+        ttt["plain_fp64_per_sweep_s"] = {str(k): v for k, v in per_sweep.items()}
+        ttt["speedup_vs_plain_fp64"] = fp64_est / solve_s
+
+    line = None
+    if rank == 0:
+        cpu_rate, cpu_desc = oracle_sample_rate(insts, seconds=args.cpu_seconds)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(), dofs_per_rank=dofs, meta_params=psrc,
+                           active_after_steps=active),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "sweep1_kernel<float,NAG> (FP32 NAG sweep, one sweep per launch)",
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": sweep_ms,
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc,
+                             "host_cores": os.cpu_count()},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(dense_b.numel() * 8),
+                    "d2h_bytes_per_step": int(hx.numel() * 8),
+                    "note": "pinned H2D of b, pack, solver start (FP64 residual), weight supply, one cycle, "
+                            "unpack, D2H of x"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "time_to_tol": ttt,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-tolerance solve")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

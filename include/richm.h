@@ -1,0 +1,336 @@
+/*
+ * richm.h - C ABI of the GB300 Richardson(m) stencil library (librichm.so).
+ *
+ * The library solves batches of linear systems A u = f (eq. 1 of "Momentum-
+ * Accelerated Richardson(m) and Their Multilevel Neural Solvers") arising from
+ *   - the anisotropic diffusion problem -div(C grad u) = f, u = 0 on the boundary,
+ *     C = R(theta) diag(1, eps) R(theta)^T, bilinear (Q1) elements on a uniform
+ *     mesh of the unit square (eq. 18 and Sec. 2.4), and
+ *   - the Helmholtz problem -Lap(u) - k^2 u = f with the 5-point stencil of eq. 22,
+ * with the long-step iterations of Table 1 (Richardson(m), MOM-, NAG- and
+ * NAGex-Richardson(m)) and the preconditioned form of eq. 17 with B^{-1} = D^{-1}.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grids. Instance b has n_b x n_b interior unknowns, h = 1/(n_b + 1). Unknown
+ *   (i, j) sits at x = (j + 1) h, y = (i + 1) h (column index = x, row index = y).
+ * Padded layout. Grid arrays live in one device buffer per field holding every
+ *   instance. Instance b occupies rows 0 .. n_b+1 of width `pitch_b` elements
+ *   starting at element `offset_b` (richm_layout): row 0 and row n_b+1 are zero
+ *   halo rows, unknown (i, j) is element offset_b + (i+1)*pitch_b + j, and the
+ *   columns n_b .. pitch_b-1 of every row are zero padding (pitch_b >= n_b + 1, a
+ *   multiple of 32; offset_b a multiple of 64). The layout in elements is the same
+ *   for every dtype. Every element outside the interior MUST be zero on input;
+ *   the library keeps it zero on output. richm_pack / richm_unpack convert from /
+ *   to dense row-major n_b x n_b blocks.
+ * Ownership. Grid buffers, weights, outputs and workspaces are caller-owned
+ *   device memory unless a parameter says "host". The operator handle is
+ *   library-owned (richm_operator_create / richm_operator_destroy) and holds a
+ *   small device copy of the instance descriptors. All device pointers must
+ *   belong to the device that was current when the operator was created, and
+ *   that device must be current in every call.
+ * Streams. `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream). Calls are stream-ordered and asynchronous unless documented
+ *   otherwise; the library synchronises only where an entry point returns host
+ *   results (richm_solve).
+ * Weights. Sweep k (0-based, global) uses coefficient index (k mod m), i.e. the
+ *   paper's w_{(k mod m)+1}. Coefficient arrays are [batch][m], row-major, in the
+ *   real type of the state dtype (float for RICHM_F32/RICHM_C64, double for
+ *   RICHM_F64/RICHM_C128).
+ * Errors. Every call returns a richm_status. Argument errors are detected before
+ *   any work is queued and leave every buffer untouched. RICHM_ERR_CUDA reports a
+ *   failed launch or CUDA call; richm_last_error() gives a message (thread-local,
+ *   valid until the next call from the same thread). No C++ exception crosses
+ *   this interface.
+ */
+#ifndef RICHM_H
+#define RICHM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RICHM_OK = 0,
+  RICHM_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, bad enum) */
+  RICHM_ERR_CUDA = 2,          /* a CUDA runtime / cuFFT call or kernel launch failed */
+  RICHM_ERR_NOMEM = 3,         /* workspace too small or a library allocation failed */
+  RICHM_ERR_NOT_CONVERGED = 4, /* richm_solve: an instance reached max_sweeps */
+  RICHM_ERR_DIVERGED = 5,      /* richm_solve: an instance's residual became non-finite or > 1e30 ||f|| */
+  RICHM_ERR_UNSUPPORTED = 6    /* valid request the library does not implement (e.g. dtype/problem mix) */
+} richm_status;
+
+typedef enum {
+  RICHM_ANISO_Q1 = 0,              /* eq. 18, bilinear elements, Dirichlet eliminated (Sec. 2.4) */
+  RICHM_HELMHOLTZ_FD5_ABC = 1,     /* eq. 22 interior rows; first-order absorbing boundary */
+  RICHM_HELMHOLTZ_FD5_DIRICHLET = 2/* eq. 22 interior rows; u = 0 on the boundary */
+} richm_problem;
+
+typedef enum {
+  RICHM_F64 = 0,   /* double */
+  RICHM_F32 = 1,   /* float */
+  RICHM_C64 = 2,   /* complex64: interleaved {float re, float im} */
+  RICHM_C128 = 3   /* complex128: interleaved {double re, double im} */
+} richm_dtype;
+
+/* One PDE instance. eps, theta: anisotropy strength (0 < eps <= 1) and angle for
+ * RICHM_ANISO_Q1; k: wavenumber for the Helmholtz kinds (k >= 0). */
+typedef struct {
+  int kind;      /* richm_problem */
+  int n;         /* interior unknowns per direction, 1 <= n <= 16383 */
+  double eps;
+  double theta;
+  double k;
+} richm_pde;
+
+typedef struct richm_operator richm_operator;
+
+/* ------------------------------------------------------------------ setup */
+
+/* Build the discrete operators of `batch` instances (eq. 18 / eq. 22).
+ * Q1 stencil (closed form of the element-assembled matrix, Sec. 2.4): with
+ * c11 = cos^2 t + eps sin^2 t, c22 = sin^2 t + eps cos^2 t, c12 = (1-eps) sin t cos t,
+ *   centre 4(c11+c22)/3, x-neighbours (c22-2c11)/3, y-neighbours (c11-2c22)/3,
+ *   corners (+1,+1),(-1,-1): -(c11+c22)/6 - c12/2; (+1,-1),(-1,+1): -(c11+c22)/6 + c12/2.
+ * Helmholtz (eq. 22): centre (4 - k^2 h^2)/h^2, neighbours -1/h^2; with the
+ *   absorbing boundary each missing neighbour adds -1/((1 - i k h) h^2) to the
+ *   diagonal (ghost value u_0 = u_1/(1 - i k h) from du/dn - i k u = 0).
+ * pdes: host [batch]. *out receives a library-owned handle. Errors: RICHM_ERR_ARG
+ * for batch < 1 or an invalid instance; RICHM_ERR_NOMEM / RICHM_ERR_CUDA if the
+ * device copy of the descriptors cannot be made. */
+richm_status richm_operator_create(const richm_pde* pdes, int batch, richm_operator** out);
+void richm_operator_destroy(richm_operator* op);
+
+/* Number of instances. */
+richm_status richm_operator_batch(const richm_operator* op, int* batch);
+
+/* Host FP64 stencil coefficients of one instance.
+ * Q1: coef[0..4] = centre, x-neighbour, y-neighbour, corner(+1,+1), corner(+1,-1).
+ * Helmholtz: coef[0] = centre, coef[1] = neighbour, coef[2..3] = (re, im) added to the
+ * diagonal per missing neighbour (0 for Dirichlet). coef: host [8]. */
+richm_status richm_stencil(const richm_operator* op, int instance, double* coef);
+
+/* Gershgorin bound max_i sum_j |a_ij| per instance (the lmax estimate used with
+ * eqs. 8-9 in the Chebyshev semi-iteration, Sec. 2.1). lmax: host [batch]. */
+richm_status richm_gershgorin(const richm_operator* op, double* lmax);
+
+/* Chebyshev-optimal weights (eqs. 8-9): w_i = 2/(lmax + lmin + (lmax - lmin) x_i),
+ * x_i = cos((2i-1) pi / 2m), i = 1..m, returned in index order. w: host [m].
+ * Errors: RICHM_ERR_ARG unless 0 < lmin < lmax and m >= 1. */
+richm_status richm_chebyshev_weights(double lmax, double lmin, int m, double* w);
+
+/* Padded layout of one instance (see the header comment): element offset of its
+ * row 0, row pitch in elements, and number of rows (n + 2). Host outputs. */
+richm_status richm_layout(const richm_operator* op, int instance, size_t* offset, int* pitch, int* rows);
+
+/* Elements of one padded field buffer holding every instance. Host output. */
+richm_status richm_buffer_elems(const richm_operator* op, size_t* elems);
+
+/* Dense <-> padded conversion on the device. dense: instances concatenated, each
+ * n_b*n_b row-major. richm_pack writes every element of `padded` (zeros outside
+ * the interior). Buffers must not overlap. */
+richm_status richm_pack(const richm_operator* op, richm_dtype dtype, const void* dense, void* padded, void* stream);
+richm_status richm_unpack(const richm_operator* op, richm_dtype dtype, const void* padded, void* dense, void* stream);
+
+/* ------------------------------------------------------------------ sweeps */
+
+typedef struct {
+  int m;        /* period length, 1 <= m <= 64 */
+  int k_start;  /* global index of the first sweep */
+  int precond;  /* 0: B^{-1} = I; 1: B^{-1} = D^{-1} (eq. 17 with the Jacobi preconditioner) */
+  int fuse;     /* sweeps per pass over HBM (temporal blocking): 0 = library choice, else 1, 2, 4 or 8 */
+} richm_sweep_opts;
+
+/* Workspace bytes richm_apply_sweeps needs for `dtype` (two padded buffers). */
+richm_status richm_sweeps_workspace(const richm_operator* op, richm_dtype dtype, size_t* bytes);
+
+/* K sweeps of the Table 1 iteration in the two-level form
+ *   y       = x_k + at_i (x_k - x_{k-1})
+ *   x_{k+1} = x_k + a_i (x_k - x_{k-1}) + w_i B^{-1} (b - A y),   i = k mod m,
+ * which is Table 1's velocity form with v_k = x_k - x_{k-1}: a = at = 0 gives
+ * Richardson(m) (eqs. 2-5), at = 0 MOM-, at = a NAG- and general at NAGex-
+ * Richardson(m); precond = 1 applies eq. 17 with B^{-1} = D^{-1}.
+ * x (in: x_{k_start}, out: x_{k_start+K}) and x_prev (in: x_{k_start-1}, out:
+ * x_{k_start+K-1}) are padded buffers; b is the padded right-hand side.
+ * w: [batch][m] (required); alpha: [batch][m] or NULL (no momentum; x_prev may then
+ * be NULL and is not written); alpha_t: [batch][m] or NULL (= alpha, i.e. NAG).
+ * dtype: RICHM_F32/RICHM_F64 for Q1, RICHM_C64/RICHM_C128 for Helmholtz (weights real).
+ * work: at least richm_sweeps_workspace bytes. K = 0 is a no-op. */
+richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, void* x_prev, const void* b,
+                                const void* w, const void* alpha, const void* alpha_t, int K,
+                                const richm_sweep_opts* opts, void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ residual */
+
+/* Workspace bytes richm_residual_norm needs (per-tile FP64 partial sums). */
+richm_status richm_residual_workspace(const richm_operator* op, size_t* bytes);
+
+/* r = b - A x and its norms (eq. 15 and the stopping test of Sec. 2.4), summed in
+ * FP64 whatever the state dtype (complex: |r|^2). Outputs are device [batch]
+ * arrays; each may be NULL: rnorm = ||r||_2, bnorm = ||b||_2, rel = rnorm / bnorm.
+ * r_out: padded buffer of the same dtype receiving r, or NULL. Deterministic:
+ * partial sums are combined in a fixed order. */
+richm_status richm_residual_norm(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
+                                 double* rnorm, double* bnorm, double* rel, void* r_out,
+                                 void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ solve */
+
+typedef struct {
+  int m;                 /* period length */
+  double tol;            /* stop an instance once ||b - A x|| / ||b|| <= tol (FP64 residual) */
+  long long max_sweeps;  /* per instance */
+  int refine_every;      /* sweeps between FP64 refinement steps / convergence checks (>= 1) */
+  int inner;             /* richm_dtype of the inner sweeps: RICHM_F32 (mixed precision) or RICHM_F64 */
+  int precond;           /* as in richm_sweep_opts */
+  int fuse;              /* as in richm_sweep_opts */
+  int use_graph;         /* 1: replay the refinement cycle as a CUDA graph */
+} richm_solve_opts;
+
+typedef struct {
+  long long sweeps;  /* sweeps applied to this instance */
+  double rel_res;    /* final FP64 relative residual */
+  int status;        /* RICHM_OK, RICHM_ERR_NOT_CONVERGED or RICHM_ERR_DIVERGED */
+} richm_solve_info;
+
+richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_opts* opts, size_t* bytes);
+
+/* Solve every instance of a Q1 batch to tolerance ("iterate until a tolerance or the
+ * maximum number of iterations", Sec. 2.3) with FP64 iterative refinement around the
+ * inner sweeps: every refine_every sweeps, x += e (FP64), r = b - A x (FP64), the
+ * inner right-hand side becomes r, e restarts at 0 and the inner velocity and weight
+ * index carry over (so the split is the same iteration in exact arithmetic).
+ * b: padded FP64 right-hand side; x: padded FP64, in = initial guess, out = solution.
+ * w / alpha / alpha_t: [batch][m] in the real type of opts->inner (alpha, alpha_t as in
+ * richm_apply_sweeps). info: host [batch]. Synchronises `stream` before returning.
+ * Returns RICHM_OK if every instance converged, else RICHM_ERR_DIVERGED if any
+ * diverged, else RICHM_ERR_NOT_CONVERGED. */
+richm_status richm_solve(richm_operator* op, const double* b, double* x, const void* w, const void* alpha,
+                         const void* alpha_t, const richm_solve_opts* opts, richm_solve_info* info,
+                         void* work, size_t work_bytes, void* stream);
+
+/* Session form of richm_solve for callers that drive the refinement cycles
+ * themselves (progress reporting, fixed-cycle timing, resuming). The handle keeps
+ * pointers to the caller's weights and workspace (which must stay valid until
+ * richm_solver_destroy) and owns a CUDA stream, two events, a pinned 4-byte host
+ * word and, once a step has run with use_graph, the instantiated graph of one
+ * cycle. richm_solver_start binds b and x, zeroes the inner state and evaluates
+ * the initial residual; richm_solver_step runs `cycles` refinement cycles (each:
+ * refine_every sweeps, the FP64 update, the FP64 residual and the per-instance
+ * test) ordered after the work already queued on `stream`, and, when active_out is
+ * not NULL, waits and returns the number of instances still iterating;
+ * richm_solver_finish waits for `stream` and fills info (host [batch]). x holds the
+ * current FP64 iterate after every step. Instances that converged, diverged or
+ * reached max_sweeps are skipped by later cycles. */
+typedef struct richm_solver richm_solver;
+richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* opts, const void* w, const void* alpha,
+                                 const void* alpha_t, void* work, size_t work_bytes, richm_solver** out);
+richm_status richm_solver_start(richm_solver* s, const double* b, double* x, void* stream);
+richm_status richm_solver_step(richm_solver* s, int cycles, int* active_out, void* stream);
+richm_status richm_solver_finish(richm_solver* s, richm_solve_info* info, void* stream);
+void richm_solver_destroy(richm_solver* s);
+
+/* One FP64 refinement step of a mixed-precision iteration on a Q1 batch:
+ *   x += e;  e_prev -= e (if e_prev is not NULL);  e = 0;  rhs_out = b - A x,
+ * with x, b FP64 padded buffers, e, e_prev and rhs_out padded buffers of the
+ * inner dtype (RICHM_F32 or RICHM_F64); e may be NULL (no update, residual only).
+ * rel: device [batch] relative residual ||b - A x|| / ||b|| (FP64), or NULL.
+ * work: at least richm_residual_workspace bytes. */
+richm_status richm_refine(richm_operator* op, double* x, const double* b, void* e, void* e_prev, int inner,
+                          void* rhs_out, double* rel, void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ differentiation */
+
+/* Checkpoint store for K unrolled sweeps with a checkpoint every s sweeps:
+ * (K/s + 1) slots of two padded buffers (x_k, x_{k-1}) for k = 0, s, 2s, ...; slot j
+ * starts at element 2*j*elems. Returns the element count (x dtype). */
+richm_status richm_checkpoint_elems(const richm_operator* op, int K, int ckpt_every, size_t* elems);
+
+/* Forward K sweeps from x0 with zero initial velocity (x_{-1} = x0), storing the
+ * checkpoints; xK receives x_K (padded). Same coefficient conventions as
+ * richm_apply_sweeps. Requires K % ckpt_every == 0. work: richm_sweeps_workspace. */
+richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, const void* x0, const void* b,
+                                        const void* w, const void* alpha, const void* alpha_t, int m, int K,
+                                        int ckpt_every, int precond, void* ckpts, void* xK,
+                                        void* work, size_t work_bytes, void* stream);
+
+/* Workspace bytes for richm_loss_log_residual and richm_sweeps_adjoint. */
+richm_status richm_adjoint_workspace(const richm_operator* op, richm_dtype dtype, int ckpt_every, size_t* bytes);
+
+/* Training loss (the log form of eq. 15, the L2 loss of Algorithm 1):
+ *   L = (1/B) sum_b ln(||b_b - A_b x_b|| / ||b_b||),
+ * and its gradient g = dL/dx = -(1/B) A r / ||r||^2 (A symmetric), r = b - A x.
+ * loss: device scalar (FP64); g: padded buffer (dtype of x) or NULL. */
+richm_status richm_loss_log_residual(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
+                                     double* loss, void* g, void* work, size_t work_bytes, void* stream);
+
+/* Reverse-mode sweep ("backpropagate", Algorithm 1) over the K sweeps recorded by
+ * richm_forward_checkpointed, with A symmetric so the adjoint applies the same
+ * stencil: for k = K-1 .. 0 (i = k mod m), with lam_{k+1} = dL/dx_{k+1} and
+ * q = w_i A B^{-1} lam_{k+1},
+ *   dL/dw_i   += <lam_{k+1}, B^{-1}(b - A y_k)>
+ *   dL/da_i   += <lam_{k+1}, x_k - x_{k-1}>
+ *   dL/dat_i  += -<q, x_k - x_{k-1}>
+ *   lam_k      = (1 + a_i) lam_{k+1} - (1 + at_i) q + c_{k+1},  c_k = -a_i lam_{k+1} + at_i q,
+ * and dL/dx0 = lam_0 + c_0 (x_{-1} = x0). Segments between checkpoints are recomputed.
+ * gK: dL/dx_K (padded). g_w, g_alpha, g_alpha_t: device [batch][m] (real type), each
+ * may be NULL; when alpha_t is NULL (NAG, at = a) the at-gradient is added into
+ * g_alpha. g_x0: padded or NULL. Gradients are written, not accumulated. */
+richm_status richm_sweeps_adjoint(richm_operator* op, richm_dtype dtype, const void* ckpts, int ckpt_every,
+                                  const void* b, const void* gK, const void* w, const void* alpha,
+                                  const void* alpha_t, int m, int K, int precond, void* g_w, void* g_alpha,
+                                  void* g_alpha_t, void* g_x0, void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ meta network */
+
+/* Meta(theta; mu) of Sec. 2.3: an MLP 2 -> 64 -> 64 -> (m+1) with ReLU, FP32,
+ * parameters packed as W1[64][2], b1[64], W2[64][64], b2[64], W3[m+1][64], b3[m+1]
+ * (W[out][in]); richm_meta_param_count gives the total (5457 for m = 16).
+ * Output map: w_i = exp(o_i) / G_b (i < m), a = sigmoid(o_m) for every step;
+ * alpha_out[b][i] = a (NAG uses at = a). inputs: [B][2] = (log10 eps, theta).
+ * G: [B] Gershgorin bounds. acts: [B][2*64 + m + 1] saved pre-activations for the
+ * backward pass, or NULL. All arrays device, FP32. 1 <= m <= 63. */
+richm_status richm_meta_param_count(int m, int* count);
+richm_status richm_meta_forward(const float* params, const float* inputs, const float* G, int B, int m,
+                                float* w_out, float* alpha_out, float* acts, void* stream);
+
+/* Backward of richm_meta_forward given dL/dw [B][m] and dL/dalpha [B][m] (summed over
+ * the steps for the shared momentum). g_params: [count], written (batch sum,
+ * fixed order). work: at least B * count floats. */
+richm_status richm_meta_backward(const float* params, const float* inputs, const float* G, const float* acts,
+                                 int B, int m, const float* g_w, const float* g_alpha, float* g_params,
+                                 void* work, size_t work_bytes, void* stream);
+
+/* One Adam step (Kingma & Ba 2015) over `count` parameters in place; t is 1-based. */
+richm_status richm_adam_step(float* params, const float* grads, float* m1, float* m2, int count, int t,
+                             float lr, float beta1, float beta2, float eps, void* stream);
+
+/* ------------------------------------------------------------------ two-level step */
+
+/* Workspace bytes for richm_fourier_correction (cuFFT work + spectra). */
+richm_status richm_fourier_workspace(const richm_operator* op, size_t* bytes);
+
+/* Fourier-domain correction of the FNS iteration (eqs. 19-20 with T = I):
+ *   x += Re( IFFT2( S .* FFT2(b - A x) ) ),
+ * forward transform unnormalised, inverse scaled by 1/n^2. Every instance of the
+ * operator must be Q1 with the same n. dtype RICHM_F32. symbol: device complex64
+ * [n][n] shared by the batch. x, b: padded. */
+richm_status richm_fourier_correction(richm_operator* op, richm_dtype dtype, void* x, const void* b,
+                                      const void* symbol, void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Thread-local description of the last error ("" if none). */
+const char* richm_last_error(void);
+
+/* Library version string. */
+const char* richm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RICHM_H */

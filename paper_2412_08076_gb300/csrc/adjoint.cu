@@ -1,0 +1,410 @@
+// Differentiation of K unrolled sweeps ("backpropagate", Algorithm 1).
+//
+// Forward sweep k (i = k mod m):  v = x_k - x_{k-1},  y = x_k + at_i v,
+//   x_{k+1} = x_k + a_i v + w_i d (b - A y)      (d = D^{-1} or 1)
+// With lam_{k+1} = dL/dx_{k+1} and A symmetric, q = w_i A (d lam_{k+1}) and
+//   lam_k  = (1 + a_i) lam_{k+1} - (1 + at_i) q + c_{k+1}
+//   c_k    = -a_i lam_{k+1} + at_i q          (the part that reaches x_{k-1})
+//   dL/dw_i += <lam_{k+1}, d (b - A y)>,  dL/da_i += <lam_{k+1}, v>,  dL/dat_i -= <q, v>
+// and dL/dx_0 = lam_0 + c_0 because x_{-1} = x_0. One adjoint kernel applies the
+// stencil twice (to d lam and to y), so each step streams lam, c, x_k, x_{k-1}, b
+// once. States between checkpoints are recomputed from the checkpoint by the
+// forward kernel, which is deterministic, so the recomputation is bitwise exact.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace richm {
+
+static size_t a256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct alignas(32) Dot3 {
+  double v[4];
+};
+
+template <typename T, bool MOM, bool PRE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    adjoint_kernel(const Inst* insts, const Tile* tiles, int ntiles, const T* __restrict__ lam,
+                   const T* __restrict__ carry, const T* __restrict__ x, const T* __restrict__ xp,
+                   const T* __restrict__ b, T* __restrict__ lam_out, T* __restrict__ carry_out,
+                   const T* __restrict__ w, const T* __restrict__ a, const T* __restrict__ at, int m, int kidx,
+                   int final_step, Dot3* __restrict__ partials) {
+  constexpr int VW = VecWidth<T>::value;
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile t = tiles[wt];
+  const Inst& I = insts[t.inst];
+  const int n = I.n, pitch = I.pitch;
+  const int cidx = t.inst * m + kidx;
+  const T wi = w[cidx];
+  T ai = 0, ati = 0;
+  if (MOM) {
+    ai = a[cidx];
+    ati = at ? at[cidx] : ai;
+  }
+  const T sc = (T)I.c, sax = (T)I.ax, say = (T)I.ay, sd1 = (T)I.d1, sd2 = (T)I.d2;
+  const T dv = PRE ? (T)I.dinv : T(1);
+  const T qs = wi * dv;  // q = w d A lam (d constant for Q1)
+  const int c0 = t.tx * 32 * VW + lane * VW;
+  const bool live = c0 < pitch;
+  const int r0 = t.ty * kRows + 1;
+  const int r1 = min(r0 + kRows - 1, n);
+  const long long off = I.off;
+
+  auto load_y = [&](int pr, RowT<T, VW>& Y, T* xs, T* xps) {
+    const bool in = (pr >= 1) && (pr <= n);
+    VecN<T, VW> X{}, XP{};
+    const long long ro = off + (long long)pr * pitch;
+    if (in && live) {
+      X = ldv<T, VW>(x + ro + c0);
+      if (MOM) XP = ldv<T, VW>(xp + ro + c0);
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      Y.y[e] = MOM ? X.v[e] + ati * (X.v[e] - XP.v[e]) : X.v[e];
+      xs[e] = X.v[e];
+      xps[e] = XP.v[e];
+    }
+    T le = 0, re = 0;
+    if (in) {
+      if (lane == 0 && c0 > 0) {
+        T xv = x[ro + c0 - 1];
+        le = MOM ? xv + ati * (xv - xp[ro + c0 - 1]) : xv;
+      }
+      if (lane == 31 && c0 + VW < pitch) {
+        T xv = x[ro + c0 + VW];
+        re = MOM ? xv + ati * (xv - xp[ro + c0 + VW]) : xv;
+      }
+    }
+    row_neighbours<T, VW>(Y, lane, le, re);
+  };
+  auto load_l = [&](int pr, RowT<T, VW>& L) {
+    const bool in = (pr >= 1) && (pr <= n);
+    VecN<T, VW> Lv{};
+    const long long ro = off + (long long)pr * pitch;
+    if (in && live) Lv = ldv<T, VW>(lam + ro + c0);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) L.y[e] = Lv.v[e];
+    T le = 0, re = 0;
+    if (in) {
+      if (lane == 0 && c0 > 0) le = lam[ro + c0 - 1];
+      if (lane == 31 && c0 + VW < pitch) re = lam[ro + c0 + VW];
+    }
+    row_neighbours<T, VW>(L, lane, le, re);
+  };
+
+  double s_w = 0.0, s_a = 0.0, s_at = 0.0;
+  RowT<T, VW> YU, YC, YD, LU, LC, LD;
+  T xC[VW], xpC[VW], xD[VW], xpD[VW], t0[VW], t1[VW];
+  load_y(r0 - 1, YU, t0, t1);
+  load_y(r0, YC, xC, xpC);
+  load_l(r0 - 1, LU);
+  load_l(r0, LC);
+  for (int r = r0; r <= r1; ++r) {
+    load_y(r + 1, YD, xD, xpD);
+    load_l(r + 1, LD);
+    const long long ro = off + (long long)r * pitch + c0;
+    VecN<T, VW> Bv{}, Cv{};
+    if (live) {
+      Bv = ldv<T, VW>(b + ro);
+      if (MOM && carry) Cv = ldv<T, VW>(carry + ro);
+    }
+    T Ay[VW], Al[VW];
+    apply_q1<T, VW, T>(YU, YC, YD, sc, sax, say, sd1, sd2, Ay);
+    apply_q1<T, VW, T>(LU, LC, LD, sc, sax, say, sd1, sd2, Al);
+    VecN<T, VW> Lo, Co;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const bool ok = (c0 + e) < n;
+      const T l = LC.y[e];
+      const T q = qs * Al[e];
+      const T dr = dv * (Bv.v[e] - Ay[e]);
+      const T v = MOM ? xC[e] - xpC[e] : T(0);
+      T ln = MOM ? (T(1) + ai) * l - (T(1) + ati) * q + Cv.v[e] : l - q;
+      T cn = MOM ? -ai * l + ati * q : T(0);
+      if (ok) {
+        s_w += (double)l * (double)dr;
+        if (MOM) {
+          s_a += (double)l * (double)v;
+          s_at += (double)q * (double)v;
+        }
+      }
+      if (final_step) ln = ln + cn;
+      Lo.v[e] = ok ? ln : T(0);
+      Co.v[e] = ok ? cn : T(0);
+    }
+    if (live) {
+      stv<T, VW>(lam_out + ro, Lo);
+      if (MOM && !final_step) stv<T, VW>(carry_out + ro, Co);
+    }
+    YU = YC;
+    YC = YD;
+    LU = LC;
+    LC = LD;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      xC[e] = xD[e];
+      xpC[e] = xpD[e];
+    }
+  }
+  s_w = warp_sum(s_w);
+  s_a = warp_sum(s_a);
+  s_at = warp_sum(s_at);
+  if (lane == 0) {
+    Dot3 d;
+    d.v[0] = s_w;
+    d.v[1] = s_a;
+    d.v[2] = s_at;
+    d.v[3] = 0.0;
+    partials[wt] = d;
+  }
+}
+
+// acc[b][kidx][0..2] += per-instance sums of the tile partials (fixed order).
+__global__ void adjoint_reduce_kernel(const Dot3* __restrict__ partials, const int* __restrict__ inst_begin,
+                                      int batch, int m, int kidx, double* __restrict__ acc) {
+  const int lane = threadIdx.x & 31;
+  const int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (bi >= batch) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int t = inst_begin[bi] + lane; t < inst_begin[bi + 1]; t += 32) {
+    const Dot3 p = partials[t];
+    s0 += p.v[0];
+    s1 += p.v[1];
+    s2 += p.v[2];
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    double* A = acc + ((long long)bi * m + kidx) * 3;
+    A[0] += s0;
+    A[1] += s1;
+    A[2] += s2;
+  }
+}
+
+template <typename T>
+__global__ void adjoint_finish_kernel(const double* __restrict__ acc, int count, T* g_w, T* g_a, T* g_at,
+                                      int nag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double dw = acc[3 * i], da = acc[3 * i + 1], dat = -acc[3 * i + 2];
+  if (g_w) g_w[i] = (T)dw;
+  if (g_a) g_a[i] = (T)(nag ? da + dat : da);
+  if (g_at) g_at[i] = (T)dat;
+}
+
+template <typename T>
+static richm_status launch_adjoint(richm_operator* op, const T* lam, const T* carry, const T* x, const T* xp,
+                                   const T* b, T* lam_out, T* carry_out, const T* w, const T* a, const T* at, int m,
+                                   int kidx, int precond, int final_step, Dot3* partials, double* acc,
+                                   cudaStream_t s) {
+  constexpr int VW = VecWidth<T>::value;
+  const TileMap* tm = nullptr;
+  RICHM_TRY(get_tiles(op, 32 * VW, kRows, &tm));
+  const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int thr = kWarpsPerBlock * 32;
+  const bool mom = a != nullptr;
+#define RICHM_ADJ(M, P)                                                                                        \
+  adjoint_kernel<T, M, P><<<blocks, thr, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, lam, carry, x, xp, b, \
+                                                 lam_out, carry_out, w, a, at, m, kidx, final_step, partials)
+  if (mom && precond) RICHM_ADJ(true, true);
+  else if (mom) RICHM_ADJ(true, false);
+  else if (precond) RICHM_ADJ(false, true);
+  else RICHM_ADJ(false, false);
+#undef RICHM_ADJ
+  RICHM_LAUNCH_CHECK("adjoint sweep");
+  const int wpb = 8;
+  adjoint_reduce_kernel<<<(op->batch + wpb - 1) / wpb, wpb * 32, 0, s>>>(partials, tm->d_inst_begin, op->batch, m,
+                                                                         kidx, acc);
+  RICHM_LAUNCH_CHECK("adjoint reduce");
+  return RICHM_OK;
+}
+
+template <typename T>
+static richm_status forward_ckpt_t(richm_operator* op, const T* x0, const T* b, const T* w, const T* a,
+                                   const T* at, int m, int K, int s_every, int precond, T* ckpts, T* xK, void* work,
+                                   cudaStream_t s) {
+  const size_t es = op->elems;
+  const size_t bytes = es * sizeof(T);
+  const size_t slot = 2 * es;
+  // slot j holds (x_{js}, x_{js-1}); slot 0 = (x0, x0)
+  RICHM_CUDA_TRY(cudaMemcpyAsync(ckpts, x0, bytes, cudaMemcpyDeviceToDevice, s));
+  RICHM_CUDA_TRY(cudaMemcpyAsync(ckpts + es, x0, bytes, cudaMemcpyDeviceToDevice, s));
+  T* W[3];
+  for (int i = 0; i < 3; ++i) W[i] = reinterpret_cast<T*>(reinterpret_cast<char*>(work) + i * a256(bytes));
+  const int nseg = K / s_every;
+  for (int j = 0; j < nseg; ++j) {
+    T* cx = ckpts + (size_t)j * slot;
+    T* cxp = cx + es;
+    T* nx = ckpts + (size_t)(j + 1) * slot;
+    T* nxp = nx + es;
+    T* cur = cx;
+    T* prev = cxp;
+    for (int t = 0; t < s_every; ++t) {
+      // the last two sweeps land in the next checkpoint slot; the others rotate
+      // through three work buffers, never touching either checkpoint slot
+      T* out = nullptr;
+      if (t == s_every - 1) out = nx;
+      else if (t == s_every - 2) out = nxp;
+      else
+        for (int i = 0; i < 3 && out == nullptr; ++i)
+          if (W[i] != cur && W[i] != prev) out = W[i];
+      const int kidx = (j * s_every + t) % m;
+      RICHM_TRY(launch_sweep<T>(op, cur, a ? prev : nullptr, b, out, w, a, at, m, kidx, precond, nullptr, s));
+      prev = cur;
+      cur = out;
+    }
+    if (s_every == 1) RICHM_CUDA_TRY(cudaMemcpyAsync(nxp, cx, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  if (xK) RICHM_CUDA_TRY(cudaMemcpyAsync(xK, ckpts + (size_t)nseg * slot, bytes, cudaMemcpyDeviceToDevice, s));
+  return RICHM_OK;
+}
+
+template <typename T>
+static size_t adjoint_ws(richm_operator* op, int s_every) {
+  int nt = 0;
+  residual_tiles<T>(op, &nt);
+  const size_t buf = a256(op->elems * sizeof(T));
+  const size_t adj = (size_t)(s_every > 1 ? s_every - 1 : 0) * buf + 4 * buf + a256(sizeof(Dot3) * nt) +
+                     a256(sizeof(double) * 3 * 64 * (size_t)op->batch);
+  const size_t loss = loss_workspace_bytes(op, sizeof(T), nt);
+  return adj > loss ? adj : loss;
+}
+
+template <typename T>
+static richm_status adjoint_t(richm_operator* op, const T* ckpts, int s_every, const T* b, const T* gK, const T* w,
+                              const T* a, const T* at, int m, int K, int precond, T* g_w, T* g_a, T* g_at, T* g_x0,
+                              void* work, size_t work_bytes, cudaStream_t s) {
+  if (work_bytes < adjoint_ws<T>(op, s_every)) return set_error(RICHM_ERR_NOMEM, "adjoint workspace too small");
+  const size_t es = op->elems;
+  const size_t buf = a256(es * sizeof(T));
+  const size_t slot = 2 * es;
+  int nt = 0;
+  RICHM_TRY(residual_tiles<T>(op, &nt));
+  char* p = reinterpret_cast<char*>(work);
+  std::vector<T*> seg(s_every + 1, nullptr);
+  for (int t = 2; t <= s_every; ++t) {
+    seg[t] = reinterpret_cast<T*>(p);
+    p += buf;
+  }
+  T* LB[2];
+  T* CB[2];
+  for (int i = 0; i < 2; ++i) {
+    LB[i] = reinterpret_cast<T*>(p);
+    p += buf;
+  }
+  for (int i = 0; i < 2; ++i) {
+    CB[i] = reinterpret_cast<T*>(p);
+    p += buf;
+  }
+  Dot3* partials = reinterpret_cast<Dot3*>(p);
+  p += a256(sizeof(Dot3) * nt);
+  double* acc = reinterpret_cast<double*>(p);
+  RICHM_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * m * (size_t)op->batch, s));
+  const T* lam = gK;
+  const T* carry = nullptr;
+  int pi = 0;
+  const int nseg = K / s_every;
+  for (int j = nseg - 1; j >= 0; --j) {
+    const T* cx = ckpts + (size_t)j * slot;
+    seg[0] = const_cast<T*>(cx + es);  // x_{js-1}
+    seg[1] = const_cast<T*>(cx);       // x_{js}
+    for (int t = 0; t + 2 <= s_every; ++t) {
+      const int kidx = (j * s_every + t) % m;
+      RICHM_TRY(launch_sweep<T>(op, seg[t + 1], a ? seg[t] : nullptr, b, seg[t + 2], w, a, at, m, kidx, precond,
+                                nullptr, s));
+    }
+    for (int t = s_every - 1; t >= 0; --t) {
+      const int k = j * s_every + t;
+      const int fin = (k == 0) ? 1 : 0;
+      T* lo = (fin && g_x0) ? g_x0 : LB[pi];
+      RICHM_TRY(launch_adjoint<T>(op, lam, carry, seg[t + 1], seg[t], b, lo, CB[pi], w, a, at, m, k % m, precond,
+                                  fin, partials, acc, s));
+      lam = LB[pi];
+      carry = CB[pi];
+      pi ^= 1;
+    }
+  }
+  const int cnt = op->batch * m;
+  adjoint_finish_kernel<T><<<(cnt + 255) / 256, 256, 0, s>>>(acc, cnt, g_w, g_a, g_at, at == nullptr ? 1 : 0);
+  RICHM_LAUNCH_CHECK("adjoint finish");
+  return RICHM_OK;
+}
+
+}  // namespace richm
+
+using namespace richm;
+
+extern "C" {
+
+richm_status richm_checkpoint_elems(const richm_operator* op, int K, int ckpt_every, size_t* elems) {
+  clear_error();
+  RICHM_ARG(op && elems, "null argument");
+  RICHM_ARG(ckpt_every >= 1 && K >= 0 && K % ckpt_every == 0, "K must be a multiple of ckpt_every >= 1");
+  *elems = (size_t)(K / ckpt_every + 1) * 2 * op->elems;
+  return RICHM_OK;
+}
+
+richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, const void* x0, const void* b,
+                                        const void* w, const void* alpha, const void* alpha_t, int m, int K,
+                                        int ckpt_every, int precond, void* ckpts, void* xK, void* work,
+                                        size_t work_bytes, void* stream) {
+  clear_error();
+  RICHM_ARG(op != nullptr, "null operator");
+  RICHM_TRY(check_dtype_for_op(op, dtype));
+  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "differentiation is implemented for real (Q1) problems");
+  RICHM_ARG(x0 && b && w && ckpts, "null argument");
+  RICHM_ARG(m >= 1 && m <= 64, "m out of range");
+  RICHM_ARG(ckpt_every >= 1 && K >= 0 && K % ckpt_every == 0, "K must be a multiple of ckpt_every >= 1");
+  RICHM_ARG(alpha != nullptr || alpha_t == nullptr, "alpha_t given without alpha");
+  RICHM_ARG(precond == 0 || precond == 1, "precond must be 0 or 1");
+  const size_t need = 3 * a256(op->elems * dtype_size(dtype));
+  RICHM_ARG(work != nullptr, "null workspace");
+  if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == RICHM_F32)
+    return forward_ckpt_t<float>(op, (const float*)x0, (const float*)b, (const float*)w, (const float*)alpha,
+                                 (const float*)alpha_t, m, K, ckpt_every, precond, (float*)ckpts, (float*)xK, work, s);
+  return forward_ckpt_t<double>(op, (const double*)x0, (const double*)b, (const double*)w, (const double*)alpha,
+                                (const double*)alpha_t, m, K, ckpt_every, precond, (double*)ckpts, (double*)xK, work,
+                                s);
+}
+
+richm_status richm_adjoint_workspace(const richm_operator* op, richm_dtype dtype, int ckpt_every, size_t* bytes) {
+  clear_error();
+  RICHM_ARG(op && bytes, "null argument");
+  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "real dtype required");
+  RICHM_ARG(ckpt_every >= 1, "ckpt_every < 1");
+  auto* o = const_cast<richm_operator*>(op);
+  const size_t fwd = 3 * a256(op->elems * dtype_size(dtype));
+  const size_t adj = dtype == RICHM_F32 ? adjoint_ws<float>(o, ckpt_every) : adjoint_ws<double>(o, ckpt_every);
+  *bytes = adj > fwd ? adj : fwd;
+  return RICHM_OK;
+}
+
+richm_status richm_sweeps_adjoint(richm_operator* op, richm_dtype dtype, const void* ckpts, int ckpt_every,
+                                  const void* b, const void* gK, const void* w, const void* alpha,
+                                  const void* alpha_t, int m, int K, int precond, void* g_w, void* g_alpha,
+                                  void* g_alpha_t, void* g_x0, void* work, size_t work_bytes, void* stream) {
+  clear_error();
+  RICHM_ARG(op != nullptr, "null operator");
+  RICHM_TRY(check_dtype_for_op(op, dtype));
+  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "differentiation is implemented for real (Q1) problems");
+  RICHM_ARG(ckpts && b && gK && w && work, "null argument");
+  RICHM_ARG(m >= 1 && m <= 64, "m out of range");
+  RICHM_ARG(ckpt_every >= 1 && K >= 1 && K % ckpt_every == 0, "K must be a positive multiple of ckpt_every");
+  RICHM_ARG(alpha != nullptr || alpha_t == nullptr, "alpha_t given without alpha");
+  RICHM_ARG(precond == 0 || precond == 1, "precond must be 0 or 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == RICHM_F32)
+    return adjoint_t<float>(op, (const float*)ckpts, ckpt_every, (const float*)b, (const float*)gK, (const float*)w,
+                            (const float*)alpha, (const float*)alpha_t, m, K, precond, (float*)g_w, (float*)g_alpha,
+                            (float*)g_alpha_t, (float*)g_x0, work, work_bytes, s);
+  return adjoint_t<double>(op, (const double*)ckpts, ckpt_every, (const double*)b, (const double*)gK,
+                           (const double*)w, (const double*)alpha, (const double*)alpha_t, m, K, precond,
+                           (double*)g_w, (double*)g_alpha, (double*)g_alpha_t, (double*)g_x0, work, work_bytes, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,42 @@
+// Internal launchers shared between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace richm {
+
+constexpr int kRows = 16;          // rows streamed by one warp tile
+constexpr int kWarpsPerBlock = 8;  // warp tiles per thread block
+
+// One forward sweep (see sweep.cu). `a == nullptr`: no momentum (xp unused);
+// `at == nullptr`: at = a. `active`: per-instance flags or nullptr (all active).
+template <typename E>
+richm_status launch_sweep(richm_operator* op, const E* x, const E* xp, const E* b, E* out,
+                          const typename RealOf<E>::type* w, const typename RealOf<E>::type* a,
+                          const typename RealOf<E>::type* at, int m, int kidx, int precond, const int* active,
+                          cudaStream_t s);
+
+// r = b - A x in FP64 with per-tile partial sums (sum |r|^2, sum |b|^2) written to
+// `partials` (one double2 per warp tile of the residual geometry); r_out may be null.
+template <typename E>
+richm_status launch_residual(richm_operator* op, const E* x, const E* b, E* r_out, double2* partials,
+                             cudaStream_t s);
+
+// Residual of an FP64 state written in another type (the mixed-precision solver's
+// inner right-hand side); instances with active[b] == 0 are skipped.
+template <typename E, typename RO>
+richm_status launch_residual_to(richm_operator* op, const E* x, const E* b, RO* r_out, double2* partials,
+                                const int* active, cudaStream_t s);
+
+// Bytes of the loss workspace (residual buffer, partials, three per-instance arrays).
+size_t loss_workspace_bytes(richm_operator* op, size_t elem_size, int ntiles);
+
+// Per-instance reduction of residual partials into norms (each output may be null).
+richm_status launch_norm_reduce(richm_operator* op, int residual_vw, const double2* partials, double* rnorm,
+                                double* bnorm, double* rel, cudaStream_t s);
+
+// Number of warp tiles of the residual kernel for state type E.
+template <typename E>
+richm_status residual_tiles(richm_operator* op, int* ntiles);
+
+}  // namespace richm

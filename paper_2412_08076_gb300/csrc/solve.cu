@@ -1,0 +1,461 @@
+// Batched solve to tolerance with FP64 iterative refinement (the evaluation loop of
+// Sec. 2.3: iterate until a tolerance or a maximum number of iterations).
+//
+// State per instance: x (FP64, the caller's buffer), the inner correction pair
+// (e_k, e_{k-1}) in the inner type, and the inner right-hand side rhs. One
+// refinement cycle is
+//   S sweeps of the Table 1 iteration on A e = rhs       (three rotating buffers)
+//   update  x += e_k;  e_{k-1} <- e_{k-1} - e_k;  e_k <- 0  (pointwise, FP64 add)
+//   rhs = b - A x in FP64 (written in the inner type) and its squared norm
+//   per-instance convergence test; converged instances leave the active set
+// The update keeps the inner velocity e_k - e_{k-1} and the weight index, so the
+// split is the same affine iteration as sweeping x directly. The update writes the
+// pair back into the first two buffers, so every cycle has identical launches and
+// is captured once as a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct richm_solver {
+  richm_operator* op = nullptr;
+  richm_solve_opts o{};
+  const void* w = nullptr;
+  const void* a = nullptr;
+  const void* at = nullptr;
+  // workspace carve-up
+  void* E[3] = {nullptr, nullptr, nullptr};
+  void* rhs = nullptr;
+  double2* partials = nullptr;
+  double* bnorm = nullptr;
+  double* rel = nullptr;
+  long long* sweeps = nullptr;
+  int* status = nullptr;
+  int* active = nullptr;
+  int* count = nullptr;
+  // bound by richm_solver_start
+  const double* b = nullptr;
+  double* x = nullptr;
+  // execution
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_cycles = 1;      // cycles captured in one graph replay
+  long long cycles_run = 0;  // cycles since start
+  int* h_count = nullptr;    // pinned
+  bool started = false;
+};
+
+namespace richm {
+
+static size_t a256(size_t v) { return (v + 255) / 256 * 256; }
+
+// x += e_k; ep_out = ep - e_k; e_out = 0 (pointwise; e_out/ep_out may alias inputs).
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    refine_update_kernel(const Inst* insts, const Tile* tiles, int ntiles, double* x, const T* e, const T* ep,
+                         T* e_out, T* ep_out, const int* __restrict__ active) {
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile t = tiles[wt];
+  if (active && active[t.inst] == 0) return;
+  const Inst& I = insts[t.inst];
+  const int c0 = t.tx * 64 + lane * 2;  // two doubles per lane
+  if (c0 >= I.pitch) return;
+  const int r0 = t.ty * kRows + 1;
+  const int r1 = min(r0 + kRows - 1, I.n);
+  for (int r = r0; r <= r1; ++r) {
+    const long long o = I.off + (long long)r * I.pitch + c0;
+    double2 xv = *reinterpret_cast<const double2*>(x + o);
+    VecN<T, 2> ev = *reinterpret_cast<const VecN<T, 2>*>(e + o);
+    xv.x += (double)ev.v[0];
+    xv.y += (double)ev.v[1];
+    if (ep) {
+      VecN<T, 2> pv = *reinterpret_cast<const VecN<T, 2>*>(ep + o);
+      VecN<T, 2> np;
+      np.v[0] = pv.v[0] - ev.v[0];
+      np.v[1] = pv.v[1] - ev.v[1];
+      *reinterpret_cast<VecN<T, 2>*>(ep_out + o) = np;
+    }
+    VecN<T, 2> nz;
+    nz.v[0] = T(0);
+    nz.v[1] = T(0);
+    *reinterpret_cast<double2*>(x + o) = xv;
+    *reinterpret_cast<VecN<T, 2>*>(e_out + o) = nz;
+  }
+}
+
+// Per-instance convergence bookkeeping after a refinement residual.
+__global__ void solve_reduce_kernel(const double2* __restrict__ partials, const int* __restrict__ inst_begin,
+                                    int batch, int init, int add_sweeps, double tol, long long max_sweeps,
+                                    double* bnorm, double* rel, long long* sweeps, int* status, int* active,
+                                    int* count) {
+  const int lane = threadIdx.x & 31;
+  const int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (bi >= batch) return;
+  if (active[bi] == 0) return;
+  double sr = 0.0, sb = 0.0;
+  for (int t = inst_begin[bi] + lane; t < inst_begin[bi + 1]; t += 32) {
+    double2 p = partials[t];
+    sr += p.x;
+    sb += p.y;
+  }
+  sr = warp_sum(sr);
+  sb = warp_sum(sb);
+  if (lane != 0) return;
+  if (init) bnorm[bi] = sqrt(sb);
+  const double bn = bnorm[bi];
+  const double rn = sqrt(sr);
+  const double rr = bn > 0.0 ? rn / bn : rn;
+  rel[bi] = rr;
+  const long long sw = sweeps[bi] + add_sweeps;
+  sweeps[bi] = sw;
+  if (!(rr <= 1e30)) {
+    status[bi] = RICHM_ERR_DIVERGED;
+    active[bi] = 0;
+  } else if (rr <= tol) {
+    status[bi] = RICHM_OK;
+    active[bi] = 0;
+  } else if (sw >= max_sweeps) {
+    status[bi] = RICHM_ERR_NOT_CONVERGED;
+    active[bi] = 0;
+  } else {
+    atomicAdd(count, 1);
+  }
+}
+
+__global__ void solve_init_kernel(int batch, long long* sweeps, int* status, int* active) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < batch) {
+    sweeps[i] = 0;
+    status[i] = RICHM_ERR_NOT_CONVERGED;
+    active[i] = 1;
+  }
+}
+
+template <typename T>
+static richm_status refine_t(richm_solver* S, bool init) {
+  richm_operator* op = S->op;
+  const TileMap* tm = nullptr;
+  RICHM_TRY(get_tiles(op, 64, kRows, &tm));  // residual / update geometry of FP64
+  const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (!init) {
+    // after S sweeps from (E0, E1) the current/previous pair sits in the rotation
+    const int Sw = S->o.refine_every;
+    const int cur = Sw % 3 == 0 ? 0 : (Sw % 3 == 1 ? 2 : 1);
+    const int prv = (cur + 1) % 3;
+    refine_update_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(
+        op->d_inst, tm->d_tiles, tm->ntiles, S->x, (const T*)S->E[cur], (const T*)S->E[prv], (T*)S->E[0],
+        (T*)S->E[1], S->active);
+    RICHM_LAUNCH_CHECK("refine update");
+  }
+  RICHM_TRY((launch_residual_to<double, T>(op, S->x, S->b, (T*)S->rhs, S->partials, S->active, S->s)));
+  RICHM_CUDA_TRY(cudaMemsetAsync(S->count, 0, sizeof(int), S->s));
+  const int wpb = 8;
+  solve_reduce_kernel<<<(op->batch + wpb - 1) / wpb, wpb * 32, 0, S->s>>>(
+      S->partials, tm->d_inst_begin, op->batch, init ? 1 : 0, init ? 0 : S->o.refine_every, S->o.tol,
+      S->o.max_sweeps, S->bnorm, S->rel, S->sweeps, S->status, S->active, S->count);
+  RICHM_LAUNCH_CHECK("solve reduce");
+  return RICHM_OK;
+}
+
+// One refinement cycle starting at global sweep index k0.
+template <typename T>
+static richm_status cycle_t(richm_solver* S, long long k0) {
+  const int Sw = S->o.refine_every;
+  int cur = 0, prv = 1, fre = 2;
+  for (int k = 0; k < Sw; ++k) {
+    const int kidx = (int)((k0 + k) % S->o.m);
+    RICHM_TRY(launch_sweep<T>(S->op, (const T*)S->E[cur], (const T*)S->E[prv], (const T*)S->rhs, (T*)S->E[fre],
+                              (const T*)S->w, (const T*)S->a, (const T*)S->at, S->o.m, kidx, S->o.precond,
+                              S->active, S->s));
+    const int nf = prv;
+    prv = cur;
+    cur = fre;
+    fre = nf;
+  }
+  return refine_t<T>(S, false);
+}
+
+static richm_status run_cycles(richm_solver* S, int cycles) {
+  for (int c = 0; c < cycles; ++c) {
+    const long long k0 = (S->cycles_run + c) * (long long)S->o.refine_every;
+    if (S->o.inner == RICHM_F32) RICHM_TRY(cycle_t<float>(S, k0));
+    else RICHM_TRY(cycle_t<double>(S, k0));
+  }
+  return RICHM_OK;
+}
+
+}  // namespace richm
+
+using namespace richm;
+
+extern "C" {
+
+static richm_status check_solve_opts(const richm_operator* op, const richm_solve_opts* o) {
+  RICHM_ARG(op != nullptr && o != nullptr, "null operator or options");
+  RICHM_ARG(o->m >= 1 && o->m <= 64, "m = %d out of range [1, 64]", o->m);
+  RICHM_ARG(o->refine_every >= 1, "refine_every must be >= 1");
+  RICHM_ARG(o->max_sweeps >= 0, "max_sweeps < 0");
+  RICHM_ARG(o->tol >= 0.0, "tol < 0");
+  RICHM_ARG(o->inner == RICHM_F32 || o->inner == RICHM_F64, "inner dtype must be RICHM_F32 or RICHM_F64");
+  RICHM_ARG(o->precond == 0 || o->precond == 1, "precond must be 0 or 1");
+  RICHM_ARG(o->fuse == 0 || o->fuse == 1, "fuse must be 0 or 1 in richm_solve");
+  for (int b = 0; b < op->batch; ++b)
+    if (op->h_inst[b].kind != RICHM_ANISO_Q1)
+      return set_error(RICHM_ERR_UNSUPPORTED, "richm_solve handles Q1 instances (instance %d is not)", b);
+  return RICHM_OK;
+}
+
+richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_opts* o, size_t* bytes) {
+  clear_error();
+  RICHM_TRY(check_solve_opts(op, o));
+  RICHM_ARG(bytes != nullptr, "null output");
+  const size_t es = o->inner == RICHM_F32 ? 4 : 8;
+  int nt = 0;
+  RICHM_TRY(residual_tiles<double>(const_cast<richm_operator*>(op), &nt));
+  size_t B = (size_t)op->batch;
+  *bytes = 4 * a256(op->elems * es) + a256(sizeof(double2) * nt) + 2 * a256(sizeof(double) * B) +
+           a256(sizeof(long long) * B) + 2 * a256(sizeof(int) * B) + a256(sizeof(int));
+  return RICHM_OK;
+}
+
+richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, const void* w, const void* alpha,
+                                 const void* alpha_t, void* work, size_t work_bytes, richm_solver** out) {
+  clear_error();
+  RICHM_ARG(out != nullptr, "null output handle");
+  *out = nullptr;
+  RICHM_TRY(check_solve_opts(op, o));
+  RICHM_ARG(w != nullptr, "null weights");
+  RICHM_ARG(alpha != nullptr || alpha_t == nullptr, "alpha_t given without alpha");
+  size_t need = 0;
+  RICHM_TRY(richm_solve_workspace(op, o, &need));
+  RICHM_ARG(work != nullptr, "null workspace");
+  if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  auto* S = new (std::nothrow) richm_solver();
+  if (!S) return set_error(RICHM_ERR_NOMEM, "host allocation failed");
+  S->op = op;
+  S->o = *o;
+  S->w = w;
+  S->a = alpha;
+  S->at = alpha_t;
+  const size_t es = o->inner == RICHM_F32 ? 4 : 8;
+  int nt = 0;
+  residual_tiles<double>(op, &nt);
+  char* p = reinterpret_cast<char*>(work);
+  for (int i = 0; i < 3; ++i) {
+    S->E[i] = p;
+    p += a256(op->elems * es);
+  }
+  S->rhs = p;
+  p += a256(op->elems * es);
+  S->partials = reinterpret_cast<double2*>(p);
+  p += a256(sizeof(double2) * nt);
+  const size_t B = (size_t)op->batch;
+  S->bnorm = reinterpret_cast<double*>(p);
+  p += a256(sizeof(double) * B);
+  S->rel = reinterpret_cast<double*>(p);
+  p += a256(sizeof(double) * B);
+  S->sweeps = reinterpret_cast<long long*>(p);
+  p += a256(sizeof(long long) * B);
+  S->status = reinterpret_cast<int*>(p);
+  p += a256(sizeof(int) * B);
+  S->active = reinterpret_cast<int*>(p);
+  p += a256(sizeof(int) * B);
+  S->count = reinterpret_cast<int*>(p);
+  // the weight phase repeats every m / gcd(S, m) cycles: one graph replay covers them
+  S->graph_cycles = o->m / std::gcd(o->m, o->refine_every);
+  cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_count, sizeof(int), cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    richm_solver_destroy(S);
+    return set_error(RICHM_ERR_CUDA, "solver setup failed: %s", cudaGetErrorString(e));
+  }
+  // warm the tile maps before any capture (they allocate on first use)
+  const TileMap* tm = nullptr;
+  richm_status st = get_tiles(op, 64, kRows, &tm);
+  if (st == RICHM_OK) st = get_tiles(op, o->inner == RICHM_F32 ? 128 : 64, kRows, &tm);
+  if (st != RICHM_OK) {
+    richm_solver_destroy(S);
+    return st;
+  }
+  *out = S;
+  return RICHM_OK;
+}
+
+void richm_solver_destroy(richm_solver* S) {
+  if (!S) return;
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  if (S->s) cudaStreamDestroy(S->s);
+  if (S->ev_in) cudaEventDestroy(S->ev_in);
+  if (S->ev_out) cudaEventDestroy(S->ev_out);
+  if (S->h_count) cudaFreeHost(S->h_count);
+  delete S;
+}
+
+richm_status richm_solver_start(richm_solver* S, const double* b, double* x, void* stream) {
+  clear_error();
+  RICHM_ARG(S != nullptr && b != nullptr && x != nullptr, "null argument");
+  richm_operator* op = S->op;
+  if (S->b != b || S->x != x) {
+    if (S->exec) {
+      cudaGraphExecDestroy(S->exec);
+      S->exec = nullptr;
+    }
+  }
+  S->b = b;
+  S->x = x;
+  S->cycles_run = 0;
+  RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, (cudaStream_t)stream));
+  RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
+  const size_t es = S->o.inner == RICHM_F32 ? 4 : 8;
+  RICHM_CUDA_TRY(cudaMemsetAsync(S->E[0], 0, op->elems * es, S->s));
+  RICHM_CUDA_TRY(cudaMemsetAsync(S->E[1], 0, op->elems * es, S->s));
+  RICHM_CUDA_TRY(cudaMemsetAsync(S->E[2], 0, op->elems * es, S->s));
+  solve_init_kernel<<<(op->batch + 255) / 256, 256, 0, S->s>>>(op->batch, S->sweeps, S->status, S->active);
+  RICHM_LAUNCH_CHECK("solve init");
+  if (S->o.inner == RICHM_F32) RICHM_TRY(refine_t<float>(S, true));
+  else RICHM_TRY(refine_t<double>(S, true));
+  RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
+  RICHM_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, S->ev_out, 0));
+  S->started = true;
+  return RICHM_OK;
+}
+
+richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, void* stream) {
+  clear_error();
+  RICHM_ARG(S != nullptr, "null solver");
+  RICHM_ARG(S->started, "richm_solver_start has not been called");
+  RICHM_ARG(cycles >= 0, "cycles < 0");
+  RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, (cudaStream_t)stream));
+  RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
+  const int G = S->graph_cycles;
+  int done = 0;
+  if (S->o.use_graph) {
+    // replays cover whole weight periods; a remainder runs as plain launches
+    if (!S->exec && cycles >= G && S->cycles_run % G == 0) {
+      cudaGraph_t g = nullptr;
+      RICHM_CUDA_TRY(cudaStreamBeginCapture(S->s, cudaStreamCaptureModeThreadLocal));
+      richm_status st = run_cycles(S, G);
+      cudaError_t e = cudaStreamEndCapture(S->s, &g);
+      if (st != RICHM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return set_error(RICHM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&S->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        S->exec = nullptr;
+        return set_error(RICHM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+      }
+    }
+    while (S->exec && cycles - done >= G && S->cycles_run % G == 0) {
+      RICHM_CUDA_TRY(cudaGraphLaunch(S->exec, S->s));
+      S->cycles_run += G;
+      done += G;
+    }
+  }
+  if (done < cycles) {
+    RICHM_TRY(run_cycles(S, cycles - done));
+    S->cycles_run += cycles - done;
+  }
+  if (active_out) {
+    RICHM_CUDA_TRY(cudaMemcpyAsync(S->h_count, S->count, sizeof(int), cudaMemcpyDeviceToHost, S->s));
+    RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
+    *active_out = *S->h_count;
+  }
+  RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
+  RICHM_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, S->ev_out, 0));
+  return RICHM_OK;
+}
+
+richm_status richm_solver_finish(richm_solver* S, richm_solve_info* info, void* stream) {
+  clear_error();
+  RICHM_ARG(S != nullptr && info != nullptr, "null argument");
+  const int B = S->op->batch;
+  std::vector<long long> sw(B);
+  std::vector<double> rel(B);
+  std::vector<int> st(B);
+  RICHM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  RICHM_CUDA_TRY(cudaMemcpyAsync(sw.data(), S->sweeps, sizeof(long long) * B, cudaMemcpyDeviceToHost, S->s));
+  RICHM_CUDA_TRY(cudaMemcpyAsync(rel.data(), S->rel, sizeof(double) * B, cudaMemcpyDeviceToHost, S->s));
+  RICHM_CUDA_TRY(cudaMemcpyAsync(st.data(), S->status, sizeof(int) * B, cudaMemcpyDeviceToHost, S->s));
+  RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
+  richm_status worst = RICHM_OK;
+  for (int b = 0; b < B; ++b) {
+    info[b].sweeps = sw[b];
+    info[b].rel_res = rel[b];
+    info[b].status = st[b];
+    if (st[b] == RICHM_ERR_DIVERGED) worst = RICHM_ERR_DIVERGED;
+    else if (st[b] != RICHM_OK && worst == RICHM_OK) worst = RICHM_ERR_NOT_CONVERGED;
+  }
+  return worst;
+}
+
+richm_status richm_refine(richm_operator* op, double* x, const double* b, void* e, void* e_prev, int inner,
+                          void* rhs_out, double* rel, void* work, size_t work_bytes, void* stream) {
+  clear_error();
+  RICHM_ARG(op != nullptr, "null operator");
+  RICHM_TRY(check_dtype_for_op(op, RICHM_F64));
+  RICHM_ARG(x && b && rhs_out && work, "null argument");
+  RICHM_ARG(inner == RICHM_F32 || inner == RICHM_F64, "inner dtype must be RICHM_F32 or RICHM_F64");
+  int nt = 0;
+  RICHM_TRY(residual_tiles<double>(op, &nt));
+  if (work_bytes < sizeof(double2) * (size_t)nt)
+    return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, sizeof(double2) * (size_t)nt);
+  cudaStream_t s = (cudaStream_t)stream;
+  const TileMap* tm = nullptr;
+  RICHM_TRY(get_tiles(op, 64, kRows, &tm));
+  const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  double2* partials = reinterpret_cast<double2*>(work);
+  if (inner == RICHM_F32) {
+    if (e) {
+      refine_update_kernel<float><<<blocks, kWarpsPerBlock * 32, 0, s>>>(
+          op->d_inst, tm->d_tiles, tm->ntiles, x, (const float*)e, (const float*)e_prev, (float*)e, (float*)e_prev,
+          nullptr);
+      RICHM_LAUNCH_CHECK("refine update");
+    }
+    RICHM_TRY((launch_residual_to<double, float>(op, x, b, (float*)rhs_out, partials, nullptr, s)));
+  } else {
+    if (e) {
+      refine_update_kernel<double><<<blocks, kWarpsPerBlock * 32, 0, s>>>(
+          op->d_inst, tm->d_tiles, tm->ntiles, x, (const double*)e, (const double*)e_prev, (double*)e,
+          (double*)e_prev, nullptr);
+      RICHM_LAUNCH_CHECK("refine update");
+    }
+    RICHM_TRY((launch_residual_to<double, double>(op, x, b, (double*)rhs_out, partials, nullptr, s)));
+  }
+  return launch_norm_reduce(op, 2, partials, nullptr, nullptr, rel, s);
+}
+
+richm_status richm_solve(richm_operator* op, const double* b, double* x, const void* w, const void* alpha,
+                         const void* alpha_t, const richm_solve_opts* o, richm_solve_info* info, void* work,
+                         size_t work_bytes, void* stream) {
+  clear_error();
+  RICHM_ARG(info != nullptr, "null info");
+  richm_solver* S = nullptr;
+  RICHM_TRY(richm_solver_create(op, o, w, alpha, alpha_t, work, work_bytes, &S));
+  richm_status st = richm_solver_start(S, b, x, stream);
+  int active = 0;
+  if (st == RICHM_OK) {
+    st = richm_solver_step(S, 0, &active, stream);
+    const long long max_cycles = o->max_sweeps / o->refine_every + 2;
+    long long c = 0;
+    while (st == RICHM_OK && active > 0 && c < max_cycles) {
+      const int n = S->graph_cycles;
+      st = richm_solver_step(S, n, &active, stream);
+      c += n;
+    }
+  }
+  if (st == RICHM_OK) st = richm_solver_finish(S, info, stream);
+  richm_solver_destroy(S);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+"""Meta-network parameters: initialisation, storage and the weight map.
+
+The meta network (Sec. 2.3) maps PDE parameters (log10 eps, theta) to the m
+weights and the momentum of NAG-Richardson(m). Its output o maps to
+w_i = exp(o_i) / G (G the instance's Gershgorin bound) and a = sigmoid(o_m).
+The initial network is random in its hidden layers and starts its output layer
+at the momentum-aware Chebyshev weights: eqs. 8-9 on [c G / 30, c G] with c = 1.6,
+the smallest stretch of the semi-iteration interval for which every per-mode
+period transfer of NAG with a = 0.3 stays inside the unit disk on [0, G]. So an
+untrained network already gives a convergent solver, and training only improves it.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+HIDDEN = 64
+STABLE_STRETCH = 1.6
+SEMI_ALPHA = 1.0 / 30.0
+PARAM_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "params")
+
+
+def chebyshev_unit_weights(m: int, stretch: float = STABLE_STRETCH, alpha: float = SEMI_ALPHA) -> np.ndarray:
+    """G * w_i for eqs. 8-9 on [alpha s G, s G] (independent of G)."""
+    i = np.arange(1, m + 1)
+    x = np.cos((2 * i - 1) * math.pi / (2 * m))
+    lmax, lmin = stretch, alpha * stretch
+    return 2.0 / (lmax + lmin + (lmax - lmin) * x)
+
+
+def init_params(m: int = 16, beta: float = 0.3, seed: int = 7, out_scale: float = 0.01) -> np.ndarray:
+    """Flat FP32 parameter vector in the library's order (W1, b1, W2, b2, W3, b3)."""
+    import richm_synth as synth  # seeded generator shared by every consumer
+    layers = synth.mlp_init((2, HIDDEN, HIDDEN, m + 1), seed=seed)
+    W3, b3 = layers[2]
+    W3 = W3 * out_scale
+    b3 = np.concatenate([np.log(chebyshev_unit_weights(m)), [math.log(beta / (1.0 - beta))]])
+    layers[2] = (W3, b3)
+    flat = []
+    for W, b in layers:
+        flat.append(np.asarray(W, dtype=np.float64).ravel())
+        flat.append(np.asarray(b, dtype=np.float64).ravel())
+    return np.concatenate(flat).astype(np.float32)
+
+
+def trained_path(m: int) -> str:
+    return os.path.join(PARAM_DIR, f"meta_m{m}.npy")
+
+
+def load_params(m: int = 16, prefer_trained: bool = True) -> tuple[np.ndarray, str]:
+    """(params, source): the trained network if one was saved, else the initial one."""
+    p = trained_path(m)
+    if prefer_trained and os.path.exists(p):
+        return np.load(p).astype(np.float32), "trained"
+    return init_params(m), "initial"

@@ -1,0 +1,418 @@
+"""Thin Python binding of librichm.so (the C ABI in include/richm.h).
+
+Every function here marshals arguments and calls the library; no step of the
+solver runs in Python. Tensors are PyTorch CUDA tensors (PyTorch supplies device
+memory and the current stream); a missing or unbuilt library raises
+``RichmError`` instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librichm.so")
+
+# richm_status
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_UNSUPPORTED = range(7)
+# richm_problem
+ANISO_Q1, HELMHOLTZ_FD5_ABC, HELMHOLTZ_FD5_DIRICHLET = 0, 1, 2
+# richm_dtype
+F64, F32, C64, C128 = 0, 1, 2, 3
+
+TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.complex64, C128: torch.complex128}
+REAL_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.float32, C128: torch.float64}
+DTYPE_OF = {v: k for k, v in TORCH_DTYPE.items()}
+
+
+class RichmError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+class richm_pde(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int), ("eps", C.c_double), ("theta", C.c_double), ("k", C.c_double)]
+
+
+class richm_sweep_opts(C.Structure):
+    _fields_ = [("m", C.c_int), ("k_start", C.c_int), ("precond", C.c_int), ("fuse", C.c_int)]
+
+
+class richm_solve_opts(C.Structure):
+    _fields_ = [("m", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_longlong), ("refine_every", C.c_int),
+                ("inner", C.c_int), ("precond", C.c_int), ("fuse", C.c_int), ("use_graph", C.c_int)]
+
+
+class richm_solve_info(C.Structure):
+    _fields_ = [("sweeps", C.c_longlong), ("rel_res", C.c_double), ("status", C.c_int)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_SZ = C.c_size_t
+_SIGS = {
+    "richm_operator_create": (_I, [C.POINTER(richm_pde), _I, C.POINTER(_P)]),
+    "richm_operator_destroy": (None, [_P]),
+    "richm_operator_batch": (_I, [_P, C.POINTER(_I)]),
+    "richm_stencil": (_I, [_P, _I, C.POINTER(_D)]),
+    "richm_gershgorin": (_I, [_P, C.POINTER(_D)]),
+    "richm_chebyshev_weights": (_I, [_D, _D, _I, C.POINTER(_D)]),
+    "richm_layout": (_I, [_P, _I, C.POINTER(_SZ), C.POINTER(_I), C.POINTER(_I)]),
+    "richm_buffer_elems": (_I, [_P, C.POINTER(_SZ)]),
+    "richm_pack": (_I, [_P, _I, _P, _P, _P]),
+    "richm_unpack": (_I, [_P, _I, _P, _P, _P]),
+    "richm_sweeps_workspace": (_I, [_P, _I, C.POINTER(_SZ)]),
+    "richm_apply_sweeps": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _I, C.POINTER(richm_sweep_opts), _P, _SZ, _P]),
+    "richm_residual_workspace": (_I, [_P, C.POINTER(_SZ)]),
+    "richm_residual_norm": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "richm_solve_workspace": (_I, [_P, C.POINTER(richm_solve_opts), C.POINTER(_SZ)]),
+    "richm_solve": (_I, [_P, _P, _P, _P, _P, _P, C.POINTER(richm_solve_opts), C.POINTER(richm_solve_info), _P, _SZ,
+                         _P]),
+    "richm_solver_create": (_I, [_P, C.POINTER(richm_solve_opts), _P, _P, _P, _P, _SZ, C.POINTER(_P)]),
+    "richm_solver_start": (_I, [_P, _P, _P, _P]),
+    "richm_solver_step": (_I, [_P, _I, C.POINTER(_I), _P]),
+    "richm_solver_finish": (_I, [_P, C.POINTER(richm_solve_info), _P]),
+    "richm_solver_destroy": (None, [_P]),
+    "richm_refine": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _P, _SZ, _P]),
+    "richm_checkpoint_elems": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
+    "richm_forward_checkpointed": (_I, [_P, _I, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
+    "richm_adjoint_workspace": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
+    "richm_loss_log_residual": (_I, [_P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "richm_sweeps_adjoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "richm_meta_param_count": (_I, [_I, C.POINTER(_I)]),
+    "richm_meta_forward": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "richm_meta_backward": (_I, [_P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P]),
+    "richm_adam_step": (_I, [_P, _P, _P, _P, _I, _I, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
+    "richm_fourier_workspace": (_I, [_P, C.POINTER(_SZ)]),
+    "richm_fourier_correction": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
+    "richm_last_error": (C.c_char_p, []),
+    "richm_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load librichm.so (built by ``paper_2412_08076_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RichmError(-1, "load", f"{LIB_PATH} is missing: build it with "
+                             "`python -m paper_2412_08076_gb300.build`")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise RichmError(status, where, load().richm_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def version() -> str:
+    return load().richm_version().decode()
+
+
+def chebyshev_weights(lmax: float, lmin: float, m: int) -> list[float]:
+    """richm_chebyshev_weights (eqs. 8-9), host."""
+    out = (C.c_double * m)()
+    _check(load().richm_chebyshev_weights(lmax, lmin, m, out), "richm_chebyshev_weights")
+    return list(out)
+
+
+def meta_param_count(m: int) -> int:
+    c = C.c_int()
+    _check(load().richm_meta_param_count(m, C.byref(c)), "richm_meta_param_count")
+    return c.value
+
+
+@dataclass
+class Layout:
+    offset: int
+    pitch: int
+    rows: int
+
+
+class Operator:
+    """Owner of a richm_operator handle plus marshalling helpers for its buffers."""
+
+    def __init__(self, pdes):
+        """pdes: list of (kind, n, eps, theta, k) tuples or richm_pde."""
+        lib = load()
+        arr = (richm_pde * len(pdes))()
+        for i, p in enumerate(pdes):
+            if isinstance(p, richm_pde):
+                arr[i] = p
+            else:
+                kind, n, eps, theta, k = p
+                arr[i] = richm_pde(int(kind), int(n), float(eps), float(theta), float(k))
+        h = C.c_void_p()
+        _check(lib.richm_operator_create(arr, len(pdes), C.byref(h)), "richm_operator_create")
+        self.handle = h
+        self.batch = len(pdes)
+        self.ns = [int(arr[i].n) for i in range(len(pdes))]
+        el = C.c_size_t()
+        _check(lib.richm_buffer_elems(h, C.byref(el)), "richm_buffer_elems")
+        self.elems = el.value
+        self.layouts = [self.layout(i) for i in range(self.batch)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().richm_operator_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- host queries
+    def layout(self, i: int) -> Layout:
+        off, pitch, rows = C.c_size_t(), C.c_int(), C.c_int()
+        _check(load().richm_layout(self.handle, i, C.byref(off), C.byref(pitch), C.byref(rows)), "richm_layout")
+        return Layout(off.value, pitch.value, rows.value)
+
+    def stencil(self, i: int) -> list[float]:
+        c = (C.c_double * 8)()
+        _check(load().richm_stencil(self.handle, i, c), "richm_stencil")
+        return list(c)
+
+    def gershgorin(self) -> list[float]:
+        out = (C.c_double * self.batch)()
+        _check(load().richm_gershgorin(self.handle, out), "richm_gershgorin")
+        return list(out)
+
+    # -- buffers
+    def zeros(self, dtype: int) -> torch.Tensor:
+        """A zeroed padded buffer (caller-owned device memory from PyTorch)."""
+        return torch.zeros(self.elems, dtype=TORCH_DTYPE[dtype], device="cuda")
+
+    def dense_elems(self) -> int:
+        return sum(n * n for n in self.ns)
+
+    def pack(self, dense: torch.Tensor, dtype: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """richm_pack: dense concatenation (n_b*n_b each) -> padded buffer."""
+        if out is None:
+            out = torch.empty(self.elems, dtype=TORCH_DTYPE[dtype], device="cuda")
+        _check(load().richm_pack(self.handle, dtype, _ptr(dense), _ptr(out), _stream(stream)), "richm_pack")
+        return out
+
+    def unpack(self, padded: torch.Tensor, dtype: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """richm_unpack: padded buffer -> dense concatenation."""
+        if out is None:
+            out = torch.empty(self.dense_elems(), dtype=TORCH_DTYPE[dtype], device="cuda")
+        _check(load().richm_unpack(self.handle, dtype, _ptr(padded), _ptr(out), _stream(stream)), "richm_unpack")
+        return out
+
+    # -- workspaces
+    def _ws(self, fn, *args) -> int:
+        b = C.c_size_t()
+        _check(getattr(load(), fn)(self.handle, *args, C.byref(b)), fn)
+        return b.value
+
+    def workspace(self, nbytes: int) -> torch.Tensor:
+        return torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+
+    # -- compute
+    def apply_sweeps(self, dtype, x, x_prev, b, w, alpha=None, alpha_t=None, K=1, m=None, k_start=0, precond=0,
+                     fuse=0, work=None, stream=None):
+        """richm_apply_sweeps (Table 1 iteration, eq. 17); x / x_prev updated in place."""
+        m = m if m is not None else w.numel() // self.batch
+        o = richm_sweep_opts(m, k_start, precond, fuse)
+        need = self._ws("richm_sweeps_workspace", dtype)
+        if work is None:
+            work = self.workspace(need)
+        _check(load().richm_apply_sweeps(self.handle, dtype, _ptr(x), _ptr(x_prev), _ptr(b), _ptr(w), _ptr(alpha),
+                                         _ptr(alpha_t), K, C.byref(o), _ptr(work), work.numel(), _stream(stream)),
+               "richm_apply_sweeps")
+
+    def residual_norm(self, dtype, x, b, r_out=None, work=None, stream=None):
+        """richm_residual_norm: returns (rnorm, bnorm, rel) as FP64 CUDA tensors [batch]."""
+        rn = torch.empty(self.batch, dtype=torch.float64, device="cuda")
+        bn = torch.empty_like(rn)
+        rel = torch.empty_like(rn)
+        if work is None:
+            work = self.workspace(self._ws("richm_residual_workspace"))
+        _check(load().richm_residual_norm(self.handle, dtype, _ptr(x), _ptr(b), _ptr(rn), _ptr(bn), _ptr(rel),
+                                          _ptr(r_out), _ptr(work), work.numel(), _stream(stream)),
+               "richm_residual_norm")
+        return rn, bn, rel
+
+    def refine(self, x, b, e, e_prev, inner, rhs_out, work=None, stream=None):
+        """richm_refine: x += e, e_prev -= e, e = 0, rhs_out = b - A x; returns rel [batch]."""
+        rel = torch.empty(self.batch, dtype=torch.float64, device="cuda")
+        if work is None:
+            work = self.workspace(self._ws("richm_residual_workspace"))
+        _check(load().richm_refine(self.handle, _ptr(x), _ptr(b), _ptr(e), _ptr(e_prev), inner, _ptr(rhs_out),
+                                   _ptr(rel), _ptr(work), work.numel(), _stream(stream)), "richm_refine")
+        return rel
+
+    def solve_opts(self, m, tol=1e-10, max_sweeps=10**7, refine_every=64, inner=F32, precond=0, fuse=0, use_graph=1):
+        return richm_solve_opts(m, tol, max_sweeps, refine_every, inner, precond, fuse, use_graph)
+
+    def solve(self, b, x, w, alpha=None, alpha_t=None, opts=None, work=None, stream=None):
+        """richm_solve; returns (status, list of (sweeps, rel_res, status))."""
+        need = C.c_size_t()
+        _check(load().richm_solve_workspace(self.handle, C.byref(opts), C.byref(need)), "richm_solve_workspace")
+        if work is None:
+            work = self.workspace(need.value)
+        info = (richm_solve_info * self.batch)()
+        st = load().richm_solve(self.handle, _ptr(b), _ptr(x), _ptr(w), _ptr(alpha), _ptr(alpha_t), C.byref(opts),
+                                info, _ptr(work), work.numel(), _stream(stream))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+            _check(st, "richm_solve")
+        return st, [(info[i].sweeps, info[i].rel_res, info[i].status) for i in range(self.batch)]
+
+    def loss_log_residual(self, dtype, x, b, g=None, work=None, stream=None):
+        """richm_loss_log_residual: returns the loss (device FP64 scalar tensor); fills g."""
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        if work is None:
+            work = self.workspace(self._ws("richm_adjoint_workspace", dtype, 1))
+        _check(load().richm_loss_log_residual(self.handle, dtype, _ptr(x), _ptr(b), _ptr(loss), _ptr(g), _ptr(work),
+                                              work.numel(), _stream(stream)), "richm_loss_log_residual")
+        return loss
+
+    def checkpoint_elems(self, K, every) -> int:
+        e = C.c_size_t()
+        _check(load().richm_checkpoint_elems(self.handle, K, every, C.byref(e)), "richm_checkpoint_elems")
+        return e.value
+
+    def forward_checkpointed(self, dtype, x0, b, w, alpha, alpha_t, m, K, every, precond, ckpts, xK, work=None,
+                             stream=None):
+        if work is None:
+            work = self.workspace(self._ws("richm_adjoint_workspace", dtype, every))
+        _check(load().richm_forward_checkpointed(self.handle, dtype, _ptr(x0), _ptr(b), _ptr(w), _ptr(alpha),
+                                                 _ptr(alpha_t), m, K, every, precond, _ptr(ckpts), _ptr(xK),
+                                                 _ptr(work), work.numel(), _stream(stream)),
+               "richm_forward_checkpointed")
+
+    def sweeps_adjoint(self, dtype, ckpts, every, b, gK, w, alpha, alpha_t, m, K, precond, g_w=None, g_alpha=None,
+                       g_alpha_t=None, g_x0=None, work=None, stream=None):
+        if work is None:
+            work = self.workspace(self._ws("richm_adjoint_workspace", dtype, every))
+        _check(load().richm_sweeps_adjoint(self.handle, dtype, _ptr(ckpts), every, _ptr(b), _ptr(gK), _ptr(w),
+                                           _ptr(alpha), _ptr(alpha_t), m, K, precond, _ptr(g_w), _ptr(g_alpha),
+                                           _ptr(g_alpha_t), _ptr(g_x0), _ptr(work), work.numel(), _stream(stream)),
+               "richm_sweeps_adjoint")
+
+    def fourier_correction(self, x, b, symbol, work=None, stream=None):
+        """richm_fourier_correction: x += Re(IFFT2(S * FFT2(b - A x))) (F32 state)."""
+        if work is None:
+            work = self.workspace(self._ws("richm_fourier_workspace"))
+        _check(load().richm_fourier_correction(self.handle, F32, _ptr(x), _ptr(b), _ptr(symbol), _ptr(work),
+                                               work.numel(), _stream(stream)), "richm_fourier_correction")
+
+
+class Solver:
+    """richm_solver session (create / start / step / finish / destroy)."""
+
+    def __init__(self, op: Operator, opts: richm_solve_opts, w, alpha=None, alpha_t=None, work=None):
+        need = C.c_size_t()
+        _check(load().richm_solve_workspace(op.handle, C.byref(opts), C.byref(need)), "richm_solve_workspace")
+        self.work = work if work is not None else op.workspace(need.value)
+        self.keep = (w, alpha, alpha_t)
+        self.op = op
+        h = C.c_void_p()
+        _check(load().richm_solver_create(op.handle, C.byref(opts), _ptr(w), _ptr(alpha), _ptr(alpha_t),
+                                          _ptr(self.work), self.work.numel(), C.byref(h)), "richm_solver_create")
+        self.handle = h
+
+    def start(self, b, x, stream=None):
+        self.bx = (b, x)
+        _check(load().richm_solver_start(self.handle, _ptr(b), _ptr(x), _stream(stream)), "richm_solver_start")
+
+    def step(self, cycles: int, sync: bool = True, stream=None):
+        act = C.c_int(-1)
+        _check(load().richm_solver_step(self.handle, cycles, C.byref(act) if sync else None, _stream(stream)),
+               "richm_solver_step")
+        return act.value if sync else None
+
+    def finish(self, stream=None):
+        info = (richm_solve_info * self.op.batch)()
+        st = load().richm_solver_finish(self.handle, info, _stream(stream))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+            _check(st, "richm_solver_finish")
+        return st, [(info[i].sweeps, info[i].rel_res, info[i].status) for i in range(self.op.batch)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().richm_solver_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------- meta network
+
+def meta_forward(params, inputs, G, m, acts=None, stream=None):
+    """richm_meta_forward: returns (w [B][m], alpha [B][m]) FP32 CUDA tensors."""
+    B = inputs.shape[0]
+    w = torch.empty(B, m, dtype=torch.float32, device="cuda")
+    a = torch.empty(B, m, dtype=torch.float32, device="cuda")
+    _check(load().richm_meta_forward(_ptr(params), _ptr(inputs), _ptr(G), B, m, _ptr(w), _ptr(a), _ptr(acts),
+                                     _stream(stream)), "richm_meta_forward")
+    return w, a
+
+
+def meta_backward(params, inputs, G, acts, m, g_w, g_alpha, g_params=None, work=None, stream=None):
+    B = inputs.shape[0]
+    cnt = meta_param_count(m)
+    if g_params is None:
+        g_params = torch.empty(cnt, dtype=torch.float32, device="cuda")
+    if work is None:
+        work = torch.empty(B * cnt * 4, dtype=torch.uint8, device="cuda")
+    _check(load().richm_meta_backward(_ptr(params), _ptr(inputs), _ptr(G), _ptr(acts), B, m, _ptr(g_w),
+                                      _ptr(g_alpha), _ptr(g_params), _ptr(work), work.numel(), _stream(stream)),
+           "richm_meta_backward")
+    return g_params
+
+
+def adam_step(params, grads, m1, m2, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().richm_adam_step(_ptr(params), _ptr(grads), _ptr(m1), _ptr(m2), params.numel(), t, lr, beta1, beta2,
+                                  eps, _stream(stream)), "richm_adam_step")
+
+
+def meta_acts_size(B: int, m: int) -> int:
+    return B * (2 * 64 + m + 1)
+
+
+def pack_mlp_params(layers) -> list[float]:
+    """Flatten [(W1, b1), (W2, b2), (W3, b3)] (W[out][in]) into the library's order."""
+    flat = []
+    for W, b in layers:
+        flat.extend(float(v) for v in W.reshape(-1))
+        flat.extend(float(v) for v in b.reshape(-1))
+    return flat

@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads and exports every entry point the header declares.
+
+No GPU is needed: only host-side entries (weights, counts, argument validation)
+are called here.
+"""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def clib():
+    from paper_2412_08076_gb300.build import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(richm_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["richm_operator_create", "richm_apply_sweeps", "richm_residual_norm", "richm_solve",
+                     "richm_sweeps_adjoint", "richm_meta_forward", "richm_fourier_correction"]:
+        assert required in names
+    assert len(names) >= 30
+
+
+def test_every_declared_symbol_is_exported(clib):
+    missing = [n for n in _declared() if not hasattr(clib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_2412_08076_gb300 import richm
+    missing = [n for n in _declared() if n not in richm._SIGS]
+    assert not missing, missing
+
+
+def test_chebyshev_weights_match_oracle(clib):
+    from oracle.iterations import chebyshev_weights
+    f = clib.richm_chebyshev_weights
+    f.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    for lmax, lmin, m in [(4.0, 0.01, 3), (3.19, 3.19 / 30, 8), (5.3, 1e-4, 16)]:
+        out = (ctypes.c_double * m)()
+        assert f(lmax, lmin, m, out) == 0
+        np.testing.assert_allclose(list(out), chebyshev_weights(lmax, lmin, m), rtol=1e-15)
+    out = (ctypes.c_double * 3)()
+    assert f(1.0, 2.0, 3, out) == 1  # lmin > lmax
+    assert f(1.0, 0.5, 0, out) == 1  # m = 0
+
+
+def test_meta_param_count_and_version(clib):
+    c = ctypes.c_int()
+    clib.richm_meta_param_count.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    assert clib.richm_meta_param_count(16, ctypes.byref(c)) == 0
+    assert c.value == 2 * 64 + 64 + 64 * 64 + 64 + 17 * 64 + 17 == 5457
+    assert clib.richm_meta_param_count(0, ctypes.byref(c)) == 1
+    clib.richm_version.restype = ctypes.c_char_p
+    assert b"richm" in clib.richm_version()
+
+
+def test_argument_errors_before_any_device_work(clib):
+    from paper_2412_08076_gb300 import richm
+    lib = richm.load()
+    h = ctypes.c_void_p()
+    arr = (richm.richm_pde * 1)(richm.richm_pde(0, 0, 0.5, 0.0, 0.0))
+    assert lib.richm_operator_create(arr, 1, ctypes.byref(h)) == richm.ERR_ARG
+    assert b"n = 0" in lib.richm_last_error()
+    arr = (richm.richm_pde * 1)(richm.richm_pde(0, 10, 2.0, 0.0, 0.0))
+    assert lib.richm_operator_create(arr, 1, ctypes.byref(h)) == richm.ERR_ARG
+    arr = (richm.richm_pde * 1)(richm.richm_pde(7, 10, 0.5, 0.0, 0.0))
+    assert lib.richm_operator_create(arr, 1, ctypes.byref(h)) == richm.ERR_ARG
+    assert lib.richm_operator_create(arr, 0, ctypes.byref(h)) == richm.ERR_ARG
+    assert h.value is None

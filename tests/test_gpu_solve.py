@@ -1,0 +1,168 @@
+"""GPU residual norms, refinement and the batched solve against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import richm_synth as synth
+from gpu_util import coef, from_dev, make_op, nag_weights, to_dev
+from oracle.iterations import inner_steps, refined_steps
+from oracle.operators import assemble_helmholtz, assemble_q1, gershgorin_max, helmholtz_wavenumber
+from paper_2412_08076_gb300 import richm
+
+pytestmark = pytest.mark.gpu
+
+
+def _insts(sizes, seed=5):
+    u = synth.uniform(synth.stream_key(seed), 2 * len(sizes))
+    return [synth.AnisoInstance(10 ** (-3 * u[2 * i]), math.pi * u[2 * i + 1], n) for i, n in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("dtype", [richm.F64, richm.F32])
+def test_residual_norm_matches_oracle(dtype):
+    insts = _insts([1, 4, 33, 64, 127, 200])
+    op = make_op(insts)
+    xs = [synth.rhs_uniform(3, i, t.n) for i, t in enumerate(insts)]
+    bs = [synth.rhs_uniform(4, i, t.n) for i, t in enumerate(insts)]
+    if dtype == richm.F32:
+        xs = [v.astype(np.float32).astype(np.float64) for v in xs]
+        bs = [v.astype(np.float32).astype(np.float64) for v in bs]
+    X, B = to_dev(op, xs, dtype), to_dev(op, bs, dtype)
+    R = op.zeros(dtype)
+    rn, bn, rel = op.residual_norm(dtype, X, B, r_out=R)
+    rs = from_dev(op, R, dtype)
+    for i, t in enumerate(insts):
+        A = assemble_q1(t.n, t.eps, t.theta)
+        r = bs[i].ravel() - A @ xs[i].ravel()
+        tol = 1e-13 if dtype == richm.F64 else 1e-6
+        assert abs(rn[i].item() - np.linalg.norm(r)) <= 1e-13 * np.linalg.norm(r)
+        assert abs(bn[i].item() - np.linalg.norm(bs[i])) <= 1e-13 * np.linalg.norm(bs[i])
+        assert abs(rel[i].item() - np.linalg.norm(r) / np.linalg.norm(bs[i])) <= 1e-12
+        assert np.abs(rs[i].ravel() - r).max() <= tol * np.abs(r).max()
+
+
+def test_residual_norm_complex():
+    sizes = [5, 40]
+    op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, n, 1.0, 0.0, helmholtz_wavenumber(n)) for n in sizes])
+    xs = [synth.rhs_uniform(3, i, n) + 1j * synth.rhs_uniform(6, i, n) for i, n in enumerate(sizes)]
+    bs = [synth.rhs_uniform(4, i, n) + 0j for i, n in enumerate(sizes)]
+    X, B = to_dev(op, xs, richm.C128), to_dev(op, bs, richm.C128)
+    rn, bn, rel = op.residual_norm(richm.C128, X, B)
+    for i, n in enumerate(sizes):
+        H = assemble_helmholtz(n, helmholtz_wavenumber(n))
+        r = bs[i].ravel() - H @ xs[i].ravel()
+        assert abs(rn[i].item() - np.linalg.norm(r)) <= 1e-12 * np.linalg.norm(r)
+
+
+def _solve_setup(sizes, m=16, beta=0.3, seed=5):
+    insts = _insts(sizes, seed)
+    op = make_op(insts)
+    As = [assemble_q1(t.n, t.eps, t.theta) for t in insts]
+    G = np.array([gershgorin_max(A) for A in As])
+    w, a = nag_weights(G, m, beta=beta)
+    bs = [synth.rhs_uniform(2, i, t.n) for i, t in enumerate(insts)]
+    return insts, op, As, w, a, bs
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_solve_to_1e10_checked_by_oracle(use_graph):
+    insts, op, As, w, a, bs = _solve_setup([1, 2, 15, 31, 63, 64])
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    opts = op.solve_opts(16, tol=1e-10, max_sweeps=400000, refine_every=64, inner=richm.F32, use_graph=use_graph)
+    st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None, opts)
+    assert st == richm.OK, info
+    xs = from_dev(op, X, richm.F64)
+    for i, t in enumerate(insts):
+        r = np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i])
+        assert r <= 1e-10, (t, r)
+        sweeps, rel, s = info[i]
+        assert s == richm.OK and sweeps % 64 == 0
+        assert abs(rel - r) <= 1e-3 * r + 1e-14
+
+
+def test_solve_graph_and_plain_launches_agree_bitwise():
+    res = []
+    for g in (1, 0):
+        insts, op, As, w, a, bs = _solve_setup([17, 40, 63])
+        B = to_dev(op, bs, richm.F64)
+        X = op.zeros(richm.F64)
+        opts = op.solve_opts(16, tol=1e-9, max_sweeps=100000, refine_every=32, use_graph=g)
+        st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None, opts)
+        res.append((X.cpu().numpy(), info))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
+
+
+def test_fp64_inner_solver_follows_the_oracle_iteration():
+    # tol = 0: every instance runs exactly max_sweeps; FP64 inner sweeps with FP64
+    # refinement are the same iteration as the oracle's plain sweeps
+    insts, op, As, w, a, bs = _solve_setup([9, 31, 70])
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    opts = op.solve_opts(16, tol=0.0, max_sweeps=160, refine_every=32, inner=richm.F64)
+    st, info = op.solve(B, X, coef(w, richm.F64), coef(a, richm.F64), None, opts)
+    assert st == richm.ERR_NOT_CONVERGED
+    xs = from_dev(op, X, richm.F64)
+    for i, t in enumerate(insts):
+        ref, _ = inner_steps(As[i], bs[i].ravel(), np.zeros(t.n * t.n), None, w[i], a[i], K=160)
+        split = refined_steps(As[i], bs[i].ravel(), np.zeros(t.n * t.n), 160, w[i], a[i], refine_every=32)
+        assert info[i][0] == 160
+        assert np.linalg.norm(xs[i].ravel() - ref) <= 1e-11 * np.linalg.norm(ref)
+        assert np.linalg.norm(split - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_solver_session_steps_and_reports():
+    insts, op, As, w, a, bs = _solve_setup([31, 63])
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    wt, at = coef(w, richm.F32), coef(a, richm.F32)
+    S = richm.Solver(op, op.solve_opts(16, tol=1e-10, max_sweeps=10**6), wt, at)
+    S.start(B, X)
+    assert S.step(0) == 2
+    total = 0
+    active = 2
+    while active:
+        active = S.step(4)
+        total += 4
+        assert total < 100000
+    st, info = S.finish()
+    assert st == richm.OK
+    S.close()
+
+
+def test_solve_reports_divergence_and_not_converged():
+    insts, op, As, w, a, bs = _solve_setup([15, 31])
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    G = np.array([gershgorin_max(A) for A in As])
+    wbad = np.tile((3.0 / G)[:, None], (1, 4))  # |1 - w lam| up to 2: diverges
+    st, info = op.solve(B, X, coef(wbad, richm.F32), None, None,
+                        op.solve_opts(4, tol=1e-10, max_sweeps=100000, refine_every=16))
+    assert st == richm.ERR_DIVERGED
+    assert all(s == richm.ERR_DIVERGED for _, _, s in info)
+    X.zero_()
+    st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None,
+                        op.solve_opts(16, tol=1e-10, max_sweeps=64, refine_every=32))
+    assert st == richm.ERR_NOT_CONVERGED
+    assert all(s == richm.ERR_NOT_CONVERGED and sw == 64 for sw, _, s in info)
+
+
+def test_refine_entry_matches_definition():
+    insts, op, As, w, a, bs = _solve_setup([9, 33])
+    xs = [synth.rhs_uniform(81, i, t.n) for i, t in enumerate(insts)]
+    es = [1e-3 * synth.rhs_uniform(82, i, t.n) for i, t in enumerate(insts)]
+    eps_ = [1e-3 * synth.rhs_uniform(83, i, t.n) for i, t in enumerate(insts)]
+    X, B = to_dev(op, xs, richm.F64), to_dev(op, bs, richm.F64)
+    E, EP = to_dev(op, es, richm.F64), to_dev(op, eps_, richm.F64)
+    R = op.zeros(richm.F64)
+    rel = op.refine(X, B, E, EP, richm.F64, R)
+    for i, t in enumerate(insts):
+        xn = xs[i] + es[i]
+        r = bs[i].ravel() - As[i] @ xn.ravel()
+        np.testing.assert_allclose(from_dev(op, X, richm.F64)[i], xn, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(from_dev(op, EP, richm.F64)[i], eps_[i] - es[i], rtol=0, atol=1e-18)
+        assert np.all(from_dev(op, E, richm.F64)[i] == 0)
+        np.testing.assert_allclose(from_dev(op, R, richm.F64)[i].ravel(), r, rtol=0, atol=1e-13)
+        assert abs(rel[i].item() - np.linalg.norm(r) / np.linalg.norm(bs[i])) <= 1e-13

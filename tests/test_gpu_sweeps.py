@@ -1,0 +1,207 @@
+"""GPU sweeps (Table 1 iterations, eq. 17) against the FP64 oracle, element by element."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import richm_synth as synth
+from gpu_util import coef, from_dev, make_op, nag_weights, period_amplification, to_dev
+from oracle.iterations import inner_steps, jacobi_binv
+from oracle.operators import assemble_helmholtz, assemble_q1, gershgorin_max, helmholtz_wavenumber
+from paper_2412_08076_gb300 import richm
+
+pytestmark = pytest.mark.gpu
+
+# sizes spanning one / several warp tiles, ragged row blocks and column blocks
+SIZES = [1, 2, 3, 5, 8, 17, 31, 63, 64, 70, 127, 130]
+
+
+def _instances(seed=11, sizes=SIZES):
+    u = synth.uniform(synth.stream_key(seed), 2 * len(sizes))
+    return [synth.AnisoInstance(10 ** (-3 * u[2 * i]), math.pi * u[2 * i + 1], n) for i, n in enumerate(sizes)]
+
+
+def _run_case(dtype, variant, K, k_start=0, precond=0, sizes=SIZES):
+    insts = _instances(sizes=sizes)
+    op = make_op(insts)
+    m = 6
+    As = [assemble_q1(t.n, t.eps, t.theta) for t in insts]
+    G = np.array([gershgorin_max(A) for A in As])
+    w, a = nag_weights(G, m, beta=0.25)
+    at = None
+    if variant == "richardson":
+        a = None
+    elif variant == "mom":
+        at = np.zeros_like(a)
+    elif variant == "nagex":
+        at = a * 0.5 + 0.1
+    if precond:
+        d = np.array([A.diagonal()[0] for A in As])
+        w = w * d[:, None]  # B^{-1} = D^{-1}: the weights act on D^{-1} r
+    x0 = [0.5 * synth.rhs_uniform(31, i, t.n) for i, t in enumerate(insts)]
+    v0 = [0.05 * synth.rhs_uniform(32, i, t.n) for i, t in enumerate(insts)]
+    bs = [synth.rhs_uniform(33, i, t.n) for i, t in enumerate(insts)]
+    if dtype == richm.F32:  # both sides start from the same FP32-rounded state
+        x0 = [v.astype(np.float32).astype(np.float64) for v in x0]
+        v0 = [v.astype(np.float32).astype(np.float64) for v in v0]
+        bs = [v.astype(np.float32).astype(np.float64) for v in bs]
+        w = w.astype(np.float32).astype(np.float64)
+        a = None if a is None else a.astype(np.float32).astype(np.float64)
+        at = None if at is None else at.astype(np.float32).astype(np.float64)
+    xprev0 = [x - v for x, v in zip(x0, v0)]
+    if dtype == richm.F32:
+        xprev0 = [v.astype(np.float32).astype(np.float64) for v in xprev0]
+        v0 = [x - p for x, p in zip(x0, xprev0)]
+    X = to_dev(op, x0, dtype)
+    XP = to_dev(op, xprev0, dtype)
+    B = to_dev(op, bs, dtype)
+    op.apply_sweeps(dtype, X, XP if a is not None else None, B, coef(w, dtype),
+                    None if a is None else coef(a, dtype), None if at is None else coef(at, dtype),
+                    K=K, m=m, k_start=k_start, precond=precond)
+    got = from_dev(op, X, dtype)
+    gotp = from_dev(op, XP, dtype) if a is not None else None
+    out = []
+    for i, t in enumerate(insts):
+        Binv = jacobi_binv(As[i]) if precond else None
+        wi = w[i] / As[i].diagonal()[0] if precond else w[i]
+        ref, refv = inner_steps(As[i], bs[i].ravel(), x0[i].ravel(), None if a is None else v0[i].ravel(), w[i],
+                                None if a is None else a[i], None if at is None else at[i], K=K,
+                                k_start=k_start, Binv=Binv)
+        out.append((got[i].ravel(), ref, None if gotp is None else gotp[i].ravel(), ref - refv,
+                    w[i] if not precond else wi, None if a is None else a[i], None if at is None else at[i], G[i]))
+    return out
+
+
+@pytest.mark.parametrize("variant", ["richardson", "nag", "mom", "nagex"])
+@pytest.mark.parametrize("precond", [0, 1])
+def test_fp64_sweeps_match_oracle(variant, precond):
+    for g, ref, gp, refp, *_ in _run_case(richm.F64, variant, K=13, k_start=4, precond=precond):
+        scale = max(np.abs(ref).max(), 1e-300)
+        assert np.abs(g - ref).max() <= 1e-12 * scale
+        if gp is not None:
+            assert np.abs(gp - refp).max() <= 1e-12 * max(np.abs(refp).max(), 1e-300)
+
+
+def test_fp64_zero_sweeps_is_noop():
+    insts = _instances(sizes=[5, 40])
+    op = make_op(insts)
+    x0 = [synth.rhs_uniform(1, i, t.n) for i, t in enumerate(insts)]
+    X = to_dev(op, x0, richm.F64)
+    op.apply_sweeps(richm.F64, X, None, X.clone(), coef(np.ones((2, 3)), richm.F64), K=0, m=3)
+    for g, r in zip(from_dev(op, X, richm.F64), x0):
+        np.testing.assert_array_equal(g, r)
+
+
+def _fp32_bound(w, a, at, G, k_start, K, xmax, bmax):
+    """Rounding bound for K FP32 sweeps started from the same state:
+    sum_k amp_k * u * c * ((1+|a|+|at|) |x| + |w| (|b| + G (1+2|at|) |x|))."""
+    u = 2.0 ** -24
+    amps = period_amplification(w, a, at, G, k_start, K)
+    tot = 0.0
+    for k in range(K):
+        i = (k_start + k) % len(w)
+        ai = 0.0 if a is None else abs(a[i])
+        ati = ai if at is None else abs(at[i])
+        per = (1 + ai + ati) * xmax + abs(w[i]) * (bmax + G * (1 + 2 * ati) * xmax)
+        tot += amps[k] * per
+    return 16.0 * u * tot
+
+
+@pytest.mark.parametrize("variant", ["richardson", "nag", "nagex"])
+def test_fp32_block_matches_oracle(variant):
+    # one fused block of 8 sweeps from the same FP32-rounded state
+    K, k_start = 8, 2
+    worst = 0.0
+    for g, ref, gp, refp, w, a, at, G in _run_case(richm.F32, variant, K=K, k_start=k_start):
+        xmax = max(np.abs(ref).max(), 1.0)
+        err = np.abs(g - ref).max()
+        bound = _fp32_bound(w, a, at, G, k_start, K, xmax, 1.0)
+        assert err <= bound, (err, bound)
+        worst = max(worst, err / xmax)
+    print(f"worst FP32 block error (rel. to max|x|): {worst:.2e}")
+
+
+def test_fp32_block_mild_weights_within_1e5():
+    # weights with |1 - w lambda| <= 1 on the spectrum: the per-block bound is the
+    # spec 1e-5 relative
+    insts = _instances(sizes=[31, 63, 127, 130])
+    op = make_op(insts)
+    As = [assemble_q1(t.n, t.eps, t.theta) for t in insts]
+    G = np.array([gershgorin_max(A) for A in As])
+    m, K = 4, 16
+    w = np.outer(1.0 / G, [0.4, 0.7, 1.0, 1.3]).astype(np.float32).astype(np.float64)
+    a = np.full_like(w, 0.25).astype(np.float32).astype(np.float64)
+    x0 = [synth.rhs_uniform(41, i, t.n).astype(np.float32).astype(np.float64) for i, t in enumerate(insts)]
+    bs = [synth.rhs_uniform(42, i, t.n).astype(np.float32).astype(np.float64) for i, t in enumerate(insts)]
+    X = to_dev(op, x0, richm.F32)
+    XP = to_dev(op, x0, richm.F32)
+    B = to_dev(op, bs, richm.F32)
+    op.apply_sweeps(richm.F32, X, XP, B, coef(w, richm.F32), coef(a, richm.F32), None, K=K, m=m)
+    for i, g in enumerate(from_dev(op, X, richm.F32)):
+        ref, _ = inner_steps(As[i], bs[i].ravel(), x0[i].ravel(), None, w[i], a[i], K=K)
+        rel = np.linalg.norm(g.ravel() - ref) / np.linalg.norm(ref)
+        assert rel <= 1e-5, rel
+
+
+@pytest.mark.parametrize("dtype", [richm.C128, richm.C64])
+def test_helmholtz_sweeps_match_oracle(dtype):
+    sizes = [1, 3, 9, 33, 64, 100]
+    insts = [synth.AnisoInstance(1.0, 0.0, n) for n in sizes]
+    ks = [helmholtz_wavenumber(n) for n in sizes]
+    # one operator per k (k is per instance in the library; the oracle assembles each)
+    op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, n, 1.0, 0.0, k) for n, k in zip(sizes, ks)])
+    m, K = 8, 12
+    ws = np.stack([synth.helmholtz_weights(m, 1.0 / (n + 1), seed=4) for n in sizes])
+    a = np.full_like(ws, 0.3)
+    x0 = [0.1 * (synth.rhs_uniform(51, i, n) + 1j * synth.rhs_uniform(52, i, n)) for i, n in enumerate(sizes)]
+    bs = [synth.point_source_rhs(n, 1, seed=5 + i)[0] for i, n in enumerate(sizes)]
+    if dtype == richm.C64:
+        x0 = [v.astype(np.complex64).astype(np.complex128) for v in x0]
+        ws = ws.astype(np.float32).astype(np.float64)
+        a = a.astype(np.float32).astype(np.float64)
+    X = to_dev(op, x0, dtype)
+    XP = to_dev(op, x0, dtype)
+    B = to_dev(op, bs, dtype)
+    op.apply_sweeps(dtype, X, XP, B, coef(ws, dtype), coef(a, dtype), None, K=K, m=m)
+    tol = 1e-12 if dtype == richm.C128 else 1e-5
+    for i, g in enumerate(from_dev(op, X, dtype)):
+        H = assemble_helmholtz(sizes[i], ks[i])
+        ref, _ = inner_steps(H, bs[i].ravel(), x0[i].ravel(), None, ws[i], a[i], K=K)
+        rel = np.linalg.norm(g.ravel() - ref) / np.linalg.norm(ref)
+        assert rel <= tol, (sizes[i], rel)
+
+
+def test_helmholtz_jacobi_preconditioned():
+    sizes = [4, 33]
+    ks = [helmholtz_wavenumber(n) for n in sizes]
+    op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, n, 1.0, 0.0, k) for n, k in zip(sizes, ks)])
+    m, K = 3, 7
+    ws = np.array([[0.3, 0.5, 0.4]] * 2)
+    a = np.full_like(ws, 0.2)
+    x0 = [0.1 * synth.rhs_uniform(61, i, n) + 0j for i, n in enumerate(sizes)]
+    bs = [synth.point_source_rhs(n, 1, seed=9)[0] for n in sizes]
+    X = to_dev(op, x0, richm.C128)
+    XP = to_dev(op, x0, richm.C128)
+    B = to_dev(op, bs, richm.C128)
+    op.apply_sweeps(richm.C128, X, XP, B, coef(ws, richm.C128), coef(a, richm.C128), None, K=K, m=m, precond=1)
+    for i, g in enumerate(from_dev(op, X, richm.C128)):
+        H = assemble_helmholtz(sizes[i], ks[i])
+        ref, _ = inner_steps(H, bs[i].ravel(), x0[i].ravel(), None, ws[i], a[i], K=K, Binv=jacobi_binv(H))
+        assert np.linalg.norm(g.ravel() - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_pack_unpack_roundtrip_and_halo_zero():
+    insts = _instances(sizes=[1, 7, 64, 129])
+    op = make_op(insts)
+    arrs = [synth.rhs_uniform(71, i, t.n) for i, t in enumerate(insts)]
+    for dt in (richm.F64, richm.F32):
+        buf = to_dev(op, arrs, dt)
+        back = from_dev(op, buf, dt)
+        for a_, b_ in zip(arrs, back):
+            np.testing.assert_array_equal(b_, a_.astype(richm.TORCH_DTYPE[dt].__str__().split(".")[-1]))
+        host = buf.cpu().numpy()
+        for i, lay in enumerate(op.layouts):
+            n = op.ns[i]
+            blk = host[lay.offset:lay.offset + lay.rows * lay.pitch].reshape(lay.rows, lay.pitch)
+            assert np.all(blk[0] == 0) and np.all(blk[-1] == 0) and np.all(blk[:, n:] == 0)

@@ -1,0 +1,198 @@
+"""GPU loss, adjoint sweeps, meta network and Adam against the oracle and finite differences."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import richm_synth as synth
+from gpu_util import coef, from_dev, make_op, nag_weights, to_dev
+from oracle.operators import assemble_q1, gershgorin_max
+from oracle.training import (adam_step, log_rel_residual, loss_and_grads, meta_output_map, mlp_forward,
+                             to_torch_sparse)
+from paper_2412_08076_gb300 import richm
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(sizes=(7, 16, 33), m=4, seed=3, dtype=richm.F64):
+    u = synth.uniform(synth.stream_key(seed), 2 * len(sizes))
+    insts = [synth.AnisoInstance(10 ** (-2 * u[2 * i]), math.pi * u[2 * i + 1], n) for i, n in enumerate(sizes)]
+    op = make_op(insts)
+    As = [assemble_q1(t.n, t.eps, t.theta) for t in insts]
+    G = np.array([gershgorin_max(A) for A in As])
+    w, a = nag_weights(G, m, beta=0.3)
+    a = a + 0.02 * np.arange(m)  # distinct per-step momenta
+    fs = [synth.rhs_uniform(21, i, t.n) for i, t in enumerate(insts)]
+    x0 = [0.1 * synth.rhs_uniform(22, i, t.n) for i, t in enumerate(insts)]
+    if dtype == richm.F32:
+        fs = [v.astype(np.float32).astype(np.float64) for v in fs]
+        x0 = [v.astype(np.float32).astype(np.float64) for v in x0]
+        w = w.astype(np.float32).astype(np.float64)
+        a = a.astype(np.float32).astype(np.float64)
+    return insts, op, As, w, a, fs, x0
+
+
+def _gpu_grads(op, dtype, x0, fs, w, a, at, m, K, every, precond=0):
+    X0 = to_dev(op, x0, dtype)
+    B = to_dev(op, fs, dtype)
+    W, A_ = coef(w, dtype), coef(a, dtype)
+    AT = None if at is None else coef(at, dtype)
+    ck = torch.zeros(op.checkpoint_elems(K, every), dtype=richm.TORCH_DTYPE[dtype], device="cuda")
+    XK = op.zeros(dtype)
+    op.forward_checkpointed(dtype, X0, B, W, A_, AT, m, K, every, precond, ck, XK)
+    gK = op.zeros(dtype)
+    loss = op.loss_log_residual(dtype, XK, B, gK)
+    gw = torch.zeros_like(W)
+    ga = torch.zeros_like(A_)
+    gat = None if at is None else torch.zeros_like(A_)
+    gx0 = op.zeros(dtype)
+    op.sweeps_adjoint(dtype, ck, every, B, gK, W, A_, AT, m, K, precond, gw, ga, gat, gx0)
+    return (loss.item(), gw.cpu().numpy(), ga.cpu().numpy(), None if gat is None else gat.cpu().numpy(),
+            from_dev(op, gx0, dtype), from_dev(op, XK, dtype))
+
+
+@pytest.mark.parametrize("every", [1, 3, 4, 12])
+def test_fp64_adjoint_matches_oracle_gradient(every):
+    insts, op, As, w, a, fs, x0 = _setup()
+    m, K = 4, 12
+    L, gw, ga, _, gx0, _ = _gpu_grads(op, richm.F64, x0, fs, w, a, None, m, K, every)
+    Lo, gwo, gao, gxo = loss_and_grads(As, [f.ravel() for f in fs], [x.ravel() for x in x0], w, a, K)
+    assert abs(L - Lo) <= 1e-12 * abs(Lo)
+    np.testing.assert_allclose(gw, gwo, rtol=1e-9, atol=1e-12 * np.abs(gwo).max())
+    np.testing.assert_allclose(ga, gao, rtol=1e-9, atol=1e-12 * np.abs(gao).max())
+    for i in range(len(insts)):
+        np.testing.assert_allclose(gx0[i].ravel(), gxo[i], rtol=1e-8, atol=1e-11 * np.abs(gxo[i]).max())
+
+
+def _fd_check(g, loss_at, h=1e-4):
+    """Central differences with h and h/2; the adjoint must match the extrapolated
+    value (4 D(h/2) - D(h)) / 3 to 1e-6 relative, and D(h) within D(h)'s own
+    truncation error (|D(h) - extrapolated|) plus 1e-6 relative."""
+    d1 = (loss_at(h) - loss_at(-h)) / (2 * h)
+    d2 = (loss_at(h / 2) - loss_at(-h / 2)) / h
+    rx = (4 * d2 - d1) / 3
+    scale = max(abs(rx), 1e-3)
+    assert abs(g - rx) <= 1e-6 * scale, (g, rx, d1)
+    assert abs(g - d1) <= 2 * abs(d1 - rx) + 1e-6 * scale, (g, d1)
+
+
+def test_fp64_adjoint_matches_central_differences():
+    # the adjoint gradient within 1e-6 relative of central finite differences (FP64)
+    insts, op, As, w, a, fs, x0 = _setup(sizes=(16, 31))
+    m, K, every = 4, 16, 8
+    at = a * 0.5 + 0.05  # NAGex: independent look-ahead momentum
+    L, gw, ga, gat, gx0, _ = _gpu_grads(op, richm.F64, x0, fs, w, a, at, m, K, every)
+
+    def loss_of(w_, a_, at_, x0_):
+        return _gpu_grads(op, richm.F64, x0_, fs, w_, a_, at_, m, K, every)[0]
+
+    for b in range(2):
+        for i in (0, 1, 3):
+            for name, arr, g in (("w", w, gw), ("a", a, ga), ("at", at, gat)):
+                def loss_at(d, name=name, arr=arr, b=b, i=i):
+                    p = arr.copy()
+                    p[b, i] += d
+                    kw = dict(w_=w, a_=a, at_=at, x0_=x0)
+                    kw[name + "_"] = p
+                    return loss_of(**kw)
+                _fd_check(g[b, i], loss_at)
+        for (r, c) in ((3, 4), (8, 8)):
+            def loss_at(d, b=b, r=r, c=c):
+                xp = [x.copy() for x in x0]
+                xp[b][r, c] += d
+                return loss_of(w, a, at, xp)
+            _fd_check(gx0[b][r, c], loss_at)
+
+
+def test_fp32_adjoint_close_to_oracle():
+    insts, op, As, w, a, fs, x0 = _setup(dtype=richm.F32)
+    m, K, every = 4, 16, 8
+    L, gw, ga, _, gx0, _ = _gpu_grads(op, richm.F32, x0, fs, w, a, None, m, K, every)
+    Lo, gwo, gao, gxo = loss_and_grads(As, [f.ravel() for f in fs], [x.ravel() for x in x0], w, a, K)
+    assert abs(L - Lo) <= 1e-5 * abs(Lo)
+    assert np.abs(gw - gwo).max() <= 2e-3 * np.abs(gwo).max()
+    assert np.abs(ga - gao).max() <= 2e-3 * np.abs(gao).max()
+
+
+def test_preconditioned_adjoint_matches_fd():
+    insts, op, As, w, a, fs, x0 = _setup(sizes=(12,))
+    d = As[0].diagonal()[0]
+    w = w * d
+    m, K, every = 4, 8, 4
+    L, gw, ga, _, gx0, _ = _gpu_grads(op, richm.F64, x0, fs, w, a, None, m, K, every, precond=1)
+    for i in range(m):
+        def loss_at(dd, i=i):
+            p = w.copy()
+            p[0, i] += dd
+            return _gpu_grads(op, richm.F64, x0, fs, p, a, None, m, K, every, precond=1)[0]
+        _fd_check(gw[0, i], loss_at)
+
+
+def _mlp(m, seed=7):
+    params = synth.mlp_init((2, 64, 64, m + 1), seed=seed)
+    flat = np.array(richm.pack_mlp_params(params), dtype=np.float64)
+    return params, flat
+
+
+def test_meta_forward_matches_oracle():
+    m, B = 16, 37
+    params, flat = _mlp(m)
+    insts = synth.batched_aniso(B, sizes=(63,), param_seed=9)
+    X = synth.meta_inputs(insts)
+    G = np.linspace(2.0, 5.0, B)
+    P = torch.tensor(flat, dtype=torch.float32, device="cuda")
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Gt = torch.tensor(G, dtype=torch.float32, device="cuda")
+    acts = torch.zeros(richm.meta_acts_size(B, m), dtype=torch.float32, device="cuda")
+    w, a = richm.meta_forward(P, Xt, Gt, m, acts)
+    p32 = [(W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)) for W, b in params]
+    o = mlp_forward(p32, X.astype(np.float32).astype(np.float64))
+    wo, ao = meta_output_map(o, G.astype(np.float32).astype(np.float64), m)
+    np.testing.assert_allclose(w.cpu().numpy(), wo, rtol=2e-5)
+    np.testing.assert_allclose(a.cpu().numpy(), np.repeat(ao[:, None], m, 1), rtol=2e-5)
+
+
+def test_meta_backward_and_adam_match_oracle():
+    m, B = 16, 9
+    params, flat = _mlp(m, seed=8)
+    insts = synth.batched_aniso(B, sizes=(63,), param_seed=10)
+    X = synth.meta_inputs(insts).astype(np.float32).astype(np.float64)
+    G = np.linspace(2.0, 5.0, B).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(0)
+    gw = rng.standard_normal((B, m)).astype(np.float32).astype(np.float64)
+    ga = rng.standard_normal((B, m)).astype(np.float32).astype(np.float64)
+    P = torch.tensor(flat, dtype=torch.float32, device="cuda")
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Gt = torch.tensor(G, dtype=torch.float32, device="cuda")
+    acts = torch.zeros(richm.meta_acts_size(B, m), dtype=torch.float32, device="cuda")
+    richm.meta_forward(P, Xt, Gt, m, acts)
+    gP = richm.meta_backward(P, Xt, Gt, acts, m, torch.tensor(gw, dtype=torch.float32, device="cuda"),
+                             torch.tensor(ga, dtype=torch.float32, device="cuda"))
+    # oracle: d/dtheta of sum(gw * w + ga * a) through the FP64 network
+    tp = torch.tensor(P.cpu().numpy().astype(np.float64), requires_grad=True)
+    sizes = [(64, 2), (64,), (64, 64), (64,), (m + 1, 64), (m + 1,)]
+    parts, off = [], 0
+    for s in sizes:
+        k = int(np.prod(s))
+        parts.append(tp[off:off + k].reshape(s))
+        off += k
+    h = torch.tensor(X)
+    h = torch.relu(h @ parts[0].T + parts[1])
+    h = torch.relu(h @ parts[2].T + parts[3])
+    o = h @ parts[4].T + parts[5]
+    wv = torch.exp(o[:, :m]) / torch.tensor(G).reshape(-1, 1)
+    av = torch.sigmoid(o[:, m])
+    (torch.sum(torch.tensor(gw) * wv) + torch.sum(torch.tensor(ga).sum(1) * av)).backward()
+    ref = tp.grad.numpy()
+    got = gP.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    # Adam
+    m1 = torch.zeros_like(P)
+    m2 = torch.zeros_like(P)
+    p0 = P.clone()
+    richm.adam_step(P, gP, m1, m2, 1, lr=1e-2)
+    richm.adam_step(P, gP, m1, m2, 2, lr=1e-2)
+    pr, a1, a2 = adam_step(p0.cpu().numpy().astype(np.float64), got.astype(np.float64), 0.0, 0.0, 1, lr=1e-2)
+    pr, a1, a2 = adam_step(pr, got.astype(np.float64), a1, a2, 2, lr=1e-2)
+    np.testing.assert_allclose(P.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
