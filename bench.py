@@ -30,6 +30,11 @@ if ROOT not in sys.path:
 METRIC = "batched Richardson(m) Gdof-sweeps/s, time to 1e-10 rel residual, % HBM peak"
 UNIT = "Gdof-sweeps/s"
 M, BETA, REFINE, TOL = 16, 0.3, 64, 1e-10
+# The solver stops at FP64 residual <= TOL * (1 - 1e-3): two independent FP64
+# evaluations of ||b - A x|| / ||b|| near 1e-10 (the library's stencil and the
+# oracle's assembled matrix) differ by ~1e-5 relative, so the margin makes the
+# oracle's own recompute land at or below TOL too.
+SOLVE_TOL = TOL * (1.0 - 1e-3)
 SIZES = (127, 255, 511)
 BATCH = 256
 
@@ -266,7 +271,9 @@ def run_ours(args):
     B64 = op.pack(dense_b.to(dev), richm.F64)
     X64 = op.zeros(richm.F64)
     w, a = richm.meta_forward(P, X, G, M)
-    opts = op.solve_opts(M, tol=TOL, max_sweeps=10**8, refine_every=REFINE, inner=richm.F32, use_graph=1)
+    fuse, tune_ms = op.autotune(M, momentum=True)
+    opts = op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10**8, refine_every=REFINE, inner=richm.F32, use_graph=1,
+                         fuse=fuse)
     S = richm.Solver(op, opts, w, a)
     S.start(B64, X64)
     stream = torch.cuda.current_stream()
@@ -303,28 +310,32 @@ def run_ours(args):
     t_max_ms = max_over_ranks(ms, world, dev)
     total_dofs = sum_over_ranks(float(dofs), world, dev)
     value = total_dofs * REFINE * args.steps / (t_max_ms / 1e3) / 1e9
-    launches_per_step = 1 + REFINE + 3  # meta forward, sweeps, update, residual, reduce
+    launches_per_step = 1 + REFINE // fuse + 3  # meta forward, sweep passes, update, residual, reduce
 
-    # -- dominant kernel (the FP32 NAG sweep): launch duration by CUDA events on its stream
+    # -- dominant kernel (the FP32 NAG sweep pass): launch duration by CUDA events on its stream
     K = 192
     xs = op.zeros(richm.F32)
     xps = op.zeros(richm.F32)
     b32 = op.zeros(richm.F32)
     b32.copy_(B64.to(torch.float32))
     ws = op.workspace(op._ws("richm_sweeps_workspace", richm.F32))
-    op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, work=ws)
+    op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=fuse, work=ws)
     torch.cuda.synchronize()
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
     reps = 3
     k0.record(stream)
     for _ in range(reps):
-        op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, work=ws)
+        op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=fuse, work=ws)
     k1.record(stream)
     torch.cuda.synchronize()
-    sweep_ms = k0.elapsed_time(k1) / (reps * K)
-    alg_bytes = 16.0 * dofs  # read x_k, x_{k-1}, b; write x_{k+1} (FP32)
-    achieved = alg_bytes / (sweep_ms / 1e3) / 1e9
+    launch_ms = k0.elapsed_time(k1) / (reps * K // fuse)
+    # algorithmic bytes per launch: one sweep reads x_k, x_{k-1}, b and writes x_{k+1}
+    # (16 B per unknown); a fused pass reads the same and writes two levels (20 B)
+    alg_bytes = (16.0 if fuse == 1 else 20.0) * dofs
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    kname = ("sweep1_kernel<float,NAG> (one FP32 NAG sweep per launch)" if fuse == 1 else
+             f"sweepT_kernel<{fuse},NAG> ({fuse} FP32 NAG sweeps per launch, temporal blocking)")
 
     # -- e2e: host buffers through the public API (pinned H2D of b, one cycle, D2H of x)
     hb = dense_b.pin_memory()
@@ -390,8 +401,9 @@ def run_ours(args):
                "max_sweeps": int(max(sweeps)), "total_dof_sweeps": float(sum(s * t.n * t.n for s, t in zip(sweeps, insts))),
                "oracle_checked": checked, "oracle_worst_rel_res": worst}
         ttt["gdof_sweeps_per_s"] = ttt["total_dof_sweeps"] / solve_s / 1e9
-        # plain FP64 GPU sweep (one instance per call, one sweep per launch): time per sweep
-        # on one instance of each size, extrapolated to the sweep counts above
+        # plain FP64 GPU sweep (one instance per call, one sweep per launch, no graph):
+        # time per sweep on a running session for one instance of each size,
+        # extrapolated to the sweep counts above
         per_sweep = {}
         seen = {}
         for i, t in enumerate(insts):
@@ -403,13 +415,15 @@ def run_ours(args):
             x1 = op1.zeros(richm.F64)
             w1 = w[i:i + 1].double().contiguous()
             a1 = a[i:i + 1].double().contiguous()
-            o1 = op1.solve_opts(M, tol=0.0, max_sweeps=64 * 8, refine_every=64, inner=richm.F64, use_graph=0)
-            op1.solve(b1, x1, w1, a1, None, o1)
-            torch.cuda.synchronize()
+            o1 = op1.solve_opts(M, tol=0.0, max_sweeps=10**9, refine_every=64, inner=richm.F64, use_graph=0,
+                                fuse=1)
+            S1 = richm.Solver(op1, o1, w1, a1)
+            S1.start(b1, x1)
+            S1.step(1, sync=True)
             c0 = time.perf_counter()
-            op1.solve(b1, x1, w1, a1, None, o1)
-            torch.cuda.synchronize()
-            per_sweep[t.n] = (time.perf_counter() - c0) / (64 * 8)
+            S1.step(6, sync=True)
+            per_sweep[t.n] = (time.perf_counter() - c0) / (6 * 64)
+            S1.close()
             op1.close()
         fp64_est = sum(per_sweep[t.n] * s for s, t in zip(sweeps, insts))
         ttt["plain_fp64_seconds_extrapolated"] = fp64_est
@@ -424,12 +438,12 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(), dofs_per_rank=dofs, meta_params=psrc,
-                           active_after_steps=active),
+                           active_after_steps=active, sweeps_per_pass=fuse, autotune_ms_per_sweep=tune_ms,
+                           solve_tol=SOLVE_TOL),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
-                         "kernel": "sweep1_kernel<float,NAG> (FP32 NAG sweep, one sweep per launch)",
-                         "alg_bytes_per_launch": alg_bytes, "launch_ms": sweep_ms,
-                         "peak_source": f"{peak_src} hbm_gbs"},
+                         "frac": achieved / hbm_peak, "traffic": None, "kernel": kname,
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
+                         "sweeps_per_launch": fuse, "peak_source": f"{peak_src} hbm_gbs (of measured)"},
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc,
                              "host_cores": os.cpu_count()},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(dense_b.numel() * 8),
@@ -452,7 +466,7 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-tolerance solve")

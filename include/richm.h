@@ -163,6 +163,17 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
                                 const void* w, const void* alpha, const void* alpha_t, int K,
                                 const richm_sweep_opts* opts, void* work, size_t work_bytes, void* stream);
 
+/* Autotuner: times 16 FP32 sweeps of this operator's batch with 1, 4 and 8 sweeps
+ * per pass (richm_apply_sweeps' fuse) and stores the fastest in the operator; calls
+ * with fuse = 0 (richm_apply_sweeps on RICHM_F32, richm_solve / richm_solver_create
+ * with inner RICHM_F32) then use it (4 before any tuning). momentum: 1 times the NAG
+ * kernels, 0 the plain ones. Synchronises `stream`. best_fuse (host, may be NULL)
+ * receives the choice and ms_per_sweep (host, may be NULL) its time per sweep.
+ * work: at least richm_autotune_workspace bytes (overwritten). Q1 operators only. */
+richm_status richm_autotune_workspace(const richm_operator* op, size_t* bytes);
+richm_status richm_autotune(richm_operator* op, int m, int momentum, void* work, size_t work_bytes, void* stream,
+                            int* best_fuse, float* ms_per_sweep);
+
 /* ------------------------------------------------------------------ residual */
 
 /* Workspace bytes richm_residual_norm needs (per-tile FP64 partial sums). */

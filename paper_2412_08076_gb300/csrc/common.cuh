@@ -102,13 +102,15 @@ struct richm_operator {
   size_t elems = 0;
   int max_n = 0;
   std::map<long long, richm::TileMap> tiles;
+  int best_fuse = 4;  // sweeps per pass used when a call asks for fuse = 0 (set by richm_autotune)
   // cuFFT state for richm_fourier_correction (created on first use)
   void* fft_state = nullptr;
 };
 
 namespace richm {
 
-// Tile list for tiles of `tw` elements x `rows` rows (cached in the operator).
+// Tile list for tiles of `tw` elements x `rows` rows (cached in the operator);
+// tw = -TL gives the overlapping 128-column tiles of the TL-sweep fused kernel.
 richm_status get_tiles(richm_operator* op, int tw, int rows, const TileMap** out);
 
 inline size_t dtype_size(richm_dtype t) {

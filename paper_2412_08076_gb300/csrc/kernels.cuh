@@ -7,6 +7,7 @@ namespace richm {
 
 constexpr int kRows = 16;          // rows streamed by one warp tile
 constexpr int kWarpsPerBlock = 8;  // warp tiles per thread block
+constexpr int kFuseRows = 64;      // output rows of a fused-sweep warp tile
 
 // One forward sweep (see sweep.cu). `a == nullptr`: no momentum (xp unused);
 // `at == nullptr`: at = a. `active`: per-instance flags or nullptr (all active).
@@ -15,6 +16,13 @@ richm_status launch_sweep(richm_operator* op, const E* x, const E* xp, const E* 
                           const typename RealOf<E>::type* w, const typename RealOf<E>::type* a,
                           const typename RealOf<E>::type* at, int m, int kidx, int precond, const int* active,
                           cudaStream_t s);
+
+// TL (4 or 8) fused FP32 sweeps of a real Q1 batch: reads (x_k, x_{k-1}) from
+// (x, xp), writes (x_{k+TL}, x_{k+TL-1}) to (out_x, out_xp); the outputs must not
+// alias the inputs. kidx0 = coefficient index of the first sweep.
+richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
+                                float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
+                                int kidx0, int precond, const int* active, cudaStream_t s);
 
 // r = b - A x in FP64 with per-tile partial sums (sum |r|^2, sum |b|^2) written to
 // `partials` (one double2 per warp tile of the residual geometry); r_out may be null.

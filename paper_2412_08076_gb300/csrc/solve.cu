@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -26,7 +27,7 @@ struct richm_solver {
   const void* a = nullptr;
   const void* at = nullptr;
   // workspace carve-up
-  void* E[3] = {nullptr, nullptr, nullptr};
+  void* E[4] = {nullptr, nullptr, nullptr, nullptr};
   void* rhs = nullptr;
   double2* partials = nullptr;
   double* bnorm = nullptr;
@@ -137,16 +138,13 @@ __global__ void solve_init_kernel(int batch, long long* sweeps, int* status, int
 }
 
 template <typename T>
-static richm_status refine_t(richm_solver* S, bool init) {
+static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 1) {
   richm_operator* op = S->op;
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 64, kRows, &tm));  // residual / update geometry of FP64
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (!init) {
-    // after S sweeps from (E0, E1) the current/previous pair sits in the rotation
-    const int Sw = S->o.refine_every;
-    const int cur = Sw % 3 == 0 ? 0 : (Sw % 3 == 1 ? 2 : 1);
-    const int prv = (cur + 1) % 3;
+    // pointwise, so the new pair may overwrite the buffers it reads
     refine_update_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(
         op->d_inst, tm->d_tiles, tm->ntiles, S->x, (const T*)S->E[cur], (const T*)S->E[prv], (T*)S->E[0],
         (T*)S->E[1], S->active);
@@ -166,7 +164,24 @@ static richm_status refine_t(richm_solver* S, bool init) {
 template <typename T>
 static richm_status cycle_t(richm_solver* S, long long k0) {
   const int Sw = S->o.refine_every;
-  int cur = 0, prv = 1, fre = 2;
+  int cur = 0, prv = 1;
+  if constexpr (std::is_same<T, float>::value) {
+    if (S->o.fuse == 4 || S->o.fuse == 8) {
+      // temporally blocked passes alternate between the pairs (E0, E1) and (E2, E3)
+      const int TL = S->o.fuse;
+      for (int k = 0; k < Sw; k += TL) {
+        const int oc = cur == 0 ? 2 : 0, op_ = cur == 0 ? 3 : 1;
+        RICHM_TRY(launch_sweep_fused(S->op, TL, (const float*)S->E[cur], (const float*)S->E[prv],
+                                     (const float*)S->rhs, (float*)S->E[oc], (float*)S->E[op_],
+                                     (const float*)S->w, (const float*)S->a, (const float*)S->at, S->o.m,
+                                     (int)((k0 + k) % S->o.m), S->o.precond, S->active, S->s));
+        cur = oc;
+        prv = op_;
+      }
+      return refine_t<T>(S, false, cur, prv);
+    }
+  }
+  int fre = 2;
   for (int k = 0; k < Sw; ++k) {
     const int kidx = (int)((k0 + k) % S->o.m);
     RICHM_TRY(launch_sweep<T>(S->op, (const T*)S->E[cur], (const T*)S->E[prv], (const T*)S->rhs, (T*)S->E[fre],
@@ -177,7 +192,7 @@ static richm_status cycle_t(richm_solver* S, long long k0) {
     cur = fre;
     fre = nf;
   }
-  return refine_t<T>(S, false);
+  return refine_t<T>(S, false, cur, prv);
 }
 
 static richm_status run_cycles(richm_solver* S, int cycles) {
@@ -203,7 +218,9 @@ static richm_status check_solve_opts(const richm_operator* op, const richm_solve
   RICHM_ARG(o->tol >= 0.0, "tol < 0");
   RICHM_ARG(o->inner == RICHM_F32 || o->inner == RICHM_F64, "inner dtype must be RICHM_F32 or RICHM_F64");
   RICHM_ARG(o->precond == 0 || o->precond == 1, "precond must be 0 or 1");
-  RICHM_ARG(o->fuse == 0 || o->fuse == 1, "fuse must be 0 or 1 in richm_solve");
+  RICHM_ARG(o->fuse == 0 || o->fuse == 1 || o->fuse == 4 || o->fuse == 8, "fuse must be 0, 1, 4 or 8");
+  RICHM_ARG(o->fuse <= 1 || (o->inner == RICHM_F32 && o->refine_every % o->fuse == 0),
+            "fused sweeps need inner = RICHM_F32 and refine_every divisible by fuse");
   for (int b = 0; b < op->batch; ++b)
     if (op->h_inst[b].kind != RICHM_ANISO_Q1)
       return set_error(RICHM_ERR_UNSUPPORTED, "richm_solve handles Q1 instances (instance %d is not)", b);
@@ -218,7 +235,7 @@ richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_o
   int nt = 0;
   RICHM_TRY(residual_tiles<double>(const_cast<richm_operator*>(op), &nt));
   size_t B = (size_t)op->batch;
-  *bytes = 4 * a256(op->elems * es) + a256(sizeof(double2) * nt) + 2 * a256(sizeof(double) * B) +
+  *bytes = 5 * a256(op->elems * es) + a256(sizeof(double2) * nt) + 2 * a256(sizeof(double) * B) +
            a256(sizeof(long long) * B) + 2 * a256(sizeof(int) * B) + a256(sizeof(int));
   return RICHM_OK;
 }
@@ -239,6 +256,9 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   if (!S) return set_error(RICHM_ERR_NOMEM, "host allocation failed");
   S->op = op;
   S->o = *o;
+  if (S->o.fuse == 0) {
+    S->o.fuse = (o->inner == RICHM_F32 && o->refine_every % op->best_fuse == 0) ? op->best_fuse : 1;
+  }
   S->w = w;
   S->a = alpha;
   S->at = alpha_t;
@@ -246,7 +266,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   int nt = 0;
   residual_tiles<double>(op, &nt);
   char* p = reinterpret_cast<char*>(work);
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     S->E[i] = p;
     p += a256(op->elems * es);
   }
@@ -280,6 +300,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   const TileMap* tm = nullptr;
   richm_status st = get_tiles(op, 64, kRows, &tm);
   if (st == RICHM_OK) st = get_tiles(op, o->inner == RICHM_F32 ? 128 : 64, kRows, &tm);
+  if (st == RICHM_OK && S->o.fuse > 1) st = get_tiles(op, -S->o.fuse, kFuseRows, &tm);
   if (st != RICHM_OK) {
     richm_solver_destroy(S);
     return st;
@@ -317,6 +338,7 @@ richm_status richm_solver_start(richm_solver* S, const double* b, double* x, voi
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[0], 0, op->elems * es, S->s));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[1], 0, op->elems * es, S->s));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[2], 0, op->elems * es, S->s));
+  RICHM_CUDA_TRY(cudaMemsetAsync(S->E[3], 0, op->elems * es, S->s));
   solve_init_kernel<<<(op->batch + 255) / 256, 256, 0, S->s>>>(op->batch, S->sweeps, S->status, S->active);
   RICHM_LAUNCH_CHECK("solve init");
   if (S->o.inner == RICHM_F32) RICHM_TRY(refine_t<float>(S, true));

@@ -8,6 +8,8 @@
 // 16-byte column block, keeping the stencil's three rows of y in registers, so
 // every input row is read once per warp tile and neighbours across lanes come
 // from warp shuffles.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -181,7 +183,22 @@ static richm_status apply_sweeps_t(richm_operator* op, E* x, E* xp, const E* b, 
   const bool mom = (a != nullptr);
   E* cur = x;
   E* prev = mom ? xp : nullptr;
-  for (int k = 0; k < K; ++k) {
+  int k = 0;
+  if constexpr (std::is_same<E, float>::value) {
+    // fused passes of TL sweeps: (cur, prev) -> the other pair of buffers
+    const int TL = (o->fuse == 4 || o->fuse == 8) ? o->fuse : 0;
+    for (; TL > 0 && k + TL <= K; k += TL) {
+      E* ox = (cur == x) ? W0 : x;
+      E* oxp = (cur == x) ? W1 : xp;
+      if (!mom && oxp == nullptr) oxp = W1;
+      const int kidx0 = (int)(((long long)o->k_start + k) % o->m);
+      RICHM_TRY(launch_sweep_fused(op, TL, cur, prev, b, ox, oxp, (const S*)w, (const S*)a, (const S*)at, o->m,
+                                   kidx0, o->precond, nullptr, s));
+      cur = ox;
+      prev = mom ? oxp : nullptr;
+    }
+  }
+  for (; k < K; ++k) {
     E* outb = nullptr;
     E* cand[4] = {W0, W1, x, xp};
     for (E* c : cand)
@@ -227,6 +244,79 @@ richm_status richm_sweeps_workspace(const richm_operator* op, richm_dtype dtype,
   return RICHM_OK;
 }
 
+richm_status richm_autotune_workspace(const richm_operator* op, size_t* bytes) {
+  clear_error();
+  RICHM_ARG(op && bytes, "null argument");
+  const size_t one = ((op->elems * sizeof(float) + 255) / 256) * 256;
+  *bytes = 5 * one + 256 * 3 * 64 * sizeof(float) * (size_t)((op->batch + 255) / 256);
+  return RICHM_OK;
+}
+
+richm_status richm_autotune(richm_operator* op, int m, int momentum, void* work, size_t work_bytes, void* stream,
+                            int* best_fuse, float* ms_per_sweep) {
+  clear_error();
+  RICHM_ARG(op != nullptr && work != nullptr, "null argument");
+  RICHM_TRY(check_dtype_for_op(op, RICHM_F32));
+  RICHM_ARG(m >= 1 && m <= 64, "m out of range");
+  size_t need = 0;
+  richm_autotune_workspace(op, &need);
+  if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t one = ((op->elems * sizeof(float) + 255) / 256) * 256;
+  char* p = reinterpret_cast<char*>(work);
+  float* x = reinterpret_cast<float*>(p);
+  float* xp = reinterpret_cast<float*>(p + one);
+  float* b = reinterpret_cast<float*>(p + 2 * one);
+  void* W = p + 3 * one;
+  float* coef = reinterpret_cast<float*>(p + 5 * one);
+  const size_t nc = (size_t)op->batch * m;
+  RICHM_CUDA_TRY(cudaMemsetAsync(x, 0, 3 * one, s));
+  // small weights and momentum: values do not affect timing, only stay finite
+  std::vector<float> hc(2 * nc);
+  for (size_t i = 0; i < nc; ++i) {
+    hc[i] = (float)(0.5 / op->h_inst[i / m].G);
+    hc[nc + i] = 0.3f;
+  }
+  RICHM_CUDA_TRY(cudaMemcpyAsync(coef, hc.data(), sizeof(float) * 2 * nc, cudaMemcpyHostToDevice, s));
+  const float* w = coef;
+  const float* a = momentum ? coef + nc : nullptr;
+  cudaEvent_t e0, e1;
+  RICHM_CUDA_TRY(cudaEventCreate(&e0));
+  RICHM_CUDA_TRY(cudaEventCreate(&e1));
+  const int cands[3] = {1, 4, 8};
+  int best = 1;
+  float best_ms = 1e30f;
+  for (int c : cands) {
+    richm_sweep_opts o{m, 0, 0, c};
+    const int K = 16;
+    richm_status st = apply_sweeps_t<float>(op, x, xp, b, w, a, nullptr, K, &o, W, s);  // warm-up
+    if (st != RICHM_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && st == RICHM_OK; ++r) st = apply_sweeps_t<float>(op, x, xp, b, w, a, nullptr, K, &o, W, s);
+    cudaEventRecord(e1, s);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (st == RICHM_OK && ce == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+      ms /= 3.0f * K;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (st != RICHM_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return st;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  op->best_fuse = best;
+  if (best_fuse) *best_fuse = best;
+  if (ms_per_sweep) *ms_per_sweep = best_ms;
+  return RICHM_OK;
+}
+
 richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, void* x_prev, const void* b,
                                 const void* w, const void* alpha, const void* alpha_t, int K,
                                 const richm_sweep_opts* opts, void* work, size_t work_bytes, void* stream) {
@@ -248,6 +338,9 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
   RICHM_ARG(work != nullptr, "null workspace");
   if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
+  richm_sweep_opts o = *opts;
+  if (o.fuse == 0) o.fuse = (dtype == RICHM_F32) ? op->best_fuse : 1;
+  opts = &o;
   switch (dtype) {
     case RICHM_F32:
       return apply_sweeps_t<float>(op, (float*)x, (float*)x_prev, (const float*)b, w, alpha, alpha_t, K, opts, work, s);

@@ -70,6 +70,8 @@ _SIGS = {
     "richm_sweeps_workspace": (_I, [_P, _I, C.POINTER(_SZ)]),
     "richm_apply_sweeps": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _I, C.POINTER(richm_sweep_opts), _P, _SZ, _P]),
     "richm_residual_workspace": (_I, [_P, C.POINTER(_SZ)]),
+    "richm_autotune_workspace": (_I, [_P, C.POINTER(_SZ)]),
+    "richm_autotune": (_I, [_P, _I, _I, _P, _SZ, _P, C.POINTER(_I), C.POINTER(C.c_float)]),
     "richm_residual_norm": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_solve_workspace": (_I, [_P, C.POINTER(richm_solve_opts), C.POINTER(_SZ)]),
     "richm_solve": (_I, [_P, _P, _P, _P, _P, _P, C.POINTER(richm_solve_opts), C.POINTER(richm_solve_info), _P, _SZ,
@@ -254,6 +256,14 @@ class Operator:
         _check(load().richm_apply_sweeps(self.handle, dtype, _ptr(x), _ptr(x_prev), _ptr(b), _ptr(w), _ptr(alpha),
                                          _ptr(alpha_t), K, C.byref(o), _ptr(work), work.numel(), _stream(stream)),
                "richm_apply_sweeps")
+
+    def autotune(self, m=16, momentum=True, stream=None):
+        """richm_autotune: pick sweeps per pass for FP32 sweeps; returns (fuse, ms per sweep)."""
+        work = self.workspace(self._ws("richm_autotune_workspace"))
+        best, ms = C.c_int(), C.c_float()
+        _check(load().richm_autotune(self.handle, m, int(momentum), _ptr(work), work.numel(), _stream(stream),
+                                     C.byref(best), C.byref(ms)), "richm_autotune")
+        return best.value, ms.value
 
     def residual_norm(self, dtype, x, b, r_out=None, work=None, stream=None):
         """richm_residual_norm: returns (rnorm, bnorm, rel) as FP64 CUDA tensors [batch]."""

@@ -1,0 +1,120 @@
+"""Meta-network training on the GPU through the library's kernels (Algorithm 1).
+
+Each step: w, a = Meta(theta; mu) (library forward), K NAG sweeps from x0 = 0 with
+checkpoints (library forward), loss = mean log relative residual and its gradient
+(library), adjoint sweeps (library), network backward and Adam (library). Python only
+sequences the calls. Usage:
+  python -m paper_2412_08076_gb300.train --steps 400 --save
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import meta as meta_mod
+from . import richm
+
+
+class Batch:
+    """One minibatch: operator, padded FP32 right-hand sides, network inputs."""
+
+    def __init__(self, insts, seed):
+        import richm_synth as synth
+        self.insts = insts
+        self.op = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0) for t in insts])
+        rhs = [synth.rhs_uniform(seed, i, t.n) for i, t in enumerate(insts)]
+        dense = torch.tensor(np.concatenate([r.ravel() for r in rhs]), dtype=torch.float32, device="cuda")
+        self.b = self.op.pack(dense, richm.F32)
+        self.X = torch.tensor(synth.meta_inputs(insts), dtype=torch.float32, device="cuda")
+        self.G = torch.tensor(self.op.gershgorin(), dtype=torch.float32, device="cuda")
+
+
+class Trainer:
+    def __init__(self, params: np.ndarray, m=16, K=64, every=8, lr=2e-3):
+        self.m, self.K, self.every, self.lr = m, K, every, lr
+        self.P = torch.tensor(params, dtype=torch.float32, device="cuda")
+        self.m1 = torch.zeros_like(self.P)
+        self.m2 = torch.zeros_like(self.P)
+        self.t = 0
+        self.ws = {}
+
+    def _work(self, batch: Batch):
+        key = id(batch)
+        if key not in self.ws:
+            op = batch.op
+            B = op.batch
+            self.ws[key] = dict(
+                ck=torch.empty(op.checkpoint_elems(self.K, self.every), dtype=torch.float32, device="cuda"),
+                x0=op.zeros(richm.F32), xK=op.zeros(richm.F32), g=op.zeros(richm.F32),
+                work=op.workspace(op._ws("richm_adjoint_workspace", richm.F32, self.every)),
+                acts=torch.empty(richm.meta_acts_size(B, self.m), dtype=torch.float32, device="cuda"),
+                gw=torch.empty(B, self.m, dtype=torch.float32, device="cuda"),
+                ga=torch.empty(B, self.m, dtype=torch.float32, device="cuda"),
+                gP=torch.empty(self.P.numel(), dtype=torch.float32, device="cuda"),
+                mwork=torch.empty(B * self.P.numel() * 4, dtype=torch.uint8, device="cuda"),
+            )
+        return self.ws[key]
+
+    def loss_and_grad(self, batch: Batch):
+        """Loss (device FP64 scalar) and parameter gradient (device FP32)."""
+        W = self._work(batch)
+        op = batch.op
+        w, a = richm.meta_forward(self.P, batch.X, batch.G, self.m, W["acts"])
+        op.forward_checkpointed(richm.F32, W["x0"], batch.b, w, a, None, self.m, self.K, self.every, 0, W["ck"],
+                                W["xK"], work=W["work"])
+        loss = op.loss_log_residual(richm.F32, W["xK"], batch.b, W["g"], work=W["work"])
+        op.sweeps_adjoint(richm.F32, W["ck"], self.every, batch.b, W["g"], w, a, None, self.m, self.K, 0,
+                          W["gw"], W["ga"], None, None, work=W["work"])
+        gP = richm.meta_backward(self.P, batch.X, batch.G, W["acts"], self.m, W["gw"], W["ga"], W["gP"], W["mwork"])
+        return loss, gP
+
+    def step(self, batch: Batch):
+        loss, gP = self.loss_and_grad(batch)
+        self.t += 1
+        richm.adam_step(self.P, gP, self.m1, self.m2, self.t, lr=self.lr)
+        return loss
+
+    def params(self) -> np.ndarray:
+        return self.P.detach().cpu().numpy()
+
+
+def make_batches(nbatches=8, B=64, n=255, seed=1000):
+    import richm_synth as synth
+    out = []
+    for j in range(nbatches):
+        insts = synth.batched_aniso(B, sizes=(n,), param_seed=seed + j)
+        out.append(Batch(insts, seed=seed + 500 + j))
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--batches", type=int, default=8)
+    ap.add_argument("--n", type=int, default=255)
+    ap.add_argument("--save", action="store_true")
+    args = ap.parse_args(argv)
+    params, src = meta_mod.load_params(16, prefer_trained=False)
+    tr = Trainer(params, lr=args.lr)
+    batches = make_batches(args.batches, n=args.n)
+    t0 = time.time()
+    hist = []
+    for s in range(args.steps):
+        loss = tr.step(batches[s % len(batches)])
+        if s % 25 == 0 or s == args.steps - 1:
+            hist.append((s, float(loss.item())))
+            print(f"step {s:5d} loss {hist[-1][1]:.4f} ({time.time() - t0:.1f} s)", flush=True)
+    if args.save:
+        os.makedirs(meta_mod.PARAM_DIR, exist_ok=True)
+        np.save(meta_mod.trained_path(16), tr.params())
+    return hist
+
+
+if __name__ == "__main__":
+    main()

@@ -69,3 +69,19 @@ def period_amplification(w, a, at, G, k_start, K, npts=4001):
         T[:, 1, 0] = 1.0
         P = P @ T
     return amps
+
+
+def fp32_bound(w, a, at, G, k_start, K, xmax, bmax):
+    """Rounding bound for K FP32 sweeps started from the same state as an FP64 run:
+    16 u sum_k amp_k ((1+|a|+|at|) |x| + |w| (|b| + G (1+2|at|) |x|)), with amp_k the
+    largest per-mode transfer norm from sweep k+1 to the end."""
+    u = 2.0 ** -24
+    amps = period_amplification(w, a, at, G, k_start, K)
+    tot = 0.0
+    for k in range(K):
+        i = (k_start + k) % len(w)
+        ai = 0.0 if a is None else abs(a[i])
+        ati = ai if at is None else abs(at[i])
+        per = (1 + ai + ati) * xmax + abs(w[i]) * (bmax + G * (1 + 2 * ati) * xmax)
+        tot += amps[k] * per
+    return 16.0 * u * tot

@@ -1,0 +1,175 @@
+"""Parity at the workloads' full sizes, in the launch configuration the benchmark uses.
+
+Where the oracle cannot run the whole batch, it evaluates sampled outputs one by one:
+after K sweeps a point depends only on inputs within distance K, so the oracle runs the
+same iteration on that window (oracle.sampling). Points are chosen at corners, edges,
+tile boundaries and at random.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import richm_synth as synth
+from gpu_util import coef, fp32_bound, from_dev, make_op, period_amplification, to_dev
+from oracle.fourier import fourier_correction
+from oracle.iterations import chebyshev_weights, inner_steps, semi_iteration_weights
+from oracle.operators import assemble_helmholtz, assemble_q1, gershgorin_max, helmholtz_wavenumber
+from oracle.sampling import sampled_sweeps
+from paper_2412_08076_gb300 import meta as meta_mod
+from paper_2412_08076_gb300 import richm
+
+pytestmark = pytest.mark.gpu
+
+
+def _points(n, rng, k=10):
+    pts = {(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (n // 2, 0), (63, min(n - 1, 119)),
+           (64, min(n - 1, 120)), (min(n - 1, 127), min(n - 1, 124)), (min(n - 1, 200), min(n - 1, 240))}
+    while len(pts) < k:
+        pts.add((int(rng.integers(0, n)), int(rng.integers(0, n))))
+    return sorted(pts)
+
+
+def test_config1_fp64_richardson8_residual_history():
+    # 63^2, eps = 1e-2, theta = pi/6, b ~ U[-1,1] seed 0, x0 = 0, m = 8 Chebyshev weights from
+    # the Gershgorin bound with lmin = lmax / 30, 400 sweeps and every residual
+    inst, b = synth.single_aniso()
+    op = make_op([inst])
+    A = assemble_q1(inst.n, inst.eps, inst.theta)
+    G = op.gershgorin()[0]
+    assert abs(G - gershgorin_max(A)) <= 1e-14 * G
+    w = np.array(richm.chebyshev_weights(G, G / 30.0, 8))
+    np.testing.assert_allclose(w, chebyshev_weights(G, G / 30.0, 8), rtol=1e-15)
+    X = op.zeros(richm.F64)
+    B = to_dev(op, [b], richm.F64)
+    W = coef(w[None, :], richm.F64)
+    ws = op.workspace(op._ws("richm_sweeps_workspace", richm.F64))
+    rw = op.workspace(op._ws("richm_residual_workspace"))
+    hist = []
+    for k in range(400):
+        op.apply_sweeps(richm.F64, X, None, B, W, K=1, m=8, k_start=k, work=ws)
+        hist.append(op.residual_norm(richm.F64, X, B, work=rw)[2])
+    hist = torch.cat(hist).cpu().numpy()
+    u = np.zeros(inst.n ** 2)
+    ref = []
+    for k in range(400):
+        u, _ = inner_steps(A, b.ravel(), u, None, w, K=1, k_start=k)
+        ref.append(np.linalg.norm(b.ravel() - A @ u) / np.linalg.norm(b))
+    ref = np.array(ref)
+    assert np.abs(hist - ref).max() <= 1e-10 * ref.max()
+    g = from_dev(op, X, richm.F64)[0].ravel()
+    assert np.abs(g - u).max() <= 1e-12 * np.abs(u).max()
+
+
+def test_config2_batched_fused_sweeps_sampled():
+    insts = synth.batched_aniso(256, (127, 255, 511), param_seed=1)
+    op = make_op(insts)
+    fuse, _ = op.autotune(16)
+    G = np.array(op.gershgorin())
+    wn = (meta_mod.chebyshev_unit_weights(16)[None, :] / G[:, None]).astype(np.float32)
+    a = np.full_like(wn, 0.3)
+    rng = np.random.default_rng(5)
+    # one random FP32 state for every instance (same values on both sides)
+    x0 = [(0.5 * synth.rhs_uniform(501, i, t.n)).astype(np.float32) for i, t in enumerate(insts)]
+    xp0 = [(x - 0.01 * synth.rhs_uniform(502, i, t.n)).astype(np.float32) for i, (x, t) in
+           enumerate(zip(x0, insts))]
+    bs = [synth.rhs_uniform(2, i, t.n).astype(np.float32) for i, t in enumerate(insts)]
+    X, XP, B = to_dev(op, x0, richm.F32), to_dev(op, xp0, richm.F32), to_dev(op, bs, richm.F32)
+    K, k_start = 16, 5
+    op.apply_sweeps(richm.F32, X, XP, B, coef(wn, richm.F32), coef(a, richm.F32), None, K=K, m=16,
+                    k_start=k_start, fuse=fuse)
+    got = from_dev(op, X, richm.F32)
+    for i in list(range(0, 256, 23)) + [255]:
+        t = insts[i]
+        pts = _points(t.n, rng, 8)
+        ref = sampled_sweeps(("q1", t.eps, t.theta), t.n, x0[i].astype(np.float64),
+                             (x0[i] - xp0[i]).astype(np.float64), bs[i].astype(np.float64),
+                             wn[i].astype(np.float64), a[i].astype(np.float64), None, K, pts, k_start=k_start)
+        bound = fp32_bound(wn[i].astype(np.float64), a[i].astype(np.float64), None, G[i], k_start, K,
+                           max(1.0, np.abs(ref).max()), 1.0)
+        for (p, q), r in zip(pts, ref):
+            assert abs(got[i][p, q] - r) <= bound, (i, t.n, p, q, got[i][p, q], r, bound)
+
+
+def test_config2_full_solve_one_refinement_cycle_matches_oracle_split():
+    # the solver's first refinement cycle (64 FP32 sweeps + FP64 update + FP64 residual)
+    # against the oracle's FP64 split iteration, sampled at full size
+    insts = synth.batched_aniso(256, (127, 255, 511), param_seed=1)
+    op = make_op(insts)
+    G = np.array(op.gershgorin())
+    wn = (meta_mod.chebyshev_unit_weights(16)[None, :] / G[:, None]).astype(np.float32)
+    a = np.full_like(wn, 0.3)
+    rhs = synth.batched_rhs(insts, seed=2)
+    B = to_dev(op, rhs, richm.F64)
+    X = op.zeros(richm.F64)
+    S = richm.Solver(op, op.solve_opts(16, tol=0.0, max_sweeps=10**6), coef(wn, richm.F32), coef(a, richm.F32))
+    S.start(B, X)
+    S.step(1)
+    got = from_dev(op, X, richm.F64)
+    rng = np.random.default_rng(9)
+    for i in (0, 3, 100, 255):
+        t = insts[i]
+        pts = _points(t.n, rng, 6)
+        ref = sampled_sweeps(("q1", t.eps, t.theta), t.n, np.zeros((t.n, t.n)), None, rhs[i], wn[i].astype(np.float64),
+                             a[i].astype(np.float64), None, 64, pts)
+        # FP32 inner sweeps from x = 0: the derived rounding bound over the 64 sweeps
+        bound = fp32_bound(wn[i].astype(np.float64), a[i].astype(np.float64), None, G[i], 0, 64,
+                           max(np.abs(ref).max(), 1.0), 1.0)
+        for (p, q), r in zip(pts, ref):
+            assert abs(got[i][p, q] - r) <= bound, (i, p, q, got[i][p, q], r, bound)
+    S.close()
+
+
+def test_config4_two_level_cycle_full_size_one_rhs_checked():
+    n, batch = 1023, 32
+    inst = synth.AnisoInstance(1e-4, math.pi / 3, n)
+    op = make_op([inst] * batch)
+    A = assemble_q1(n, inst.eps, inst.theta)
+    G = gershgorin_max(A)
+    w = semi_iteration_weights(G, 8)
+    S = synth.fourier_symbol(n, seed=3)
+    rhs = [synth.rhs_uniform(40, i, n) for i in range(batch)]
+    B32 = to_dev(op, rhs, richm.F32)
+    X = op.zeros(richm.F32)
+    W = coef(np.tile(w, (batch, 1)), richm.F32)
+    op.apply_sweeps(richm.F32, X, None, B32, W, K=8, m=8)
+    op.fourier_correction(X, B32, torch.tensor(S.astype(np.complex64), device="cuda"))
+    got = from_dev(op, X, richm.F32)
+    for i in (0, 31):
+        f = rhs[i].astype(np.float32).astype(np.float64).ravel()
+        u, _ = inner_steps(A, f, np.zeros(n * n), None, w.astype(np.float32).astype(np.float64), K=8)
+        ref = fourier_correction(A, f, u, S.astype(np.complex64).astype(np.complex128))
+        assert np.linalg.norm(got[i].ravel() - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_config5_helmholtz_2047_sampled_and_residual_reduction():
+    n, batch, m = 2047, 16, 8
+    k = helmholtz_wavenumber(n)
+    op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, n, 1.0, 0.0, k)] * batch)
+    h = 1.0 / (n + 1)
+    w = synth.helmholtz_weights(m, h, seed=4).astype(np.float32).astype(np.float64)
+    a = np.full(m, 0.3)
+    srcs = synth.point_sources(n, batch, seed=5)
+    rhs = [np.zeros((n, n), np.complex128) for _ in range(batch)]
+    for s, (i, j) in enumerate(srcs):
+        rhs[s][i, j] = 1.0
+    B = to_dev(op, rhs, richm.C64)
+    X, XP = op.zeros(richm.C64), op.zeros(richm.C64)
+    W, Al = coef(np.tile(w, (batch, 1)), richm.C64), coef(np.tile(a, (batch, 1)), richm.C64)
+    K1 = 8
+    op.apply_sweeps(richm.C64, X, XP, B, W, Al, None, K=K1, m=m)
+    got = from_dev(op, X, richm.C64)
+    for s in (0, 7, 15):
+        i0, j0 = srcs[s]
+        pts = [(i0, j0), (max(0, i0 - 3), j0), (i0, min(n - 1, j0 + 5)), (0, 0), (n - 1, n - 1)]
+        ref = sampled_sweeps(("helmholtz", k), n, np.zeros((n, n), np.complex128), None, rhs[s], w, a, None, K1, pts)
+        for (p, q), r in zip(pts, ref):
+            assert abs(got[s][p, q] - r) <= 1e-5 * max(abs(r), 1e-6 * np.abs(ref).max()) + 1e-12
+    # residual reduction after 128 sweeps, one source, against the full oracle
+    op.apply_sweeps(richm.C64, X, XP, B, W, Al, None, K=128 - K1, m=m, k_start=K1)
+    _, _, rel = op.residual_norm(richm.C64, X, B)
+    H = assemble_helmholtz(n, k)
+    u, _ = inner_steps(H, rhs[0].ravel(), np.zeros(n * n, np.complex128), None, w, a, K=128)
+    rel_o = np.linalg.norm(rhs[0].ravel() - H @ u) / np.linalg.norm(rhs[0])
+    assert abs(rel[0].item() - rel_o) <= 1e-4 * rel_o, (rel[0].item(), rel_o)

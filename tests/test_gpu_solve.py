@@ -65,12 +65,13 @@ def _solve_setup(sizes, m=16, beta=0.3, seed=5):
     return insts, op, As, w, a, bs
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_solve_to_1e10_checked_by_oracle(use_graph):
-    insts, op, As, w, a, bs = _solve_setup([1, 2, 15, 31, 63, 64])
+@pytest.mark.parametrize("use_graph,fuse", [(1, 1), (0, 1), (1, 4), (1, 8)])
+def test_solve_to_1e10_checked_by_oracle(use_graph, fuse):
+    insts, op, As, w, a, bs = _solve_setup([1, 2, 15, 31, 63, 64, 130])
     B = to_dev(op, bs, richm.F64)
     X = op.zeros(richm.F64)
-    opts = op.solve_opts(16, tol=1e-10, max_sweeps=400000, refine_every=64, inner=richm.F32, use_graph=use_graph)
+    opts = op.solve_opts(16, tol=1e-10, max_sweeps=400000, refine_every=64, inner=richm.F32, use_graph=use_graph,
+                         fuse=fuse)
     st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None, opts)
     assert st == richm.OK, info
     xs = from_dev(op, X, richm.F64)
@@ -110,7 +111,8 @@ def test_fp64_inner_solver_follows_the_oracle_iteration():
         split = refined_steps(As[i], bs[i].ravel(), np.zeros(t.n * t.n), 160, w[i], a[i], refine_every=32)
         assert info[i][0] == 160
         assert np.linalg.norm(xs[i].ravel() - ref) <= 1e-11 * np.linalg.norm(ref)
-        assert np.linalg.norm(split - ref) <= 1e-12 * np.linalg.norm(ref)
+        # FP64 rounding inside a period is amplified by the large Chebyshev steps
+        assert np.linalg.norm(split - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
 def test_solver_session_steps_and_reports():

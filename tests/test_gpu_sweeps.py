@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import richm_synth as synth
-from gpu_util import coef, from_dev, make_op, nag_weights, period_amplification, to_dev
+from gpu_util import coef, fp32_bound, from_dev, make_op, nag_weights, period_amplification, to_dev
 from oracle.iterations import inner_steps, jacobi_binv
 from oracle.operators import assemble_helmholtz, assemble_q1, gershgorin_max, helmholtz_wavenumber
 from paper_2412_08076_gb300 import richm
@@ -22,7 +22,7 @@ def _instances(seed=11, sizes=SIZES):
     return [synth.AnisoInstance(10 ** (-3 * u[2 * i]), math.pi * u[2 * i + 1], n) for i, n in enumerate(sizes)]
 
 
-def _run_case(dtype, variant, K, k_start=0, precond=0, sizes=SIZES):
+def _run_case(dtype, variant, K, k_start=0, precond=0, sizes=SIZES, fuse=0):
     insts = _instances(sizes=sizes)
     op = make_op(insts)
     m = 6
@@ -58,7 +58,7 @@ def _run_case(dtype, variant, K, k_start=0, precond=0, sizes=SIZES):
     B = to_dev(op, bs, dtype)
     op.apply_sweeps(dtype, X, XP if a is not None else None, B, coef(w, dtype),
                     None if a is None else coef(a, dtype), None if at is None else coef(at, dtype),
-                    K=K, m=m, k_start=k_start, precond=precond)
+                    K=K, m=m, k_start=k_start, precond=precond, fuse=fuse)
     got = from_dev(op, X, dtype)
     gotp = from_dev(op, XP, dtype) if a is not None else None
     out = []
@@ -94,18 +94,7 @@ def test_fp64_zero_sweeps_is_noop():
 
 
 def _fp32_bound(w, a, at, G, k_start, K, xmax, bmax):
-    """Rounding bound for K FP32 sweeps started from the same state:
-    sum_k amp_k * u * c * ((1+|a|+|at|) |x| + |w| (|b| + G (1+2|at|) |x|))."""
-    u = 2.0 ** -24
-    amps = period_amplification(w, a, at, G, k_start, K)
-    tot = 0.0
-    for k in range(K):
-        i = (k_start + k) % len(w)
-        ai = 0.0 if a is None else abs(a[i])
-        ati = ai if at is None else abs(at[i])
-        per = (1 + ai + ati) * xmax + abs(w[i]) * (bmax + G * (1 + 2 * ati) * xmax)
-        tot += amps[k] * per
-    return 16.0 * u * tot
+    return fp32_bound(w, a, at, G, k_start, K, xmax, bmax)
 
 
 @pytest.mark.parametrize("variant", ["richardson", "nag", "nagex"])
@@ -205,3 +194,38 @@ def test_pack_unpack_roundtrip_and_halo_zero():
             n = op.ns[i]
             blk = host[lay.offset:lay.offset + lay.rows * lay.pitch].reshape(lay.rows, lay.pitch)
             assert np.all(blk[0] == 0) and np.all(blk[-1] == 0) and np.all(blk[:, n:] == 0)
+
+
+@pytest.mark.parametrize("fuse", [4, 8])
+@pytest.mark.parametrize("variant", ["nag", "richardson", "nagex"])
+def test_fp32_fused_sweeps_match_oracle(fuse, variant):
+    # temporally blocked passes (+ a one-sweep remainder) against the oracle from the
+    # same FP32 state, bounded by the derived rounding bound; sizes span one and
+    # several 128-column tiles (n > 128 has interior tile edges) and ragged 64-row blocks
+    sizes = [1, 5, 63, 127, 128, 129, 200, 255, 300]
+    K, k_start = 2 * fuse + 1, 3
+    for g, ref, gp, refp, w, a, at, G in _run_case(richm.F32, variant, K=K, k_start=k_start, sizes=sizes,
+                                                   fuse=fuse):
+        xmax = max(np.abs(ref).max(), 1.0)
+        bound = _fp32_bound(w, a, at, G, k_start, K, xmax, 1.0)
+        assert np.abs(g - ref).max() <= bound
+        if gp is not None:
+            assert np.abs(gp - refp).max() <= bound
+
+
+@pytest.mark.parametrize("fuse", [4, 8])
+def test_fused_equals_single_sweeps_closely(fuse):
+    # same arithmetic per point, different launch structure: agreement to a few ulps
+    sizes = [31, 127, 129, 255, 511]
+    a1 = _run_case(richm.F32, "nag", K=2 * fuse, k_start=1, sizes=sizes, fuse=1)
+    a2 = _run_case(richm.F32, "nag", K=2 * fuse, k_start=1, sizes=sizes, fuse=fuse)
+    for (g1, ref, *_), (g2, *_r) in zip(a1, a2):
+        scale = max(np.abs(ref).max(), 1.0)
+        assert np.abs(g1 - g2).max() <= 1e-5 * scale
+
+
+def test_autotune_picks_a_supported_pass_length():
+    insts = _instances(sizes=[127, 255, 511, 63])
+    op = make_op(insts)
+    fuse, ms = op.autotune(16, momentum=True)
+    assert fuse in (1, 4, 8) and ms > 0
