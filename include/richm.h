@@ -188,6 +188,24 @@ richm_status richm_residual_norm(richm_operator* op, richm_dtype dtype, const vo
                                  double* rnorm, double* bnorm, double* rel, void* r_out,
                                  void* work, size_t work_bytes, void* stream);
 
+/* The same residual and norms as richm_residual_norm for callers that cannot
+ * allocate device memory where they need them: code running inside a memory pool or
+ * allocator callback it does not own, or a process whose device memory another
+ * framework reserved up front. The paper has no counterpart; this is an interface
+ * convenience. The scratch (per-tile partial sums and per-instance tile offsets)
+ * lives in file-scope device arrays of the library, present on every GPU that loads
+ * it until the process exits (1 MiB + 256 KiB); the call allocates nothing.
+ * Limits: at most 65536 warp tiles (tiles of 16 rows x 32 lanes x one 16-byte vector,
+ * e.g. about 33 M FP64 unknowns) and 65536 instances; larger batches return
+ * RICHM_ERR_NOMEM before any work is queued. The first call on a device looks up the
+ * arrays' device addresses (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. Every call shares the arrays and rewrites all
+ * the entries it reads, so nothing needs clearing, but calls that overlap on the GPU
+ * (different streams, threads or devices' contexts racing on one array) race: order
+ * them. Outputs and error behaviour are those of richm_residual_norm. */
+richm_status richm_residual_norm_static(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
+                                        double* rnorm, double* bnorm, double* rel, void* r_out, void* stream);
+
 /* ------------------------------------------------------------------ solve */
 
 typedef struct {

@@ -73,6 +73,7 @@ _SIGS = {
     "richm_autotune_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_autotune": (_I, [_P, _I, _I, _P, _SZ, _P, C.POINTER(_I), C.POINTER(C.c_float)]),
     "richm_residual_norm": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "richm_residual_norm_static": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "richm_solve_workspace": (_I, [_P, C.POINTER(richm_solve_opts), C.POINTER(_SZ)]),
     "richm_solve": (_I, [_P, _P, _P, _P, _P, _P, C.POINTER(richm_solve_opts), C.POINTER(richm_solve_info), _P, _SZ,
                          _P]),
