@@ -10,8 +10,12 @@
 // the physical boundary need no halo there; at interior tile edges the result of
 // level s is wrong in the s outermost columns, so neighbouring tiles overlap by TL
 // columns on each side and only the inner columns are stored. Each pass reads x_k,
-// x_{k-1}, b once (plus the overlaps and TL halo rows above and below each 64-row
+// x_{k-1}, b once (plus the overlaps and TL halo rows above and below each 128-row
 // tile) and writes the last two levels: 20 bytes per unknown per TL sweeps.
+// Input rows are prefetched PF row steps ahead with cp.async into per-warp
+// shared-memory rings (each lane copies and later reads only its own 16 bytes, so no
+// barrier is needed), which keeps HBM latency out of the level pipeline; the b rows
+// stay in their ring until the last level has used them.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -36,18 +40,196 @@ struct SweepTArgs {
   const int* active;
 };
 
-template <int TL, bool MOM, bool PRE>
-__global__ void __launch_bounds__(kFuseWarps * 32) sweepT_kernel(const SweepTArgs A) {
+// Per-warp state of the pipeline. Window slots rotate by phase: at phase p the new
+// row of every level goes into slot p; after it, U = slot (p+1)%3, C = slot (p+2)%3,
+// D = slot p. Unrolling the row loop by three makes every slot index a constant.
+// Each lane keeps only its own four values per row; the neighbours across lanes
+// are exchanged by shuffles when the stencil is applied.
+// Keep each window row's two cross-lane neighbours in registers (computed once when
+// the row enters the window) instead of re-shuffling them for every use.
+constexpr bool kStoreNeighbours = false;
+
+template <int TL>
+struct FusedState {
+  float Y[TL + 1][3][4];   // level s: rows of y_{s-1} (this lane's four columns)
+  float YL[TL + 1][3];     // their left / right cross-lane neighbours (kStoreNeighbours)
+  float YR[TL + 1][3];
+  float xc[TL + 1][4];     // level s: x_{s-1} on the centre row (MOM and NAGex only)
+  float vc[TL + 1][4];     // level s: x_{s-1} - x_{s-2} on the centre row
+  float prevx[TL + 1][4];  // output of level s at the previous row step
+};
+
+constexpr int kPrefetch = 2;  // row steps between issuing a row's copies and using it
+
+template <int TL>
+struct FusedRings {
+  // one spare slot in each ring: a slot is re-targeted two row steps after its last read
+  static constexpr int NS = kPrefetch + 2;       // x_k and x_{k-1} row slots
+  static constexpr int NB = TL + kPrefetch + 2;  // b row slots (kept until level TL)
+  static constexpr int FLOATS = (2 * NS + NB) * 128;
+};
+
+struct FusedCtx {
+  const float* xb;
+  const float* xpb;
+  const float* bb;
+  float* ox;
+  float* oxp;
+  float* ring;  // this warp's rings: x[NS][128], xp[NS][128], b[NB][128]
+  int n, pitch, c0, lane, r0, r1, rlast;
+  bool live, store_cols;
+  float sc, sax, say, sd1, sd2;
+  float ml, mr;   // 0 where this lane's left / right neighbour lies beyond the warp, else 1
+  float cm[4];    // 1 for this lane's columns inside the domain, else 0
+};
+
+// Neighbours of a row from adjacent lanes; the warp's edge lanes get 0 (their
+// neighbour is either outside the domain, hence 0, or in the tile overlap, whose
+// values are discarded). The masks are multiplies, which keeps the selects off the
+// integer pipe.
+__device__ __forceinline__ void row_neighbours_m(RowT<float, 4>& r, float ml, float mr) {
+  r.yl = ml * __shfl_up_sync(0xffffffffu, r.y[3], 1);
+  r.yr = mr * __shfl_down_sync(0xffffffffu, r.y[0], 1);
+}
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int nbytes = valid ? 16 : 0;  // 0: zero-fill, no global read
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ int ring_slot(int r, int nslots) { return (r + 64 * nslots) % nslots; }
+
+// Issue the copies of input row r (x_k, x_{k-1}, b) into the rings (zero-filled
+// outside rows 1..n, beyond the tile's last needed row, or beyond the row pitch).
+template <int TL, bool MOM>
+__device__ __forceinline__ void issue_row(const FusedCtx& c, int r) {
+  using R = FusedRings<TL>;
+  const bool valid = (r >= 1) && (r <= c.n) && (r <= c.rlast) && c.live;
+  const long long ro = (long long)(valid ? r : 0) * c.pitch + (c.live ? c.c0 : 0);
+  float* xr = c.ring + ring_slot(r, R::NS) * 128 + c.lane * 4;
+  cp_async16(xr, c.xb + ro, valid);
+  if (MOM) cp_async16(c.ring + (R::NS + ring_slot(r, R::NS)) * 128 + c.lane * 4, c.xpb + ro, valid);
+  cp_async16(c.ring + (2 * R::NS + ring_slot(r, R::NB)) * 128 + c.lane * 4, c.bb + ro, valid);
+  cp_async_commit();
+}
+
+// One row step of the pipeline at input row rr and window phase PH.
+// NAGF: at == a, so x_{k+1} = y + w (b - A y) needs only the window.
+template <int TL, bool MOM, bool NAGF, int PH>
+__device__ __forceinline__ void fused_step(int rr, const FusedCtx& c, FusedState<TL>& st, const float* wl,
+                                           const float* al, const float* atl) {
+  using R = FusedRings<TL>;
+  constexpr int VW = 4;
+  constexpr int SD = PH, SU = (PH + 1) % 3, SC = (PH + 2) % 3;
+  issue_row<TL, MOM>(c, rr + kPrefetch);
+  cp_async_wait<kPrefetch>();  // the copies of row rr have landed
+  float x0[VW], xm[VW];
+  {
+    const float4 X = *reinterpret_cast<const float4*>(c.ring + ring_slot(rr, R::NS) * 128 + c.lane * 4);
+    x0[0] = X.x; x0[1] = X.y; x0[2] = X.z; x0[3] = X.w;
+    if (MOM) {
+      const float4 XP = *reinterpret_cast<const float4*>(c.ring + (R::NS + ring_slot(rr, R::NS)) * 128 + c.lane * 4);
+      xm[0] = XP.x; xm[1] = XP.y; xm[2] = XP.z; xm[3] = XP.w;
+    } else {
+      xm[0] = xm[1] = xm[2] = xm[3] = 0.f;
+    }
+  }
+  float newx[TL + 1][VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) newx[0][e] = x0[e];
+#pragma unroll
+  for (int s = 1; s <= TL; ++s) {
+    const int row = rr - s;
+    const float4 B4 = *reinterpret_cast<const float4*>(c.ring + (2 * R::NS + ring_slot(row, R::NB)) * 128 + c.lane * 4);
+    const float Bv[VW] = {B4.x, B4.y, B4.z, B4.w};
+    // extend level s's window with row rr - s + 1 of y_{s-1}
+    float* Yn = st.Y[s][SD];
+    float vn[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const float xs1 = newx[s - 1][e];
+      const float xs2 = (s == 1) ? xm[e] : st.prevx[s - 2][e];
+      vn[e] = MOM ? xs1 - xs2 : 0.f;
+      Yn[e] = MOM ? fmaf(atl[s], vn[e], xs1) : xs1;
+    }
+    // neighbours across lanes by shuffles (zero beyond the warp's 128 columns)
+    RowT<float, VW> YU, YC, YD;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      YU.y[e] = st.Y[s][SU][e];
+      YC.y[e] = st.Y[s][SC][e];
+      YD.y[e] = Yn[e];
+    }
+    if constexpr (kStoreNeighbours) {
+      row_neighbours_m(YD, c.ml, c.mr);
+      st.YL[s][SD] = YD.yl;
+      st.YR[s][SD] = YD.yr;
+      YU.yl = st.YL[s][SU];
+      YU.yr = st.YR[s][SU];
+      YC.yl = st.YL[s][SC];
+      YC.yr = st.YR[s][SC];
+    } else {
+      row_neighbours_m(YU, c.ml, c.mr);
+      row_neighbours_m(YC, c.ml, c.mr);
+      row_neighbours_m(YD, c.ml, c.mr);
+    }
+    float Ay[VW];
+    apply_q1<float, VW, float>(YU, YC, YD, c.sc, c.sax, c.say, c.sd1, c.sd2, Ay);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      float nx;
+      if (!MOM || NAGF) {
+        nx = fmaf(wl[s], Bv[e] - Ay[e], YC.y[e]);  // NAG: y = x + a v is the window centre
+      } else {
+        nx = fmaf(wl[s], Bv[e] - Ay[e], fmaf(al[s], st.vc[s][e], st.xc[s][e]));
+        st.xc[s][e] = newx[s - 1][e];
+        st.vc[s][e] = vn[e];
+      }
+      newx[s][e] = nx * c.cm[e];
+    }
+    if (row < 1 || row > c.n) {  // warp-uniform: rows outside the domain stay zero
+#pragma unroll
+      for (int e = 0; e < VW; ++e) newx[s][e] = 0.f;
+    }
+  }
+  if (c.store_cols) {
+    const int ra = rr - TL, rb = rr - TL + 1;
+    if (ra >= c.r0 && ra <= c.r1) {
+      VecN<float, VW> O;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) O.v[e] = newx[TL][e];
+      stv<float, VW>(c.ox + (long long)ra * c.pitch + c.c0, O);
+    }
+    if (MOM && rb >= c.r0 && rb <= c.r1) {
+      VecN<float, VW> O;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) O.v[e] = newx[TL - 1][e];
+      stv<float, VW>(c.oxp + (long long)rb * c.pitch + c.c0, O);
+    }
+  }
+  if (MOM) {
+#pragma unroll
+    for (int s = 0; s + 2 <= TL; ++s)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) st.prevx[s][e] = newx[s][e];
+  }
+}
+
+template <int TL, bool MOM, bool PRE, bool NAGF>
+__global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kernel(const SweepTArgs A) {
   constexpr int VW = 4;
   constexpr int STRIDE = 128 - 2 * TL;
+  extern __shared__ __align__(16) float fused_smem[];
   const int lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kFuseWarps + (threadIdx.x >> 5);
   if (wt >= A.ntiles) return;
   const Tile t = A.tiles[wt];
   if (A.active && A.active[t.inst] == 0) return;
   const Inst& I = A.insts[t.inst];
-  const int n = I.n, pitch = I.pitch;
-  const float sc = (float)I.c, sax = (float)I.ax, say = (float)I.ay, sd1 = (float)I.d1, sd2 = (float)I.d2;
   const float dv = PRE ? (float)I.dinv : 1.f;
 
   float wl[TL + 1], al[TL + 1], atl[TL + 1];
@@ -58,112 +240,62 @@ __global__ void __launch_bounds__(kFuseWarps * 32) sweepT_kernel(const SweepTArg
     al[s] = MOM ? A.a[ci] : 0.f;
     atl[s] = MOM ? (A.at ? A.at[ci] : al[s]) : 0.f;
   }
-
-  const int cs = t.tx * STRIDE;            // first column of the tile
-  const int c0 = cs + lane * VW;           // this lane's first column
-  const bool live = c0 < pitch;
-  const bool last_tile = (cs + 128 >= n);
+  FusedCtx c;
+  c.n = I.n;
+  c.pitch = I.pitch;
+  c.lane = lane;
+  c.sc = (float)I.c;
+  c.sax = (float)I.ax;
+  c.say = (float)I.ay;
+  c.sd1 = (float)I.d1;
+  c.sd2 = (float)I.d2;
+  const int cs = t.tx * STRIDE;  // first column of the tile
+  c.c0 = cs + lane * VW;         // this lane's first column
+  c.live = c.c0 < c.pitch;
+  c.ml = (lane == 0) ? 0.f : 1.f;
+  c.mr = (lane == 31) ? 0.f : 1.f;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) c.cm[e] = (c.c0 + e < c.n) ? 1.f : 0.f;
+  const bool last_tile = (cs + 128 >= c.n);
   const int vlo = cs + (t.tx > 0 ? TL : 0);
-  const int vhi = last_tile ? pitch : cs + 128 - TL;
-  const bool store_cols = live && c0 >= vlo && c0 + VW <= vhi;
-  const int r0 = t.ty * kFuseRows + 1;
-  const int r1 = min(r0 + kFuseRows - 1, n);
-  const float* xb = A.x + I.off;
-  const float* xpb = MOM ? A.xp + I.off : nullptr;
-  const float* bb = A.b + I.off;
-  float* ox = A.out_x + I.off;
-  float* oxp = MOM ? A.out_xp + I.off : nullptr;
+  const int vhi = last_tile ? c.pitch : cs + 128 - TL;
+  c.store_cols = c.live && c.c0 >= vlo && c.c0 + VW <= vhi;
+  c.r0 = t.ty * kFuseRows + 1;
+  c.r1 = min(c.r0 + kFuseRows - 1, c.n);
+  c.rlast = c.r1 + TL;
+  c.xb = A.x + I.off;
+  c.xpb = MOM ? A.xp + I.off : A.x + I.off;
+  c.bb = A.b + I.off;
+  c.ox = A.out_x + I.off;
+  c.oxp = MOM ? A.out_xp + I.off : nullptr;
+  c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<TL>::FLOATS;
 
-  // per-level state
-  RowT<float, VW> YU[TL + 1], YC[TL + 1], YD[TL + 1];
-  float xc[TL + 1][VW], vc[TL + 1][VW];   // centre row of level s: x_{s-1}, v_{s-1}
-  float prevx[TL + 1][VW];                // level s output of the previous iteration
-  float bd[TL + 1][VW];                   // b delay line: bd[s] = b[rr - s]
+  FusedState<TL> st;
 #pragma unroll
   for (int s = 0; s <= TL; ++s) {
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      YU[s].y[e] = YC[s].y[e] = YD[s].y[e] = 0.f;
-      xc[s][e] = vc[s][e] = prevx[s][e] = bd[s][e] = 0.f;
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+      for (int e = 0; e < VW; ++e) st.Y[s][q][e] = 0.f;
+      st.YL[s][q] = st.YR[s][q] = 0.f;
     }
-    YU[s].yl = YU[s].yr = YC[s].yl = YC[s].yr = YD[s].yl = YD[s].yr = 0.f;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) st.xc[s][e] = st.vc[s][e] = st.prevx[s][e] = 0.f;
   }
-
-  for (int rr = r0 - TL; rr <= r1 + TL; ++rr) {
+  // b rows above the tile's first input row are never loaded: zero their slots
+  for (int q = 0; q < FusedRings<TL>::FLOATS / 128; ++q)
+    *reinterpret_cast<float4*>(c.ring + q * 128 + lane * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int rstart = c.r0 - TL;
 #pragma unroll
-    for (int s = TL; s >= 1; --s)
-#pragma unroll
-      for (int e = 0; e < VW; ++e) bd[s][e] = bd[s - 1][e];
-    float x0[VW], xm[VW];
-    {
-      VecN<float, VW> X{}, XP{}, Bv{};
-      if (rr >= 1 && rr <= n && live) {
-        const long long ro = (long long)rr * pitch + c0;
-        X = ldv<float, VW>(xb + ro);
-        if (MOM) XP = ldv<float, VW>(xpb + ro);
-        Bv = ldv<float, VW>(bb + ro);
-      }
-#pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        x0[e] = X.v[e];
-        xm[e] = XP.v[e];
-        bd[0][e] = Bv.v[e];
-      }
-    }
-    float newx[TL + 1][VW];
-#pragma unroll
-    for (int e = 0; e < VW; ++e) newx[0][e] = x0[e];
-#pragma unroll
-    for (int s = 1; s <= TL; ++s) {
-      // extend level s's window with row rr - s + 1 of y_{s-1}
-      RowT<float, VW> Yn;
-      float vn[VW];
-#pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        const float xs1 = newx[s - 1][e];
-        const float xs2 = (s == 1) ? xm[e] : prevx[s - 2][e];
-        vn[e] = MOM ? xs1 - xs2 : 0.f;
-        Yn.y[e] = MOM ? xs1 + atl[s] * vn[e] : xs1;
-      }
-      row_neighbours<float, VW>(Yn, lane, 0.f, 0.f);
-      YU[s] = YC[s];
-      YC[s] = YD[s];
-      YD[s] = Yn;
-      // level s at row rr - s (centre of the window)
-      float Ay[VW];
-      apply_q1<float, VW, float>(YU[s], YC[s], YD[s], sc, sax, say, sd1, sd2, Ay);
-      const int row = rr - s;
-      const bool row_in = (row >= 1) && (row <= n);
-#pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        float nx = xc[s][e] + wl[s] * (bd[s][e] - Ay[e]);
-        if (MOM) nx = nx + al[s] * vc[s][e];
-        newx[s][e] = (row_in && (c0 + e) < n) ? nx : 0.f;
-        xc[s][e] = newx[s - 1][e];
-        vc[s][e] = vn[e];
-      }
-    }
-    // outputs: x_{k+TL} at row rr - TL, x_{k+TL-1} at row rr - TL + 1
-    if (store_cols) {
-      const int ra = rr - TL, rb = rr - TL + 1;
-      if (ra >= r0 && ra <= r1) {
-        VecN<float, VW> O;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) O.v[e] = newx[TL][e];
-        stv<float, VW>(ox + (long long)ra * pitch + c0, O);
-      }
-      if (MOM && rb >= r0 && rb <= r1) {
-        VecN<float, VW> O;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) O.v[e] = newx[TL - 1][e];
-        stv<float, VW>(oxp + (long long)rb * pitch + c0, O);
-      }
-    }
-#pragma unroll
-    for (int s = 0; s <= TL; ++s)
-#pragma unroll
-      for (int e = 0; e < VW; ++e) prevx[s][e] = newx[s][e];
+  for (int d = 0; d < kPrefetch; ++d) issue_row<TL, MOM>(c, rstart + d);
+  // rows r0-TL .. r1+TL in steps of three (a few extra steps at the end only
+  // compute rows that are neither stored nor used)
+  for (int rr = rstart; rr <= c.r1 + TL; rr += 3) {
+    fused_step<TL, MOM, NAGF, 0>(rr, c, st, wl, al, atl);
+    fused_step<TL, MOM, NAGF, 1>(rr + 1, c, st, wl, al, atl);
+    fused_step<TL, MOM, NAGF, 2>(rr + 2, c, st, wl, al, atl);
   }
+  cp_async_wait<0>();
 }
 
 richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
@@ -174,12 +306,16 @@ richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, cons
   SweepTArgs A{op->d_inst, tm->d_tiles, tm->ntiles, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, active};
   const int blocks = (tm->ntiles + kFuseWarps - 1) / kFuseWarps;
   const int thr = kFuseWarps * 32;
+  const size_t smem = (TL == 4 ? FusedRings<4>::FLOATS : FusedRings<8>::FLOATS) * sizeof(float) * kFuseWarps;
   const bool mom = a != nullptr;
-#define RICHM_FUSED(TLV)                                                                         \
-  if (mom && precond) sweepT_kernel<TLV, true, true><<<blocks, thr, 0, s>>>(A);                 \
-  else if (mom) sweepT_kernel<TLV, true, false><<<blocks, thr, 0, s>>>(A);                      \
-  else if (precond) sweepT_kernel<TLV, false, true><<<blocks, thr, 0, s>>>(A);                  \
-  else sweepT_kernel<TLV, false, false><<<blocks, thr, 0, s>>>(A);
+  const bool nag = mom && at == nullptr;  // at = a
+#define RICHM_FUSED(TLV)                                                                          \
+  if (nag && precond) sweepT_kernel<TLV, true, true, true><<<blocks, thr, smem, s>>>(A);         \
+  else if (nag) sweepT_kernel<TLV, true, false, true><<<blocks, thr, smem, s>>>(A);              \
+  else if (mom && precond) sweepT_kernel<TLV, true, true, false><<<blocks, thr, smem, s>>>(A);   \
+  else if (mom) sweepT_kernel<TLV, true, false, false><<<blocks, thr, smem, s>>>(A);             \
+  else if (precond) sweepT_kernel<TLV, false, true, false><<<blocks, thr, smem, s>>>(A);         \
+  else sweepT_kernel<TLV, false, false, false><<<blocks, thr, smem, s>>>(A);
   if (TL == 4) {
     RICHM_FUSED(4)
   } else if (TL == 8) {
