@@ -182,6 +182,28 @@ def oracle_sample_rate(instances, seconds: float = 12.0, sweeps_per_chunk: int =
     return dofs / el / 1e9, desc
 
 
+def kernel_traffic(kind: str, dofs: int):
+    """DRAM bytes per launch from the committed ncu summary of this kernel
+    (profiles/traffic.txt: kind, sha256 of its sources, bytes per unknown, sources),
+    scaled by unknowns; None when the sources changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) < 4 or parts[0] != kind:
+            continue
+        h = hashlib.sha256()
+        for f in parts[3:]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        return float(parts[2]) * dofs if h.hexdigest() == parts[1] else None
+    return None
+
+
 def run_reference(args):
     """The oracle as the reference arm: same metric and workload, bounded samples."""
     rank, world = dist_env()
@@ -312,30 +334,54 @@ def run_ours(args):
     value = total_dofs * REFINE * args.steps / (t_max_ms / 1e3) / 1e9
     launches_per_step = 1 + REFINE // fuse + 3  # meta forward, sweep passes, update, residual, reduce
 
-    # -- dominant kernel (the FP32 NAG sweep pass): launch duration by CUDA events on its stream
-    K = 192
+    # -- dominant kernel (the FP32 NAG sweep pass) and the one-sweep kernel: launch
+    #    durations by CUDA events on the launching stream
     xs = op.zeros(richm.F32)
     xps = op.zeros(richm.F32)
     b32 = op.zeros(richm.F32)
     b32.copy_(B64.to(torch.float32))
     ws = op.workspace(op._ws("richm_sweeps_workspace", richm.F32))
-    op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=fuse, work=ws)
-    torch.cuda.synchronize()
-    k0 = torch.cuda.Event(enable_timing=True)
-    k1 = torch.cuda.Event(enable_timing=True)
-    reps = 3
-    k0.record(stream)
-    for _ in range(reps):
-        op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=fuse, work=ws)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    launch_ms = k0.elapsed_time(k1) / (reps * K // fuse)
-    # algorithmic bytes per launch: one sweep reads x_k, x_{k-1}, b and writes x_{k+1}
-    # (16 B per unknown); a fused pass reads the same and writes two levels (20 B)
-    alg_bytes = (16.0 if fuse == 1 else 20.0) * dofs
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
-    kname = ("sweep1_kernel<float,NAG> (one FP32 NAG sweep per launch)" if fuse == 1 else
-             f"sweepT_kernel<{fuse},NAG> ({fuse} FP32 NAG sweeps per launch, temporal blocking)")
+
+    def launch_ms(f, K=192, reps=3):
+        op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=f, work=ws)
+        torch.cuda.synchronize()
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(reps):
+            op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=f, work=ws)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        return k0.elapsed_time(k1) / (reps * K // f)
+
+    one_ms = launch_ms(1)
+    one_gbs = 16.0 * dofs / (one_ms / 1e3) / 1e9  # read x_k, x_{k-1}, b; write x_{k+1}
+    if fuse == 1:
+        kname = "sweep1_kernel<float,NAG> (one FP32 NAG sweep per launch)"
+        alg_bytes = 16.0 * dofs
+        achieved = one_gbs
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": kernel_traffic("sweep1", dofs), "kernel": kname, "alg_bytes_per_launch": alg_bytes,
+                "launch_ms": one_ms, "sweeps_per_launch": 1, "peak_source": f"{peak_src} hbm_gbs (of measured)"}
+    else:
+        fused_ms = launch_ms(fuse)
+        kname = f"sweepT_kernel<{fuse},NAG> ({fuse} FP32 NAG sweeps per launch, temporal blocking)"
+        # instruction-issue bound: algorithmic FP32 work per unknown and sweep of the NAG
+        # 9-point update is 19 flops (y: 3, A y: 13, b - A y: 1, y + w r: 2); the peak
+        # is 152 SMs x 128 FP32 lanes x 2 flops (FMA) x the clock sampled under load
+        sm_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
+        fp32_peak = 152 * 128 * 2 * sm_ghz / 1e3  # TFLOP/s
+        flops = 19.0 * dofs * fuse
+        achieved = flops / (fused_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": kernel_traffic(f"sweepT{fuse}", dofs),
+                "kernel": kname, "alg_flops_per_launch": flops, "launch_ms": fused_ms, "sweeps_per_launch": fuse,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_ghz:.3f} GHz (sampled)",
+                "hbm_view": {"alg_bytes_per_launch": 20.0 * dofs,
+                             "achieved_gbs": 20.0 * dofs / (fused_ms / 1e3) / 1e9,
+                             "frac_of_measured_hbm": 20.0 * dofs / (fused_ms / 1e3) / 1e9 / hbm_peak},
+                "one_sweep_kernel": {"kernel": "sweep1_kernel<float,NAG>", "launch_ms": one_ms,
+                                     "achieved_gbs": one_gbs, "frac_of_measured_hbm": one_gbs / hbm_peak}}
 
     # -- e2e: host buffers through the public API (pinned H2D of b, one cycle, D2H of x)
     hb = dense_b.pin_memory()
@@ -440,10 +486,7 @@ def run_ours(args):
             "config": dict(workload_config(), dofs_per_rank=dofs, meta_params=psrc,
                            active_after_steps=active, sweeps_per_pass=fuse, autotune_ms_per_sweep=tune_ms,
                            solve_tol=SOLVE_TOL),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "kernel": kname,
-                         "alg_bytes_per_launch": alg_bytes, "launch_ms": launch_ms,
-                         "sweeps_per_launch": fuse, "peak_source": f"{peak_src} hbm_gbs (of measured)"},
+            "roofline": roof,
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc,
                              "host_cores": os.cpu_count()},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(dense_b.numel() * 8),

@@ -7,7 +7,7 @@ namespace richm {
 
 constexpr int kRows = 16;          // rows streamed by one warp tile
 constexpr int kWarpsPerBlock = 8;  // warp tiles per thread block
-constexpr int kFuseRows = 128;     // output rows of a fused-sweep warp tile
+constexpr int kFuseRows = 256;     // output rows of a fused-sweep warp tile
 
 // One forward sweep (see sweep.cu). `a == nullptr`: no momentum (xp unused);
 // `at == nullptr`: at = a. `active`: per-instance flags or nullptr (all active).

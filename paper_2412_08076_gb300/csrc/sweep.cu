@@ -34,7 +34,7 @@ struct SweepArgs {
 };
 
 template <typename E, bool MOM, bool PRE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep1_kernel(const SweepArgs<E> A) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) sweep1_kernel(const SweepArgs<E> A) {
   using S = typename RealOf<E>::type;
   constexpr int VW = VecWidth<E>::value;
   constexpr bool CPLX = IsCplx<E>::value;

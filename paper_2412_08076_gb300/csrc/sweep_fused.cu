@@ -10,7 +10,7 @@
 // the physical boundary need no halo there; at interior tile edges the result of
 // level s is wrong in the s outermost columns, so neighbouring tiles overlap by TL
 // columns on each side and only the inner columns are stored. Each pass reads x_k,
-// x_{k-1}, b once (plus the overlaps and TL halo rows above and below each 128-row
+// x_{k-1}, b once (plus the overlaps and TL halo rows above and below each 256-row
 // tile) and writes the last two levels: 20 bytes per unknown per TL sweeps.
 // Input rows are prefetched PF row steps ahead with cp.async into per-warp
 // shared-memory rings (each lane copies and later reads only its own 16 bytes, so no
@@ -46,13 +46,16 @@ struct SweepTArgs {
 // Each lane keeps only its own four values per row; the neighbours across lanes
 // are exchanged by shuffles when the stencil is applied.
 // Keep each window row's two cross-lane neighbours in registers (computed once when
-// the row enters the window) instead of re-shuffling them for every use.
-constexpr bool kStoreNeighbours = false;
+// the row enters the window) instead of re-shuffling them for every use: fewer
+// shuffles for 24 more registers, a gain for 8 sweeps per pass (2 blocks per SM
+// either way), a loss for 4 (it would spill at the 4-blocks-per-SM register cap).
+template <int TL>
+__host__ __device__ constexpr bool store_neighbours() { return TL >= 8; }
 
 template <int TL>
 struct FusedState {
   float Y[TL + 1][3][4];   // level s: rows of y_{s-1} (this lane's four columns)
-  float YL[TL + 1][3];     // their left / right cross-lane neighbours (kStoreNeighbours)
+  float YL[TL + 1][3];     // their left / right cross-lane neighbours (store_neighbours)
   float YR[TL + 1][3];
   float xc[TL + 1][4];     // level s: x_{s-1} on the centre row (MOM and NAGex only)
   float vc[TL + 1][4];     // level s: x_{s-1} - x_{s-2} on the centre row
@@ -164,7 +167,7 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx& c, FusedState
       YC.y[e] = st.Y[s][SC][e];
       YD.y[e] = Yn[e];
     }
-    if constexpr (kStoreNeighbours) {
+    if constexpr (store_neighbours<TL>()) {
       row_neighbours_m(YD, c.ml, c.mr);
       st.YL[s][SD] = YD.yl;
       st.YR[s][SD] = YD.yr;

@@ -55,3 +55,39 @@ def load_params(m: int = 16, prefer_trained: bool = True) -> tuple[np.ndarray, s
     if prefer_trained and os.path.exists(p):
         return np.load(p).astype(np.float32), "trained"
     return init_params(m), "initial"
+
+
+def symbol_max(eps: float, theta: float, grid: int = 513) -> float:
+    """Upper bound on the Q1 operator's spectrum: the maximum of the stencil's Fourier
+    symbol c + 2 ax cos x + 2 ay cos y + 2 d1 cos(x + y) + 2 d2 cos(x - y) over
+    x in [0, pi], y in [-pi, pi] (a symmetric Toeplitz-block-Toeplitz matrix's
+    eigenvalues lie within the range of its symbol)."""
+    c, s = math.cos(theta), math.sin(theta)
+    c11 = c * c + eps * s * s
+    c22 = s * s + eps * c * c
+    c12 = (1.0 - eps) * s * c
+    cen = 4.0 * (c11 + c22) / 3.0
+    ax = (c22 - 2.0 * c11) / 3.0
+    ay = (c11 - 2.0 * c22) / 3.0
+    d1 = -(c11 + c22) / 6.0 - 0.5 * c12
+    d2 = -(c11 + c22) / 6.0 + 0.5 * c12
+    x = np.linspace(0.0, math.pi, grid)
+    y = np.linspace(-math.pi, math.pi, 2 * grid - 1)
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    S = cen + 2 * ax * np.cos(X) + 2 * ay * np.cos(Y) + 2 * d1 * np.cos(X + Y) + 2 * d2 * np.cos(X - Y)
+    return float(S.max())
+
+
+def period_radius(w, beta: float, lam) -> np.ndarray:
+    """Spectral radius of one NAG period's 2x2 per-mode transfer at each eigenvalue lam
+    (A symmetric, so every eigenvector evolves independently)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    P = np.tile(np.eye(2), (lam.size, 1, 1))
+    for wi in w:
+        mu = 1.0 - wi * lam
+        T = np.zeros((lam.size, 2, 2))
+        T[:, 0, 0] = mu * (1.0 + beta)
+        T[:, 0, 1] = -mu * beta
+        T[:, 1, 0] = 1.0
+        P = T @ P
+    return np.abs(np.linalg.eigvals(P)).max(axis=1)

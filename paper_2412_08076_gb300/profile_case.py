@@ -17,6 +17,48 @@ from . import meta as meta_mod
 from . import richm
 
 
+TRAFFIC_SOURCES = {
+    "sweep1": ["paper_2412_08076_gb300/csrc/sweep.cu", "paper_2412_08076_gb300/csrc/common.cuh",
+               "paper_2412_08076_gb300/csrc/kernels.cuh"],
+    "sweepT4": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh",
+                "paper_2412_08076_gb300/csrc/kernels.cuh"],
+    "sweepT8": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh",
+                "paper_2412_08076_gb300/csrc/kernels.cuh"],
+}
+
+
+def record_traffic(report: str, kind: str, unknowns: int, root: str) -> float:
+    """Read dram__bytes_read/write.sum of the captured launch from an ncu report and
+    store DRAM bytes per unknown in profiles/traffic.txt with a hash of the kernel's
+    sources (bench.py reports traffic only while the hash still matches)."""
+    import csv
+    import hashlib
+    import os
+    import subprocess
+    out = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], capture_output=True, text=True,
+                         check=True).stdout
+    rows = list(csv.reader(out.splitlines()))
+    hdr, units, data = rows[0], rows[1], rows[2]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    tot = 0.0
+    for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        i = hdr.index(name)
+        tot += float(data[i].replace(",", "")) * scale[units[i]]
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[kind]:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    path = os.path.join(root, "profiles", "traffic.txt")
+    lines = []
+    if os.path.exists(path):
+        lines = [ln for ln in open(path).read().splitlines() if ln and not ln.startswith(kind + " ")]
+    per = tot / unknowns
+    lines.append(f"{kind} {h.hexdigest()} {per:.6f} {' '.join(TRAFFIC_SOURCES[kind])}")
+    with open(path, "w") as fh:
+        fh.write("\n".join(sorted(lines)) + "\n")
+    return per
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--what", choices=["sweep", "cycle", "adjoint", "helmholtz"], default="sweep")
@@ -24,7 +66,16 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=511)
     ap.add_argument("--sweeps", type=int, default=6)
     ap.add_argument("--fuse", type=int, default=1)
+    ap.add_argument("--record-traffic", metavar="NCU_REPORT", default=None,
+                    help="store the report's DRAM bytes per unknown in profiles/traffic.txt and exit")
+    ap.add_argument("--kind", default="sweepT8")
     args = ap.parse_args(argv)
+    if args.record_traffic:
+        import os
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        per = record_traffic(args.record_traffic, args.kind, args.batch * args.n * args.n, root)
+        print(f"{args.kind}: {per:.3f} DRAM bytes per unknown per launch")
+        return
     import richm_synth as synth
     m = 16
     insts = synth.batched_aniso(args.batch, sizes=(args.n,), param_seed=1)

@@ -4,7 +4,7 @@ Each step: w, a = Meta(theta; mu) (library forward), K NAG sweeps from x0 = 0 wi
 checkpoints (library forward), loss = mean log relative residual and its gradient
 (library), adjoint sweeps (library), network backward and Adam (library). Python only
 sequences the calls. Usage:
-  python -m paper_2412_08076_gb300.train --steps 400 --save
+  python -m paper_2412_08076_gb300.train --steps 1000 --out paper_2412_08076_gb300/params/meta_m16.npy
 """
 from __future__ import annotations
 
@@ -73,10 +73,10 @@ class Trainer:
         gP = richm.meta_backward(self.P, batch.X, batch.G, W["acts"], self.m, W["gw"], W["ga"], W["gP"], W["mwork"])
         return loss, gP
 
-    def step(self, batch: Batch):
+    def step(self, batch: Batch, lr: float | None = None):
         loss, gP = self.loss_and_grad(batch)
         self.t += 1
-        richm.adam_step(self.P, gP, self.m1, self.m2, self.t, lr=self.lr)
+        richm.adam_step(self.P, gP, self.m1, self.m2, self.t, lr=self.lr if lr is None else lr)
         return loss
 
     def params(self) -> np.ndarray:
@@ -92,27 +92,37 @@ def make_batches(nbatches=8, B=64, n=255, seed=1000):
     return out
 
 
+def train(steps=1000, lr=2e-3, nbatches=8, n=255, log_every=100, verbose=True):
+    """Algorithm 1 with the config-3 workload (64 instances of n x n per batch, K = 64,
+    checkpoints every 8) from the initial network; cosine-decayed Adam step size.
+    Deterministic: seeded data, fixed-order kernels. Returns (params, loss history)."""
+    params, _ = meta_mod.load_params(16, prefer_trained=False)
+    tr = Trainer(params, lr=lr)
+    batches = make_batches(nbatches, n=n)
+    hist = []
+    t0 = time.time()
+    for s in range(steps):
+        lr_s = lr * 0.5 * (1.0 + math.cos(math.pi * s / max(1, steps)))
+        loss = tr.step(batches[s % len(batches)], lr=lr_s)
+        if s % log_every == 0 or s == steps - 1:
+            hist.append((s, float(loss.item())))
+            if verbose:
+                print(f"step {s:5d} loss {hist[-1][1]:.4f} ({time.time() - t0:.1f} s)", flush=True)
+    return tr.params(), hist
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batches", type=int, default=8)
     ap.add_argument("--n", type=int, default=255)
-    ap.add_argument("--save", action="store_true")
+    ap.add_argument("--out", default=None, help="where to save the parameters (.npy)")
     args = ap.parse_args(argv)
-    params, src = meta_mod.load_params(16, prefer_trained=False)
-    tr = Trainer(params, lr=args.lr)
-    batches = make_batches(args.batches, n=args.n)
-    t0 = time.time()
-    hist = []
-    for s in range(args.steps):
-        loss = tr.step(batches[s % len(batches)])
-        if s % 25 == 0 or s == args.steps - 1:
-            hist.append((s, float(loss.item())))
-            print(f"step {s:5d} loss {hist[-1][1]:.4f} ({time.time() - t0:.1f} s)", flush=True)
-    if args.save:
-        os.makedirs(meta_mod.PARAM_DIR, exist_ok=True)
-        np.save(meta_mod.trained_path(16), tr.params())
+    params, hist = train(args.steps, args.lr, args.batches, args.n)
+    if args.out:
+        os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+        np.save(args.out, params)
     return hist
 
 
