@@ -204,6 +204,125 @@ def kernel_traffic(kind: str, dofs: int):
     return None
 
 
+def secondary_workloads(dev):
+    """Bounded measurements of the other four workloads (not part of the headline)."""
+    import numpy as np
+    import torch
+
+    import richm_synth as synth
+    from paper_2412_08076_gb300 import richm
+    from paper_2412_08076_gb300 import meta as meta_mod
+    from paper_2412_08076_gb300.train import Trainer, make_batches
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # 63^2 FP64 Richardson(8), Chebyshev weights from Gershgorin, lmin = lmax/30:
+    # 400 sweeps, one launch each, with the residual after every sweep
+    inst, b = synth.single_aniso()
+    op = richm.Operator([(richm.ANISO_Q1, inst.n, inst.eps, inst.theta, 0.0)])
+    G = op.gershgorin()[0]
+    w = torch.tensor([richm.chebyshev_weights(G, G / 30.0, 8)], dtype=torch.float64, device=dev)
+    B = op.pack(torch.tensor(b.ravel(), device=dev), richm.F64)
+    X = op.zeros(richm.F64)
+    ws = op.workspace(op._ws("richm_sweeps_workspace", richm.F64))
+    rw = op.workspace(op._ws("richm_residual_workspace"))
+    hist = torch.empty(400, dtype=torch.float64, device=dev)
+    e0, e1 = ev(), ev()
+    e0.record()
+    for k in range(400):
+        op.apply_sweeps(richm.F64, X, None, B, w, K=1, m=8, k_start=k, work=ws)
+        hist[k:k + 1] = op.residual_norm(richm.F64, X, B, work=rw)[2]
+    e1.record()
+    torch.cuda.synchronize()
+    out["fp64_63sq_richardson8"] = {"sweeps": 400, "us_per_sweep_with_residual": 1e3 * e0.elapsed_time(e1) / 400,
+                                    "rel_res_after_400": float(hist[-1].item()),
+                                    "note": "latency-bound (3969 unknowns); parity vs oracle in tests"}
+    op.close()
+
+    # training step: meta forward, 64 checkpointed NAG sweeps on 64 x 255^2, loss,
+    # adjoint, meta backward, Adam
+    params, _ = meta_mod.load_params(16, prefer_trained=False)
+    tr = Trainer(params)
+    batches = make_batches(2, n=255, seed=1000)
+    for j in range(3):
+        tr.step(batches[j % 2])
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for j in range(10):
+        tr.step(batches[j % 2])
+    e1.record()
+    torch.cuda.synchronize()
+    out["training_step_64x255sq_K64"] = {"ms_per_step": e0.elapsed_time(e1) / 10,
+                                         "note": "gradient checks vs oracle and finite differences in tests"}
+
+    # two-level cycle on 32 x 1023^2: 8 FP32 Richardson sweeps + Fourier correction +
+    # FP64 refinement
+    n, nb = 1023, 32
+    op = richm.Operator([(richm.ANISO_Q1, n, 1e-4, math.pi / 3, 0.0)] * nb)
+    G = op.gershgorin()[0]
+    w8 = torch.tensor([richm.chebyshev_weights(G, G / 30.0, 8)] * nb, dtype=torch.float32, device=dev)
+    S = torch.tensor(synth.fourier_symbol(n, seed=3).astype(np.complex64), device=dev)
+    rhs = np.concatenate([synth.rhs_uniform(40, i, n).ravel() for i in range(nb)])
+    B64 = op.pack(torch.tensor(rhs, device=dev), richm.F64)
+    X64 = op.zeros(richm.F64)
+    E = op.zeros(richm.F32)
+    R = op.zeros(richm.F32)
+    fw = op.workspace(op._ws("richm_fourier_workspace"))
+    ws = op.workspace(op._ws("richm_sweeps_workspace", richm.F32))
+    rw = op.workspace(op._ws("richm_residual_workspace"))
+    rel = op.refine(X64, B64, None, None, richm.F32, R, work=rw)
+
+    def cycle():
+        op.apply_sweeps(richm.F32, E, None, R, w8, K=8, m=8, work=ws)
+        op.fourier_correction(E, R, S, work=fw)
+        return op.refine(X64, B64, E, None, richm.F32, R, work=rw)
+
+    cycle()
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for _ in range(5):
+        rel = cycle()
+    e1.record()
+    torch.cuda.synchronize()
+    out["two_level_32x1023sq"] = {"ms_per_cycle": e0.elapsed_time(e1) / 5,
+                                  "gdof_sweeps_per_s": nb * n * n * 8 / (e0.elapsed_time(e1) / 5e3) / 1e9,
+                                  "note": "random symbol: parity only (vs oracle in tests)"}
+    op.close()
+
+    # Helmholtz: 16 x 2047^2 complex64, NAG m = 8, seeded weights, 128 sweeps
+    n, nb = 2047, 16
+    k = 2 * math.pi * (n + 1) / 10
+    op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, n, 1.0, 0.0, k)] * nb)
+    h = 1.0 / (n + 1)
+    wh = torch.tensor(np.tile(synth.helmholtz_weights(8, h, seed=4), (nb, 1)), dtype=torch.float32, device=dev)
+    ah = torch.full_like(wh, 0.3)
+    src = np.zeros((nb, n * n), np.complex64)
+    for s_, (i, j) in enumerate(synth.point_sources(n, nb, seed=5)):
+        src[s_, i * n + j] = 1.0
+    Bc = op.pack(torch.tensor(src.ravel(), device=dev), richm.C64)
+    Xc, XPc = op.zeros(richm.C64), op.zeros(richm.C64)
+    ws = op.workspace(op._ws("richm_sweeps_workspace", richm.C64))
+    op.apply_sweeps(richm.C64, Xc, XPc, Bc, wh, ah, None, K=8, m=8, work=ws)
+    Xc.zero_()
+    XPc.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    op.apply_sweeps(richm.C64, Xc, XPc, Bc, wh, ah, None, K=128, m=8, work=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    _, _, relh = op.residual_norm(richm.C64, Xc, Bc)
+    out["helmholtz_16x2047sq_c64"] = {"ms_128_sweeps": e0.elapsed_time(e1),
+                                      "gdof_sweeps_per_s": nb * n * n * 128 / (e0.elapsed_time(e1) / 1e3) / 1e9,
+                                      "rel_res_after_128_max": float(relh.max().item()),
+                                      "rel_res_after_128_min": float(relh.min().item()),
+                                      "note": "one complex sweep per launch; oracle residual check in tests"}
+    op.close()
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm: same metric and workload, bounded samples."""
     rank, world = dist_env()
@@ -476,6 +595,9 @@ def run_ours(args):
         ttt["plain_fp64_per_sweep_s"] = {str(k): v for k, v in per_sweep.items()}
         ttt["speedup_vs_plain_fp64"] = fp64_est / solve_s
 
+    S.close()
+    fuse_rows = op.tuned()[1]
+    workloads = None if args.no_secondary else secondary_workloads(dev)
     line = None
     if rank == 0:
         cpu_rate, cpu_desc = oracle_sample_rate(insts, seconds=args.cpu_seconds)
@@ -484,7 +606,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(), dofs_per_rank=dofs, meta_params=psrc,
-                           active_after_steps=active, sweeps_per_pass=fuse, autotune_ms_per_sweep=tune_ms,
+                           active_after_steps=active, sweeps_per_pass=fuse, fused_tile_rows=fuse_rows,
+                           autotune_ms_per_sweep=tune_ms,
                            solve_tol=SOLVE_TOL),
             "roofline": roof,
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc,
@@ -496,9 +619,9 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "time_to_tol": ttt,
+            "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
-    S.close()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -513,6 +636,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-tolerance solve")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -163,16 +163,21 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
                                 const void* w, const void* alpha, const void* alpha_t, int K,
                                 const richm_sweep_opts* opts, void* work, size_t work_bytes, void* stream);
 
-/* Autotuner: times 16 FP32 sweeps of this operator's batch with 1, 4 and 8 sweeps
- * per pass (richm_apply_sweeps' fuse) and stores the fastest in the operator; calls
- * with fuse = 0 (richm_apply_sweeps on RICHM_F32, richm_solve / richm_solver_create
- * with inner RICHM_F32) then use it (4 before any tuning). momentum: 1 times the NAG
+/* Autotuner: times 16 FP32 sweeps of this operator's batch with 1 sweep per launch
+ * and with 4 or 8 sweeps per pass (richm_apply_sweeps' fuse) on warp tiles of 64,
+ * 128 or 256 rows, and stores the fastest pair in the operator. Every fused launch
+ * then uses the tuned tile height, and calls with fuse = 0 (richm_apply_sweeps on
+ * RICHM_F32, richm_solve / richm_solver_create with inner RICHM_F32) the tuned pass
+ * length (before any tuning: 4 sweeps per pass, 256 rows). momentum: 1 times the NAG
  * kernels, 0 the plain ones. Synchronises `stream`. best_fuse (host, may be NULL)
- * receives the choice and ms_per_sweep (host, may be NULL) its time per sweep.
+ * receives the pass length and ms_per_sweep (host, may be NULL) its time per sweep.
  * work: at least richm_autotune_workspace bytes (overwritten). Q1 operators only. */
 richm_status richm_autotune_workspace(const richm_operator* op, size_t* bytes);
 richm_status richm_autotune(richm_operator* op, int m, int momentum, void* work, size_t work_bytes, void* stream,
                             int* best_fuse, float* ms_per_sweep);
+
+/* The operator's current pass length and fused tile height (host outputs, may be NULL). */
+richm_status richm_tuned(const richm_operator* op, int* fuse, int* rows);
 
 /* ------------------------------------------------------------------ residual */
 

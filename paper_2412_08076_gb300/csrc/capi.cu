@@ -2,8 +2,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace richm {
 
@@ -221,6 +224,16 @@ richm_status richm_operator_create(const richm_pde* pdes, int batch, richm_opera
   }
   op->elems = (size_t)off;
   cudaError_t e = cudaGetDevice(&op->device);
+  if (e == cudaSuccess) {
+    // kernel attributes, once per device (a stream capture may follow later calls)
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), op->device) == done.end()) {
+      e = init_sweep_attributes();
+      if (e == cudaSuccess) done.push_back(op->device);
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&op->d_inst, sizeof(Inst) * batch);
   if (e == cudaSuccess)
     e = cudaMemcpy(op->d_inst, op->h_inst.data(), sizeof(Inst) * batch, cudaMemcpyHostToDevice);

@@ -102,7 +102,8 @@ struct richm_operator {
   size_t elems = 0;
   int max_n = 0;
   std::map<long long, richm::TileMap> tiles;
-  int best_fuse = 4;  // sweeps per pass used when a call asks for fuse = 0 (set by richm_autotune)
+  int best_fuse = 4;    // sweeps per pass used when a call asks for fuse = 0 (set by richm_autotune)
+  int best_rows = 256;  // rows of a fused-sweep warp tile (set by richm_autotune)
   // cuFFT state for richm_fourier_correction (created on first use)
   void* fft_state = nullptr;
 };

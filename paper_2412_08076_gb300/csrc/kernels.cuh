@@ -7,7 +7,11 @@ namespace richm {
 
 constexpr int kRows = 16;          // rows streamed by one warp tile
 constexpr int kWarpsPerBlock = 8;  // warp tiles per thread block
-constexpr int kFuseRows = 256;     // output rows of a fused-sweep warp tile
+constexpr int kFuseRows = 256;     // default output rows of a fused-sweep warp tile
+
+// Kernel attributes that must be set before the first launch (called once per
+// process and device by richm_operator_create).
+cudaError_t init_sweep_attributes();
 
 // One forward sweep (see sweep.cu). `a == nullptr`: no momentum (xp unused);
 // `at == nullptr`: at = a. `active`: per-instance flags or nullptr (all active).
@@ -20,9 +24,10 @@ richm_status launch_sweep(richm_operator* op, const E* x, const E* xp, const E* 
 // TL (4 or 8) fused FP32 sweeps of a real Q1 batch: reads (x_k, x_{k-1}) from
 // (x, xp), writes (x_{k+TL}, x_{k+TL-1}) to (out_x, out_xp); the outputs must not
 // alias the inputs. kidx0 = coefficient index of the first sweep.
+// rows: output rows of a warp tile (64, 128 or 256); <= 0 takes the operator's tuned value.
 richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
                                 float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
-                                int kidx0, int precond, const int* active, cudaStream_t s);
+                                int kidx0, int precond, const int* active, cudaStream_t s, int rows = 0);
 
 // r = b - A x in FP64 with per-tile partial sums (sum |r|^2, sum |b|^2) written to
 // `partials` (one double2 per warp tile of the residual geometry); r_out may be null.

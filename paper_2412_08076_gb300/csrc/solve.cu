@@ -300,7 +300,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   const TileMap* tm = nullptr;
   richm_status st = get_tiles(op, 64, kRows, &tm);
   if (st == RICHM_OK) st = get_tiles(op, o->inner == RICHM_F32 ? 128 : 64, kRows, &tm);
-  if (st == RICHM_OK && S->o.fuse > 1) st = get_tiles(op, -S->o.fuse, kFuseRows, &tm);
+  if (st == RICHM_OK && S->o.fuse > 1) st = get_tiles(op, -S->o.fuse, op->best_rows, &tm);
   if (st != RICHM_OK) {
     richm_solver_destroy(S);
     return st;

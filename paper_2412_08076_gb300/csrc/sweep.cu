@@ -33,11 +33,27 @@ struct SweepArgs {
   const int* active;
 };
 
+// Rows are prefetched kS1Prefetch row steps ahead with cp.async into per-warp
+// shared-memory rings. A ring row holds the warp's 32 lane chunks of 16 bytes plus
+// one chunk on each side (copied by lanes 0 and 31), so every lane reads back only
+// what it copied itself: no barrier is needed.
+constexpr int kS1Prefetch = 2;
+constexpr int kS1Slots = 4;  // prefetched rows in flight + the row being consumed
+__host__ __device__ constexpr int s1_ring_chunks(bool mom) { return kS1Slots * (34 + (mom ? 34 : 0) + 32); }
+
+__device__ __forceinline__ void cp_async_chunk(uint4* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int nbytes = valid ? 16 : 0;  // 0: zero-fill without reading global memory
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+
 template <typename E, bool MOM, bool PRE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) sweep1_kernel(const SweepArgs<E> A) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) sweep1_kernel(const SweepArgs<E> A) {
   using S = typename RealOf<E>::type;
   constexpr int VW = VecWidth<E>::value;
   constexpr bool CPLX = IsCplx<E>::value;
+  constexpr int XC = 34, BC = 32;  // chunks per x row (with the two edge chunks) and per b row
+  extern __shared__ __align__(16) uint4 s1_ring[];
   const int lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (wt >= A.ntiles) return;
@@ -59,54 +75,83 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) sweep1_kernel(const Sw
   const int r0 = t.ty * kRows + 1;
   const int r1 = min(r0 + kRows - 1, n);
   const E* xb = A.x + I.off;
-  const E* xpb = MOM ? A.xp + I.off : nullptr;
+  const E* xpb = MOM ? A.xp + I.off : A.x + I.off;
   const E* bb = A.b + I.off;
   E* ob = A.out + I.off;
+  uint4* ring = s1_ring + (threadIdx.x >> 5) * s1_ring_chunks(MOM);
+  uint4* xr = ring;                                        // [slot][XC]
+  uint4* xpr = ring + kS1Slots * XC;                       // [slot][XC] (MOM)
+  uint4* br = ring + kS1Slots * (XC + (MOM ? XC : 0));     // [slot][BC]
+  const bool has_left = c0 > 0, has_right = c0 + VW < pitch;
 
-  auto load = [&](int pr, RowT<E, VW>& Y, E* xs, E* xps) {
-    const bool in = (pr >= 1) && (pr <= n);
-    VecN<E, VW> X{}, XP{};
-    const long long ro = (long long)pr * pitch;
-    if (in && live) {
-      X = ldv<E, VW>(xb + ro + c0);
-      if (MOM) XP = ldv<E, VW>(xpb + ro + c0);
+  // copies of x[q], x_{k-1}[q] (the next window row) and b[q - 1] (the next output row)
+  auto issue = [&](int q) {
+    const int sl = q & (kS1Slots - 1);
+    const bool rv = (q >= 1) && (q <= n) && (q <= r1 + 1);
+    const long long ro = (long long)(rv ? q : 0) * pitch;
+    cp_async_chunk(xr + sl * XC + 1 + lane, xb + ro + (live ? c0 : 0), rv && live);
+    if (MOM) cp_async_chunk(xpr + sl * XC + 1 + lane, xpb + ro + (live ? c0 : 0), rv && live);
+    if (lane == 0) {
+      cp_async_chunk(xr + sl * XC, xb + ro + (has_left ? c0 - VW : 0), rv && has_left);
+      if (MOM) cp_async_chunk(xpr + sl * XC, xpb + ro + (has_left ? c0 - VW : 0), rv && has_left);
     }
+    if (lane == 31) {
+      cp_async_chunk(xr + sl * XC + 33, xb + ro + (has_right ? c0 + VW : 0), rv && has_right);
+      if (MOM) cp_async_chunk(xpr + sl * XC + 33, xpb + ro + (has_right ? c0 + VW : 0), rv && has_right);
+    }
+    const int qb = q - 1;
+    const bool bv = (qb >= r0) && (qb <= r1) && live;
+    cp_async_chunk(br + sl * BC + lane, bb + (long long)(bv ? qb : 0) * pitch + (live ? c0 : 0), bv);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  // y row of x[q] from ring slot q (neighbours across lanes by shuffles, edges from
+  // the edge chunks); keeps x and x_{k-1} of the row for the update
+  auto take = [&](int q, RowT<E, VW>& Y, E* xs, E* xps) {
+    const int sl = q & (kS1Slots - 1);
+    VecN<E, VW> X, XP;
+    *reinterpret_cast<uint4*>(&X) = xr[sl * XC + 1 + lane];
+    if (MOM) *reinterpret_cast<uint4*>(&XP) = xpr[sl * XC + 1 + lane];
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       Y.y[e] = MOM ? X.v[e] + ati * (X.v[e] - XP.v[e]) : X.v[e];
       xs[e] = X.v[e];
-      xps[e] = XP.v[e];
+      xps[e] = MOM ? XP.v[e] : E{};
     }
     E le{}, re{};
-    if (in) {
-      if (lane == 0 && c0 > 0) {
-        E xv = xb[ro + c0 - 1];
-        le = xv;
-        if (MOM) {
-          E pv = xpb[ro + c0 - 1];
-          le = xv + ati * (xv - pv);
-        }
+    if (lane == 0) {
+      VecN<E, VW> L, LP;
+      *reinterpret_cast<uint4*>(&L) = xr[sl * XC];
+      le = L.v[VW - 1];
+      if (MOM) {
+        *reinterpret_cast<uint4*>(&LP) = xpr[sl * XC];
+        le = le + ati * (le - LP.v[VW - 1]);
       }
-      if (lane == 31 && c0 + VW < pitch) {
-        E xv = xb[ro + c0 + VW];
-        re = xv;
-        if (MOM) {
-          E pv = xpb[ro + c0 + VW];
-          re = xv + ati * (xv - pv);
-        }
+    }
+    if (lane == 31) {
+      VecN<E, VW> R, RP;
+      *reinterpret_cast<uint4*>(&R) = xr[sl * XC + 33];
+      re = R.v[0];
+      if (MOM) {
+        *reinterpret_cast<uint4*>(&RP) = xpr[sl * XC + 33];
+        re = re + ati * (re - RP.v[0]);
       }
     }
     row_neighbours<E, VW>(Y, lane, le, re);
   };
 
+  for (int q = r0 - 1; q <= r0 + kS1Prefetch; ++q) issue(q);
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kS1Prefetch) : "memory");
   RowT<E, VW> U, C, D;
   E xC[VW], xpC[VW], xD[VW], xpD[VW], tmp0[VW], tmp1[VW];
-  load(r0 - 1, U, tmp0, tmp1);
-  load(r0, C, xC, xpC);
+  take(r0 - 1, U, tmp0, tmp1);
+  take(r0, C, xC, xpC);
   for (int r = r0; r <= r1; ++r) {
-    load(r + 1, D, xD, xpD);
-    VecN<E, VW> Bv{};
-    if (live) Bv = ldv<E, VW>(bb + (long long)r * pitch + c0);
+    issue(r + 1 + kS1Prefetch);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kS1Prefetch) : "memory");
+    take(r + 1, D, xD, xpD);
+    VecN<E, VW> Bv;
+    *reinterpret_cast<uint4*>(&Bv) = br[((r + 1) & (kS1Slots - 1)) * BC + lane];
     E Ay[VW];
     if constexpr (CPLX) {
       apply_fd5<E, VW, S>(U, C, D, r - 1, c0, n, sc, sax, sabr, sabi, Ay);
@@ -140,6 +185,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) sweep1_kernel(const Sw
       xpC[e] = xpD[e];
     }
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename E>
@@ -154,12 +200,37 @@ richm_status launch_sweep(richm_operator* op, const E* x, const E* xp, const E* 
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const dim3 block(kWarpsPerBlock * 32);
   const bool mom = (a != nullptr);
-  if (mom && precond) sweep1_kernel<E, true, true><<<blocks, block, 0, s>>>(A);
-  else if (mom) sweep1_kernel<E, true, false><<<blocks, block, 0, s>>>(A);
-  else if (precond) sweep1_kernel<E, false, true><<<blocks, block, 0, s>>>(A);
-  else sweep1_kernel<E, false, false><<<blocks, block, 0, s>>>(A);
+  const size_t sm_mom = sizeof(uint4) * kWarpsPerBlock * s1_ring_chunks(true);
+  const size_t sm_plain = sizeof(uint4) * kWarpsPerBlock * s1_ring_chunks(false);
+  if (mom && precond) sweep1_kernel<E, true, true><<<blocks, block, sm_mom, s>>>(A);
+  else if (mom) sweep1_kernel<E, true, false><<<blocks, block, sm_mom, s>>>(A);
+  else if (precond) sweep1_kernel<E, false, true><<<blocks, block, sm_plain, s>>>(A);
+  else sweep1_kernel<E, false, false><<<blocks, block, sm_plain, s>>>(A);
   RICHM_LAUNCH_CHECK("sweep");
   return RICHM_OK;
+}
+
+// The one-sweep kernels use more than the default 48 KB of dynamic shared memory.
+template <typename E>
+static cudaError_t sweep1_attributes() {
+  const int mom = (int)(sizeof(uint4) * kWarpsPerBlock * s1_ring_chunks(true));
+  const int plain = (int)(sizeof(uint4) * kWarpsPerBlock * s1_ring_chunks(false));
+  cudaError_t e = cudaFuncSetAttribute(sweep1_kernel<E, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mom);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep1_kernel<E, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mom);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep1_kernel<E, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep1_kernel<E, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain);
+  return e;
+}
+
+cudaError_t init_sweep_attributes() {
+  cudaError_t e = sweep1_attributes<float>();
+  if (e == cudaSuccess) e = sweep1_attributes<double>();
+  if (e == cudaSuccess) e = sweep1_attributes<cplx<float>>();
+  if (e == cudaSuccess) e = sweep1_attributes<cplx<double>>();
+  return e;
 }
 
 #define RICHM_INST_SWEEP(E)                                                                                  \
@@ -283,37 +354,48 @@ richm_status richm_autotune(richm_operator* op, int m, int momentum, void* work,
   cudaEvent_t e0, e1;
   RICHM_CUDA_TRY(cudaEventCreate(&e0));
   RICHM_CUDA_TRY(cudaEventCreate(&e1));
-  const int cands[3] = {1, 4, 8};
-  int best = 1;
+  // candidates: (sweeps per pass, rows of a fused warp tile)
+  const int cands[7][2] = {{1, 0}, {4, 64}, {4, 128}, {4, 256}, {8, 64}, {8, 128}, {8, 256}};
+  int best = 1, best_rows = op->best_rows;
   float best_ms = 1e30f;
-  for (int c : cands) {
+  for (const auto& cr : cands) {
+    const int c = cr[0];
+    if (c > 1) op->best_rows = cr[1];
     richm_sweep_opts o{m, 0, 0, c};
     const int K = 16;
     richm_status st = apply_sweeps_t<float>(op, x, xp, b, w, a, nullptr, K, &o, W, s);  // warm-up
-    if (st != RICHM_OK) break;
-    cudaEventRecord(e0, s);
+    if (st == RICHM_OK) cudaEventRecord(e0, s);
     for (int r = 0; r < 3 && st == RICHM_OK; ++r) st = apply_sweeps_t<float>(op, x, xp, b, w, a, nullptr, K, &o, W, s);
-    cudaEventRecord(e1, s);
-    cudaError_t ce = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (st == RICHM_OK && ce == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
-      ms /= 3.0f * K;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = c;
-      }
-    }
     if (st != RICHM_OK) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       return st;
     }
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+      ms /= 3.0f * K;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+        if (c > 1) best_rows = cr[1];
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  op->best_rows = best_rows;
   op->best_fuse = best;
   if (best_fuse) *best_fuse = best;
   if (ms_per_sweep) *ms_per_sweep = best_ms;
+  return RICHM_OK;
+}
+
+richm_status richm_tuned(const richm_operator* op, int* fuse, int* rows) {
+  clear_error();
+  RICHM_ARG(op != nullptr, "null operator");
+  if (fuse) *fuse = op->best_fuse;
+  if (rows) *rows = op->best_rows;
   return RICHM_OK;
 }
 

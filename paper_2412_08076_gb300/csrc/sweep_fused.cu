@@ -10,7 +10,7 @@
 // the physical boundary need no halo there; at interior tile edges the result of
 // level s is wrong in the s outermost columns, so neighbouring tiles overlap by TL
 // columns on each side and only the inner columns are stored. Each pass reads x_k,
-// x_{k-1}, b once (plus the overlaps and TL halo rows above and below each 256-row
+// x_{k-1}, b once (plus the overlaps and TL halo rows above and below each row-block
 // tile) and writes the last two levels: 20 bytes per unknown per TL sweeps.
 // Input rows are prefetched PF row steps ahead with cp.async into per-warp
 // shared-memory rings (each lane copies and later reads only its own 16 bytes, so no
@@ -38,6 +38,7 @@ struct SweepTArgs {
   int m;
   int kidx0;  // coefficient index of the first sweep of the pass
   const int* active;
+  int rows;   // output rows of a warp tile
 };
 
 // Per-warp state of the pipeline. Window slots rotate by phase: at phase p the new
@@ -263,8 +264,8 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   const int vlo = cs + (t.tx > 0 ? TL : 0);
   const int vhi = last_tile ? c.pitch : cs + 128 - TL;
   c.store_cols = c.live && c.c0 >= vlo && c.c0 + VW <= vhi;
-  c.r0 = t.ty * kFuseRows + 1;
-  c.r1 = min(c.r0 + kFuseRows - 1, c.n);
+  c.r0 = t.ty * A.rows + 1;
+  c.r1 = min(c.r0 + A.rows - 1, c.n);
   c.rlast = c.r1 + TL;
   c.xb = A.x + I.off;
   c.xpb = MOM ? A.xp + I.off : A.x + I.off;
@@ -303,10 +304,11 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
 
 richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
                                 float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
-                                int kidx0, int precond, const int* active, cudaStream_t s) {
+                                int kidx0, int precond, const int* active, cudaStream_t s, int rows) {
+  if (rows <= 0) rows = op->best_rows;
   const TileMap* tm = nullptr;
-  RICHM_TRY(get_tiles(op, -TL, kFuseRows, &tm));
-  SweepTArgs A{op->d_inst, tm->d_tiles, tm->ntiles, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, active};
+  RICHM_TRY(get_tiles(op, -TL, rows, &tm));
+  SweepTArgs A{op->d_inst, tm->d_tiles, tm->ntiles, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, active, rows};
   const int blocks = (tm->ntiles + kFuseWarps - 1) / kFuseWarps;
   const int thr = kFuseWarps * 32;
   const size_t smem = (TL == 4 ? FusedRings<4>::FLOATS : FusedRings<8>::FLOATS) * sizeof(float) * kFuseWarps;

@@ -72,6 +72,7 @@ _SIGS = {
     "richm_residual_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_autotune_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_autotune": (_I, [_P, _I, _I, _P, _SZ, _P, C.POINTER(_I), C.POINTER(C.c_float)]),
+    "richm_tuned": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "richm_residual_norm": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_residual_norm_static": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "richm_solve_workspace": (_I, [_P, C.POINTER(richm_solve_opts), C.POINTER(_SZ)]),
@@ -265,6 +266,12 @@ class Operator:
         _check(load().richm_autotune(self.handle, m, int(momentum), _ptr(work), work.numel(), _stream(stream),
                                      C.byref(best), C.byref(ms)), "richm_autotune")
         return best.value, ms.value
+
+    def tuned(self):
+        """richm_tuned: (sweeps per pass, fused tile rows) the operator uses."""
+        f, r = C.c_int(), C.c_int()
+        _check(load().richm_tuned(self.handle, C.byref(f), C.byref(r)), "richm_tuned")
+        return f.value, r.value
 
     def residual_norm(self, dtype, x, b, r_out=None, work=None, stream=None):
         """richm_residual_norm: returns (rnorm, bnorm, rel) as FP64 CUDA tensors [batch]."""
