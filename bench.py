@@ -502,37 +502,21 @@ def run_ours(args):
                 "one_sweep_kernel": {"kernel": "sweep1_kernel<float,NAG>", "launch_ms": one_ms,
                                      "achieved_gbs": one_gbs, "frac_of_measured_hbm": one_gbs / hbm_peak}}
 
-    # -- e2e: host buffers through the public API (pinned H2D of b, one cycle, D2H of x)
+    # -- e2e: the call a user makes with host buffers: richm_solve_host copies b from
+    #    pinned host memory, packs, solves every instance to tolerance from x = 0,
+    #    unpacks and copies x back (synchronous); value = dof-sweeps done / wall time
     hb = dense_b.pin_memory()
     hx = torch.empty(op.dense_elems(), dtype=torch.float64).pin_memory()
-    dB = torch.empty(op.dense_elems(), dtype=torch.float64, device=dev)
-    S2 = richm.Solver(op, opts, w, a)
-    Bp = op.zeros(richm.F64)
-    Xp = op.zeros(richm.F64)
-
-    def e2e_step():
-        dB.copy_(hb, non_blocking=True)
-        op.pack(dB, richm.F64, out=Bp)
-        Xp.zero_()
-        S2.start(Bp, Xp)
-        weight_supply()
-        S2.step(1, sync=False)
-        hx.copy_(op.unpack(Xp, richm.F64), non_blocking=True)
-
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    n_e2e = max(3, min(args.steps, 10))
-    q0 = torch.cuda.Event(enable_timing=True)
-    q1 = torch.cuda.Event(enable_timing=True)
-    q0.record(stream)
-    for _ in range(n_e2e):
-        e2e_step()
-    q1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = q0.elapsed_time(q1) / n_e2e
-    e2e_val = dofs * REFINE / (e2e_ms / 1e3) / 1e9
-    S2.close()
+    e2e_runs = []
+    for rep in range(1 + max(1, args.e2e_runs)):
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        st_e, info_e = op.solve_host(hb, hx, w, a, None, opts)
+        el = time.perf_counter() - c0
+        if rep > 0:  # the first call warms the host path
+            e2e_runs.append((el, sum(sw * t.n * t.n for (sw, _, _), t in zip(info_e, insts)), st_e))
+    e2e_s = sum(r[0] for r in e2e_runs) / len(e2e_runs)
+    e2e_val = sum(r[1] for r in e2e_runs) / sum(r[0] for r in e2e_runs) / 1e9
 
     # -- time to tolerance: full solve from x0 = 0 (timed once)
     ttt = None
@@ -613,9 +597,11 @@ def run_ours(args):
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc,
                              "host_cores": os.cpu_count()},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(dense_b.numel() * 8),
-                    "d2h_bytes_per_step": int(hx.numel() * 8),
-                    "note": "pinned H2D of b, pack, solver start (FP64 residual), weight supply, one cycle, "
-                            "unpack, D2H of x"},
+                    "d2h_bytes_per_step": int(hx.numel() * 8), "seconds_per_call": e2e_s,
+                    "statuses": [r[2] for r in e2e_runs],
+                    "note": "one step = one richm_solve_host call: pinned H2D of b, pack, solve every instance "
+                            "to 1e-10 from x = 0 (FP32 sweeps + FP64 refinement), unpack, D2H of x; "
+                            "value = dof-sweeps performed / wall time"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "time_to_tol": ttt,
@@ -637,6 +623,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-tolerance solve")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
+    ap.add_argument("--e2e-runs", type=int, default=2, help="timed richm_solve_host calls")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -263,9 +263,24 @@ typedef struct richm_solver richm_solver;
 richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* opts, const void* w, const void* alpha,
                                  const void* alpha_t, void* work, size_t work_bytes, richm_solver** out);
 richm_status richm_solver_start(richm_solver* s, const double* b, double* x, void* stream);
+/* As richm_solver_start with the initial guess x = 0 (written by the call): the
+ * initial residual is b, so no stencil is applied. */
+richm_status richm_solver_start_zero(richm_solver* s, const double* b, double* x, void* stream);
 richm_status richm_solver_step(richm_solver* s, int cycles, int* active_out, void* stream);
 richm_status richm_solver_finish(richm_solver* s, richm_solve_info* info, void* stream);
 void richm_solver_destroy(richm_solver* s);
+
+/* richm_solve from host memory, from the initial guess 0: copies b_host (dense,
+ * instances concatenated, n_b*n_b row-major, FP64; pinned memory makes the copy
+ * asynchronous and fast) to the device, packs it, solves as richm_solve, unpacks the
+ * solution and copies it to x_host (same dense layout), then synchronises `stream`.
+ * w / alpha / alpha_t are device arrays as in richm_solve. work: at least
+ * richm_solve_host_workspace bytes (the solve workspace, two padded FP64 buffers and a
+ * dense staging buffer). Returns as richm_solve. */
+richm_status richm_solve_host_workspace(const richm_operator* op, const richm_solve_opts* opts, size_t* bytes);
+richm_status richm_solve_host(richm_operator* op, const double* b_host, double* x_host, const void* w,
+                              const void* alpha, const void* alpha_t, const richm_solve_opts* opts,
+                              richm_solve_info* info, void* work, size_t work_bytes, void* stream);
 
 /* One FP64 refinement step of a mixed-precision iteration on a Q1 batch:
  *   x += e;  e_prev -= e (if e_prev is not NULL);  e = 0;  rhs_out = b - A x,

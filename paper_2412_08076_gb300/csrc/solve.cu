@@ -128,6 +128,36 @@ __global__ void solve_reduce_kernel(const double2* __restrict__ partials, const 
   }
 }
 
+// x0 = 0: the initial residual is b itself; rhs = b (inner type) and the tile's
+// partial sums (|b|^2, |b|^2), without the FP64 stencil.
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    zero_start_kernel(const Inst* insts, const Tile* tiles, int ntiles, const double* __restrict__ b,
+                      T* __restrict__ rhs, double2* __restrict__ partials) {
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile t = tiles[wt];
+  const Inst& I = insts[t.inst];
+  const int c0 = t.tx * 64 + lane * 2;  // two doubles per lane (FP64 residual geometry)
+  const bool live = c0 < I.pitch;
+  const int r0 = t.ty * kRows + 1;
+  const int r1 = min(r0 + kRows - 1, I.n);
+  double sb = 0.0;
+  for (int r = r0; r <= r1 && live; ++r) {
+    const long long o = I.off + (long long)r * I.pitch + c0;
+    const double2 bv = *reinterpret_cast<const double2*>(b + o);
+    VecN<T, 2> out;
+    out.v[0] = (T)bv.x;
+    out.v[1] = (T)bv.y;
+    *reinterpret_cast<VecN<T, 2>*>(rhs + o) = out;
+    sb += bv.x * bv.x;  // same order as the residual kernel's sum; padding columns are zero
+    sb += bv.y * bv.y;
+  }
+  sb = warp_sum(sb);
+  if (lane == 0) partials[wt] = make_double2(sb, sb);
+}
+
 __global__ void solve_init_kernel(int batch, long long* sweeps, int* status, int* active) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < batch) {
@@ -138,11 +168,16 @@ __global__ void solve_init_kernel(int batch, long long* sweeps, int* status, int
 }
 
 template <typename T>
-static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 1) {
+static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 1, bool x0_zero = false) {
   richm_operator* op = S->op;
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 64, kRows, &tm));  // residual / update geometry of FP64
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (init && x0_zero) {
+    zero_start_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(op->d_inst, tm->d_tiles, tm->ntiles, S->b,
+                                                                   (T*)S->rhs, S->partials);
+    RICHM_LAUNCH_CHECK("zero start");
+  }
   if (!init) {
     // pointwise, so the new pair may overwrite the buffers it reads
     refine_update_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(
@@ -150,7 +185,8 @@ static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 
         (T*)S->E[1], S->active);
     RICHM_LAUNCH_CHECK("refine update");
   }
-  RICHM_TRY((launch_residual_to<double, T>(op, S->x, S->b, (T*)S->rhs, S->partials, S->active, S->s)));
+  if (!(init && x0_zero))
+    RICHM_TRY((launch_residual_to<double, T>(op, S->x, S->b, (T*)S->rhs, S->partials, S->active, S->s)));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->count, 0, sizeof(int), S->s));
   const int wpb = 8;
   solve_reduce_kernel<<<(op->batch + wpb - 1) / wpb, wpb * 32, 0, S->s>>>(
@@ -319,7 +355,7 @@ void richm_solver_destroy(richm_solver* S) {
   delete S;
 }
 
-richm_status richm_solver_start(richm_solver* S, const double* b, double* x, void* stream) {
+static richm_status solver_start_impl(richm_solver* S, const double* b, double* x, bool x0_zero, void* stream) {
   clear_error();
   RICHM_ARG(S != nullptr && b != nullptr && x != nullptr, "null argument");
   richm_operator* op = S->op;
@@ -341,12 +377,21 @@ richm_status richm_solver_start(richm_solver* S, const double* b, double* x, voi
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[3], 0, op->elems * es, S->s));
   solve_init_kernel<<<(op->batch + 255) / 256, 256, 0, S->s>>>(op->batch, S->sweeps, S->status, S->active);
   RICHM_LAUNCH_CHECK("solve init");
-  if (S->o.inner == RICHM_F32) RICHM_TRY(refine_t<float>(S, true));
-  else RICHM_TRY(refine_t<double>(S, true));
+  if (x0_zero) RICHM_CUDA_TRY(cudaMemsetAsync(x, 0, op->elems * sizeof(double), S->s));
+  if (S->o.inner == RICHM_F32) RICHM_TRY(refine_t<float>(S, true, 0, 1, x0_zero));
+  else RICHM_TRY(refine_t<double>(S, true, 0, 1, x0_zero));
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
   RICHM_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, S->ev_out, 0));
   S->started = true;
   return RICHM_OK;
+}
+
+richm_status richm_solver_start(richm_solver* S, const double* b, double* x, void* stream) {
+  return solver_start_impl(S, b, x, false, stream);
+}
+
+richm_status richm_solver_start_zero(richm_solver* S, const double* b, double* x, void* stream) {
+  return solver_start_impl(S, b, x, true, stream);
 }
 
 richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, void* stream) {
@@ -454,6 +499,59 @@ richm_status richm_refine(richm_operator* op, double* x, const double* b, void* 
     RICHM_TRY((launch_residual_to<double, double>(op, x, b, (double*)rhs_out, partials, nullptr, s)));
   }
   return launch_norm_reduce(op, 2, partials, nullptr, nullptr, rel, s);
+}
+
+richm_status richm_solve_host_workspace(const richm_operator* op, const richm_solve_opts* o, size_t* bytes) {
+  clear_error();
+  size_t sw = 0;
+  RICHM_TRY(richm_solve_workspace(op, o, &sw));
+  RICHM_ARG(bytes != nullptr, "null output");
+  size_t dense = 0;
+  for (int b = 0; b < op->batch; ++b) dense += (size_t)op->h_inst[b].n * op->h_inst[b].n;
+  *bytes = sw + 2 * a256(op->elems * sizeof(double)) + a256(dense * sizeof(double));
+  return RICHM_OK;
+}
+
+richm_status richm_solve_host(richm_operator* op, const double* b_host, double* x_host, const void* w,
+                              const void* alpha, const void* alpha_t, const richm_solve_opts* o,
+                              richm_solve_info* info, void* work, size_t work_bytes, void* stream) {
+  clear_error();
+  RICHM_ARG(b_host != nullptr && x_host != nullptr && info != nullptr, "null argument");
+  size_t need = 0, sw = 0;
+  RICHM_TRY(richm_solve_host_workspace(op, o, &need));
+  RICHM_TRY(richm_solve_workspace(op, o, &sw));
+  RICHM_ARG(work != nullptr, "null workspace");
+  if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  size_t dense = 0;
+  for (int b = 0; b < op->batch; ++b) dense += (size_t)op->h_inst[b].n * op->h_inst[b].n;
+  char* p = reinterpret_cast<char*>(work) + sw;
+  double* bd = reinterpret_cast<double*>(p);
+  double* xd = reinterpret_cast<double*>(p + a256(op->elems * sizeof(double)));
+  double* stage = reinterpret_cast<double*>(p + 2 * a256(op->elems * sizeof(double)));
+  cudaStream_t s = (cudaStream_t)stream;
+  RICHM_CUDA_TRY(cudaMemcpyAsync(stage, b_host, dense * sizeof(double), cudaMemcpyHostToDevice, s));
+  RICHM_TRY(richm_pack(op, RICHM_F64, stage, bd, stream));
+  richm_solver* S = nullptr;
+  RICHM_TRY(richm_solver_create(op, o, w, alpha, alpha_t, work, sw, &S));
+  richm_status st = richm_solver_start_zero(S, bd, xd, stream);
+  int active = 0;
+  if (st == RICHM_OK) {
+    st = richm_solver_step(S, 0, &active, stream);
+    const long long max_cycles = o->max_sweeps / o->refine_every + 2;
+    long long c = 0;
+    while (st == RICHM_OK && active > 0 && c < max_cycles) {
+      st = richm_solver_step(S, S->graph_cycles, &active, stream);
+      c += S->graph_cycles;
+    }
+  }
+  if (st == RICHM_OK) st = richm_solver_finish(S, info, stream);
+  richm_solver_destroy(S);
+  if (st != RICHM_OK && st != RICHM_ERR_NOT_CONVERGED && st != RICHM_ERR_DIVERGED) return st;
+  const richm_status solve_st = st;
+  RICHM_TRY(richm_unpack(op, RICHM_F64, xd, stage, stream));
+  RICHM_CUDA_TRY(cudaMemcpyAsync(x_host, stage, dense * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RICHM_CUDA_TRY(cudaStreamSynchronize(s));
+  return solve_st;
 }
 
 richm_status richm_solve(richm_operator* op, const double* b, double* x, const void* w, const void* alpha,

@@ -80,6 +80,10 @@ _SIGS = {
                          _P]),
     "richm_solver_create": (_I, [_P, C.POINTER(richm_solve_opts), _P, _P, _P, _P, _SZ, C.POINTER(_P)]),
     "richm_solver_start": (_I, [_P, _P, _P, _P]),
+    "richm_solver_start_zero": (_I, [_P, _P, _P, _P]),
+    "richm_solve_host_workspace": (_I, [_P, C.POINTER(richm_solve_opts), C.POINTER(_SZ)]),
+    "richm_solve_host": (_I, [_P, _P, _P, _P, _P, _P, C.POINTER(richm_solve_opts), C.POINTER(richm_solve_info), _P,
+                              _SZ, _P]),
     "richm_solver_step": (_I, [_P, _I, C.POINTER(_I), _P]),
     "richm_solver_finish": (_I, [_P, C.POINTER(richm_solve_info), _P]),
     "richm_solver_destroy": (None, [_P]),
@@ -310,6 +314,23 @@ class Operator:
             _check(st, "richm_solve")
         return st, [(info[i].sweeps, info[i].rel_res, info[i].status) for i in range(self.batch)]
 
+    def solve_host(self, b_host, x_host, w, alpha=None, alpha_t=None, opts=None, work=None, stream=None):
+        """richm_solve_host: b_host / x_host are CPU float64 tensors (dense concatenation;
+        pinned for fast copies); returns (status, info)."""
+        if b_host.is_cuda or x_host.is_cuda or b_host.dtype != torch.float64 or x_host.dtype != torch.float64:
+            raise ValueError("b_host and x_host must be CPU float64 tensors")
+        need = C.c_size_t()
+        _check(load().richm_solve_host_workspace(self.handle, C.byref(opts), C.byref(need)),
+               "richm_solve_host_workspace")
+        if work is None:
+            work = self.workspace(need.value)
+        info = (richm_solve_info * self.batch)()
+        st = load().richm_solve_host(self.handle, b_host.data_ptr(), x_host.data_ptr(), _ptr(w), _ptr(alpha),
+                                     _ptr(alpha_t), C.byref(opts), info, _ptr(work), work.numel(), _stream(stream))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+            _check(st, "richm_solve_host")
+        return st, [(info[i].sweeps, info[i].rel_res, info[i].status) for i in range(self.batch)]
+
     def loss_log_residual(self, dtype, x, b, g=None, work=None, stream=None):
         """richm_loss_log_residual: returns the loss (device FP64 scalar tensor); fills g."""
         loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -364,9 +385,10 @@ class Solver:
                                           _ptr(self.work), self.work.numel(), C.byref(h)), "richm_solver_create")
         self.handle = h
 
-    def start(self, b, x, stream=None):
+    def start(self, b, x, stream=None, zero=False):
         self.bx = (b, x)
-        _check(load().richm_solver_start(self.handle, _ptr(b), _ptr(x), _stream(stream)), "richm_solver_start")
+        fn = load().richm_solver_start_zero if zero else load().richm_solver_start
+        _check(fn(self.handle, _ptr(b), _ptr(x), _stream(stream)), "richm_solver_start")
 
     def step(self, cycles: int, sync: bool = True, stream=None):
         act = C.c_int(-1)

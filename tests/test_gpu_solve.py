@@ -168,3 +168,24 @@ def test_refine_entry_matches_definition():
         assert np.all(from_dev(op, E, richm.F64)[i] == 0)
         np.testing.assert_allclose(from_dev(op, R, richm.F64)[i].ravel(), r, rtol=0, atol=1e-13)
         assert abs(rel[i].item() - np.linalg.norm(r) / np.linalg.norm(bs[i])) <= 1e-13
+
+
+def test_solve_host_matches_device_solve():
+    # host buffers in and out, zero initial guess: the same iteration as richm_solve
+    insts, op, As, w, a, bs = _solve_setup([15, 40, 63, 100])
+    wt, at = coef(w, richm.F32), coef(a, richm.F32)
+    opts = op.solve_opts(16, tol=1e-10, max_sweeps=400000)
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    st_d, info_d = op.solve(B, X, wt, at, None, opts)
+    hb = torch.tensor(np.concatenate([v.ravel() for v in bs])).pin_memory()
+    hx = torch.full((op.dense_elems(),), np.nan, dtype=torch.float64).pin_memory()
+    st_h, info_h = op.solve_host(hb, hx, wt, at, None, opts)
+    assert st_d == st_h == richm.OK
+    assert info_d == info_h
+    np.testing.assert_array_equal(hx.numpy(), op.unpack(X, richm.F64).cpu().numpy())
+    off = 0
+    for i, t in enumerate(insts):
+        u = hx.numpy()[off:off + t.n * t.n]
+        off += t.n * t.n
+        assert np.linalg.norm(bs[i].ravel() - As[i] @ u) / np.linalg.norm(bs[i]) <= 1e-10
