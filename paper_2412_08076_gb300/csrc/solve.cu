@@ -11,9 +11,11 @@
 // The update keeps the inner velocity e_k - e_{k-1} and the weight index, so the
 // split is the same affine iteration as sweeping x directly. The update writes the
 // pair back into the first two buffers, so every cycle has identical launches and
-// is captured once as a CUDA graph.
+// is captured once as a CUDA graph (one per fused tile height: as instances
+// converge, shorter tiles keep the remaining work spread over the GPU).
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <numeric>
 #include <type_traits>
 
@@ -42,10 +44,12 @@ struct richm_solver {
   // execution
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  std::map<int, cudaGraphExec_t> execs;  // one captured cycle per fused tile height
   int graph_cycles = 1;      // cycles captured in one graph replay
   long long cycles_run = 0;  // cycles since start
-  int* h_count = nullptr;    // pinned
+  int* h_count = nullptr;    // pinned: [0] active count, [1 .. batch] per-instance active flags
+  int rows_now = 256;        // fused tile height used by the next cycles
+  int rows_max = 256;        // the operator's tuned tile height
   bool started = false;
 };
 
@@ -210,7 +214,7 @@ static richm_status cycle_t(richm_solver* S, long long k0) {
         RICHM_TRY(launch_sweep_fused(S->op, TL, (const float*)S->E[cur], (const float*)S->E[prv],
                                      (const float*)S->rhs, (float*)S->E[oc], (float*)S->E[op_],
                                      (const float*)S->w, (const float*)S->a, (const float*)S->at, S->o.m,
-                                     (int)((k0 + k) % S->o.m), S->o.precond, S->active, S->s));
+                                     (int)((k0 + k) % S->o.m), S->o.precond, S->active, S->s, S->rows_now));
         cur = oc;
         prv = op_;
       }
@@ -229,6 +233,30 @@ static richm_status cycle_t(richm_solver* S, long long k0) {
     fre = nf;
   }
   return refine_t<T>(S, false, cur, prv);
+}
+
+// Fused tile height for the instances still iterating: the largest of the tuned
+// height, 128, 64, 32 whose warp tiles fill ~90 % of the block slots (152 SMs x the
+// kernel's blocks per SM x 4 warps); as instances converge the tiles get shorter so
+// the remaining work still spreads over the whole GPU.
+static int choose_rows(const richm_solver* S) {
+  const richm_operator* op = S->op;
+  const int TL = S->o.fuse;
+  const double slots = 152.0 * (TL == 8 ? 2 : 4) * 4;
+  int best = 32;
+  for (int rows : {256, 128, 64, 32}) {
+    if (rows > S->rows_max) continue;
+    long long warps = 0;
+    for (int b = 0; b < op->batch; ++b) {
+      if (!S->h_count[1 + b]) continue;
+      const int n = op->h_inst[b].n, stride = 128 - 2 * TL;
+      const int tx = 1 + (n > 128 ? (n - 128 + stride - 1) / stride : 0);
+      warps += (long long)tx * ((n + rows - 1) / rows);
+    }
+    if (warps >= 0.9 * slots) return rows;
+    best = rows;
+  }
+  return best;
 }
 
 static richm_status run_cycles(richm_solver* S, int cycles) {
@@ -327,7 +355,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_count, sizeof(int), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_count, sizeof(int) * (op->batch + 1), cudaHostAllocDefault);
   if (e != cudaSuccess) {
     richm_solver_destroy(S);
     return set_error(RICHM_ERR_CUDA, "solver setup failed: %s", cudaGetErrorString(e));
@@ -336,7 +364,10 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   const TileMap* tm = nullptr;
   richm_status st = get_tiles(op, 64, kRows, &tm);
   if (st == RICHM_OK) st = get_tiles(op, o->inner == RICHM_F32 ? 128 : 64, kRows, &tm);
-  if (st == RICHM_OK && S->o.fuse > 1) st = get_tiles(op, -S->o.fuse, op->best_rows, &tm);
+  S->rows_max = S->rows_now = op->best_rows;
+  if (S->o.fuse > 1)
+    for (int rows : {256, 128, 64, 32})
+      if (st == RICHM_OK && rows <= S->rows_max) st = get_tiles(op, -S->o.fuse, rows, &tm);
   if (st != RICHM_OK) {
     richm_solver_destroy(S);
     return st;
@@ -347,7 +378,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
 
 void richm_solver_destroy(richm_solver* S) {
   if (!S) return;
-  if (S->exec) cudaGraphExecDestroy(S->exec);
+  for (auto& kv : S->execs) cudaGraphExecDestroy(kv.second);
   if (S->s) cudaStreamDestroy(S->s);
   if (S->ev_in) cudaEventDestroy(S->ev_in);
   if (S->ev_out) cudaEventDestroy(S->ev_out);
@@ -360,14 +391,13 @@ static richm_status solver_start_impl(richm_solver* S, const double* b, double* 
   RICHM_ARG(S != nullptr && b != nullptr && x != nullptr, "null argument");
   richm_operator* op = S->op;
   if (S->b != b || S->x != x) {
-    if (S->exec) {
-      cudaGraphExecDestroy(S->exec);
-      S->exec = nullptr;
-    }
+    for (auto& kv : S->execs) cudaGraphExecDestroy(kv.second);
+    S->execs.clear();
   }
   S->b = b;
   S->x = x;
   S->cycles_run = 0;
+  S->rows_now = S->rows_max;
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, (cudaStream_t)stream));
   RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
   const size_t es = S->o.inner == RICHM_F32 ? 4 : 8;
@@ -405,7 +435,8 @@ richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, voi
   int done = 0;
   if (S->o.use_graph) {
     // replays cover whole weight periods; a remainder runs as plain launches
-    if (!S->exec && cycles >= G && S->cycles_run % G == 0) {
+    auto it = S->execs.find(S->rows_now);
+    if (it == S->execs.end() && cycles >= G && S->cycles_run % G == 0) {
       cudaGraph_t g = nullptr;
       RICHM_CUDA_TRY(cudaStreamBeginCapture(S->s, cudaStreamCaptureModeThreadLocal));
       richm_status st = run_cycles(S, G);
@@ -415,15 +446,14 @@ richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, voi
         return st;
       }
       if (e != cudaSuccess) return set_error(RICHM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&S->exec, g, 0);
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
       cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        S->exec = nullptr;
-        return set_error(RICHM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
-      }
+      if (e != cudaSuccess) return set_error(RICHM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+      it = S->execs.emplace(S->rows_now, ex).first;
     }
-    while (S->exec && cycles - done >= G && S->cycles_run % G == 0) {
-      RICHM_CUDA_TRY(cudaGraphLaunch(S->exec, S->s));
+    while (it != S->execs.end() && cycles - done >= G && S->cycles_run % G == 0) {
+      RICHM_CUDA_TRY(cudaGraphLaunch(it->second, S->s));
       S->cycles_run += G;
       done += G;
     }
@@ -434,8 +464,12 @@ richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, voi
   }
   if (active_out) {
     RICHM_CUDA_TRY(cudaMemcpyAsync(S->h_count, S->count, sizeof(int), cudaMemcpyDeviceToHost, S->s));
+    if (S->o.fuse > 1)
+      RICHM_CUDA_TRY(cudaMemcpyAsync(S->h_count + 1, S->active, sizeof(int) * S->op->batch, cudaMemcpyDeviceToHost,
+                                     S->s));
     RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
     *active_out = *S->h_count;
+    if (S->o.fuse > 1 && *active_out > 0) S->rows_now = choose_rows(S);
   }
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
   RICHM_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, S->ev_out, 0));

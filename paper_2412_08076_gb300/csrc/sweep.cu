@@ -399,6 +399,16 @@ richm_status richm_tuned(const richm_operator* op, int* fuse, int* rows) {
   return RICHM_OK;
 }
 
+richm_status richm_set_tuning(richm_operator* op, int fuse, int rows) {
+  clear_error();
+  RICHM_ARG(op != nullptr, "null operator");
+  RICHM_ARG(fuse == 1 || fuse == 4 || fuse == 8, "fuse must be 1, 4 or 8");
+  RICHM_ARG(rows == 32 || rows == 64 || rows == 128 || rows == 256, "rows must be 32, 64, 128 or 256");
+  op->best_fuse = fuse;
+  op->best_rows = rows;
+  return RICHM_OK;
+}
+
 richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, void* x_prev, const void* b,
                                 const void* w, const void* alpha, const void* alpha_t, int K,
                                 const richm_sweep_opts* opts, void* work, size_t work_bytes, void* stream) {

@@ -73,6 +73,7 @@ _SIGS = {
     "richm_autotune_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_autotune": (_I, [_P, _I, _I, _P, _SZ, _P, C.POINTER(_I), C.POINTER(C.c_float)]),
     "richm_tuned": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
+    "richm_set_tuning": (_I, [_P, _I, _I]),
     "richm_residual_norm": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_residual_norm_static": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "richm_solve_workspace": (_I, [_P, C.POINTER(richm_solve_opts), C.POINTER(_SZ)]),
@@ -276,6 +277,10 @@ class Operator:
         f, r = C.c_int(), C.c_int()
         _check(load().richm_tuned(self.handle, C.byref(f), C.byref(r)), "richm_tuned")
         return f.value, r.value
+
+    def set_tuning(self, fuse: int, rows: int):
+        """richm_set_tuning: fix the pass length and the fused tile height."""
+        _check(load().richm_set_tuning(self.handle, fuse, rows), "richm_set_tuning")
 
     def residual_norm(self, dtype, x, b, r_out=None, work=None, stream=None):
         """richm_residual_norm: returns (rnorm, bnorm, rel) as FP64 CUDA tensors [batch]."""
