@@ -582,6 +582,49 @@ def run_ours(args):
     S.close()
     fuse_rows = op.tuned()[1]
     workloads = None if args.no_secondary else secondary_workloads(dev)
+    # -- experiment: bfloat16 storage of the inner iterate (FP32 arithmetic, FP64 refinement)
+    bf16 = None
+    if not args.no_solve:
+        xb16 = op.zeros(richm.BF16)
+        xpb16 = op.zeros(richm.BF16)
+        wsb = op.workspace(op._ws("richm_sweeps_workspace", richm.BF16))
+        op.apply_sweeps(richm.BF16, xb16, xpb16, b32, w, a, None, K=192, m=M, fuse=fuse, work=wsb)
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(3):
+            op.apply_sweeps(richm.BF16, xb16, xpb16, b32, w, a, None, K=192, m=M, fuse=fuse, work=wsb)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        bf_ms = q0.elapsed_time(q1) / (3 * 192 // fuse)
+        ob = op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10**8, refine_every=REFINE, inner=richm.BF16, use_graph=1,
+                           fuse=fuse)
+        Xb = op.zeros(richm.F64)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        st_b, info_b = op.solve(B64, Xb, w, a, None, ob)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        from oracle.operators import assemble_q1
+        xbh = op.unpack(Xb, richm.F64).cpu().numpy()
+        offs = np.cumsum([0] + [t.n * t.n for t in insts])
+        worst_b = 0.0
+        for i in range(0, len(insts), 64):
+            t = insts[i]
+            A = assemble_q1(t.n, t.eps, t.theta)
+            u = xbh[offs[i]:offs[i + 1]]
+            worst_b = max(worst_b, np.linalg.norm(rhs[i].ravel() - A @ u) / np.linalg.norm(rhs[i]))
+        bf16 = {"fused_launch_ms": bf_ms, "fused_gdof_sweeps_per_s": dofs * fuse / (bf_ms / 1e3) / 1e9,
+                "fp32_fused_gdof_sweeps_per_s": dofs * fuse / (roof["launch_ms"] / 1e3) / 1e9
+                if roof.get("sweeps_per_launch", 1) > 1 else None,
+                "solve_seconds": t0.elapsed_time(t1) / 1e3, "status": int(st_b),
+                "converged": sum(1 for _, _, s_ in info_b if s_ == richm.OK),
+                "max_sweeps": int(max(sw_ for sw_, _, _ in info_b)), "oracle_checked": 4,
+                "oracle_worst_rel_res": worst_b,
+                "note": "bfloat16 inner state (x_k, x_{k-1} and the correction stored as bf16), FP32 arithmetic "
+                        "and rhs, FP64 refinement every 64 sweeps; an experiment, not the headline"}
+
     line = None
     if rank == 0:
         cpu_rate, cpu_desc = oracle_sample_rate(insts, seconds=args.cpu_seconds)
@@ -606,6 +649,7 @@ def run_ours(args):
             "clocks": clk,
             "time_to_tol": ttt,
             "workloads": workloads,
+            "bf16_state_experiment": bf16,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -73,7 +73,9 @@ typedef enum {
   RICHM_F64 = 0,   /* double */
   RICHM_F32 = 1,   /* float */
   RICHM_C64 = 2,   /* complex64: interleaved {float re, float im} */
-  RICHM_C128 = 3   /* complex128: interleaved {double re, double im} */
+  RICHM_C128 = 3,  /* complex128: interleaved {double re, double im} */
+  RICHM_BF16 = 4   /* bfloat16 storage of the iterate with FP32 arithmetic (Q1 sweeps and the solver's
+                      inner state only; the right-hand side and the weights stay FP32) */
 } richm_dtype;
 
 /* One PDE instance. eps, theta: anisotropy strength (0 < eps <= 1) and angle for
@@ -158,6 +160,9 @@ richm_status richm_sweeps_workspace(const richm_operator* op, richm_dtype dtype,
  * w: [batch][m] (required); alpha: [batch][m] or NULL (no momentum; x_prev may then
  * be NULL and is not written); alpha_t: [batch][m] or NULL (= alpha, i.e. NAG).
  * dtype: RICHM_F32/RICHM_F64 for Q1, RICHM_C64/RICHM_C128 for Helmholtz (weights real).
+ * RICHM_BF16 (Q1): x and x_prev hold bfloat16, b and the weights are FP32, the sweeps
+ * run in FP32 in fused passes only (fuse 4 or 8, or 0 with a tuned pass length > 1;
+ * K must be a multiple of it) and each pass rounds its two output levels to bfloat16.
  * work: at least richm_sweeps_workspace bytes. K = 0 is a no-op. */
 richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, void* x_prev, const void* b,
                                 const void* w, const void* alpha, const void* alpha_t, int K,
@@ -221,7 +226,8 @@ typedef struct {
   double tol;            /* stop an instance once ||b - A x|| / ||b|| <= tol (FP64 residual) */
   long long max_sweeps;  /* per instance */
   int refine_every;      /* sweeps between FP64 refinement steps / convergence checks (>= 1) */
-  int inner;             /* richm_dtype of the inner sweeps: RICHM_F32 (mixed precision) or RICHM_F64 */
+  int inner;             /* richm_dtype of the inner sweeps: RICHM_F32 (mixed precision), RICHM_F64, or
+                            RICHM_BF16 (bfloat16 inner state, FP32 arithmetic and rhs; fused sweeps) */
   int precond;           /* as in richm_sweep_opts */
   int fuse;              /* as in richm_sweep_opts */
   int use_graph;         /* 1: replay the refinement cycle as a CUDA graph */

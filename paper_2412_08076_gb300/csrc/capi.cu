@@ -120,11 +120,13 @@ static richm_status pack_dispatch(const richm_operator* op, richm_dtype dt, cons
   cudaStream_t s = (cudaStream_t)stream;
   size_t es = dtype_size(dt);
   if (PACK) {
-    if (es == 4) pack_kernel<uint32_t><<<grid, 256, 0, s>>>(op->d_inst, (const uint32_t*)src, (uint32_t*)dst);
+    if (es == 2) pack_kernel<uint16_t><<<grid, 256, 0, s>>>(op->d_inst, (const uint16_t*)src, (uint16_t*)dst);
+    else if (es == 4) pack_kernel<uint32_t><<<grid, 256, 0, s>>>(op->d_inst, (const uint32_t*)src, (uint32_t*)dst);
     else if (es == 8) pack_kernel<unsigned long long><<<grid, 256, 0, s>>>(op->d_inst, (const unsigned long long*)src, (unsigned long long*)dst);
     else pack_kernel<W16><<<grid, 256, 0, s>>>(op->d_inst, (const W16*)src, (W16*)dst);
   } else {
-    if (es == 4) unpack_kernel<uint32_t><<<grid, 256, 0, s>>>(op->d_inst, (const uint32_t*)src, (uint32_t*)dst);
+    if (es == 2) unpack_kernel<uint16_t><<<grid, 256, 0, s>>>(op->d_inst, (const uint16_t*)src, (uint16_t*)dst);
+    else if (es == 4) unpack_kernel<uint32_t><<<grid, 256, 0, s>>>(op->d_inst, (const uint32_t*)src, (uint32_t*)dst);
     else if (es == 8) unpack_kernel<unsigned long long><<<grid, 256, 0, s>>>(op->d_inst, (const unsigned long long*)src, (unsigned long long*)dst);
     else unpack_kernel<W16><<<grid, 256, 0, s>>>(op->d_inst, (const W16*)src, (W16*)dst);
   }

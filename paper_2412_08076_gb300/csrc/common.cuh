@@ -9,6 +9,7 @@
 // row is loaded once per tile.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -120,10 +121,11 @@ inline size_t dtype_size(richm_dtype t) {
     case RICHM_F32: return 4;
     case RICHM_C64: return 8;
     case RICHM_C128: return 16;
+    case RICHM_BF16: return 2;
   }
   return 0;
 }
-inline bool dtype_valid(int t) { return t >= RICHM_F64 && t <= RICHM_C128; }
+inline bool dtype_valid(int t) { return t >= RICHM_F64 && t <= RICHM_BF16; }
 inline bool dtype_complex(richm_dtype t) { return t == RICHM_C64 || t == RICHM_C128; }
 
 // True if every instance of the operator is of a problem kind that uses `t`.

@@ -29,6 +29,12 @@ richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, cons
                                 float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
                                 int kidx0, int precond, const int* active, cudaStream_t s, int rows = 0);
 
+// The same with bfloat16 state (x, x_prev and the outputs); b and the arithmetic are FP32.
+richm_status launch_sweep_fused_bf16(richm_operator* op, int TL, const __nv_bfloat16* x, const __nv_bfloat16* xp,
+                                     const float* b, __nv_bfloat16* out_x, __nv_bfloat16* out_xp, const float* w,
+                                     const float* a, const float* at, int m, int kidx0, int precond,
+                                     const int* active, cudaStream_t s, int rows = 0);
+
 // r = b - A x in FP64 with per-tile partial sums (sum |r|^2, sum |b|^2) written to
 // `partials` (one double2 per warp tile of the residual geometry); r_out may be null.
 template <typename E>

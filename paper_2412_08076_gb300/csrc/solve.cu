@@ -57,6 +57,24 @@ namespace richm {
 
 static size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 
+// Inner right-hand-side type: FP64 for FP64 inner sweeps, FP32 otherwise (also for
+// bfloat16 state, whose arithmetic is FP32).
+template <typename T> struct RhsOf { using type = float; };
+template <> struct RhsOf<double> { using type = double; };
+
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ double to_f(double v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v) { return (T)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename T> __device__ __forceinline__ T diff_e(T p, T e) { return p - e; }
+template <> __device__ __forceinline__ __nv_bfloat16 diff_e<__nv_bfloat16>(__nv_bfloat16 p, __nv_bfloat16 e) {
+  return __float2bfloat16_rn(__bfloat162float(p) - __bfloat162float(e));
+}
+
 // x += e_k; ep_out = ep - e_k; e_out = 0 (pointwise; e_out/ep_out may alias inputs).
 template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -76,18 +94,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const long long o = I.off + (long long)r * I.pitch + c0;
     double2 xv = *reinterpret_cast<const double2*>(x + o);
     VecN<T, 2> ev = *reinterpret_cast<const VecN<T, 2>*>(e + o);
-    xv.x += (double)ev.v[0];
-    xv.y += (double)ev.v[1];
+    xv.x += to_d(ev.v[0]);
+    xv.y += to_d(ev.v[1]);
     if (ep) {
       VecN<T, 2> pv = *reinterpret_cast<const VecN<T, 2>*>(ep + o);
       VecN<T, 2> np;
-      np.v[0] = pv.v[0] - ev.v[0];
-      np.v[1] = pv.v[1] - ev.v[1];
+      np.v[0] = diff_e(pv.v[0], ev.v[0]);
+      np.v[1] = diff_e(pv.v[1], ev.v[1]);
       *reinterpret_cast<VecN<T, 2>*>(ep_out + o) = np;
     }
     VecN<T, 2> nz;
-    nz.v[0] = T(0);
-    nz.v[1] = T(0);
+    nz.v[0] = from_f<T>(0.f);
+    nz.v[1] = from_f<T>(0.f);
     *reinterpret_cast<double2*>(x + o) = xv;
     *reinterpret_cast<VecN<T, 2>*>(e_out + o) = nz;
   }
@@ -173,13 +191,14 @@ __global__ void solve_init_kernel(int batch, long long* sweeps, int* status, int
 
 template <typename T>
 static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 1, bool x0_zero = false) {
+  using R = typename RhsOf<T>::type;
   richm_operator* op = S->op;
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 64, kRows, &tm));  // residual / update geometry of FP64
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (init && x0_zero) {
-    zero_start_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(op->d_inst, tm->d_tiles, tm->ntiles, S->b,
-                                                                   (T*)S->rhs, S->partials);
+    zero_start_kernel<R><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(op->d_inst, tm->d_tiles, tm->ntiles, S->b,
+                                                                   (R*)S->rhs, S->partials);
     RICHM_LAUNCH_CHECK("zero start");
   }
   if (!init) {
@@ -190,7 +209,7 @@ static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 
     RICHM_LAUNCH_CHECK("refine update");
   }
   if (!(init && x0_zero))
-    RICHM_TRY((launch_residual_to<double, T>(op, S->x, S->b, (T*)S->rhs, S->partials, S->active, S->s)));
+    RICHM_TRY((launch_residual_to<double, R>(op, S->x, S->b, (R*)S->rhs, S->partials, S->active, S->s)));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->count, 0, sizeof(int), S->s));
   const int wpb = 8;
   solve_reduce_kernel<<<(op->batch + wpb - 1) / wpb, wpb * 32, 0, S->s>>>(
@@ -205,6 +224,19 @@ template <typename T>
 static richm_status cycle_t(richm_solver* S, long long k0) {
   const int Sw = S->o.refine_every;
   int cur = 0, prv = 1;
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    const int TL = S->o.fuse;
+    for (int k = 0; k < Sw; k += TL) {
+      const int oc = cur == 0 ? 2 : 0, op_ = cur == 0 ? 3 : 1;
+      RICHM_TRY(launch_sweep_fused_bf16(S->op, TL, (const T*)S->E[cur], (const T*)S->E[prv], (const float*)S->rhs,
+                                        (T*)S->E[oc], (T*)S->E[op_], (const float*)S->w, (const float*)S->a,
+                                        (const float*)S->at, S->o.m, (int)((k0 + k) % S->o.m), S->o.precond,
+                                        S->active, S->s, S->rows_now));
+      cur = oc;
+      prv = op_;
+    }
+    return refine_t<T>(S, false, cur, prv);
+  } else {
   if constexpr (std::is_same<T, float>::value) {
     if (S->o.fuse == 4 || S->o.fuse == 8) {
       // temporally blocked passes alternate between the pairs (E0, E1) and (E2, E3)
@@ -233,6 +265,7 @@ static richm_status cycle_t(richm_solver* S, long long k0) {
     fre = nf;
   }
   return refine_t<T>(S, false, cur, prv);
+  }
 }
 
 // Fused tile height for the instances still iterating: the largest of the tuned
@@ -263,6 +296,7 @@ static richm_status run_cycles(richm_solver* S, int cycles) {
   for (int c = 0; c < cycles; ++c) {
     const long long k0 = (S->cycles_run + c) * (long long)S->o.refine_every;
     if (S->o.inner == RICHM_F32) RICHM_TRY(cycle_t<float>(S, k0));
+    else if (S->o.inner == RICHM_BF16) RICHM_TRY(cycle_t<__nv_bfloat16>(S, k0));
     else RICHM_TRY(cycle_t<double>(S, k0));
   }
   return RICHM_OK;
@@ -280,11 +314,18 @@ static richm_status check_solve_opts(const richm_operator* op, const richm_solve
   RICHM_ARG(o->refine_every >= 1, "refine_every must be >= 1");
   RICHM_ARG(o->max_sweeps >= 0, "max_sweeps < 0");
   RICHM_ARG(o->tol >= 0.0, "tol < 0");
-  RICHM_ARG(o->inner == RICHM_F32 || o->inner == RICHM_F64, "inner dtype must be RICHM_F32 or RICHM_F64");
+  RICHM_ARG(o->inner == RICHM_F32 || o->inner == RICHM_F64 || o->inner == RICHM_BF16,
+            "inner dtype must be RICHM_F32, RICHM_F64 or RICHM_BF16");
   RICHM_ARG(o->precond == 0 || o->precond == 1, "precond must be 0 or 1");
   RICHM_ARG(o->fuse == 0 || o->fuse == 1 || o->fuse == 4 || o->fuse == 8, "fuse must be 0, 1, 4 or 8");
-  RICHM_ARG(o->fuse <= 1 || (o->inner == RICHM_F32 && o->refine_every % o->fuse == 0),
-            "fused sweeps need inner = RICHM_F32 and refine_every divisible by fuse");
+  RICHM_ARG(o->fuse <= 1 || (o->inner != RICHM_F64 && o->refine_every % o->fuse == 0),
+            "fused sweeps need an FP32 or bfloat16 inner state and refine_every divisible by fuse");
+  if (o->inner == RICHM_BF16) {
+    const int f = o->fuse ? o->fuse : op->best_fuse;
+    if ((f != 4 && f != 8) || o->refine_every % f != 0)
+      return set_error(RICHM_ERR_UNSUPPORTED, "bfloat16 inner state needs fused sweeps (4 or 8 per pass) dividing "
+                                              "refine_every");
+  }
   for (int b = 0; b < op->batch; ++b)
     if (op->h_inst[b].kind != RICHM_ANISO_Q1)
       return set_error(RICHM_ERR_UNSUPPORTED, "richm_solve handles Q1 instances (instance %d is not)", b);
@@ -295,11 +336,12 @@ richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_o
   clear_error();
   RICHM_TRY(check_solve_opts(op, o));
   RICHM_ARG(bytes != nullptr, "null output");
-  const size_t es = o->inner == RICHM_F32 ? 4 : 8;
+  const size_t es = o->inner == RICHM_F64 ? 8 : (o->inner == RICHM_F32 ? 4 : 2);  // inner state
+  const size_t rs = o->inner == RICHM_F64 ? 8 : 4;                                  // inner rhs
   int nt = 0;
   RICHM_TRY(residual_tiles<double>(const_cast<richm_operator*>(op), &nt));
   size_t B = (size_t)op->batch;
-  *bytes = 5 * a256(op->elems * es) + a256(sizeof(double2) * nt) + 2 * a256(sizeof(double) * B) +
+  *bytes = 4 * a256(op->elems * es) + a256(op->elems * rs) + a256(sizeof(double2) * nt) + 2 * a256(sizeof(double) * B) +
            a256(sizeof(long long) * B) + 2 * a256(sizeof(int) * B) + a256(sizeof(int));
   return RICHM_OK;
 }
@@ -321,12 +363,13 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   S->op = op;
   S->o = *o;
   if (S->o.fuse == 0) {
-    S->o.fuse = (o->inner == RICHM_F32 && o->refine_every % op->best_fuse == 0) ? op->best_fuse : 1;
+    S->o.fuse = (o->inner != RICHM_F64 && o->refine_every % op->best_fuse == 0) ? op->best_fuse : 1;
   }
   S->w = w;
   S->a = alpha;
   S->at = alpha_t;
-  const size_t es = o->inner == RICHM_F32 ? 4 : 8;
+  const size_t es = o->inner == RICHM_F64 ? 8 : (o->inner == RICHM_F32 ? 4 : 2);
+  const size_t rs = o->inner == RICHM_F64 ? 8 : 4;
   int nt = 0;
   residual_tiles<double>(op, &nt);
   char* p = reinterpret_cast<char*>(work);
@@ -335,7 +378,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
     p += a256(op->elems * es);
   }
   S->rhs = p;
-  p += a256(op->elems * es);
+  p += a256(op->elems * rs);
   S->partials = reinterpret_cast<double2*>(p);
   p += a256(sizeof(double2) * nt);
   const size_t B = (size_t)op->batch;
@@ -363,7 +406,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   // warm the tile maps before any capture (they allocate on first use)
   const TileMap* tm = nullptr;
   richm_status st = get_tiles(op, 64, kRows, &tm);
-  if (st == RICHM_OK) st = get_tiles(op, o->inner == RICHM_F32 ? 128 : 64, kRows, &tm);
+  if (st == RICHM_OK) st = get_tiles(op, o->inner == RICHM_F64 ? 64 : 128, kRows, &tm);
   S->rows_max = S->rows_now = op->best_rows;
   if (S->o.fuse > 1)
     for (int rows : {256, 128, 64, 32})
@@ -400,7 +443,7 @@ static richm_status solver_start_impl(richm_solver* S, const double* b, double* 
   S->rows_now = S->rows_max;
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, (cudaStream_t)stream));
   RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
-  const size_t es = S->o.inner == RICHM_F32 ? 4 : 8;
+  const size_t es = S->o.inner == RICHM_F64 ? 8 : (S->o.inner == RICHM_F32 ? 4 : 2);
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[0], 0, op->elems * es, S->s));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[1], 0, op->elems * es, S->s));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[2], 0, op->elems * es, S->s));
@@ -409,6 +452,7 @@ static richm_status solver_start_impl(richm_solver* S, const double* b, double* 
   RICHM_LAUNCH_CHECK("solve init");
   if (x0_zero) RICHM_CUDA_TRY(cudaMemsetAsync(x, 0, op->elems * sizeof(double), S->s));
   if (S->o.inner == RICHM_F32) RICHM_TRY(refine_t<float>(S, true, 0, 1, x0_zero));
+  else if (S->o.inner == RICHM_BF16) RICHM_TRY(refine_t<__nv_bfloat16>(S, true, 0, 1, x0_zero));
   else RICHM_TRY(refine_t<double>(S, true, 0, 1, x0_zero));
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
   RICHM_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, S->ev_out, 0));

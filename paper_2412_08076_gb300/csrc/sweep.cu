@@ -431,9 +431,37 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
   if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
   richm_sweep_opts o = *opts;
-  if (o.fuse == 0) o.fuse = (dtype == RICHM_F32) ? op->best_fuse : 1;
+  if (o.fuse == 0) o.fuse = (dtype == RICHM_F32 || dtype == RICHM_BF16) ? op->best_fuse : 1;
   opts = &o;
   switch (dtype) {
+    case RICHM_BF16: {
+      // fused passes only: (x, x_prev) -> (W0, W1) -> (x, x_prev) ...
+      const int TL = o.fuse;
+      if (TL != 4 && TL != 8)
+        return set_error(RICHM_ERR_UNSUPPORTED, "bfloat16 state needs fused passes (fuse 4 or 8)");
+      if (K % TL != 0) return set_error(RICHM_ERR_UNSUPPORTED, "bfloat16 state: K must be a multiple of %d", TL);
+      using B16 = __nv_bfloat16;
+      const size_t bytes = op->elems * sizeof(B16);
+      B16* W0 = reinterpret_cast<B16*>(work);
+      B16* W1 = reinterpret_cast<B16*>(reinterpret_cast<char*>(work) + ((bytes + 255) / 256) * 256);
+      B16* cur = (B16*)x;
+      B16* prev = (B16*)x_prev;
+      const bool mom = alpha != nullptr;
+      for (int k = 0; k < K; k += TL) {
+        B16* ox = (cur == (B16*)x) ? W0 : (B16*)x;
+        B16* oxp = (cur == (B16*)x) ? W1 : (mom ? (B16*)x_prev : W1);
+        RICHM_TRY(launch_sweep_fused_bf16(op, TL, cur, mom ? prev : nullptr, (const float*)b, ox, oxp,
+                                          (const float*)w, (const float*)alpha, (const float*)alpha_t, o.m,
+                                          (int)(((long long)o.k_start + k) % o.m), o.precond, nullptr, s));
+        cur = ox;
+        prev = oxp;
+      }
+      if (cur != (B16*)x) {
+        RICHM_CUDA_TRY(cudaMemcpyAsync(x, cur, bytes, cudaMemcpyDeviceToDevice, s));
+        if (mom) RICHM_CUDA_TRY(cudaMemcpyAsync(x_prev, prev, bytes, cudaMemcpyDeviceToDevice, s));
+      }
+      return RICHM_OK;
+    }
     case RICHM_F32:
       return apply_sweeps_t<float>(op, (float*)x, (float*)x_prev, (const float*)b, w, alpha, alpha_t, K, opts, work, s);
     case RICHM_F64:

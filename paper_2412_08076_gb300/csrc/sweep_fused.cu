@@ -27,11 +27,11 @@ struct SweepTArgs {
   const Inst* insts;
   const Tile* tiles;
   int ntiles;
-  const float* x;
-  const float* xp;
+  const void* x;     // state storage type ST (float or bf16)
+  const void* xp;
   const float* b;
-  float* out_x;   // x_{k+TL}
-  float* out_xp;  // x_{k+TL-1}
+  void* out_x;       // x_{k+TL}
+  void* out_xp;      // x_{k+TL-1}
   const float* w;
   const float* a;
   const float* at;
@@ -65,21 +65,48 @@ struct FusedState {
 
 constexpr int kPrefetch = 2;  // row steps between issuing a row's copies and using it
 
-template <int TL>
+template <typename ST, int TL>
 struct FusedRings {
   // one spare slot in each ring: a slot is re-targeted two row steps after its last read
   static constexpr int NS = kPrefetch + 2;       // x_k and x_{k-1} row slots
   static constexpr int NB = TL + kPrefetch + 2;  // b row slots (kept until level TL)
-  static constexpr int FLOATS = (2 * NS + NB) * 128;
+  static constexpr int XROW = 128 * (int)sizeof(ST);  // bytes of one state row (128 columns)
+  static constexpr int BYTES = 2 * NS * XROW + NB * 128 * 4;
 };
 
+// State storage: FP32, or bfloat16 (arithmetic stays FP32; values are rounded to
+// nearest-even when a pass stores its result).
+__device__ __forceinline__ void st4_to_float(const float* p, float* v) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void st4_to_float(const __nv_bfloat16* p, float* v) {
+  const uint2 q = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+  const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void float_to_st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void float_to_st4(__nv_bfloat16* p, const float* v) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 q;
+  q.x = *reinterpret_cast<const unsigned*>(&lo);
+  q.y = *reinterpret_cast<const unsigned*>(&hi);
+  *reinterpret_cast<uint2*>(p) = q;
+}
+
+template <typename ST>
 struct FusedCtx {
-  const float* xb;
-  const float* xpb;
+  const ST* xb;
+  const ST* xpb;
   const float* bb;
-  float* ox;
-  float* oxp;
-  float* ring;  // this warp's rings: x[NS][128], xp[NS][128], b[NB][128]
+  ST* ox;
+  ST* oxp;
+  unsigned char* ring;  // this warp's rings: x[NS] rows, xp[NS] rows (ST), b[NB] rows (float)
   int n, pitch, c0, lane, r0, r1, rlast;
   bool live, store_cols;
   float sc, sax, say, sd1, sd2;
@@ -96,10 +123,20 @@ __device__ __forceinline__ void row_neighbours_m(RowT<float, 4>& r, float ml, fl
   r.yr = mr * __shfl_down_sync(0xffffffffu, r.y[0], 1);
 }
 
-__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   const int nbytes = valid ? 16 : 0;  // 0: zero-fill, no global read
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int nbytes = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+template <typename ST>
+__device__ __forceinline__ void cp_async_state(void* smem, const ST* gmem, bool valid) {
+  if constexpr (sizeof(ST) == 4) cp_async16(smem, gmem, valid);  // four FP32 values
+  else cp_async8(smem, gmem, valid);                               // four bf16 values
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -109,35 +146,35 @@ __device__ __forceinline__ int ring_slot(int r, int nslots) { return (r + 64 * n
 
 // Issue the copies of input row r (x_k, x_{k-1}, b) into the rings (zero-filled
 // outside rows 1..n, beyond the tile's last needed row, or beyond the row pitch).
-template <int TL, bool MOM>
-__device__ __forceinline__ void issue_row(const FusedCtx& c, int r) {
-  using R = FusedRings<TL>;
+template <typename ST, int TL, bool MOM>
+__device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
+  using R = FusedRings<ST, TL>;
   const bool valid = (r >= 1) && (r <= c.n) && (r <= c.rlast) && c.live;
   const long long ro = (long long)(valid ? r : 0) * c.pitch + (c.live ? c.c0 : 0);
-  float* xr = c.ring + ring_slot(r, R::NS) * 128 + c.lane * 4;
-  cp_async16(xr, c.xb + ro, valid);
-  if (MOM) cp_async16(c.ring + (R::NS + ring_slot(r, R::NS)) * 128 + c.lane * 4, c.xpb + ro, valid);
-  cp_async16(c.ring + (2 * R::NS + ring_slot(r, R::NB)) * 128 + c.lane * 4, c.bb + ro, valid);
+  const int xs = ring_slot(r, R::NS);
+  cp_async_state<ST>(c.ring + xs * R::XROW + c.lane * 4 * (int)sizeof(ST), c.xb + ro, valid);
+  if (MOM)
+    cp_async_state<ST>(c.ring + (R::NS + xs) * R::XROW + c.lane * 4 * (int)sizeof(ST), c.xpb + ro, valid);
+  cp_async16(c.ring + 2 * R::NS * R::XROW + ring_slot(r, R::NB) * 512 + c.lane * 16, c.bb + ro, valid);
   cp_async_commit();
 }
 
 // One row step of the pipeline at input row rr and window phase PH.
 // NAGF: at == a, so x_{k+1} = y + w (b - A y) needs only the window.
-template <int TL, bool MOM, bool NAGF, int PH>
-__device__ __forceinline__ void fused_step(int rr, const FusedCtx& c, FusedState<TL>& st, const float* wl,
+template <typename ST, int TL, bool MOM, bool NAGF, int PH>
+__device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedState<TL>& st, const float* wl,
                                            const float* al, const float* atl) {
-  using R = FusedRings<TL>;
+  using R = FusedRings<ST, TL>;
   constexpr int VW = 4;
   constexpr int SD = PH, SU = (PH + 1) % 3, SC = (PH + 2) % 3;
-  issue_row<TL, MOM>(c, rr + kPrefetch);
+  issue_row<ST, TL, MOM>(c, rr + kPrefetch);
   cp_async_wait<kPrefetch>();  // the copies of row rr have landed
   float x0[VW], xm[VW];
   {
-    const float4 X = *reinterpret_cast<const float4*>(c.ring + ring_slot(rr, R::NS) * 128 + c.lane * 4);
-    x0[0] = X.x; x0[1] = X.y; x0[2] = X.z; x0[3] = X.w;
+    const int xs = ring_slot(rr, R::NS);
+    st4_to_float(reinterpret_cast<const ST*>(c.ring + xs * R::XROW) + c.lane * 4, x0);
     if (MOM) {
-      const float4 XP = *reinterpret_cast<const float4*>(c.ring + (R::NS + ring_slot(rr, R::NS)) * 128 + c.lane * 4);
-      xm[0] = XP.x; xm[1] = XP.y; xm[2] = XP.z; xm[3] = XP.w;
+      st4_to_float(reinterpret_cast<const ST*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, xm);
     } else {
       xm[0] = xm[1] = xm[2] = xm[3] = 0.f;
     }
@@ -148,7 +185,8 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx& c, FusedState
 #pragma unroll
   for (int s = 1; s <= TL; ++s) {
     const int row = rr - s;
-    const float4 B4 = *reinterpret_cast<const float4*>(c.ring + (2 * R::NS + ring_slot(row, R::NB)) * 128 + c.lane * 4);
+    const float4 B4 =
+        *reinterpret_cast<const float4*>(c.ring + 2 * R::NS * R::XROW + ring_slot(row, R::NB) * 512 + c.lane * 16);
     const float Bv[VW] = {B4.x, B4.y, B4.z, B4.w};
     // extend level s's window with row rr - s + 1 of y_{s-1}
     float* Yn = st.Y[s][SD];
@@ -202,18 +240,8 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx& c, FusedState
   }
   if (c.store_cols) {
     const int ra = rr - TL, rb = rr - TL + 1;
-    if (ra >= c.r0 && ra <= c.r1) {
-      VecN<float, VW> O;
-#pragma unroll
-      for (int e = 0; e < VW; ++e) O.v[e] = newx[TL][e];
-      stv<float, VW>(c.ox + (long long)ra * c.pitch + c.c0, O);
-    }
-    if (MOM && rb >= c.r0 && rb <= c.r1) {
-      VecN<float, VW> O;
-#pragma unroll
-      for (int e = 0; e < VW; ++e) O.v[e] = newx[TL - 1][e];
-      stv<float, VW>(c.oxp + (long long)rb * c.pitch + c.c0, O);
-    }
+    if (ra >= c.r0 && ra <= c.r1) float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, newx[TL]);
+    if (MOM && rb >= c.r0 && rb <= c.r1) float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, newx[TL - 1]);
   }
   if (MOM) {
 #pragma unroll
@@ -223,11 +251,11 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx& c, FusedState
   }
 }
 
-template <int TL, bool MOM, bool PRE, bool NAGF>
+template <typename ST, int TL, bool MOM, bool PRE, bool NAGF>
 __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kernel(const SweepTArgs A) {
   constexpr int VW = 4;
   constexpr int STRIDE = 128 - 2 * TL;
-  extern __shared__ __align__(16) float fused_smem[];
+  extern __shared__ __align__(16) unsigned char fused_smem[];
   const int lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kFuseWarps + (threadIdx.x >> 5);
   if (wt >= A.ntiles) return;
@@ -244,7 +272,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
     al[s] = MOM ? A.a[ci] : 0.f;
     atl[s] = MOM ? (A.at ? A.at[ci] : al[s]) : 0.f;
   }
-  FusedCtx c;
+  FusedCtx<ST> c;
   c.n = I.n;
   c.pitch = I.pitch;
   c.lane = lane;
@@ -267,12 +295,12 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   c.r0 = t.ty * A.rows + 1;
   c.r1 = min(c.r0 + A.rows - 1, c.n);
   c.rlast = c.r1 + TL;
-  c.xb = A.x + I.off;
-  c.xpb = MOM ? A.xp + I.off : A.x + I.off;
+  c.xb = reinterpret_cast<const ST*>(A.x) + I.off;
+  c.xpb = reinterpret_cast<const ST*>(MOM ? A.xp : A.x) + I.off;
   c.bb = A.b + I.off;
-  c.ox = A.out_x + I.off;
-  c.oxp = MOM ? A.out_xp + I.off : nullptr;
-  c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<TL>::FLOATS;
+  c.ox = reinterpret_cast<ST*>(A.out_x) + I.off;
+  c.oxp = MOM ? reinterpret_cast<ST*>(A.out_xp) + I.off : nullptr;
+  c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<ST, TL>::BYTES;
 
   FusedState<TL> st;
 #pragma unroll
@@ -287,40 +315,42 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
     for (int e = 0; e < VW; ++e) st.xc[s][e] = st.vc[s][e] = st.prevx[s][e] = 0.f;
   }
   // b rows above the tile's first input row are never loaded: zero their slots
-  for (int q = 0; q < FusedRings<TL>::FLOATS / 128; ++q)
-    *reinterpret_cast<float4*>(c.ring + q * 128 + lane * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = 0; q < FusedRings<ST, TL>::BYTES / 512; ++q)
+    *reinterpret_cast<float4*>(c.ring + q * 512 + lane * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
   const int rstart = c.r0 - TL;
 #pragma unroll
-  for (int d = 0; d < kPrefetch; ++d) issue_row<TL, MOM>(c, rstart + d);
+  for (int d = 0; d < kPrefetch; ++d) issue_row<ST, TL, MOM>(c, rstart + d);
   // rows r0-TL .. r1+TL in steps of three (a few extra steps at the end only
   // compute rows that are neither stored nor used)
   for (int rr = rstart; rr <= c.r1 + TL; rr += 3) {
-    fused_step<TL, MOM, NAGF, 0>(rr, c, st, wl, al, atl);
-    fused_step<TL, MOM, NAGF, 1>(rr + 1, c, st, wl, al, atl);
-    fused_step<TL, MOM, NAGF, 2>(rr + 2, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, 0>(rr, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, 1>(rr + 1, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, 2>(rr + 2, c, st, wl, al, atl);
   }
   cp_async_wait<0>();
 }
 
-richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
-                                float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
-                                int kidx0, int precond, const int* active, cudaStream_t s, int rows) {
+template <typename ST>
+static richm_status launch_fused_t(richm_operator* op, int TL, const ST* x, const ST* xp, const float* b, ST* out_x,
+                                   ST* out_xp, const float* w, const float* a, const float* at, int m, int kidx0,
+                                   int precond, const int* active, cudaStream_t s, int rows) {
   if (rows <= 0) rows = op->best_rows;
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, -TL, rows, &tm));
   SweepTArgs A{op->d_inst, tm->d_tiles, tm->ntiles, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, active, rows};
   const int blocks = (tm->ntiles + kFuseWarps - 1) / kFuseWarps;
   const int thr = kFuseWarps * 32;
-  const size_t smem = (TL == 4 ? FusedRings<4>::FLOATS : FusedRings<8>::FLOATS) * sizeof(float) * kFuseWarps;
+  const size_t smem =
+      (size_t)(TL == 4 ? FusedRings<ST, 4>::BYTES : FusedRings<ST, 8>::BYTES) * kFuseWarps;
   const bool mom = a != nullptr;
   const bool nag = mom && at == nullptr;  // at = a
-#define RICHM_FUSED(TLV)                                                                          \
-  if (nag && precond) sweepT_kernel<TLV, true, true, true><<<blocks, thr, smem, s>>>(A);         \
-  else if (nag) sweepT_kernel<TLV, true, false, true><<<blocks, thr, smem, s>>>(A);              \
-  else if (mom && precond) sweepT_kernel<TLV, true, true, false><<<blocks, thr, smem, s>>>(A);   \
-  else if (mom) sweepT_kernel<TLV, true, false, false><<<blocks, thr, smem, s>>>(A);             \
-  else if (precond) sweepT_kernel<TLV, false, true, false><<<blocks, thr, smem, s>>>(A);         \
-  else sweepT_kernel<TLV, false, false, false><<<blocks, thr, smem, s>>>(A);
+#define RICHM_FUSED(TLV)                                                                              \
+  if (nag && precond) sweepT_kernel<ST, TLV, true, true, true><<<blocks, thr, smem, s>>>(A);         \
+  else if (nag) sweepT_kernel<ST, TLV, true, false, true><<<blocks, thr, smem, s>>>(A);              \
+  else if (mom && precond) sweepT_kernel<ST, TLV, true, true, false><<<blocks, thr, smem, s>>>(A);   \
+  else if (mom) sweepT_kernel<ST, TLV, true, false, false><<<blocks, thr, smem, s>>>(A);             \
+  else if (precond) sweepT_kernel<ST, TLV, false, true, false><<<blocks, thr, smem, s>>>(A);         \
+  else sweepT_kernel<ST, TLV, false, false, false><<<blocks, thr, smem, s>>>(A);
   if (TL == 4) {
     RICHM_FUSED(4)
   } else if (TL == 8) {
@@ -331,6 +361,20 @@ richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, cons
 #undef RICHM_FUSED
   RICHM_LAUNCH_CHECK("fused sweep");
   return RICHM_OK;
+}
+
+richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
+                                float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
+                                int kidx0, int precond, const int* active, cudaStream_t s, int rows) {
+  return launch_fused_t<float>(op, TL, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, precond, active, s, rows);
+}
+
+richm_status launch_sweep_fused_bf16(richm_operator* op, int TL, const __nv_bfloat16* x, const __nv_bfloat16* xp,
+                                     const float* b, __nv_bfloat16* out_x, __nv_bfloat16* out_xp, const float* w,
+                                     const float* a, const float* at, int m, int kidx0, int precond,
+                                     const int* active, cudaStream_t s, int rows) {
+  return launch_fused_t<__nv_bfloat16>(op, TL, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, precond, active, s,
+                                       rows);
 }
 
 }  // namespace richm

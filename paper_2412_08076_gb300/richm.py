@@ -22,10 +22,11 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_UNSUPPORT
 # richm_problem
 ANISO_Q1, HELMHOLTZ_FD5_ABC, HELMHOLTZ_FD5_DIRICHLET = 0, 1, 2
 # richm_dtype
-F64, F32, C64, C128 = 0, 1, 2, 3
+F64, F32, C64, C128, BF16 = 0, 1, 2, 3, 4
 
-TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.complex64, C128: torch.complex128}
-REAL_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.float32, C128: torch.float64}
+TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.complex64, C128: torch.complex128,
+               BF16: torch.bfloat16}
+REAL_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.float32, C128: torch.float64, BF16: torch.float32}
 DTYPE_OF = {v: k for k, v in TORCH_DTYPE.items()}
 
 

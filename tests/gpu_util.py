@@ -24,7 +24,8 @@ def to_dev(op, arrays, dtype):
 
 def from_dev(op, buf, dtype):
     """Padded device buffer -> list of (n, n) numpy arrays."""
-    d = op.unpack(buf, dtype).cpu().numpy()
+    d = op.unpack(buf, dtype)
+    d = (d.float() if d.dtype == torch.bfloat16 else d).cpu().numpy()
     out, off = [], 0
     for n in op.ns:
         out.append(d[off:off + n * n].reshape(n, n))

@@ -189,3 +189,29 @@ def test_solve_host_matches_device_solve():
         u = hx.numpy()[off:off + t.n * t.n]
         off += t.n * t.n
         assert np.linalg.norm(bs[i].ravel() - As[i] @ u) / np.linalg.norm(bs[i]) <= 1e-10
+
+
+def test_bf16_inner_state_converges_with_mild_steps_and_reports_divergence_otherwise():
+    # bfloat16 inner iterate (FP32 arithmetic), FP64 refinement. With steps that damp
+    # every mode (|1 - w lam| <= 1) the refinement removes the storage rounding and the
+    # FP64 tolerance is reached; with the large steps of a Chebyshev-type schedule the
+    # rounding made at each pass boundary is amplified by the following steps, and the
+    # solver must report divergence instead of producing garbage.
+    insts, op, As, w, a, bs = _solve_setup([15, 31])
+    G = np.array([gershgorin_max(A) for A in As])
+    mild = np.tile((1.0 / G)[:, None], (1, 16))
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    opts = op.solve_opts(16, tol=1e-10, max_sweeps=2_000_000, inner=richm.BF16, fuse=8)
+    st, info = op.solve(B, X, coef(mild, richm.F32), coef(np.full_like(mild, 0.2), richm.F32), None, opts)
+    assert st == richm.OK, info
+    xs = from_dev(op, X, richm.F64)
+    for i, t in enumerate(insts):
+        assert np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i]) <= 1e-10
+    X.zero_()
+    st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None, opts)
+    assert st in (richm.OK, richm.ERR_DIVERGED)
+    for sweeps, rel, status in info:
+        assert status in (richm.OK, richm.ERR_DIVERGED)
+        if status == richm.OK:
+            assert rel <= 1e-10

@@ -229,3 +229,43 @@ def test_autotune_picks_a_supported_pass_length():
     op = make_op(insts)
     fuse, ms = op.autotune(16, momentum=True)
     assert fuse in (1, 4, 8) and ms > 0
+
+
+@pytest.mark.parametrize("fuse", [4, 8])
+def test_bf16_state_fused_pass_matches_oracle(fuse):
+    # bfloat16 iterate, FP32 arithmetic and right-hand side: one pass from the same
+    # bf16-representable state is the FP32 result rounded once to bfloat16
+    sizes = [5, 63, 130, 255]
+    insts = _instances(sizes=sizes)
+    op = make_op(insts)
+    As = [assemble_q1(t.n, t.eps, t.theta) for t in insts]
+    G = np.array([gershgorin_max(A) for A in As])
+    m = 16
+    w, a = nag_weights(G, m, beta=0.3)
+    w = w.astype(np.float32).astype(np.float64)
+    a = a.astype(np.float32).astype(np.float64)
+    bf = lambda v: torch.tensor(v).to(torch.bfloat16).to(torch.float64).numpy()  # noqa: E731
+    x0 = [bf(0.5 * synth.rhs_uniform(31, i, t.n)) for i, t in enumerate(insts)]
+    xp0 = [bf(x - 0.02 * synth.rhs_uniform(32, i, t.n)) for i, (x, t) in enumerate(zip(x0, insts))]
+    bs = [synth.rhs_uniform(33, i, t.n).astype(np.float32).astype(np.float64) for i, t in enumerate(insts)]
+    X, XP = to_dev(op, x0, richm.BF16), to_dev(op, xp0, richm.BF16)
+    B = to_dev(op, bs, richm.F32)
+    op.apply_sweeps(richm.BF16, X, XP, B, coef(w, richm.F32), coef(a, richm.F32), None, K=fuse, m=m, k_start=3,
+                    fuse=fuse)
+    got = [g.astype(np.float64) for g in from_dev(op, X, richm.BF16)]
+    for i, t in enumerate(insts):
+        ref, _ = inner_steps(As[i], bs[i].ravel(), x0[i].ravel(), (x0[i] - xp0[i]).ravel(), w[i], a[i], K=fuse,
+                             k_start=3)
+        xmax = max(np.abs(ref).max(), 1.0)
+        bound = fp32_bound(w[i], a[i], None, G[i], 3, fuse, xmax, 1.0) + 2.0 ** -8 * np.abs(ref).max()
+        assert np.abs(got[i].ravel() - ref).max() <= bound
+
+
+def test_bf16_state_requires_fused_passes():
+    insts = _instances(sizes=[31])
+    op = make_op(insts)
+    X = op.zeros(richm.BF16)
+    B = op.zeros(richm.F32)
+    with pytest.raises(richm.RichmError) as ei:
+        op.apply_sweeps(richm.BF16, X, None, B, coef(np.ones((1, 4)), richm.F32), K=6, m=4, fuse=4)
+    assert ei.value.status == richm.ERR_UNSUPPORTED
