@@ -384,6 +384,18 @@ richm_status richm_fourier_correction(richm_operator* op, richm_dtype dtype, voi
 
 /* ------------------------------------------------------------------ misc */
 
+/* Self-test of the library's own FP32 <-> FP64 conversions (no counterpart in the
+ * paper: GB300 runs conversions to and from FP64 on its reduced-rate FP64 pipe, so
+ * the refinement residual and update move the IEEE 754 fields with integer
+ * operations instead). Compares them bit for bit with the hardware conversions:
+ * widening on all 2^32 binary32 inputs, round-to-nearest-even narrowing on every
+ * binary64 high word (sign, exponent, top 20 fraction bits) combined with eight low
+ * words at and around the rounding boundary (2^35 inputs). Writes the mismatch
+ * counts (widening, narrowing; 0 and 0 when correct) to host mismatches[2].
+ * Allocates 16 bytes of device memory, runs on the legacy default stream of the
+ * current device and blocks until done (tens of milliseconds on a GB300). */
+richm_status richm_selftest_conversions(long long* mismatches);
+
 /* Thread-local description of the last error ("" if none). */
 const char* richm_last_error(void);
 

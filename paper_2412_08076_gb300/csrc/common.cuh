@@ -160,6 +160,42 @@ template <typename E> __device__ inline E zero_e() { return E{}; }
 template <> __device__ inline float zero_e<float>() { return 0.f; }
 template <> __device__ inline double zero_e<double>() { return 0.0; }
 
+// binary32 <-> binary64 conversions by moving the IEEE 754 fields with integer
+// operations. GB300 runs FP64 instructions, conversions to and from FP64 included, at
+// a small fraction of its FP32 rate; these keep the FP64 pipe free for arithmetic.
+// Normal numbers (and zero for the widening) take the integer path, every other input
+// (subnormal, infinite, NaN, and narrowing results outside the binary32 normal range)
+// the hardware conversion, so both give the hardware's bits for every input.
+//
+// Widening is exact: exponent bias 127 -> 1023, the 23 fraction bits become the top
+// of the 52.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex - 1u < 254u) {
+    const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+
+// Narrowing rounds to nearest, ties to even: keep the top 23 of the 52 fraction
+// bits and add one unit when the 29 dropped bits exceed half a unit, or equal it and
+// the kept fraction is odd (a carry out of the fraction steps the exponent, which
+// also rounds FLT_MAX + half an ulp up to infinity as IEEE 754 does).
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex - 897u < 254u) {  // binary32 exponent ex - 896 in [1, 254]
+    unsigned bits = (hi & 0x80000000u) | ((ex - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u))) ? 1u : 0u;
+    return __uint_as_float(bits);
+  }
+  return (float)d;
+}
+
 template <typename E> __device__ inline double abs2_d(E v) { return (double)v * (double)v; }
 template <> __device__ inline double abs2_d<cplx<float>>(cplx<float> v) { return (double)v.re * v.re + (double)v.im * v.im; }
 template <> __device__ inline double abs2_d<cplx<double>>(cplx<double> v) { return v.re * v.re + v.im * v.im; }
@@ -221,6 +257,27 @@ __device__ inline void apply_q1(const RowT<E, VW>& U, const RowT<E, VW>& C, cons
     E dw = (e == 0) ? D.yl : D.y[e - 1];
     E de = (e == VW - 1) ? D.yr : D.y[e + 1];
     out[e] = c * C.y[e] + ax * (cw + ce) + ay * (U.y[e] + D.y[e]) + d1 * (de + uw) + d2 * (ue + dw);
+  }
+}
+
+// b - A y of the 9-point Q1 stencil (FP64) at the VW points of the centre row, with
+// b taken into the first fused multiply-add: four sums and five multiply-adds.
+template <int VW>
+__device__ inline void resid_q1(const RowT<double, VW>& U, const RowT<double, VW>& C, const RowT<double, VW>& D,
+                                const double* b, double c, double ax, double ay, double d1, double d2, double* out) {
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    const double cw = (e == 0) ? C.yl : C.y[e - 1];
+    const double ce = (e == VW - 1) ? C.yr : C.y[e + 1];
+    const double uw = (e == 0) ? U.yl : U.y[e - 1];
+    const double ue = (e == VW - 1) ? U.yr : U.y[e + 1];
+    const double dw = (e == 0) ? D.yl : D.y[e - 1];
+    const double de = (e == VW - 1) ? D.yr : D.y[e + 1];
+    double t = fma(-c, C.y[e], b[e]);
+    t = fma(-ax, cw + ce, t);
+    t = fma(-ay, U.y[e] + D.y[e], t);
+    t = fma(-d1, de + uw, t);
+    out[e] = fma(-d2, ue + dw, t);
   }
 }
 

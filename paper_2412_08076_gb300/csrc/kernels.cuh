@@ -42,10 +42,12 @@ richm_status launch_residual(richm_operator* op, const E* x, const E* b, E* r_ou
                              cudaStream_t s);
 
 // Residual of an FP64 state written in another type (the mixed-precision solver's
-// inner right-hand side); instances with active[b] == 0 are skipped.
+// inner right-hand side); instances with active[b] == 0 are skipped. With
+// `refinement` the partials hold (|r|^2, 0): the solver knows |b| from its first
+// residual and skips that sum.
 template <typename E, typename RO>
 richm_status launch_residual_to(richm_operator* op, const E* x, const E* b, RO* r_out, double2* partials,
-                                const int* active, cudaStream_t s);
+                                const int* active, cudaStream_t s, bool refinement);
 
 // Bytes of the loss workspace (residual buffer, partials, three per-instance arrays).
 size_t loss_workspace_bytes(richm_operator* op, size_t elem_size, int ntiles);

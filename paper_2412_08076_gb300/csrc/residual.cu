@@ -5,6 +5,7 @@
 // are summed in FP64: first per warp tile (written to a partials array), then per
 // instance by one warp in a fixed order, so results are bitwise reproducible.
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -16,18 +17,22 @@ template <> struct WideOf<cplx<float>> { using type = cplx<double>; };
 template <> struct WideOf<cplx<double>> { using type = cplx<double>; };
 
 template <typename ED, typename E> __device__ inline ED widen(E v) { return (ED)v; }
+template <> __device__ inline double widen<double, float>(float v) { return f32_to_f64_exact(v); }
 template <> __device__ inline cplx<double> widen<cplx<double>, cplx<float>>(cplx<float> v) {
-  return {(double)v.re, (double)v.im};
+  return {f32_to_f64_exact(v.re), f32_to_f64_exact(v.im)};
 }
 template <> __device__ inline cplx<double> widen<cplx<double>, cplx<double>>(cplx<double> v) { return v; }
 template <typename E, typename ED> __device__ inline E narrow(ED v) { return (E)v; }
+template <> __device__ inline float narrow<float, double>(double v) { return f64_to_f32_rn(v); }
 template <> __device__ inline cplx<float> narrow<cplx<float>, cplx<double>>(cplx<double> v) {
-  return {(float)v.re, (float)v.im};
+  return {f64_to_f32_rn(v.re), f64_to_f32_rn(v.im)};
 }
 template <> __device__ inline cplx<double> narrow<cplx<double>, cplx<double>>(cplx<double> v) { return v; }
 
 // MODE 0: residual (+ optional r_out) and partial sums (|r|^2, |b|^2).
 // MODE 1: out = scale_b * (A x) (used for the loss gradient), no partials.
+// MODE 2: the solver's refinement residual (real FP64 x and b): b folded into the
+//         stencil's multiply-adds and partial sums (|r|^2, 0), since |b| is known.
 template <typename E, int MODE, typename RO>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     resid_kernel(const Inst* insts, const Tile* tiles, int ntiles, const E* __restrict__ x,
@@ -48,7 +53,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int r0 = t.ty * kRows + 1;
   const int r1 = min(r0 + kRows - 1, n);
   const E* xb = x + I.off;
-  const E* bb = (MODE == 0) ? b + I.off : nullptr;
+  const E* bb = (MODE != 1) ? b + I.off : nullptr;
   RO* ob = r_out ? r_out + I.off : nullptr;
   const double sc = (MODE == 1) ? scale[t.inst] : 0.0;
 
@@ -80,7 +85,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       apply_q1<ED, VW, double>(U, C, D, I.c, I.ax, I.ay, I.d1, I.d2, Ax);
     }
     VecN<RO, VW> O;
-    if (MODE == 0) {
+    if constexpr (MODE == 2) {
+      static_assert(!CPLX, "the refinement residual is real");
+      VecN<E, VW> Bv{};
+      if (live) Bv = ldv<E, VW>(bb + (long long)r * pitch + c0);
+      double rv[VW];
+      resid_q1<VW>(U, C, D, Bv.v, I.c, I.ax, I.ay, I.d1, I.d2, rv);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const bool ok = (c0 + e) < n;
+        if (ok) sr = fma(rv[e], rv[e], sr);
+        O.v[e] = ok ? narrow<RO, ED>(rv[e]) : RO{};
+      }
+    } else if (MODE == 0) {
       VecN<E, VW> Bv{};
       if (live) Bv = ldv<E, VW>(bb + (long long)r * pitch + c0);
 #pragma unroll
@@ -105,7 +122,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     U = C;
     C = D;
   }
-  if (MODE == 0) {
+  if (MODE != 1) {
     sr = warp_sum(sr);
     sb = warp_sum(sb);
     if (lane == 0) partials[wt] = make_double2(sr, sb);
@@ -156,10 +173,18 @@ richm_status residual_tiles(richm_operator* op, int* ntiles) {
 
 template <typename E, typename RO>
 richm_status launch_residual_to(richm_operator* op, const E* x, const E* b, RO* r_out, double2* partials,
-                                const int* active, cudaStream_t s) {
+                                const int* active, cudaStream_t s, bool refinement) {
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 32 * VecWidth<E>::value, kRows, &tm));
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if constexpr (std::is_same<E, double>::value) {
+    if (refinement) {
+      resid_kernel<E, 2, RO><<<blocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, x, b,
+                                                                    r_out, partials, nullptr, active);
+      RICHM_LAUNCH_CHECK("refinement residual");
+      return RICHM_OK;
+    }
+  }
   resid_kernel<E, 0, RO><<<blocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, x, b, r_out,
                                                                 partials, nullptr, active);
   RICHM_LAUNCH_CHECK("residual");
@@ -169,13 +194,13 @@ richm_status launch_residual_to(richm_operator* op, const E* x, const E* b, RO* 
 template <typename E>
 richm_status launch_residual(richm_operator* op, const E* x, const E* b, E* r_out, double2* partials,
                              cudaStream_t s) {
-  return launch_residual_to<E, E>(op, x, b, r_out, partials, nullptr, s);
+  return launch_residual_to<E, E>(op, x, b, r_out, partials, nullptr, s, false);
 }
 
 template richm_status launch_residual_to<double, float>(richm_operator*, const double*, const double*, float*,
-                                                        double2*, const int*, cudaStream_t);
+                                                        double2*, const int*, cudaStream_t, bool);
 template richm_status launch_residual_to<double, double>(richm_operator*, const double*, const double*, double*,
-                                                         double2*, const int*, cudaStream_t);
+                                                         double2*, const int*, cudaStream_t, bool);
 
 template <typename E>
 static richm_status launch_scaled_apply(richm_operator* op, const E* x, E* out, const double* scale,

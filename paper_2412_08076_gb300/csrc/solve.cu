@@ -62,9 +62,9 @@ static size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 template <typename T> struct RhsOf { using type = float; };
 template <> struct RhsOf<double> { using type = double; };
 
-__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(float v) { return f32_to_f64_exact(v); }
 __device__ __forceinline__ double to_d(double v) { return v; }
-__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return f32_to_f64_exact(__bfloat162float(v)); }
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ double to_f(double v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -209,7 +209,7 @@ static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 
     RICHM_LAUNCH_CHECK("refine update");
   }
   if (!(init && x0_zero))
-    RICHM_TRY((launch_residual_to<double, R>(op, S->x, S->b, (R*)S->rhs, S->partials, S->active, S->s)));
+    RICHM_TRY((launch_residual_to<double, R>(op, S->x, S->b, (R*)S->rhs, S->partials, S->active, S->s, !init)));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->count, 0, sizeof(int), S->s));
   const int wpb = 8;
   solve_reduce_kernel<<<(op->batch + wpb - 1) / wpb, wpb * 32, 0, S->s>>>(
@@ -566,7 +566,7 @@ richm_status richm_refine(richm_operator* op, double* x, const double* b, void* 
           nullptr);
       RICHM_LAUNCH_CHECK("refine update");
     }
-    RICHM_TRY((launch_residual_to<double, float>(op, x, b, (float*)rhs_out, partials, nullptr, s)));
+    RICHM_TRY((launch_residual_to<double, float>(op, x, b, (float*)rhs_out, partials, nullptr, s, false)));
   } else {
     if (e) {
       refine_update_kernel<double><<<blocks, kWarpsPerBlock * 32, 0, s>>>(
@@ -574,7 +574,7 @@ richm_status richm_refine(richm_operator* op, double* x, const double* b, void* 
           (double*)e_prev, nullptr);
       RICHM_LAUNCH_CHECK("refine update");
     }
-    RICHM_TRY((launch_residual_to<double, double>(op, x, b, (double*)rhs_out, partials, nullptr, s)));
+    RICHM_TRY((launch_residual_to<double, double>(op, x, b, (double*)rhs_out, partials, nullptr, s, false)));
   }
   return launch_norm_reduce(op, 2, partials, nullptr, nullptr, rel, s);
 }

@@ -101,6 +101,7 @@ _SIGS = {
     "richm_adam_step": (_I, [_P, _P, _P, _P, _I, _I, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
     "richm_fourier_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_fourier_correction": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
+    "richm_selftest_conversions": (_I, [C.POINTER(C.c_longlong)]),
     "richm_last_error": (C.c_char_p, []),
     "richm_version": (C.c_char_p, []),
 }
@@ -149,6 +150,14 @@ def _stream(stream=None) -> int | None:
 
 def version() -> str:
     return load().richm_version().decode()
+
+
+def selftest_conversions() -> tuple[int, int]:
+    """richm_selftest_conversions: (widening, narrowing) mismatch counts against the
+    hardware FP32 <-> FP64 conversions; (0, 0) when the integer-field versions agree."""
+    out = (C.c_longlong * 2)()
+    _check(load().richm_selftest_conversions(out), "richm_selftest_conversions")
+    return int(out[0]), int(out[1])
 
 
 def chebyshev_weights(lmax: float, lmin: float, m: int) -> list[float]:

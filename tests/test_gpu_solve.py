@@ -83,6 +83,30 @@ def test_solve_to_1e10_checked_by_oracle(use_graph, fuse):
         assert abs(rel - r) <= 1e-3 * r + 1e-14
 
 
+@pytest.mark.parametrize("inner", [richm.F32, richm.F64])
+def test_refinement_residual_norm_matches_oracle(inner):
+    # tol = 0 stops every instance after max_sweeps; the reported relative residual is
+    # the solver's refinement residual (b folded into the FP64 stencil, |b| from the
+    # first residual) of the x it returns
+    insts, op, As, w, a, bs = _solve_setup([1, 5, 33, 64, 97, 130])
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    opts = op.solve_opts(16, tol=0.0, max_sweeps=128, refine_every=64, inner=inner, fuse=1 if inner == richm.F64 else 8)
+    st, info = op.solve(B, X, coef(w, inner), coef(a, inner), None, opts)
+    assert st == richm.ERR_NOT_CONVERGED
+    xs = from_dev(op, X, richm.F64)
+    for i, t in enumerate(insts):
+        r = np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i])
+        assert info[i][0] == 128
+        # both sides round b - A x in FP64 in different orders: an absolute difference of
+        # a few ulp of |b| + |A||x|, relative to |b| (instances that converged far)
+        assert abs(info[i][1] - r) <= 1e-12 * r + 1e-13, (t, info[i][1], r)
+
+
+def test_integer_field_conversions_match_hardware():
+    assert richm.selftest_conversions() == (0, 0)
+
+
 def test_solve_graph_and_plain_launches_agree_bitwise():
     res = []
     for g in (1, 0):
