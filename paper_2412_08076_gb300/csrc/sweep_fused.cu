@@ -15,7 +15,14 @@
 // Input rows are prefetched PF row steps ahead with cp.async into per-warp
 // shared-memory rings (each lane copies and later reads only its own 16 bytes, so no
 // barrier is needed), which keeps HBM latency out of the level pipeline; the b rows
-// stay in their ring until the last level has used them.
+// stay in their ring until the last level has used them. Each b row is copied into
+// two slots NB apart, so that every level reads its row at a fixed offset from the
+// step's slot, without wrapping.
+//
+// Nothing outside the domain needs clearing at any level: rows outside 1..n get the
+// weight 0 (their inputs are zero, so they stay zero), and the lanes' stencil
+// coefficients that couple to columns >= n are zero, so those columns (zero in every
+// input, b included) stay zero as well.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -69,9 +76,10 @@ template <typename ST, int TL>
 struct FusedRings {
   // one spare slot in each ring: a slot is re-targeted two row steps after its last read
   static constexpr int NS = kPrefetch + 2;       // x_k and x_{k-1} row slots
-  static constexpr int NB = TL + kPrefetch + 2;  // b row slots (kept until level TL)
+  static constexpr int NB = TL + kPrefetch + 2;  // b row slots (kept until level TL), each held twice
   static constexpr int XROW = 128 * (int)sizeof(ST);  // bytes of one state row (128 columns)
-  static constexpr int BYTES = 2 * NS * XROW + NB * 128 * 4;
+  static constexpr int BOFF = 2 * NS * XROW;          // start of the b ring
+  static constexpr int BYTES = BOFF + 2 * NB * 128 * 4;
 };
 
 // State storage: FP32, or bfloat16 (arithmetic stays FP32; values are rounded to
@@ -109,10 +117,26 @@ struct FusedCtx {
   unsigned char* ring;  // this warp's rings: x[NS] rows, xp[NS] rows (ST), b[NB] rows (float)
   int n, pitch, c0, lane, r0, r1, rlast;
   bool live, store_cols;
-  float sc, sax, say, sd1, sd2;
+  float sc, say;
+  float ax[4], d1[4], d2[4];  // per column of this lane: 0 for columns >= n
   float ml, mr;   // 0 where this lane's left / right neighbour lies beyond the warp, else 1
-  float cm[4];    // 1 for this lane's columns inside the domain, else 0
 };
+
+// A y of the 9-point Q1 stencil with per-column x-neighbour and corner coefficients.
+__device__ __forceinline__ void apply_q1_cols(const RowT<float, 4>& U, const RowT<float, 4>& C,
+                                              const RowT<float, 4>& D, float c, float ay, const float* ax,
+                                              const float* d1, const float* d2, float* out) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float cw = (e == 0) ? C.yl : C.y[e - 1];
+    const float ce = (e == 3) ? C.yr : C.y[e + 1];
+    const float uw = (e == 0) ? U.yl : U.y[e - 1];
+    const float ue = (e == 3) ? U.yr : U.y[e + 1];
+    const float dw = (e == 0) ? D.yl : D.y[e - 1];
+    const float de = (e == 3) ? D.yr : D.y[e + 1];
+    out[e] = c * C.y[e] + ax[e] * (cw + ce) + ay * (U.y[e] + D.y[e]) + d1[e] * (de + uw) + d2[e] * (ue + dw);
+  }
+}
 
 // Neighbours of a row from adjacent lanes; the warp's edge lanes get 0 (their
 // neighbour is either outside the domain, hence 0, or in the tile overlap, whose
@@ -155,7 +179,9 @@ __device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
   cp_async_state<ST>(c.ring + xs * R::XROW + c.lane * 4 * (int)sizeof(ST), c.xb + ro, valid);
   if (MOM)
     cp_async_state<ST>(c.ring + (R::NS + xs) * R::XROW + c.lane * 4 * (int)sizeof(ST), c.xpb + ro, valid);
-  cp_async16(c.ring + 2 * R::NS * R::XROW + ring_slot(r, R::NB) * 512 + c.lane * 16, c.bb + ro, valid);
+  unsigned char* bs = c.ring + R::BOFF + ring_slot(r, R::NB) * 512 + c.lane * 16;
+  cp_async16(bs, c.bb + ro, valid);
+  cp_async16(bs + R::NB * 512, c.bb + ro, valid);
   cp_async_commit();
 }
 
@@ -182,12 +208,15 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
   float newx[TL + 1][VW];
 #pragma unroll
   for (int e = 0; e < VW; ++e) newx[0][e] = x0[e];
+  // b row rr - s sits at slot (rr mod NB) + NB - s: one of its two copies, never wrapped
+  const unsigned char* bstep = c.ring + R::BOFF + (ring_slot(rr, R::NB) + R::NB) * 512 + c.lane * 16;
 #pragma unroll
   for (int s = 1; s <= TL; ++s) {
     const int row = rr - s;
-    const float4 B4 =
-        *reinterpret_cast<const float4*>(c.ring + 2 * R::NS * R::XROW + ring_slot(row, R::NB) * 512 + c.lane * 16);
+    const float4 B4 = *reinterpret_cast<const float4*>(bstep - s * 512);
     const float Bv[VW] = {B4.x, B4.y, B4.z, B4.w};
+    // rows outside 1..n keep their (zero) values: weight 0
+    const float ws = ((unsigned)(row - 1) < (unsigned)c.n) ? wl[s] : 0.f;
     // extend level s's window with row rr - s + 1 of y_{s-1}
     float* Yn = st.Y[s][SD];
     float vn[VW];
@@ -220,22 +249,16 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
       row_neighbours_m(YD, c.ml, c.mr);
     }
     float Ay[VW];
-    apply_q1<float, VW, float>(YU, YC, YD, c.sc, c.sax, c.say, c.sd1, c.sd2, Ay);
+    apply_q1_cols(YU, YC, YD, c.sc, c.say, c.ax, c.d1, c.d2, Ay);
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
-      float nx;
       if (!MOM || NAGF) {
-        nx = fmaf(wl[s], Bv[e] - Ay[e], YC.y[e]);  // NAG: y = x + a v is the window centre
+        newx[s][e] = fmaf(ws, Bv[e] - Ay[e], YC.y[e]);  // NAG: y = x + a v is the window centre
       } else {
-        nx = fmaf(wl[s], Bv[e] - Ay[e], fmaf(al[s], st.vc[s][e], st.xc[s][e]));
+        newx[s][e] = fmaf(ws, Bv[e] - Ay[e], fmaf(al[s], st.vc[s][e], st.xc[s][e]));
         st.xc[s][e] = newx[s - 1][e];
         st.vc[s][e] = vn[e];
       }
-      newx[s][e] = nx * c.cm[e];
-    }
-    if (row < 1 || row > c.n) {  // warp-uniform: rows outside the domain stay zero
-#pragma unroll
-      for (int e = 0; e < VW; ++e) newx[s][e] = 0.f;
     }
   }
   if (c.store_cols) {
@@ -277,17 +300,19 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   c.pitch = I.pitch;
   c.lane = lane;
   c.sc = (float)I.c;
-  c.sax = (float)I.ax;
   c.say = (float)I.ay;
-  c.sd1 = (float)I.d1;
-  c.sd2 = (float)I.d2;
   const int cs = t.tx * STRIDE;  // first column of the tile
   c.c0 = cs + lane * VW;         // this lane's first column
   c.live = c.c0 < c.pitch;
   c.ml = (lane == 0) ? 0.f : 1.f;
   c.mr = (lane == 31) ? 0.f : 1.f;
 #pragma unroll
-  for (int e = 0; e < VW; ++e) c.cm[e] = (c.c0 + e < c.n) ? 1.f : 0.f;
+  for (int e = 0; e < VW; ++e) {
+    const bool in = c.c0 + e < c.n;
+    c.ax[e] = in ? (float)I.ax : 0.f;
+    c.d1[e] = in ? (float)I.d1 : 0.f;
+    c.d2[e] = in ? (float)I.d2 : 0.f;
+  }
   const bool last_tile = (cs + 128 >= c.n);
   const int vlo = cs + (t.tx > 0 ? TL : 0);
   const int vhi = last_tile ? c.pitch : cs + 128 - TL;
@@ -315,8 +340,9 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
     for (int e = 0; e < VW; ++e) st.xc[s][e] = st.vc[s][e] = st.prevx[s][e] = 0.f;
   }
   // b rows above the tile's first input row are never loaded: zero their slots
-  for (int q = 0; q < FusedRings<ST, TL>::BYTES / 512; ++q)
-    *reinterpret_cast<float4*>(c.ring + q * 512 + lane * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = 0; q < 2 * FusedRings<ST, TL>::NB; ++q)
+    *reinterpret_cast<float4*>(c.ring + FusedRings<ST, TL>::BOFF + q * 512 + lane * 16) =
+        make_float4(0.f, 0.f, 0.f, 0.f);
   const int rstart = c.r0 - TL;
 #pragma unroll
   for (int d = 0; d < kPrefetch; ++d) issue_row<ST, TL, MOM>(c, rstart + d);
@@ -328,6 +354,33 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
     fused_step<ST, TL, MOM, NAGF, 2>(rr + 2, c, st, wl, al, atl);
   }
   cp_async_wait<0>();
+}
+
+template <typename ST, int TL>
+static cudaError_t fused_attributes_tl() {
+  const int bytes = FusedRings<ST, TL>::BYTES * kFuseWarps;
+  cudaError_t e = cudaSuccess;
+#define RICHM_FUSED_ATTR(MOM, PRE, NAGF)                                                                  \
+  if (e == cudaSuccess)                                                                                   \
+    e = cudaFuncSetAttribute(sweepT_kernel<ST, TL, MOM, PRE, NAGF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             bytes);
+  RICHM_FUSED_ATTR(true, true, true)
+  RICHM_FUSED_ATTR(true, false, true)
+  RICHM_FUSED_ATTR(true, true, false)
+  RICHM_FUSED_ATTR(true, false, false)
+  RICHM_FUSED_ATTR(false, true, false)
+  RICHM_FUSED_ATTR(false, false, false)
+#undef RICHM_FUSED_ATTR
+  return e;
+}
+
+// The fused kernels' rings can exceed the default 48 KB of dynamic shared memory.
+cudaError_t init_fused_attributes() {
+  cudaError_t e = fused_attributes_tl<float, 4>();
+  if (e == cudaSuccess) e = fused_attributes_tl<float, 8>();
+  if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 4>();
+  if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 8>();
+  return e;
 }
 
 template <typename ST>
