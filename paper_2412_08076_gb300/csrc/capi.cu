@@ -43,16 +43,19 @@ richm_status get_tiles(richm_operator* op, int tw, int rows, const TileMap** out
   for (int b = 0; b < op->batch; ++b) {
     tm.h_inst_begin[b] = (int)h.size();
     const Inst& I = op->h_inst[b];
-    int tx_n, ty_n;
+    const int ty_n = (I.n + rows - 1) / rows;
     if (tw > 0) {  // plain tiles of tw columns
-      tx_n = (I.pitch + tw - 1) / tw;
-    } else {  // fused tiles: 128 columns overlapping by 2*TL at interior edges
-      const int TL = -tw, stride = 128 - 2 * TL;
-      tx_n = 1 + (I.n > 128 ? (I.n - 128 + stride - 1) / stride : 0);
+      const int tx_n = (I.pitch + tw - 1) / tw;
+      for (int ty = 0; ty < ty_n; ++ty)
+        for (int tx = 0; tx < tx_n; ++tx) h.push_back(Tile{b, ty, tx, 0});
+    } else {  // fused tiles: 128 columns overlapping by 2*TL at interior edges, and a tail
+      int full = 0, half = 0;
+      fused_columns(I.n, -tw, &full, &half);
+      for (int ty = 0; ty < ty_n; ++ty)
+        for (int tx = 0; tx < full; ++tx) h.push_back(Tile{b, ty, tx, 0});
+      if (half)
+        for (int ty = 0; ty < ty_n; ty += 2) h.push_back(Tile{b, ty, full, ty + 1 < ty_n ? ty + 3 : 1});
     }
-    ty_n = (I.n + rows - 1) / rows;
-    for (int ty = 0; ty < ty_n; ++ty)
-      for (int tx = 0; tx < tx_n; ++tx) h.push_back(Tile{b, ty, tx, 0});
   }
   tm.h_inst_begin[op->batch] = (int)h.size();
   tm.ntiles = (int)h.size();

@@ -282,9 +282,8 @@ static int choose_rows(const richm_solver* S) {
     long long warps = 0;
     for (int b = 0; b < op->batch; ++b) {
       if (!S->h_count[1 + b]) continue;
-      const int n = op->h_inst[b].n, stride = 128 - 2 * TL;
-      const int tx = 1 + (n > 128 ? (n - 128 + stride - 1) / stride : 0);
-      warps += (long long)tx * ((n + rows - 1) / rows);
+      const int n = op->h_inst[b].n;
+      warps += fused_warps(n, TL, (n + rows - 1) / rows);
     }
     if (warps >= 0.9 * slots) return rows;
     best = rows;

@@ -115,7 +115,12 @@ struct FusedCtx {
   ST* ox;
   ST* oxp;
   unsigned char* ring;  // this warp's rings: x[NS] rows, xp[NS] rows (ST), b[NB] rows (float)
-  int n, pitch, c0, lane, r0, r1, rlast;
+  int n, pitch, c0, lane;
+  // Rows are counted in the frame of the tile's first row band (lanes 0-15 of a tail
+  // pair hold band ty, lanes 16-31 band pad - 2, whose pointers are shifted by the
+  // band offset): this lane's rows 1..n are rlo .. rlo + n - 1, its inputs are
+  // loaded up to row vhi and its results stored for rows r0 .. shi.
+  int rlo, vhi, r0, shi;
   bool live, store_cols;
   float sc, say;
   float ax[4], d1[4], d2[4];  // per column of this lane: 0 for columns >= n
@@ -173,7 +178,7 @@ __device__ __forceinline__ int ring_slot(int r, int nslots) { return (r + 64 * n
 template <typename ST, int TL, bool MOM>
 __device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
   using R = FusedRings<ST, TL>;
-  const bool valid = (r >= 1) && (r <= c.n) && (r <= c.rlast) && c.live;
+  const bool valid = ((unsigned)(r - c.rlo) <= (unsigned)(c.vhi - c.rlo)) && c.live;
   const long long ro = (long long)(valid ? r : 0) * c.pitch + (c.live ? c.c0 : 0);
   const int xs = ring_slot(r, R::NS);
   cp_async_state<ST>(c.ring + xs * R::XROW + c.lane * 4 * (int)sizeof(ST), c.xb + ro, valid);
@@ -216,7 +221,7 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
     const float4 B4 = *reinterpret_cast<const float4*>(bstep - s * 512);
     const float Bv[VW] = {B4.x, B4.y, B4.z, B4.w};
     // rows outside 1..n keep their (zero) values: weight 0
-    const float ws = ((unsigned)(row - 1) < (unsigned)c.n) ? wl[s] : 0.f;
+    const float ws = ((unsigned)(row - c.rlo) < (unsigned)c.n) ? wl[s] : 0.f;
     // extend level s's window with row rr - s + 1 of y_{s-1}
     float* Yn = st.Y[s][SD];
     float vn[VW];
@@ -263,8 +268,8 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
   }
   if (c.store_cols) {
     const int ra = rr - TL, rb = rr - TL + 1;
-    if (ra >= c.r0 && ra <= c.r1) float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, newx[TL]);
-    if (MOM && rb >= c.r0 && rb <= c.r1) float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, newx[TL - 1]);
+    if (ra >= c.r0 && ra <= c.shi) float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, newx[TL]);
+    if (MOM && rb >= c.r0 && rb <= c.shi) float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, newx[TL - 1]);
   }
   if (MOM) {
 #pragma unroll
@@ -301,11 +306,17 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   c.lane = lane;
   c.sc = (float)I.c;
   c.say = (float)I.ay;
-  const int cs = t.tx * STRIDE;  // first column of the tile
-  c.c0 = cs + lane * VW;         // this lane's first column
-  c.live = c.c0 < c.pitch;
-  c.ml = (lane == 0) ? 0.f : 1.f;
-  c.mr = (lane == 31) ? 0.f : 1.f;
+  // a tail pair: 16 lanes per 64-column tile, lanes 16-31 on row band pad - 2
+  const bool tail = t.pad > 0;
+  const int tlane = tail ? (lane & 15) : lane;
+  const bool idle = tail && lane >= 16 && t.pad == 1;
+  const int band = (tail && lane >= 16 && !idle) ? t.pad - 2 : t.ty;
+  const int dr = (band - t.ty) * A.rows;  // this lane's row offset from band ty
+  const int cs = t.tx * STRIDE;    // first column of the tile
+  c.c0 = cs + tlane * VW;          // this lane's first column
+  c.live = c.c0 < c.pitch && !idle;
+  c.ml = (tlane == 0) ? 0.f : 1.f;
+  c.mr = (tlane == (tail ? 15 : 31)) ? 0.f : 1.f;
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
     const bool in = c.c0 + e < c.n;
@@ -313,18 +324,26 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
     c.d1[e] = in ? (float)I.d1 : 0.f;
     c.d2[e] = in ? (float)I.d2 : 0.f;
   }
-  const bool last_tile = (cs + 128 >= c.n);
-  const int vlo = cs + (t.tx > 0 ? TL : 0);
-  const int vhi = last_tile ? c.pitch : cs + 128 - TL;
-  c.store_cols = c.live && c.c0 >= vlo && c.c0 + VW <= vhi;
+  const bool last_tile = tail || (cs + 128 >= c.n);
+  const int clo = cs + (t.tx > 0 ? TL : 0);
+  const int chi = last_tile ? c.pitch : cs + 128 - TL;
+  c.store_cols = c.live && c.c0 >= clo && c.c0 + VW <= chi;
   c.r0 = t.ty * A.rows + 1;
-  c.r1 = min(c.r0 + A.rows - 1, c.n);
-  c.rlast = c.r1 + TL;
-  c.xb = reinterpret_cast<const ST*>(A.x) + I.off;
-  c.xpb = reinterpret_cast<const ST*>(MOM ? A.xp : A.x) + I.off;
-  c.bb = A.b + I.off;
-  c.ox = reinterpret_cast<ST*>(A.out_x) + I.off;
-  c.oxp = MOM ? reinterpret_cast<ST*>(A.out_xp) + I.off : nullptr;
+  const int r1 = min(c.r0 + dr + A.rows - 1, c.n);  // this lane's last row (own frame)
+  c.rlo = 1 - dr;
+  c.vhi = min(r1 + TL, c.n) - dr;
+  c.shi = r1 - dr;
+  // the loop covers the longer of the two bands of a tail pair
+  const int endA = min(c.r0 + A.rows - 1, c.n) + TL;
+  const int endB = (tail && t.pad > 1) ? min((t.pad - 2) * A.rows + A.rows, c.n) + TL - (t.pad - 2 - t.ty) * A.rows
+                                       : endA;
+  const int rend = max(endA, endB);
+  const long long sh = (long long)dr * c.pitch;
+  c.xb = reinterpret_cast<const ST*>(A.x) + I.off + sh;
+  c.xpb = reinterpret_cast<const ST*>(MOM ? A.xp : A.x) + I.off + sh;
+  c.bb = A.b + I.off + sh;
+  c.ox = reinterpret_cast<ST*>(A.out_x) + I.off + sh;
+  c.oxp = MOM ? reinterpret_cast<ST*>(A.out_xp) + I.off + sh : nullptr;
   c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<ST, TL>::BYTES;
 
   FusedState<TL> st;
@@ -348,7 +367,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   for (int d = 0; d < kPrefetch; ++d) issue_row<ST, TL, MOM>(c, rstart + d);
   // rows r0-TL .. r1+TL in steps of three (a few extra steps at the end only
   // compute rows that are neither stored nor used)
-  for (int rr = rstart; rr <= c.r1 + TL; rr += 3) {
+  for (int rr = rstart; rr <= rend; rr += 3) {
     fused_step<ST, TL, MOM, NAGF, 0>(rr, c, st, wl, al, atl);
     fused_step<ST, TL, MOM, NAGF, 1>(rr + 1, c, st, wl, al, atl);
     fused_step<ST, TL, MOM, NAGF, 2>(rr + 2, c, st, wl, al, atl);

@@ -22,9 +22,11 @@ def _instances(seed=11, sizes=SIZES):
     return [synth.AnisoInstance(10 ** (-3 * u[2 * i]), math.pi * u[2 * i + 1], n) for i, n in enumerate(sizes)]
 
 
-def _run_case(dtype, variant, K, k_start=0, precond=0, sizes=SIZES, fuse=0):
+def _run_case(dtype, variant, K, k_start=0, precond=0, sizes=SIZES, fuse=0, rows=None):
     insts = _instances(sizes=sizes)
     op = make_op(insts)
+    if rows is not None:
+        op.set_tuning(fuse, rows)
     m = 6
     As = [assemble_q1(t.n, t.eps, t.theta) for t in insts]
     G = np.array([gershgorin_max(A) for A in As])
@@ -211,6 +213,23 @@ def test_fp32_fused_sweeps_match_oracle(fuse, variant):
         assert np.abs(g - ref).max() <= bound
         if gp is not None:
             assert np.abs(gp - refp).max() <= bound
+
+
+@pytest.mark.parametrize("fuse", [4, 8])
+@pytest.mark.parametrize("rows", [32, 64])
+def test_fused_tail_tiles_match_oracle(fuse, rows):
+    # sizes whose last column block is a 64-column tail tile (129..176 and 241..288
+    # columns at 8 sweeps per pass, 129..184 and 249..304 at 4), with an even and an
+    # odd number of row bands: tail tiles of two bands share a warp, an odd one out
+    # runs with idle lanes
+    sizes = [129, 150, 176, 241, 255, 288, 300, 511]
+    K, k_start = 2 * fuse, 1
+    for g, ref, gp, refp, w, a, at, G in _run_case(richm.F32, "nag", K=K, k_start=k_start, sizes=sizes, fuse=fuse,
+                                                   rows=rows):
+        xmax = max(np.abs(ref).max(), 1.0)
+        bound = _fp32_bound(w, a, at, G, k_start, K, xmax, 1.0)
+        assert np.abs(g - ref).max() <= bound
+        assert np.abs(gp - refp).max() <= bound
 
 
 @pytest.mark.parametrize("fuse", [4, 8])
