@@ -122,15 +122,16 @@ struct FusedCtx {
   // loaded up to row vhi and its results stored for rows r0 .. shi.
   int rlo, vhi, r0, shi;
   bool live, store_cols;
-  float sc, say;
-  float ax[4], d1[4], d2[4];  // per column of this lane: 0 for columns >= n
+  float nc, nay;                 // -c, -ay
+  float nax[4], nd1[4], nd2[4];  // -ax, -d1, -d2 per column of this lane: 0 for columns >= n
   float ml, mr;   // 0 where this lane's left / right neighbour lies beyond the warp, else 1
 };
 
-// A y of the 9-point Q1 stencil with per-column x-neighbour and corner coefficients.
-__device__ __forceinline__ void apply_q1_cols(const RowT<float, 4>& U, const RowT<float, 4>& C,
-                                              const RowT<float, 4>& D, float c, float ay, const float* ax,
-                                              const float* d1, const float* d2, float* out) {
+// b - A y of the 9-point Q1 stencil with per-column x-neighbour and corner
+// coefficients (passed negated): b enters the first of five multiply-adds.
+__device__ __forceinline__ void resid_q1_cols(const RowT<float, 4>& U, const RowT<float, 4>& C,
+                                              const RowT<float, 4>& D, const float* b, float nc, float nay,
+                                              const float* nax, const float* nd1, const float* nd2, float* out) {
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const float cw = (e == 0) ? C.yl : C.y[e - 1];
@@ -139,7 +140,11 @@ __device__ __forceinline__ void apply_q1_cols(const RowT<float, 4>& U, const Row
     const float ue = (e == 3) ? U.yr : U.y[e + 1];
     const float dw = (e == 0) ? D.yl : D.y[e - 1];
     const float de = (e == 3) ? D.yr : D.y[e + 1];
-    out[e] = c * C.y[e] + ax[e] * (cw + ce) + ay * (U.y[e] + D.y[e]) + d1[e] * (de + uw) + d2[e] * (ue + dw);
+    float t = fmaf(nc, C.y[e], b[e]);
+    t = fmaf(nax[e], cw + ce, t);
+    t = fmaf(nay, U.y[e] + D.y[e], t);
+    t = fmaf(nd1[e], de + uw, t);
+    out[e] = fmaf(nd2[e], ue + dw, t);
   }
 }
 
@@ -253,14 +258,14 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
       row_neighbours_m(YC, c.ml, c.mr);
       row_neighbours_m(YD, c.ml, c.mr);
     }
-    float Ay[VW];
-    apply_q1_cols(YU, YC, YD, c.sc, c.say, c.ax, c.d1, c.d2, Ay);
+    float ry[VW];
+    resid_q1_cols(YU, YC, YD, Bv, c.nc, c.nay, c.nax, c.nd1, c.nd2, ry);
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       if (!MOM || NAGF) {
-        newx[s][e] = fmaf(ws, Bv[e] - Ay[e], YC.y[e]);  // NAG: y = x + a v is the window centre
+        newx[s][e] = fmaf(ws, ry[e], YC.y[e]);  // NAG: y = x + a v is the window centre
       } else {
-        newx[s][e] = fmaf(ws, Bv[e] - Ay[e], fmaf(al[s], st.vc[s][e], st.xc[s][e]));
+        newx[s][e] = fmaf(ws, ry[e], fmaf(al[s], st.vc[s][e], st.xc[s][e]));
         st.xc[s][e] = newx[s - 1][e];
         st.vc[s][e] = vn[e];
       }
@@ -304,8 +309,8 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   c.n = I.n;
   c.pitch = I.pitch;
   c.lane = lane;
-  c.sc = (float)I.c;
-  c.say = (float)I.ay;
+  c.nc = -(float)I.c;
+  c.nay = -(float)I.ay;
   // a tail pair: 16 lanes per 64-column tile, lanes 16-31 on row band pad - 2
   const bool tail = t.pad > 0;
   const int tlane = tail ? (lane & 15) : lane;
@@ -320,9 +325,9 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
     const bool in = c.c0 + e < c.n;
-    c.ax[e] = in ? (float)I.ax : 0.f;
-    c.d1[e] = in ? (float)I.d1 : 0.f;
-    c.d2[e] = in ? (float)I.d2 : 0.f;
+    c.nax[e] = in ? -(float)I.ax : 0.f;
+    c.nd1[e] = in ? -(float)I.d1 : 0.f;
+    c.nd2[e] = in ? -(float)I.d2 : 0.f;
   }
   const bool last_tile = tail || (cs + 128 >= c.n);
   const int clo = cs + (t.tx > 0 ? TL : 0);
