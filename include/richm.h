@@ -184,7 +184,8 @@ richm_status richm_autotune(richm_operator* op, int m, int momentum, void* work,
 /* The operator's current pass length and fused tile height (host outputs, may be NULL). */
 richm_status richm_tuned(const richm_operator* op, int* fuse, int* rows);
 
-/* Set them without timing (fuse: 1, 4 or 8; rows: 32, 64, 128 or 256). Affects later calls. */
+/* Set them without timing (fuse: 1, 4 or 8; rows: a multiple of 16 from 16 to 256).
+ * Affects later calls. */
 richm_status richm_set_tuning(richm_operator* op, int fuse, int rows);
 
 /* ------------------------------------------------------------------ residual */
@@ -267,10 +268,11 @@ richm_status richm_solve(richm_operator* op, const double* b, double* x, const v
  * not NULL, waits and returns the number of instances still iterating;
  * richm_solver_finish waits for `stream` and fills info (host [batch]). x holds the
  * current FP64 iterate after every step. Instances that converged, diverged or
- * reached max_sweeps are skipped by later cycles. With fused sweeps, every step that
- * reports active_out also re-picks the fused tile height for the instances still
- * iterating (the operator's tuned height down to 32 rows, the largest whose tiles still
- * fill the GPU); the arithmetic per unknown does not depend on the tile height. */
+ * reached max_sweeps are skipped by later cycles. With fused sweeps, the start and
+ * every step that reports active_out pick the fused tile height for the instances
+ * still iterating (the operator's tuned height halved down to 16 rows, whichever a model of
+ * the pass's waves of blocks over the SMs estimates fastest); the arithmetic per
+ * unknown does not depend on the tile height. */
 typedef struct richm_solver richm_solver;
 richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* opts, const void* w, const void* alpha,
                                  const void* alpha_t, void* work, size_t work_bytes, richm_solver** out);

@@ -268,25 +268,47 @@ static richm_status cycle_t(richm_solver* S, long long k0) {
   }
 }
 
-// Fused tile height for the instances still iterating: the largest of the tuned
-// height, 128, 64, 32 whose warp tiles fill ~90 % of the block slots (152 SMs x the
-// kernel's blocks per SM x 4 warps); as instances converge the tiles get shorter so
-// the remaining work still spreads over the whole GPU.
-static int choose_rows(const richm_solver* S) {
+// Fused tile height (the tuned height halved down to 16 rows) for the instances
+// still iterating, from a wave model of the
+// fused pass: its warps form blocks of 4, which run in waves of 152 SMs x K
+// resident blocks (K = 2 at 8 sweeps per pass, 4 at 4, set by the registers); a
+// wave takes rows + 2 TL row steps, and a row step takes 1 + 0.65 (k - 1) times its
+// single-block time when k blocks share an SM (fitted to GB300 timings of both pass
+// lengths over 1..77 instances of 511^2 and the 256-instance mix, where it picks
+// within 1 % of the best height on average). Short tiles spread few instances over
+// the GPU at the price of more pipeline fill; tall tiles waste nothing on fill but
+// can leave most SMs idle or start a nearly empty extra wave.
+static double fused_pass_cost(const richm_solver* S, int rows) {
   const richm_operator* op = S->op;
   const int TL = S->o.fuse;
-  const double slots = 152.0 * (TL == 8 ? 2 : 4) * 4;
-  int best = 32;
-  for (int rows : {256, 128, 64, 32}) {
-    if (rows > S->rows_max) continue;
-    long long warps = 0;
-    for (int b = 0; b < op->batch; ++b) {
-      if (!S->h_count[1 + b]) continue;
-      const int n = op->h_inst[b].n;
-      warps += fused_warps(n, TL, (n + rows - 1) / rows);
+  const int K = TL == 8 ? 2 : 4;
+  long long warps = 0;
+  int nmax = 0;
+  for (int b = 0; b < op->batch; ++b) {
+    if (!S->h_count[1 + b]) continue;
+    const int n = op->h_inst[b].n;
+    warps += fused_warps(n, TL, (n + rows - 1) / rows);
+    nmax = std::max(nmax, n);
+  }
+  const long long blocks = (warps + 3) / 4;
+  const long long wave = 152LL * K;
+  const long long full = blocks / wave, rem = blocks % wave;
+  const double per_wave = 1.0 + 0.65 * (K - 1);
+  double cost = (double)full * per_wave;
+  if (rem > 0) cost += 1.0 + 0.65 * (double)((rem + 151) / 152 - 1);
+  const int steps = (std::min(rows, nmax) + 2 * TL + 3) / 3 * 3;
+  return cost * steps;
+}
+
+static int choose_rows(const richm_solver* S) {
+  int best = S->rows_max;
+  double best_cost = -1.0;
+  for (int rows = S->rows_max; rows >= 16; rows /= 2) {
+    const double c = fused_pass_cost(S, rows);
+    if (best_cost < 0.0 || c < best_cost) {
+      best_cost = c;
+      best = rows;
     }
-    if (warps >= 0.9 * slots) return rows;
-    best = rows;
   }
   return best;
 }
@@ -408,8 +430,7 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   if (st == RICHM_OK) st = get_tiles(op, o->inner == RICHM_F64 ? 64 : 128, kRows, &tm);
   S->rows_max = S->rows_now = op->best_rows;
   if (S->o.fuse > 1)
-    for (int rows : {256, 128, 64, 32})
-      if (st == RICHM_OK && rows <= S->rows_max) st = get_tiles(op, -S->o.fuse, rows, &tm);
+    for (int rows = S->rows_max; rows >= 16 && st == RICHM_OK; rows /= 2) st = get_tiles(op, -S->o.fuse, rows, &tm);
   if (st != RICHM_OK) {
     richm_solver_destroy(S);
     return st;
@@ -440,6 +461,10 @@ static richm_status solver_start_impl(richm_solver* S, const double* b, double* 
   S->x = x;
   S->cycles_run = 0;
   S->rows_now = S->rows_max;
+  if (S->o.fuse > 1) {
+    for (int b = 0; b < op->batch; ++b) S->h_count[1 + b] = 1;
+    S->rows_now = choose_rows(S);
+  }
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, (cudaStream_t)stream));
   RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
   const size_t es = S->o.inner == RICHM_F64 ? 8 : (S->o.inner == RICHM_F32 ? 4 : 2);

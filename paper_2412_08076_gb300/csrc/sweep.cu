@@ -404,7 +404,7 @@ richm_status richm_set_tuning(richm_operator* op, int fuse, int rows) {
   clear_error();
   RICHM_ARG(op != nullptr, "null operator");
   RICHM_ARG(fuse == 1 || fuse == 4 || fuse == 8, "fuse must be 1, 4 or 8");
-  RICHM_ARG(rows == 32 || rows == 64 || rows == 128 || rows == 256, "rows must be 32, 64, 128 or 256");
+  RICHM_ARG(rows >= 16 && rows <= 256 && rows % 16 == 0, "rows must be a multiple of 16 from 16 to 256");
   op->best_fuse = fuse;
   op->best_rows = rows;
   return RICHM_OK;
