@@ -240,6 +240,10 @@ typedef struct {
   int status;        /* RICHM_OK, RICHM_ERR_NOT_CONVERGED or RICHM_ERR_DIVERGED */
 } richm_solve_info;
 
+/* Workspace bytes of richm_solve / richm_solver_create: four inner-state buffers, the
+ * inner right-hand side, per-tile partial sums, per-instance arrays and, for an FP32 or
+ * bfloat16 inner state, a second padded FP64 solution buffer (fused cycles alternate
+ * between it and x). */
 richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_opts* opts, size_t* bytes);
 
 /* Solve every instance of a Q1 batch to tolerance ("iterate until a tolerance or the
@@ -259,15 +263,18 @@ richm_status richm_solve(richm_operator* op, const double* b, double* x, const v
 /* Session form of richm_solve for callers that drive the refinement cycles
  * themselves (progress reporting, fixed-cycle timing, resuming). The handle keeps
  * pointers to the caller's weights and workspace (which must stay valid until
- * richm_solver_destroy) and owns a CUDA stream, two events, a pinned 4-byte host
- * word and, once a step has run with use_graph, the instantiated graph of one
- * cycle. richm_solver_start binds b and x, zeroes the inner state and evaluates
- * the initial residual; richm_solver_step runs `cycles` refinement cycles (each:
- * refine_every sweeps, the FP64 update, the FP64 residual and the per-instance
+ * richm_solver_destroy) and owns a CUDA stream, two events, pinned host words for the
+ * active count and flags and, once steps have run with use_graph, the instantiated
+ * graphs of a cycle. richm_solver_start binds b and x, zeroes the inner state and
+ * evaluates the initial residual; richm_solver_step runs `cycles` refinement cycles
+ * (each: refine_every sweeps, the FP64 update, the FP64 residual and the per-instance
  * test) ordered after the work already queued on `stream`, and, when active_out is
  * not NULL, waits and returns the number of instances still iterating;
- * richm_solver_finish waits for `stream` and fills info (host [batch]). x holds the
- * current FP64 iterate after every step. Instances that converged, diverged or
+ * richm_solver_finish waits for `stream`, fills info (host [batch]) and leaves the
+ * current FP64 iterate of every instance in x. Between steps, fused cycles may hold the
+ * newest iterate of an instance in the workspace's second FP64 buffer: call
+ * richm_solver_finish (it may be called between steps as well) before reading x.
+ * Without fused cycles x is current after every step. Instances that converged, diverged or
  * reached max_sweeps are skipped by later cycles. With fused sweeps, the start and
  * every step that reports active_out pick the fused tile height for the instances
  * still iterating (the operator's tuned height halved down to 16 rows, whichever a model of

@@ -25,16 +25,20 @@ richm_status launch_sweep(richm_operator* op, const E* x, const E* xp, const E* 
 // TL (4 or 8) fused FP32 sweeps of a real Q1 batch: reads (x_k, x_{k-1}) from
 // (x, xp), writes (x_{k+TL}, x_{k+TL-1}) to (out_x, out_xp); the outputs must not
 // alias the inputs. kidx0 = coefficient index of the first sweep.
-// rows: output rows of a warp tile (64, 128 or 256); <= 0 takes the operator's tuned value.
+// rows: output rows of a warp tile (a multiple of 16 up to 256); <= 0 takes the operator's
+// tuned value. absorb: the input pair (x, xp) stands for (0, xp - x), the state after
+// the mixed-precision refinement moved x into the FP64 solution (the solver's first
+// pass of a cycle).
 richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
                                 float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
-                                int kidx0, int precond, const int* active, cudaStream_t s, int rows = 0);
+                                int kidx0, int precond, const int* active, cudaStream_t s, int rows = 0,
+                                bool absorb = false);
 
 // The same with bfloat16 state (x, x_prev and the outputs); b and the arithmetic are FP32.
 richm_status launch_sweep_fused_bf16(richm_operator* op, int TL, const __nv_bfloat16* x, const __nv_bfloat16* xp,
                                      const float* b, __nv_bfloat16* out_x, __nv_bfloat16* out_xp, const float* w,
                                      const float* a, const float* at, int m, int kidx0, int precond,
-                                     const int* active, cudaStream_t s, int rows = 0);
+                                     const int* active, cudaStream_t s, int rows = 0, bool absorb = false);
 
 // r = b - A x in FP64 with per-tile partial sums (sum |r|^2, sum |b|^2) written to
 // `partials` (one double2 per warp tile of the residual geometry); r_out may be null.

@@ -4,14 +4,24 @@
 // State per instance: x (FP64, the caller's buffer), the inner correction pair
 // (e_k, e_{k-1}) in the inner type, and the inner right-hand side rhs. One
 // refinement cycle is
-//   S sweeps of the Table 1 iteration on A e = rhs       (three rotating buffers)
-//   update  x += e_k;  e_{k-1} <- e_{k-1} - e_k;  e_k <- 0  (pointwise, FP64 add)
+//   S sweeps of the Table 1 iteration on A e = rhs
+//   update  x += e_k;  e_{k-1} <- e_{k-1} - e_k;  e_k <- 0  (FP64 add)
 //   rhs = b - A x in FP64 (written in the inner type) and its squared norm
 //   per-instance convergence test; converged instances leave the active set
 // The update keeps the inner velocity e_k - e_{k-1} and the weight index, so the
-// split is the same affine iteration as sweeping x directly. The update writes the
-// pair back into the first two buffers, so every cycle has identical launches and
-// is captured once as a CUDA graph (one per fused tile height: as instances
+// split is the same affine iteration as sweeping x directly.
+//
+// With fused sweeps (FP32 or bfloat16 state) the update costs no pass of its own:
+// the refinement kernel forms x + e_k on the fly, writes it to the other of two
+// FP64 buffers (the caller's x and one in the workspace, alternating by cycle) and
+// takes its residual; the stored pair (e_k, e_{k-1}) is left as it is and the next
+// cycle's first fused pass reads it as (0, e_{k-1} - e_k). richm_solver_finish copies
+// the solution of every instance whose last cycle wrote the workspace buffer back to
+// x. Otherwise (one sweep per launch, or FP64 state) a pointwise kernel applies the
+// update in place before the residual.
+//
+// A cycle's launches depend only on the fused tile height and on the parity of the
+// cycle index; each such cycle is captured once as a CUDA graph (as instances
 // converge, shorter tiles keep the remaining work spread over the GPU).
 #include <algorithm>
 #include <cmath>
@@ -38,13 +48,15 @@ struct richm_solver {
   int* status = nullptr;
   int* active = nullptr;
   int* count = nullptr;
+  double* x2 = nullptr;  // second FP64 solution buffer (fused cycles)
+  int* xloc = nullptr;   // [batch]: 1 where an instance's newest x is in x2
   // bound by richm_solver_start
   const double* b = nullptr;
   double* x = nullptr;
   // execution
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  std::map<int, cudaGraphExec_t> execs;  // one captured cycle per fused tile height
+  std::map<int, cudaGraphExec_t> execs;  // captured cycles by fused tile height and cycle parity
   int graph_cycles = 1;      // cycles captured in one graph replay
   long long cycles_run = 0;  // cycles since start
   int* h_count = nullptr;    // pinned: [0] active count, [1 .. batch] per-instance active flags
@@ -111,15 +123,112 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
-// Per-instance convergence bookkeeping after a refinement residual.
+// Refinement after a fused cycle: for the tile's rows, x_out = x_in + e (FP64; e is
+// the cycle's final correction, read here and left in place) and
+// rhs = b - A (x_in + e) in FP64 (b folded into the multiply-adds, the sum formed on
+// the fly for the halo rows too), with the tile's partial sum (|r|^2, 0).
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    refine_fused_kernel(const Inst* insts, const Tile* tiles, int ntiles, const double* __restrict__ x_in,
+                        const T* __restrict__ e, const double* __restrict__ b, float* __restrict__ rhs,
+                        double* __restrict__ x_out, double2* __restrict__ partials, const int* __restrict__ active) {
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile t = tiles[wt];
+  if (active[t.inst] == 0) return;
+  const Inst& I = insts[t.inst];
+  const int n = I.n, pitch = I.pitch;
+  const int c0 = t.tx * 64 + lane * 2;  // two doubles per lane
+  const bool live = c0 < pitch;
+  const int r0 = t.ty * kRows + 1;
+  const int r1 = min(r0 + kRows - 1, n);
+  const double* xb = x_in + I.off;
+  const T* eb = e + I.off;
+  auto load = [&](int pr, RowT<double, 2>& Y) {
+    const bool in = (pr >= 1) && (pr <= n);
+    const long long ro = (long long)pr * pitch;
+    double2 xv = make_double2(0.0, 0.0);
+    VecN<T, 2> ev;
+    ev.v[0] = ev.v[1] = from_f<T>(0.f);
+    if (in && live) {
+      xv = *reinterpret_cast<const double2*>(xb + ro + c0);
+      ev = *reinterpret_cast<const VecN<T, 2>*>(eb + ro + c0);
+    }
+    Y.y[0] = xv.x + to_d(ev.v[0]);
+    Y.y[1] = xv.y + to_d(ev.v[1]);
+    double le = 0.0, re = 0.0;
+    if (in) {
+      if (lane == 0 && c0 > 0) le = xb[ro + c0 - 1] + to_d(eb[ro + c0 - 1]);
+      if (lane == 31 && c0 + 2 < pitch) re = xb[ro + c0 + 2] + to_d(eb[ro + c0 + 2]);
+    }
+    row_neighbours<double, 2>(Y, lane, le, re);
+  };
+  double sr = 0.0;
+  RowT<double, 2> U, C, D;
+  load(r0 - 1, U);
+  load(r0, C);
+  for (int r = r0; r <= r1; ++r) {
+    load(r + 1, D);
+    const long long o = I.off + (long long)r * pitch + c0;
+    double2 bv = make_double2(0.0, 0.0);
+    if (live) bv = *reinterpret_cast<const double2*>(b + o);
+    const double bb[2] = {bv.x, bv.y};
+    double rv[2];
+    resid_q1<2>(U, C, D, bb, I.c, I.ax, I.ay, I.d1, I.d2, rv);
+    float2 out;
+    const bool ok0 = c0 < n, ok1 = c0 + 1 < n;
+    if (ok0) sr = fma(rv[0], rv[0], sr);
+    if (ok1) sr = fma(rv[1], rv[1], sr);
+    out.x = ok0 ? f64_to_f32_rn(rv[0]) : 0.f;
+    out.y = ok1 ? f64_to_f32_rn(rv[1]) : 0.f;
+    if (live) {
+      *reinterpret_cast<float2*>(rhs + o) = out;
+      *reinterpret_cast<double2*>(x_out + o) = make_double2(C.y[0], C.y[1]);
+    }
+    U = C;
+    C = D;
+  }
+  sr = warp_sum(sr);
+  if (lane == 0) partials[wt] = make_double2(sr, 0.0);
+}
+
+// x <- x2 for the instances whose newest solution is in x2 (xloc[b] == 1).
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    solution_gather_kernel(const Inst* insts, const Tile* tiles, int ntiles, const double* __restrict__ x2,
+                           double* __restrict__ x, const int* __restrict__ xloc) {
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile t = tiles[wt];
+  if (xloc[t.inst] == 0) return;
+  const Inst& I = insts[t.inst];
+  const int c0 = t.tx * 64 + lane * 2;
+  if (c0 >= I.pitch) return;
+  const int r0 = t.ty * kRows + 1;
+  const int r1 = min(r0 + kRows - 1, I.n);
+  for (int r = r0; r <= r1; ++r) {
+    const long long o = I.off + (long long)r * I.pitch + c0;
+    *reinterpret_cast<double2*>(x + o) = *reinterpret_cast<const double2*>(x2 + o);
+  }
+}
+
+__global__ void clear_ints_kernel(int* v, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) v[i] = 0;
+}
+
+// Per-instance convergence bookkeeping after a refinement residual; xpar >= 0 records
+// where the cycle wrote the solution of the instances that took part (1: x2).
 __global__ void solve_reduce_kernel(const double2* __restrict__ partials, const int* __restrict__ inst_begin,
                                     int batch, int init, int add_sweeps, double tol, long long max_sweeps,
                                     double* bnorm, double* rel, long long* sweeps, int* status, int* active,
-                                    int* count) {
+                                    int* count, int xpar, int* xloc) {
   const int lane = threadIdx.x & 31;
   const int bi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (bi >= batch) return;
   if (active[bi] == 0) return;
+  if (lane == 0 && xpar >= 0) xloc[bi] = xpar;
   double sr = 0.0, sb = 0.0;
   for (int t = inst_begin[bi] + lane; t < inst_begin[bi + 1]; t += 32) {
     double2 p = partials[t];
@@ -180,79 +289,107 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   if (lane == 0) partials[wt] = make_double2(sb, sb);
 }
 
-__global__ void solve_init_kernel(int batch, long long* sweeps, int* status, int* active) {
+__global__ void solve_init_kernel(int batch, long long* sweeps, int* status, int* active, int* xloc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < batch) {
     sweeps[i] = 0;
     status[i] = RICHM_ERR_NOT_CONVERGED;
     active[i] = 1;
+    xloc[i] = 0;
   }
 }
 
+// Fused cycles keep the solution in two FP64 buffers, alternating by cycle.
+static bool fused_cycles(const richm_solver* S) {
+  return S->o.fuse > 1 && (S->o.inner == RICHM_F32 || S->o.inner == RICHM_BF16);
+}
+
+// Refinement closing cycle number `cycle` (ignored for init), whose final pair is
+// (E[cur], E[prv]).
 template <typename T>
-static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 1, bool x0_zero = false) {
+static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 1, bool x0_zero = false,
+                             long long cycle = 0) {
   using R = typename RhsOf<T>::type;
   richm_operator* op = S->op;
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 64, kRows, &tm));  // residual / update geometry of FP64
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int xpar = -1;
   if (init && x0_zero) {
     zero_start_kernel<R><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(op->d_inst, tm->d_tiles, tm->ntiles, S->b,
                                                                    (R*)S->rhs, S->partials);
     RICHM_LAUNCH_CHECK("zero start");
   }
-  if (!init) {
-    // pointwise, so the new pair may overwrite the buffers it reads
-    refine_update_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(
-        op->d_inst, tm->d_tiles, tm->ntiles, S->x, (const T*)S->E[cur], (const T*)S->E[prv], (T*)S->E[0],
-        (T*)S->E[1], S->active);
-    RICHM_LAUNCH_CHECK("refine update");
+  if constexpr (!std::is_same<T, double>::value) {
+    if (!init && fused_cycles(S)) {
+      xpar = (int)((cycle + 1) & 1);
+      double* xin = (cycle & 1) ? S->x2 : S->x;
+      double* xout = xpar ? S->x2 : S->x;
+      refine_fused_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(op->d_inst, tm->d_tiles, tm->ntiles, xin,
+                                                                        (const T*)S->E[cur], S->b, (float*)S->rhs,
+                                                                        xout, S->partials, S->active);
+      RICHM_LAUNCH_CHECK("fused refinement");
+    }
   }
-  if (!(init && x0_zero))
-    RICHM_TRY((launch_residual_to<double, R>(op, S->x, S->b, (R*)S->rhs, S->partials, S->active, S->s, !init)));
+  if (xpar < 0) {
+    if (!init) {
+      // pointwise, so the new pair may overwrite the buffers it reads
+      refine_update_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(
+          op->d_inst, tm->d_tiles, tm->ntiles, S->x, (const T*)S->E[cur], (const T*)S->E[prv], (T*)S->E[0],
+          (T*)S->E[1], S->active);
+      RICHM_LAUNCH_CHECK("refine update");
+    }
+    if (!(init && x0_zero))
+      RICHM_TRY((launch_residual_to<double, R>(op, S->x, S->b, (R*)S->rhs, S->partials, S->active, S->s, !init)));
+  }
   RICHM_CUDA_TRY(cudaMemsetAsync(S->count, 0, sizeof(int), S->s));
   const int wpb = 8;
   solve_reduce_kernel<<<(op->batch + wpb - 1) / wpb, wpb * 32, 0, S->s>>>(
       S->partials, tm->d_inst_begin, op->batch, init ? 1 : 0, init ? 0 : S->o.refine_every, S->o.tol,
-      S->o.max_sweeps, S->bnorm, S->rel, S->sweeps, S->status, S->active, S->count);
+      S->o.max_sweeps, S->bnorm, S->rel, S->sweeps, S->status, S->active, S->count, xpar, S->xloc);
   RICHM_LAUNCH_CHECK("solve reduce");
   return RICHM_OK;
 }
 
 // One refinement cycle starting at global sweep index k0.
+// One refinement cycle (number `cycle`) starting at global sweep index k0.
 template <typename T>
-static richm_status cycle_t(richm_solver* S, long long k0) {
+static richm_status cycle_t(richm_solver* S, long long k0, long long cycle) {
   const int Sw = S->o.refine_every;
   int cur = 0, prv = 1;
-  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-    const int TL = S->o.fuse;
-    for (int k = 0; k < Sw; k += TL) {
-      const int oc = cur == 0 ? 2 : 0, op_ = cur == 0 ? 3 : 1;
-      RICHM_TRY(launch_sweep_fused_bf16(S->op, TL, (const T*)S->E[cur], (const T*)S->E[prv], (const float*)S->rhs,
-                                        (T*)S->E[oc], (T*)S->E[op_], (const float*)S->w, (const float*)S->a,
-                                        (const float*)S->at, S->o.m, (int)((k0 + k) % S->o.m), S->o.precond,
-                                        S->active, S->s, S->rows_now));
-      cur = oc;
-      prv = op_;
-    }
-    return refine_t<T>(S, false, cur, prv);
-  } else {
-  if constexpr (std::is_same<T, float>::value) {
-    if (S->o.fuse == 4 || S->o.fuse == 8) {
-      // temporally blocked passes alternate between the pairs (E0, E1) and (E2, E3)
+  if constexpr (!std::is_same<T, double>::value) {
+    if (fused_cycles(S)) {
+      // temporally blocked passes alternate between the pairs (E0, E1) and (E2, E3);
+      // a cycle starts on the pair the previous one ended on, which its first pass
+      // absorbs (see the file comment)
       const int TL = S->o.fuse;
+      const long long passes = Sw / TL;
+      if ((cycle * passes) & 1) cur = 2, prv = 3;
       for (int k = 0; k < Sw; k += TL) {
         const int oc = cur == 0 ? 2 : 0, op_ = cur == 0 ? 3 : 1;
-        RICHM_TRY(launch_sweep_fused(S->op, TL, (const float*)S->E[cur], (const float*)S->E[prv],
-                                     (const float*)S->rhs, (float*)S->E[oc], (float*)S->E[op_],
-                                     (const float*)S->w, (const float*)S->a, (const float*)S->at, S->o.m,
-                                     (int)((k0 + k) % S->o.m), S->o.precond, S->active, S->s, S->rows_now));
+        const bool absorb = k == 0;
+        if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+          RICHM_TRY(launch_sweep_fused_bf16(S->op, TL, (const T*)S->E[cur], (const T*)S->E[prv],
+                                            (const float*)S->rhs, (T*)S->E[oc], (T*)S->E[op_], (const float*)S->w,
+                                            (const float*)S->a, (const float*)S->at, S->o.m,
+                                            (int)((k0 + k) % S->o.m), S->o.precond, S->active, S->s, S->rows_now,
+                                            absorb));
+        } else {
+          RICHM_TRY(launch_sweep_fused(S->op, TL, (const float*)S->E[cur], (const float*)S->E[prv],
+                                       (const float*)S->rhs, (float*)S->E[oc], (float*)S->E[op_],
+                                       (const float*)S->w, (const float*)S->a, (const float*)S->at, S->o.m,
+                                       (int)((k0 + k) % S->o.m), S->o.precond, S->active, S->s, S->rows_now,
+                                       absorb));
+        }
         cur = oc;
         prv = op_;
       }
-      return refine_t<T>(S, false, cur, prv);
+      return refine_t<T>(S, false, cur, prv, false, cycle);
     }
   }
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    return set_error(RICHM_ERR_UNSUPPORTED, "bfloat16 inner state needs fused sweeps");
+  } else {
   int fre = 2;
   for (int k = 0; k < Sw; ++k) {
     const int kidx = (int)((k0 + k) % S->o.m);
@@ -315,10 +452,11 @@ static int choose_rows(const richm_solver* S) {
 
 static richm_status run_cycles(richm_solver* S, int cycles) {
   for (int c = 0; c < cycles; ++c) {
-    const long long k0 = (S->cycles_run + c) * (long long)S->o.refine_every;
-    if (S->o.inner == RICHM_F32) RICHM_TRY(cycle_t<float>(S, k0));
-    else if (S->o.inner == RICHM_BF16) RICHM_TRY(cycle_t<__nv_bfloat16>(S, k0));
-    else RICHM_TRY(cycle_t<double>(S, k0));
+    const long long cyc = S->cycles_run + c;
+    const long long k0 = cyc * (long long)S->o.refine_every;
+    if (S->o.inner == RICHM_F32) RICHM_TRY(cycle_t<float>(S, k0, cyc));
+    else if (S->o.inner == RICHM_BF16) RICHM_TRY(cycle_t<__nv_bfloat16>(S, k0, cyc));
+    else RICHM_TRY(cycle_t<double>(S, k0, cyc));
   }
   return RICHM_OK;
 }
@@ -362,8 +500,9 @@ richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_o
   int nt = 0;
   RICHM_TRY(residual_tiles<double>(const_cast<richm_operator*>(op), &nt));
   size_t B = (size_t)op->batch;
+  const size_t x2 = o->inner == RICHM_F64 ? 0 : a256(op->elems * sizeof(double));  // fused cycles' second x
   *bytes = 4 * a256(op->elems * es) + a256(op->elems * rs) + a256(sizeof(double2) * nt) + 2 * a256(sizeof(double) * B) +
-           a256(sizeof(long long) * B) + 2 * a256(sizeof(int) * B) + a256(sizeof(int));
+           a256(sizeof(long long) * B) + 3 * a256(sizeof(int) * B) + a256(sizeof(int)) + x2;
   return RICHM_OK;
 }
 
@@ -413,7 +552,11 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   p += a256(sizeof(int) * B);
   S->active = reinterpret_cast<int*>(p);
   p += a256(sizeof(int) * B);
+  S->xloc = reinterpret_cast<int*>(p);
+  p += a256(sizeof(int) * B);
   S->count = reinterpret_cast<int*>(p);
+  p += a256(sizeof(int));
+  if (o->inner != RICHM_F64) S->x2 = reinterpret_cast<double*>(p);
   // the weight phase repeats every m / gcd(S, m) cycles: one graph replay covers them
   S->graph_cycles = o->m / std::gcd(o->m, o->refine_every);
   cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
@@ -472,8 +615,10 @@ static richm_status solver_start_impl(richm_solver* S, const double* b, double* 
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[1], 0, op->elems * es, S->s));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[2], 0, op->elems * es, S->s));
   RICHM_CUDA_TRY(cudaMemsetAsync(S->E[3], 0, op->elems * es, S->s));
-  solve_init_kernel<<<(op->batch + 255) / 256, 256, 0, S->s>>>(op->batch, S->sweeps, S->status, S->active);
+  solve_init_kernel<<<(op->batch + 255) / 256, 256, 0, S->s>>>(op->batch, S->sweeps, S->status, S->active,
+                                                                  S->xloc);
   RICHM_LAUNCH_CHECK("solve init");
+  if (fused_cycles(S)) RICHM_CUDA_TRY(cudaMemsetAsync(S->x2, 0, op->elems * sizeof(double), S->s));
   if (x0_zero) RICHM_CUDA_TRY(cudaMemsetAsync(x, 0, op->elems * sizeof(double), S->s));
   if (S->o.inner == RICHM_F32) RICHM_TRY(refine_t<float>(S, true, 0, 1, x0_zero));
   else if (S->o.inner == RICHM_BF16) RICHM_TRY(refine_t<__nv_bfloat16>(S, true, 0, 1, x0_zero));
@@ -502,25 +647,28 @@ richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, voi
   const int G = S->graph_cycles;
   int done = 0;
   if (S->o.use_graph) {
-    // replays cover whole weight periods; a remainder runs as plain launches
-    auto it = S->execs.find(S->rows_now);
-    if (it == S->execs.end() && cycles >= G && S->cycles_run % G == 0) {
-      cudaGraph_t g = nullptr;
-      RICHM_CUDA_TRY(cudaStreamBeginCapture(S->s, cudaStreamCaptureModeThreadLocal));
-      richm_status st = run_cycles(S, G);
-      cudaError_t e = cudaStreamEndCapture(S->s, &g);
-      if (st != RICHM_OK) {
-        if (g) cudaGraphDestroy(g);
-        return st;
+    // replays cover whole weight periods; a remainder runs as plain launches. The
+    // graph of a replay depends on the tile height and on the parity of its first cycle.
+    while (cycles - done >= G && S->cycles_run % G == 0) {
+      const int key = S->rows_now * 2 + (int)(S->cycles_run & 1);
+      auto it = S->execs.find(key);
+      if (it == S->execs.end()) {
+        cudaGraph_t g = nullptr;
+        RICHM_CUDA_TRY(cudaStreamBeginCapture(S->s, cudaStreamCaptureModeThreadLocal));
+        richm_status st = run_cycles(S, G);
+        cudaError_t e = cudaStreamEndCapture(S->s, &g);
+        if (st != RICHM_OK) {
+          if (g) cudaGraphDestroy(g);
+          return st;
+        }
+        if (e != cudaSuccess) return set_error(RICHM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess)
+          return set_error(RICHM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        it = S->execs.emplace(key, ex).first;
       }
-      if (e != cudaSuccess) return set_error(RICHM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-      cudaGraphExec_t ex = nullptr;
-      e = cudaGraphInstantiate(&ex, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return set_error(RICHM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
-      it = S->execs.emplace(S->rows_now, ex).first;
-    }
-    while (it != S->execs.end() && cycles - done >= G && S->cycles_run % G == 0) {
       RICHM_CUDA_TRY(cudaGraphLaunch(it->second, S->s));
       S->cycles_run += G;
       done += G;
@@ -552,6 +700,17 @@ richm_status richm_solver_finish(richm_solver* S, richm_solve_info* info, void* 
   std::vector<double> rel(B);
   std::vector<int> st(B);
   RICHM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  if (S->started && fused_cycles(S)) {
+    // solutions last written to the workspace buffer go back to x
+    const TileMap* tm = nullptr;
+    RICHM_TRY(get_tiles(S->op, 64, kRows, &tm));
+    const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    solution_gather_kernel<<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(S->op->d_inst, tm->d_tiles, tm->ntiles, S->x2,
+                                                                      S->x, S->xloc);
+    RICHM_LAUNCH_CHECK("solution gather");
+    clear_ints_kernel<<<(B + 255) / 256, 256, 0, S->s>>>(S->xloc, B);
+    RICHM_LAUNCH_CHECK("clear");
+  }
   RICHM_CUDA_TRY(cudaMemcpyAsync(sw.data(), S->sweeps, sizeof(long long) * B, cudaMemcpyDeviceToHost, S->s));
   RICHM_CUDA_TRY(cudaMemcpyAsync(rel.data(), S->rel, sizeof(double) * B, cudaMemcpyDeviceToHost, S->s));
   RICHM_CUDA_TRY(cudaMemcpyAsync(st.data(), S->status, sizeof(int) * B, cudaMemcpyDeviceToHost, S->s));

@@ -197,7 +197,7 @@ __device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
 
 // One row step of the pipeline at input row rr and window phase PH.
 // NAGF: at == a, so x_{k+1} = y + w (b - A y) needs only the window.
-template <typename ST, int TL, bool MOM, bool NAGF, int PH>
+template <typename ST, int TL, bool MOM, bool NAGF, bool ABS, int PH>
 __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedState<TL>& st, const float* wl,
                                            const float* al, const float* atl) {
   using R = FusedRings<ST, TL>;
@@ -213,6 +213,15 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
       st4_to_float(reinterpret_cast<const ST*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, xm);
     } else {
       xm[0] = xm[1] = xm[2] = xm[3] = 0.f;
+    }
+    if constexpr (ABS) {
+      // the stored pair (e, e_prev) stands for (0, e_prev - e): e has been added to the
+      // FP64 solution, the difference keeps the velocity
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        xm[e] = MOM ? xm[e] - x0[e] : 0.f;
+        x0[e] = 0.f;
+      }
     }
   }
   float newx[TL + 1][VW];
@@ -284,7 +293,7 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
   }
 }
 
-template <typename ST, int TL, bool MOM, bool PRE, bool NAGF>
+template <typename ST, int TL, bool MOM, bool PRE, bool NAGF, bool ABS>
 __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kernel(const SweepTArgs A) {
   constexpr int VW = 4;
   constexpr int STRIDE = 128 - 2 * TL;
@@ -373,9 +382,9 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   // rows r0-TL .. r1+TL in steps of three (a few extra steps at the end only
   // compute rows that are neither stored nor used)
   for (int rr = rstart; rr <= rend; rr += 3) {
-    fused_step<ST, TL, MOM, NAGF, 0>(rr, c, st, wl, al, atl);
-    fused_step<ST, TL, MOM, NAGF, 1>(rr + 1, c, st, wl, al, atl);
-    fused_step<ST, TL, MOM, NAGF, 2>(rr + 2, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, ABS, 0>(rr, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, ABS, 1>(rr + 1, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, ABS, 2>(rr + 2, c, st, wl, al, atl);
   }
   cp_async_wait<0>();
 }
@@ -384,16 +393,22 @@ template <typename ST, int TL>
 static cudaError_t fused_attributes_tl() {
   const int bytes = FusedRings<ST, TL>::BYTES * kFuseWarps;
   cudaError_t e = cudaSuccess;
-#define RICHM_FUSED_ATTR(MOM, PRE, NAGF)                                                                  \
-  if (e == cudaSuccess)                                                                                   \
-    e = cudaFuncSetAttribute(sweepT_kernel<ST, TL, MOM, PRE, NAGF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             bytes);
-  RICHM_FUSED_ATTR(true, true, true)
-  RICHM_FUSED_ATTR(true, false, true)
-  RICHM_FUSED_ATTR(true, true, false)
-  RICHM_FUSED_ATTR(true, false, false)
-  RICHM_FUSED_ATTR(false, true, false)
-  RICHM_FUSED_ATTR(false, false, false)
+#define RICHM_FUSED_ATTR(MOM, PRE, NAGF, ABS)                                                               \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(sweepT_kernel<ST, TL, MOM, PRE, NAGF, ABS>,                                      \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  RICHM_FUSED_ATTR(true, true, true, false)
+  RICHM_FUSED_ATTR(true, false, true, false)
+  RICHM_FUSED_ATTR(true, true, false, false)
+  RICHM_FUSED_ATTR(true, false, false, false)
+  RICHM_FUSED_ATTR(false, true, false, false)
+  RICHM_FUSED_ATTR(false, false, false, false)
+  RICHM_FUSED_ATTR(true, true, true, true)
+  RICHM_FUSED_ATTR(true, false, true, true)
+  RICHM_FUSED_ATTR(true, true, false, true)
+  RICHM_FUSED_ATTR(true, false, false, true)
+  RICHM_FUSED_ATTR(false, true, false, true)
+  RICHM_FUSED_ATTR(false, false, false, true)
 #undef RICHM_FUSED_ATTR
   return e;
 }
@@ -410,7 +425,7 @@ cudaError_t init_fused_attributes() {
 template <typename ST>
 static richm_status launch_fused_t(richm_operator* op, int TL, const ST* x, const ST* xp, const float* b, ST* out_x,
                                    ST* out_xp, const float* w, const float* a, const float* at, int m, int kidx0,
-                                   int precond, const int* active, cudaStream_t s, int rows) {
+                                   int precond, const int* active, cudaStream_t s, int rows, bool absorb) {
   if (rows <= 0) rows = op->best_rows;
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, -TL, rows, &tm));
@@ -421,19 +436,22 @@ static richm_status launch_fused_t(richm_operator* op, int TL, const ST* x, cons
       (size_t)(TL == 4 ? FusedRings<ST, 4>::BYTES : FusedRings<ST, 8>::BYTES) * kFuseWarps;
   const bool mom = a != nullptr;
   const bool nag = mom && at == nullptr;  // at = a
-#define RICHM_FUSED(TLV)                                                                              \
-  if (nag && precond) sweepT_kernel<ST, TLV, true, true, true><<<blocks, thr, smem, s>>>(A);         \
-  else if (nag) sweepT_kernel<ST, TLV, true, false, true><<<blocks, thr, smem, s>>>(A);              \
-  else if (mom && precond) sweepT_kernel<ST, TLV, true, true, false><<<blocks, thr, smem, s>>>(A);   \
-  else if (mom) sweepT_kernel<ST, TLV, true, false, false><<<blocks, thr, smem, s>>>(A);             \
-  else if (precond) sweepT_kernel<ST, TLV, false, true, false><<<blocks, thr, smem, s>>>(A);         \
-  else sweepT_kernel<ST, TLV, false, false, false><<<blocks, thr, smem, s>>>(A);
-  if (TL == 4) {
-    RICHM_FUSED(4)
-  } else if (TL == 8) {
-    RICHM_FUSED(8)
+#define RICHM_FUSED(TLV, ABS)                                                                              \
+  if (nag && precond) sweepT_kernel<ST, TLV, true, true, true, ABS><<<blocks, thr, smem, s>>>(A);         \
+  else if (nag) sweepT_kernel<ST, TLV, true, false, true, ABS><<<blocks, thr, smem, s>>>(A);              \
+  else if (mom && precond) sweepT_kernel<ST, TLV, true, true, false, ABS><<<blocks, thr, smem, s>>>(A);   \
+  else if (mom) sweepT_kernel<ST, TLV, true, false, false, ABS><<<blocks, thr, smem, s>>>(A);             \
+  else if (precond) sweepT_kernel<ST, TLV, false, true, false, ABS><<<blocks, thr, smem, s>>>(A);         \
+  else sweepT_kernel<ST, TLV, false, false, false, ABS><<<blocks, thr, smem, s>>>(A);
+  if (TL != 4 && TL != 8) return set_error(RICHM_ERR_ARG, "fused sweeps support 4 or 8 sweeps per pass");
+  if (TL == 4 && !absorb) {
+    RICHM_FUSED(4, false)
+  } else if (TL == 4) {
+    RICHM_FUSED(4, true)
+  } else if (!absorb) {
+    RICHM_FUSED(8, false)
   } else {
-    return set_error(RICHM_ERR_ARG, "fused sweeps support 4 or 8 sweeps per pass");
+    RICHM_FUSED(8, true)
   }
 #undef RICHM_FUSED
   RICHM_LAUNCH_CHECK("fused sweep");
@@ -442,16 +460,17 @@ static richm_status launch_fused_t(richm_operator* op, int TL, const ST* x, cons
 
 richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, const float* xp, const float* b,
                                 float* out_x, float* out_xp, const float* w, const float* a, const float* at, int m,
-                                int kidx0, int precond, const int* active, cudaStream_t s, int rows) {
-  return launch_fused_t<float>(op, TL, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, precond, active, s, rows);
+                                int kidx0, int precond, const int* active, cudaStream_t s, int rows, bool absorb) {
+  return launch_fused_t<float>(op, TL, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, precond, active, s, rows,
+                               absorb);
 }
 
 richm_status launch_sweep_fused_bf16(richm_operator* op, int TL, const __nv_bfloat16* x, const __nv_bfloat16* xp,
                                      const float* b, __nv_bfloat16* out_x, __nv_bfloat16* out_xp, const float* w,
                                      const float* a, const float* at, int m, int kidx0, int precond,
-                                     const int* active, cudaStream_t s, int rows) {
+                                     const int* active, cudaStream_t s, int rows, bool absorb) {
   return launch_fused_t<__nv_bfloat16>(op, TL, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, precond, active, s,
-                                       rows);
+                                       rows, absorb);
 }
 
 }  // namespace richm

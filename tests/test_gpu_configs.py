@@ -106,6 +106,7 @@ def test_config2_full_solve_one_refinement_cycle_matches_oracle_split():
     S = richm.Solver(op, op.solve_opts(16, tol=0.0, max_sweeps=10**6), coef(wn, richm.F32), coef(a, richm.F32))
     S.start(B, X)
     S.step(1)
+    S.finish()  # fused cycles alternate two FP64 buffers; finish leaves the iterate in X
     got = from_dev(op, X, richm.F64)
     rng = np.random.default_rng(9)
     for i in (0, 3, 100, 255):

@@ -139,6 +139,38 @@ def test_fp64_inner_solver_follows_the_oracle_iteration():
         assert np.linalg.norm(split - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("fuse", [1, 8])
+def test_solver_finish_between_steps_leaves_the_iterate_in_x(fuse):
+    # fused cycles alternate between x and a workspace buffer: finish (callable between
+    # steps) must leave every instance's newest iterate in x, also for instances that
+    # stopped on an odd cycle, and stepping on afterwards must not change the result
+    insts, op, As, w, a, bs = _solve_setup([31, 63, 100])
+    B = to_dev(op, bs, richm.F64)
+    res = []
+    for pause in (None, 3):
+        X = op.zeros(richm.F64)
+        S = richm.Solver(op, op.solve_opts(16, tol=1e-8, max_sweeps=10**6, fuse=fuse), coef(w, richm.F32),
+                         coef(a, richm.F32))
+        S.start(B, X)
+        done = 0
+        active = len(insts)
+        while active:
+            active = S.step(1)
+            done += 1
+            if pause is not None and done == pause:
+                st, info = S.finish()
+                xs = from_dev(op, X, richm.F64)
+                for i, t in enumerate(insts):
+                    r = np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i])
+                    assert abs(info[i][1] - r) <= 1e-9 * r + 1e-14, (i, info[i][1], r)
+        st, info = S.finish()
+        assert st == richm.OK
+        res.append((X.cpu().numpy(), info))
+        S.close()
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
+
+
 def test_solver_session_steps_and_reports():
     insts, op, As, w, a, bs = _solve_setup([31, 63])
     B = to_dev(op, bs, richm.F64)
