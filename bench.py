@@ -451,7 +451,9 @@ def run_ours(args):
     t_max_ms = max_over_ranks(ms, world, dev)
     total_dofs = sum_over_ranks(float(dofs), world, dev)
     value = total_dofs * REFINE * args.steps / (t_max_ms / 1e3) / 1e9
-    launches_per_step = 1 + REFINE // fuse + 3  # meta forward, sweep passes, update, residual, reduce
+    # meta forward, sweep passes, then either the fused refinement and the reduction
+    # (fused passes) or the update, the residual and the reduction (one sweep per launch)
+    launches_per_step = 1 + REFINE // fuse + (2 if fuse > 1 else 3)
 
     # -- dominant kernel (the FP32 NAG sweep pass) and the one-sweep kernel: launch
     #    durations by CUDA events on the launching stream

@@ -24,6 +24,8 @@ TRAFFIC_SOURCES = {
                 "paper_2412_08076_gb300/csrc/kernels.cuh"],
     "sweepT8": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh",
                 "paper_2412_08076_gb300/csrc/kernels.cuh"],
+    "refine": ["paper_2412_08076_gb300/csrc/solve.cu", "paper_2412_08076_gb300/csrc/common.cuh",
+               "paper_2412_08076_gb300/csrc/kernels.cuh"],
 }
 
 
