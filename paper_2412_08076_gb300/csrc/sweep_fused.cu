@@ -67,7 +67,7 @@ struct FusedState {
   float YR[TL + 1][3];
   float xc[TL + 1][4];     // level s: x_{s-1} on the centre row (MOM and NAGex only)
   float vc[TL + 1][4];     // level s: x_{s-1} - x_{s-2} on the centre row
-  float prevx[TL + 1][4];  // output of level s at the previous row step
+  float prevx[2][TL + 1][4];  // outputs of level s at the last row steps (two slots)
 };
 
 constexpr int kPrefetch = 2;  // row steps between issuing a row's copies and using it
@@ -197,7 +197,10 @@ __device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
 
 // One row step of the pipeline at input row rr and window phase PH.
 // NAGF: at == a, so x_{k+1} = y + w (b - A y) needs only the window.
-template <typename ST, int TL, bool MOM, bool NAGF, bool ABS, int PH>
+// The level outputs that the next step needs (x_{k+s} of row rr - s) go to prevx[PW],
+// the previous step's are read from prevx[1 - PW]; the three unrolled phases write
+// slots 0, 1, 0, and the loop copies slot 0 to slot 1 once per three steps.
+template <typename ST, int TL, bool MOM, bool NAGF, bool ABS, int PH, int PW>
 __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedState<TL>& st, const float* wl,
                                            const float* al, const float* atl) {
   using R = FusedRings<ST, TL>;
@@ -242,7 +245,7 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       const float xs1 = newx[s - 1][e];
-      const float xs2 = (s == 1) ? xm[e] : st.prevx[s - 2][e];
+      const float xs2 = (s == 1) ? xm[e] : st.prevx[1 - PW][s - 2][e];
       vn[e] = MOM ? xs1 - xs2 : 0.f;
       Yn[e] = MOM ? fmaf(atl[s], vn[e], xs1) : xs1;
     }
@@ -289,7 +292,7 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedS
 #pragma unroll
     for (int s = 0; s + 2 <= TL; ++s)
 #pragma unroll
-      for (int e = 0; e < VW; ++e) st.prevx[s][e] = newx[s][e];
+      for (int e = 0; e < VW; ++e) st.prevx[PW][s][e] = newx[s][e];
   }
 }
 
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
       st.YL[s][q] = st.YR[s][q] = 0.f;
     }
 #pragma unroll
-    for (int e = 0; e < VW; ++e) st.xc[s][e] = st.vc[s][e] = st.prevx[s][e] = 0.f;
+    for (int e = 0; e < VW; ++e) st.xc[s][e] = st.vc[s][e] = st.prevx[0][s][e] = st.prevx[1][s][e] = 0.f;
   }
   // b rows above the tile's first input row are never loaded: zero their slots
   for (int q = 0; q < 2 * FusedRings<ST, TL>::NB; ++q)
@@ -382,9 +385,15 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   // rows r0-TL .. r1+TL in steps of three (a few extra steps at the end only
   // compute rows that are neither stored nor used)
   for (int rr = rstart; rr <= rend; rr += 3) {
-    fused_step<ST, TL, MOM, NAGF, ABS, 0>(rr, c, st, wl, al, atl);
-    fused_step<ST, TL, MOM, NAGF, ABS, 1>(rr + 1, c, st, wl, al, atl);
-    fused_step<ST, TL, MOM, NAGF, ABS, 2>(rr + 2, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, ABS, 0, 0>(rr, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, ABS, 1, 1>(rr + 1, c, st, wl, al, atl);
+    fused_step<ST, TL, MOM, NAGF, ABS, 2, 0>(rr + 2, c, st, wl, al, atl);
+    if (MOM) {
+#pragma unroll
+      for (int s = 0; s + 2 <= TL; ++s)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) st.prevx[1][s][e] = st.prevx[0][s][e];
+    }
   }
   cp_async_wait<0>();
 }
