@@ -12,7 +12,8 @@ Modules
   operators   anisotropic Q1 FEM matrix (Sec. 2.4, eq. 18) and the Helmholtz
               5-point matrix with a first-order absorbing boundary (eq. 22)
   iterations  Richardson(m), MOM/NAG/NAGex-Richardson(m) (Table 1),
-              preconditioned form (eq. 17), Chebyshev weights (eqs. 8-9),
+              preconditioned form (eq. 17) with the Jacobi and SSOR
+              preconditioners, Chebyshev weights (eqs. 8-9),
               residual (eq. 15) and solve-to-tolerance, FP64 refinement split
   training    loss (log form of eq. 15), its gradient, meta MLP, Adam (Alg. 1)
   fourier     two-level step with a Fourier-domain correction (eqs. 19-20)

@@ -67,6 +67,32 @@ def jacobi_binv(A):
     return lambda r: r / d
 
 
+def ssor_binv(A, alpha):
+    """B^{-1} = alpha (2 - alpha) (D - alpha U)^{-1} D (D - alpha L)^{-1}, the SSOR member
+    of the stationary preconditioners listed after eq. 17 (A = D - L - U with D diagonal,
+    -L and -U the strictly lower and upper triangles of A).
+
+    Reading: the paper does not state the ordering of the unknowns; L and U are taken in
+    the row-major (lexicographic) numbering in which A is assembled here. The two
+    triangular solves are library routines (scipy), one step each.
+    Pinned by: u + B^{-1}(f - A u) equals one forward and one backward point SOR sweep
+    written as loops; a diagonal A gives alpha (2 - alpha) D^{-1}; B^{-1} is symmetric
+    positive definite and the eigenvalues of B^{-1} A lie in (0, 1] for an SPD A and
+    0 < alpha < 2 (tests).
+    """
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import spsolve_triangular
+    A = sp.csr_matrix(A)
+    d = A.diagonal()
+    lower = sp.csr_matrix(sp.diags(d) + alpha * sp.tril(A, -1))  # D - alpha L
+    upper = sp.csr_matrix(sp.diags(d) + alpha * sp.triu(A, 1))   # D - alpha U
+
+    def apply(r):
+        z = spsolve_triangular(lower, np.asarray(r, dtype=np.float64), lower=True)
+        return alpha * (2.0 - alpha) * spsolve_triangular(upper, d * z, lower=False)
+    return apply
+
+
 def residual(A, f, u):
     """f - A u."""
     return f - A @ u

@@ -8,7 +8,7 @@ import pytest
 import richm_synth as synth
 from oracle.iterations import (chebyshev_weights, inner_steps, jacobi_binv,
                                outer_iterations_to_tol, refined_steps, rel_residual,
-                               semi_iteration_weights)
+                               semi_iteration_weights, ssor_binv)
 from oracle.operators import assemble_q1, diffusion_tensor
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -131,6 +131,52 @@ def test_jacobi_preconditioner_is_rescaled_weight():
     x1, _ = inner_steps(A, f, np.zeros(n * n), None, w, a, K=11, Binv=jacobi_binv(A))
     x2, _ = inner_steps(A, f, np.zeros(n * n), None, w / d, a, K=11)
     np.testing.assert_allclose(x1, x2, rtol=1e-13, atol=1e-15)
+
+
+def _sor_sweeps_by_loops(A, f, u, alpha):
+    """One forward, then one backward point SOR sweep (in-place updates in the row-major
+    numbering), written as plain loops over the points."""
+    Ad = A.toarray()
+    u = np.array(u, dtype=np.float64, copy=True)
+    N = len(u)
+    for order in (range(N), range(N - 1, -1, -1)):
+        for p in order:
+            sigma = Ad[p] @ u - Ad[p, p] * u[p]
+            u[p] = (1.0 - alpha) * u[p] + alpha * (f[p] - sigma) / Ad[p, p]
+    return u
+
+
+@pytest.mark.parametrize("n,eps,theta,alpha", [(2, 1.0, 0.3, 1.0), (3, 1e-2, 1.0, 1.3), (5, 1e-3, 2.2, 0.7),
+                                               (4, 1e-6, math.pi / 10, 1.9)])
+def test_ssor_preconditioner_is_a_forward_and_a_backward_sor_sweep(n, eps, theta, alpha):
+    A = assemble_q1(n, eps, theta)
+    f = synth.rhs_uniform(5, n, n).ravel()
+    u = synth.rhs_uniform(6, n, n).ravel()
+    want = _sor_sweeps_by_loops(A, f, u, alpha)
+    got = u + ssor_binv(A, alpha)(f - A @ u)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+def test_ssor_of_a_diagonal_matrix_is_scaled_jacobi():
+    import scipy.sparse as sp
+    d = np.linspace(1.0, 3.0, 7)
+    r = synth.rhs_uniform(7, 0, 7)[0]
+    for alpha in (0.5, 1.0, 1.5):
+        got = ssor_binv(sp.diags(d), alpha)(r)
+        np.testing.assert_allclose(got, alpha * (2 - alpha) * r / d, rtol=1e-15)
+
+
+@pytest.mark.parametrize("alpha", [0.6, 1.0, 1.8])
+def test_ssor_preconditioner_is_spd_and_clusters_the_spectrum_in_0_1(alpha):
+    n = 4
+    A = assemble_q1(n, 1e-2, 0.9)
+    Binv = ssor_binv(A, alpha)
+    M = np.column_stack([Binv(e) for e in np.eye(n * n)])
+    np.testing.assert_allclose(M, M.T, atol=1e-13 * np.abs(M).max())
+    assert np.linalg.eigvalsh((M + M.T) / 2).min() > 0
+    lam = np.linalg.eigvals(M @ A.toarray())
+    assert np.abs(lam.imag).max() < 1e-10
+    assert lam.real.min() > 0 and lam.real.max() <= 1 + 1e-12
 
 
 def test_refinement_split_is_the_same_iteration():
