@@ -142,11 +142,16 @@ richm_status richm_unpack(const richm_operator* op, richm_dtype dtype, const voi
 typedef struct {
   int m;        /* period length, 1 <= m <= 64 */
   int k_start;  /* global index of the first sweep */
-  int precond;  /* 0: B^{-1} = I; 1: B^{-1} = D^{-1} (eq. 17 with the Jacobi preconditioner) */
+  int precond;  /* 0: B^{-1} = I; 1: B^{-1} = D^{-1} (eq. 17 with the Jacobi preconditioner);
+                   2: B^{-1} = relax (2 - relax) (D - relax U)^{-1} D (D - relax L)^{-1}, the SSOR
+                   preconditioner listed after eq. 17, with A = D - L - U split in the row-major
+                   numbering of each instance's unknowns (Q1, RICHM_F32 or RICHM_F64, one sweep per
+                   pass) */
   int fuse;     /* sweeps per pass over HBM (temporal blocking): 0 = library choice, else 1, 2, 4 or 8 */
+  double relax; /* SSOR relaxation factor, 0 < relax < 2 (precond = 2 only) */
 } richm_sweep_opts;
 
-/* Workspace bytes richm_apply_sweeps needs for `dtype` (two padded buffers). */
+/* Workspace bytes richm_apply_sweeps needs for `dtype` (three padded buffers). */
 richm_status richm_sweeps_workspace(const richm_operator* op, richm_dtype dtype, size_t* bytes);
 
 /* K sweeps of the Table 1 iteration in the two-level form
@@ -229,9 +234,10 @@ typedef struct {
   int refine_every;      /* sweeps between FP64 refinement steps / convergence checks (>= 1) */
   int inner;             /* richm_dtype of the inner sweeps: RICHM_F32 (mixed precision), RICHM_F64, or
                             RICHM_BF16 (bfloat16 inner state, FP32 arithmetic and rhs; fused sweeps) */
-  int precond;           /* as in richm_sweep_opts */
+  int precond;           /* as in richm_sweep_opts (2, SSOR: one sweep per launch, fuse 0 or 1) */
   int fuse;              /* as in richm_sweep_opts */
   int use_graph;         /* 1: replay the refinement cycle as a CUDA graph */
+  double relax;          /* as in richm_sweep_opts */
 } richm_solve_opts;
 
 typedef struct {

@@ -113,6 +113,22 @@ struct alignas(16) W16 {
   unsigned long long a, b;
 };
 
+// Rows 0 and n + 1 of every instance of a padded buffer of `esize`-byte elements.
+__global__ void zero_halo_rows_kernel(const Inst* insts, unsigned char* buf, int esize) {
+  const Inst& I = insts[blockIdx.x];
+  const long long row = blockIdx.y == 0 ? 0 : (long long)(I.n + 1);
+  uint4* p = reinterpret_cast<uint4*>(buf + (I.off + row * I.pitch) * esize);
+  const int chunks = I.pitch * esize / 16;  // pitch is a multiple of 32 elements
+  for (int q = threadIdx.x; q < chunks; q += blockDim.x) p[q] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+richm_status launch_zero_halo(const richm_operator* op, void* buf, size_t esize, cudaStream_t s) {
+  zero_halo_rows_kernel<<<dim3(op->batch, 2), 128, 0, s>>>(op->d_inst, reinterpret_cast<unsigned char*>(buf),
+                                                           (int)esize);
+  RICHM_LAUNCH_CHECK("zero halo rows");
+  return RICHM_OK;
+}
+
 template <bool PACK>
 static richm_status pack_dispatch(const richm_operator* op, richm_dtype dt, const void* src, void* dst,
                                   void* stream) {

@@ -40,6 +40,19 @@ richm_status launch_sweep_fused_bf16(richm_operator* op, int TL, const __nv_bflo
                                      const float* a, const float* at, int m, int kidx0, int precond,
                                      const int* active, cudaStream_t s, int rows = 0, bool absorb = false);
 
+// Zero rows 0 and n + 1 of every instance of a padded buffer (esize-byte elements). The
+// sweep kernels write rows 1..n of their outputs only; a workspace buffer whose result
+// is copied back to the caller gets its halo rows cleared first.
+richm_status launch_zero_halo(const richm_operator* op, void* buf, size_t esize, cudaStream_t s);
+
+// One SSOR-preconditioned sweep of a Q1 batch (E = float or double): forward triangular
+// solve into z, backward solve and the Table 1 update into (out_x, out_xp). z: a padded
+// scratch buffer (no initial contents needed); the outputs must not alias the inputs.
+template <typename E>
+richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, const E* b, E* z, E* out_x, E* out_xp,
+                               const E* w, const E* a, const E* at, int m, int kidx, double relax, const int* active,
+                               cudaStream_t s);
+
 // r = b - A x in FP64 with per-tile partial sums (sum |r|^2, sum |b|^2) written to
 // `partials` (one double2 per warp tile of the residual geometry); r_out may be null.
 template <typename E>

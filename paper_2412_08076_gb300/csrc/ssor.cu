@@ -1,0 +1,315 @@
+// SSOR-preconditioned sweeps (eq. 17 with B^{-1} = w (2 - w) (D - w U)^{-1} D (D - w L)^{-1},
+// the SSOR member of the stationary preconditioners listed after eq. 17; w is the
+// relaxation factor, A = D - L - U split in the row-major numbering of each instance).
+//
+// One sweep of the Table 1 iteration (velocity form, look-ahead at, momentum a, weight w_i)
+//   y = x + at (x - x_prev),  r = b - A y,  x_new = x + a (x - x_prev) + w_i B^{-1} r
+// is two passes over an instance, each a triangular solve with the 9-point stencil:
+//   forward  (rows top to bottom):  z = (D - w L)^{-1} r, with r formed on the fly;
+//   backward (rows bottom to top):  s = (D - w U)^{-1} D z, then x_new and x_prev_new = x.
+// In the forward solve, z(i, j) = r(i, j)/c - (w/c) [ax z(i, j-1) + ay z(i-1, j)
+// + d1 z(i-1, j-1) + d2 z(i-1, j+1)]: the previous row enters as known values, and along
+// the row the recurrence z_j = q_j - kappa z_{j-1} (kappa = w ax / c, |kappa| < 1 for the
+// Q1 stencil and 0 < w < 2) is a first-order linear recurrence with a constant
+// coefficient. A warp owns one instance and walks its rows in order; within a row each
+// lane takes VW consecutive columns, composes the affine maps of its columns, and a
+// log-depth scan of those maps across the lanes (shuffles) gives every lane its incoming
+// value, after which it replays its columns. Rows wider than 32 VW columns are taken in
+// chunks, carrying the last value. The backward solve is the mirror image (rows and
+// columns reversed, upper neighbours). The intermediate z lives in a padded buffer;
+// the backward pass overwrites it with s row by row (the row above reads s below).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace richm {
+
+constexpr int kSsorWarps = 4;  // instances per block, one warp each
+
+template <typename E> struct SsorVW;
+template <> struct SsorVW<float> { static constexpr int v = 16; };
+template <> struct SsorVW<double> { static constexpr int v = 8; };
+
+// VW values of row `row` (1..n, else zeros) at columns c0.. of an instance's buffer,
+// with the left and right neighbours of the lane's first and last column (zero outside
+// 0..pitch-1; the lane's own loads and shuffles inside a chunk).
+template <typename E, int VW>
+struct RowVW {
+  E v[VW];
+  E l, r;
+};
+
+// 16-byte vector loads and stores of VW consecutive values (constant indices only, so
+// the values stay in registers).
+template <typename E, int VW>
+__device__ __forceinline__ void ld16(const E* p, E* v) {
+  if constexpr (sizeof(E) == 4) {
+#pragma unroll
+    for (int q = 0; q < VW / 4; ++q) {
+      const float4 t = reinterpret_cast<const float4*>(p)[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < VW / 2; ++q) {
+      const double2 t = reinterpret_cast<const double2*>(p)[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  }
+}
+template <typename E, int VW>
+__device__ __forceinline__ void st16(E* p, const E* v) {
+  if constexpr (sizeof(E) == 4) {
+#pragma unroll
+    for (int q = 0; q < VW / 4; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < VW / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+  }
+}
+
+template <typename E, int VW>
+__device__ __forceinline__ void load_vw(const E* base, int row, int n, int pitch, int c0, int lane, bool live,
+                                        bool first_chunk, RowVW<E, VW>& R) {
+  const bool in = row >= 1 && row <= n;
+  const E* p = base + (long long)row * pitch + c0;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) R.v[e] = E(0);
+  if (in && live) ld16<E, VW>(p, R.v);
+  E l = __shfl_up_sync(0xffffffffu, R.v[VW - 1], 1);
+  E r = __shfl_down_sync(0xffffffffu, R.v[0], 1);
+  if (lane == 0) l = (in && !first_chunk) ? p[-1] : E(0);
+  if (lane == 31) r = (in && c0 + VW < pitch) ? p[VW] : E(0);
+  R.l = l;
+  R.r = r;
+}
+
+template <typename E, int VW>
+__device__ __forceinline__ E left_of(const RowVW<E, VW>& R, int e) { return e == 0 ? R.l : R.v[e - 1]; }
+template <typename E, int VW>
+__device__ __forceinline__ E right_of(const RowVW<E, VW>& R, int e) { return e == VW - 1 ? R.r : R.v[e + 1]; }
+
+// y = x + at (x - x_prev) on a row (neighbours included).
+template <typename E, int VW>
+__device__ __forceinline__ void lookahead(RowVW<E, VW>& X, const RowVW<E, VW>& XP, E at) {
+#pragma unroll
+  for (int e = 0; e < VW; ++e) X.v[e] = X.v[e] + at * (X.v[e] - XP.v[e]);
+  X.l = X.l + at * (X.l - XP.l);
+  X.r = X.r + at * (X.r - XP.r);
+}
+
+// Inclusive scan of affine maps z -> P + Q z over the lanes, in lane order (UP) or in
+// reverse lane order; composing a map after the ones before it.
+template <typename E, bool UP>
+__device__ __forceinline__ void scan_maps(E& P, E& Q, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const E Pp = UP ? __shfl_up_sync(0xffffffffu, P, d) : __shfl_down_sync(0xffffffffu, P, d);
+    const E Qp = UP ? __shfl_up_sync(0xffffffffu, Q, d) : __shfl_down_sync(0xffffffffu, Q, d);
+    const bool has = UP ? lane >= d : lane + d < 32;
+    if (has) {
+      P = P + Q * Pp;
+      Q = Q * Qp;
+    }
+  }
+}
+
+template <typename E>
+struct SsorArgs {
+  const Inst* insts;
+  int batch;
+  const E* x;
+  const E* xp;  // null without momentum
+  const E* b;
+  E* z;         // intermediate (padded)
+  E* out_x;
+  E* out_xp;    // null without momentum
+  const E* w;
+  const E* a;   // null without momentum
+  const E* at;  // null: at = a
+  int m, kidx;
+  E relax;
+  const int* active;
+};
+
+template <typename E, int VW>
+__global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_kernel(const SsorArgs<E> A) {
+  const int lane = threadIdx.x & 31;
+  const int inst = blockIdx.x * kSsorWarps + (threadIdx.x >> 5);
+  if (inst >= A.batch) return;
+  if (A.active && A.active[inst] == 0) return;
+  const Inst& I = A.insts[inst];
+  const int n = I.n, pitch = I.pitch;
+  const E c = (E)I.c, ax = (E)I.ax, ay = (E)I.ay, d1 = (E)I.d1, d2 = (E)I.d2;
+  const E rc = E(1) / c;
+  const E kx = A.relax * ax * rc, ky = A.relax * ay * rc, k1 = A.relax * d1 * rc, k2 = A.relax * d2 * rc;
+  const int ci = inst * A.m + A.kidx;
+  const E ati = A.a ? (A.at ? A.at[ci] : A.a[ci]) : E(0);
+  const E* xb = A.x + I.off;
+  const E* xpb = A.xp ? A.xp + I.off : nullptr;
+  const E* bb = A.b + I.off;
+  E* zb = A.z + I.off;
+  constexpr int CH = 32 * VW;
+  const int nch = (pitch + CH - 1) / CH;
+  for (int i = 1; i <= n; ++i) {
+    E carry = E(0);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int c0 = ch * CH + lane * VW;
+      const bool live = c0 < pitch;
+      RowVW<E, VW> YU, YC, YD, ZU, T;
+      load_vw<E, VW>(xb, i - 1, n, pitch, c0, lane, live, ch == 0, YU);
+      load_vw<E, VW>(xb, i, n, pitch, c0, lane, live, ch == 0, YC);
+      load_vw<E, VW>(xb, i + 1, n, pitch, c0, lane, live, ch == 0, YD);
+      if (xpb && ati != E(0)) {
+        load_vw<E, VW>(xpb, i - 1, n, pitch, c0, lane, live, ch == 0, T);
+        lookahead<E, VW>(YU, T, ati);
+        load_vw<E, VW>(xpb, i, n, pitch, c0, lane, live, ch == 0, T);
+        lookahead<E, VW>(YC, T, ati);
+        load_vw<E, VW>(xpb, i + 1, n, pitch, c0, lane, live, ch == 0, T);
+        lookahead<E, VW>(YD, T, ati);
+      }
+      load_vw<E, VW>(zb, i - 1, n, pitch, c0, lane, live, ch == 0, ZU);
+      load_vw<E, VW>(bb, i, n, pitch, c0, lane, live, ch == 0, T);  // b (neighbours unused)
+      E q[VW], k[VW];
+      E P = E(0), Q = E(1);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const E Ay = c * YC.v[e] + ax * (left_of(YC, e) + right_of(YC, e)) + ay * (YU.v[e] + YD.v[e]) +
+                     d1 * (right_of(YD, e) + left_of(YU, e)) + d2 * (right_of(YU, e) + left_of(YD, e));
+        const bool ok = c0 + e < n;
+        q[e] = ok ? (T.v[e] - Ay) * rc - (ky * ZU.v[e] + k1 * left_of(ZU, e) + k2 * right_of(ZU, e)) : E(0);
+        k[e] = ok ? -kx : E(0);
+        P = q[e] + k[e] * P;
+        Q = k[e] * Q;
+      }
+      scan_maps<E, true>(P, Q, lane);
+      E Pe = __shfl_up_sync(0xffffffffu, P, 1), Qe = __shfl_up_sync(0xffffffffu, Q, 1);
+      if (lane == 0) Pe = E(0), Qe = E(1);
+      E zv = Pe + Qe * carry;
+      E out[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        zv = q[e] + k[e] * zv;
+        out[e] = zv;
+      }
+      if (live) st16<E, VW>(zb + (long long)i * pitch + c0, out);
+      carry = __shfl_sync(0xffffffffu, P + Q * carry, 31);
+    }
+    __syncwarp();  // row i of z is read by other lanes in the next row
+  }
+}
+
+template <typename E, int VW>
+__global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_kernel(const SsorArgs<E> A) {
+  const int lane = threadIdx.x & 31;
+  const int inst = blockIdx.x * kSsorWarps + (threadIdx.x >> 5);
+  if (inst >= A.batch) return;
+  if (A.active && A.active[inst] == 0) return;
+  const Inst& I = A.insts[inst];
+  const int n = I.n, pitch = I.pitch;
+  const E c = (E)I.c, ax = (E)I.ax, ay = (E)I.ay, d1 = (E)I.d1, d2 = (E)I.d2;
+  const E rc = E(1) / c;
+  const E kx = A.relax * ax * rc, ky = A.relax * ay * rc, k1 = A.relax * d1 * rc, k2 = A.relax * d2 * rc;
+  const int ci = inst * A.m + A.kidx;
+  const E wi = A.w[ci] * A.relax * (E(2) - A.relax);
+  const E ai = A.a ? A.a[ci] : E(0);
+  const E* xb = A.x + I.off;
+  const E* xpb = A.xp ? A.xp + I.off : nullptr;
+  E* zb = A.z + I.off;
+  E* ox = A.out_x + I.off;
+  E* oxp = A.out_xp ? A.out_xp + I.off : nullptr;
+  constexpr int CH = 32 * VW;
+  const int nch = (pitch + CH - 1) / CH;
+  {
+    // the output's halo rows (the buffer may come uninitialised from a rotation)
+    E zero[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) zero[e] = E(0);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int c0 = ch * CH + lane * VW;
+      if (c0 < pitch) {
+        st16<E, VW>(ox + c0, zero);
+        st16<E, VW>(ox + (long long)(n + 1) * pitch + c0, zero);
+        if (oxp) {
+          st16<E, VW>(oxp + c0, zero);
+          st16<E, VW>(oxp + (long long)(n + 1) * pitch + c0, zero);
+        }
+      }
+    }
+  }
+  for (int i = n; i >= 1; --i) {
+    E carry = E(0);
+    for (int ch = nch - 1; ch >= 0; --ch) {
+      const int c0 = ch * CH + lane * VW;
+      const bool live = c0 < pitch;
+      RowVW<E, VW> SD, ZC;
+      load_vw<E, VW>(zb, i + 1, n, pitch, c0, lane, live, ch == 0, SD);  // s of the row below
+      load_vw<E, VW>(zb, i, n, pitch, c0, lane, live, ch == 0, ZC);      // z of this row
+      E t[VW], k[VW];
+      E P = E(0), Q = E(1);
+#pragma unroll
+      for (int e = VW - 1; e >= 0; --e) {
+        const bool ok = c0 + e < n;
+        t[e] = ok ? ZC.v[e] - (ky * SD.v[e] + k1 * right_of(SD, e) + k2 * left_of(SD, e)) : E(0);
+        k[e] = ok ? -kx : E(0);
+        P = t[e] + k[e] * P;
+        Q = k[e] * Q;
+      }
+      scan_maps<E, false>(P, Q, lane);
+      E Pe = __shfl_down_sync(0xffffffffu, P, 1), Qe = __shfl_down_sync(0xffffffffu, Q, 1);
+      if (lane == 31) Pe = E(0), Qe = E(1);
+      E sv = Pe + Qe * carry;
+      E sr[VW];
+#pragma unroll
+      for (int e = VW - 1; e >= 0; --e) {
+        sv = t[e] + k[e] * sv;
+        sr[e] = sv;
+      }
+      carry = __shfl_sync(0xffffffffu, P + Q * carry, 0);
+      if (live) {
+        const long long o = (long long)i * pitch + c0;
+        E xv[VW], xpv[VW], xn[VW];
+        ld16<E, VW>(xb + o, xv);
+        if (xpb) ld16<E, VW>(xpb + o, xpv);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          const E v = xpb ? xv[e] - xpv[e] : E(0);
+          xn[e] = xv[e] + ai * v + wi * sr[e];
+        }
+        st16<E, VW>(ox + o, xn);
+        if (oxp) st16<E, VW>(oxp + o, xv);
+        st16<E, VW>(zb + o, sr);
+      }
+    }
+    __syncwarp();  // row i of s is read by other lanes in the next row
+  }
+}
+
+template <typename E>
+richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, const E* b, E* z, E* out_x, E* out_xp,
+                               const E* w, const E* a, const E* at, int m, int kidx, double relax, const int* active,
+                               cudaStream_t s) {
+  constexpr int VW = SsorVW<E>::v;
+  // out_xp (x_k copied for the caller) may be null when the caller keeps x_k in place
+  SsorArgs<E> A{op->d_inst, op->batch, x, a ? xp : nullptr, b, z, out_x, a ? out_xp : nullptr,
+                w, a, at, m, kidx, (E)relax, active};
+  const int blocks = (op->batch + kSsorWarps - 1) / kSsorWarps;
+  ssor_forward_kernel<E, VW><<<blocks, kSsorWarps * 32, 0, s>>>(A);
+  RICHM_LAUNCH_CHECK("SSOR forward solve");
+  ssor_backward_kernel<E, VW><<<blocks, kSsorWarps * 32, 0, s>>>(A);
+  RICHM_LAUNCH_CHECK("SSOR backward solve");
+  return RICHM_OK;
+}
+
+template richm_status launch_ssor_sweep<float>(richm_operator*, const float*, const float*, const float*, float*,
+                                               float*, float*, const float*, const float*, const float*, int, int,
+                                               double, const int*, cudaStream_t);
+template richm_status launch_ssor_sweep<double>(richm_operator*, const double*, const double*, const double*,
+                                                double*, double*, double*, const double*, const double*,
+                                                const double*, int, int, double, const int*, cudaStream_t);
+
+}  // namespace richm

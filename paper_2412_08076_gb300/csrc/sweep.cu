@@ -256,6 +256,30 @@ static richm_status apply_sweeps_t(richm_operator* op, E* x, E* xp, const E* b, 
   E* cur = x;
   E* prev = mom ? xp : nullptr;
   int k = 0;
+  // the rotation may end in a workspace buffer that is copied back whole
+  RICHM_TRY(launch_zero_halo(op, W0, sizeof(E), s));
+  RICHM_TRY(launch_zero_halo(op, W1, sizeof(E), s));
+  if constexpr (std::is_same<E, float>::value || std::is_same<E, double>::value) {
+    if (o->precond == 2) {
+      // SSOR: one forward and one backward solve per sweep; the third buffer holds z
+      E* Z = reinterpret_cast<E*>(reinterpret_cast<char*>(work) + 2 * (((bytes + 255) / 256) * 256));
+      for (; k < K; ++k) {
+        E* outb = nullptr;
+        E* cand[4] = {W0, W1, x, xp};
+        for (E* c : cand)
+          if (c != nullptr && c != cur && c != prev) {
+            outb = c;
+            break;
+          }
+        const int kidx = (int)(((long long)o->k_start + k) % o->m);
+        // x_{k+1} -> outb; x_k stays where it is and becomes the new previous iterate
+        RICHM_TRY(launch_ssor_sweep<E>(op, cur, prev, b, Z, outb, nullptr, (const S*)w, (const S*)a,
+                                       (const S*)at, o->m, kidx, o->relax, nullptr, s));
+        prev = mom ? cur : nullptr;
+        cur = outb;
+      }
+    }
+  }
   if constexpr (std::is_same<E, float>::value) {
     // fused passes of TL sweeps: (cur, prev) -> the other pair of buffers
     const int TL = (o->fuse == 4 || o->fuse == 8) ? o->fuse : 0;
@@ -312,7 +336,7 @@ richm_status richm_sweeps_workspace(const richm_operator* op, richm_dtype dtype,
   RICHM_ARG(op && bytes, "null argument");
   RICHM_ARG(dtype_valid(dtype), "invalid dtype %d", (int)dtype);
   const size_t one = ((op->elems * dtype_size(dtype) + 255) / 256) * 256;
-  *bytes = 2 * one;
+  *bytes = 3 * one;  // two rotation buffers and the SSOR intermediate
   return RICHM_OK;
 }
 
@@ -362,7 +386,7 @@ richm_status richm_autotune(richm_operator* op, int m, int momentum, void* work,
   for (const auto& cr : cands) {
     const int c = cr[0];
     if (c > 1) op->best_rows = cr[1];
-    richm_sweep_opts o{m, 0, 0, c};
+    richm_sweep_opts o{m, 0, 0, c, 1.0};
     const int K = 16;
     richm_status st = apply_sweeps_t<float>(op, x, xp, b, w, a, nullptr, K, &o, W, s);  // warm-up
     if (st == RICHM_OK) cudaEventRecord(e0, s);
@@ -419,7 +443,12 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
   RICHM_ARG(K >= 0, "K = %d < 0", K);
   RICHM_ARG(opts->m >= 1 && opts->m <= 64, "m = %d out of range [1, 64]", opts->m);
   RICHM_ARG(opts->k_start >= 0, "k_start < 0");
-  RICHM_ARG(opts->precond == 0 || opts->precond == 1, "precond must be 0 or 1");
+  RICHM_ARG(opts->precond == 0 || opts->precond == 1 || opts->precond == 2, "precond must be 0, 1 or 2");
+  if (opts->precond == 2) {
+    RICHM_ARG(opts->relax > 0.0 && opts->relax < 2.0, "SSOR relaxation factor %g outside (0, 2)", opts->relax);
+    if (dtype != RICHM_F32 && dtype != RICHM_F64)
+      return set_error(RICHM_ERR_UNSUPPORTED, "SSOR preconditioning takes RICHM_F32 or RICHM_F64 Q1 state");
+  }
   RICHM_ARG(opts->fuse == 0 || opts->fuse == 1 || opts->fuse == 2 || opts->fuse == 4 || opts->fuse == 8,
             "fuse must be 0, 1, 2, 4 or 8");
   RICHM_ARG(x != nullptr && b != nullptr && w != nullptr, "null x, b or w");
@@ -433,6 +462,7 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
   cudaStream_t s = (cudaStream_t)stream;
   richm_sweep_opts o = *opts;
   if (o.fuse == 0) o.fuse = (dtype == RICHM_F32 || dtype == RICHM_BF16) ? op->best_fuse : 1;
+  if (o.precond == 2) o.fuse = 1;  // the triangular solves cannot be fused in time
   opts = &o;
   switch (dtype) {
     case RICHM_BF16: {
@@ -448,6 +478,8 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
       B16* cur = (B16*)x;
       B16* prev = (B16*)x_prev;
       const bool mom = alpha != nullptr;
+      RICHM_TRY(launch_zero_halo(op, W0, sizeof(B16), s));
+      RICHM_TRY(launch_zero_halo(op, W1, sizeof(B16), s));
       for (int k = 0; k < K; k += TL) {
         B16* ox = (cur == (B16*)x) ? W0 : (B16*)x;
         B16* oxp = (cur == (B16*)x) ? W1 : (mom ? (B16*)x_prev : W1);

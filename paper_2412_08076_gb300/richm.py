@@ -41,12 +41,14 @@ class richm_pde(C.Structure):
 
 
 class richm_sweep_opts(C.Structure):
-    _fields_ = [("m", C.c_int), ("k_start", C.c_int), ("precond", C.c_int), ("fuse", C.c_int)]
+    _fields_ = [("m", C.c_int), ("k_start", C.c_int), ("precond", C.c_int), ("fuse", C.c_int),
+                ("relax", C.c_double)]
 
 
 class richm_solve_opts(C.Structure):
     _fields_ = [("m", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_longlong), ("refine_every", C.c_int),
-                ("inner", C.c_int), ("precond", C.c_int), ("fuse", C.c_int), ("use_graph", C.c_int)]
+                ("inner", C.c_int), ("precond", C.c_int), ("fuse", C.c_int), ("use_graph", C.c_int),
+                ("relax", C.c_double)]
 
 
 class richm_solve_info(C.Structure):
@@ -263,10 +265,11 @@ class Operator:
 
     # -- compute
     def apply_sweeps(self, dtype, x, x_prev, b, w, alpha=None, alpha_t=None, K=1, m=None, k_start=0, precond=0,
-                     fuse=0, work=None, stream=None):
-        """richm_apply_sweeps (Table 1 iteration, eq. 17); x / x_prev updated in place."""
+                     fuse=0, work=None, stream=None, relax=1.0):
+        """richm_apply_sweeps (Table 1 iteration, eq. 17); x / x_prev updated in place.
+        precond: 0 none, 1 Jacobi, 2 SSOR with relaxation factor `relax`."""
         m = m if m is not None else w.numel() // self.batch
-        o = richm_sweep_opts(m, k_start, precond, fuse)
+        o = richm_sweep_opts(m, k_start, precond, fuse, relax)
         need = self._ws("richm_sweeps_workspace", dtype)
         if work is None:
             work = self.workspace(need)
@@ -313,8 +316,9 @@ class Operator:
                                    _ptr(rel), _ptr(work), work.numel(), _stream(stream)), "richm_refine")
         return rel
 
-    def solve_opts(self, m, tol=1e-10, max_sweeps=10**7, refine_every=64, inner=F32, precond=0, fuse=0, use_graph=1):
-        return richm_solve_opts(m, tol, max_sweeps, refine_every, inner, precond, fuse, use_graph)
+    def solve_opts(self, m, tol=1e-10, max_sweeps=10**7, refine_every=64, inner=F32, precond=0, fuse=0, use_graph=1,
+                   relax=1.0):
+        return richm_solve_opts(m, tol, max_sweeps, refine_every, inner, precond, fuse, use_graph, relax)
 
     def solve(self, b, x, w, alpha=None, alpha_t=None, opts=None, work=None, stream=None):
         """richm_solve; returns (status, list of (sweeps, rel_res, status))."""
