@@ -339,6 +339,41 @@ def secondary_workloads(dev):
                                   "note": "random symbol: parity only (vs oracle in tests)"}
     op.close()
 
+    # SSOR-preconditioned NAG-Richardson(16) against the Jacobi-preconditioned one on the
+    # setting of the paper's SSOR tables (eps = 1e-6, theta = pi/10), 152 instances of
+    # 255^2 (one warp per instance for the triangular solves): the same weight recipe
+    # (momentum-aware Chebyshev semi-iteration, beta = 0.3) on each preconditioned
+    # spectrum bound, (0, 1] for SSOR and (0, G/d] for Jacobi; FP32 sweeps, FP64
+    # refinement every 64 sweeps, to 1e-10
+    n, nb = 255, 152
+    op = richm.Operator([(richm.ANISO_Q1, n, 1e-6, math.pi / 10, 0.0)] * nb)
+    G = op.gershgorin()[0]
+    dgl = op.stencil(0)[0]
+    rhs = np.concatenate([synth.rhs_uniform(46, i, n).ravel() for i in range(nb)])
+    B64 = op.pack(torch.tensor(rhs, device=dev), richm.F64)
+    res = {}
+    for name, pc, bound, relax in (("ssor", 2, 1.0, 1.5), ("jacobi", 1, G / dgl, 1.0)):
+        wv = np.array(richm.chebyshev_weights(1.6 * bound, 1.6 * bound / 30.0, 16))
+        wt = torch.tensor(np.tile(wv, (nb, 1)), dtype=torch.float32, device=dev)
+        at_ = torch.full_like(wt, 0.3)
+        o = op.solve_opts(16, tol=SOLVE_TOL, max_sweeps=400000, refine_every=64, inner=richm.F32, precond=pc,
+                          fuse=1 if pc == 2 else 0, relax=relax)
+        X = op.zeros(richm.F64)
+        t0, t1 = ev(), ev()
+        t0.record()
+        st_, info_ = op.solve(B64, X, wt, at_, None, o)
+        t1.record()
+        torch.cuda.synchronize()
+        sw_ = max(sw for sw, _, _ in info_)
+        res[name] = {"status": int(st_), "max_sweeps": int(sw_), "seconds": t0.elapsed_time(t1) / 1e3,
+                     "worst_rel_res": max(r for _, r, _ in info_),
+                     "gdof_sweeps_per_s": nb * n * n * sw_ / (t0.elapsed_time(t1) / 1e3) / 1e9}
+    res["sweep_ratio_jacobi_over_ssor"] = res["jacobi"]["max_sweeps"] / max(1, res["ssor"]["max_sweeps"])
+    res["note"] = ("SSOR: one warp per instance walks the rows (scan of the row recurrence), latency-bound; "
+                   "parity vs oracle in tests/test_gpu_ssor.py")
+    out["ssor_vs_jacobi_152x255sq_eps1e-6"] = res
+    op.close()
+
     # Helmholtz: 16 x 2047^2 complex64, NAG m = 8, seeded weights, 128 sweeps
     n, nb = 2047, 16
     k = 2 * math.pi * (n + 1) / 10

@@ -13,6 +13,7 @@ constexpr int kFuseRows = 256;     // default output rows of a fused-sweep warp 
 // process and device by richm_operator_create).
 cudaError_t init_sweep_attributes();  // also the fused kernels' (init_fused_attributes)
 cudaError_t init_fused_attributes();
+cudaError_t init_ssor_attributes();
 
 // One forward sweep (see sweep.cu). `a == nullptr`: no momentum (xp unused);
 // `at == nullptr`: at = a. `active`: per-instance flags or nullptr (all active).

@@ -393,9 +393,15 @@ static richm_status cycle_t(richm_solver* S, long long k0, long long cycle) {
   int fre = 2;
   for (int k = 0; k < Sw; ++k) {
     const int kidx = (int)((k0 + k) % S->o.m);
-    RICHM_TRY(launch_sweep<T>(S->op, (const T*)S->E[cur], (const T*)S->E[prv], (const T*)S->rhs, (T*)S->E[fre],
-                              (const T*)S->w, (const T*)S->a, (const T*)S->at, S->o.m, kidx, S->o.precond,
-                              S->active, S->s));
+    if (S->o.precond == 2) {  // SSOR: the fourth state buffer holds the triangular solves' intermediate
+      RICHM_TRY(launch_ssor_sweep<T>(S->op, (const T*)S->E[cur], S->a ? (const T*)S->E[prv] : nullptr,
+                                     (const T*)S->rhs, (T*)S->E[3], (T*)S->E[fre], nullptr, (const T*)S->w,
+                                     (const T*)S->a, (const T*)S->at, S->o.m, kidx, S->o.relax, S->active, S->s));
+    } else {
+      RICHM_TRY(launch_sweep<T>(S->op, (const T*)S->E[cur], (const T*)S->E[prv], (const T*)S->rhs,
+                                (T*)S->E[fre], (const T*)S->w, (const T*)S->a, (const T*)S->at, S->o.m, kidx,
+                                S->o.precond, S->active, S->s));
+    }
     const int nf = prv;
     prv = cur;
     cur = fre;
@@ -475,7 +481,13 @@ static richm_status check_solve_opts(const richm_operator* op, const richm_solve
   RICHM_ARG(o->tol >= 0.0, "tol < 0");
   RICHM_ARG(o->inner == RICHM_F32 || o->inner == RICHM_F64 || o->inner == RICHM_BF16,
             "inner dtype must be RICHM_F32, RICHM_F64 or RICHM_BF16");
-  RICHM_ARG(o->precond == 0 || o->precond == 1, "precond must be 0 or 1");
+  RICHM_ARG(o->precond == 0 || o->precond == 1 || o->precond == 2, "precond must be 0, 1 or 2");
+  if (o->precond == 2) {
+    RICHM_ARG(o->relax > 0.0 && o->relax < 2.0, "SSOR relaxation factor %g outside (0, 2)", o->relax);
+    RICHM_ARG(o->fuse == 0 || o->fuse == 1, "SSOR sweeps run one per launch (fuse 0 or 1)");
+    if (o->inner != RICHM_F32 && o->inner != RICHM_F64)
+      return set_error(RICHM_ERR_UNSUPPORTED, "SSOR preconditioning takes an FP32 or FP64 inner state");
+  }
   RICHM_ARG(o->fuse == 0 || o->fuse == 1 || o->fuse == 4 || o->fuse == 8, "fuse must be 0, 1, 4 or 8");
   RICHM_ARG(o->fuse <= 1 || (o->inner != RICHM_F64 && o->refine_every % o->fuse == 0),
             "fused sweeps need an FP32 or bfloat16 inner state and refine_every divisible by fuse");
@@ -523,7 +535,8 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   S->op = op;
   S->o = *o;
   if (S->o.fuse == 0) {
-    S->o.fuse = (o->inner != RICHM_F64 && o->refine_every % op->best_fuse == 0) ? op->best_fuse : 1;
+    S->o.fuse = (o->inner != RICHM_F64 && o->precond != 2 && o->refine_every % op->best_fuse == 0) ? op->best_fuse
+                                                                                                    : 1;
   }
   S->w = w;
   S->a = alpha;

@@ -18,6 +18,8 @@
 // chunks, carrying the last value. The backward solve is the mirror image (rows and
 // columns reversed, upper neighbours). The intermediate z lives in a padded buffer;
 // the backward pass overwrites it with s row by row (the row above reads s below).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -289,6 +291,365 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_kernel(const Ss
   }
 }
 
+// ---------------------------------------------------------------- single-chunk rows
+// Rows of at most 32 VW columns (FP32: n <= 511, FP64: n <= 255) are one chunk, so the
+// whole previous row of z (forward) or s (backward) and the three-row window of the
+// look-ahead iterate stay in registers, and the next row's inputs are loaded one row
+// ahead. With a single chunk the incoming value of the row is 0, so the scan needs only
+// the P parts: the multiplier of a lane's map is (-kappa)^VW (lanes holding columns
+// >= n have multiplier 0, but they only ever follow the interior lanes in the forward
+// direction, and in the backward direction the lanes after them contribute P = 0).
+
+// y of a row from x and x_prev values loaded as plain vectors (zeros outside 1..n).
+template <typename E, int VW>
+__device__ __forceinline__ void y_from(const E* xv, const E* xpv, E at, bool mom, RowVW<E, VW>& Y) {
+#pragma unroll
+  for (int e = 0; e < VW; ++e) Y.v[e] = mom ? xv[e] + at * (xv[e] - xpv[e]) : xv[e];
+  Y.l = __shfl_up_sync(0xffffffffu, Y.v[VW - 1], 1);
+  Y.r = __shfl_down_sync(0xffffffffu, Y.v[0], 1);
+}
+
+template <typename E, int VW>
+__device__ __forceinline__ void edges_zero(RowVW<E, VW>& Y, int lane) {
+  if (lane == 0) Y.l = E(0);   // column -1: boundary
+  if (lane == 31) Y.r = E(0);  // beyond the pitch
+}
+
+template <typename E, int VW>
+__device__ __forceinline__ void ld_row_or_zero(const E* base, int row, int n, int pitch, int c0, bool live, E* v) {
+  if (live && row >= 1 && row <= n) {
+    ld16<E, VW>(base + (long long)row * pitch + c0, v);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VW; ++e) v[e] = E(0);
+  }
+}
+
+namespace {
+
+constexpr int kRowPF = 3;              // row steps between issuing a row's copies and using it
+constexpr int kRowSlots = kRowPF + 1;  // ring slots per array
+
+__device__ __forceinline__ void row_cp16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void row_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void row_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(kRowPF - 1) : "memory"); }
+__device__ __forceinline__ void row_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+}  // namespace
+
+// Shared-memory rings of one warp: kRowSlots slots of three row arrays (each lane copies
+// and reads back only its own VW values, so no barrier is needed).
+template <typename E, int VW>
+struct RowRing {
+  static constexpr int ROW = 32 * VW * (int)sizeof(E);  // bytes of one array row
+  static constexpr int BYTES = 3 * kRowSlots * ROW;
+  unsigned char* base;
+  int lane;
+  __device__ E* at(int array, int slot) const {
+    return reinterpret_cast<E*>(base + (array * kRowSlots + slot) * ROW) + lane * VW;
+  }
+  // copy VW values of row `row` (zero-filled unless valid) into (array, slot)
+  __device__ void issue(int array, int slot, const E* src_base, int row, int pitch, int c0, bool valid) const {
+    const E* src = src_base + (long long)(valid ? row : 0) * pitch + c0;
+    unsigned char* dst = reinterpret_cast<unsigned char*>(at(array, slot));
+#pragma unroll
+    for (int q = 0; q < VW * (int)sizeof(E) / 16; ++q) row_cp16(dst + 16 * q, src + q * (16 / (int)sizeof(E)), valid);
+  }
+};
+
+// Per-warp state of the forward row pipeline.
+template <typename E, int VW>
+struct FwdRow {
+  RowVW<E, VW> Y[3];  // look-ahead iterate y of rows i-1, i, i+1 (slots rotate by phase)
+  RowVW<E, VW> Z;     // z of the previous row
+  E rp[VW];           // b/c - (A y)/c of the current row (formed one row ahead)
+};
+
+// rp = b/c - (A y)/c at the centre row C, with coefficients already divided by c.
+template <typename E, int VW>
+__device__ __forceinline__ void scaled_rhs(const RowVW<E, VW>& U, const RowVW<E, VW>& C, const RowVW<E, VW>& D,
+                                           const E* bv, E rc, E axr, E ayr, E d1r, E d2r, E* rp) {
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    E t = fma(-axr, left_of(C, e) + right_of(C, e), -C.v[e]);
+    t = fma(-ayr, U.v[e] + D.v[e], t);
+    t = fma(-d1r, right_of(D, e) + left_of(U, e), t);
+    t = fma(-d2r, right_of(U, e) + left_of(D, e), t);
+    rp[e] = fma(bv[e], rc, t);
+  }
+}
+
+// Row i of the forward solve at window phase PH (y(i) in slot PH): takes the inputs of
+// row i + 2 from the ring, solves row i and forms rp of row i + 1.
+template <typename E, int VW, int PH>
+__device__ __forceinline__ void fwd_row(int i, FwdRow<E, VW>& S, const RowRing<E, VW>& ring, const E* k, const E* mk,
+                                        const E* qd, E ky, E k1, E k2, E rc, E axr, E ayr, E d1r, E d2r, E ati,
+                                        bool mom, int lane, bool live, int pitch, E* zrow,
+                                        const E* xb, const E* xpb, const E* bb, int n, int c0) {
+  constexpr int SU = (PH + 2) % 3, SC = PH, SD = (PH + 1) % 3;
+  // inputs of step i + 1: x, x_prev of row i + 2 and b of row i + 1
+  row_wait();
+  const int sl = (i + 1) % kRowSlots;
+  E xv[VW], xpv[VW], bv[VW];
+  ld16<E, VW>(ring.at(0, sl), xv);
+  if (mom) ld16<E, VW>(ring.at(1, sl), xpv);
+  ld16<E, VW>(ring.at(2, sl), bv);
+  {
+    const int t = i + 1 + kRowPF;
+    const int sn = t % kRowSlots;
+    const bool vx = live && t + 1 <= n, vb = live && t >= 1 && t <= n;
+    ring.issue(0, sn, xb, t + 1, pitch, c0, vx);
+    if (mom) ring.issue(1, sn, xpb, t + 1, pitch, c0, vx);
+    ring.issue(2, sn, bb, t, pitch, c0, vb);
+    row_commit();
+  }
+  // row i: q = rp - (w/c) (ay z(i-1, j) + d1 z(i-1, j-1) + d2 z(i-1, j+1)), then the row recurrence
+  E q[VW];
+  E P = E(0);
+#pragma unroll
+  for (int e = 0; e < VW; ++e)  // z = 0 beyond the domain (mask 0)
+    q[e] = mk[e] * (S.rp[e] - (ky * S.Z.v[e] + k1 * left_of(S.Z, e) + k2 * right_of(S.Z, e)));
+  // y of row i + 2 into the slot of row i - 1, and rp of row i + 1 (independent of row i)
+  y_from<E, VW>(xv, xpv, ati, mom, S.Y[SU]);
+  edges_zero<E, VW>(S.Y[SU], lane);
+  E rpn[VW];
+  scaled_rhs<E, VW>(S.Y[SC], S.Y[SD], S.Y[SU], bv, rc, axr, ayr, d1r, d2r, rpn);
+#pragma unroll
+  for (int e = 0; e < VW; ++e) P = q[e] + k[e] * P;
+#pragma unroll
+  for (int d = 0; d < 5; ++d) {
+    const E Pp = __shfl_up_sync(0xffffffffu, P, 1 << d);
+    if (lane >= (1 << d)) P = P + qd[d] * Pp;
+  }
+  E zv = __shfl_up_sync(0xffffffffu, P, 1);
+  if (lane == 0) zv = E(0);
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    zv = q[e] + k[e] * zv;
+    S.Z.v[e] = zv;
+  }
+  if (live) st16<E, VW>(zrow, S.Z.v);
+  S.Z.l = __shfl_up_sync(0xffffffffu, S.Z.v[VW - 1], 1);
+  S.Z.r = __shfl_down_sync(0xffffffffu, S.Z.v[0], 1);
+  edges_zero<E, VW>(S.Z, lane);
+#pragma unroll
+  for (int e = 0; e < VW; ++e) S.rp[e] = rpn[e];
+}
+
+template <typename E, int VW>
+__global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_row_kernel(const SsorArgs<E> A) {
+  extern __shared__ __align__(16) unsigned char ssor_smem[];
+  const int lane = threadIdx.x & 31;
+  const int inst = blockIdx.x * kSsorWarps + (threadIdx.x >> 5);
+  if (inst >= A.batch) return;
+  if (A.active && A.active[inst] == 0) return;
+  const Inst& I = A.insts[inst];
+  const int n = I.n, pitch = I.pitch;
+  const E rc = E(1) / (E)I.c;
+  const E axr = (E)I.ax * rc, ayr = (E)I.ay * rc, d1r = (E)I.d1 * rc, d2r = (E)I.d2 * rc;
+  const E kx = A.relax * axr, ky = A.relax * ayr, k1 = A.relax * d1r, k2 = A.relax * d2r;
+  E qd[5];  // multipliers of 2^d consecutive lanes' maps
+  {
+    E q = E(1);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) q *= -kx;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      qd[d] = q;
+      q *= q;
+    }
+  }
+  const int ci = inst * A.m + A.kidx;
+  const E ati = A.a ? (A.at ? A.at[ci] : A.a[ci]) : E(0);
+  const bool mom = A.xp != nullptr && ati != E(0);
+  const E* xb = A.x + I.off;
+  const E* xpb = A.xp ? A.xp + I.off : xb;
+  const E* bb = A.b + I.off;
+  E* zb = A.z + I.off;
+  const int c0 = lane * VW;
+  const bool live = c0 < pitch;
+  E k[VW], mk[VW];  // recurrence coefficient and mask per column: 0 beyond the domain (z = 0 there)
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    mk[e] = (c0 + e < n) ? E(1) : E(0);
+    k[e] = -kx * mk[e];
+  }
+  RowRing<E, VW> ring{ssor_smem + (threadIdx.x >> 5) * RowRing<E, VW>::BYTES, lane};
+  // step t (0..n) brings x and x_prev of row t + 1 and b of row t
+  auto issue = [&](int t) {
+    const int sl = t % kRowSlots;
+    const bool vx = live && t + 1 <= n, vb = live && t >= 1 && t <= n;
+    ring.issue(0, sl, xb, t + 1, pitch, c0, vx);
+    if (mom) ring.issue(1, sl, xpb, t + 1, pitch, c0, vx);
+    ring.issue(2, sl, bb, t, pitch, c0, vb);
+    row_commit();
+  };
+  FwdRow<E, VW> S;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) S.Z.v[e] = S.Y[2].v[e] = E(0);
+  S.Z.l = S.Z.r = S.Y[2].l = S.Y[2].r = E(0);
+#pragma unroll
+  for (int t = 0; t < kRowPF; ++t) issue(t);
+  E xv[VW], xpv[VW], bv[VW];
+  row_wait();  // step 0: x, x_prev of row 1
+  ld16<E, VW>(ring.at(0, 0), xv);
+  if (mom) ld16<E, VW>(ring.at(1, 0), xpv);
+  y_from<E, VW>(xv, xpv, ati, mom, S.Y[0]);
+  edges_zero<E, VW>(S.Y[0], lane);
+  issue(kRowPF);
+  row_wait();  // step 1: x, x_prev of row 2, b of row 1
+  ld16<E, VW>(ring.at(0, 1), xv);
+  if (mom) ld16<E, VW>(ring.at(1, 1), xpv);
+  ld16<E, VW>(ring.at(2, 1), bv);
+  y_from<E, VW>(xv, xpv, ati, mom, S.Y[1]);
+  edges_zero<E, VW>(S.Y[1], lane);
+  issue(kRowPF + 1);
+  scaled_rhs<E, VW>(S.Y[2], S.Y[0], S.Y[1], bv, rc, axr, ayr, d1r, d2r, S.rp);
+  // the loop consumed steps 0 and 1; fwd_row(i) consumes step i + 1 and issues step i + 1 + PF
+  for (int i = 1; i <= n; i += 3) {
+    fwd_row<E, VW, 0>(i, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, pitch,
+                      zb + (long long)i * pitch + c0, xb, xpb, bb, n, c0);
+    if (i + 1 > n) break;
+    fwd_row<E, VW, 1>(i + 1, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, pitch,
+                      zb + (long long)(i + 1) * pitch + c0, xb, xpb, bb, n, c0);
+    if (i + 2 > n) break;
+    fwd_row<E, VW, 2>(i + 2, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, pitch,
+                      zb + (long long)(i + 2) * pitch + c0, xb, xpb, bb, n, c0);
+  }
+  row_wait_all();
+}
+
+template <typename E, int VW>
+__global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_row_kernel(const SsorArgs<E> A) {
+  extern __shared__ __align__(16) unsigned char ssor_smem[];
+  const int lane = threadIdx.x & 31;
+  const int inst = blockIdx.x * kSsorWarps + (threadIdx.x >> 5);
+  if (inst >= A.batch) return;
+  if (A.active && A.active[inst] == 0) return;
+  const Inst& I = A.insts[inst];
+  const int n = I.n, pitch = I.pitch;
+  const E c = (E)I.c, ax = (E)I.ax, ay = (E)I.ay, d1 = (E)I.d1, d2 = (E)I.d2;
+  const E rc = E(1) / c;
+  const E kx = A.relax * ax * rc, ky = A.relax * ay * rc, k1 = A.relax * d1 * rc, k2 = A.relax * d2 * rc;
+  E qd[5];
+  {
+    E q = E(1);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) q *= -kx;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      qd[d] = q;
+      q *= q;
+    }
+  }
+  const int ci = inst * A.m + A.kidx;
+  const E wi = A.w[ci] * A.relax * (E(2) - A.relax);
+  const E ai = A.a ? A.a[ci] : E(0);
+  const bool mom = A.xp != nullptr;
+  const E* xb = A.x + I.off;
+  const E* xpb = A.xp ? A.xp + I.off : xb;
+  const E* zb = A.z + I.off;
+  E* ox = A.out_x + I.off;
+  E* oxp = A.out_xp ? A.out_xp + I.off : nullptr;
+  const int c0 = lane * VW;
+  const bool live = c0 < pitch;
+  E zero[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) zero[e] = E(0);
+  if (live) {  // the output's halo rows (the buffer may come uninitialised from a rotation)
+    st16<E, VW>(ox + c0, zero);
+    st16<E, VW>(ox + (long long)(n + 1) * pitch + c0, zero);
+    if (oxp) {
+      st16<E, VW>(oxp + c0, zero);
+      st16<E, VW>(oxp + (long long)(n + 1) * pitch + c0, zero);
+    }
+  }
+  E k[VW], mk[VW];  // recurrence coefficient and mask per column: 0 beyond the domain
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    mk[e] = (c0 + e < n) ? E(1) : E(0);
+    k[e] = -kx * mk[e];
+  }
+  RowRing<E, VW> ring{ssor_smem + (threadIdx.x >> 5) * RowRing<E, VW>::BYTES, lane};
+  // step t (n down to 1) brings z, x and x_prev of row t into slot (n - t) mod slots
+  auto issue = [&](int t) {
+    const int sl = (n - t) % kRowSlots;
+    const bool v = live && t >= 1;
+    ring.issue(0, sl, zb, t, pitch, c0, v);
+    ring.issue(1, sl, xb, t, pitch, c0, v);
+    if (mom) ring.issue(2, sl, xpb, t, pitch, c0, v);
+    row_commit();
+  };
+  RowVW<E, VW> SD;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) SD.v[e] = E(0);
+  SD.l = SD.r = E(0);
+#pragma unroll
+  for (int t = 0; t < kRowPF; ++t) issue(n - t);
+  for (int i = n; i >= 1; --i) {
+    const int sl = (n - i) % kRowSlots;
+    row_wait();
+    E zc[VW], xv[VW], xpv[VW];
+    ld16<E, VW>(ring.at(0, sl), zc);
+    ld16<E, VW>(ring.at(1, sl), xv);
+    if (mom) ld16<E, VW>(ring.at(2, sl), xpv);
+    issue(i - kRowPF);
+    E t[VW];
+    E P = E(0);
+#pragma unroll
+    for (int e = VW - 1; e >= 0; --e) {
+      t[e] = mk[e] * (zc[e] - (ky * SD.v[e] + k1 * right_of(SD, e) + k2 * left_of(SD, e)));
+      P = t[e] + k[e] * P;
+    }
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      const E Pp = __shfl_down_sync(0xffffffffu, P, 1 << d);
+      if (lane + (1 << d) < 32) P = P + qd[d] * Pp;
+    }
+    E sv = __shfl_down_sync(0xffffffffu, P, 1);
+    if (lane == 31) sv = E(0);
+#pragma unroll
+    for (int e = VW - 1; e >= 0; --e) {
+      sv = t[e] + k[e] * sv;
+      SD.v[e] = sv;
+    }
+    if (live) {
+      const long long o = (long long)i * pitch + c0;
+      E xn[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) xn[e] = xv[e] + ai * (mom ? xv[e] - xpv[e] : E(0)) + wi * SD.v[e];
+      st16<E, VW>(ox + o, xn);
+      if (oxp) st16<E, VW>(oxp + o, xv);
+    }
+    SD.l = __shfl_up_sync(0xffffffffu, SD.v[VW - 1], 1);
+    SD.r = __shfl_down_sync(0xffffffffu, SD.v[0], 1);
+    edges_zero<E, VW>(SD, lane);
+  }
+  row_wait_all();
+}
+
+// The row kernels' rings exceed the default 48 KB of dynamic shared memory per block.
+template <typename E>
+static cudaError_t ssor_row_attributes() {
+  constexpr int VW = SsorVW<E>::v;
+  const int bytes = RowRing<E, VW>::BYTES * kSsorWarps;
+  cudaError_t e = cudaFuncSetAttribute(ssor_forward_row_kernel<E, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ssor_backward_row_kernel<E, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+cudaError_t init_ssor_attributes() {
+  cudaError_t e = ssor_row_attributes<float>();
+  if (e == cudaSuccess) e = ssor_row_attributes<double>();
+  return e;
+}
+
 template <typename E>
 richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, const E* b, E* z, E* out_x, E* out_xp,
                                const E* w, const E* a, const E* at, int m, int kidx, double relax, const int* active,
@@ -298,6 +659,16 @@ richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, cons
   SsorArgs<E> A{op->d_inst, op->batch, x, a ? xp : nullptr, b, z, out_x, a ? out_xp : nullptr,
                 w, a, at, m, kidx, (E)relax, active};
   const int blocks = (op->batch + kSsorWarps - 1) / kSsorWarps;
+  int max_pitch = 0;
+  for (const Inst& I : op->h_inst) max_pitch = std::max(max_pitch, I.pitch);
+  if (max_pitch <= 32 * VW) {  // every row is one chunk
+    const size_t smem = (size_t)RowRing<E, VW>::BYTES * kSsorWarps;
+    ssor_forward_row_kernel<E, VW><<<blocks, kSsorWarps * 32, smem, s>>>(A);
+    RICHM_LAUNCH_CHECK("SSOR forward solve");
+    ssor_backward_row_kernel<E, VW><<<blocks, kSsorWarps * 32, smem, s>>>(A);
+    RICHM_LAUNCH_CHECK("SSOR backward solve");
+    return RICHM_OK;
+  }
   ssor_forward_kernel<E, VW><<<blocks, kSsorWarps * 32, 0, s>>>(A);
   RICHM_LAUNCH_CHECK("SSOR forward solve");
   ssor_backward_kernel<E, VW><<<blocks, kSsorWarps * 32, 0, s>>>(A);

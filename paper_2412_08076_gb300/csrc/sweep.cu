@@ -231,6 +231,7 @@ cudaError_t init_sweep_attributes() {
   if (e == cudaSuccess) e = sweep1_attributes<cplx<float>>();
   if (e == cudaSuccess) e = sweep1_attributes<cplx<double>>();
   if (e == cudaSuccess) e = init_fused_attributes();
+  if (e == cudaSuccess) e = init_ssor_attributes();
   return e;
 }
 

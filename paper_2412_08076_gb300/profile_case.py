@@ -63,7 +63,7 @@ def record_traffic(report: str, kind: str, unknowns: int, root: str) -> float:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["sweep", "cycle", "adjoint", "helmholtz"], default="sweep")
+    ap.add_argument("--what", choices=["sweep", "cycle", "adjoint", "helmholtz", "ssor"], default="sweep")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--n", type=int, default=511)
     ap.add_argument("--sweeps", type=int, default=6)
@@ -103,6 +103,13 @@ def main(argv=None):
         b = op.pack(dense.float(), richm.F32)
         x, xp = op.zeros(richm.F32), op.zeros(richm.F32)
         op.apply_sweeps(richm.F32, x, xp, b, w, a, None, K=args.sweeps, m=m, fuse=args.fuse)
+    elif args.what == "ssor":
+        # SSOR-preconditioned NAG sweeps (B^{-1} A has its spectrum in (0, 1])
+        b = op.pack(dense.float(), richm.F32)
+        x, xp = op.zeros(richm.F32), op.zeros(richm.F32)
+        ws = torch.tensor(meta_mod.chebyshev_unit_weights(m)[None, :].repeat(args.batch, 0), dtype=torch.float32,
+                          device="cuda")
+        op.apply_sweeps(richm.F32, x, xp, b, ws, a, None, K=args.sweeps, m=m, precond=2, relax=1.5)
     elif args.what == "cycle":
         b = op.pack(dense, richm.F64)
         x = op.zeros(richm.F64)

@@ -12,8 +12,11 @@ from paper_2412_08076_gb300 import richm
 
 pytestmark = pytest.mark.gpu
 
-# one and several row chunks (512 columns per chunk in FP32, 256 in FP64), ragged sizes
+# one and several row chunks (512 columns per chunk in FP32, 256 in FP64), ragged sizes;
+# a batch whose rows all fit one chunk runs the register-resident row kernels, any wider
+# instance sends the whole batch through the chunked kernels
 SIZES = [1, 2, 3, 5, 17, 31, 64, 130, 255, 300, 513]
+SIZES_ONE_CHUNK = {"f32": [1, 2, 5, 31, 64, 130, 300, 511], "f64": [1, 2, 5, 31, 64, 130, 255]}
 
 
 def _instances(seed, sizes):
@@ -63,8 +66,10 @@ def _case(dtype, variant, relax, K, k_start=2, sizes=SIZES, wscale=1.0):
 
 @pytest.mark.parametrize("variant", ["richardson", "nag", "nagex"])
 @pytest.mark.parametrize("relax", [1.0, 1.6])
-def test_fp64_ssor_sweeps_match_oracle(variant, relax):
-    for t, g, ref, gp, refp in _case(richm.F64, variant, relax, K=3):
+@pytest.mark.parametrize("chunks", ["one", "several"])
+def test_fp64_ssor_sweeps_match_oracle(variant, relax, chunks):
+    sizes = SIZES_ONE_CHUNK["f64"] if chunks == "one" else SIZES
+    for t, g, ref, gp, refp in _case(richm.F64, variant, relax, K=3, sizes=sizes):
         scale = max(np.abs(ref).max(), 1e-300)
         assert np.abs(g - ref).max() <= 1e-12 * scale, (t, np.abs(g - ref).max() / scale)
         if gp is not None:
@@ -72,10 +77,12 @@ def test_fp64_ssor_sweeps_match_oracle(variant, relax):
 
 
 @pytest.mark.parametrize("variant", ["richardson", "nag"])
-def test_fp32_ssor_sweeps_within_1e5(variant):
+@pytest.mark.parametrize("chunks", ["one", "several"])
+def test_fp32_ssor_sweeps_within_1e5(variant, chunks):
     # damping weights (every mode of B^{-1} A contracts), two sweeps from the same
     # FP32-rounded state: FP32 rounding of the two triangular solves stays ~1e-6 relative
-    for t, g, ref, gp, refp in _case(richm.F32, variant, 1.2, K=2, wscale=0.7):
+    sizes = SIZES_ONE_CHUNK["f32"] if chunks == "one" else SIZES
+    for t, g, ref, gp, refp in _case(richm.F32, variant, 1.2, K=2, wscale=0.7, sizes=sizes):
         scale = max(np.abs(ref).max(), 1.0)
         assert np.abs(g - ref).max() <= 1e-5 * scale, (t, np.abs(g - ref).max() / scale)
 
@@ -97,3 +104,52 @@ def test_ssor_sweep_leaves_padding_zero_and_rejects_bad_arguments():
     for bad in (0.0, 2.0, -0.5):
         with pytest.raises(richm.RichmError):
             op.apply_sweeps(richm.F64, X, XP, B, w, a, K=1, m=3, precond=2, relax=bad)
+
+
+def _paper_instances(sizes, theta=math.pi / 10, eps=1e-6):
+    return [synth.AnisoInstance(eps, theta, n) for n in sizes]
+
+
+@pytest.mark.parametrize("inner", [richm.F32, richm.F64])
+def test_ssor_preconditioned_solve_to_1e10_checked_by_oracle(inner):
+    # eps = 1e-6, theta = pi/10 (the setting of the paper's SSOR tables); B^{-1} A has its
+    # spectrum in (0, 1], so the momentum-aware Chebyshev weights take the bound 1
+    from gpu_util import nag_weights
+    insts = _paper_instances([15, 31, 63])
+    op = make_op(insts)
+    w, a = nag_weights(np.ones(len(insts)), 16, beta=0.3)
+    bs = [synth.rhs_uniform(44, i, t.n) for i, t in enumerate(insts)]
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    opts = op.solve_opts(16, tol=1e-10, max_sweeps=200000, refine_every=64, inner=inner, precond=2, fuse=1,
+                         relax=1.0)
+    st, info = op.solve(B, X, coef(w, inner), coef(a, inner), None, opts)
+    assert st == richm.OK, info
+    xs = from_dev(op, X, richm.F64)
+    for i, t in enumerate(insts):
+        A = assemble_q1(t.n, t.eps, t.theta)
+        r = np.linalg.norm(bs[i].ravel() - A @ xs[i].ravel()) / np.linalg.norm(bs[i])
+        assert r <= 1e-10, (t, r)
+        assert abs(info[i][1] - r) <= 1e-3 * r + 1e-14
+
+
+def test_ssor_needs_fewer_sweeps_than_jacobi():
+    # the same NAG(16) weight construction on each preconditioned spectrum: (0, 1] for
+    # SSOR, (0, G / d] for Jacobi (d the diagonal, G the Gershgorin bound)
+    from gpu_util import nag_weights
+    insts = _paper_instances([31, 63])
+    op = make_op(insts)
+    G = np.array(op.gershgorin())
+    d = np.array([op.stencil(i)[0] for i in range(len(insts))])
+    bs = [synth.rhs_uniform(45, i, t.n) for i, t in enumerate(insts)]
+    B = to_dev(op, bs, richm.F64)
+    sweeps = {}
+    for pc, bound in ((1, G / d), (2, np.ones(len(insts)))):
+        w, a = nag_weights(bound, 16, beta=0.3)
+        X = op.zeros(richm.F64)
+        opts = op.solve_opts(16, tol=1e-8, max_sweeps=400000, refine_every=64, inner=richm.F64, precond=pc, fuse=1,
+                             relax=1.0)
+        st, info = op.solve(B, X, coef(w, richm.F64), coef(a, richm.F64), None, opts)
+        assert st == richm.OK, (pc, info)
+        sweeps[pc] = [s for s, _, _ in info]
+    assert all(s2 < s1 for s1, s2 in zip(sweeps[1], sweeps[2])), sweeps
