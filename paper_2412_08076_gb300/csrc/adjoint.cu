@@ -10,6 +10,8 @@
 // stencil twice (to d lam and to y), so each step streams lam, c, x_k, x_{k-1}, b
 // once. States between checkpoints are recomputed from the checkpoint by the
 // forward kernel, which is deterministic, so the recomputation is bitwise exact.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -113,6 +115,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     apply_q1<T, VW, T>(YU, YC, YD, sc, sax, say, sd1, sd2, Ay);
     apply_q1<T, VW, T>(LU, LC, LD, sc, sax, say, sd1, sd2, Al);
     VecN<T, VW> Lo, Co;
+    // FP32 state: the row's few products are summed in FP32 and the row sums in FP64
+    // (GB300's FP64 pipe would otherwise bound the kernel); FP64 state sums in FP64
+    T rw = T(0), ra = T(0), rat = T(0);
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       const bool ok = (c0 + e) < n;
@@ -123,15 +128,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       T ln = MOM ? (T(1) + ai) * l - (T(1) + ati) * q + Cv.v[e] : l - q;
       T cn = MOM ? -ai * l + ati * q : T(0);
       if (ok) {
-        s_w += (double)l * (double)dr;
-        if (MOM) {
-          s_a += (double)l * (double)v;
-          s_at += (double)q * (double)v;
+        if constexpr (std::is_same<T, float>::value) {
+          rw = fmaf(l, dr, rw);
+          if (MOM) {
+            ra = fmaf(l, v, ra);
+            rat = fmaf(q, v, rat);
+          }
+        } else {
+          s_w += (double)l * (double)dr;
+          if (MOM) {
+            s_a += (double)l * (double)v;
+            s_at += (double)q * (double)v;
+          }
         }
       }
       if (final_step) ln = ln + cn;
       Lo.v[e] = ok ? ln : T(0);
       Co.v[e] = ok ? cn : T(0);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      s_w += f32_to_f64_exact(rw);
+      if (MOM) {
+        s_a += f32_to_f64_exact(ra);
+        s_at += f32_to_f64_exact(rat);
+      }
     }
     if (live) {
       stv<T, VW>(lam_out + ro, Lo);
