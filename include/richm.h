@@ -386,12 +386,15 @@ richm_status richm_adam_step(float* params, const float* grads, float* m1, float
 
 /* ------------------------------------------------------------------ two-level step */
 
-/* Workspace bytes for richm_fourier_correction (cuFFT work + spectra). */
+/* Workspace bytes for richm_fourier_correction: the real residual, its half spectrum
+ * (n x (n/2 + 1) per instance) and the cuFFT work area. */
 richm_status richm_fourier_workspace(const richm_operator* op, size_t* bytes);
 
 /* Fourier-domain correction of the FNS iteration (eqs. 19-20 with T = I):
  *   x += Re( IFFT2( S .* FFT2(b - A x) ) ),
- * forward transform unnormalised, inverse scaled by 1/n^2. Every instance of the
+ * forward transform unnormalised, inverse scaled by 1/n^2 (computed with real-to-complex
+ * and complex-to-real transforms and the symmetrised symbol (S(k) + conj S(-k)) / 2,
+ * which gives the same real part). Every instance of the
  * operator must be Q1 with the same n. dtype RICHM_F32. symbol: device complex64
  * [n][n] shared by the batch. x, b: padded. */
 richm_status richm_fourier_correction(richm_operator* op, richm_dtype dtype, void* x, const void* b,

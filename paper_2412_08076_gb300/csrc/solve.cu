@@ -762,7 +762,7 @@ richm_status richm_refine(richm_operator* op, double* x, const double* b, void* 
           nullptr);
       RICHM_LAUNCH_CHECK("refine update");
     }
-    RICHM_TRY((launch_residual_to<double, float>(op, x, b, (float*)rhs_out, partials, nullptr, s, false)));
+    RICHM_TRY((launch_residual_to<double, float>(op, x, b, (float*)rhs_out, partials, nullptr, s, rel == nullptr)));
   } else {
     if (e) {
       refine_update_kernel<double><<<blocks, kWarpsPerBlock * 32, 0, s>>>(
@@ -770,8 +770,11 @@ richm_status richm_refine(richm_operator* op, double* x, const double* b, void* 
           (double*)e_prev, nullptr);
       RICHM_LAUNCH_CHECK("refine update");
     }
-    RICHM_TRY((launch_residual_to<double, double>(op, x, b, (double*)rhs_out, partials, nullptr, s, false)));
+    RICHM_TRY((launch_residual_to<double, double>(op, x, b, (double*)rhs_out, partials, nullptr, s,
+                                                  rel == nullptr)));
   }
+  // without rel the residual skips |b|^2 (the refinement form) and no norm is formed
+  if (!rel) return RICHM_OK;
   return launch_norm_reduce(op, 2, partials, nullptr, nullptr, rel, s);
 }
 
