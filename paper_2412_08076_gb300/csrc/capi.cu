@@ -50,7 +50,8 @@ richm_status get_tiles(richm_operator* op, int tw, int rows, const TileMap** out
         for (int tx = 0; tx < tx_n; ++tx) h.push_back(Tile{b, ty, tx, 0});
     } else {  // fused tiles: 128 columns overlapping by 2*TL at interior edges, and a tail
       int full = 0, half = 0;
-      fused_columns(I.n, -tw, &full, &half);
+      if (tw <= -100) fused_columns(I.n, -tw - 100, &full, &half, 64);  // complex: two columns per lane
+      else fused_columns(I.n, -tw, &full, &half);
       for (int ty = 0; ty < ty_n; ++ty)
         for (int tx = 0; tx < full; ++tx) h.push_back(Tile{b, ty, tx, 0});
       if (half)

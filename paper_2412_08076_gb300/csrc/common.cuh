@@ -112,13 +112,14 @@ struct richm_operator {
 namespace richm {
 
 // Column tiling of the TL-sweep fused kernel for an instance of n columns: `full`
-// warp-wide tiles of 128 columns at stride 128 - 2 TL, and, when the rest fits, one
-// 64-column tail tile at the same stride (`half` = 1). Tail tiles of two row bands
-// of an instance share one warp (16 lanes each).
-inline void fused_columns(int n, int TL, int* full, int* half) {
-  const int stride = 128 - 2 * TL;
-  const int t = 1 + (n > 128 ? (n - 128 + stride - 1) / stride : 0);
-  if (t > 1 && n <= (t - 1) * stride + 64) {
+// warp-wide tiles of `width` columns (128 real, 64 complex) at stride width - 2 TL,
+// and, when the rest fits, one tail tile of width / 2 columns at the same stride
+// (`half` = 1). Tail tiles of two row bands of an instance share one warp (16 lanes
+// each).
+inline void fused_columns(int n, int TL, int* full, int* half, int width = 128) {
+  const int stride = width - 2 * TL;
+  const int t = 1 + (n > width ? (n - width + stride - 1) / stride : 0);
+  if (t > 1 && n <= (t - 1) * stride + width / 2) {
     *full = t - 1;
     *half = 1;
   } else {
@@ -136,6 +137,7 @@ inline long long fused_warps(int n, int TL, int bands) {
 
 // Tile list for tiles of `tw` elements x `rows` rows (cached in the operator);
 // tw = -TL gives the overlapping 128-column tiles of the TL-sweep fused kernel
+// (tw = -100 - TL: the 64-column tiles of the complex fused kernel)
 // (Tile.pad = 0: a full tile; pad > 0: a pair of tail tiles at column block tx, row
 // band ty in lanes 0-15 and row band pad - 2 in lanes 16-31, none if pad == 1).
 richm_status get_tiles(richm_operator* op, int tw, int rows, const TileMap** out);

@@ -35,6 +35,13 @@ richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, cons
                                 int kidx0, int precond, const int* active, cudaStream_t s, int rows = 0,
                                 bool absorb = false);
 
+// TL (4) fused complex64 sweeps of a Helmholtz batch (no preconditioner), same
+// conventions as launch_sweep_fused.
+richm_status launch_sweep_fused_cx(richm_operator* op, int TL, const cplx<float>* x, const cplx<float>* xp,
+                                   const cplx<float>* b, cplx<float>* out_x, cplx<float>* out_xp, const float* w,
+                                   const float* a, const float* at, int m, int kidx0, const int* active,
+                                   cudaStream_t s, int rows = 0);
+
 // The same with bfloat16 state (x, x_prev and the outputs); b and the arithmetic are FP32.
 richm_status launch_sweep_fused_bf16(richm_operator* op, int TL, const __nv_bfloat16* x, const __nv_bfloat16* xp,
                                      const float* b, __nv_bfloat16* out_x, __nv_bfloat16* out_xp, const float* w,

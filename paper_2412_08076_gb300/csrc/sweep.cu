@@ -281,6 +281,20 @@ static richm_status apply_sweeps_t(richm_operator* op, E* x, E* xp, const E* b, 
       }
     }
   }
+  if constexpr (std::is_same<E, cplx<float>>::value) {
+    // complex Helmholtz: fused passes of 4 sweeps (no preconditioner)
+    const int TL = (o->fuse == 4 && o->precond == 0) ? 4 : 0;
+    for (; TL > 0 && k + TL <= K; k += TL) {
+      E* ox = (cur == x) ? W0 : x;
+      E* oxp = (cur == x) ? W1 : xp;
+      if (!mom && oxp == nullptr) oxp = W1;
+      const int kidx0 = (int)(((long long)o->k_start + k) % o->m);
+      RICHM_TRY(launch_sweep_fused_cx(op, TL, cur, prev, b, ox, oxp, (const float*)w, (const float*)a,
+                                      (const float*)at, o->m, kidx0, nullptr, s));
+      cur = ox;
+      prev = mom ? oxp : nullptr;
+    }
+  }
   if constexpr (std::is_same<E, float>::value) {
     // fused passes of TL sweeps: (cur, prev) -> the other pair of buffers
     const int TL = (o->fuse == 4 || o->fuse == 8) ? o->fuse : 0;
@@ -462,7 +476,11 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
   if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
   richm_sweep_opts o = *opts;
-  if (o.fuse == 0) o.fuse = (dtype == RICHM_F32 || dtype == RICHM_BF16) ? op->best_fuse : 1;
+  if (o.fuse == 0) {
+    if (dtype == RICHM_F32 || dtype == RICHM_BF16) o.fuse = op->best_fuse;
+    else if (dtype == RICHM_C64 && o.precond == 0) o.fuse = 4;
+    else o.fuse = 1;
+  }
   if (o.precond == 2) o.fuse = 1;  // the triangular solves cannot be fused in time
   opts = &o;
   switch (dtype) {

@@ -398,6 +398,195 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------- complex Helmholtz
+// The same row pipeline for the 5-point complex Helmholtz operator (eq. 22) with a
+// first-order absorbing (or Dirichlet) boundary and complex64 state. A lane holds two
+// complex columns (16 bytes), so a warp tile is 64 columns wide (tails 32); the ring
+// and row bookkeeping of FusedCtx run in float units (pitch and columns doubled). Only
+// the centre row of a level's window needs cross-lane neighbours. The diagonal of a row
+// next to the boundary gains the absorbing term per missing neighbour: rows 1 and n
+// through the level's row index, columns 0 and n - 1 through per-lane column terms.
+// Columns from n on stay zero through a zero neighbour coefficient, rows outside 1..n
+// through the zero weight, as in the Q1 kernel.
+struct CxCoef {
+  float nb[2];        // neighbour coefficient per column of this lane (0 from column n on)
+  float dre[2], dim[2];  // diagonal of an interior row per column (with the column terms)
+  float abre, abim;   // added to the diagonal per missing row neighbour
+};
+
+template <int TL, bool MOM, bool NAGF, int PH, int PW>
+__device__ __forceinline__ void fused_step_cx(int rr, const FusedCtx<float>& c, const CxCoef& k,
+                                              FusedState<TL>& st, const float* wl, const float* al,
+                                              const float* atl) {
+  using R = FusedRings<float, TL>;
+  constexpr int SD = PH, SU = (PH + 1) % 3, SC = (PH + 2) % 3;
+  issue_row<float, TL, MOM>(c, rr + kPrefetch);
+  cp_async_wait<kPrefetch>();
+  float x0[4], xm[4];
+  {
+    const int xs = ring_slot(rr, R::NS);
+    st4_to_float(reinterpret_cast<const float*>(c.ring + xs * R::XROW) + c.lane * 4, x0);
+    if (MOM) st4_to_float(reinterpret_cast<const float*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, xm);
+    else xm[0] = xm[1] = xm[2] = xm[3] = 0.f;
+  }
+  float newx[TL + 1][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) newx[0][e] = x0[e];
+  const unsigned char* bstep = c.ring + R::BOFF + (ring_slot(rr, R::NB) + R::NB) * 512 + c.lane * 16;
+#pragma unroll
+  for (int s = 1; s <= TL; ++s) {
+    const int row = rr - s;
+    const float4 B4 = *reinterpret_cast<const float4*>(bstep - s * 512);
+    const float Bv[4] = {B4.x, B4.y, B4.z, B4.w};
+    const float ws = ((unsigned)(row - c.rlo) < (unsigned)c.n) ? wl[s] : 0.f;
+    const float rm = (float)((row == c.rlo) + (row == c.rlo + c.n - 1));  // missing row neighbours
+    float* Yn = st.Y[s][SD];
+    float vn[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float xs1 = newx[s - 1][e];
+      const float xs2 = (s == 1) ? xm[e] : st.prevx[1 - PW][s - 2][e];
+      vn[e] = MOM ? xs1 - xs2 : 0.f;
+      Yn[e] = MOM ? fmaf(atl[s], vn[e], xs1) : xs1;
+    }
+    const float* YU = st.Y[s][SU];
+    const float* YC = st.Y[s][SC];
+    // complex neighbours of the centre row across lanes (zero beyond the tile's lanes)
+    const float lre = c.ml * __shfl_up_sync(0xffffffffu, YC[2], 1);
+    const float lim = c.ml * __shfl_up_sync(0xffffffffu, YC[3], 1);
+    const float rre = c.mr * __shfl_down_sync(0xffffffffu, YC[0], 1);
+    const float rim = c.mr * __shfl_down_sync(0xffffffffu, YC[1], 1);
+    float ry[4];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float yre = YC[2 * e], yim = YC[2 * e + 1];
+      const float wre = e == 0 ? lre : YC[0], wim = e == 0 ? lim : YC[1];
+      const float ere = e == 1 ? rre : YC[2], eim = e == 1 ? rim : YC[3];
+      const float sre = (wre + ere) + (YU[2 * e] + Yn[2 * e]);
+      const float sim = (wim + eim) + (YU[2 * e + 1] + Yn[2 * e + 1]);
+      const float dre = fmaf(rm, k.abre, k.dre[e]), dim = fmaf(rm, k.abim, k.dim[e]);
+      ry[2 * e] = fmaf(-k.nb[e], sre, fmaf(dim, yim, fmaf(-dre, yre, Bv[2 * e])));
+      ry[2 * e + 1] = fmaf(-k.nb[e], sim, fmaf(-dim, yre, fmaf(-dre, yim, Bv[2 * e + 1])));
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (!MOM || NAGF) {
+        newx[s][e] = fmaf(ws, ry[e], YC[e]);
+      } else {
+        newx[s][e] = fmaf(ws, ry[e], fmaf(al[s], st.vc[s][e], st.xc[s][e]));
+        st.xc[s][e] = newx[s - 1][e];
+        st.vc[s][e] = vn[e];
+      }
+    }
+  }
+  if (c.store_cols) {
+    const int ra = rr - TL, rb = rr - TL + 1;
+    if (ra >= c.r0 && ra <= c.shi) float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, newx[TL]);
+    if (MOM && rb >= c.r0 && rb <= c.shi) float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, newx[TL - 1]);
+  }
+  if (MOM) {
+#pragma unroll
+    for (int s = 0; s + 2 <= TL; ++s)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) st.prevx[PW][s][e] = newx[s][e];
+  }
+}
+
+template <int TL, bool MOM, bool NAGF>
+__global__ void __launch_bounds__(kFuseWarps * 32, 3) sweepT_cx_kernel(const SweepTArgs A) {
+  constexpr int STRIDE = 64 - 2 * TL;
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kFuseWarps + (threadIdx.x >> 5);
+  if (wt >= A.ntiles) return;
+  const Tile t = A.tiles[wt];
+  if (A.active && A.active[t.inst] == 0) return;
+  const Inst& I = A.insts[t.inst];
+  float wl[TL + 1], al[TL + 1], atl[TL + 1];
+#pragma unroll
+  for (int s = 1; s <= TL; ++s) {
+    const int ci = t.inst * A.m + (A.kidx0 + s - 1) % A.m;
+    wl[s] = A.w[ci];
+    al[s] = MOM ? A.a[ci] : 0.f;
+    atl[s] = MOM ? (A.at ? A.at[ci] : al[s]) : 0.f;
+  }
+  const int n = I.n;
+  const bool tail = t.pad > 0;
+  const int tlane = tail ? (lane & 15) : lane;
+  const bool idle = tail && lane >= 16 && t.pad == 1;
+  const int band = (tail && lane >= 16 && !idle) ? t.pad - 2 : t.ty;
+  const int dr = (band - t.ty) * A.rows;
+  const int cs = t.tx * STRIDE;         // first complex column of the tile
+  const int cc = cs + tlane * 2;        // this lane's first complex column
+  FusedCtx<float> c;
+  c.n = n;
+  c.pitch = 2 * I.pitch;                // float units
+  c.lane = lane;
+  c.c0 = 2 * cc;
+  c.live = cc < I.pitch && !idle;
+  c.ml = (tlane == 0) ? 0.f : 1.f;
+  c.mr = (tlane == (tail ? 15 : 31)) ? 0.f : 1.f;
+  CxCoef k;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int col = cc + e;
+    const float cm = (float)((col == 0) + (col == n - 1));
+    k.nb[e] = col < n ? (float)I.ax : 0.f;
+    k.dre[e] = (float)I.c + cm * (float)I.abc_re;
+    k.dim[e] = cm * (float)I.abc_im;
+  }
+  k.abre = (float)I.abc_re;
+  k.abim = (float)I.abc_im;
+  const bool last_tile = tail || (cs + 64 >= n);
+  const int clo = cs + (t.tx > 0 ? TL : 0);
+  const int chi = last_tile ? I.pitch : cs + 64 - TL;
+  c.store_cols = c.live && cc >= clo && cc + 2 <= chi;
+  c.r0 = t.ty * A.rows + 1;
+  const int r1 = min(c.r0 + dr + A.rows - 1, n);
+  c.rlo = 1 - dr;
+  c.vhi = min(r1 + TL, n) - dr;
+  c.shi = r1 - dr;
+  const int endA = min(c.r0 + A.rows - 1, n) + TL;
+  const int endB = (tail && t.pad > 1) ? min((t.pad - 2) * A.rows + A.rows, n) + TL - (t.pad - 2 - t.ty) * A.rows
+                                       : endA;
+  const int rend = max(endA, endB);
+  const long long off = 2 * (I.off + (long long)dr * I.pitch);
+  c.xb = reinterpret_cast<const float*>(A.x) + off;
+  c.xpb = reinterpret_cast<const float*>(MOM ? A.xp : A.x) + off;
+  c.bb = A.b + off;
+  c.ox = reinterpret_cast<float*>(A.out_x) + off;
+  c.oxp = MOM ? reinterpret_cast<float*>(A.out_xp) + off : nullptr;
+  c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<float, TL>::BYTES;
+  FusedState<TL> st;
+#pragma unroll
+  for (int s = 0; s <= TL; ++s) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) st.Y[s][q][e] = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) st.xc[s][e] = st.vc[s][e] = st.prevx[0][s][e] = st.prevx[1][s][e] = 0.f;
+  }
+  for (int q = 0; q < 2 * FusedRings<float, TL>::NB; ++q)
+    *reinterpret_cast<float4*>(c.ring + FusedRings<float, TL>::BOFF + q * 512 + lane * 16) =
+        make_float4(0.f, 0.f, 0.f, 0.f);
+  const int rstart = c.r0 - TL;
+#pragma unroll
+  for (int d = 0; d < kPrefetch; ++d) issue_row<float, TL, MOM>(c, rstart + d);
+  for (int rr = rstart; rr <= rend; rr += 3) {
+    fused_step_cx<TL, MOM, NAGF, 0, 0>(rr, c, k, st, wl, al, atl);
+    fused_step_cx<TL, MOM, NAGF, 1, 1>(rr + 1, c, k, st, wl, al, atl);
+    fused_step_cx<TL, MOM, NAGF, 2, 0>(rr + 2, c, k, st, wl, al, atl);
+    if (MOM) {
+#pragma unroll
+      for (int s = 0; s + 2 <= TL; ++s)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) st.prevx[1][s][e] = st.prevx[0][s][e];
+    }
+  }
+  cp_async_wait<0>();
+}
+
 template <typename ST, int TL>
 static cudaError_t fused_attributes_tl() {
   const int bytes = FusedRings<ST, TL>::BYTES * kFuseWarps;
@@ -424,7 +613,15 @@ static cudaError_t fused_attributes_tl() {
 
 // The fused kernels' rings can exceed the default 48 KB of dynamic shared memory.
 cudaError_t init_fused_attributes() {
-  cudaError_t e = fused_attributes_tl<float, 4>();
+  const int cx_bytes = FusedRings<float, 4>::BYTES * kFuseWarps;
+  cudaError_t e = cudaFuncSetAttribute(sweepT_cx_kernel<4, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       cx_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweepT_cx_kernel<4, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cx_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweepT_cx_kernel<4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             cx_bytes);
+  if (e == cudaSuccess) e = fused_attributes_tl<float, 4>();
   if (e == cudaSuccess) e = fused_attributes_tl<float, 8>();
   if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 4>();
   if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 8>();
@@ -472,6 +669,27 @@ richm_status launch_sweep_fused(richm_operator* op, int TL, const float* x, cons
                                 int kidx0, int precond, const int* active, cudaStream_t s, int rows, bool absorb) {
   return launch_fused_t<float>(op, TL, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, precond, active, s, rows,
                                absorb);
+}
+
+richm_status launch_sweep_fused_cx(richm_operator* op, int TL, const cplx<float>* x, const cplx<float>* xp,
+                                   const cplx<float>* b, cplx<float>* out_x, cplx<float>* out_xp, const float* w,
+                                   const float* a, const float* at, int m, int kidx0, const int* active,
+                                   cudaStream_t s, int rows) {
+  if (TL != 4) return set_error(RICHM_ERR_ARG, "complex fused sweeps take 4 sweeps per pass");
+  if (rows <= 0) rows = op->best_rows;
+  const TileMap* tm = nullptr;
+  RICHM_TRY(get_tiles(op, -100 - TL, rows, &tm));
+  SweepTArgs A{op->d_inst, tm->d_tiles, tm->ntiles, x, xp, reinterpret_cast<const float*>(b), out_x, out_xp,
+               w, a, at, m, kidx0, active, rows};
+  const int blocks = (tm->ntiles + kFuseWarps - 1) / kFuseWarps;
+  const size_t smem = (size_t)FusedRings<float, 4>::BYTES * kFuseWarps;
+  const bool mom = a != nullptr;
+  const bool nag = mom && at == nullptr;
+  if (nag) sweepT_cx_kernel<4, true, true><<<blocks, kFuseWarps * 32, smem, s>>>(A);
+  else if (mom) sweepT_cx_kernel<4, true, false><<<blocks, kFuseWarps * 32, smem, s>>>(A);
+  else sweepT_cx_kernel<4, false, false><<<blocks, kFuseWarps * 32, smem, s>>>(A);
+  RICHM_LAUNCH_CHECK("complex fused sweep");
+  return RICHM_OK;
 }
 
 richm_status launch_sweep_fused_bf16(richm_operator* op, int TL, const __nv_bfloat16* x, const __nv_bfloat16* xp,

@@ -163,6 +163,61 @@ def test_helmholtz_sweeps_match_oracle(dtype):
         assert rel <= tol, (sizes[i], rel)
 
 
+@pytest.mark.parametrize("variant", ["nag", "nagex", "richardson"])
+@pytest.mark.parametrize("kind", [richm.HELMHOLTZ_FD5_ABC, richm.HELMHOLTZ_FD5_DIRICHLET])
+def test_helmholtz_fused_passes_match_oracle(variant, kind):
+    # complex fused passes of 4 sweeps (64-column tiles, 32-column tails at 65..88
+    # columns, several tiles from 89 on), 32-row bands (pairs of tail tiles and an odd
+    # one), plus a one-sweep remainder
+    sizes = [5, 64, 70, 88, 150, 130]
+    ks = [helmholtz_wavenumber(n) for n in sizes]
+    op = richm.Operator([(kind, n, 1.0, 0.0, k) for n, k in zip(sizes, ks)])
+    op.set_tuning(4, 32)
+    m, K = 8, 9
+    ws = np.stack([synth.helmholtz_weights(m, 1.0 / (n + 1), seed=4) for n in sizes]).astype(np.float32)
+    a = np.full_like(ws, 0.3)
+    at = None
+    if variant == "richardson":
+        a = None
+    elif variant == "nagex":
+        at = np.full_like(ws, 0.1)
+    x0 = [(0.1 * (synth.rhs_uniform(51, i, n) + 1j * synth.rhs_uniform(52, i, n))).astype(np.complex64)
+          for i, n in enumerate(sizes)]
+    v0 = [(0.01 * (synth.rhs_uniform(53, i, n) - 1j * synth.rhs_uniform(54, i, n))).astype(np.complex64)
+          for i, n in enumerate(sizes)]
+    xp0 = [(x - v).astype(np.complex64) for x, v in zip(x0, v0)]
+    bs = [synth.point_source_rhs(n, 1, seed=5 + i)[0].astype(np.complex64) for i, n in enumerate(sizes)]
+    X, XP, B = to_dev(op, x0, richm.C64), to_dev(op, xp0, richm.C64), to_dev(op, bs, richm.C64)
+    op.apply_sweeps(richm.C64, X, XP if a is not None else None, B, coef(ws, richm.C64),
+                    None if a is None else coef(a, richm.C64), None if at is None else coef(at, richm.C64),
+                    K=K, m=m, fuse=4)
+    for i, g in enumerate(from_dev(op, X, richm.C64)):
+        H = assemble_helmholtz(sizes[i], ks[i], absorbing=kind == richm.HELMHOLTZ_FD5_ABC)
+        v = None if a is None else (x0[i].astype(np.complex128) - xp0[i].astype(np.complex128)).ravel()
+        ref, _ = inner_steps(H, bs[i].astype(np.complex128).ravel(), x0[i].astype(np.complex128).ravel(), v,
+                             ws[i].astype(np.float64), None if a is None else a[i].astype(np.float64),
+                             None if at is None else at[i].astype(np.float64), K=K)
+        rel = np.linalg.norm(g.ravel() - ref) / np.linalg.norm(ref)
+        assert rel <= 1e-5, (sizes[i], rel)
+
+
+def test_helmholtz_fused_equals_one_sweep_passes_closely():
+    sizes = [33, 88, 200]
+    ks = [helmholtz_wavenumber(n) for n in sizes]
+    res = []
+    for fuse in (1, 4):
+        op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, n, 1.0, 0.0, k) for n, k in zip(sizes, ks)])
+        ws = np.stack([synth.helmholtz_weights(8, 1.0 / (n + 1), seed=4) for n in sizes])
+        x0 = [0.1 * (synth.rhs_uniform(55, i, n) + 1j * synth.rhs_uniform(56, i, n)) for i, n in enumerate(sizes)]
+        X, XP = to_dev(op, x0, richm.C64), to_dev(op, x0, richm.C64)
+        B = to_dev(op, [synth.point_source_rhs(n, 1, seed=9 + i)[0] for i, n in enumerate(sizes)], richm.C64)
+        op.apply_sweeps(richm.C64, X, XP, B, coef(ws, richm.C64), coef(np.full_like(ws, 0.3), richm.C64), None,
+                        K=16, m=8, fuse=fuse)
+        res.append(from_dev(op, X, richm.C64))
+    for g1, g4 in zip(*res):
+        assert np.abs(g1 - g4).max() <= 1e-5 * max(np.abs(g1).max(), 1e-30)
+
+
 def test_helmholtz_jacobi_preconditioned():
     sizes = [4, 33]
     ks = [helmholtz_wavenumber(n) for n in sizes]
