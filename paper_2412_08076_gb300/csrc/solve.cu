@@ -25,6 +25,7 @@
 // converge, shorter tiles keep the remaining work spread over the GPU).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <numeric>
 #include <type_traits>
@@ -60,6 +61,8 @@ struct richm_solver {
   int graph_cycles = 1;      // cycles captured in one graph replay
   long long cycles_run = 0;  // cycles since start
   int* h_count = nullptr;    // pinned: [0] active count, [1 .. batch] per-instance active flags
+  int* h_stage = nullptr;    // pinned: two more such records for readbacks still in flight
+  cudaEvent_t ev_read[2] = {nullptr, nullptr};
   int rows_now = 256;        // fused tile height used by the next cycles
   int rows_max = 256;        // the operator's tuned tile height
   bool started = false;
@@ -471,6 +474,10 @@ static richm_status run_cycles(richm_solver* S, int cycles) {
 
 using namespace richm;
 
+static richm_status launch_cycles(richm_solver* S, int cycles);
+static richm_status enqueue_readback(richm_solver* S, int* rec);
+static richm_status run_to_completion(richm_solver* S, long long max_cycles, cudaStream_t stream);
+
 extern "C" {
 
 static richm_status check_solve_opts(const richm_operator* op, const richm_solve_opts* o) {
@@ -576,6 +583,10 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_count, sizeof(int) * (op->batch + 1), cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&S->h_stage, sizeof(int) * 2 * (op->batch + 1), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_read[0], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_read[1], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     richm_solver_destroy(S);
     return set_error(RICHM_ERR_CUDA, "solver setup failed: %s", cudaGetErrorString(e));
@@ -602,6 +613,9 @@ void richm_solver_destroy(richm_solver* S) {
   if (S->ev_in) cudaEventDestroy(S->ev_in);
   if (S->ev_out) cudaEventDestroy(S->ev_out);
   if (S->h_count) cudaFreeHost(S->h_count);
+  if (S->h_stage) cudaFreeHost(S->h_stage);
+  for (cudaEvent_t ev : S->ev_read)
+    if (ev) cudaEventDestroy(ev);
   delete S;
 }
 
@@ -657,6 +671,23 @@ richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, voi
   RICHM_ARG(cycles >= 0, "cycles < 0");
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, (cudaStream_t)stream));
   RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
+  RICHM_TRY(launch_cycles(S, cycles));
+  if (active_out) {
+    RICHM_TRY(enqueue_readback(S, S->h_count));
+    RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
+    *active_out = *S->h_count;
+    if (S->o.fuse > 1 && *active_out > 0) S->rows_now = choose_rows(S);
+  }
+  RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
+  RICHM_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, S->ev_out, 0));
+  return RICHM_OK;
+}
+
+}  // extern "C"
+
+// Queue `cycles` refinement cycles on the solver's stream (graph replays where whole
+// weight periods fit, plain launches for the rest).
+static richm_status launch_cycles(richm_solver* S, int cycles) {
   const int G = S->graph_cycles;
   int done = 0;
   if (S->o.use_graph) {
@@ -691,19 +722,54 @@ richm_status richm_solver_step(richm_solver* S, int cycles, int* active_out, voi
     RICHM_TRY(run_cycles(S, cycles - done));
     S->cycles_run += cycles - done;
   }
-  if (active_out) {
-    RICHM_CUDA_TRY(cudaMemcpyAsync(S->h_count, S->count, sizeof(int), cudaMemcpyDeviceToHost, S->s));
-    if (S->o.fuse > 1)
-      RICHM_CUDA_TRY(cudaMemcpyAsync(S->h_count + 1, S->active, sizeof(int) * S->op->batch, cudaMemcpyDeviceToHost,
-                                     S->s));
-    RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
-    *active_out = *S->h_count;
-    if (S->o.fuse > 1 && *active_out > 0) S->rows_now = choose_rows(S);
-  }
-  RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
-  RICHM_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, S->ev_out, 0));
   return RICHM_OK;
 }
+
+// Copy the active count (and, with fused passes, the per-instance flags) into a
+// pinned host record, ordered after the work queued on the solver's stream.
+static richm_status enqueue_readback(richm_solver* S, int* rec) {
+  RICHM_CUDA_TRY(cudaMemcpyAsync(rec, S->count, sizeof(int), cudaMemcpyDeviceToHost, S->s));
+  if (S->o.fuse > 1)
+    RICHM_CUDA_TRY(cudaMemcpyAsync(rec + 1, S->active, sizeof(int) * S->op->batch, cudaMemcpyDeviceToHost, S->s));
+  return RICHM_OK;
+}
+
+// The loop of richm_solve: cycles until no instance is active or max_cycles ran. The
+// readback of a cycle's active count is not waited for before the next cycle is
+// queued, so the GPU does not idle on the host round trip; the tile height and the
+// stopping decision use the count of the cycle before (one cycle may run with every
+// instance already converged; its kernels skip inactive instances).
+static richm_status run_to_completion(richm_solver* S, long long max_cycles, cudaStream_t stream) {
+  RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, stream));
+  RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
+  RICHM_TRY(enqueue_readback(S, S->h_count));  // after solver start
+  RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
+  int active = *S->h_count;
+  if (S->o.fuse > 1 && active > 0) S->rows_now = choose_rows(S);
+  const size_t rec = (size_t)S->op->batch + 1;
+  long long c = 0;
+  int pending = -1;  // slot of the readback in flight
+  while (active > 0 && c < max_cycles) {
+    RICHM_TRY(launch_cycles(S, S->graph_cycles));
+    c += S->graph_cycles;
+    if (pending >= 0) {
+      RICHM_CUDA_TRY(cudaEventSynchronize(S->ev_read[pending]));
+      memcpy(S->h_count, S->h_stage + pending * rec, sizeof(int) * rec);
+      active = *S->h_count;
+      if (S->o.fuse > 1 && active > 0) S->rows_now = choose_rows(S);
+    }
+    const int slot = pending < 0 ? 0 : 1 - pending;
+    RICHM_TRY(enqueue_readback(S, S->h_stage + slot * rec));
+    RICHM_CUDA_TRY(cudaEventRecord(S->ev_read[slot], S->s));
+    pending = slot;
+  }
+  RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
+  RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
+  RICHM_CUDA_TRY(cudaStreamWaitEvent(stream, S->ev_out, 0));
+  return RICHM_OK;
+}
+
+extern "C" {
 
 richm_status richm_solver_finish(richm_solver* S, richm_solve_info* info, void* stream) {
   clear_error();
@@ -811,16 +877,7 @@ richm_status richm_solve_host(richm_operator* op, const double* b_host, double* 
   richm_solver* S = nullptr;
   RICHM_TRY(richm_solver_create(op, o, w, alpha, alpha_t, work, sw, &S));
   richm_status st = richm_solver_start_zero(S, bd, xd, stream);
-  int active = 0;
-  if (st == RICHM_OK) {
-    st = richm_solver_step(S, 0, &active, stream);
-    const long long max_cycles = o->max_sweeps / o->refine_every + 2;
-    long long c = 0;
-    while (st == RICHM_OK && active > 0 && c < max_cycles) {
-      st = richm_solver_step(S, S->graph_cycles, &active, stream);
-      c += S->graph_cycles;
-    }
-  }
+  if (st == RICHM_OK) st = run_to_completion(S, o->max_sweeps / o->refine_every + 2, s);
   if (st == RICHM_OK) st = richm_solver_finish(S, info, stream);
   richm_solver_destroy(S);
   if (st != RICHM_OK && st != RICHM_ERR_NOT_CONVERGED && st != RICHM_ERR_DIVERGED) return st;
@@ -839,17 +896,7 @@ richm_status richm_solve(richm_operator* op, const double* b, double* x, const v
   richm_solver* S = nullptr;
   RICHM_TRY(richm_solver_create(op, o, w, alpha, alpha_t, work, work_bytes, &S));
   richm_status st = richm_solver_start(S, b, x, stream);
-  int active = 0;
-  if (st == RICHM_OK) {
-    st = richm_solver_step(S, 0, &active, stream);
-    const long long max_cycles = o->max_sweeps / o->refine_every + 2;
-    long long c = 0;
-    while (st == RICHM_OK && active > 0 && c < max_cycles) {
-      const int n = S->graph_cycles;
-      st = richm_solver_step(S, n, &active, stream);
-      c += n;
-    }
-  }
+  if (st == RICHM_OK) st = run_to_completion(S, o->max_sweeps / o->refine_every + 2, (cudaStream_t)stream);
   if (st == RICHM_OK) st = richm_solver_finish(S, info, stream);
   richm_solver_destroy(S);
   return st;
