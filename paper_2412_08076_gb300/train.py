@@ -92,12 +92,12 @@ def make_batches(nbatches=8, B=64, n=255, seed=1000):
     return out
 
 
-def train(steps=1000, lr=2e-3, nbatches=8, n=255, log_every=100, verbose=True):
+def train(steps=1000, lr=2e-3, nbatches=8, n=255, log_every=100, verbose=True, K=64):
     """Algorithm 1 with the config-3 workload (64 instances of n x n per batch, K = 64,
     checkpoints every 8) from the initial network; cosine-decayed Adam step size.
     Deterministic: seeded data, fixed-order kernels. Returns (params, loss history)."""
     params, _ = meta_mod.load_params(16, prefer_trained=False)
-    tr = Trainer(params, lr=lr)
+    tr = Trainer(params, K=K, lr=lr)
     batches = make_batches(nbatches, n=n)
     hist = []
     t0 = time.time()
@@ -117,9 +117,10 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batches", type=int, default=8)
     ap.add_argument("--n", type=int, default=255)
+    ap.add_argument("--K", type=int, default=64, help="unrolled sweeps per loss evaluation")
     ap.add_argument("--out", default=None, help="where to save the parameters (.npy)")
     args = ap.parse_args(argv)
-    params, hist = train(args.steps, args.lr, args.batches, args.n)
+    params, hist = train(args.steps, args.lr, args.batches, args.n, K=args.K)
     if args.out:
         os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
         np.save(args.out, params)
