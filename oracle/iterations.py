@@ -93,6 +93,15 @@ def ssor_binv(A, alpha):
     return apply
 
 
+def ssor_binv_matrix(A, alpha):
+    """The SSOR B^{-1} of `ssor_binv` as a dense matrix (its columns are B^{-1} e_j);
+    for small instances, where a matrix product is the plain way to differentiate
+    through it."""
+    apply = ssor_binv(A, alpha)
+    N = A.shape[0]
+    return np.stack([apply(np.eye(1, N, j).ravel()) for j in range(N)], axis=1)
+
+
 def residual(A, f, u):
     """f - A u."""
     return f - A @ u

@@ -32,11 +32,12 @@ def to_torch_sparse(A):
                                    torch.from_numpy(A.data), size=A.shape)
 
 
-def unrolled_nag(At, f, u0, w, a, K, Dinv=None):
+def unrolled_nag(At, f, u0, w, a, K, Dinv=None, Binv=None):
     """K inner NAG steps (Table 1, at = a) in torch; u^{-1} = u0 (zero velocity).
 
     w, a: tensors of length m (a may be a length-m tensor or a scalar tensor).
     Dinv: optional tensor, elementwise B^{-1} = D^{-1} (eq. 17).
+    Binv: optional dense tensor, B^{-1} as a matrix (e.g. the SSOR preconditioner).
     """
     m = w.shape[0]
     u = u0
@@ -48,6 +49,8 @@ def unrolled_nag(At, f, u0, w, a, K, Dinv=None):
         r = f - At @ ut
         if Dinv is not None:
             r = Dinv * r
+        if Binv is not None:
+            r = Binv @ r
         v = ai * v + w[i] * r
         u = u + v
     return u
@@ -58,11 +61,13 @@ def log_rel_residual(At, f, u):
     return torch.log(torch.linalg.vector_norm(f - At @ u) / torch.linalg.vector_norm(f))
 
 
-def loss_and_grads(As, fs, u0s, ws, alphas, K, Dinvs=None):
+def loss_and_grads(As, fs, u0s, ws, alphas, K, Dinvs=None, Binvs=None):
     """Mean log relative residual after K NAG steps and its gradient.
 
     As: list of scipy matrices; fs, u0s: lists of flat numpy arrays; ws: (B, m);
     alphas: (B, m) per-step momentum or (B,) one momentum per instance.
+    Dinvs: optional per-instance diagonals of D^{-1}; Binvs: optional per-instance
+    dense B^{-1} matrices (oracle.iterations.ssor_binv_matrix).
     Returns (L, dL/dw (B, m), dL/dalpha (same shape as alphas), [dL/du0_b]).
     Pinned by: central finite differences (tests).
     """
@@ -75,15 +80,16 @@ def loss_and_grads(As, fs, u0s, ws, alphas, K, Dinvs=None):
         At = to_torch_sparse(As[b])
         f = torch.from_numpy(np.asarray(fs[b], dtype=np.float64))
         Dinv = None if Dinvs is None else torch.from_numpy(np.asarray(Dinvs[b]))
-        uK = unrolled_nag(At, f, u0_t[b], w_t[b], a_t[b], K, Dinv)
+        Binv = None if Binvs is None else torch.from_numpy(np.asarray(Binvs[b], dtype=np.float64))
+        uK = unrolled_nag(At, f, u0_t[b], w_t[b], a_t[b], K, Dinv, Binv)
         total = total + log_rel_residual(At, f, uK)
     L = total / B
     L.backward()
     return float(L.detach()), w_t.grad.numpy(), a_t.grad.numpy(), [u.grad.numpy() for u in u0_t]
 
 
-def loss_only(As, fs, u0s, ws, alphas, K):
-    """The same loss in numpy (used for finite differences)."""
+def loss_only(As, fs, u0s, ws, alphas, K, Binvs=None):
+    """The same loss without gradients (used for finite differences)."""
     with torch.no_grad():
         tot = 0.0
         for b in range(len(As)):
@@ -91,7 +97,9 @@ def loss_only(As, fs, u0s, ws, alphas, K):
             f = torch.from_numpy(np.asarray(fs[b], dtype=np.float64))
             uK = unrolled_nag(At, f, torch.tensor(np.asarray(u0s[b], dtype=np.float64)),
                               torch.tensor(np.asarray(ws[b], dtype=np.float64)),
-                              torch.tensor(np.asarray(alphas[b], dtype=np.float64)), K)
+                              torch.tensor(np.asarray(alphas[b], dtype=np.float64)), K,
+                              Binv=None if Binvs is None else torch.from_numpy(np.asarray(Binvs[b],
+                                                                                           dtype=np.float64)))
             tot += float(log_rel_residual(At, f, uK))
     return tot / len(As)
 

@@ -129,3 +129,46 @@ def test_two_level_exact_inverse_symbol_on_periodic_free_case():
     u1 = two_level_cycle(A, f, np.zeros(n * n), w, np.zeros((n, n)))
     u2, _ = inner_steps(A, f, np.zeros(n * n), None, w, K=8)
     np.testing.assert_array_equal(u1, u2)
+
+
+def test_ssor_preconditioned_loss_and_gradient():
+    # forward: the dense-B^{-1} unroll equals the Table 1 steps with the SSOR solves as
+    # triangular-solve callables; gradient: central differences of that forward
+    from oracle.iterations import ssor_binv, ssor_binv_matrix
+    As, fs, u0s, w, a, K = _problem(n=6, K=8)
+    relax = 1.4
+    Bm = [ssor_binv_matrix(A, relax) for A in As]
+    w = w * 2.0  # B^{-1} A has its spectrum in (0, 1]: weights of order 1
+    L, gw, ga, gu = loss_and_grads(As, fs, u0s, w, a, K, Binvs=Bm)
+    ref = 0.0
+    for b in range(2):
+        u, _ = inner_steps(As[b], fs[b], u0s[b], None, w[b], a[b], K=K, Binv=ssor_binv(As[b], relax))
+        ref += math.log(np.linalg.norm(fs[b] - As[b] @ u) / np.linalg.norm(fs[b]))
+    assert abs(L - ref / 2) < 1e-12
+    h = 1e-5
+    for b in range(2):
+        for i in range(w.shape[1]):
+            for arr, g in ((w, gw), (a, ga)):
+                p, q = arr.copy(), arr.copy()
+                p[b, i] += h
+                q[b, i] -= h
+                args_p = (p, a) if arr is w else (w, p)
+                args_q = (q, a) if arr is w else (w, q)
+                fd = (loss_only(As, fs, u0s, *args_p, K, Binvs=Bm) - loss_only(As, fs, u0s, *args_q, K, Binvs=Bm)) / (2 * h)
+                assert abs(fd - g[b, i]) <= 1e-6 * max(1.0, abs(fd)), (b, i, fd, g[b, i])
+        for idx in [0, 7, 20, 35]:
+            up = [u.copy() for u in u0s]
+            um = [u.copy() for u in u0s]
+            up[b][idx] += h
+            um[b][idx] -= h
+            fd = (loss_only(As, fs, up, w, a, K, Binvs=Bm) - loss_only(As, fs, um, w, a, K, Binvs=Bm)) / (2 * h)
+            assert abs(fd - gu[b][idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_ssor_binv_matrix_is_the_operator():
+    from oracle.iterations import ssor_binv, ssor_binv_matrix
+    A = assemble_q1(5, 0.05, 0.7)
+    M = ssor_binv_matrix(A, 1.2)
+    r = synth.rhs_uniform(5, 0, 5).ravel()
+    np.testing.assert_allclose(M @ r, ssor_binv(A, 1.2)(r), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(M, M.T, atol=1e-14 * np.abs(M).max())
