@@ -329,10 +329,12 @@ richm_status richm_checkpoint_elems(const richm_operator* op, int K, int ckpt_ev
 
 /* Forward K sweeps from x0 with zero initial velocity (x_{-1} = x0), storing the
  * checkpoints; xK receives x_K (padded). Same coefficient conventions as
- * richm_apply_sweeps. Requires K % ckpt_every == 0. work: richm_sweeps_workspace. */
+ * richm_apply_sweeps: precond 0 none, 1 Jacobi, 2 SSOR with relaxation factor relax
+ * in (0, 2) (ignored otherwise). Requires K % ckpt_every == 0. work: at least
+ * richm_adjoint_workspace bytes (four padded buffers suffice). */
 richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, const void* x0, const void* b,
                                         const void* w, const void* alpha, const void* alpha_t, int m, int K,
-                                        int ckpt_every, int precond, void* ckpts, void* xK,
+                                        int ckpt_every, int precond, double relax, void* ckpts, void* xK,
                                         void* work, size_t work_bytes, void* stream);
 
 /* Workspace bytes for richm_loss_log_residual and richm_sweeps_adjoint. */
@@ -346,10 +348,11 @@ richm_status richm_loss_log_residual(richm_operator* op, richm_dtype dtype, cons
                                      double* loss, void* g, void* work, size_t work_bytes, void* stream);
 
 /* Reverse-mode sweep ("backpropagate", Algorithm 1) over the K sweeps recorded by
- * richm_forward_checkpointed, with A symmetric so the adjoint applies the same
- * stencil: for k = K-1 .. 0 (i = k mod m), with lam_{k+1} = dL/dx_{k+1} and
- * q = w_i A B^{-1} lam_{k+1},
- *   dL/dw_i   += <lam_{k+1}, B^{-1}(b - A y_k)>
+ * richm_forward_checkpointed (same precond and relax), with A and B^{-1} symmetric so
+ * the adjoint applies the same stencil and preconditioner: for k = K-1 .. 0
+ * (i = k mod m), with lam_{k+1} = dL/dx_{k+1}, u = B^{-1} lam_{k+1} (for SSOR one
+ * forward and one backward triangular solve per step) and q = w_i A u,
+ *   dL/dw_i   += <lam_{k+1}, B^{-1}(b - A y_k)> = <u, b - A y_k>
  *   dL/da_i   += <lam_{k+1}, x_k - x_{k-1}>
  *   dL/dat_i  += -<q, x_k - x_{k-1}>
  *   lam_k      = (1 + a_i) lam_{k+1} - (1 + at_i) q + c_{k+1},  c_k = -a_i lam_{k+1} + at_i q,
@@ -359,8 +362,9 @@ richm_status richm_loss_log_residual(richm_operator* op, richm_dtype dtype, cons
  * g_alpha. g_x0: padded or NULL. Gradients are written, not accumulated. */
 richm_status richm_sweeps_adjoint(richm_operator* op, richm_dtype dtype, const void* ckpts, int ckpt_every,
                                   const void* b, const void* gK, const void* w, const void* alpha,
-                                  const void* alpha_t, int m, int K, int precond, void* g_w, void* g_alpha,
-                                  void* g_alpha_t, void* g_x0, void* work, size_t work_bytes, void* stream);
+                                  const void* alpha_t, int m, int K, int precond, double relax, void* g_w,
+                                  void* g_alpha, void* g_alpha_t, void* g_x0, void* work, size_t work_bytes,
+                                  void* stream);
 
 /* ------------------------------------------------------------------ meta network */
 

@@ -25,6 +25,7 @@ class SweepContext:
     K: int = 64
     every: int = 8
     precond: int = 0
+    relax: float = 1.0       # SSOR relaxation factor (precond 2)
 
 
 class UnrolledSweeps(torch.autograd.Function):
@@ -36,7 +37,7 @@ class UnrolledSweeps(torch.autograd.Function):
         w = w.contiguous()
         alpha = alpha.contiguous()
         op.forward_checkpointed(sc.dtype, x0.contiguous(), sc.b, w, alpha, None, sc.m, sc.K, sc.every, sc.precond,
-                                ck, xK)
+                                ck, xK, relax=sc.relax)
         ctx.save_for_backward(w, alpha, ck)
         ctx.sc = sc
         return xK
@@ -49,7 +50,7 @@ class UnrolledSweeps(torch.autograd.Function):
         ga = torch.zeros_like(alpha)
         gx0 = sc.op.zeros(sc.dtype)
         sc.op.sweeps_adjoint(sc.dtype, ck, sc.every, sc.b, gK.contiguous(), w, alpha, None, sc.m, sc.K, sc.precond,
-                             gw, ga, None, gx0)
+                             gw, ga, None, gx0, relax=sc.relax)
         return gw, ga, gx0, None
 
 

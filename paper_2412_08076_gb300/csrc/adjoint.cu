@@ -10,6 +10,10 @@
 // stencil twice (to d lam and to y), so each step streams lam, c, x_k, x_{k-1}, b
 // once. States between checkpoints are recomputed from the checkpoint by the
 // forward kernel, which is deterministic, so the recomputation is bitwise exact.
+//
+// With the SSOR preconditioner (d replaced by the symmetric matrix B^{-1}) the step
+// first forms u = B^{-1} lam_{k+1} with the SSOR solves; then q = w_i A u and, because
+// <lam, B^{-1} r> = <B^{-1} lam, r>, dL/dw_i += <u, b - A y> with no second solve.
 #include <type_traits>
 
 #include "common.cuh"
@@ -23,10 +27,12 @@ struct alignas(32) Dot3 {
   double v[4];
 };
 
-template <typename T, bool MOM, bool PRE>
+// PM: 0 no preconditioner, 1 Jacobi (d = 1/c), 2 a matrix B^{-1} applied beforehand
+// (u = B^{-1} lam in `ub`: the stencil and the weight gradient take u, the rest lam).
+template <typename T, bool MOM, int PM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     adjoint_kernel(const Inst* insts, const Tile* tiles, int ntiles, const T* __restrict__ lam,
-                   const T* __restrict__ carry, const T* __restrict__ x, const T* __restrict__ xp,
+                   const T* __restrict__ ub, const T* __restrict__ carry, const T* __restrict__ x, const T* __restrict__ xp,
                    const T* __restrict__ b, T* __restrict__ lam_out, T* __restrict__ carry_out,
                    const T* __restrict__ w, const T* __restrict__ a, const T* __restrict__ at, int m, int kidx,
                    int final_step, Dot3* __restrict__ partials) {
@@ -45,8 +51,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     ati = at ? at[cidx] : ai;
   }
   const T sc = (T)I.c, sax = (T)I.ax, say = (T)I.ay, sd1 = (T)I.d1, sd2 = (T)I.d2;
-  const T dv = PRE ? (T)I.dinv : T(1);
-  const T qs = wi * dv;  // q = w d A lam (d constant for Q1)
+  const T dv = PM == 1 ? (T)I.dinv : T(1);
+  const T qs = wi * dv;  // q = w d A lam (d constant for Q1), or w A u
+  const T* __restrict__ sl = PM == 2 ? ub : lam;  // the array the stencil is applied to
   const int c0 = t.tx * 32 * VW + lane * VW;
   const bool live = c0 < pitch;
   const int r0 = t.ty * kRows + 1;
@@ -84,13 +91,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const bool in = (pr >= 1) && (pr <= n);
     VecN<T, VW> Lv{};
     const long long ro = off + (long long)pr * pitch;
-    if (in && live) Lv = ldv<T, VW>(lam + ro + c0);
+    if (in && live) Lv = ldv<T, VW>(sl + ro + c0);
 #pragma unroll
     for (int e = 0; e < VW; ++e) L.y[e] = Lv.v[e];
     T le = 0, re = 0;
     if (in) {
-      if (lane == 0 && c0 > 0) le = lam[ro + c0 - 1];
-      if (lane == 31 && c0 + VW < pitch) re = lam[ro + c0 + VW];
+      if (lane == 0 && c0 > 0) le = sl[ro + c0 - 1];
+      if (lane == 31 && c0 + VW < pitch) re = sl[ro + c0 + VW];
     }
     row_neighbours<T, VW>(L, lane, le, re);
   };
@@ -106,10 +113,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     load_y(r + 1, YD, xD, xpD);
     load_l(r + 1, LD);
     const long long ro = off + (long long)r * pitch + c0;
-    VecN<T, VW> Bv{}, Cv{};
+    VecN<T, VW> Bv{}, Cv{}, Lm{};
     if (live) {
       Bv = ldv<T, VW>(b + ro);
       if (MOM && carry) Cv = ldv<T, VW>(carry + ro);
+      if (PM == 2) Lm = ldv<T, VW>(lam + ro);
     }
     T Ay[VW], Al[VW];
     apply_q1<T, VW, T>(YU, YC, YD, sc, sax, say, sd1, sd2, Ay);
@@ -121,7 +129,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       const bool ok = (c0 + e) < n;
-      const T l = LC.y[e];
+      const T l = PM == 2 ? Lm.v[e] : LC.y[e];  // lam
+      const T u = LC.y[e];                      // lam, d lam folded into dr, or B^{-1} lam
       const T q = qs * Al[e];
       const T dr = dv * (Bv.v[e] - Ay[e]);
       const T v = MOM ? xC[e] - xpC[e] : T(0);
@@ -129,13 +138,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       T cn = MOM ? -ai * l + ati * q : T(0);
       if (ok) {
         if constexpr (std::is_same<T, float>::value) {
-          rw = fmaf(l, dr, rw);
+          rw = fmaf(u, dr, rw);
           if (MOM) {
             ra = fmaf(l, v, ra);
             rat = fmaf(q, v, rat);
           }
         } else {
-          s_w += (double)l * (double)dr;
+          s_w += (double)u * (double)dr;
           if (MOM) {
             s_a += (double)l * (double)v;
             s_at += (double)q * (double)v;
@@ -216,23 +225,28 @@ __global__ void adjoint_finish_kernel(const double* __restrict__ acc, int count,
 }
 
 template <typename T>
-static richm_status launch_adjoint(richm_operator* op, const T* lam, const T* carry, const T* x, const T* xp,
-                                   const T* b, T* lam_out, T* carry_out, const T* w, const T* a, const T* at, int m,
-                                   int kidx, int precond, int final_step, Dot3* partials, double* acc,
-                                   cudaStream_t s) {
+static richm_status launch_adjoint(richm_operator* op, const T* lam, const T* ub, const T* carry, const T* x,
+                                   const T* xp, const T* b, T* lam_out, T* carry_out, const T* w, const T* a,
+                                   const T* at, int m, int kidx, int precond, int final_step, Dot3* partials,
+                                   double* acc, cudaStream_t s) {
   constexpr int VW = VecWidth<T>::value;
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 32 * VW, kRows, &tm));
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int thr = kWarpsPerBlock * 32;
   const bool mom = a != nullptr;
-#define RICHM_ADJ(M, P)                                                                                        \
-  adjoint_kernel<T, M, P><<<blocks, thr, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, lam, carry, x, xp, b, \
-                                                 lam_out, carry_out, w, a, at, m, kidx, final_step, partials)
-  if (mom && precond) RICHM_ADJ(true, true);
-  else if (mom) RICHM_ADJ(true, false);
-  else if (precond) RICHM_ADJ(false, true);
-  else RICHM_ADJ(false, false);
+#define RICHM_ADJ(M, P)                                                                                       \
+  adjoint_kernel<T, M, P><<<blocks, thr, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, lam, ub, carry, x, xp, \
+                                                 b, lam_out, carry_out, w, a, at, m, kidx, final_step, partials)
+  if (mom) {
+    if (precond == 2) RICHM_ADJ(true, 2);
+    else if (precond == 1) RICHM_ADJ(true, 1);
+    else RICHM_ADJ(true, 0);
+  } else {
+    if (precond == 2) RICHM_ADJ(false, 2);
+    else if (precond == 1) RICHM_ADJ(false, 1);
+    else RICHM_ADJ(false, 0);
+  }
 #undef RICHM_ADJ
   RICHM_LAUNCH_CHECK("adjoint sweep");
   const int wpb = 8;
@@ -242,18 +256,27 @@ static richm_status launch_adjoint(richm_operator* op, const T* lam, const T* ca
   return RICHM_OK;
 }
 
+// One forward sweep with any preconditioner (z: SSOR scratch).
+template <typename T>
+static richm_status sweep_any(richm_operator* op, const T* x, const T* xp, const T* b, T* out, const T* w,
+                              const T* a, const T* at, int m, int kidx, int precond, double relax, T* z,
+                              cudaStream_t s) {
+  if (precond == 2) return launch_ssor_sweep<T>(op, x, xp, b, z, out, nullptr, w, a, at, m, kidx, relax, nullptr, s);
+  return launch_sweep<T>(op, x, xp, b, out, w, a, at, m, kidx, precond, nullptr, s);
+}
+
 template <typename T>
 static richm_status forward_ckpt_t(richm_operator* op, const T* x0, const T* b, const T* w, const T* a,
-                                   const T* at, int m, int K, int s_every, int precond, T* ckpts, T* xK, void* work,
-                                   cudaStream_t s) {
+                                   const T* at, int m, int K, int s_every, int precond, double relax, T* ckpts,
+                                   T* xK, void* work, cudaStream_t s) {
   const size_t es = op->elems;
   const size_t bytes = es * sizeof(T);
   const size_t slot = 2 * es;
   // slot j holds (x_{js}, x_{js-1}); slot 0 = (x0, x0)
   RICHM_CUDA_TRY(cudaMemcpyAsync(ckpts, x0, bytes, cudaMemcpyDeviceToDevice, s));
   RICHM_CUDA_TRY(cudaMemcpyAsync(ckpts + es, x0, bytes, cudaMemcpyDeviceToDevice, s));
-  T* W[3];
-  for (int i = 0; i < 3; ++i) W[i] = reinterpret_cast<T*>(reinterpret_cast<char*>(work) + i * a256(bytes));
+  T* W[4];  // three rotating states and the SSOR scratch
+  for (int i = 0; i < 4; ++i) W[i] = reinterpret_cast<T*>(reinterpret_cast<char*>(work) + i * a256(bytes));
   const int nseg = K / s_every;
   for (int j = 0; j < nseg; ++j) {
     T* cx = ckpts + (size_t)j * slot;
@@ -272,7 +295,7 @@ static richm_status forward_ckpt_t(richm_operator* op, const T* x0, const T* b, 
         for (int i = 0; i < 3 && out == nullptr; ++i)
           if (W[i] != cur && W[i] != prev) out = W[i];
       const int kidx = (j * s_every + t) % m;
-      RICHM_TRY(launch_sweep<T>(op, cur, a ? prev : nullptr, b, out, w, a, at, m, kidx, precond, nullptr, s));
+      RICHM_TRY(sweep_any<T>(op, cur, a ? prev : nullptr, b, out, w, a, at, m, kidx, precond, relax, W[3], s));
       prev = cur;
       cur = out;
     }
@@ -287,7 +310,8 @@ static size_t adjoint_ws(richm_operator* op, int s_every) {
   int nt = 0;
   residual_tiles<T>(op, &nt);
   const size_t buf = a256(op->elems * sizeof(T));
-  const size_t adj = (size_t)(s_every > 1 ? s_every - 1 : 0) * buf + 4 * buf + a256(sizeof(Dot3) * nt) +
+  // segment states, lam and carry pairs, u = B^{-1} lam and the SSOR scratch
+  const size_t adj = (size_t)(s_every > 1 ? s_every - 1 : 0) * buf + 6 * buf + a256(sizeof(Dot3) * nt) +
                      a256(sizeof(double) * 3 * 64 * (size_t)op->batch);
   const size_t loss = loss_workspace_bytes(op, sizeof(T), nt);
   return adj > loss ? adj : loss;
@@ -295,8 +319,8 @@ static size_t adjoint_ws(richm_operator* op, int s_every) {
 
 template <typename T>
 static richm_status adjoint_t(richm_operator* op, const T* ckpts, int s_every, const T* b, const T* gK, const T* w,
-                              const T* a, const T* at, int m, int K, int precond, T* g_w, T* g_a, T* g_at, T* g_x0,
-                              void* work, size_t work_bytes, cudaStream_t s) {
+                              const T* a, const T* at, int m, int K, int precond, double relax, T* g_w, T* g_a,
+                              T* g_at, T* g_x0, void* work, size_t work_bytes, cudaStream_t s) {
   if (work_bytes < adjoint_ws<T>(op, s_every)) return set_error(RICHM_ERR_NOMEM, "adjoint workspace too small");
   const size_t es = op->elems;
   const size_t buf = a256(es * sizeof(T));
@@ -319,6 +343,10 @@ static richm_status adjoint_t(richm_operator* op, const T* ckpts, int s_every, c
     CB[i] = reinterpret_cast<T*>(p);
     p += buf;
   }
+  T* U = reinterpret_cast<T*>(p);  // B^{-1} lam (SSOR)
+  p += buf;
+  T* Z = reinterpret_cast<T*>(p);  // SSOR scratch
+  p += buf;
   Dot3* partials = reinterpret_cast<Dot3*>(p);
   p += a256(sizeof(Dot3) * nt);
   double* acc = reinterpret_cast<double*>(p);
@@ -333,15 +361,16 @@ static richm_status adjoint_t(richm_operator* op, const T* ckpts, int s_every, c
     seg[1] = const_cast<T*>(cx);       // x_{js}
     for (int t = 0; t + 2 <= s_every; ++t) {
       const int kidx = (j * s_every + t) % m;
-      RICHM_TRY(launch_sweep<T>(op, seg[t + 1], a ? seg[t] : nullptr, b, seg[t + 2], w, a, at, m, kidx, precond,
-                                nullptr, s));
+      RICHM_TRY(sweep_any<T>(op, seg[t + 1], a ? seg[t] : nullptr, b, seg[t + 2], w, a, at, m, kidx, precond,
+                             relax, Z, s));
     }
     for (int t = s_every - 1; t >= 0; --t) {
       const int k = j * s_every + t;
       const int fin = (k == 0) ? 1 : 0;
       T* lo = (fin && g_x0) ? g_x0 : LB[pi];
-      RICHM_TRY(launch_adjoint<T>(op, lam, carry, seg[t + 1], seg[t], b, lo, CB[pi], w, a, at, m, k % m, precond,
-                                  fin, partials, acc, s));
+      if (precond == 2) RICHM_TRY(launch_ssor_apply<T>(op, lam, Z, U, relax, s));
+      RICHM_TRY(launch_adjoint<T>(op, lam, U, carry, seg[t + 1], seg[t], b, lo, CB[pi], w, a, at, m, k % m,
+                                  precond, fin, partials, acc, s));
       lam = LB[pi];
       carry = CB[pi];
       pi ^= 1;
@@ -367,10 +396,16 @@ richm_status richm_checkpoint_elems(const richm_operator* op, int K, int ckpt_ev
   return RICHM_OK;
 }
 
+static richm_status check_precond(int precond, double relax) {
+  RICHM_ARG(precond >= 0 && precond <= 2, "precond must be 0, 1 or 2");
+  RICHM_ARG(precond != 2 || (relax > 0.0 && relax < 2.0), "SSOR relaxation factor must lie in (0, 2)");
+  return RICHM_OK;
+}
+
 richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, const void* x0, const void* b,
                                         const void* w, const void* alpha, const void* alpha_t, int m, int K,
-                                        int ckpt_every, int precond, void* ckpts, void* xK, void* work,
-                                        size_t work_bytes, void* stream) {
+                                        int ckpt_every, int precond, double relax, void* ckpts, void* xK,
+                                        void* work, size_t work_bytes, void* stream) {
   clear_error();
   RICHM_ARG(op != nullptr, "null operator");
   RICHM_TRY(check_dtype_for_op(op, dtype));
@@ -379,17 +414,18 @@ richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, c
   RICHM_ARG(m >= 1 && m <= 64, "m out of range");
   RICHM_ARG(ckpt_every >= 1 && K >= 0 && K % ckpt_every == 0, "K must be a multiple of ckpt_every >= 1");
   RICHM_ARG(alpha != nullptr || alpha_t == nullptr, "alpha_t given without alpha");
-  RICHM_ARG(precond == 0 || precond == 1, "precond must be 0 or 1");
-  const size_t need = 3 * a256(op->elems * dtype_size(dtype));
+  RICHM_TRY(check_precond(precond, relax));
+  const size_t need = 4 * a256(op->elems * dtype_size(dtype));
   RICHM_ARG(work != nullptr, "null workspace");
   if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
   if (dtype == RICHM_F32)
     return forward_ckpt_t<float>(op, (const float*)x0, (const float*)b, (const float*)w, (const float*)alpha,
-                                 (const float*)alpha_t, m, K, ckpt_every, precond, (float*)ckpts, (float*)xK, work, s);
+                                 (const float*)alpha_t, m, K, ckpt_every, precond, relax, (float*)ckpts, (float*)xK,
+                                 work, s);
   return forward_ckpt_t<double>(op, (const double*)x0, (const double*)b, (const double*)w, (const double*)alpha,
-                                (const double*)alpha_t, m, K, ckpt_every, precond, (double*)ckpts, (double*)xK, work,
-                                s);
+                                (const double*)alpha_t, m, K, ckpt_every, precond, relax, (double*)ckpts,
+                                (double*)xK, work, s);
 }
 
 richm_status richm_adjoint_workspace(const richm_operator* op, richm_dtype dtype, int ckpt_every, size_t* bytes) {
@@ -398,7 +434,7 @@ richm_status richm_adjoint_workspace(const richm_operator* op, richm_dtype dtype
   RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "real dtype required");
   RICHM_ARG(ckpt_every >= 1, "ckpt_every < 1");
   auto* o = const_cast<richm_operator*>(op);
-  const size_t fwd = 3 * a256(op->elems * dtype_size(dtype));
+  const size_t fwd = 4 * a256(op->elems * dtype_size(dtype));
   const size_t adj = dtype == RICHM_F32 ? adjoint_ws<float>(o, ckpt_every) : adjoint_ws<double>(o, ckpt_every);
   *bytes = adj > fwd ? adj : fwd;
   return RICHM_OK;
@@ -406,8 +442,9 @@ richm_status richm_adjoint_workspace(const richm_operator* op, richm_dtype dtype
 
 richm_status richm_sweeps_adjoint(richm_operator* op, richm_dtype dtype, const void* ckpts, int ckpt_every,
                                   const void* b, const void* gK, const void* w, const void* alpha,
-                                  const void* alpha_t, int m, int K, int precond, void* g_w, void* g_alpha,
-                                  void* g_alpha_t, void* g_x0, void* work, size_t work_bytes, void* stream) {
+                                  const void* alpha_t, int m, int K, int precond, double relax, void* g_w,
+                                  void* g_alpha, void* g_alpha_t, void* g_x0, void* work, size_t work_bytes,
+                                  void* stream) {
   clear_error();
   RICHM_ARG(op != nullptr, "null operator");
   RICHM_TRY(check_dtype_for_op(op, dtype));
@@ -416,14 +453,14 @@ richm_status richm_sweeps_adjoint(richm_operator* op, richm_dtype dtype, const v
   RICHM_ARG(m >= 1 && m <= 64, "m out of range");
   RICHM_ARG(ckpt_every >= 1 && K >= 1 && K % ckpt_every == 0, "K must be a positive multiple of ckpt_every");
   RICHM_ARG(alpha != nullptr || alpha_t == nullptr, "alpha_t given without alpha");
-  RICHM_ARG(precond == 0 || precond == 1, "precond must be 0 or 1");
+  RICHM_TRY(check_precond(precond, relax));
   cudaStream_t s = (cudaStream_t)stream;
   if (dtype == RICHM_F32)
     return adjoint_t<float>(op, (const float*)ckpts, ckpt_every, (const float*)b, (const float*)gK, (const float*)w,
-                            (const float*)alpha, (const float*)alpha_t, m, K, precond, (float*)g_w, (float*)g_alpha,
-                            (float*)g_alpha_t, (float*)g_x0, work, work_bytes, s);
+                            (const float*)alpha, (const float*)alpha_t, m, K, precond, relax, (float*)g_w,
+                            (float*)g_alpha, (float*)g_alpha_t, (float*)g_x0, work, work_bytes, s);
   return adjoint_t<double>(op, (const double*)ckpts, ckpt_every, (const double*)b, (const double*)gK,
-                           (const double*)w, (const double*)alpha, (const double*)alpha_t, m, K, precond,
+                           (const double*)w, (const double*)alpha, (const double*)alpha_t, m, K, precond, relax,
                            (double*)g_w, (double*)g_alpha, (double*)g_alpha_t, (double*)g_x0, work, work_bytes, s);
 }
 

@@ -61,6 +61,11 @@ richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, cons
                                const E* w, const E* a, const E* at, int m, int kidx, double relax, const int* active,
                                cudaStream_t s);
 
+// out = B^{-1} r with the SSOR B^{-1} of relaxation factor `relax` (the same two
+// triangular solves, y = 0); z: padded scratch. out must alias neither r nor z.
+template <typename E>
+richm_status launch_ssor_apply(richm_operator* op, const E* r, E* z, E* out, double relax, cudaStream_t s);
+
 // r = b - A x in FP64 with per-tile partial sums (sum |r|^2, sum |b|^2) written to
 // `partials` (one double2 per warp tile of the residual geometry); r_out may be null.
 template <typename E>

@@ -18,6 +18,10 @@
 // chunks, carrying the last value. The backward solve is the mirror image (rows and
 // columns reversed, upper neighbours). The intermediate z lives in a padded buffer;
 // the backward pass overwrites it with s row by row (the row above reads s below).
+//
+// With x == nullptr the same kernels apply the preconditioner alone, out = B^{-1} b
+// (y = 0, no momentum, w = 1): the adjoint of a preconditioned sweep needs B^{-1} of
+// the incoming gradient.
 #include <algorithm>
 
 #include "common.cuh"
@@ -124,13 +128,13 @@ template <typename E>
 struct SsorArgs {
   const Inst* insts;
   int batch;
-  const E* x;
+  const E* x;   // null: apply B^{-1} to b (y = 0, out_x = B^{-1} b)
   const E* xp;  // null without momentum
   const E* b;
   E* z;         // intermediate (padded)
   E* out_x;
   E* out_xp;    // null without momentum
-  const E* w;
+  const E* w;   // null: w = 1
   const E* a;   // null without momentum
   const E* at;  // null: at = a
   int m, kidx;
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_kernel(const Sso
   const E kx = A.relax * ax * rc, ky = A.relax * ay * rc, k1 = A.relax * d1 * rc, k2 = A.relax * d2 * rc;
   const int ci = inst * A.m + A.kidx;
   const E ati = A.a ? (A.at ? A.at[ci] : A.a[ci]) : E(0);
-  const E* xb = A.x + I.off;
+  const E* xb = A.x ? A.x + I.off : nullptr;
   const E* xpb = A.xp ? A.xp + I.off : nullptr;
   const E* bb = A.b + I.off;
   E* zb = A.z + I.off;
@@ -162,11 +166,13 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_kernel(const Sso
     for (int ch = 0; ch < nch; ++ch) {
       const int c0 = ch * CH + lane * VW;
       const bool live = c0 < pitch;
-      RowVW<E, VW> YU, YC, YD, ZU, T;
-      load_vw<E, VW>(xb, i - 1, n, pitch, c0, lane, live, ch == 0, YU);
-      load_vw<E, VW>(xb, i, n, pitch, c0, lane, live, ch == 0, YC);
-      load_vw<E, VW>(xb, i + 1, n, pitch, c0, lane, live, ch == 0, YD);
-      if (xpb && ati != E(0)) {
+      RowVW<E, VW> YU{}, YC{}, YD{}, ZU, T;
+      if (xb) {
+        load_vw<E, VW>(xb, i - 1, n, pitch, c0, lane, live, ch == 0, YU);
+        load_vw<E, VW>(xb, i, n, pitch, c0, lane, live, ch == 0, YC);
+        load_vw<E, VW>(xb, i + 1, n, pitch, c0, lane, live, ch == 0, YD);
+      }
+      if (xb && xpb && ati != E(0)) {
         load_vw<E, VW>(xpb, i - 1, n, pitch, c0, lane, live, ch == 0, T);
         lookahead<E, VW>(YU, T, ati);
         load_vw<E, VW>(xpb, i, n, pitch, c0, lane, live, ch == 0, T);
@@ -217,9 +223,9 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_kernel(const Ss
   const E rc = E(1) / c;
   const E kx = A.relax * ax * rc, ky = A.relax * ay * rc, k1 = A.relax * d1 * rc, k2 = A.relax * d2 * rc;
   const int ci = inst * A.m + A.kidx;
-  const E wi = A.w[ci] * A.relax * (E(2) - A.relax);
+  const E wi = (A.w ? A.w[ci] : E(1)) * A.relax * (E(2) - A.relax);
   const E ai = A.a ? A.a[ci] : E(0);
-  const E* xb = A.x + I.off;
+  const E* xb = A.x ? A.x + I.off : nullptr;
   const E* xpb = A.xp ? A.xp + I.off : nullptr;
   E* zb = A.z + I.off;
   E* ox = A.out_x + I.off;
@@ -274,8 +280,8 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_kernel(const Ss
       carry = __shfl_sync(0xffffffffu, P + Q * carry, 0);
       if (live) {
         const long long o = (long long)i * pitch + c0;
-        E xv[VW], xpv[VW], xn[VW];
-        ld16<E, VW>(xb + o, xv);
+        E xv[VW] = {}, xpv[VW], xn[VW];
+        if (xb) ld16<E, VW>(xb + o, xv);
         if (xpb) ld16<E, VW>(xpb + o, xpv);
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
@@ -391,7 +397,7 @@ __device__ __forceinline__ void scaled_rhs(const RowVW<E, VW>& U, const RowVW<E,
 template <typename E, int VW, int PH>
 __device__ __forceinline__ void fwd_row(int i, FwdRow<E, VW>& S, const RowRing<E, VW>& ring, const E* k, const E* mk,
                                         const E* qd, E ky, E k1, E k2, E rc, E axr, E ayr, E d1r, E d2r, E ati,
-                                        bool mom, int lane, bool live, int pitch, E* zrow,
+                                        bool mom, int lane, bool live, bool hx, int pitch, E* zrow,
                                         const E* xb, const E* xpb, const E* bb, int n, int c0) {
   constexpr int SU = (PH + 2) % 3, SC = PH, SD = (PH + 1) % 3;
   // inputs of step i + 1: x, x_prev of row i + 2 and b of row i + 1
@@ -404,7 +410,7 @@ __device__ __forceinline__ void fwd_row(int i, FwdRow<E, VW>& S, const RowRing<E
   {
     const int t = i + 1 + kRowPF;
     const int sn = t % kRowSlots;
-    const bool vx = live && t + 1 <= n, vb = live && t >= 1 && t <= n;
+    const bool vx = hx && live && t + 1 <= n, vb = live && t >= 1 && t <= n;
     ring.issue(0, sn, xb, t + 1, pitch, c0, vx);
     if (mom) ring.issue(1, sn, xpb, t + 1, pitch, c0, vx);
     ring.issue(2, sn, bb, t, pitch, c0, vb);
@@ -468,10 +474,11 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_row_kernel(const
   }
   const int ci = inst * A.m + A.kidx;
   const E ati = A.a ? (A.at ? A.at[ci] : A.a[ci]) : E(0);
-  const bool mom = A.xp != nullptr && ati != E(0);
-  const E* xb = A.x + I.off;
-  const E* xpb = A.xp ? A.xp + I.off : xb;
+  const bool hx = A.x != nullptr;  // else y = 0: the x copies are zero fills from b's address
+  const bool mom = hx && A.xp != nullptr && ati != E(0);
   const E* bb = A.b + I.off;
+  const E* xb = hx ? A.x + I.off : bb;
+  const E* xpb = A.xp ? A.xp + I.off : xb;
   E* zb = A.z + I.off;
   const int c0 = lane * VW;
   const bool live = c0 < pitch;
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_row_kernel(const
   // step t (0..n) brings x and x_prev of row t + 1 and b of row t
   auto issue = [&](int t) {
     const int sl = t % kRowSlots;
-    const bool vx = live && t + 1 <= n, vb = live && t >= 1 && t <= n;
+    const bool vx = hx && live && t + 1 <= n, vb = live && t >= 1 && t <= n;
     ring.issue(0, sl, xb, t + 1, pitch, c0, vx);
     if (mom) ring.issue(1, sl, xpb, t + 1, pitch, c0, vx);
     ring.issue(2, sl, bb, t, pitch, c0, vb);
@@ -514,13 +521,13 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_row_kernel(const
   scaled_rhs<E, VW>(S.Y[2], S.Y[0], S.Y[1], bv, rc, axr, ayr, d1r, d2r, S.rp);
   // the loop consumed steps 0 and 1; fwd_row(i) consumes step i + 1 and issues step i + 1 + PF
   for (int i = 1; i <= n; i += 3) {
-    fwd_row<E, VW, 0>(i, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, pitch,
+    fwd_row<E, VW, 0>(i, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, hx, pitch,
                       zb + (long long)i * pitch + c0, xb, xpb, bb, n, c0);
     if (i + 1 > n) break;
-    fwd_row<E, VW, 1>(i + 1, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, pitch,
+    fwd_row<E, VW, 1>(i + 1, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, hx, pitch,
                       zb + (long long)(i + 1) * pitch + c0, xb, xpb, bb, n, c0);
     if (i + 2 > n) break;
-    fwd_row<E, VW, 2>(i + 2, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, pitch,
+    fwd_row<E, VW, 2>(i + 2, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, hx, pitch,
                       zb + (long long)(i + 2) * pitch + c0, xb, xpb, bb, n, c0);
   }
   row_wait_all();
@@ -550,12 +557,13 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_row_kernel(cons
     }
   }
   const int ci = inst * A.m + A.kidx;
-  const E wi = A.w[ci] * A.relax * (E(2) - A.relax);
+  const E wi = (A.w ? A.w[ci] : E(1)) * A.relax * (E(2) - A.relax);
   const E ai = A.a ? A.a[ci] : E(0);
-  const bool mom = A.xp != nullptr;
-  const E* xb = A.x + I.off;
-  const E* xpb = A.xp ? A.xp + I.off : xb;
+  const bool hx = A.x != nullptr;  // else x = 0: zero fills from z's address
+  const bool mom = hx && A.xp != nullptr;
   const E* zb = A.z + I.off;
+  const E* xb = hx ? A.x + I.off : zb;
+  const E* xpb = A.xp ? A.xp + I.off : xb;
   E* ox = A.out_x + I.off;
   E* oxp = A.out_xp ? A.out_xp + I.off : nullptr;
   const int c0 = lane * VW;
@@ -583,7 +591,7 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_row_kernel(cons
     const int sl = (n - t) % kRowSlots;
     const bool v = live && t >= 1;
     ring.issue(0, sl, zb, t, pitch, c0, v);
-    ring.issue(1, sl, xb, t, pitch, c0, v);
+    ring.issue(1, sl, xb, t, pitch, c0, v && hx);
     if (mom) ring.issue(2, sl, xpb, t, pitch, c0, v);
     row_commit();
   };
@@ -679,6 +687,15 @@ richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, cons
   return RICHM_OK;
 }
 
+template <typename E>
+richm_status launch_ssor_apply(richm_operator* op, const E* r, E* z, E* out, double relax, cudaStream_t s) {
+  return launch_ssor_sweep<E>(op, nullptr, nullptr, r, z, out, nullptr, nullptr, nullptr, nullptr, 1, 0, relax,
+                              nullptr, s);
+}
+
+template richm_status launch_ssor_apply<float>(richm_operator*, const float*, float*, float*, double, cudaStream_t);
+template richm_status launch_ssor_apply<double>(richm_operator*, const double*, double*, double*, double,
+                                                cudaStream_t);
 template richm_status launch_ssor_sweep<float>(richm_operator*, const float*, const float*, const float*, float*,
                                                float*, float*, const float*, const float*, const float*, int, int,
                                                double, const int*, cudaStream_t);

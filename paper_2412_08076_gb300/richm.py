@@ -93,10 +93,12 @@ _SIGS = {
     "richm_solver_destroy": (None, [_P]),
     "richm_refine": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _P, _SZ, _P]),
     "richm_checkpoint_elems": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
-    "richm_forward_checkpointed": (_I, [_P, _I, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _SZ, _P]),
+    "richm_forward_checkpointed": (_I, [_P, _I, _P, _P, _P, _P, _P, _I, _I, _I, _I, C.c_double, _P, _P, _P, _SZ,
+                                        _P]),
     "richm_adjoint_workspace": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
     "richm_loss_log_residual": (_I, [_P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
-    "richm_sweeps_adjoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "richm_sweeps_adjoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P, _P, _I, _I, _I, C.c_double, _P, _P, _P, _P, _P,
+                                  _SZ, _P]),
     "richm_meta_param_count": (_I, [_I, C.POINTER(_I)]),
     "richm_meta_forward": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "richm_meta_backward": (_I, [_P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P]),
@@ -365,20 +367,24 @@ class Operator:
         return e.value
 
     def forward_checkpointed(self, dtype, x0, b, w, alpha, alpha_t, m, K, every, precond, ckpts, xK, work=None,
-                             stream=None):
+                             stream=None, relax=1.0):
+        """richm_forward_checkpointed (precond 2: SSOR with relaxation factor `relax`)."""
         if work is None:
             work = self.workspace(self._ws("richm_adjoint_workspace", dtype, every))
         _check(load().richm_forward_checkpointed(self.handle, dtype, _ptr(x0), _ptr(b), _ptr(w), _ptr(alpha),
-                                                 _ptr(alpha_t), m, K, every, precond, _ptr(ckpts), _ptr(xK),
+                                                 _ptr(alpha_t), m, K, every, precond, float(relax), _ptr(ckpts),
+                                                 _ptr(xK),
                                                  _ptr(work), work.numel(), _stream(stream)),
                "richm_forward_checkpointed")
 
     def sweeps_adjoint(self, dtype, ckpts, every, b, gK, w, alpha, alpha_t, m, K, precond, g_w=None, g_alpha=None,
-                       g_alpha_t=None, g_x0=None, work=None, stream=None):
+                       g_alpha_t=None, g_x0=None, work=None, stream=None, relax=1.0):
+        """richm_sweeps_adjoint (the same precond and relax as the forward)."""
         if work is None:
             work = self.workspace(self._ws("richm_adjoint_workspace", dtype, every))
         _check(load().richm_sweeps_adjoint(self.handle, dtype, _ptr(ckpts), every, _ptr(b), _ptr(gK), _ptr(w),
-                                           _ptr(alpha), _ptr(alpha_t), m, K, precond, _ptr(g_w), _ptr(g_alpha),
+                                           _ptr(alpha), _ptr(alpha_t), m, K, precond, float(relax), _ptr(g_w),
+                                           _ptr(g_alpha),
                                            _ptr(g_alpha_t), _ptr(g_x0), _ptr(work), work.numel(), _stream(stream)),
                "richm_sweeps_adjoint")
 

@@ -35,8 +35,14 @@ class Batch:
 
 
 class Trainer:
-    def __init__(self, params: np.ndarray, m=16, K=64, every=8, lr=2e-3):
+    """Algorithm 1 on the GPU: meta forward, K checkpointed sweeps, loss, adjoint sweeps,
+    meta backward, Adam. precond 2 trains the SSOR-preconditioned iteration (relaxation
+    factor `relax`); its weights are then scaled by 1 instead of the Gershgorin bound,
+    since the spectrum of B^{-1} A lies in (0, 1]."""
+
+    def __init__(self, params: np.ndarray, m=16, K=64, every=8, lr=2e-3, precond=0, relax=1.0):
         self.m, self.K, self.every, self.lr = m, K, every, lr
+        self.precond, self.relax = precond, relax
         self.P = torch.tensor(params, dtype=torch.float32, device="cuda")
         self.m1 = torch.zeros_like(self.P)
         self.m2 = torch.zeros_like(self.P)
@@ -64,14 +70,19 @@ class Trainer:
         """Loss (device FP64 scalar) and parameter gradient (device FP32)."""
         W = self._work(batch)
         op = batch.op
-        w, a = richm.meta_forward(self.P, batch.X, batch.G, self.m, W["acts"])
-        op.forward_checkpointed(richm.F32, W["x0"], batch.b, w, a, None, self.m, self.K, self.every, 0, W["ck"],
-                                W["xK"], work=W["work"])
+        G = self.scale(batch)
+        w, a = richm.meta_forward(self.P, batch.X, G, self.m, W["acts"])
+        op.forward_checkpointed(richm.F32, W["x0"], batch.b, w, a, None, self.m, self.K, self.every, self.precond,
+                                W["ck"], W["xK"], work=W["work"], relax=self.relax)
         loss = op.loss_log_residual(richm.F32, W["xK"], batch.b, W["g"], work=W["work"])
-        op.sweeps_adjoint(richm.F32, W["ck"], self.every, batch.b, W["g"], w, a, None, self.m, self.K, 0,
-                          W["gw"], W["ga"], None, None, work=W["work"])
-        gP = richm.meta_backward(self.P, batch.X, batch.G, W["acts"], self.m, W["gw"], W["ga"], W["gP"], W["mwork"])
+        op.sweeps_adjoint(richm.F32, W["ck"], self.every, batch.b, W["g"], w, a, None, self.m, self.K, self.precond,
+                          W["gw"], W["ga"], None, None, work=W["work"], relax=self.relax)
+        gP = richm.meta_backward(self.P, batch.X, G, W["acts"], self.m, W["gw"], W["ga"], W["gP"], W["mwork"])
         return loss, gP
+
+    def scale(self, batch: Batch):
+        """The per-instance spectral scale G of the output map w_i = exp(o_i) / G."""
+        return torch.ones_like(batch.G) if self.precond == 2 else batch.G
 
     def step(self, batch: Batch, lr: float | None = None):
         loss, gP = self.loss_and_grad(batch)

@@ -7,6 +7,7 @@ import torch
 
 import richm_synth as synth
 from gpu_util import coef, from_dev, make_op, nag_weights, to_dev
+from oracle.iterations import ssor_binv_matrix
 from oracle.operators import assemble_q1, gershgorin_max
 from oracle.training import (adam_step, log_rel_residual, loss_and_grads, meta_output_map, mlp_forward,
                              to_torch_sparse)
@@ -33,21 +34,21 @@ def _setup(sizes=(7, 16, 33), m=4, seed=3, dtype=richm.F64):
     return insts, op, As, w, a, fs, x0
 
 
-def _gpu_grads(op, dtype, x0, fs, w, a, at, m, K, every, precond=0):
+def _gpu_grads(op, dtype, x0, fs, w, a, at, m, K, every, precond=0, relax=1.0):
     X0 = to_dev(op, x0, dtype)
     B = to_dev(op, fs, dtype)
     W, A_ = coef(w, dtype), coef(a, dtype)
     AT = None if at is None else coef(at, dtype)
     ck = torch.zeros(op.checkpoint_elems(K, every), dtype=richm.TORCH_DTYPE[dtype], device="cuda")
     XK = op.zeros(dtype)
-    op.forward_checkpointed(dtype, X0, B, W, A_, AT, m, K, every, precond, ck, XK)
+    op.forward_checkpointed(dtype, X0, B, W, A_, AT, m, K, every, precond, ck, XK, relax=relax)
     gK = op.zeros(dtype)
     loss = op.loss_log_residual(dtype, XK, B, gK)
     gw = torch.zeros_like(W)
     ga = torch.zeros_like(A_)
     gat = None if at is None else torch.zeros_like(A_)
     gx0 = op.zeros(dtype)
-    op.sweeps_adjoint(dtype, ck, every, B, gK, W, A_, AT, m, K, precond, gw, ga, gat, gx0)
+    op.sweeps_adjoint(dtype, ck, every, B, gK, W, A_, AT, m, K, precond, gw, ga, gat, gx0, relax=relax)
     return (loss.item(), gw.cpu().numpy(), ga.cpu().numpy(), None if gat is None else gat.cpu().numpy(),
             from_dev(op, gx0, dtype), from_dev(op, XK, dtype))
 
@@ -196,3 +197,77 @@ def test_meta_backward_and_adam_match_oracle():
     pr, a1, a2 = adam_step(p0.cpu().numpy().astype(np.float64), got.astype(np.float64), 0.0, 0.0, 1, lr=1e-2)
     pr, a1, a2 = adam_step(pr, got.astype(np.float64), a1, a2, 2, lr=1e-2)
     np.testing.assert_allclose(P.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+
+
+# ---------------------------------------------------------------- SSOR-preconditioned sweeps
+
+def _ssor_weights(w):
+    """NAG weights for the SSOR-preconditioned spectrum, which lies in (0, 1]: the same
+    construction with G = 1 for every instance (shape of w)."""
+    return nag_weights(np.ones(w.shape[0]), w.shape[1], beta=0.3)[0]
+
+
+@pytest.mark.parametrize("every", [1, 4])
+def test_fp64_ssor_adjoint_matches_oracle_gradient(every):
+    insts, op, As, w, a, fs, x0 = _setup()
+    w = _ssor_weights(w)
+    m, K, relax = 4, 12, 1.3
+    Bm = [ssor_binv_matrix(A, relax) for A in As]
+    L, gw, ga, _, gx0, XK = _gpu_grads(op, richm.F64, x0, fs, w, a, None, m, K, every, precond=2, relax=relax)
+    Lo, gwo, gao, gxo = loss_and_grads(As, [f.ravel() for f in fs], [x.ravel() for x in x0], w, a, K, Binvs=Bm)
+    assert abs(L - Lo) <= 1e-12 * abs(Lo)
+    np.testing.assert_allclose(gw, gwo, rtol=1e-9, atol=1e-12 * np.abs(gwo).max())
+    np.testing.assert_allclose(ga, gao, rtol=1e-9, atol=1e-12 * np.abs(gao).max())
+    for i in range(len(insts)):
+        np.testing.assert_allclose(gx0[i].ravel(), gxo[i], rtol=1e-8, atol=1e-11 * np.abs(gxo[i]).max())
+
+
+def test_fp32_ssor_adjoint_close_to_oracle():
+    insts, op, As, w, a, fs, x0 = _setup(dtype=richm.F32)
+    w = _ssor_weights(w).astype(np.float32).astype(np.float64)
+    m, K, every, relax = 4, 16, 8, 1.5
+    Bm = [ssor_binv_matrix(A, relax) for A in As]
+    L, gw, ga, _, gx0, _ = _gpu_grads(op, richm.F32, x0, fs, w, a, None, m, K, every, precond=2, relax=relax)
+    Lo, gwo, gao, gxo = loss_and_grads(As, [f.ravel() for f in fs], [x.ravel() for x in x0], w, a, K, Binvs=Bm)
+    assert abs(L - Lo) <= 1e-5 * abs(Lo)
+    assert np.abs(gw - gwo).max() <= 2e-3 * np.abs(gwo).max()
+    assert np.abs(ga - gao).max() <= 2e-3 * np.abs(gao).max()
+
+
+@pytest.mark.parametrize("n", [20, 300])
+def test_fp64_ssor_nagex_adjoint_matches_central_differences(n):
+    # NAGex (independent look-ahead momentum); n = 300 takes the multi-chunk SSOR kernels
+    insts, op, As, w, a, fs, x0 = _setup(sizes=(n,))
+    w = _ssor_weights(w)
+    m, K, every, relax = 4, 8, 4, 1.2
+    at = a * 0.5 + 0.05
+    L, gw, ga, gat, gx0, _ = _gpu_grads(op, richm.F64, x0, fs, w, a, at, m, K, every, precond=2, relax=relax)
+
+    def loss_of(w_, a_, at_, x0_):
+        return _gpu_grads(op, richm.F64, x0_, fs, w_, a_, at_, m, K, every, precond=2, relax=relax)[0]
+
+    for i in (0, 2):
+        for name, arr, g in (("w", w, gw), ("a", a, ga), ("at", at, gat)):
+            def loss_at(d, name=name, arr=arr, i=i):
+                p = arr.copy()
+                p[0, i] += d
+                kw = dict(w_=w, a_=a, at_=at, x0_=x0)
+                kw[name + "_"] = p
+                return loss_of(**kw)
+            _fd_check(g[0, i], loss_at)
+    for (r, c) in ((3, 4), (n - 2, n // 2)):
+        def loss_at(d, r=r, c=c):
+            xp = [x.copy() for x in x0]
+            xp[0][r, c] += d
+            return loss_of(w, a, at, xp)
+        _fd_check(gx0[0][r, c], loss_at)
+
+
+def test_ssor_adjoint_argument_errors():
+    insts, op, As, w, a, fs, x0 = _setup(sizes=(8,))
+    m, K, every = 4, 4, 2
+    for bad in (0.0, 2.0, -1.0):
+        with pytest.raises(richm.RichmError):
+            _gpu_grads(op, richm.F64, x0, fs, w, a, None, m, K, every, precond=2, relax=bad)
+    with pytest.raises(richm.RichmError):
+        _gpu_grads(op, richm.F64, x0, fs, w, a, None, m, K, every, precond=3)
