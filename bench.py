@@ -508,7 +508,8 @@ def run_ours(args):
     def weight_supply():
         lib = richm.load()
         richm._check(lib.richm_meta_forward(richm._ptr(P), richm._ptr(X), richm._ptr(G), len(insts), M,
-                                            richm._ptr(w), richm._ptr(a), None, richm._stream(stream)),
+                                            richm.HEAD_NAG_SHARED, richm._ptr(w), richm._ptr(a), None, None,
+                                            richm._stream(stream)),
                      "richm_meta_forward")
 
     for _ in range(args.warmup):

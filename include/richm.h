@@ -78,6 +78,16 @@ typedef enum {
                       inner state only; the right-hand side and the weights stay FP32) */
 } richm_dtype;
 
+/* Output head of the meta network (Sec. 2.3): which Table 1 method its outputs
+ * parametrise, and how many there are for m steps. */
+typedef enum {
+  RICHM_HEAD_NAG_SHARED = 0, /* m + 1: w_i and one momentum a for every step (NAG, at = a) */
+  RICHM_HEAD_RICHARDSON = 1, /* m: w_i only (Richardson(m)) */
+  RICHM_HEAD_MOM = 2,        /* 2m: w_i, a_i; at_i = 0 (MOM) */
+  RICHM_HEAD_NAG = 3,        /* 2m: w_i, a_i; at_i = a_i (NAG) */
+  RICHM_HEAD_NAGEX = 4       /* 3m: w_i, a_i, at_i (NAGex) */
+} richm_meta_head;
+
 /* One PDE instance. eps, theta: anisotropy strength (0 < eps <= 1) and angle for
  * RICHM_ANISO_Q1; k: wavenumber for the Helmholtz kinds (k >= 0). */
 typedef struct {
@@ -368,23 +378,31 @@ richm_status richm_sweeps_adjoint(richm_operator* op, richm_dtype dtype, const v
 
 /* ------------------------------------------------------------------ meta network */
 
-/* Meta(theta; mu) of Sec. 2.3: an MLP 2 -> 64 -> 64 -> (m+1) with ReLU, FP32,
- * parameters packed as W1[64][2], b1[64], W2[64][64], b2[64], W3[m+1][64], b3[m+1]
- * (W[out][in]); richm_meta_param_count gives the total (5457 for m = 16).
- * Output map: w_i = exp(o_i) / G_b (i < m), a = sigmoid(o_m) for every step;
- * alpha_out[b][i] = a (NAG uses at = a). inputs: [B][2] = (log10 eps, theta).
- * G: [B] Gershgorin bounds. acts: [B][2*64 + m + 1] saved pre-activations for the
- * backward pass, or NULL. All arrays device, FP32. 1 <= m <= 63. */
-richm_status richm_meta_param_count(int m, int* count);
-richm_status richm_meta_forward(const float* params, const float* inputs, const float* G, int B, int m,
-                                float* w_out, float* alpha_out, float* acts, void* stream);
+/* Meta(theta; mu) of Sec. 2.3: an MLP 2 -> 64 -> 64 -> nout with ReLU, FP32, nout the
+ * head's output count (richm_meta_head, at most 64), parameters packed as W1[64][2],
+ * b1[64], W2[64][64], b2[64], W3[nout][64], b3[nout] (W[out][in]);
+ * richm_meta_param_count gives the total (5457 for m = 16 and the shared-momentum head).
+ * Output map: w_i = exp(o_i) / G_b (i < m); the shared head writes a = sigmoid(o_m) to
+ * every alpha_out[b][i]; the per-step heads write alpha_out[b][i] = sigmoid(o_{m+i}); the
+ * NAGex head writes alpha_t_out[b][i] = sigmoid(o_{2m+i}); the MOM head writes zeros to
+ * alpha_t_out if it is not NULL (the sweeps' at = 0). inputs: [B][2] = (log10 eps,
+ * theta). G: [B] spectral scales (the Gershgorin bounds, or 1 for an SSOR-preconditioned
+ * spectrum). acts: [B][2*64 + nout] saved pre-activations for the backward pass, or
+ * NULL. alpha_out may be NULL for the Richardson head, alpha_t_out for every head but
+ * NAGex. All arrays device, FP32. Errors: RICHM_ERR_ARG for an unknown head, m < 1 or
+ * more than 64 outputs, or a null array the head needs. */
+richm_status richm_meta_param_count(int m, int head, int* count);
+richm_status richm_meta_forward(const float* params, const float* inputs, const float* G, int B, int m, int head,
+                                float* w_out, float* alpha_out, float* alpha_t_out, float* acts, void* stream);
 
-/* Backward of richm_meta_forward given dL/dw [B][m] and dL/dalpha [B][m] (summed over
- * the steps for the shared momentum). g_params: [count], written (batch sum,
- * fixed order). work: at least B * count floats. */
+/* Backward of richm_meta_forward given dL/dw, dL/dalpha and (NAGex head) dL/dalpha_t,
+ * each [B][m] (dL/dalpha summed over the steps for the shared momentum; g_alpha may be
+ * NULL for the Richardson head, g_alpha_t for every head but NAGex). g_params: [count],
+ * written (batch sum, fixed order). work: at least B * count floats. */
 richm_status richm_meta_backward(const float* params, const float* inputs, const float* G, const float* acts,
-                                 int B, int m, const float* g_w, const float* g_alpha, float* g_params,
-                                 void* work, size_t work_bytes, void* stream);
+                                 int B, int m, int head, const float* g_w, const float* g_alpha,
+                                 const float* g_alpha_t, float* g_params, void* work, size_t work_bytes,
+                                 void* stream);
 
 /* One Adam step (Kingma & Ba 2015) over `count` parameters in place; t is 1-based. */
 richm_status richm_adam_step(float* params, const float* grads, float* m1, float* m2, int count, int t,

@@ -32,10 +32,12 @@ def to_torch_sparse(A):
                                    torch.from_numpy(A.data), size=A.shape)
 
 
-def unrolled_nag(At, f, u0, w, a, K, Dinv=None, Binv=None):
-    """K inner NAG steps (Table 1, at = a) in torch; u^{-1} = u0 (zero velocity).
+def unrolled_nag(At, f, u0, w, a, K, Dinv=None, Binv=None, at=None):
+    """K inner steps of Table 1's NAGex form in torch; u^{-1} = u0 (zero velocity).
 
     w, a: tensors of length m (a may be a length-m tensor or a scalar tensor).
+    at: the look-ahead momenta (length m), or None for at = a (NAG); zeros give MOM,
+    and a = at = 0 Richardson(m).
     Dinv: optional tensor, elementwise B^{-1} = D^{-1} (eq. 17).
     Binv: optional dense tensor, B^{-1} as a matrix (e.g. the SSOR preconditioner).
     """
@@ -45,7 +47,8 @@ def unrolled_nag(At, f, u0, w, a, K, Dinv=None, Binv=None):
     for k in range(K):
         i = k % m
         ai = a[i] if a.dim() > 0 else a
-        ut = u + ai * v
+        ati = ai if at is None else at[i]
+        ut = u + ati * v
         r = f - At @ ut
         if Dinv is not None:
             r = Dinv * r
@@ -129,10 +132,42 @@ def meta_output_map(o, G, m):
     return w, a
 
 
-def mlp_loss_and_grads(params, X, G, m, As, fs, K):
-    """Training loss of Algorithm 1 (x0 = 0, NAG, K steps) and its gradient wrt the MLP.
+# Output heads of the meta network: which Table 1 method its outputs parametrise.
+HEAD_NAG_SHARED, HEAD_RICHARDSON, HEAD_MOM, HEAD_NAG, HEAD_NAGEX = 0, 1, 2, 3, 4
 
-    Returns (L, [(dW, db) per layer], w (B, m), a (B,)). Pinned by: finite differences.
+
+def head_outputs(head, m):
+    """Number of network outputs of a head: m weights, plus one shared momentum (NAG
+    with a single a), m per-step momenta (MOM, NAG) or 2m (NAGex: a_i and at_i)."""
+    return {HEAD_NAG_SHARED: m + 1, HEAD_RICHARDSON: m, HEAD_MOM: 2 * m, HEAD_NAG: 2 * m, HEAD_NAGEX: 3 * m}[head]
+
+
+def head_map(o, G, m, head):
+    """(w, a, at), each (B, m), from network outputs o (B, head_outputs) in torch:
+    w_i = exp(o_i) / G; a_i = sigmoid of the momentum output(s); at per Table 1's row
+    (NAG: at = a; MOM: 0; NAGex: its own outputs; Richardson: a = at = 0)."""
+    B = o.shape[0]
+    w = torch.exp(o[:, :m]) / G.reshape(-1, 1)
+    zero = torch.zeros(B, m, dtype=o.dtype)
+    if head == HEAD_RICHARDSON:
+        return w, zero, zero
+    if head == HEAD_NAG_SHARED:
+        a = torch.sigmoid(o[:, m]).reshape(-1, 1).expand(B, m)
+        return w, a, a
+    a = torch.sigmoid(o[:, m:2 * m])
+    if head == HEAD_MOM:
+        return w, a, zero
+    if head == HEAD_NAG:
+        return w, a, a
+    return w, a, torch.sigmoid(o[:, 2 * m:3 * m])
+
+
+def mlp_loss_and_grads(params, X, G, m, As, fs, K, head=HEAD_NAG_SHARED, Binvs=None):
+    """Training loss of Algorithm 1 (x0 = 0, K steps of the head's Table 1 method,
+    optionally with dense B^{-1} matrices) and its gradient wrt the MLP.
+
+    Returns (L, [(dW, db) per layer], w (B, m), a): a is (B,) for the shared-momentum
+    head, else the (B, m) momenta. Pinned by: finite differences.
     """
     tp = [(torch.tensor(np.asarray(W, dtype=np.float64), requires_grad=True),
            torch.tensor(np.asarray(b, dtype=np.float64), requires_grad=True)) for W, b in params]
@@ -141,19 +176,20 @@ def mlp_loss_and_grads(params, X, G, m, As, fs, K):
         h = h @ W.T + b
         if li < len(tp) - 1:
             h = torch.relu(h)
-    Gt = torch.from_numpy(np.asarray(G, dtype=np.float64)).reshape(-1, 1)
-    w = torch.exp(h[:, :m]) / Gt
-    a = torch.sigmoid(h[:, m])
+    Gt = torch.from_numpy(np.asarray(G, dtype=np.float64))
+    w, a, at = head_map(h, Gt, m, head)
     total = 0.0
     for b in range(len(As)):
         At = to_torch_sparse(As[b])
         f = torch.from_numpy(np.asarray(fs[b], dtype=np.float64))
-        uK = unrolled_nag(At, f, torch.zeros_like(f), w[b], a[b], K)
+        Binv = None if Binvs is None else torch.from_numpy(np.asarray(Binvs[b], dtype=np.float64))
+        uK = unrolled_nag(At, f, torch.zeros_like(f), w[b], a[b], K, Binv=Binv, at=at[b])
         total = total + log_rel_residual(At, f, uK)
     L = total / len(As)
     L.backward()
     grads = [(W.grad.numpy(), b.grad.numpy()) for W, b in tp]
-    return float(L.detach()), grads, w.detach().numpy(), a.detach().numpy()
+    a_out = a[:, 0] if head == HEAD_NAG_SHARED else a
+    return float(L.detach()), grads, w.detach().numpy(), a_out.detach().numpy()
 
 
 def adam_step(p, g, m1, m2, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

@@ -5,9 +5,14 @@ weights and the momentum of NAG-Richardson(m). Its output o maps to
 w_i = exp(o_i) / G (G the instance's Gershgorin bound) and a = sigmoid(o_m).
 The initial network is random in its hidden layers and starts its output layer
 at the momentum-aware Chebyshev weights: eqs. 8-9 on [c G / 30, c G] with c = 1.6,
-the smallest stretch of the semi-iteration interval for which every per-mode
-period transfer of NAG with a = 0.3 stays inside the unit disk on [0, G]. So an
-untrained network already gives a convergent solver, and training only improves it.
+a stretch of the semi-iteration interval for which every per-mode period transfer
+of NAG with a = 0.3 stays inside the unit disk on [0, G]. So an untrained network
+already gives a convergent solver, and training only improves it.
+
+The other output heads (Richardson, MOM, NAG and NAGex with per-step momenta) start
+the same way: Chebyshev weights for Richardson (c = 1), and for the momentum heads
+the smallest stretch c (in steps of 0.05) whose period transfers with momentum beta
+stay in the unit disk, every a_i (and at_i) at beta.
 """
 from __future__ import annotations
 
@@ -30,13 +35,42 @@ def chebyshev_unit_weights(m: int, stretch: float = STABLE_STRETCH, alpha: float
     return 2.0 / (lmax + lmin + (lmax - lmin) * x)
 
 
-def init_params(m: int = 16, beta: float = 0.3, seed: int = 7, out_scale: float = 0.01) -> np.ndarray:
+HEAD_NAG_SHARED, HEAD_RICHARDSON, HEAD_MOM, HEAD_NAG, HEAD_NAGEX = 0, 1, 2, 3, 4
+
+
+def head_outputs(head: int, m: int) -> int:
+    return {HEAD_NAG_SHARED: m + 1, HEAD_RICHARDSON: m, HEAD_MOM: 2 * m, HEAD_NAG: 2 * m, HEAD_NAGEX: 3 * m}[head]
+
+
+def stable_stretch(m: int, beta: float, lookahead: bool, step: float = 0.05, top: float = 4.0) -> float:
+    """Smallest c = 1 + k step for which the period transfer of Chebyshev weights on
+    [c/30, c] with momentum beta (look-ahead beta for NAG, 0 for MOM) has spectral
+    radius <= 1 at every eigenvalue of [0, 1]."""
+    lam = np.linspace(0.0, 1.0, 4001)
+    for k in range(int(round((top - 1.0) / step)) + 1):
+        c = 1.0 + k * step
+        r = period_radius(chebyshev_unit_weights(m, c), beta, lam, beta if lookahead else 0.0)
+        if r.max() <= 1.0 + 1e-12:
+            return c
+    raise ValueError(f"no stable stretch up to {top} for m = {m}, beta = {beta}")
+
+
+def init_params(m: int = 16, beta: float = 0.3, seed: int = 7, out_scale: float = 0.01,
+                head: int = HEAD_NAG_SHARED) -> np.ndarray:
     """Flat FP32 parameter vector in the library's order (W1, b1, W2, b2, W3, b3)."""
     import richm_synth as synth  # seeded generator shared by every consumer
-    layers = synth.mlp_init((2, HIDDEN, HIDDEN, m + 1), seed=seed)
+    layers = synth.mlp_init((2, HIDDEN, HIDDEN, head_outputs(head, m)), seed=seed)
     W3, b3 = layers[2]
     W3 = W3 * out_scale
-    b3 = np.concatenate([np.log(chebyshev_unit_weights(m)), [math.log(beta / (1.0 - beta))]])
+    logit = math.log(beta / (1.0 - beta))
+    if head == HEAD_NAG_SHARED:
+        b3 = np.concatenate([np.log(chebyshev_unit_weights(m)), [logit]])
+    elif head == HEAD_RICHARDSON:
+        b3 = np.log(chebyshev_unit_weights(m, 1.0))
+    else:
+        c = stable_stretch(m, beta, head != HEAD_MOM)
+        moms = (2 if head == HEAD_NAGEX else 1) * m
+        b3 = np.concatenate([np.log(chebyshev_unit_weights(m, c)), np.full(moms, logit)])
     layers[2] = (W3, b3)
     flat = []
     for W, b in layers:
@@ -45,16 +79,19 @@ def init_params(m: int = 16, beta: float = 0.3, seed: int = 7, out_scale: float 
     return np.concatenate(flat).astype(np.float32)
 
 
-def trained_path(m: int) -> str:
-    return os.path.join(PARAM_DIR, f"meta_m{m}.npy")
+def trained_path(m: int, head: int = HEAD_NAG_SHARED, precond: int = 0) -> str:
+    if head == HEAD_NAG_SHARED and precond == 0:
+        return os.path.join(PARAM_DIR, f"meta_m{m}.npy")
+    return os.path.join(PARAM_DIR, f"meta_m{m}_head{head}_precond{precond}.npy")
 
 
-def load_params(m: int = 16, prefer_trained: bool = True) -> tuple[np.ndarray, str]:
+def load_params(m: int = 16, prefer_trained: bool = True, head: int = HEAD_NAG_SHARED,
+                precond: int = 0) -> tuple[np.ndarray, str]:
     """(params, source): the trained network if one was saved, else the initial one."""
-    p = trained_path(m)
+    p = trained_path(m, head, precond)
     if prefer_trained and os.path.exists(p):
         return np.load(p).astype(np.float32), "trained"
-    return init_params(m), "initial"
+    return init_params(m, head=head), "initial"
 
 
 def symbol_max(eps: float, theta: float, grid: int = 513) -> float:
@@ -78,16 +115,18 @@ def symbol_max(eps: float, theta: float, grid: int = 513) -> float:
     return float(S.max())
 
 
-def period_radius(w, beta: float, lam) -> np.ndarray:
-    """Spectral radius of one NAG period's 2x2 per-mode transfer at each eigenvalue lam
-    (A symmetric, so every eigenvector evolves independently)."""
+def period_radius(w, beta: float, lam, lookahead: float | None = None) -> np.ndarray:
+    """Spectral radius of one period's 2x2 per-mode transfer at each eigenvalue lam
+    (A symmetric, so every eigenvector evolves independently) for the Table 1 step
+    e' = e + beta (e - e_prev) - w lam (e + at (e - e_prev)), at = `lookahead`
+    (default beta: NAG; 0: MOM)."""
+    at = beta if lookahead is None else lookahead
     lam = np.asarray(lam, dtype=np.float64)
     P = np.tile(np.eye(2), (lam.size, 1, 1))
     for wi in w:
-        mu = 1.0 - wi * lam
         T = np.zeros((lam.size, 2, 2))
-        T[:, 0, 0] = mu * (1.0 + beta)
-        T[:, 0, 1] = -mu * beta
+        T[:, 0, 0] = 1.0 + beta - wi * lam * (1.0 + at)
+        T[:, 0, 1] = -beta + wi * lam * at
         T[:, 1, 0] = 1.0
         P = T @ P
     return np.abs(np.linalg.eigvals(P)).max(axis=1)

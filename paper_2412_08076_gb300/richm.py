@@ -23,6 +23,9 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_UNSUPPORT
 ANISO_Q1, HELMHOLTZ_FD5_ABC, HELMHOLTZ_FD5_DIRICHLET = 0, 1, 2
 # richm_dtype
 F64, F32, C64, C128, BF16 = 0, 1, 2, 3, 4
+HEAD_NAG_SHARED, HEAD_RICHARDSON, HEAD_MOM, HEAD_NAG, HEAD_NAGEX = 0, 1, 2, 3, 4
+HEAD_OUTPUTS = {HEAD_NAG_SHARED: lambda m: m + 1, HEAD_RICHARDSON: lambda m: m, HEAD_MOM: lambda m: 2 * m,
+                HEAD_NAG: lambda m: 2 * m, HEAD_NAGEX: lambda m: 3 * m}
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.complex64, C128: torch.complex128,
                BF16: torch.bfloat16}
@@ -99,9 +102,9 @@ _SIGS = {
     "richm_loss_log_residual": (_I, [_P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_sweeps_adjoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P, _P, _I, _I, _I, C.c_double, _P, _P, _P, _P, _P,
                                   _SZ, _P]),
-    "richm_meta_param_count": (_I, [_I, C.POINTER(_I)]),
-    "richm_meta_forward": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
-    "richm_meta_backward": (_I, [_P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _SZ, _P]),
+    "richm_meta_param_count": (_I, [_I, _I, C.POINTER(_I)]),
+    "richm_meta_forward": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P]),
+    "richm_meta_backward": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_adam_step": (_I, [_P, _P, _P, _P, _I, _I, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
     "richm_fourier_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_fourier_correction": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
@@ -171,9 +174,9 @@ def chebyshev_weights(lmax: float, lmin: float, m: int) -> list[float]:
     return list(out)
 
 
-def meta_param_count(m: int) -> int:
+def meta_param_count(m: int, head: int = HEAD_NAG_SHARED) -> int:
     c = C.c_int()
-    _check(load().richm_meta_param_count(m, C.byref(c)), "richm_meta_param_count")
+    _check(load().richm_meta_param_count(m, head, C.byref(c)), "richm_meta_param_count")
     return c.value
 
 
@@ -443,24 +446,36 @@ class Solver:
 # ------------------------------------------------------------- meta network
 
 def meta_forward(params, inputs, G, m, acts=None, stream=None):
-    """richm_meta_forward: returns (w [B][m], alpha [B][m]) FP32 CUDA tensors."""
-    B = inputs.shape[0]
-    w = torch.empty(B, m, dtype=torch.float32, device="cuda")
-    a = torch.empty(B, m, dtype=torch.float32, device="cuda")
-    _check(load().richm_meta_forward(_ptr(params), _ptr(inputs), _ptr(G), B, m, _ptr(w), _ptr(a), _ptr(acts),
-                                     _stream(stream)), "richm_meta_forward")
+    """richm_meta_forward with the shared-momentum head: returns (w [B][m], alpha [B][m])
+    FP32 CUDA tensors (the sweeps take at = alpha)."""
+    w, a, _ = meta_forward_head(params, inputs, G, m, HEAD_NAG_SHARED, acts, stream)
     return w, a
 
 
-def meta_backward(params, inputs, G, acts, m, g_w, g_alpha, g_params=None, work=None, stream=None):
+def meta_forward_head(params, inputs, G, m, head, acts=None, stream=None):
+    """richm_meta_forward with any head: returns (w, alpha, alpha_t), each [B][m] FP32 CUDA
+    tensors or None, as the sweeps take them: alpha None for Richardson (no momentum),
+    alpha_t None where at = alpha (NAG heads), zeros for MOM."""
     B = inputs.shape[0]
-    cnt = meta_param_count(m)
+    w = torch.empty(B, m, dtype=torch.float32, device="cuda")
+    a = None if head == HEAD_RICHARDSON else torch.empty(B, m, dtype=torch.float32, device="cuda")
+    at = torch.empty(B, m, dtype=torch.float32, device="cuda") if head in (HEAD_MOM, HEAD_NAGEX) else None
+    _check(load().richm_meta_forward(_ptr(params), _ptr(inputs), _ptr(G), B, m, head, _ptr(w), _ptr(a), _ptr(at),
+                                     _ptr(acts), _stream(stream)), "richm_meta_forward")
+    return w, a, at
+
+
+def meta_backward(params, inputs, G, acts, m, g_w, g_alpha, g_params=None, work=None, stream=None,
+                  head=HEAD_NAG_SHARED, g_alpha_t=None):
+    B = inputs.shape[0]
+    cnt = meta_param_count(m, head)
     if g_params is None:
         g_params = torch.empty(cnt, dtype=torch.float32, device="cuda")
     if work is None:
         work = torch.empty(B * cnt * 4, dtype=torch.uint8, device="cuda")
-    _check(load().richm_meta_backward(_ptr(params), _ptr(inputs), _ptr(G), _ptr(acts), B, m, _ptr(g_w),
-                                      _ptr(g_alpha), _ptr(g_params), _ptr(work), work.numel(), _stream(stream)),
+    _check(load().richm_meta_backward(_ptr(params), _ptr(inputs), _ptr(G), _ptr(acts), B, m, head, _ptr(g_w),
+                                      _ptr(g_alpha), _ptr(g_alpha_t), _ptr(g_params), _ptr(work), work.numel(),
+                                      _stream(stream)),
            "richm_meta_backward")
     return g_params
 
@@ -470,8 +485,8 @@ def adam_step(params, grads, m1, m2, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-
                                   eps, _stream(stream)), "richm_adam_step")
 
 
-def meta_acts_size(B: int, m: int) -> int:
-    return B * (2 * 64 + m + 1)
+def meta_acts_size(B: int, m: int, head: int = HEAD_NAG_SHARED) -> int:
+    return B * (2 * 64 + HEAD_OUTPUTS[head](m))
 
 
 def pack_mlp_params(layers) -> list[float]:

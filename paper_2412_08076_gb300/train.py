@@ -3,7 +3,8 @@
 Each step: w, a = Meta(theta; mu) (library forward), K NAG sweeps from x0 = 0 with
 checkpoints (library forward), loss = mean log relative residual and its gradient
 (library), adjoint sweeps (library), network backward and Adam (library). Python only
-sequences the calls. Usage:
+sequences the calls. The network's head selects the Table 1 method (Richardson, MOM,
+NAG, NAGex; shared or per-step momenta) and --precond 2 the SSOR preconditioner. Usage:
   python -m paper_2412_08076_gb300.train --steps 1000 --out paper_2412_08076_gb300/params/meta_m16.npy
 """
 from __future__ import annotations
@@ -23,11 +24,12 @@ from . import richm
 class Batch:
     """One minibatch: operator, padded FP32 right-hand sides, network inputs."""
 
-    def __init__(self, insts, seed):
+    def __init__(self, insts, seed, normal_rhs=False):
         import richm_synth as synth
         self.insts = insts
         self.op = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0) for t in insts])
-        rhs = [synth.rhs_uniform(seed, i, t.n) for i, t in enumerate(insts)]
+        gen = synth.rhs_normal if normal_rhs else synth.rhs_uniform
+        rhs = [gen(seed, i, t.n) for i, t in enumerate(insts)]
         dense = torch.tensor(np.concatenate([r.ravel() for r in rhs]), dtype=torch.float32, device="cuda")
         self.b = self.op.pack(dense, richm.F32)
         self.X = torch.tensor(synth.meta_inputs(insts), dtype=torch.float32, device="cuda")
@@ -40,9 +42,10 @@ class Trainer:
     factor `relax`); its weights are then scaled by 1 instead of the Gershgorin bound,
     since the spectrum of B^{-1} A lies in (0, 1]."""
 
-    def __init__(self, params: np.ndarray, m=16, K=64, every=8, lr=2e-3, precond=0, relax=1.0):
+    def __init__(self, params: np.ndarray, m=16, K=64, every=8, lr=2e-3, precond=0, relax=1.0,
+                 head=richm.HEAD_NAG_SHARED):
         self.m, self.K, self.every, self.lr = m, K, every, lr
-        self.precond, self.relax = precond, relax
+        self.precond, self.relax, self.head = precond, relax, head
         self.P = torch.tensor(params, dtype=torch.float32, device="cuda")
         self.m1 = torch.zeros_like(self.P)
         self.m2 = torch.zeros_like(self.P)
@@ -58,9 +61,10 @@ class Trainer:
                 ck=torch.empty(op.checkpoint_elems(self.K, self.every), dtype=torch.float32, device="cuda"),
                 x0=op.zeros(richm.F32), xK=op.zeros(richm.F32), g=op.zeros(richm.F32),
                 work=op.workspace(op._ws("richm_adjoint_workspace", richm.F32, self.every)),
-                acts=torch.empty(richm.meta_acts_size(B, self.m), dtype=torch.float32, device="cuda"),
+                acts=torch.empty(richm.meta_acts_size(B, self.m, self.head), dtype=torch.float32, device="cuda"),
                 gw=torch.empty(B, self.m, dtype=torch.float32, device="cuda"),
-                ga=torch.empty(B, self.m, dtype=torch.float32, device="cuda"),
+                ga=torch.zeros(B, self.m, dtype=torch.float32, device="cuda"),
+                gat=torch.zeros(B, self.m, dtype=torch.float32, device="cuda"),
                 gP=torch.empty(self.P.numel(), dtype=torch.float32, device="cuda"),
                 mwork=torch.empty(B * self.P.numel() * 4, dtype=torch.uint8, device="cuda"),
             )
@@ -71,13 +75,15 @@ class Trainer:
         W = self._work(batch)
         op = batch.op
         G = self.scale(batch)
-        w, a = richm.meta_forward(self.P, batch.X, G, self.m, W["acts"])
-        op.forward_checkpointed(richm.F32, W["x0"], batch.b, w, a, None, self.m, self.K, self.every, self.precond,
+        w, a, at = richm.meta_forward_head(self.P, batch.X, G, self.m, self.head, W["acts"])
+        op.forward_checkpointed(richm.F32, W["x0"], batch.b, w, a, at, self.m, self.K, self.every, self.precond,
                                 W["ck"], W["xK"], work=W["work"], relax=self.relax)
         loss = op.loss_log_residual(richm.F32, W["xK"], batch.b, W["g"], work=W["work"])
-        op.sweeps_adjoint(richm.F32, W["ck"], self.every, batch.b, W["g"], w, a, None, self.m, self.K, self.precond,
-                          W["gw"], W["ga"], None, None, work=W["work"], relax=self.relax)
-        gP = richm.meta_backward(self.P, batch.X, G, W["acts"], self.m, W["gw"], W["ga"], W["gP"], W["mwork"])
+        gat = W["gat"] if self.head == richm.HEAD_NAGEX else None
+        op.sweeps_adjoint(richm.F32, W["ck"], self.every, batch.b, W["g"], w, a, at, self.m, self.K, self.precond,
+                          W["gw"], W["ga"] if a is not None else None, gat, None, work=W["work"], relax=self.relax)
+        gP = richm.meta_backward(self.P, batch.X, G, W["acts"], self.m, W["gw"], W["ga"], W["gP"], W["mwork"],
+                                 head=self.head, g_alpha_t=gat)
         return loss, gP
 
     def scale(self, batch: Batch):
@@ -94,12 +100,12 @@ class Trainer:
         return self.P.detach().cpu().numpy()
 
 
-def make_batches(nbatches=8, B=64, n=255, seed=1000):
+def make_batches(nbatches=8, B=64, n=255, seed=1000, log_eps=(-3.0, 0.0), normal_rhs=False):
     import richm_synth as synth
     out = []
     for j in range(nbatches):
-        insts = synth.batched_aniso(B, sizes=(n,), param_seed=seed + j)
-        out.append(Batch(insts, seed=seed + 500 + j))
+        insts = synth.batched_aniso(B, sizes=(n,), param_seed=seed + j, log_eps=log_eps)
+        out.append(Batch(insts, seed=seed + 500 + j, normal_rhs=normal_rhs))
     return out
 
 

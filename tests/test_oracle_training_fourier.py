@@ -172,3 +172,68 @@ def test_ssor_binv_matrix_is_the_operator():
     r = synth.rhs_uniform(5, 0, 5).ravel()
     np.testing.assert_allclose(M @ r, ssor_binv(A, 1.2)(r), rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(M, M.T, atol=1e-14 * np.abs(M).max())
+
+
+def test_head_map_hand_evaluated():
+    import torch
+    from oracle.training import (HEAD_MOM, HEAD_NAG, HEAD_NAG_SHARED, HEAD_NAGEX, HEAD_RICHARDSON, head_map,
+                                 head_outputs)
+    m = 2
+    assert [head_outputs(h, m) for h in range(5)] == [3, 2, 4, 4, 6]
+    L2, L3 = math.log(2.0), math.log(3.0)  # sigmoid(ln 3) = 3/4, sigmoid(-ln 3) = 1/4
+    o = torch.tensor([[0.0, L2, L3, -L3, 0.0, L3]], dtype=torch.float64)
+    G = torch.tensor([4.0], dtype=torch.float64)
+    expect = {
+        HEAD_RICHARDSON: ([0.25, 0.5], [0, 0], [0, 0]),
+        HEAD_NAG_SHARED: ([0.25, 0.5], [0.75, 0.75], [0.75, 0.75]),
+        HEAD_MOM: ([0.25, 0.5], [0.75, 0.25], [0, 0]),
+        HEAD_NAG: ([0.25, 0.5], [0.75, 0.25], [0.75, 0.25]),
+        HEAD_NAGEX: ([0.25, 0.5], [0.75, 0.25], [0.5, 0.75]),
+    }
+    for head, (we, ae, ate) in expect.items():
+        w, a, at = head_map(o[:, :head_outputs(head, m)], G, m, head)
+        np.testing.assert_allclose(w.numpy(), [we], rtol=1e-15)
+        np.testing.assert_allclose(a.numpy(), [ae], rtol=1e-15)
+        np.testing.assert_allclose(at.numpy(), [ate], rtol=1e-15)
+
+
+def test_unrolled_with_lookahead_momenta_matches_inner_steps():
+    # the torch unroll with separate at equals the Table 1 steps of the numpy oracle
+    import torch
+    from oracle.training import to_torch_sparse, unrolled_nag
+    As, fs, u0s, w, a, K = _problem(B=1, n=6, K=11, m=3)
+    at = np.array([0.1, 0.6, 0.35])
+    for at_ in (at, np.zeros(3)):
+        u = unrolled_nag(to_torch_sparse(As[0]), torch.from_numpy(fs[0]), torch.from_numpy(u0s[0]),
+                         torch.from_numpy(w[0]), torch.from_numpy(a[0]), K, at=torch.from_numpy(at_))
+        ref, _ = inner_steps(As[0], fs[0], u0s[0], None, w[0], a[0], at_, K=K)
+        np.testing.assert_allclose(u.numpy(), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_head_training_gradients_match_central_differences():
+    # every head, and the NAGex head through a dense SSOR B^{-1}
+    from oracle.iterations import ssor_binv_matrix
+    from oracle.training import HEAD_MOM, HEAD_NAGEX, HEAD_RICHARDSON, head_outputs
+    m, K, n = 3, 9, 5
+    insts = [synth.AnisoInstance(1e-2, 0.5, n), synth.AnisoInstance(0.5, 2.0, n)]
+    As = [assemble_q1(n, t.eps, t.theta) for t in insts]
+    fs = [synth.rhs_uniform(5, b, n).ravel() for b in range(2)]
+    X = synth.meta_inputs(insts)
+    rng = np.random.default_rng(1)
+    for head, ssor in ((HEAD_RICHARDSON, False), (HEAD_MOM, False), (HEAD_NAGEX, False), (HEAD_NAGEX, True)):
+        params = synth.mlp_init((2, 6, 6, head_outputs(head, m)), seed=4)
+        params = [(W * 0.3, b * 0.3) for W, b in params]
+        Bm = [ssor_binv_matrix(A, 1.2) for A in As] if ssor else None
+        G = np.ones(2) if ssor else np.array([gershgorin_max(A) for A in As])
+        L, grads, _, _ = mlp_loss_and_grads(params, X, G, m, As, fs, K, head=head, Binvs=Bm)
+        h = 1e-5
+        for li in range(3):
+            W, b = params[li]
+            r, c = rng.integers(0, W.shape[0]), rng.integers(0, W.shape[1])
+            vals = []
+            for sgn in (1, -1):
+                P = [(Wk.copy(), bk.copy()) for Wk, bk in params]
+                P[li][0][r, c] += sgn * h
+                vals.append(mlp_loss_and_grads(P, X, G, m, As, fs, K, head=head, Binvs=Bm)[0])
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - grads[li][0][r, c]) <= 1e-6 * max(1.0, abs(fd)), (head, ssor, li, fd)
