@@ -21,8 +21,14 @@
 //
 // Nothing outside the domain needs clearing at any level: rows outside 1..n get the
 // weight 0 (their inputs are zero, so they stay zero), and the lanes' stencil
-// coefficients that couple to columns >= n are zero, so those columns (zero in every
-// input, b included) stay zero as well.
+// couplings into columns >= n are masked, so those columns (zero in every input, b
+// included) stay zero as well.
+//
+// The real kernel is bound by instruction issue, so its arithmetic runs on pairs of
+// columns with the packed FP32 instructions of sm_100 and later (one issue slot for
+// two multiply-adds): a lane's four columns are two aligned pairs, and the stencil is
+// arranged so that only the sum of the horizontal couplings needs per-column
+// (unpaired) adds.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -51,24 +57,36 @@ struct SweepTArgs {
 // Per-warp state of the pipeline. Window slots rotate by phase: at phase p the new
 // row of every level goes into slot p; after it, U = slot (p+1)%3, C = slot (p+2)%3,
 // D = slot p. Unrolling the row loop by three makes every slot index a constant.
-// Each lane keeps only its own four values per row; the neighbours across lanes
-// are exchanged by shuffles when the stencil is applied.
-// Keep each window row's two cross-lane neighbours in registers (computed once when
-// the row enters the window) instead of re-shuffling them for every use: fewer
-// shuffles for 24 more registers, a gain for 8 sweeps per pass (2 blocks per SM
-// either way), a loss for 4 (it would spill at the 4-blocks-per-SM register cap).
-template <int TL>
-__host__ __device__ constexpr bool store_neighbours() { return TL >= 8; }
-
+// Each lane keeps only its own values per row; what crosses lanes is exchanged by
+// shuffles when the stencil is applied. Complex kernel: four floats (two complex
+// columns) per row.
 template <int TL>
 struct FusedState {
-  float Y[TL + 1][3][4];   // level s: rows of y_{s-1} (this lane's four columns)
-  float YL[TL + 1][3];     // their left / right cross-lane neighbours (store_neighbours)
-  float YR[TL + 1][3];
+  float Y[TL + 1][3][4];   // level s: rows of y_{s-1} (this lane's four values)
   float xc[TL + 1][4];     // level s: x_{s-1} on the centre row (MOM and NAGex only)
   float vc[TL + 1][4];     // level s: x_{s-1} - x_{s-2} on the centre row
   float prevx[2][TL + 1][4];  // outputs of level s at the last row steps (two slots)
 };
+
+// The real kernel's state: the same rows, this lane's four columns as two pairs.
+template <int TL>
+struct PairState {
+  float2 Y[TL + 1][3][2];
+  float2 xc[TL + 1][2];
+  float2 vc[TL + 1][2];
+  float2 prevx[2][TL + 1][2];
+};
+
+__device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long A, B, D;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D) : "l"(A), "l"(B));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(D));
+  return r;
+}
 
 constexpr int kPrefetch = 2;  // row steps between issuing a row's copies and using it
 
@@ -122,39 +140,38 @@ struct FusedCtx {
   // loaded up to row vhi and its results stored for rows r0 .. shi.
   int rlo, vhi, r0, shi;
   bool live, store_cols;
-  float nc, nay;                 // -c, -ay
-  float nax[4], nd1[4], nd2[4];  // -ax, -d1, -d2 per column of this lane: 0 for columns >= n
+  float2 nc2, nay2;        // (-c, -c), (-ay, -ay)
+  float2 ax2, d12, d22;    // (ax, ax), (d1, d1), (d2, d2)
+  float2 negm[2];          // -1 per column of this lane inside the domain, 0 for columns >= n
   float ml, mr;   // 0 where this lane's left / right neighbour lies beyond the warp, else 1
 };
 
-// b - A y of the 9-point Q1 stencil with per-column x-neighbour and corner
-// coefficients (passed negated): b enters the first of five multiply-adds.
-__device__ __forceinline__ void resid_q1_cols(const RowT<float, 4>& U, const RowT<float, 4>& C,
-                                              const RowT<float, 4>& D, const float* b, float nc, float nay,
-                                              const float* nax, const float* nd1, const float* nd2, float* out) {
+// b - A y of the 9-point Q1 stencil at this lane's four columns (two pairs) from the
+// window rows U, C, D:  A y = c C + ay (U + D) + S,  S_e = W_{e-1} + E_{e+1}, with
+//   W_j = ax C_j + d1 U_j + d2 D_j   (column j's coupling to column j + 1),
+//   E_j = ax C_j + d2 U_j + d1 D_j   (column j's coupling to column j - 1).
+// W and E are formed on aligned pairs; only S needs per-column adds. The warp's edge
+// lanes take 0 from beyond the warp (outside the domain, hence 0, or in the tile
+// overlap, whose values are discarded); the masks are multiplies.
+template <typename ST>
+__device__ __forceinline__ void resid_pairs(const float2* U, const float2* C, const float2* D, const float2* b,
+                                            const FusedCtx<ST>& c, float2* out) {
+  float2 W[2], E[2];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const float cw = (e == 0) ? C.yl : C.y[e - 1];
-    const float ce = (e == 3) ? C.yr : C.y[e + 1];
-    const float uw = (e == 0) ? U.yl : U.y[e - 1];
-    const float ue = (e == 3) ? U.yr : U.y[e + 1];
-    const float dw = (e == 0) ? D.yl : D.y[e - 1];
-    const float de = (e == 3) ? D.yr : D.y[e + 1];
-    float t = fmaf(nc, C.y[e], b[e]);
-    t = fmaf(nax[e], cw + ce, t);
-    t = fmaf(nay, U.y[e] + D.y[e], t);
-    t = fmaf(nd1[e], de + uw, t);
-    out[e] = fmaf(nd2[e], ue + dw, t);
+  for (int p = 0; p < 2; ++p) {
+    const float2 axc = __fmul2_rn(c.ax2, C[p]);
+    W[p] = __ffma2_rn(c.d22, D[p], __ffma2_rn(c.d12, U[p], axc));
+    E[p] = __ffma2_rn(c.d12, D[p], __ffma2_rn(c.d22, U[p], axc));
   }
-}
-
-// Neighbours of a row from adjacent lanes; the warp's edge lanes get 0 (their
-// neighbour is either outside the domain, hence 0, or in the tile overlap, whose
-// values are discarded). The masks are multiplies, which keeps the selects off the
-// integer pipe.
-__device__ __forceinline__ void row_neighbours_m(RowT<float, 4>& r, float ml, float mr) {
-  r.yl = ml * __shfl_up_sync(0xffffffffu, r.y[3], 1);
-  r.yr = mr * __shfl_down_sync(0xffffffffu, r.y[0], 1);
+  const float wm1 = c.ml * __shfl_up_sync(0xffffffffu, W[1].y, 1);  // W of column -1
+  const float e4 = c.mr * __shfl_down_sync(0xffffffffu, E[0].x, 1);  // E of column 4
+  const float2 S[2] = {make_float2(wm1 + E[0].y, W[0].x + E[1].x), make_float2(W[0].y + E[1].y, W[1].x + e4)};
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    float2 t = __ffma2_rn(c.nc2, C[p], b[p]);
+    t = __ffma2_rn(c.nay2, __fadd2_rn(U[p], D[p]), t);
+    out[p] = __ffma2_rn(c.negm[p], S[p], t);
+  }
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
@@ -201,98 +218,87 @@ __device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
 // the previous step's are read from prevx[1 - PW]; the three unrolled phases write
 // slots 0, 1, 0, and the loop copies slot 0 to slot 1 once per three steps.
 template <typename ST, int TL, bool MOM, bool NAGF, bool ABS, int PH, int PW>
-__device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, FusedState<TL>& st, const float* wl,
-                                           const float* al, const float* atl) {
+__device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, PairState<TL>& st, const float2* wl,
+                                           const float2* al, const float2* atl) {
   using R = FusedRings<ST, TL>;
-  constexpr int VW = 4;
   constexpr int SD = PH, SU = (PH + 1) % 3, SC = (PH + 2) % 3;
   issue_row<ST, TL, MOM>(c, rr + kPrefetch);
   cp_async_wait<kPrefetch>();  // the copies of row rr have landed
-  float x0[VW], xm[VW];
+  float2 x0[2], xm[2];
   {
     const int xs = ring_slot(rr, R::NS);
-    st4_to_float(reinterpret_cast<const ST*>(c.ring + xs * R::XROW) + c.lane * 4, x0);
+    float v[4];
+    st4_to_float(reinterpret_cast<const ST*>(c.ring + xs * R::XROW) + c.lane * 4, v);
+    x0[0] = make_float2(v[0], v[1]);
+    x0[1] = make_float2(v[2], v[3]);
     if (MOM) {
-      st4_to_float(reinterpret_cast<const ST*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, xm);
+      st4_to_float(reinterpret_cast<const ST*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, v);
+      xm[0] = make_float2(v[0], v[1]);
+      xm[1] = make_float2(v[2], v[3]);
     } else {
-      xm[0] = xm[1] = xm[2] = xm[3] = 0.f;
+      xm[0] = xm[1] = pair(0.f);
     }
     if constexpr (ABS) {
       // the stored pair (e, e_prev) stands for (0, e_prev - e): e has been added to the
       // FP64 solution, the difference keeps the velocity
 #pragma unroll
-      for (int e = 0; e < VW; ++e) {
-        xm[e] = MOM ? xm[e] - x0[e] : 0.f;
-        x0[e] = 0.f;
+      for (int p = 0; p < 2; ++p) {
+        xm[p] = MOM ? sub2(xm[p], x0[p]) : pair(0.f);
+        x0[p] = pair(0.f);
       }
     }
   }
-  float newx[TL + 1][VW];
-#pragma unroll
-  for (int e = 0; e < VW; ++e) newx[0][e] = x0[e];
+  float2 newx[TL + 1][2];
+  newx[0][0] = x0[0];
+  newx[0][1] = x0[1];
   // b row rr - s sits at slot (rr mod NB) + NB - s: one of its two copies, never wrapped
   const unsigned char* bstep = c.ring + R::BOFF + (ring_slot(rr, R::NB) + R::NB) * 512 + c.lane * 16;
 #pragma unroll
   for (int s = 1; s <= TL; ++s) {
     const int row = rr - s;
     const float4 B4 = *reinterpret_cast<const float4*>(bstep - s * 512);
-    const float Bv[VW] = {B4.x, B4.y, B4.z, B4.w};
+    const float2 Bv[2] = {make_float2(B4.x, B4.y), make_float2(B4.z, B4.w)};
     // rows outside 1..n keep their (zero) values: weight 0
-    const float ws = ((unsigned)(row - c.rlo) < (unsigned)c.n) ? wl[s] : 0.f;
+    const float2 ws = ((unsigned)(row - c.rlo) < (unsigned)c.n) ? wl[s] : pair(0.f);
     // extend level s's window with row rr - s + 1 of y_{s-1}
-    float* Yn = st.Y[s][SD];
-    float vn[VW];
+    float2* Yn = st.Y[s][SD];
+    float2 vn[2];
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      const float xs1 = newx[s - 1][e];
-      const float xs2 = (s == 1) ? xm[e] : st.prevx[1 - PW][s - 2][e];
-      vn[e] = MOM ? xs1 - xs2 : 0.f;
-      Yn[e] = MOM ? fmaf(atl[s], vn[e], xs1) : xs1;
+    for (int p = 0; p < 2; ++p) {
+      const float2 xs1 = newx[s - 1][p];
+      const float2 xs2 = (s == 1) ? xm[p] : st.prevx[1 - PW][s - 2][p];
+      vn[p] = MOM ? sub2(xs1, xs2) : pair(0.f);
+      Yn[p] = MOM ? __ffma2_rn(atl[s], vn[p], xs1) : xs1;
     }
-    // neighbours across lanes by shuffles (zero beyond the warp's 128 columns)
-    RowT<float, VW> YU, YC, YD;
+    float2 ry[2];
+    resid_pairs<ST>(st.Y[s][SU], st.Y[s][SC], Yn, Bv, c, ry);
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      YU.y[e] = st.Y[s][SU][e];
-      YC.y[e] = st.Y[s][SC][e];
-      YD.y[e] = Yn[e];
-    }
-    if constexpr (store_neighbours<TL>()) {
-      row_neighbours_m(YD, c.ml, c.mr);
-      st.YL[s][SD] = YD.yl;
-      st.YR[s][SD] = YD.yr;
-      YU.yl = st.YL[s][SU];
-      YU.yr = st.YR[s][SU];
-      YC.yl = st.YL[s][SC];
-      YC.yr = st.YR[s][SC];
-    } else {
-      row_neighbours_m(YU, c.ml, c.mr);
-      row_neighbours_m(YC, c.ml, c.mr);
-      row_neighbours_m(YD, c.ml, c.mr);
-    }
-    float ry[VW];
-    resid_q1_cols(YU, YC, YD, Bv, c.nc, c.nay, c.nax, c.nd1, c.nd2, ry);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) {
+    for (int p = 0; p < 2; ++p) {
       if (!MOM || NAGF) {
-        newx[s][e] = fmaf(ws, ry[e], YC.y[e]);  // NAG: y = x + a v is the window centre
+        newx[s][p] = __ffma2_rn(ws, ry[p], st.Y[s][SC][p]);  // NAG: y = x + a v is the window centre
       } else {
-        newx[s][e] = fmaf(ws, ry[e], fmaf(al[s], st.vc[s][e], st.xc[s][e]));
-        st.xc[s][e] = newx[s - 1][e];
-        st.vc[s][e] = vn[e];
+        newx[s][p] = __ffma2_rn(ws, ry[p], __ffma2_rn(al[s], st.vc[s][p], st.xc[s][p]));
+        st.xc[s][p] = newx[s - 1][p];
+        st.vc[s][p] = vn[p];
       }
     }
   }
   if (c.store_cols) {
     const int ra = rr - TL, rb = rr - TL + 1;
-    if (ra >= c.r0 && ra <= c.shi) float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, newx[TL]);
-    if (MOM && rb >= c.r0 && rb <= c.shi) float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, newx[TL - 1]);
+    if (ra >= c.r0 && ra <= c.shi) {
+      const float v[4] = {newx[TL][0].x, newx[TL][0].y, newx[TL][1].x, newx[TL][1].y};
+      float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, v);
+    }
+    if (MOM && rb >= c.r0 && rb <= c.shi) {
+      const float v[4] = {newx[TL - 1][0].x, newx[TL - 1][0].y, newx[TL - 1][1].x, newx[TL - 1][1].y};
+      float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, v);
+    }
   }
   if (MOM) {
 #pragma unroll
     for (int s = 0; s + 2 <= TL; ++s)
 #pragma unroll
-      for (int e = 0; e < VW; ++e) st.prevx[PW][s][e] = newx[s][e];
+      for (int p = 0; p < 2; ++p) st.prevx[PW][s][p] = newx[s][p];
   }
 }
 
@@ -309,20 +315,24 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   const Inst& I = A.insts[t.inst];
   const float dv = PRE ? (float)I.dinv : 1.f;
 
-  float wl[TL + 1], al[TL + 1], atl[TL + 1];
+  float2 wl[TL + 1], al[TL + 1], atl[TL + 1];
 #pragma unroll
   for (int s = 1; s <= TL; ++s) {
     const int ci = t.inst * A.m + (A.kidx0 + s - 1) % A.m;
-    wl[s] = A.w[ci] * dv;
-    al[s] = MOM ? A.a[ci] : 0.f;
-    atl[s] = MOM ? (A.at ? A.at[ci] : al[s]) : 0.f;
+    const float as = MOM ? A.a[ci] : 0.f;
+    wl[s] = pair(A.w[ci] * dv);
+    al[s] = pair(as);
+    atl[s] = pair(MOM ? (A.at ? A.at[ci] : as) : 0.f);
   }
   FusedCtx<ST> c;
   c.n = I.n;
   c.pitch = I.pitch;
   c.lane = lane;
-  c.nc = -(float)I.c;
-  c.nay = -(float)I.ay;
+  c.nc2 = pair(-(float)I.c);
+  c.nay2 = pair(-(float)I.ay);
+  c.ax2 = pair((float)I.ax);
+  c.d12 = pair((float)I.d1);
+  c.d22 = pair((float)I.d2);
   // a tail pair: 16 lanes per 64-column tile, lanes 16-31 on row band pad - 2
   const bool tail = t.pad > 0;
   const int tlane = tail ? (lane & 15) : lane;
@@ -335,12 +345,8 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   c.ml = (tlane == 0) ? 0.f : 1.f;
   c.mr = (tlane == (tail ? 15 : 31)) ? 0.f : 1.f;
 #pragma unroll
-  for (int e = 0; e < VW; ++e) {
-    const bool in = c.c0 + e < c.n;
-    c.nax[e] = in ? -(float)I.ax : 0.f;
-    c.nd1[e] = in ? -(float)I.d1 : 0.f;
-    c.nd2[e] = in ? -(float)I.d2 : 0.f;
-  }
+  for (int p = 0; p < 2; ++p)
+    c.negm[p] = make_float2(c.c0 + 2 * p < c.n ? -1.f : 0.f, c.c0 + 2 * p + 1 < c.n ? -1.f : 0.f);
   const bool last_tile = tail || (cs + 128 >= c.n);
   const int clo = cs + (t.tx > 0 ? TL : 0);
   const int chi = last_tile ? c.pitch : cs + 128 - TL;
@@ -363,17 +369,15 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   c.oxp = MOM ? reinterpret_cast<ST*>(A.out_xp) + I.off + sh : nullptr;
   c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<ST, TL>::BYTES;
 
-  FusedState<TL> st;
+  PairState<TL> st;
 #pragma unroll
   for (int s = 0; s <= TL; ++s) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 3; ++q)
 #pragma unroll
-      for (int e = 0; e < VW; ++e) st.Y[s][q][e] = 0.f;
-      st.YL[s][q] = st.YR[s][q] = 0.f;
-    }
+      for (int p = 0; p < 2; ++p) st.Y[s][q][p] = pair(0.f);
 #pragma unroll
-    for (int e = 0; e < VW; ++e) st.xc[s][e] = st.vc[s][e] = st.prevx[0][s][e] = st.prevx[1][s][e] = 0.f;
+    for (int p = 0; p < 2; ++p) st.xc[s][p] = st.vc[s][p] = st.prevx[0][s][p] = st.prevx[1][s][p] = pair(0.f);
   }
   // b rows above the tile's first input row are never loaded: zero their slots
   for (int q = 0; q < 2 * FusedRings<ST, TL>::NB; ++q)
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
 #pragma unroll
       for (int s = 0; s + 2 <= TL; ++s)
 #pragma unroll
-        for (int e = 0; e < VW; ++e) st.prevx[1][s][e] = st.prevx[0][s][e];
+        for (int p = 0; p < 2; ++p) st.prevx[1][s][p] = st.prevx[0][s][p];
     }
   }
   cp_async_wait<0>();
