@@ -416,8 +416,9 @@ static richm_status cycle_t(richm_solver* S, long long k0, long long cycle) {
 
 // Fused tile height (the tuned height halved down to 16 rows) for the instances
 // still iterating, from a wave model of the
-// fused pass: its warps form blocks of 4, which run in waves of 152 SMs x K
-// resident blocks (K = 2 at 8 sweeps per pass, 4 at 4, set by the registers); a
+// fused pass: its tiles form blocks (4 one-warp tiles at 4 sweeps per pass, 2 two-warp
+// tiles at 8), which run in waves of 152 SMs x K resident blocks (K = 4, set by the
+// registers); a
 // wave takes rows + 2 TL row steps, and a row step takes 1 + 0.65 (k - 1) times its
 // single-block time when k blocks share an SM (fitted to GB300 timings of both pass
 // lengths over 1..77 instances of 511^2 and the 256-instance mix, where it picks
@@ -427,7 +428,8 @@ static richm_status cycle_t(richm_solver* S, long long k0, long long cycle) {
 static double fused_pass_cost(const richm_solver* S, int rows) {
   const richm_operator* op = S->op;
   const int TL = S->o.fuse;
-  const int K = TL == 8 ? 2 : 4;
+  const int K = 4;
+  const int per_block = TL == 8 ? 2 : 4;
   long long warps = 0;
   int nmax = 0;
   for (int b = 0; b < op->batch; ++b) {
@@ -436,7 +438,7 @@ static double fused_pass_cost(const richm_solver* S, int rows) {
     warps += fused_warps(n, TL, (n + rows - 1) / rows);
     nmax = std::max(nmax, n);
   }
-  const long long blocks = (warps + 3) / 4;
+  const long long blocks = (warps + per_block - 1) / per_block;
   const long long wave = 152LL * K;
   const long long full = blocks / wave, rem = blocks % wave;
   const double per_wave = 1.0 + 0.65 * (K - 1);

@@ -212,49 +212,55 @@ __device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
   cp_async_commit();
 }
 
-// One row step of the pipeline at input row rr and window phase PH.
-// NAGF: at == a, so x_{k+1} = y + w (b - A y) needs only the window.
-// The level outputs that the next step needs (x_{k+s} of row rr - s) go to prevx[PW],
-// the previous step's are read from prevx[1 - PW]; the three unrolled phases write
-// slots 0, 1, 0, and the loop copies slot 0 to slot 1 once per three steps.
-template <typename ST, int TL, bool MOM, bool NAGF, bool ABS, int PH, int PW>
-__device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, PairState<TL>& st, const float2* wl,
-                                           const float2* al, const float2* atl) {
+// The first level's inputs of row step rr: issue the copies of row rr + kPrefetch, wait
+// for those of row rr, and read x_k and x_{k-1} of row rr from the rings.
+template <typename ST, int TL, bool MOM, bool ABS>
+__device__ __forceinline__ void step_inputs(int rr, const FusedCtx<ST>& c, float2* x0, float2* xm) {
   using R = FusedRings<ST, TL>;
-  constexpr int SD = PH, SU = (PH + 1) % 3, SC = (PH + 2) % 3;
   issue_row<ST, TL, MOM>(c, rr + kPrefetch);
   cp_async_wait<kPrefetch>();  // the copies of row rr have landed
-  float2 x0[2], xm[2];
-  {
-    const int xs = ring_slot(rr, R::NS);
-    float v[4];
-    st4_to_float(reinterpret_cast<const ST*>(c.ring + xs * R::XROW) + c.lane * 4, v);
-    x0[0] = make_float2(v[0], v[1]);
-    x0[1] = make_float2(v[2], v[3]);
-    if (MOM) {
-      st4_to_float(reinterpret_cast<const ST*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, v);
-      xm[0] = make_float2(v[0], v[1]);
-      xm[1] = make_float2(v[2], v[3]);
-    } else {
-      xm[0] = xm[1] = pair(0.f);
-    }
-    if constexpr (ABS) {
-      // the stored pair (e, e_prev) stands for (0, e_prev - e): e has been added to the
-      // FP64 solution, the difference keeps the velocity
+  const int xs = ring_slot(rr, R::NS);
+  float v[4];
+  st4_to_float(reinterpret_cast<const ST*>(c.ring + xs * R::XROW) + c.lane * 4, v);
+  x0[0] = make_float2(v[0], v[1]);
+  x0[1] = make_float2(v[2], v[3]);
+  if (MOM) {
+    st4_to_float(reinterpret_cast<const ST*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, v);
+    xm[0] = make_float2(v[0], v[1]);
+    xm[1] = make_float2(v[2], v[3]);
+  } else {
+    xm[0] = xm[1] = pair(0.f);
+  }
+  if constexpr (ABS) {
+    // the stored pair (e, e_prev) stands for (0, e_prev - e): e has been added to the
+    // FP64 solution, the difference keeps the velocity
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        xm[p] = MOM ? sub2(xm[p], x0[p]) : pair(0.f);
-        x0[p] = pair(0.f);
-      }
+    for (int p = 0; p < 2; ++p) {
+      xm[p] = MOM ? sub2(xm[p], x0[p]) : pair(0.f);
+      x0[p] = pair(0.f);
     }
   }
-  float2 newx[TL + 1][2];
-  newx[0][0] = x0[0];
-  newx[0][1] = x0[1];
+}
+
+// Levels S0..S1 of row step rr at window phase PH: level s computes row rr - s of
+// x_{k+s}. in1: the row entering level S0 (level S0 - 1's output of this step, row
+// rr - S0 + 1); in2: the level S0 - 2 row of the previous step (row rr - S0 + 1 of
+// x_{k+S0-2}), the look-ahead's other input. NAGF: at == a, so x_{k+1} = y + w (b - A y)
+// needs only the window. The outputs that the next step needs (levels S0 - 1 .. DL)
+// go to prevx[PW], the previous step's are read from prevx[1 - PW]; the three unrolled
+// phases write slots 0, 1, 0, and the loop copies slot 0 to slot 1 once per three steps.
+template <typename ST, int TL, int S0, int S1, int DL, bool MOM, bool NAGF, int PH, int PW>
+__device__ __forceinline__ void step_levels(int rr, const FusedCtx<ST>& c, PairState<TL>& st, const float2* in1,
+                                            const float2* in2, const float2* wl, const float2* al,
+                                            const float2* atl, float2 (*newx)[2]) {
+  using R = FusedRings<ST, TL>;
+  constexpr int SD = PH, SU = (PH + 1) % 3, SC = (PH + 2) % 3;
+  newx[S0 - 1][0] = in1[0];
+  newx[S0 - 1][1] = in1[1];
   // b row rr - s sits at slot (rr mod NB) + NB - s: one of its two copies, never wrapped
   const unsigned char* bstep = c.ring + R::BOFF + (ring_slot(rr, R::NB) + R::NB) * 512 + c.lane * 16;
 #pragma unroll
-  for (int s = 1; s <= TL; ++s) {
+  for (int s = S0; s <= S1; ++s) {
     const int row = rr - s;
     const float4 B4 = *reinterpret_cast<const float4*>(bstep - s * 512);
     const float2 Bv[2] = {make_float2(B4.x, B4.y), make_float2(B4.z, B4.w)};
@@ -266,7 +272,7 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, PairSt
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const float2 xs1 = newx[s - 1][p];
-      const float2 xs2 = (s == 1) ? xm[p] : st.prevx[1 - PW][s - 2][p];
+      const float2 xs2 = (s == S0) ? in2[p] : st.prevx[1 - PW][s - 2][p];
       vn[p] = MOM ? sub2(xs1, xs2) : pair(0.f);
       Yn[p] = MOM ? __ffma2_rn(atl[s], vn[p], xs1) : xs1;
     }
@@ -283,39 +289,50 @@ __device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, PairSt
       }
     }
   }
-  if (c.store_cols) {
-    const int ra = rr - TL, rb = rr - TL + 1;
-    if (ra >= c.r0 && ra <= c.shi) {
-      const float v[4] = {newx[TL][0].x, newx[TL][0].y, newx[TL][1].x, newx[TL][1].y};
-      float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, v);
-    }
-    if (MOM && rb >= c.r0 && rb <= c.shi) {
-      const float v[4] = {newx[TL - 1][0].x, newx[TL - 1][0].y, newx[TL - 1][1].x, newx[TL - 1][1].y};
-      float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, v);
-    }
-  }
   if (MOM) {
 #pragma unroll
-    for (int s = 0; s + 2 <= TL; ++s)
+    for (int s = S0 - 1; s <= DL; ++s)
 #pragma unroll
       for (int p = 0; p < 2; ++p) st.prevx[PW][s][p] = newx[s][p];
   }
 }
 
-template <typename ST, int TL, bool MOM, bool PRE, bool NAGF, bool ABS>
-__global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kernel(const SweepTArgs A) {
+// Store rows rr - TL of x_{k+TL} and rr - TL + 1 of x_{k+TL-1} (this lane's columns).
+template <typename ST, int TL, bool MOM>
+__device__ __forceinline__ void step_store(int rr, const FusedCtx<ST>& c, const float2* last, const float2* prev) {
+  if (c.store_cols) {
+    const int ra = rr - TL, rb = rr - TL + 1;
+    if (ra >= c.r0 && ra <= c.shi) {
+      const float v[4] = {last[0].x, last[0].y, last[1].x, last[1].y};
+      float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, v);
+    }
+    if (MOM && rb >= c.r0 && rb <= c.shi) {
+      const float v[4] = {prev[0].x, prev[0].y, prev[1].x, prev[1].y};
+      float_to_st4(c.oxp + (long long)rb * c.pitch + c.c0, v);
+    }
+  }
+}
+
+// One row step of the whole pipeline (levels 1..TL) in one warp.
+template <typename ST, int TL, bool MOM, bool NAGF, bool ABS, int PH, int PW>
+__device__ __forceinline__ void fused_step(int rr, const FusedCtx<ST>& c, PairState<TL>& st, const float2* wl,
+                                           const float2* al, const float2* atl) {
+  float2 x0[2], xm[2];
+  step_inputs<ST, TL, MOM, ABS>(rr, c, x0, xm);
+  float2 newx[TL + 1][2];
+  step_levels<ST, TL, 1, TL, TL - 2, MOM, NAGF, PH, PW>(rr, c, st, x0, xm, wl, al, atl, newx);
+  step_store<ST, TL, MOM>(rr, c, newx[TL], newx[TL - 1]);
+}
+
+// Per-warp setup of a fused tile: coefficients of the TL levels, row and column frames,
+// pointers (the ring pointer is the caller's). Returns the last input row step.
+template <typename ST, int TL, bool MOM, bool PRE>
+__device__ __forceinline__ int fused_setup(const SweepTArgs& A, const Tile& t, int lane, FusedCtx<ST>& c,
+                                           float2* wl, float2* al, float2* atl) {
   constexpr int VW = 4;
   constexpr int STRIDE = 128 - 2 * TL;
-  extern __shared__ __align__(16) unsigned char fused_smem[];
-  const int lane = threadIdx.x & 31;
-  const int wt = blockIdx.x * kFuseWarps + (threadIdx.x >> 5);
-  if (wt >= A.ntiles) return;
-  const Tile t = A.tiles[wt];
-  if (A.active && A.active[t.inst] == 0) return;
   const Inst& I = A.insts[t.inst];
   const float dv = PRE ? (float)I.dinv : 1.f;
-
-  float2 wl[TL + 1], al[TL + 1], atl[TL + 1];
 #pragma unroll
   for (int s = 1; s <= TL; ++s) {
     const int ci = t.inst * A.m + (A.kidx0 + s - 1) % A.m;
@@ -324,7 +341,6 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
     al[s] = pair(as);
     atl[s] = pair(MOM ? (A.at ? A.at[ci] : as) : 0.f);
   }
-  FusedCtx<ST> c;
   c.n = I.n;
   c.pitch = I.pitch;
   c.lane = lane;
@@ -356,20 +372,21 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
   c.rlo = 1 - dr;
   c.vhi = min(r1 + TL, c.n) - dr;
   c.shi = r1 - dr;
-  // the loop covers the longer of the two bands of a tail pair
-  const int endA = min(c.r0 + A.rows - 1, c.n) + TL;
-  const int endB = (tail && t.pad > 1) ? min((t.pad - 2) * A.rows + A.rows, c.n) + TL - (t.pad - 2 - t.ty) * A.rows
-                                       : endA;
-  const int rend = max(endA, endB);
   const long long sh = (long long)dr * c.pitch;
   c.xb = reinterpret_cast<const ST*>(A.x) + I.off + sh;
   c.xpb = reinterpret_cast<const ST*>(MOM ? A.xp : A.x) + I.off + sh;
   c.bb = A.b + I.off + sh;
   c.ox = reinterpret_cast<ST*>(A.out_x) + I.off + sh;
   c.oxp = MOM ? reinterpret_cast<ST*>(A.out_xp) + I.off + sh : nullptr;
-  c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<ST, TL>::BYTES;
+  // the loop covers the longer of the two bands of a tail pair
+  const int endA = min(c.r0 + A.rows - 1, c.n) + TL;
+  const int endB = (tail && t.pad > 1) ? min((t.pad - 2) * A.rows + A.rows, c.n) + TL - (t.pad - 2 - t.ty) * A.rows
+                                       : endA;
+  return max(endA, endB);
+}
 
-  PairState<TL> st;
+template <int TL>
+__device__ __forceinline__ void zero_state(PairState<TL>& st) {
 #pragma unroll
   for (int s = 0; s <= TL; ++s) {
 #pragma unroll
@@ -379,10 +396,31 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
 #pragma unroll
     for (int p = 0; p < 2; ++p) st.xc[s][p] = st.vc[s][p] = st.prevx[0][s][p] = st.prevx[1][s][p] = pair(0.f);
   }
-  // b rows above the tile's first input row are never loaded: zero their slots
+}
+
+// b rows above the tile's first input row are never loaded: zero their slots
+template <typename ST, int TL>
+__device__ __forceinline__ void zero_b_ring(const FusedCtx<ST>& c) {
   for (int q = 0; q < 2 * FusedRings<ST, TL>::NB; ++q)
-    *reinterpret_cast<float4*>(c.ring + FusedRings<ST, TL>::BOFF + q * 512 + lane * 16) =
+    *reinterpret_cast<float4*>(c.ring + FusedRings<ST, TL>::BOFF + q * 512 + c.lane * 16) =
         make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <typename ST, int TL, bool MOM, bool PRE, bool NAGF, bool ABS>
+__global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kernel(const SweepTArgs A) {
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kFuseWarps + (threadIdx.x >> 5);
+  if (wt >= A.ntiles) return;
+  const Tile t = A.tiles[wt];
+  if (A.active && A.active[t.inst] == 0) return;
+  float2 wl[TL + 1], al[TL + 1], atl[TL + 1];
+  FusedCtx<ST> c;
+  const int rend = fused_setup<ST, TL, MOM, PRE>(A, t, lane, c, wl, al, atl);
+  c.ring = fused_smem + (threadIdx.x >> 5) * FusedRings<ST, TL>::BYTES;
+  PairState<TL> st;
+  zero_state<TL>(st);
+  zero_b_ring<ST, TL>(c);
   const int rstart = c.r0 - TL;
 #pragma unroll
   for (int d = 0; d < kPrefetch; ++d) issue_row<ST, TL, MOM>(c, rstart + d);
@@ -400,6 +438,118 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
     }
   }
   cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- 8 levels on two warps
+// The 8-level pipeline of a tile split over two warps of one block: the lower warp runs
+// levels 1-4 (and all loads), the upper warp levels 5-8 (and the stores) one row step
+// behind. Each step the lower warp hands over the row of x_{k+4} it produced and the
+// x_{k+3} row of its previous step (the upper warp's first look-ahead) through a
+// three-slot exchange in shared memory; the upper warp reads the b rows from the lower
+// warp's ring. A named barrier of the two warps per row step orders the exchange and
+// the ring reuse (a slot is rewritten three steps after it was read). Each warp holds
+// the state of four levels, so four blocks (16 warps) fit an SM instead of eight warps
+// of the one-warp kernel, while HBM traffic stays that of eight sweeps per pass. Both
+// warps of a tile leave together or not at all, and run the same number of barriers.
+constexpr int kSplitTiles = 2;  // tiles per block, two warps each
+constexpr int kXchBytes = 3 * 2 * 512;  // three slots of two 128-column FP32 rows
+
+template <typename ST>
+__host__ __device__ constexpr int split_tile_bytes() { return FusedRings<ST, 8>::BYTES + kXchBytes; }
+
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+template <typename ST, bool MOM, bool NAGF, bool ABS, int PH, int PW>
+__device__ __forceinline__ void lower_step(int rr, const FusedCtx<ST>& c, PairState<8>& st, unsigned char* xslot,
+                                           const float2* wl, const float2* al, const float2* atl) {
+  float2 x0[2], xm[2];
+  step_inputs<ST, 8, MOM, ABS>(rr, c, x0, xm);
+  float2 newx[9][2];
+  // hand over x_{k+3} of the previous step before this step overwrites it
+  const float2 p3[2] = {st.prevx[1 - PW][3][0], st.prevx[1 - PW][3][1]};
+  step_levels<ST, 8, 1, 4, 3, MOM, NAGF, PH, PW>(rr, c, st, x0, xm, wl, al, atl, newx);
+  *reinterpret_cast<float4*>(xslot + c.lane * 16) = make_float4(newx[4][0].x, newx[4][0].y, newx[4][1].x,
+                                                                 newx[4][1].y);
+  *reinterpret_cast<float4*>(xslot + 512 + c.lane * 16) = make_float4(p3[0].x, p3[0].y, p3[1].x, p3[1].y);
+}
+
+template <typename ST, bool MOM, bool NAGF, int PH, int PW>
+__device__ __forceinline__ void upper_step(int rr, const FusedCtx<ST>& c, PairState<8>& st,
+                                           const unsigned char* xslot, const float2* wl, const float2* al,
+                                           const float2* atl) {
+  const float4 a4 = *reinterpret_cast<const float4*>(xslot + c.lane * 16);
+  const float4 b4 = *reinterpret_cast<const float4*>(xslot + 512 + c.lane * 16);
+  const float2 in1[2] = {make_float2(a4.x, a4.y), make_float2(a4.z, a4.w)};
+  const float2 in2[2] = {make_float2(b4.x, b4.y), make_float2(b4.z, b4.w)};
+  float2 newx[9][2];
+  step_levels<ST, 8, 5, 8, 6, MOM, NAGF, PH, PW>(rr, c, st, in1, in2, wl, al, atl, newx);
+  step_store<ST, 8, MOM>(rr, c, newx[8], newx[7]);
+}
+
+template <typename ST, bool MOM, bool PRE, bool NAGF, bool ABS>
+__global__ void __launch_bounds__(kSplitTiles * 64, 4) sweepT8s_kernel(const SweepTArgs A) {
+  constexpr int TL = 8;
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int pid = warp >> 1;           // this block's tile
+  const bool upper = (warp & 1) != 0;  // levels 5-8, else 1-4
+  const int wt = blockIdx.x * kSplitTiles + pid;
+  if (wt >= A.ntiles) return;  // both warps of the tile
+  const Tile t = A.tiles[wt];
+  if (A.active && A.active[t.inst] == 0) return;  // both warps of the tile
+  float2 wl[TL + 1], al[TL + 1], atl[TL + 1];
+  FusedCtx<ST> c;
+  const int rend = fused_setup<ST, TL, MOM, PRE>(A, t, lane, c, wl, al, atl);
+  c.ring = fused_smem + pid * split_tile_bytes<ST>();
+  unsigned char* xch = c.ring + FusedRings<ST, TL>::BYTES;
+  const int bar = 1 + pid;
+  const int rstart = c.r0 - TL;
+  if (!upper) {
+    zero_b_ring<ST, TL>(c);
+    for (int q = 0; q < 6; ++q)
+      *reinterpret_cast<float4*>(xch + q * 512 + lane * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  pair_sync(bar);
+  if (!upper) {
+    PairState<TL> st;
+    zero_state<TL>(st);
+#pragma unroll
+    for (int d = 0; d < kPrefetch; ++d) issue_row<ST, TL, MOM>(c, rstart + d);
+    for (int rr = rstart; rr <= rend + 1; rr += 3) {
+      lower_step<ST, MOM, NAGF, ABS, 0, 0>(rr, c, st, xch, wl, al, atl);
+      pair_sync(bar);
+      lower_step<ST, MOM, NAGF, ABS, 1, 1>(rr + 1, c, st, xch + 1024, wl, al, atl);
+      pair_sync(bar);
+      lower_step<ST, MOM, NAGF, ABS, 2, 0>(rr + 2, c, st, xch + 2048, wl, al, atl);
+      pair_sync(bar);
+      if (MOM) {
+#pragma unroll
+        for (int s = 0; s <= 3; ++s)
+#pragma unroll
+          for (int p = 0; p < 2; ++p) st.prevx[1][s][p] = st.prevx[0][s][p];
+      }
+    }
+    cp_async_wait<0>();
+  } else {
+    PairState<TL> st;
+    zero_state<TL>(st);
+    // one row step behind: step rr - 1 + q reads the slot the lower warp wrote at q - 1
+    for (int rr = rstart; rr <= rend + 1; rr += 3) {
+      upper_step<ST, MOM, NAGF, 0, 0>(rr - 1, c, st, xch + 2048, wl, al, atl);
+      pair_sync(bar);
+      upper_step<ST, MOM, NAGF, 1, 1>(rr, c, st, xch, wl, al, atl);
+      pair_sync(bar);
+      upper_step<ST, MOM, NAGF, 2, 0>(rr + 1, c, st, xch + 1024, wl, al, atl);
+      pair_sync(bar);
+      if (MOM) {
+#pragma unroll
+        for (int s = 4; s <= 6; ++s)
+#pragma unroll
+          for (int p = 0; p < 2; ++p) st.prevx[1][s][p] = st.prevx[0][s][p];
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------- complex Helmholtz
@@ -591,6 +741,30 @@ __global__ void __launch_bounds__(kFuseWarps * 32, 3) sweepT_cx_kernel(const Swe
   cp_async_wait<0>();
 }
 
+template <typename ST>
+static cudaError_t split_attributes() {
+  const int bytes = split_tile_bytes<ST>() * kSplitTiles;
+  cudaError_t e = cudaSuccess;
+#define RICHM_SPLIT_ATTR(MOM, PRE, NAGF, ABS)                                                                 \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(sweepT8s_kernel<ST, MOM, PRE, NAGF, ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             bytes);
+  RICHM_SPLIT_ATTR(true, true, true, false)
+  RICHM_SPLIT_ATTR(true, false, true, false)
+  RICHM_SPLIT_ATTR(true, true, false, false)
+  RICHM_SPLIT_ATTR(true, false, false, false)
+  RICHM_SPLIT_ATTR(false, true, false, false)
+  RICHM_SPLIT_ATTR(false, false, false, false)
+  RICHM_SPLIT_ATTR(true, true, true, true)
+  RICHM_SPLIT_ATTR(true, false, true, true)
+  RICHM_SPLIT_ATTR(true, true, false, true)
+  RICHM_SPLIT_ATTR(true, false, false, true)
+  RICHM_SPLIT_ATTR(false, true, false, true)
+  RICHM_SPLIT_ATTR(false, false, false, true)
+#undef RICHM_SPLIT_ATTR
+  return e;
+}
+
 template <typename ST, int TL>
 static cudaError_t fused_attributes_tl() {
   const int bytes = FusedRings<ST, TL>::BYTES * kFuseWarps;
@@ -626,9 +800,9 @@ cudaError_t init_fused_attributes() {
     e = cudaFuncSetAttribute(sweepT_cx_kernel<4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              cx_bytes);
   if (e == cudaSuccess) e = fused_attributes_tl<float, 4>();
-  if (e == cudaSuccess) e = fused_attributes_tl<float, 8>();
+  if (e == cudaSuccess) e = split_attributes<float>();
   if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 4>();
-  if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 8>();
+  if (e == cudaSuccess) e = split_attributes<__nv_bfloat16>();
   return e;
 }
 
@@ -640,12 +814,31 @@ static richm_status launch_fused_t(richm_operator* op, int TL, const ST* x, cons
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, -TL, rows, &tm));
   SweepTArgs A{op->d_inst, tm->d_tiles, tm->ntiles, x, xp, b, out_x, out_xp, w, a, at, m, kidx0, active, rows};
-  const int blocks = (tm->ntiles + kFuseWarps - 1) / kFuseWarps;
-  const int thr = kFuseWarps * 32;
-  const size_t smem =
-      (size_t)(TL == 4 ? FusedRings<ST, 4>::BYTES : FusedRings<ST, 8>::BYTES) * kFuseWarps;
   const bool mom = a != nullptr;
   const bool nag = mom && at == nullptr;  // at = a
+  if (TL == 8) {  // two warps per tile, two tiles per block
+    const int blocks = (tm->ntiles + kSplitTiles - 1) / kSplitTiles;
+    const int thr = kSplitTiles * 64;
+    const size_t smem = (size_t)split_tile_bytes<ST>() * kSplitTiles;
+#define RICHM_SPLIT(ABS)                                                                                   \
+  if (nag && precond) sweepT8s_kernel<ST, true, true, true, ABS><<<blocks, thr, smem, s>>>(A);             \
+  else if (nag) sweepT8s_kernel<ST, true, false, true, ABS><<<blocks, thr, smem, s>>>(A);                  \
+  else if (mom && precond) sweepT8s_kernel<ST, true, true, false, ABS><<<blocks, thr, smem, s>>>(A);       \
+  else if (mom) sweepT8s_kernel<ST, true, false, false, ABS><<<blocks, thr, smem, s>>>(A);                 \
+  else if (precond) sweepT8s_kernel<ST, false, true, false, ABS><<<blocks, thr, smem, s>>>(A);             \
+  else sweepT8s_kernel<ST, false, false, false, ABS><<<blocks, thr, smem, s>>>(A);
+    if (absorb) {
+      RICHM_SPLIT(true)
+    } else {
+      RICHM_SPLIT(false)
+    }
+#undef RICHM_SPLIT
+    RICHM_LAUNCH_CHECK("fused sweep");
+    return RICHM_OK;
+  }
+  const int blocks = (tm->ntiles + kFuseWarps - 1) / kFuseWarps;
+  const int thr = kFuseWarps * 32;
+  const size_t smem = (size_t)FusedRings<ST, 4>::BYTES * kFuseWarps;
 #define RICHM_FUSED(TLV, ABS)                                                                              \
   if (nag && precond) sweepT_kernel<ST, TLV, true, true, true, ABS><<<blocks, thr, smem, s>>>(A);         \
   else if (nag) sweepT_kernel<ST, TLV, true, false, true, ABS><<<blocks, thr, smem, s>>>(A);              \
@@ -654,14 +847,10 @@ static richm_status launch_fused_t(richm_operator* op, int TL, const ST* x, cons
   else if (precond) sweepT_kernel<ST, TLV, false, true, false, ABS><<<blocks, thr, smem, s>>>(A);         \
   else sweepT_kernel<ST, TLV, false, false, false, ABS><<<blocks, thr, smem, s>>>(A);
   if (TL != 4 && TL != 8) return set_error(RICHM_ERR_ARG, "fused sweeps support 4 or 8 sweeps per pass");
-  if (TL == 4 && !absorb) {
+  if (!absorb) {
     RICHM_FUSED(4, false)
-  } else if (TL == 4) {
-    RICHM_FUSED(4, true)
-  } else if (!absorb) {
-    RICHM_FUSED(8, false)
   } else {
-    RICHM_FUSED(8, true)
+    RICHM_FUSED(4, true)
   }
 #undef RICHM_FUSED
   RICHM_LAUNCH_CHECK("fused sweep");
