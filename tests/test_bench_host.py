@@ -54,5 +54,6 @@ def test_weak_scaling_value_arithmetic():
     sys.path.insert(0, ROOT)
     import bench
     dofs, steps, ms = 1.0e7, 10, 250.0
+    assert bench.REFINE == 256  # sweeps per step (one refinement cycle)
     v = dofs * 2 * bench.REFINE * steps / (ms / 1e3) / 1e9
-    assert abs(v - 2 * dofs * 64 * 10 / 0.25 / 1e9) < 1e-9
+    assert abs(v - 2 * dofs * 256 * 10 / 0.25 / 1e9) < 1e-9
