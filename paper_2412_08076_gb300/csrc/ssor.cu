@@ -29,7 +29,7 @@
 
 namespace richm {
 
-constexpr int kSsorWarps = 1;  // instances per block (one warp each; the row rings take 78 KB)
+constexpr int kSsorWarps = 1;  // instances per block of the multi-chunk kernels (one warp each)
 
 template <typename E> struct SsorVW;
 template <> struct SsorVW<float> { static constexpr int v = 16; };
@@ -350,32 +350,59 @@ __device__ __forceinline__ void row_wait_all() { asm volatile("cp.async.wait_gro
 
 }  // namespace
 
-// Shared-memory rings of one warp: kRowSlots slots of three row arrays (each lane copies
-// and reads back only its own VW values, so no barrier is needed).
+// A row of 32 lanes x VW values in shared memory, interleaved in 16-byte chunks: chunk q
+// of lane l at (32 q + l) x 16 bytes, so that each 16-byte access of a warp covers 512
+// consecutive bytes (no bank conflicts; a lane's own VW values contiguous would put
+// eight lanes of a quarter warp on four banks).
 template <typename E, int VW>
+__device__ __forceinline__ void ld_il(const unsigned char* row, int lane, E* v) {
+  constexpr int C = 16 / (int)sizeof(E);
+#pragma unroll
+  for (int q = 0; q < VW / C; ++q) {
+    if constexpr (sizeof(E) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(row + (32 * q + lane) * 16);
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    } else {
+      const double2 t = *reinterpret_cast<const double2*>(row + (32 * q + lane) * 16);
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  }
+}
+template <typename E, int VW>
+__device__ __forceinline__ void st_il(unsigned char* row, int lane, const E* v) {
+  constexpr int C = 16 / (int)sizeof(E);
+#pragma unroll
+  for (int q = 0; q < VW / C; ++q) {
+    if constexpr (sizeof(E) == 4)
+      *reinterpret_cast<float4*>(row + (32 * q + lane) * 16) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2],
+                                                                           v[4 * q + 3]);
+    else
+      *reinterpret_cast<double2*>(row + (32 * q + lane) * 16) = make_double2(v[2 * q], v[2 * q + 1]);
+  }
+}
+
+// Shared-memory rings: NSLOT slots of three interleaved row arrays, filled with cp.async
+// by the warp that reads them, or read by another warp after a barrier.
+template <typename E, int VW, int NSLOT = kRowSlots>
 struct RowRing {
   static constexpr int ROW = 32 * VW * (int)sizeof(E);  // bytes of one array row
-  static constexpr int BYTES = 3 * kRowSlots * ROW;
+  static constexpr int BYTES = 3 * NSLOT * ROW;
   unsigned char* base;
   int lane;
-  __device__ E* at(int array, int slot) const {
-    return reinterpret_cast<E*>(base + (array * kRowSlots + slot) * ROW) + lane * VW;
-  }
-  // copy VW values of row `row` (zero-filled unless valid) into (array, slot)
-  __device__ void issue(int array, int slot, const E* src_base, int row, int pitch, int c0, bool valid) const {
-    const E* src = src_base + (long long)(valid ? row : 0) * pitch + c0;
-    unsigned char* dst = reinterpret_cast<unsigned char*>(at(array, slot));
+  __device__ unsigned char* row(int array, int slot) const { return base + (array * NSLOT + slot) * ROW; }
+  __device__ void load(int array, int slot, E* v) const { ld_il<E, VW>(row(array, slot), lane, v); }
+  // copy this lane's VW values of row `r` (zero-filled unless valid) into (array, slot)
+  __device__ void issue(int array, int slot, const E* src_base, int r, int pitch, int c0, bool valid) const {
+    const E* src = src_base + (long long)(valid ? r : 0) * pitch + c0;
+    unsigned char* dst = row(array, slot);
 #pragma unroll
-    for (int q = 0; q < VW * (int)sizeof(E) / 16; ++q) row_cp16(dst + 16 * q, src + q * (16 / (int)sizeof(E)), valid);
+    for (int q = 0; q < VW * (int)sizeof(E) / 16; ++q)
+      row_cp16(dst + (32 * q + lane) * 16, src + q * (16 / (int)sizeof(E)), valid);
   }
-};
-
-// Per-warp state of the forward row pipeline.
-template <typename E, int VW>
-struct FwdRow {
-  RowVW<E, VW> Y[3];  // look-ahead iterate y of rows i-1, i, i+1 (slots rotate by phase)
-  RowVW<E, VW> Z;     // z of the previous row
-  E rp[VW];           // b/c - (A y)/c of the current row (formed one row ahead)
 };
 
 // rp = b/c - (A y)/c at the centre row C, with coefficients already divided by c.
@@ -392,43 +419,41 @@ __device__ __forceinline__ void scaled_rhs(const RowVW<E, VW>& U, const RowVW<E,
   }
 }
 
-// Row i of the forward solve at window phase PH (y(i) in slot PH): takes the inputs of
-// row i + 2 from the ring, solves row i and forms rp of row i + 1.
-template <typename E, int VW, int PH>
-__device__ __forceinline__ void fwd_row(int i, FwdRow<E, VW>& S, const RowRing<E, VW>& ring, const E* k, const E* mk,
-                                        const E* qd, E ky, E k1, E k2, E rc, E axr, E ayr, E d1r, E d2r, E ati,
-                                        bool mom, int lane, bool live, bool hx, int pitch, E* zrow,
-                                        const E* xb, const E* xpb, const E* bb, int n, int c0) {
-  constexpr int SU = (PH + 2) % 3, SC = PH, SD = (PH + 1) % 3;
-  // inputs of step i + 1: x, x_prev of row i + 2 and b of row i + 1
-  row_wait();
-  const int sl = (i + 1) % kRowSlots;
-  E xv[VW], xpv[VW], bv[VW];
-  ld16<E, VW>(ring.at(0, sl), xv);
-  if (mom) ld16<E, VW>(ring.at(1, sl), xpv);
-  ld16<E, VW>(ring.at(2, sl), bv);
-  {
-    const int t = i + 1 + kRowPF;
-    const int sn = t % kRowSlots;
-    const bool vx = hx && live && t + 1 <= n, vb = live && t >= 1 && t <= n;
-    ring.issue(0, sn, xb, t + 1, pitch, c0, vx);
-    if (mom) ring.issue(1, sn, xpb, t + 1, pitch, c0, vx);
-    ring.issue(2, sn, bb, t, pitch, c0, vb);
-    row_commit();
-  }
-  // row i: q = rp - (w/c) (ay z(i-1, j) + d1 z(i-1, j-1) + d2 z(i-1, j+1)), then the row recurrence
+// ---------------------------------------------------------------- two-warp row pipelines
+// The single-warp row kernels spend most of a row on work off the recurrence's critical
+// path (loading and forming the next rows' right-hand sides, the Table 1 update), which
+// one warp issues in order with the recurrence. Here each instance has two warps: the
+// solver warp runs only the row recurrence, the helper warp streams the inputs and does
+// the rest, and they meet once per row at a named barrier (`bar.sync 1, 64`; the block is
+// the instance, both warps run the same number of iterations, and both leave together).
+//   forward:  at iteration t the helper stores rp of row t + 1 (formed at t - 1) in a
+//             two-slot ring and forms rp of row t + 2; the solver solves row t from rp.
+//   backward: at iteration t the solver solves row n - t and leaves s in a two-slot ring;
+//             the helper applies the update to row n - t + 1 with the s of iteration t - 1
+//             and keeps the z rows the solver reads resident (its copies of a row land
+//             before the barrier that precedes the solver's use).
+constexpr int kPipeSlotsB = kRowPF + 2;  // backward ring: a slot is re-targeted one iteration after its last read
+
+__device__ __forceinline__ void pipe_sync() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+template <typename E, int VW>
+struct PipeSizes {
+  static constexpr int RPB = 2 * 32 * VW * (int)sizeof(E);  // two slots of one row
+  static constexpr int FWD = RowRing<E, VW>::BYTES + RPB;
+  static constexpr int BWD = RowRing<E, VW, kPipeSlotsB>::BYTES + RPB;
+};
+
+// Solver warp, forward: row i from rp (this lane's VW values) and the previous row of z.
+template <typename E, int VW>
+__device__ __forceinline__ void fwd_solve_row(const E* rp, RowVW<E, VW>& Z, const E* k, const E* mk, const E* qd,
+                                              E ky, E k1, E k2, int lane, bool live, E* zrow) {
   E q[VW];
   E P = E(0);
 #pragma unroll
-  for (int e = 0; e < VW; ++e)  // z = 0 beyond the domain (mask 0)
-    q[e] = mk[e] * (S.rp[e] - (ky * S.Z.v[e] + k1 * left_of(S.Z, e) + k2 * right_of(S.Z, e)));
-  // y of row i + 2 into the slot of row i - 1, and rp of row i + 1 (independent of row i)
-  y_from<E, VW>(xv, xpv, ati, mom, S.Y[SU]);
-  edges_zero<E, VW>(S.Y[SU], lane);
-  E rpn[VW];
-  scaled_rhs<E, VW>(S.Y[SC], S.Y[SD], S.Y[SU], bv, rc, axr, ayr, d1r, d2r, rpn);
-#pragma unroll
-  for (int e = 0; e < VW; ++e) P = q[e] + k[e] * P;
+  for (int e = 0; e < VW; ++e) {  // z = 0 beyond the domain (mask 0)
+    q[e] = mk[e] * (rp[e] - (ky * Z.v[e] + k1 * left_of(Z, e) + k2 * right_of(Z, e)));
+    P = q[e] + k[e] * P;
+  }
 #pragma unroll
   for (int d = 0; d < 5; ++d) {
     const E Pp = __shfl_up_sync(0xffffffffu, P, 1 << d);
@@ -439,219 +464,297 @@ __device__ __forceinline__ void fwd_row(int i, FwdRow<E, VW>& S, const RowRing<E
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
     zv = q[e] + k[e] * zv;
-    S.Z.v[e] = zv;
+    Z.v[e] = zv;
   }
-  if (live) st16<E, VW>(zrow, S.Z.v);
-  S.Z.l = __shfl_up_sync(0xffffffffu, S.Z.v[VW - 1], 1);
-  S.Z.r = __shfl_down_sync(0xffffffffu, S.Z.v[0], 1);
-  edges_zero<E, VW>(S.Z, lane);
-#pragma unroll
-  for (int e = 0; e < VW; ++e) S.rp[e] = rpn[e];
+  if (live) st16<E, VW>(zrow, Z.v);
+  Z.l = __shfl_up_sync(0xffffffffu, Z.v[VW - 1], 1);
+  Z.r = __shfl_down_sync(0xffffffffu, Z.v[0], 1);
+  edges_zero<E, VW>(Z, lane);
+}
+
+// Helper warp, forward, iteration t at window phase PH (rows t, t + 1, t + 2 of y in
+// slots PH, PH + 1, PH + 2 mod 3): publish rp of row t + 1, take step t + 2 (x, x_prev
+// of row t + 3, b of row t + 2), put y of row t + 3 into slot PH and form rp of row t + 2.
+template <typename E, int VW, int PH>
+__device__ __forceinline__ void fwd_helper_iter(int t, RowVW<E, VW>* Y, E* rp, unsigned char* rpring, const RowRing<E, VW>& ring,
+                                                int n, int pitch, int c0, bool live, bool hx, bool mom, E ati,
+                                                E rc, E axr, E ayr, E d1r, E d2r, int lane, const E* xb,
+                                                const E* xpb, const E* bb) {
+  constexpr int S0 = PH, S1 = (PH + 1) % 3, S2 = (PH + 2) % 3;
+  st_il<E, VW>(rpring + ((t + 1) & 1) * RowRing<E, VW>::ROW, lane, rp);
+  row_wait();
+  const int sl = (t + 2) % kRowSlots;
+  E xv[VW], xpv[VW], bv[VW];
+  ring.load(0, sl, xv);
+  if (mom) ring.load(1, sl, xpv);
+  ring.load(2, sl, bv);
+  {
+    const int s = t + 2 + kRowPF;
+    const int sn = s % kRowSlots;
+    const bool vx = hx && live && s + 1 <= n, vb = live && s >= 1 && s <= n;
+    ring.issue(0, sn, xb, s + 1, pitch, c0, vx);
+    if (mom) ring.issue(1, sn, xpb, s + 1, pitch, c0, vx);
+    ring.issue(2, sn, bb, s, pitch, c0, vb);
+    row_commit();
+  }
+  y_from<E, VW>(xv, xpv, ati, mom, Y[S0]);
+  edges_zero<E, VW>(Y[S0], lane);
+  scaled_rhs<E, VW>(Y[S1], Y[S2], Y[S0], bv, rc, axr, ayr, d1r, d2r, rp);
 }
 
 template <typename E, int VW>
-__global__ void __launch_bounds__(kSsorWarps * 32) ssor_forward_row_kernel(const SsorArgs<E> A) {
+__global__ void __launch_bounds__(64) ssor_forward_pipe_kernel(const SsorArgs<E> A) {
   extern __shared__ __align__(16) unsigned char ssor_smem[];
   const int lane = threadIdx.x & 31;
-  const int inst = blockIdx.x * kSsorWarps + (threadIdx.x >> 5);
-  if (inst >= A.batch) return;
-  if (A.active && A.active[inst] == 0) return;
+  const bool helper = threadIdx.x >= 32;
+  const int inst = blockIdx.x;
+  if (A.active && A.active[inst] == 0) return;  // both warps
   const Inst& I = A.insts[inst];
   const int n = I.n, pitch = I.pitch;
   const E rc = E(1) / (E)I.c;
   const E axr = (E)I.ax * rc, ayr = (E)I.ay * rc, d1r = (E)I.d1 * rc, d2r = (E)I.d2 * rc;
   const E kx = A.relax * axr, ky = A.relax * ayr, k1 = A.relax * d1r, k2 = A.relax * d2r;
-  E qd[5];  // multipliers of 2^d consecutive lanes' maps
-  {
-    E q = E(1);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) q *= -kx;
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-      qd[d] = q;
-      q *= q;
-    }
-  }
-  const int ci = inst * A.m + A.kidx;
-  const E ati = A.a ? (A.at ? A.at[ci] : A.a[ci]) : E(0);
-  const bool hx = A.x != nullptr;  // else y = 0: the x copies are zero fills from b's address
-  const bool mom = hx && A.xp != nullptr && ati != E(0);
-  const E* bb = A.b + I.off;
-  const E* xb = hx ? A.x + I.off : bb;
-  const E* xpb = A.xp ? A.xp + I.off : xb;
-  E* zb = A.z + I.off;
   const int c0 = lane * VW;
   const bool live = c0 < pitch;
-  E k[VW], mk[VW];  // recurrence coefficient and mask per column: 0 beyond the domain (z = 0 there)
+  unsigned char* rpring = ssor_smem + RowRing<E, VW>::BYTES;
+  if (helper) {
+    const int ci = inst * A.m + A.kidx;
+    const E ati = A.a ? (A.at ? A.at[ci] : A.a[ci]) : E(0);
+    const bool hx = A.x != nullptr;  // else y = 0: the x copies are zero fills from b's address
+    const bool mom = hx && A.xp != nullptr && ati != E(0);
+    const E* bb = A.b + I.off;
+    const E* xb = hx ? A.x + I.off : bb;
+    const E* xpb = A.xp ? A.xp + I.off : xb;
+    RowRing<E, VW> ring{ssor_smem, lane};
+    // step s brings x and x_prev of row s + 1 and b of row s
+    auto issue = [&](int s) {
+      const int sl = s % kRowSlots;
+      const bool vx = hx && live && s + 1 <= n, vb = live && s >= 1 && s <= n;
+      ring.issue(0, sl, xb, s + 1, pitch, c0, vx);
+      if (mom) ring.issue(1, sl, xpb, s + 1, pitch, c0, vx);
+      ring.issue(2, sl, bb, s, pitch, c0, vb);
+      row_commit();
+    };
+    RowVW<E, VW> Y[3];  // slot 0: row 0 (zero), 1: row 1, 2: row 2
 #pragma unroll
-  for (int e = 0; e < VW; ++e) {
-    mk[e] = (c0 + e < n) ? E(1) : E(0);
-    k[e] = -kx * mk[e];
+    for (int e = 0; e < VW; ++e) Y[0].v[e] = E(0);
+    Y[0].l = Y[0].r = E(0);
+#pragma unroll
+    for (int s = 0; s < kRowPF; ++s) issue(s);
+    E xv[VW], xpv[VW], bv[VW], rp[VW];
+    row_wait();  // step 0: x, x_prev of row 1
+    ring.load(0, 0, xv);
+    if (mom) ring.load(1, 0, xpv);
+    y_from<E, VW>(xv, xpv, ati, mom, Y[1]);
+    edges_zero<E, VW>(Y[1], lane);
+    issue(kRowPF);
+    row_wait();  // step 1: x, x_prev of row 2, b of row 1
+    ring.load(0, 1, xv);
+    if (mom) ring.load(1, 1, xpv);
+    ring.load(2, 1, bv);
+    y_from<E, VW>(xv, xpv, ati, mom, Y[2]);
+    edges_zero<E, VW>(Y[2], lane);
+    issue(kRowPF + 1);
+    scaled_rhs<E, VW>(Y[0], Y[1], Y[2], bv, rc, axr, ayr, d1r, d2r, rp);  // rp of row 1
+    for (int t = 0; t <= n; t += 3) {
+      fwd_helper_iter<E, VW, 0>(t, Y, rp, rpring, ring, n, pitch, c0, live, hx, mom, ati, rc, axr, ayr, d1r, d2r,
+                                lane, xb, xpb, bb);
+      pipe_sync();
+      if (t + 1 > n) break;
+      fwd_helper_iter<E, VW, 1>(t + 1, Y, rp, rpring, ring, n, pitch, c0, live, hx, mom, ati, rc, axr, ayr, d1r, d2r,
+                                lane, xb, xpb, bb);
+      pipe_sync();
+      if (t + 2 > n) break;
+      fwd_helper_iter<E, VW, 2>(t + 2, Y, rp, rpring, ring, n, pitch, c0, live, hx, mom, ati, rc, axr, ayr, d1r, d2r,
+                                lane, xb, xpb, bb);
+      pipe_sync();
+    }
+    row_wait_all();
+  } else {
+    E qd[5];  // multipliers of 2^d consecutive lanes' maps
+    {
+      E q = E(1);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) q *= -kx;
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        qd[d] = q;
+        q *= q;
+      }
+    }
+    E k[VW], mk[VW];  // recurrence coefficient and mask per column: 0 beyond the domain (z = 0 there)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      mk[e] = (c0 + e < n) ? E(1) : E(0);
+      k[e] = -kx * mk[e];
+    }
+    E* zb = A.z + I.off;
+    RowVW<E, VW> Z;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) Z.v[e] = E(0);
+    Z.l = Z.r = E(0);
+    for (int t = 0; t <= n; t += 3) {
+      // iteration t: row t (none at t = 0), from the rp the helper published at t - 1
+      if (t >= 1) {
+        E rp[VW];
+        ld_il<E, VW>(rpring + (t & 1) * RowRing<E, VW>::ROW, lane, rp);
+        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, ky, k1, k2, lane, live, zb + (long long)t * pitch + c0);
+      }
+      pipe_sync();
+      if (t + 1 > n) break;
+      {
+        E rp[VW];
+        ld_il<E, VW>(rpring + ((t + 1) & 1) * RowRing<E, VW>::ROW, lane, rp);
+        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, ky, k1, k2, lane, live, zb + (long long)(t + 1) * pitch + c0);
+      }
+      pipe_sync();
+      if (t + 2 > n) break;
+      {
+        E rp[VW];
+        ld_il<E, VW>(rpring + ((t + 2) & 1) * RowRing<E, VW>::ROW, lane, rp);
+        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, ky, k1, k2, lane, live, zb + (long long)(t + 2) * pitch + c0);
+      }
+      pipe_sync();
+    }
   }
-  RowRing<E, VW> ring{ssor_smem + (threadIdx.x >> 5) * RowRing<E, VW>::BYTES, lane};
-  // step t (0..n) brings x and x_prev of row t + 1 and b of row t
-  auto issue = [&](int t) {
-    const int sl = t % kRowSlots;
-    const bool vx = hx && live && t + 1 <= n, vb = live && t >= 1 && t <= n;
-    ring.issue(0, sl, xb, t + 1, pitch, c0, vx);
-    if (mom) ring.issue(1, sl, xpb, t + 1, pitch, c0, vx);
-    ring.issue(2, sl, bb, t, pitch, c0, vb);
-    row_commit();
-  };
-  FwdRow<E, VW> S;
-#pragma unroll
-  for (int e = 0; e < VW; ++e) S.Z.v[e] = S.Y[2].v[e] = E(0);
-  S.Z.l = S.Z.r = S.Y[2].l = S.Y[2].r = E(0);
-#pragma unroll
-  for (int t = 0; t < kRowPF; ++t) issue(t);
-  E xv[VW], xpv[VW], bv[VW];
-  row_wait();  // step 0: x, x_prev of row 1
-  ld16<E, VW>(ring.at(0, 0), xv);
-  if (mom) ld16<E, VW>(ring.at(1, 0), xpv);
-  y_from<E, VW>(xv, xpv, ati, mom, S.Y[0]);
-  edges_zero<E, VW>(S.Y[0], lane);
-  issue(kRowPF);
-  row_wait();  // step 1: x, x_prev of row 2, b of row 1
-  ld16<E, VW>(ring.at(0, 1), xv);
-  if (mom) ld16<E, VW>(ring.at(1, 1), xpv);
-  ld16<E, VW>(ring.at(2, 1), bv);
-  y_from<E, VW>(xv, xpv, ati, mom, S.Y[1]);
-  edges_zero<E, VW>(S.Y[1], lane);
-  issue(kRowPF + 1);
-  scaled_rhs<E, VW>(S.Y[2], S.Y[0], S.Y[1], bv, rc, axr, ayr, d1r, d2r, S.rp);
-  // the loop consumed steps 0 and 1; fwd_row(i) consumes step i + 1 and issues step i + 1 + PF
-  for (int i = 1; i <= n; i += 3) {
-    fwd_row<E, VW, 0>(i, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, hx, pitch,
-                      zb + (long long)i * pitch + c0, xb, xpb, bb, n, c0);
-    if (i + 1 > n) break;
-    fwd_row<E, VW, 1>(i + 1, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, hx, pitch,
-                      zb + (long long)(i + 1) * pitch + c0, xb, xpb, bb, n, c0);
-    if (i + 2 > n) break;
-    fwd_row<E, VW, 2>(i + 2, S, ring, k, mk, qd, ky, k1, k2, rc, axr, ayr, d1r, d2r, ati, mom, lane, live, hx, pitch,
-                      zb + (long long)(i + 2) * pitch + c0, xb, xpb, bb, n, c0);
-  }
-  row_wait_all();
 }
 
 template <typename E, int VW>
-__global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_row_kernel(const SsorArgs<E> A) {
+__global__ void __launch_bounds__(64) ssor_backward_pipe_kernel(const SsorArgs<E> A) {
   extern __shared__ __align__(16) unsigned char ssor_smem[];
+  using Ring = RowRing<E, VW, kPipeSlotsB>;
   const int lane = threadIdx.x & 31;
-  const int inst = blockIdx.x * kSsorWarps + (threadIdx.x >> 5);
-  if (inst >= A.batch) return;
-  if (A.active && A.active[inst] == 0) return;
+  const bool helper = threadIdx.x >= 32;
+  const int inst = blockIdx.x;
+  if (A.active && A.active[inst] == 0) return;  // both warps
   const Inst& I = A.insts[inst];
   const int n = I.n, pitch = I.pitch;
-  const E c = (E)I.c, ax = (E)I.ax, ay = (E)I.ay, d1 = (E)I.d1, d2 = (E)I.d2;
-  const E rc = E(1) / c;
-  const E kx = A.relax * ax * rc, ky = A.relax * ay * rc, k1 = A.relax * d1 * rc, k2 = A.relax * d2 * rc;
-  E qd[5];
-  {
-    E q = E(1);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) q *= -kx;
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-      qd[d] = q;
-      q *= q;
-    }
-  }
-  const int ci = inst * A.m + A.kidx;
-  const E wi = (A.w ? A.w[ci] : E(1)) * A.relax * (E(2) - A.relax);
-  const E ai = A.a ? A.a[ci] : E(0);
-  const bool hx = A.x != nullptr;  // else x = 0: zero fills from z's address
-  const bool mom = hx && A.xp != nullptr;
-  const E* zb = A.z + I.off;
-  const E* xb = hx ? A.x + I.off : zb;
-  const E* xpb = A.xp ? A.xp + I.off : xb;
-  E* ox = A.out_x + I.off;
-  E* oxp = A.out_xp ? A.out_xp + I.off : nullptr;
+  const E rc = E(1) / (E)I.c;
+  const E kx = A.relax * (E)I.ax * rc, ky = A.relax * (E)I.ay * rc, k1 = A.relax * (E)I.d1 * rc,
+          k2 = A.relax * (E)I.d2 * rc;
   const int c0 = lane * VW;
   const bool live = c0 < pitch;
-  E zero[VW];
+  Ring ring{ssor_smem, lane};
+  unsigned char* sring = ssor_smem + Ring::BYTES;
+  if (helper) {
+    const int ci = inst * A.m + A.kidx;
+    const E wi = (A.w ? A.w[ci] : E(1)) * A.relax * (E(2) - A.relax);
+    const E ai = A.a ? A.a[ci] : E(0);
+    const bool hx = A.x != nullptr;  // else x = 0: zero fills from z's address
+    const bool mom = hx && A.xp != nullptr;
+    const E* zb = A.z + I.off;
+    const E* xb = hx ? A.x + I.off : zb;
+    const E* xpb = A.xp ? A.xp + I.off : xb;
+    E* ox = A.out_x + I.off;
+    E* oxp = A.out_xp ? A.out_xp + I.off : nullptr;
+    E zero[VW];
 #pragma unroll
-  for (int e = 0; e < VW; ++e) zero[e] = E(0);
-  if (live) {  // the output's halo rows (the buffer may come uninitialised from a rotation)
-    st16<E, VW>(ox + c0, zero);
-    st16<E, VW>(ox + (long long)(n + 1) * pitch + c0, zero);
-    if (oxp) {
-      st16<E, VW>(oxp + c0, zero);
-      st16<E, VW>(oxp + (long long)(n + 1) * pitch + c0, zero);
+    for (int e = 0; e < VW; ++e) zero[e] = E(0);
+    if (live) {  // the output's halo rows (the buffer may come uninitialised from a rotation)
+      st16<E, VW>(ox + c0, zero);
+      st16<E, VW>(ox + (long long)(n + 1) * pitch + c0, zero);
+      if (oxp) {
+        st16<E, VW>(oxp + c0, zero);
+        st16<E, VW>(oxp + (long long)(n + 1) * pitch + c0, zero);
+      }
+    }
+    // the copies of row r (z, x, x_prev) go to slot (n - r) mod slots
+    auto issue = [&](int r) {
+      const int sl = (n - r) % kPipeSlotsB;
+      const bool v = live && r >= 1;
+      ring.issue(0, sl, zb, r, pitch, c0, v);
+      ring.issue(1, sl, xb, r, pitch, c0, v && hx);
+      if (mom) ring.issue(2, sl, xpb, r, pitch, c0, v);
+      row_commit();
+    };
+#pragma unroll
+    for (int q = 0; q < kRowPF; ++q) issue(n - q);
+    row_wait();  // row n for the solver's first iteration
+    pipe_sync();
+    for (int t = 0; t <= n; ++t) {
+      if (t >= 1 && live) {  // the update of row n - t + 1 with the s of iteration t - 1
+        const int r = n - t + 1;
+        const int sl = (t - 1) % kPipeSlotsB;
+        E xv[VW], xpv[VW], sv[VW], xn[VW];
+        ring.load(1, sl, xv);
+        if (mom) ring.load(2, sl, xpv);
+        ld_il<E, VW>(sring + ((t - 1) & 1) * Ring::ROW, lane, sv);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) xn[e] = xv[e] + ai * (mom ? xv[e] - xpv[e] : E(0)) + wi * sv[e];
+        const long long o = (long long)r * pitch + c0;
+        st16<E, VW>(ox + o, xn);
+        if (oxp) st16<E, VW>(oxp + o, xv);
+      }
+      issue(n - t - kRowPF);
+      row_wait();  // row n - t - 1 for the solver's next iteration
+      pipe_sync();
+    }
+    row_wait_all();
+  } else {
+    E qd[5];
+    {
+      E q = E(1);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) q *= -kx;
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        qd[d] = q;
+        q *= q;
+      }
+    }
+    E k[VW], mk[VW];  // recurrence coefficient and mask per column: 0 beyond the domain
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      mk[e] = (c0 + e < n) ? E(1) : E(0);
+      k[e] = -kx * mk[e];
+    }
+    RowVW<E, VW> SD;  // s of the row below
+#pragma unroll
+    for (int e = 0; e < VW; ++e) SD.v[e] = E(0);
+    SD.l = SD.r = E(0);
+    pipe_sync();
+    for (int t = 0; t <= n; ++t) {
+      if (t < n) {  // row n - t
+        E zc[VW];
+        ring.load(0, t % kPipeSlotsB, zc);
+        E tv[VW];
+        E P = E(0);
+#pragma unroll
+        for (int e = VW - 1; e >= 0; --e) {
+          tv[e] = mk[e] * (zc[e] - (ky * SD.v[e] + k1 * right_of(SD, e) + k2 * left_of(SD, e)));
+          P = tv[e] + k[e] * P;
+        }
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          const E Pp = __shfl_down_sync(0xffffffffu, P, 1 << d);
+          if (lane + (1 << d) < 32) P = P + qd[d] * Pp;
+        }
+        E sv = __shfl_down_sync(0xffffffffu, P, 1);
+        if (lane == 31) sv = E(0);
+#pragma unroll
+        for (int e = VW - 1; e >= 0; --e) {
+          sv = tv[e] + k[e] * sv;
+          SD.v[e] = sv;
+        }
+        st_il<E, VW>(sring + (t & 1) * Ring::ROW, lane, SD.v);
+        SD.l = __shfl_up_sync(0xffffffffu, SD.v[VW - 1], 1);
+        SD.r = __shfl_down_sync(0xffffffffu, SD.v[0], 1);
+        edges_zero<E, VW>(SD, lane);
+      }
+      pipe_sync();
     }
   }
-  E k[VW], mk[VW];  // recurrence coefficient and mask per column: 0 beyond the domain
-#pragma unroll
-  for (int e = 0; e < VW; ++e) {
-    mk[e] = (c0 + e < n) ? E(1) : E(0);
-    k[e] = -kx * mk[e];
-  }
-  RowRing<E, VW> ring{ssor_smem + (threadIdx.x >> 5) * RowRing<E, VW>::BYTES, lane};
-  // step t (n down to 1) brings z, x and x_prev of row t into slot (n - t) mod slots
-  auto issue = [&](int t) {
-    const int sl = (n - t) % kRowSlots;
-    const bool v = live && t >= 1;
-    ring.issue(0, sl, zb, t, pitch, c0, v);
-    ring.issue(1, sl, xb, t, pitch, c0, v && hx);
-    if (mom) ring.issue(2, sl, xpb, t, pitch, c0, v);
-    row_commit();
-  };
-  RowVW<E, VW> SD;
-#pragma unroll
-  for (int e = 0; e < VW; ++e) SD.v[e] = E(0);
-  SD.l = SD.r = E(0);
-#pragma unroll
-  for (int t = 0; t < kRowPF; ++t) issue(n - t);
-  for (int i = n; i >= 1; --i) {
-    const int sl = (n - i) % kRowSlots;
-    row_wait();
-    E zc[VW], xv[VW], xpv[VW];
-    ld16<E, VW>(ring.at(0, sl), zc);
-    ld16<E, VW>(ring.at(1, sl), xv);
-    if (mom) ld16<E, VW>(ring.at(2, sl), xpv);
-    issue(i - kRowPF);
-    E t[VW];
-    E P = E(0);
-#pragma unroll
-    for (int e = VW - 1; e >= 0; --e) {
-      t[e] = mk[e] * (zc[e] - (ky * SD.v[e] + k1 * right_of(SD, e) + k2 * left_of(SD, e)));
-      P = t[e] + k[e] * P;
-    }
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-      const E Pp = __shfl_down_sync(0xffffffffu, P, 1 << d);
-      if (lane + (1 << d) < 32) P = P + qd[d] * Pp;
-    }
-    E sv = __shfl_down_sync(0xffffffffu, P, 1);
-    if (lane == 31) sv = E(0);
-#pragma unroll
-    for (int e = VW - 1; e >= 0; --e) {
-      sv = t[e] + k[e] * sv;
-      SD.v[e] = sv;
-    }
-    if (live) {
-      const long long o = (long long)i * pitch + c0;
-      E xn[VW];
-#pragma unroll
-      for (int e = 0; e < VW; ++e) xn[e] = xv[e] + ai * (mom ? xv[e] - xpv[e] : E(0)) + wi * SD.v[e];
-      st16<E, VW>(ox + o, xn);
-      if (oxp) st16<E, VW>(oxp + o, xv);
-    }
-    SD.l = __shfl_up_sync(0xffffffffu, SD.v[VW - 1], 1);
-    SD.r = __shfl_down_sync(0xffffffffu, SD.v[0], 1);
-    edges_zero<E, VW>(SD, lane);
-  }
-  row_wait_all();
 }
 
 // The row kernels' rings exceed the default 48 KB of dynamic shared memory per block.
 template <typename E>
 static cudaError_t ssor_row_attributes() {
   constexpr int VW = SsorVW<E>::v;
-  const int bytes = RowRing<E, VW>::BYTES * kSsorWarps;
-  cudaError_t e = cudaFuncSetAttribute(ssor_forward_row_kernel<E, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       bytes);
+  cudaError_t e = cudaFuncSetAttribute(ssor_forward_pipe_kernel<E, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PipeSizes<E, VW>::FWD);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(ssor_backward_row_kernel<E, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(ssor_backward_pipe_kernel<E, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PipeSizes<E, VW>::BWD);
   return e;
 }
 
@@ -672,11 +775,10 @@ richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, cons
   const int blocks = (op->batch + kSsorWarps - 1) / kSsorWarps;
   int max_pitch = 0;
   for (const Inst& I : op->h_inst) max_pitch = std::max(max_pitch, I.pitch);
-  if (max_pitch <= 32 * VW) {  // every row is one chunk
-    const size_t smem = (size_t)RowRing<E, VW>::BYTES * kSsorWarps;
-    ssor_forward_row_kernel<E, VW><<<blocks, kSsorWarps * 32, smem, s>>>(A);
+  if (max_pitch <= 32 * VW) {  // every row is one chunk: two-warp row pipelines, one block per instance
+    ssor_forward_pipe_kernel<E, VW><<<op->batch, 64, PipeSizes<E, VW>::FWD, s>>>(A);
     RICHM_LAUNCH_CHECK("SSOR forward solve");
-    ssor_backward_row_kernel<E, VW><<<blocks, kSsorWarps * 32, smem, s>>>(A);
+    ssor_backward_pipe_kernel<E, VW><<<op->batch, 64, PipeSizes<E, VW>::BWD, s>>>(A);
     RICHM_LAUNCH_CHECK("SSOR backward solve");
     return RICHM_OK;
   }

@@ -271,6 +271,20 @@ def test_fp32_fused_sweeps_match_oracle(fuse, variant):
 
 
 @pytest.mark.parametrize("fuse", [4, 8])
+@pytest.mark.parametrize("variant", ["nag", "nagex"])
+def test_fp32_fused_jacobi_preconditioned_sweeps_match_oracle(fuse, variant):
+    # the fused kernels' B^{-1} = D^{-1} variants (weights scaled by the constant 1/d)
+    sizes = [5, 127, 129, 255, 300]
+    K, k_start = 2 * fuse, 2
+    for g, ref, gp, refp, w, a, at, G in _run_case(richm.F32, variant, K=K, k_start=k_start, sizes=sizes,
+                                                   precond=1, fuse=fuse):
+        xmax = max(np.abs(ref).max(), 1.0)
+        bound = _fp32_bound(w, a, at, G, k_start, K, xmax, 1.0)
+        assert np.abs(g - ref).max() <= bound
+        assert np.abs(gp - refp).max() <= bound
+
+
+@pytest.mark.parametrize("fuse", [4, 8])
 @pytest.mark.parametrize("rows", [16, 48, 64])
 def test_fused_tail_tiles_match_oracle(fuse, rows):
     # sizes whose last column block is a 64-column tail tile (129..176 and 241..288
