@@ -419,6 +419,65 @@ __device__ __forceinline__ void scaled_rhs(const RowVW<E, VW>& U, const RowVW<E,
   }
 }
 
+// FP32 rows of 16 columns per lane: the same on packed pairs of columns (sm_100's FFMA2
+// and friends: one issue slot for two columns), with the horizontal couplings written
+// per column as west / east terms W_j = axr C_j + d1r U_j + d2r D_j and
+// E_j = axr C_j + d2r U_j + d1r D_j formed on pairs, so that only their shifted sum
+// W_{e-1} + E_{e+1} needs per-column adds.
+template <>
+__device__ __forceinline__ void scaled_rhs<float, 16>(const RowVW<float, 16>& U, const RowVW<float, 16>& C,
+                                                      const RowVW<float, 16>& D, const float* bv, float rc, float axr,
+                                                      float ayr, float d1r, float d2r, float* rp) {
+  const float2 ax2 = make_float2(axr, axr), d12 = make_float2(d1r, d1r), d22 = make_float2(d2r, d2r);
+  const float2 nay2 = make_float2(-ayr, -ayr), rc2 = make_float2(rc, rc), m1 = make_float2(-1.f, -1.f);
+  float W[16], E[16];
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const float2 c2 = make_float2(C.v[2 * p], C.v[2 * p + 1]);
+    const float2 u2 = make_float2(U.v[2 * p], U.v[2 * p + 1]);
+    const float2 d2 = make_float2(D.v[2 * p], D.v[2 * p + 1]);
+    const float2 axc = __fmul2_rn(ax2, c2);
+    const float2 w2 = __ffma2_rn(d22, d2, __ffma2_rn(d12, u2, axc));
+    const float2 e2 = __ffma2_rn(d12, d2, __ffma2_rn(d22, u2, axc));
+    W[2 * p] = w2.x;
+    W[2 * p + 1] = w2.y;
+    E[2 * p] = e2.x;
+    E[2 * p + 1] = e2.y;
+  }
+  const float wl = fmaf(d2r, D.l, fmaf(d1r, U.l, axr * C.l));  // W of the column left of this lane
+  const float er = fmaf(d1r, D.r, fmaf(d2r, U.r, axr * C.r));  // E of the column right of this lane
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const float2 c2 = make_float2(C.v[2 * p], C.v[2 * p + 1]);
+    const float2 u2 = make_float2(U.v[2 * p], U.v[2 * p + 1]);
+    const float2 d2 = make_float2(D.v[2 * p], D.v[2 * p + 1]);
+    const float2 b2 = make_float2(bv[2 * p], bv[2 * p + 1]);
+    const float2 s2 = make_float2((p == 0 ? wl : W[2 * p - 1]) + E[2 * p + 1],
+                                  W[2 * p] + (p == 7 ? er : E[2 * p + 2]));
+    float2 t = __ffma2_rn(m1, c2, __fmul2_rn(b2, rc2));
+    t = __ffma2_rn(nay2, __fadd2_rn(u2, d2), t);
+    t = __ffma2_rn(m1, s2, t);
+    rp[2 * p] = t.x;
+    rp[2 * p + 1] = t.y;
+  }
+}
+
+template <>
+__device__ __forceinline__ void y_from<float, 16>(const float* xv, const float* xpv, float at, bool mom,
+                                                  RowVW<float, 16>& Y) {
+  const float2 at2 = make_float2(at, at), m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const float2 x2 = make_float2(xv[2 * p], xv[2 * p + 1]);
+    float2 y2 = x2;
+    if (mom) y2 = __ffma2_rn(at2, __ffma2_rn(m1, make_float2(xpv[2 * p], xpv[2 * p + 1]), x2), x2);
+    Y.v[2 * p] = y2.x;
+    Y.v[2 * p + 1] = y2.y;
+  }
+  Y.l = __shfl_up_sync(0xffffffffu, Y.v[15], 1);
+  Y.r = __shfl_down_sync(0xffffffffu, Y.v[0], 1);
+}
+
 // ---------------------------------------------------------------- two-warp row pipelines
 // The single-warp row kernels spend most of a row on work off the recurrence's critical
 // path (loading and forming the next rows' right-hand sides, the Table 1 update), which
@@ -443,29 +502,85 @@ struct PipeSizes {
   static constexpr int BWD = RowRing<E, VW, kPipeSlotsB>::BYTES + RPB;
 };
 
+// Per-lane constants of the in-row recurrence v_e = q_e + k_e v_{e-1} over this lane's
+// VW columns in recurrence order (the backward solve passes its columns reversed). The
+// composed map's offset P = sum_e ce_e q_e (ce_e = product of k after e) is summed as
+// four independent partial sums, and the replay runs in groups of four columns: local
+// recurrences from 0, a carry chain over the groups, and a fix-up with pk_e = product
+// of k from the group's first column to e. Dependent steps per row: 6 + 9 instead of
+// 16 + 16 for VW = 16.
+template <typename E, int VW>
+struct RecCoef {
+  E ce[VW];
+  E pk[VW];
+};
+
+template <typename E, int VW>
+__device__ __forceinline__ void rec_coef(const E* k, RecCoef<E, VW>& R) {
+  E p = E(1);
+#pragma unroll
+  for (int e = VW - 1; e >= 0; --e) {
+    R.ce[e] = p;
+    p *= k[e];
+  }
+#pragma unroll
+  for (int g = 0; g < VW / 4; ++g) {
+    E q = E(1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      q *= k[4 * g + j];
+      R.pk[4 * g + j] = q;
+    }
+  }
+}
+
+template <typename E, int VW>
+__device__ __forceinline__ E rec_compose(const E* q, const RecCoef<E, VW>& R) {
+  E s[4] = {E(0), E(0), E(0), E(0)};
+#pragma unroll
+  for (int e = 0; e < VW; ++e) s[e % 4] = fma(R.ce[e], q[e], s[e % 4]);
+  return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
+template <typename E, int VW>
+__device__ __forceinline__ void rec_replay(const E* q, const E* k, const RecCoef<E, VW>& R, E vin, E* v) {
+  E loc[VW];
+#pragma unroll
+  for (int g = 0; g < VW / 4; ++g) {
+    E u = E(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      u = fma(k[4 * g + j], u, q[4 * g + j]);
+      loc[4 * g + j] = u;
+    }
+  }
+  E carry = vin;
+#pragma unroll
+  for (int g = 0; g < VW / 4; ++g) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[4 * g + j] = fma(R.pk[4 * g + j], carry, loc[4 * g + j]);
+    carry = v[4 * g + 3];
+  }
+}
+
 // Solver warp, forward: row i from rp (this lane's VW values) and the previous row of z.
 template <typename E, int VW>
 __device__ __forceinline__ void fwd_solve_row(const E* rp, RowVW<E, VW>& Z, const E* k, const E* mk, const E* qd,
-                                              E ky, E k1, E k2, int lane, bool live, E* zrow) {
+                                              const RecCoef<E, VW>& R, E ky, E k1, E k2, int lane, bool live,
+                                              E* zrow) {
   E q[VW];
-  E P = E(0);
 #pragma unroll
-  for (int e = 0; e < VW; ++e) {  // z = 0 beyond the domain (mask 0)
+  for (int e = 0; e < VW; ++e)  // z = 0 beyond the domain (mask 0)
     q[e] = mk[e] * (rp[e] - (ky * Z.v[e] + k1 * left_of(Z, e) + k2 * right_of(Z, e)));
-    P = q[e] + k[e] * P;
-  }
+  E P = rec_compose<E, VW>(q, R);
 #pragma unroll
   for (int d = 0; d < 5; ++d) {
     const E Pp = __shfl_up_sync(0xffffffffu, P, 1 << d);
     if (lane >= (1 << d)) P = P + qd[d] * Pp;
   }
-  E zv = __shfl_up_sync(0xffffffffu, P, 1);
-  if (lane == 0) zv = E(0);
-#pragma unroll
-  for (int e = 0; e < VW; ++e) {
-    zv = q[e] + k[e] * zv;
-    Z.v[e] = zv;
-  }
+  E zin = __shfl_up_sync(0xffffffffu, P, 1);
+  if (lane == 0) zin = E(0);
+  rec_replay<E, VW>(q, k, R, zin, Z.v);
   if (live) st16<E, VW>(zrow, Z.v);
   Z.l = __shfl_up_sync(0xffffffffu, Z.v[VW - 1], 1);
   Z.r = __shfl_down_sync(0xffffffffu, Z.v[0], 1);
@@ -588,6 +703,8 @@ __global__ void __launch_bounds__(64) ssor_forward_pipe_kernel(const SsorArgs<E>
       mk[e] = (c0 + e < n) ? E(1) : E(0);
       k[e] = -kx * mk[e];
     }
+    RecCoef<E, VW> R;
+    rec_coef<E, VW>(k, R);
     E* zb = A.z + I.off;
     RowVW<E, VW> Z;
 #pragma unroll
@@ -598,21 +715,21 @@ __global__ void __launch_bounds__(64) ssor_forward_pipe_kernel(const SsorArgs<E>
       if (t >= 1) {
         E rp[VW];
         ld_il<E, VW>(rpring + (t & 1) * RowRing<E, VW>::ROW, lane, rp);
-        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, ky, k1, k2, lane, live, zb + (long long)t * pitch + c0);
+        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, R, ky, k1, k2, lane, live, zb + (long long)t * pitch + c0);
       }
       pipe_sync();
       if (t + 1 > n) break;
       {
         E rp[VW];
         ld_il<E, VW>(rpring + ((t + 1) & 1) * RowRing<E, VW>::ROW, lane, rp);
-        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, ky, k1, k2, lane, live, zb + (long long)(t + 1) * pitch + c0);
+        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, R, ky, k1, k2, lane, live, zb + (long long)(t + 1) * pitch + c0);
       }
       pipe_sync();
       if (t + 2 > n) break;
       {
         E rp[VW];
         ld_il<E, VW>(rpring + ((t + 2) & 1) * RowRing<E, VW>::ROW, lane, rp);
-        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, ky, k1, k2, lane, live, zb + (long long)(t + 2) * pitch + c0);
+        fwd_solve_row<E, VW>(rp, Z, k, mk, qd, R, ky, k1, k2, lane, live, zb + (long long)(t + 2) * pitch + c0);
       }
       pipe_sync();
     }
@@ -708,6 +825,11 @@ __global__ void __launch_bounds__(64) ssor_backward_pipe_kernel(const SsorArgs<E
       mk[e] = (c0 + e < n) ? E(1) : E(0);
       k[e] = -kx * mk[e];
     }
+    E kr[VW];  // the recurrence runs over the columns in reverse
+#pragma unroll
+    for (int e = 0; e < VW; ++e) kr[e] = k[VW - 1 - e];
+    RecCoef<E, VW> R;
+    rec_coef<E, VW>(kr, R);
     RowVW<E, VW> SD;  // s of the row below
 #pragma unroll
     for (int e = 0; e < VW; ++e) SD.v[e] = E(0);
@@ -717,25 +839,22 @@ __global__ void __launch_bounds__(64) ssor_backward_pipe_kernel(const SsorArgs<E
       if (t < n) {  // row n - t
         E zc[VW];
         ring.load(0, t % kPipeSlotsB, zc);
-        E tv[VW];
-        E P = E(0);
+        E tr[VW];  // t in reversed column order
 #pragma unroll
-        for (int e = VW - 1; e >= 0; --e) {
-          tv[e] = mk[e] * (zc[e] - (ky * SD.v[e] + k1 * right_of(SD, e) + k2 * left_of(SD, e)));
-          P = tv[e] + k[e] * P;
-        }
+        for (int e = VW - 1; e >= 0; --e)
+          tr[VW - 1 - e] = mk[e] * (zc[e] - (ky * SD.v[e] + k1 * right_of(SD, e) + k2 * left_of(SD, e)));
+        E P = rec_compose<E, VW>(tr, R);
 #pragma unroll
         for (int d = 0; d < 5; ++d) {
           const E Pp = __shfl_down_sync(0xffffffffu, P, 1 << d);
           if (lane + (1 << d) < 32) P = P + qd[d] * Pp;
         }
-        E sv = __shfl_down_sync(0xffffffffu, P, 1);
-        if (lane == 31) sv = E(0);
+        E sin = __shfl_down_sync(0xffffffffu, P, 1);
+        if (lane == 31) sin = E(0);
+        E sr[VW];
+        rec_replay<E, VW>(tr, kr, R, sin, sr);
 #pragma unroll
-        for (int e = VW - 1; e >= 0; --e) {
-          sv = tv[e] + k[e] * sv;
-          SD.v[e] = sv;
-        }
+        for (int e = 0; e < VW; ++e) SD.v[e] = sr[VW - 1 - e];
         st_il<E, VW>(sring + (t & 1) * Ring::ROW, lane, SD.v);
         SD.l = __shfl_up_sync(0xffffffffu, SD.v[VW - 1], 1);
         SD.r = __shfl_down_sync(0xffffffffu, SD.v[0], 1);
