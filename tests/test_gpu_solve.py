@@ -65,6 +65,23 @@ def _solve_setup(sizes, m=16, beta=0.3, seed=5):
     return insts, op, As, w, a, bs
 
 
+@pytest.mark.parametrize("refine_every", [128, 256])
+def test_solve_with_long_refinement_intervals_checked_by_oracle(refine_every):
+    # the benchmark's interval: FP32 sweeps carry the momentum across refinements, so a
+    # longer interval only moves where FP32 rounding is corrected
+    insts, op, As, w, a, bs = _solve_setup([15, 63, 130, 255])
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    opts = op.solve_opts(16, tol=1e-10, max_sweeps=400000, refine_every=refine_every, inner=richm.F32, fuse=8)
+    st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None, opts)
+    assert st == richm.OK, info
+    xs = from_dev(op, X, richm.F64)
+    for i, t in enumerate(insts):
+        r = np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i])
+        assert r <= 1e-10, (t, r)
+        assert info[i][0] % refine_every == 0
+
+
 @pytest.mark.parametrize("use_graph,fuse", [(1, 1), (0, 1), (1, 4), (1, 8)])
 def test_solve_to_1e10_checked_by_oracle(use_graph, fuse):
     insts, op, As, w, a, bs = _solve_setup([1, 2, 15, 31, 63, 64, 130])
