@@ -278,11 +278,25 @@ static richm_status forward_ckpt_t(richm_operator* op, const T* x0, const T* b, 
   T* W[4];  // three rotating states and the SSOR scratch
   for (int i = 0; i < 4; ++i) W[i] = reinterpret_cast<T*>(reinterpret_cast<char*>(work) + i * a256(bytes));
   const int nseg = K / s_every;
+  // FP32 segments of 8 (or 4) sweeps without SSOR: one temporally blocked pass per
+  // segment writes exactly the pair the next checkpoint holds (x_{k+TL}, x_{k+TL-1});
+  // it agrees with the one-sweep kernels that recompute the segments backward to FP32
+  // rounding (not bit for bit)
+  int TL = 0;
+  if constexpr (std::is_same<T, float>::value) {
+    if (precond != 2 && a != nullptr && (s_every == 8 || s_every == 4)) TL = s_every;
+  }
   for (int j = 0; j < nseg; ++j) {
     T* cx = ckpts + (size_t)j * slot;
     T* cxp = cx + es;
     T* nx = ckpts + (size_t)(j + 1) * slot;
     T* nxp = nx + es;
+    if constexpr (std::is_same<T, float>::value) {
+      if (TL) {
+        RICHM_TRY(launch_sweep_fused(op, TL, cx, cxp, b, nx, nxp, w, a, at, m, (j * s_every) % m, precond, nullptr, s));
+        continue;
+      }
+    }
     T* cur = cx;
     T* prev = cxp;
     for (int t = 0; t < s_every; ++t) {
