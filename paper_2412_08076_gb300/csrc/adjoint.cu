@@ -27,16 +27,33 @@ struct alignas(32) Dot3 {
   double v[4];
 };
 
+// Rows stream through per-warp shared-memory rings filled by cp.async two row steps
+// ahead (each lane copies and reads back only its own 16-byte chunks; lanes 0 and 31
+// also the chunks just outside the warp for the stencils' edge neighbours), as in the
+// one-sweep kernel: x, x_prev and the stenciled array of the window row, b, the carry
+// and (PM 2) lam of the output row.
+constexpr int kAdjPF = 2;
+constexpr int kAdjSlots = 4;
+constexpr int kAdjXC = 34, kAdjBC = 32;  // chunks per stencil row (with the two edge chunks) and per plain row
+__host__ __device__ constexpr int adj_ring_chunks() { return kAdjSlots * (3 * kAdjXC + 3 * kAdjBC); }
+
+__device__ __forceinline__ void adj_cp(uint4* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
 // PM: 0 no preconditioner, 1 Jacobi (d = 1/c), 2 a matrix B^{-1} applied beforehand
 // (u = B^{-1} lam in `ub`: the stencil and the weight gradient take u, the rest lam).
 template <typename T, bool MOM, int PM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     adjoint_kernel(const Inst* insts, const Tile* tiles, int ntiles, const T* __restrict__ lam,
-                   const T* __restrict__ ub, const T* __restrict__ carry, const T* __restrict__ x, const T* __restrict__ xp,
-                   const T* __restrict__ b, T* __restrict__ lam_out, T* __restrict__ carry_out,
-                   const T* __restrict__ w, const T* __restrict__ a, const T* __restrict__ at, int m, int kidx,
-                   int final_step, Dot3* __restrict__ partials) {
+                   const T* __restrict__ ub, const T* __restrict__ carry, const T* __restrict__ x,
+                   const T* __restrict__ xp, const T* __restrict__ b, T* __restrict__ lam_out,
+                   T* __restrict__ carry_out, const T* __restrict__ w, const T* __restrict__ a,
+                   const T* __restrict__ at, int m, int kidx, int final_step, Dot3* __restrict__ partials) {
   constexpr int VW = VecWidth<T>::value;
+  extern __shared__ __align__(16) uint4 adj_ring[];
   const int lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (wt >= ntiles) return;
@@ -59,15 +76,56 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int r0 = t.ty * kRows + 1;
   const int r1 = min(r0 + kRows - 1, n);
   const long long off = I.off;
+  const bool has_left = c0 > 0, has_right = c0 + VW < pitch;
+  const bool has_carry = MOM && carry != nullptr;
+  uint4* ring = adj_ring + (threadIdx.x >> 5) * adj_ring_chunks();
+  uint4* xr = ring;                        // [slot][XC]
+  uint4* xpr = xr + kAdjSlots * kAdjXC;    // [slot][XC]
+  uint4* lr = xpr + kAdjSlots * kAdjXC;    // [slot][XC] stenciled array
+  uint4* br = lr + kAdjSlots * kAdjXC;     // [slot][BC]
+  uint4* cr = br + kAdjSlots * kAdjBC;     // [slot][BC] carry
+  uint4* mr = cr + kAdjSlots * kAdjBC;     // [slot][BC] lam (PM 2)
 
-  auto load_y = [&](int pr, RowT<T, VW>& Y, T* xs, T* xps) {
-    const bool in = (pr >= 1) && (pr <= n);
-    VecN<T, VW> X{}, XP{};
-    const long long ro = off + (long long)pr * pitch;
-    if (in && live) {
-      X = ldv<T, VW>(x + ro + c0);
-      if (MOM) XP = ldv<T, VW>(xp + ro + c0);
+  // window row q of x, x_prev and the stenciled array; output row q - 1 of b, carry, lam
+  auto issue = [&](int q) {
+    const int so = q & (kAdjSlots - 1);
+    const bool rv = (q >= 1) && (q <= n) && (q <= r1 + 1);
+    const long long ro = off + (long long)(rv ? q : 0) * pitch;
+    const int cc = live ? c0 : 0;
+    adj_cp(xr + so * kAdjXC + 1 + lane, x + ro + cc, rv && live);
+    if (MOM) adj_cp(xpr + so * kAdjXC + 1 + lane, xp + ro + cc, rv && live);
+    adj_cp(lr + so * kAdjXC + 1 + lane, sl + ro + cc, rv && live);
+    if (lane == 0) {
+      const int lc = has_left ? c0 - VW : 0;
+      adj_cp(xr + so * kAdjXC, x + ro + lc, rv && has_left);
+      if (MOM) adj_cp(xpr + so * kAdjXC, xp + ro + lc, rv && has_left);
+      adj_cp(lr + so * kAdjXC, sl + ro + lc, rv && has_left);
     }
+    if (lane == 31) {
+      const int rc = has_right ? c0 + VW : 0;
+      adj_cp(xr + so * kAdjXC + 33, x + ro + rc, rv && has_right);
+      if (MOM) adj_cp(xpr + so * kAdjXC + 33, xp + ro + rc, rv && has_right);
+      adj_cp(lr + so * kAdjXC + 33, sl + ro + rc, rv && has_right);
+    }
+    const int qb = q - 1;
+    const bool bv = (qb >= r0) && (qb <= r1) && live;
+    const long long bo = off + (long long)(bv ? qb : 0) * pitch + (live ? c0 : 0);
+    adj_cp(br + so * kAdjBC + lane, b + bo, bv);
+    if (has_carry) adj_cp(cr + so * kAdjBC + lane, carry + bo, bv);
+    if (PM == 2) adj_cp(mr + so * kAdjBC + lane, lam + bo, bv);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  auto chunk = [&](const uint4* r, int i) {
+    VecN<T, VW> v;
+    *reinterpret_cast<uint4*>(&v) = r[i];
+    return v;
+  };
+  // y = x + at (x - x_prev) of window row q with its neighbours; x, x_prev kept
+  auto take_y = [&](int q, RowT<T, VW>& Y, T* xs, T* xps) {
+    const int so = q & (kAdjSlots - 1);
+    const VecN<T, VW> X = chunk(xr, so * kAdjXC + 1 + lane);
+    VecN<T, VW> XP{};
+    if (MOM) XP = chunk(xpr, so * kAdjXC + 1 + lane);
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       Y.y[e] = MOM ? X.v[e] + ati * (X.v[e] - XP.v[e]) : X.v[e];
@@ -75,50 +133,47 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       xps[e] = XP.v[e];
     }
     T le = 0, re = 0;
-    if (in) {
-      if (lane == 0 && c0 > 0) {
-        T xv = x[ro + c0 - 1];
-        le = MOM ? xv + ati * (xv - xp[ro + c0 - 1]) : xv;
-      }
-      if (lane == 31 && c0 + VW < pitch) {
-        T xv = x[ro + c0 + VW];
-        re = MOM ? xv + ati * (xv - xp[ro + c0 + VW]) : xv;
-      }
+    if (lane == 0) {
+      const VecN<T, VW> L = chunk(xr, so * kAdjXC);
+      le = L.v[VW - 1];
+      if (MOM) le = le + ati * (le - chunk(xpr, so * kAdjXC).v[VW - 1]);
+    }
+    if (lane == 31) {
+      const VecN<T, VW> R = chunk(xr, so * kAdjXC + 33);
+      re = R.v[0];
+      if (MOM) re = re + ati * (re - chunk(xpr, so * kAdjXC + 33).v[0]);
     }
     row_neighbours<T, VW>(Y, lane, le, re);
   };
-  auto load_l = [&](int pr, RowT<T, VW>& L) {
-    const bool in = (pr >= 1) && (pr <= n);
-    VecN<T, VW> Lv{};
-    const long long ro = off + (long long)pr * pitch;
-    if (in && live) Lv = ldv<T, VW>(sl + ro + c0);
+  auto take_l = [&](int q, RowT<T, VW>& L) {
+    const int so = q & (kAdjSlots - 1);
+    const VecN<T, VW> Lv = chunk(lr, so * kAdjXC + 1 + lane);
 #pragma unroll
     for (int e = 0; e < VW; ++e) L.y[e] = Lv.v[e];
-    T le = 0, re = 0;
-    if (in) {
-      if (lane == 0 && c0 > 0) le = sl[ro + c0 - 1];
-      if (lane == 31 && c0 + VW < pitch) re = sl[ro + c0 + VW];
-    }
+    const T le = lane == 0 ? chunk(lr, so * kAdjXC).v[VW - 1] : T(0);
+    const T re = lane == 31 ? chunk(lr, so * kAdjXC + 33).v[0] : T(0);
     row_neighbours<T, VW>(L, lane, le, re);
   };
 
+  for (int q = r0 - 1; q <= r0 + kAdjPF; ++q) issue(q);
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kAdjPF) : "memory");
   double s_w = 0.0, s_a = 0.0, s_at = 0.0;
   RowT<T, VW> YU, YC, YD, LU, LC, LD;
   T xC[VW], xpC[VW], xD[VW], xpD[VW], t0[VW], t1[VW];
-  load_y(r0 - 1, YU, t0, t1);
-  load_y(r0, YC, xC, xpC);
-  load_l(r0 - 1, LU);
-  load_l(r0, LC);
+  take_y(r0 - 1, YU, t0, t1);
+  take_y(r0, YC, xC, xpC);
+  take_l(r0 - 1, LU);
+  take_l(r0, LC);
   for (int r = r0; r <= r1; ++r) {
-    load_y(r + 1, YD, xD, xpD);
-    load_l(r + 1, LD);
-    const long long ro = off + (long long)r * pitch + c0;
-    VecN<T, VW> Bv{}, Cv{}, Lm{};
-    if (live) {
-      Bv = ldv<T, VW>(b + ro);
-      if (MOM && carry) Cv = ldv<T, VW>(carry + ro);
-      if (PM == 2) Lm = ldv<T, VW>(lam + ro);
-    }
+    issue(r + 1 + kAdjPF);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kAdjPF) : "memory");
+    take_y(r + 1, YD, xD, xpD);
+    take_l(r + 1, LD);
+    const int so = (r + 1) & (kAdjSlots - 1);
+    const VecN<T, VW> Bv = chunk(br, so * kAdjBC + lane);
+    VecN<T, VW> Cv{}, Lm{};
+    if (has_carry) Cv = chunk(cr, so * kAdjBC + lane);
+    if (PM == 2) Lm = chunk(mr, so * kAdjBC + lane);
     T Ay[VW], Al[VW];
     apply_q1<T, VW, T>(YU, YC, YD, sc, sax, say, sd1, sd2, Ay);
     apply_q1<T, VW, T>(LU, LC, LD, sc, sax, say, sd1, sd2, Al);
@@ -163,6 +218,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       }
     }
     if (live) {
+      const long long ro = off + (long long)r * pitch + c0;
       stv<T, VW>(lam_out + ro, Lo);
       if (MOM && !final_step) stv<T, VW>(carry_out + ro, Co);
     }
@@ -176,6 +232,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       xpC[e] = xpD[e];
     }
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   s_w = warp_sum(s_w);
   s_a = warp_sum(s_a);
   s_at = warp_sum(s_at);
@@ -187,6 +244,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     d.v[3] = 0.0;
     partials[wt] = d;
   }
+}
+
+// The adjoint kernels' rings exceed the default 48 KB of dynamic shared memory.
+template <typename T>
+static cudaError_t adjoint_attributes_t() {
+  const int bytes = (int)(sizeof(uint4) * kWarpsPerBlock * adj_ring_chunks());
+  cudaError_t e = cudaSuccess;
+#define RICHM_ADJ_ATTR(M, P) \
+  if (e == cudaSuccess)      \
+    e = cudaFuncSetAttribute(adjoint_kernel<T, M, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  RICHM_ADJ_ATTR(true, 0)
+  RICHM_ADJ_ATTR(true, 1)
+  RICHM_ADJ_ATTR(true, 2)
+  RICHM_ADJ_ATTR(false, 0)
+  RICHM_ADJ_ATTR(false, 1)
+  RICHM_ADJ_ATTR(false, 2)
+#undef RICHM_ADJ_ATTR
+  return e;
+}
+
+cudaError_t init_adjoint_attributes() {
+  cudaError_t e = adjoint_attributes_t<float>();
+  if (e == cudaSuccess) e = adjoint_attributes_t<double>();
+  return e;
 }
 
 // acc[b][kidx][0..2] += per-instance sums of the tile partials (fixed order).
@@ -235,9 +316,10 @@ static richm_status launch_adjoint(richm_operator* op, const T* lam, const T* ub
   const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int thr = kWarpsPerBlock * 32;
   const bool mom = a != nullptr;
-#define RICHM_ADJ(M, P)                                                                                       \
-  adjoint_kernel<T, M, P><<<blocks, thr, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, lam, ub, carry, x, xp, \
-                                                 b, lam_out, carry_out, w, a, at, m, kidx, final_step, partials)
+  const size_t smem = sizeof(uint4) * kWarpsPerBlock * adj_ring_chunks();
+#define RICHM_ADJ(M, P)                                                                                         \
+  adjoint_kernel<T, M, P><<<blocks, thr, smem, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, lam, ub, carry, x, xp, \
+                                                    b, lam_out, carry_out, w, a, at, m, kidx, final_step, partials)
   if (mom) {
     if (precond == 2) RICHM_ADJ(true, 2);
     else if (precond == 1) RICHM_ADJ(true, 1);

@@ -11,9 +11,10 @@ constexpr int kFuseRows = 256;     // default output rows of a fused-sweep warp 
 
 // Kernel attributes that must be set before the first launch (called once per
 // process and device by richm_operator_create).
-cudaError_t init_sweep_attributes();  // also the fused kernels' (init_fused_attributes)
+cudaError_t init_sweep_attributes();  // also the fused, SSOR and adjoint kernels
 cudaError_t init_fused_attributes();
 cudaError_t init_ssor_attributes();
+cudaError_t init_adjoint_attributes();
 
 // One forward sweep (see sweep.cu). `a == nullptr`: no momentum (xp unused);
 // `at == nullptr`: at = a. `active`: per-instance flags or nullptr (all active).

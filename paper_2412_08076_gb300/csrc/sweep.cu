@@ -232,6 +232,7 @@ cudaError_t init_sweep_attributes() {
   if (e == cudaSuccess) e = sweep1_attributes<cplx<double>>();
   if (e == cudaSuccess) e = init_fused_attributes();
   if (e == cudaSuccess) e = init_ssor_attributes();
+  if (e == cudaSuccess) e = init_adjoint_attributes();
   return e;
 }
 
