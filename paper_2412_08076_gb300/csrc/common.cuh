@@ -22,6 +22,10 @@
 
 namespace richm {
 
+constexpr int kRows = 16;          // rows streamed by one warp tile of the one-sweep, residual and adjoint kernels
+constexpr int kWarpsPerBlock = 8;  // warp tiles per thread block of those kernels
+constexpr int kFuseRows = 256;     // default output rows of a fused-sweep warp tile
+
 // --------------------------------------------------------------- errors
 
 richm_status set_error(richm_status s, const char* fmt, ...);

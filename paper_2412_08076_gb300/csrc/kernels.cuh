@@ -5,10 +5,6 @@
 
 namespace richm {
 
-constexpr int kRows = 16;          // rows streamed by one warp tile
-constexpr int kWarpsPerBlock = 8;  // warp tiles per thread block
-constexpr int kFuseRows = 256;     // default output rows of a fused-sweep warp tile
-
 // Kernel attributes that must be set before the first launch (called once per
 // process and device by richm_operator_create).
 cudaError_t init_sweep_attributes();  // also the fused, SSOR and adjoint kernels

@@ -17,15 +17,13 @@ from . import meta as meta_mod
 from . import richm
 
 
+# the sources a kernel is compiled from (its translation unit and the shared device
+# header; kernels.cuh only declares host launchers)
 TRAFFIC_SOURCES = {
-    "sweep1": ["paper_2412_08076_gb300/csrc/sweep.cu", "paper_2412_08076_gb300/csrc/common.cuh",
-               "paper_2412_08076_gb300/csrc/kernels.cuh"],
-    "sweepT4": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh",
-                "paper_2412_08076_gb300/csrc/kernels.cuh"],
-    "sweepT8": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh",
-                "paper_2412_08076_gb300/csrc/kernels.cuh"],
-    "refine": ["paper_2412_08076_gb300/csrc/solve.cu", "paper_2412_08076_gb300/csrc/common.cuh",
-               "paper_2412_08076_gb300/csrc/kernels.cuh"],
+    "sweep1": ["paper_2412_08076_gb300/csrc/sweep.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
+    "sweepT4": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
+    "sweepT8": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
+    "refine": ["paper_2412_08076_gb300/csrc/solve.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
 }
 
 
