@@ -11,13 +11,13 @@
 // + d1 z(i-1, j-1) + d2 z(i-1, j+1)]: the previous row enters as known values, and along
 // the row the recurrence z_j = q_j - kappa z_{j-1} (kappa = w ax / c, |kappa| < 1 for the
 // Q1 stencil and 0 < w < 2) is a first-order linear recurrence with a constant
-// coefficient. A warp owns one instance and walks its rows in order; within a row each
-// lane takes VW consecutive columns, composes the affine maps of its columns, and a
-// log-depth scan of those maps across the lanes (shuffles) gives every lane its incoming
-// value, after which it replays its columns. Rows wider than 32 VW columns are taken in
-// chunks, carrying the last value. The backward solve is the mirror image (rows and
-// columns reversed, upper neighbours). The intermediate z lives in a padded buffer;
-// the backward pass overwrites it with s row by row (the row above reads s below).
+// coefficient. The instance's rows are walked in order; within a row each lane takes VW
+// consecutive columns, composes the affine maps of its columns, and a log-depth scan of
+// those maps across the lanes (shuffles) gives every lane its incoming value, after which
+// it replays its columns. Rows of at most 32 VW columns run on two warps per instance
+// (the row pipelines below); wider rows are taken in chunks by one warp, carrying the
+// last value. The backward solve is the mirror image (rows and columns reversed, upper
+// neighbours). The intermediate z lives in a padded buffer.
 //
 // With x == nullptr the same kernels apply the preconditioner alone, out = B^{-1} b
 // (y = 0, no momentum, w = 1): the adjoint of a preconditioned sweep needs B^{-1} of
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(kSsorWarps * 32) ssor_backward_kernel(const Ss
 // ---------------------------------------------------------------- single-chunk rows
 // Rows of at most 32 VW columns (FP32: n <= 511, FP64: n <= 255) are one chunk, so the
 // whole previous row of z (forward) or s (backward) and the three-row window of the
-// look-ahead iterate stay in registers, and the next row's inputs are loaded one row
-// ahead. With a single chunk the incoming value of the row is 0, so the scan needs only
+// look-ahead iterate stay in registers, and the inputs arrive through cp.async rings
+// twelve rows ahead. With a single chunk the incoming value of the row is 0, so the scan needs only
 // the P parts: the multiplier of a lane's map is (-kappa)^VW (lanes holding columns
 // >= n have multiplier 0, but they only ever follow the interior lanes in the forward
 // direction, and in the backward direction the lanes after them contribute P = 0).
@@ -321,15 +321,6 @@ __device__ __forceinline__ void edges_zero(RowVW<E, VW>& Y, int lane) {
   if (lane == 31) Y.r = E(0);  // beyond the pitch
 }
 
-template <typename E, int VW>
-__device__ __forceinline__ void ld_row_or_zero(const E* base, int row, int n, int pitch, int c0, bool live, E* v) {
-  if (live && row >= 1 && row <= n) {
-    ld16<E, VW>(base + (long long)row * pitch + c0, v);
-  } else {
-#pragma unroll
-    for (int e = 0; e < VW; ++e) v[e] = E(0);
-  }
-}
 
 namespace {
 
