@@ -280,16 +280,45 @@ def secondary_workloads(dev):
     ws = op.workspace(op._ws("richm_sweeps_workspace", richm.F64))
     rw = op.workspace(op._ws("richm_residual_workspace"))
     hist = torch.empty(400, dtype=torch.float64, device=dev)
+
+    def run400():
+        for k in range(400):
+            op.apply_sweeps(richm.F64, X, None, B, w, K=1, m=8, k_start=k, work=ws)
+            hist[k:k + 1] = op.residual_norm(richm.F64, X, B, work=rw)[2]
+
+    run400()  # warm-up: tile maps and allocations happen outside the timed region
+    torch.cuda.synchronize()
+    X.zero_()
     e0, e1 = ev(), ev()
     e0.record()
-    for k in range(400):
-        op.apply_sweeps(richm.F64, X, None, B, w, K=1, m=8, k_start=k, work=ws)
-        hist[k:k + 1] = op.residual_norm(richm.F64, X, B, work=rw)[2]
+    run400()
     e1.record()
     torch.cuda.synchronize()
-    out["fp64_63sq_richardson8"] = {"sweeps": 400, "us_per_sweep_with_residual": 1e3 * e0.elapsed_time(e1) / 400,
+    eager_us = 1e3 * e0.elapsed_time(e1) / 400
+    # the same 800 launches captured once as a CUDA graph (the launch latency of a
+    # 3969-unknown problem otherwise dominates)
+    graph_us = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        X.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            run400()
+        X.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_us = 1e3 * e0.elapsed_time(e1) / 400
+    except Exception as exc:  # capture is an optimisation of this measurement only
+        print(f"note: CUDA graph capture of the 63^2 loop failed ({exc})", file=sys.stderr)
+    out["fp64_63sq_richardson8"] = {"sweeps": 400, "us_per_sweep_with_residual": eager_us,
+                                    "us_per_sweep_with_residual_graph": graph_us,
                                     "rel_res_after_400": float(hist[-1].item()),
-                                    "note": "latency-bound (3969 unknowns); parity vs oracle in tests"}
+                                    "note": "latency-bound (3969 unknowns): one sweep and one residual norm "
+                                            "per step; parity vs oracle in tests"}
     op.close()
 
     # training step: meta forward, 64 checkpointed NAG sweeps on 64 x 255^2, loss,
