@@ -356,7 +356,7 @@ def secondary_workloads(dev):
     rel = op.refine(X64, B64, None, None, richm.F32, R, work=rw)
 
     def cycle():
-        op.apply_sweeps(richm.F32, E, None, R, w8, K=8, m=8, work=ws)
+        op.apply_sweeps(richm.F32, E, None, R, w8, K=8, m=8, fuse=8, work=ws)  # one 8-sweep pass
         op.fourier_correction(E, R, S, work=fw)
         return op.refine(X64, B64, E, None, richm.F32, R, work=rw)
 
