@@ -613,7 +613,7 @@ def run_ours(args):
                 "launch_ms": one_ms, "sweeps_per_launch": 1, "peak_source": f"{peak_src} hbm_gbs (of measured)"}
     else:
         fused_ms = launch_ms(fuse)
-        kname = (f"sweepT8s_kernel<NAG> (8 FP32 NAG sweeps per launch, temporal blocking, two warps per tile)"
+        kname = (f"sweepT8_kernel<NAG> (8 FP32 NAG sweeps per launch, temporal blocking, two warps per tile, skewed levels)"
                  if fuse == 8 else f"sweepT_kernel<{fuse},NAG> ({fuse} FP32 NAG sweeps per launch, temporal blocking)")
         # instruction-issue bound: algorithmic FP32 work per unknown and sweep of the NAG
         # 9-point update is 19 flops (y: 3, A y: 13, b - A y: 1, y + w r: 2); the peak

@@ -417,9 +417,8 @@ static richm_status cycle_t(richm_solver* S, long long k0, long long cycle) {
 // Fused tile height (the tuned height halved down to 16 rows) for the instances
 // still iterating, from a wave model of the
 // fused pass: its tiles form blocks (4 one-warp tiles at 4 sweeps per pass, 2 two-warp
-// tiles at 8), which run in waves of 152 SMs x K resident blocks (K = 4, set by the
-// registers); a
-// wave takes rows + 2 TL row steps, and a row step takes 1 + 0.65 (k - 1) times its
+// tiles at 8), which run in waves of 152 SMs x K resident blocks (K = 4 and 3, set by
+// the registers); a wave takes rows + 2 TL row steps, and a row step takes 1 + 0.65 (k - 1) times its
 // single-block time when k blocks share an SM (fitted to GB300 timings of both pass
 // lengths over 1..77 instances of 511^2 and the 256-instance mix, where it picks
 // within 1 % of the best height on average). Short tiles spread few instances over
@@ -428,8 +427,8 @@ static richm_status cycle_t(richm_solver* S, long long k0, long long cycle) {
 static double fused_pass_cost(const richm_solver* S, int rows) {
   const richm_operator* op = S->op;
   const int TL = S->o.fuse;
-  const int K = 4;
-  const int per_block = TL == 8 ? 2 : 4;
+  const int K = TL == 8 ? 3 : 4;           // resident blocks per SM
+  const int per_block = TL == 8 ? 2 : 4;  // tiles per block
   long long warps = 0;
   int nmax = 0;
   for (int b = 0; b < op->batch; ++b) {

@@ -90,11 +90,12 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 
 constexpr int kPrefetch = 2;  // row steps between issuing a row's copies and using it
 
-template <typename ST, int TL>
+// XB: extra b slots for a pipeline that reads b rows further back (the skewed kernel).
+template <typename ST, int TL, int XB = 0>
 struct FusedRings {
   // one spare slot in each ring: a slot is re-targeted two row steps after its last read
-  static constexpr int NS = kPrefetch + 2;       // x_k and x_{k-1} row slots
-  static constexpr int NB = TL + kPrefetch + 2;  // b row slots (kept until level TL), each held twice
+  static constexpr int NS = kPrefetch + 2;            // x_k and x_{k-1} row slots
+  static constexpr int NB = TL + kPrefetch + 2 + XB;  // b row slots (kept until level TL), each held twice
   static constexpr int XROW = 128 * (int)sizeof(ST);  // bytes of one state row (128 columns)
   static constexpr int BOFF = 2 * NS * XROW;          // start of the b ring
   static constexpr int BYTES = BOFF + 2 * NB * 128 * 4;
@@ -197,9 +198,9 @@ __device__ __forceinline__ int ring_slot(int r, int nslots) { return (r + 64 * n
 
 // Issue the copies of input row r (x_k, x_{k-1}, b) into the rings (zero-filled
 // outside rows 1..n, beyond the tile's last needed row, or beyond the row pitch).
-template <typename ST, int TL, bool MOM>
+template <typename ST, int TL, bool MOM, int XB = 0>
 __device__ __forceinline__ void issue_row(const FusedCtx<ST>& c, int r) {
-  using R = FusedRings<ST, TL>;
+  using R = FusedRings<ST, TL, XB>;
   const bool valid = ((unsigned)(r - c.rlo) <= (unsigned)(c.vhi - c.rlo)) && c.live;
   const long long ro = (long long)(valid ? r : 0) * c.pitch + (c.live ? c.c0 : 0);
   const int xs = ring_slot(r, R::NS);
@@ -399,11 +400,11 @@ __device__ __forceinline__ void zero_state(PairState<TL>& st) {
 }
 
 // b rows above the tile's first input row are never loaded: zero their slots
-template <typename ST, int TL>
+template <typename ST, int TL, int XB = 0>
 __device__ __forceinline__ void zero_b_ring(const FusedCtx<ST>& c) {
-  for (int q = 0; q < 2 * FusedRings<ST, TL>::NB; ++q)
-    *reinterpret_cast<float4*>(c.ring + FusedRings<ST, TL>::BOFF + q * 512 + c.lane * 16) =
-        make_float4(0.f, 0.f, 0.f, 0.f);
+  using R = FusedRings<ST, TL, XB>;
+  for (int q = 0; q < 2 * R::NB; ++q)
+    *reinterpret_cast<float4*>(c.ring + R::BOFF + q * 512 + c.lane * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 template <typename ST, int TL, bool MOM, bool PRE, bool NAGF, bool ABS>
@@ -442,52 +443,162 @@ __global__ void __launch_bounds__(kFuseWarps * 32, TL == 4 ? 4 : 2) sweepT_kerne
 
 // ---------------------------------------------------------------- 8 levels on two warps
 // The 8-level pipeline of a tile split over two warps of one block: the lower warp runs
-// levels 1-4 (and all loads), the upper warp levels 5-8 (and the stores) one row step
-// behind. Each step the lower warp hands over the row of x_{k+4} it produced and the
-// x_{k+3} row of its previous step (the upper warp's first look-ahead) through a
-// three-slot exchange in shared memory; the upper warp reads the b rows from the lower
-// warp's ring. A named barrier of the two warps per row step orders the exchange and
-// the ring reuse (a slot is rewritten three steps after it was read). Each warp holds
-// the state of four levels, so four blocks (16 warps) fit an SM instead of eight warps
-// of the one-warp kernel, while HBM traffic stays that of eight sweeps per pass. Both
-// warps of a tile leave together or not at all, and run the same number of barriers.
+// levels 1-4 (and all loads), the upper warp levels 5-8 (and the stores). Each warp
+// holds the state of four levels, so three blocks of two tiles (12 warps) fit an SM
+// where the one-warp kernel fits two blocks of four warps, while HBM traffic stays that
+// of eight sweeps per pass.
+//
+// The levels are skewed by two rows: level s at row step rr inserts the row that level
+// s - 1 produced at the previous step (row rr - 2s + 1) and updates row rr - 2s. The
+// levels of one step then depend only on the previous step, so a warp's four levels are
+// four independent chains (processed top level first, so that each level takes its
+// pending row before the level below replaces it). A level hands the next one
+// (x_s, x_{s-1}) of the row it updated; the last level stores both. The lower warp
+// passes level 4's pair to the upper warp through a two-slot exchange in shared memory,
+// which level 5 inserts at the next step, and the upper warp reads the b rows from the
+// lower warp's ring (kept for the 16-row skew). A named barrier of the two warps per
+// row step orders the exchange and the ring reuse. Both warps of a tile leave together
+// or not at all, and pass the same barriers.
 constexpr int kSplitTiles = 2;  // tiles per block, two warps each
-constexpr int kXchBytes = 3 * 2 * 512;  // three slots of two 128-column FP32 rows
-
-template <typename ST>
-__host__ __device__ constexpr int split_tile_bytes() { return FusedRings<ST, 8>::BYTES + kXchBytes; }
 
 __device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
 
-template <typename ST, bool MOM, bool NAGF, bool ABS, int PH, int PW>
-__device__ __forceinline__ void lower_step(int rr, const FusedCtx<ST>& c, PairState<8>& st, unsigned char* xslot,
-                                           const float2* wl, const float2* al, const float2* atl) {
-  float2 x0[2], xm[2];
-  step_inputs<ST, 8, MOM, ABS>(rr, c, x0, xm);
-  float2 newx[9][2];
-  // hand over x_{k+3} of the previous step before this step overwrites it
-  const float2 p3[2] = {st.prevx[1 - PW][3][0], st.prevx[1 - PW][3][1]};
-  step_levels<ST, 8, 1, 4, 3, MOM, NAGF, PH, PW>(rr, c, st, x0, xm, wl, al, atl, newx);
-  *reinterpret_cast<float4*>(xslot + c.lane * 16) = make_float4(newx[4][0].x, newx[4][0].y, newx[4][1].x,
-                                                                 newx[4][1].y);
-  *reinterpret_cast<float4*>(xslot + 512 + c.lane * 16) = make_float4(p3[0].x, p3[0].y, p3[1].x, p3[1].y);
+constexpr int kSkewXB = 8;             // b rows back to rr - 16
+constexpr int kSkewXch = 2 * 2 * 512;  // two slots of (x_4, x_3) rows
+
+template <typename ST>
+__host__ __device__ constexpr int skew_tile_bytes() { return FusedRings<ST, 8, kSkewXB>::BYTES + kSkewXch; }
+
+// Four levels of one warp. Level j: window rows of y_{s-1} (slots rotate by phase),
+// x_{s-1} and x_{s-1} - x_{s-2} of the centre row; P[j]: the (x_{s-1}, x_{s-2}) row that
+// level j inserts at the next step (j >= 1; level 0's comes from the loads or the exchange).
+struct SkewState {
+  float2 Y[4][3][2];
+  float2 XC[4][2];
+  float2 VC[4][2];
+  float2 P[4][2][2];
+};
+
+// Level s of step rr (state slot j): insert the row (px, pxo), update the centre row
+// rr - 2s; the new (x_s, x_{s-1}) of that row go to xo, xl.
+template <typename ST, bool MOM, bool NAGF, int PH>
+__device__ __forceinline__ void skew_level(int rr, int s, int j, const FusedCtx<ST>& c, SkewState& st,
+                                           const float2* px, const float2* pxo, const unsigned char* bstep,
+                                           float2 w2, float2 a2, float2 at2, float2* xo, float2* xl) {
+  constexpr int SD = PH, SU = (PH + 1) % 3, SC = (PH + 2) % 3;
+  float2 vn[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    vn[p] = MOM ? sub2(px[p], pxo[p]) : pair(0.f);
+    st.Y[j][SD][p] = MOM ? __ffma2_rn(at2, vn[p], px[p]) : px[p];
+  }
+  const int row = rr - 2 * s;
+  const float4 B4 = *reinterpret_cast<const float4*>(bstep - 2 * s * 512);
+  const float2 Bv[2] = {make_float2(B4.x, B4.y), make_float2(B4.z, B4.w)};
+  const float2 ws = ((unsigned)(row - c.rlo) < (unsigned)c.n) ? w2 : pair(0.f);
+  float2 ry[2];
+  resid_pairs<ST>(st.Y[j][SU], st.Y[j][SC], st.Y[j][SD], Bv, c, ry);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    if (!MOM || NAGF) xo[p] = __ffma2_rn(ws, ry[p], st.Y[j][SC][p]);  // y = x + a v is the window centre
+    else xo[p] = __ffma2_rn(ws, ry[p], __ffma2_rn(a2, st.VC[j][p], st.XC[j][p]));
+    xl[p] = st.XC[j][p];
+    st.XC[j][p] = px[p];
+    if (MOM && !NAGF) st.VC[j][p] = vn[p];
+  }
 }
 
-template <typename ST, bool MOM, bool NAGF, int PH, int PW>
-__device__ __forceinline__ void upper_step(int rr, const FusedCtx<ST>& c, PairState<8>& st,
-                                           const unsigned char* xslot, const float2* wl, const float2* al,
-                                           const float2* atl) {
-  const float4 a4 = *reinterpret_cast<const float4*>(xslot + c.lane * 16);
-  const float4 b4 = *reinterpret_cast<const float4*>(xslot + 512 + c.lane * 16);
-  const float2 in1[2] = {make_float2(a4.x, a4.y), make_float2(a4.z, a4.w)};
-  const float2 in2[2] = {make_float2(b4.x, b4.y), make_float2(b4.z, b4.w)};
-  float2 newx[9][2];
-  step_levels<ST, 8, 5, 8, 6, MOM, NAGF, PH, PW>(rr, c, st, in1, in2, wl, al, atl, newx);
-  step_store<ST, 8, MOM>(rr, c, newx[8], newx[7]);
+template <typename ST, bool MOM, bool NAGF, bool ABS, int PH>
+__device__ __forceinline__ void skew_lower_step(int rr, int it, const FusedCtx<ST>& c, SkewState& st,
+                                                unsigned char* xch, const float2* wl, const float2* al,
+                                                const float2* atl) {
+  using R = FusedRings<ST, 8, kSkewXB>;
+  issue_row<ST, 8, MOM, kSkewXB>(c, rr + kPrefetch);
+  cp_async_wait<kPrefetch + 1>();  // the copies of row rr - 1 have landed
+  const unsigned char* bstep = c.ring + R::BOFF + (ring_slot(rr, R::NB) + R::NB) * 512 + c.lane * 16;
+  float2 xo[2], xl[2];
+  // level 4: its row goes to the upper warp
+  skew_level<ST, MOM, NAGF, PH>(rr, 4, 3, c, st, st.P[3][0], st.P[3][1], bstep, wl[4], al[4], atl[4], xo, xl);
+  {
+    unsigned char* xs = xch + (it & 1) * 1024 + c.lane * 16;
+    *reinterpret_cast<float4*>(xs) = make_float4(xo[0].x, xo[0].y, xo[1].x, xo[1].y);
+    *reinterpret_cast<float4*>(xs + 512) = make_float4(xl[0].x, xl[0].y, xl[1].x, xl[1].y);
+  }
+  // levels 3, 2
+#pragma unroll
+  for (int j = 2; j >= 1; --j) {
+    skew_level<ST, MOM, NAGF, PH>(rr, 1 + j, j, c, st, st.P[j][0], st.P[j][1], bstep, wl[1 + j], al[1 + j],
+                                  atl[1 + j], st.P[j + 1][0], st.P[j + 1][1]);
+  }
+  // level 1 inserts the loaded row rr - 1
+  float2 x0[2], xm[2];
+  {
+    const int xs = ring_slot(rr - 1, R::NS);
+    float v[4];
+    st4_to_float(reinterpret_cast<const ST*>(c.ring + xs * R::XROW) + c.lane * 4, v);
+    x0[0] = make_float2(v[0], v[1]);
+    x0[1] = make_float2(v[2], v[3]);
+    if (MOM) {
+      st4_to_float(reinterpret_cast<const ST*>(c.ring + (R::NS + xs) * R::XROW) + c.lane * 4, v);
+      xm[0] = make_float2(v[0], v[1]);
+      xm[1] = make_float2(v[2], v[3]);
+    } else {
+      xm[0] = xm[1] = pair(0.f);
+    }
+    if constexpr (ABS) {
+      // the stored pair (e, e_prev) stands for (0, e_prev - e)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        xm[p] = MOM ? sub2(xm[p], x0[p]) : pair(0.f);
+        x0[p] = pair(0.f);
+      }
+    }
+  }
+  skew_level<ST, MOM, NAGF, PH>(rr, 1, 0, c, st, x0, xm, bstep, wl[1], al[1], atl[1], st.P[1][0], st.P[1][1]);
+}
+
+template <typename ST, bool MOM, bool NAGF, int PH>
+__device__ __forceinline__ void skew_upper_step(int rr, int it, const FusedCtx<ST>& c, SkewState& st,
+                                                const unsigned char* xch, const float2* wl, const float2* al,
+                                                const float2* atl) {
+  using R = FusedRings<ST, 8, kSkewXB>;
+  const unsigned char* bstep = c.ring + R::BOFF + (ring_slot(rr, R::NB) + R::NB) * 512 + c.lane * 16;
+  float2 xo[2], xl[2];
+  // level 8: store row rr - 16 of x_{k+8} and x_{k+7}
+  skew_level<ST, MOM, NAGF, PH>(rr, 8, 3, c, st, st.P[3][0], st.P[3][1], bstep, wl[8], al[8], atl[8], xo, xl);
+  if (c.store_cols) {
+    const int ra = rr - 16;
+    if (ra >= c.r0 && ra <= c.shi) {
+      const float v8[4] = {xo[0].x, xo[0].y, xo[1].x, xo[1].y};
+      float_to_st4(c.ox + (long long)ra * c.pitch + c.c0, v8);
+      if (MOM) {
+        const float v7[4] = {xl[0].x, xl[0].y, xl[1].x, xl[1].y};
+        float_to_st4(c.oxp + (long long)ra * c.pitch + c.c0, v7);
+      }
+    }
+  }
+  // levels 7, 6
+#pragma unroll
+  for (int j = 2; j >= 1; --j) {
+    skew_level<ST, MOM, NAGF, PH>(rr, 5 + j, j, c, st, st.P[j][0], st.P[j][1], bstep, wl[5 + j], al[5 + j],
+                                  atl[5 + j], st.P[j + 1][0], st.P[j + 1][1]);
+  }
+  // level 5 inserts the row the lower warp's level 4 produced at the previous step
+  float2 xi[2], xim[2];
+  {
+    const unsigned char* xs = xch + ((it - 1) & 1) * 1024 + c.lane * 16;
+    const float4 x4 = *reinterpret_cast<const float4*>(xs);
+    const float4 x3 = *reinterpret_cast<const float4*>(xs + 512);
+    xi[0] = make_float2(x4.x, x4.y);
+    xi[1] = make_float2(x4.z, x4.w);
+    xim[0] = make_float2(x3.x, x3.y);
+    xim[1] = make_float2(x3.z, x3.w);
+  }
+  skew_level<ST, MOM, NAGF, PH>(rr, 5, 0, c, st, xi, xim, bstep, wl[5], al[5], atl[5], st.P[1][0], st.P[1][1]);
 }
 
 template <typename ST, bool MOM, bool PRE, bool NAGF, bool ABS>
-__global__ void __launch_bounds__(kSplitTiles * 64, 4) sweepT8s_kernel(const SweepTArgs A) {
+__global__ void __launch_bounds__(kSplitTiles * 64, 3) sweepT8_kernel(const SweepTArgs A) {
   constexpr int TL = 8;
   extern __shared__ __align__(16) unsigned char fused_smem[];
   const int lane = threadIdx.x & 31;
@@ -500,54 +611,58 @@ __global__ void __launch_bounds__(kSplitTiles * 64, 4) sweepT8s_kernel(const Swe
   if (A.active && A.active[t.inst] == 0) return;  // both warps of the tile
   float2 wl[TL + 1], al[TL + 1], atl[TL + 1];
   FusedCtx<ST> c;
-  const int rend = fused_setup<ST, TL, MOM, PRE>(A, t, lane, c, wl, al, atl);
-  c.ring = fused_smem + pid * split_tile_bytes<ST>();
-  unsigned char* xch = c.ring + FusedRings<ST, TL>::BYTES;
+  const int rend = fused_setup<ST, TL, MOM, PRE>(A, t, lane, c, wl, al, atl) + TL;  // TL more steps of skew
+  c.ring = fused_smem + pid * skew_tile_bytes<ST>();
+  unsigned char* xch = c.ring + FusedRings<ST, TL, kSkewXB>::BYTES;
   const int bar = 1 + pid;
-  const int rstart = c.r0 - TL;
+  const int rstart = c.r0 - TL + 1;  // level 1's window starts with row r0 - 8
+  SkewState st;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      st.Y[j][0][p] = st.Y[j][1][p] = st.Y[j][2][p] = pair(0.f);
+      st.XC[j][p] = st.VC[j][p] = st.P[j][0][p] = st.P[j][1][p] = pair(0.f);
+    }
   if (!upper) {
-    zero_b_ring<ST, TL>(c);
-    for (int q = 0; q < 6; ++q)
+    zero_b_ring<ST, TL, kSkewXB>(c);
+    for (int q = 0; q < 4; ++q)
       *reinterpret_cast<float4*>(xch + q * 512 + lane * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d <= kPrefetch; ++d) issue_row<ST, TL, MOM, kSkewXB>(c, rstart - 1 + d);
   }
   pair_sync(bar);
+  // Both warps pass the barriers of every step rstart .. rstart + nsteps - 1 (whole groups
+  // of three, the last steps only compute rows that are neither stored nor used). Level s
+  // is first needed at step r0 - 8 + 3s (its window fills two steps earlier) and last at
+  // r1 + 8 + s, so the lower warp has no work in the last four steps and the upper warp
+  // none in the first twelve (before r0 + 5); they only pass those barriers. Step q from
+  // rstart runs at window phase q mod 3 in both warps.
+  const int nsteps = 3 * ((rend - rstart + 3) / 3);
   if (!upper) {
-    PairState<TL> st;
-    zero_state<TL>(st);
-#pragma unroll
-    for (int d = 0; d < kPrefetch; ++d) issue_row<ST, TL, MOM>(c, rstart + d);
-    for (int rr = rstart; rr <= rend + 1; rr += 3) {
-      lower_step<ST, MOM, NAGF, ABS, 0, 0>(rr, c, st, xch, wl, al, atl);
+    const int nl = 3 * ((rend - 4 - rstart + 3) / 3);
+    int q = 0;
+    for (; q < nl; q += 3) {
+      skew_lower_step<ST, MOM, NAGF, ABS, 0>(rstart + q, q, c, st, xch, wl, al, atl);
       pair_sync(bar);
-      lower_step<ST, MOM, NAGF, ABS, 1, 1>(rr + 1, c, st, xch + 1024, wl, al, atl);
+      skew_lower_step<ST, MOM, NAGF, ABS, 1>(rstart + q + 1, q + 1, c, st, xch, wl, al, atl);
       pair_sync(bar);
-      lower_step<ST, MOM, NAGF, ABS, 2, 0>(rr + 2, c, st, xch + 2048, wl, al, atl);
+      skew_lower_step<ST, MOM, NAGF, ABS, 2>(rstart + q + 2, q + 2, c, st, xch, wl, al, atl);
       pair_sync(bar);
-      if (MOM) {
-#pragma unroll
-        for (int s = 0; s <= 3; ++s)
-#pragma unroll
-          for (int p = 0; p < 2; ++p) st.prevx[1][s][p] = st.prevx[0][s][p];
-      }
     }
+    for (; q < nsteps; ++q) pair_sync(bar);
     cp_async_wait<0>();
   } else {
-    PairState<TL> st;
-    zero_state<TL>(st);
-    // one row step behind: step rr - 1 + q reads the slot the lower warp wrote at q - 1
-    for (int rr = rstart; rr <= rend + 1; rr += 3) {
-      upper_step<ST, MOM, NAGF, 0, 0>(rr - 1, c, st, xch + 2048, wl, al, atl);
+    constexpr int kIdle = 12;  // r0 + 5 - rstart, a multiple of three
+    int q = 0;
+    for (; q < kIdle; ++q) pair_sync(bar);
+    for (; q < nsteps; q += 3) {
+      skew_upper_step<ST, MOM, NAGF, 0>(rstart + q, q, c, st, xch, wl, al, atl);
       pair_sync(bar);
-      upper_step<ST, MOM, NAGF, 1, 1>(rr, c, st, xch, wl, al, atl);
+      skew_upper_step<ST, MOM, NAGF, 1>(rstart + q + 1, q + 1, c, st, xch, wl, al, atl);
       pair_sync(bar);
-      upper_step<ST, MOM, NAGF, 2, 0>(rr + 1, c, st, xch + 1024, wl, al, atl);
+      skew_upper_step<ST, MOM, NAGF, 2>(rstart + q + 2, q + 2, c, st, xch, wl, al, atl);
       pair_sync(bar);
-      if (MOM) {
-#pragma unroll
-        for (int s = 4; s <= 6; ++s)
-#pragma unroll
-          for (int p = 0; p < 2; ++p) st.prevx[1][s][p] = st.prevx[0][s][p];
-      }
     }
   }
 }
@@ -742,26 +857,26 @@ __global__ void __launch_bounds__(kFuseWarps * 32, 3) sweepT_cx_kernel(const Swe
 }
 
 template <typename ST>
-static cudaError_t split_attributes() {
-  const int bytes = split_tile_bytes<ST>() * kSplitTiles;
+static cudaError_t skew_attributes() {
+  const int bytes = skew_tile_bytes<ST>() * kSplitTiles;
   cudaError_t e = cudaSuccess;
-#define RICHM_SPLIT_ATTR(MOM, PRE, NAGF, ABS)                                                                 \
+#define RICHM_SKEW_ATTR(MOM, PRE, NAGF, ABS)                                                                  \
   if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(sweepT8s_kernel<ST, MOM, PRE, NAGF, ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+    e = cudaFuncSetAttribute(sweepT8_kernel<ST, MOM, PRE, NAGF, ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              bytes);
-  RICHM_SPLIT_ATTR(true, true, true, false)
-  RICHM_SPLIT_ATTR(true, false, true, false)
-  RICHM_SPLIT_ATTR(true, true, false, false)
-  RICHM_SPLIT_ATTR(true, false, false, false)
-  RICHM_SPLIT_ATTR(false, true, false, false)
-  RICHM_SPLIT_ATTR(false, false, false, false)
-  RICHM_SPLIT_ATTR(true, true, true, true)
-  RICHM_SPLIT_ATTR(true, false, true, true)
-  RICHM_SPLIT_ATTR(true, true, false, true)
-  RICHM_SPLIT_ATTR(true, false, false, true)
-  RICHM_SPLIT_ATTR(false, true, false, true)
-  RICHM_SPLIT_ATTR(false, false, false, true)
-#undef RICHM_SPLIT_ATTR
+  RICHM_SKEW_ATTR(true, true, true, false)
+  RICHM_SKEW_ATTR(true, false, true, false)
+  RICHM_SKEW_ATTR(true, true, false, false)
+  RICHM_SKEW_ATTR(true, false, false, false)
+  RICHM_SKEW_ATTR(false, true, false, false)
+  RICHM_SKEW_ATTR(false, false, false, false)
+  RICHM_SKEW_ATTR(true, true, true, true)
+  RICHM_SKEW_ATTR(true, false, true, true)
+  RICHM_SKEW_ATTR(true, true, false, true)
+  RICHM_SKEW_ATTR(true, false, false, true)
+  RICHM_SKEW_ATTR(false, true, false, true)
+  RICHM_SKEW_ATTR(false, false, false, true)
+#undef RICHM_SKEW_ATTR
   return e;
 }
 
@@ -800,9 +915,9 @@ cudaError_t init_fused_attributes() {
     e = cudaFuncSetAttribute(sweepT_cx_kernel<4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              cx_bytes);
   if (e == cudaSuccess) e = fused_attributes_tl<float, 4>();
-  if (e == cudaSuccess) e = split_attributes<float>();
+  if (e == cudaSuccess) e = skew_attributes<float>();
   if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 4>();
-  if (e == cudaSuccess) e = split_attributes<__nv_bfloat16>();
+  if (e == cudaSuccess) e = skew_attributes<__nv_bfloat16>();
   return e;
 }
 
@@ -819,20 +934,20 @@ static richm_status launch_fused_t(richm_operator* op, int TL, const ST* x, cons
   if (TL == 8) {  // two warps per tile, two tiles per block
     const int blocks = (tm->ntiles + kSplitTiles - 1) / kSplitTiles;
     const int thr = kSplitTiles * 64;
-    const size_t smem = (size_t)split_tile_bytes<ST>() * kSplitTiles;
-#define RICHM_SPLIT(ABS)                                                                                   \
-  if (nag && precond) sweepT8s_kernel<ST, true, true, true, ABS><<<blocks, thr, smem, s>>>(A);             \
-  else if (nag) sweepT8s_kernel<ST, true, false, true, ABS><<<blocks, thr, smem, s>>>(A);                  \
-  else if (mom && precond) sweepT8s_kernel<ST, true, true, false, ABS><<<blocks, thr, smem, s>>>(A);       \
-  else if (mom) sweepT8s_kernel<ST, true, false, false, ABS><<<blocks, thr, smem, s>>>(A);                 \
-  else if (precond) sweepT8s_kernel<ST, false, true, false, ABS><<<blocks, thr, smem, s>>>(A);             \
-  else sweepT8s_kernel<ST, false, false, false, ABS><<<blocks, thr, smem, s>>>(A);
+    const size_t smem = (size_t)skew_tile_bytes<ST>() * kSplitTiles;
+#define RICHM_SKEW(ABS)                                                                                    \
+  if (nag && precond) sweepT8_kernel<ST, true, true, true, ABS><<<blocks, thr, smem, s>>>(A);             \
+  else if (nag) sweepT8_kernel<ST, true, false, true, ABS><<<blocks, thr, smem, s>>>(A);                  \
+  else if (mom && precond) sweepT8_kernel<ST, true, true, false, ABS><<<blocks, thr, smem, s>>>(A);       \
+  else if (mom) sweepT8_kernel<ST, true, false, false, ABS><<<blocks, thr, smem, s>>>(A);                 \
+  else if (precond) sweepT8_kernel<ST, false, true, false, ABS><<<blocks, thr, smem, s>>>(A);             \
+  else sweepT8_kernel<ST, false, false, false, ABS><<<blocks, thr, smem, s>>>(A);
     if (absorb) {
-      RICHM_SPLIT(true)
+      RICHM_SKEW(true)
     } else {
-      RICHM_SPLIT(false)
+      RICHM_SKEW(false)
     }
-#undef RICHM_SPLIT
+#undef RICHM_SKEW
     RICHM_LAUNCH_CHECK("fused sweep");
     return RICHM_OK;
   }
