@@ -4,7 +4,7 @@ import math
 import numpy as np
 
 import richm_synth as synth
-from oracle.fourier import fourier_correction, two_level_cycle
+from oracle.fourier import fourier_correction, fourier_correction_vjp, two_level_cycle
 from oracle.iterations import inner_steps, semi_iteration_weights
 from oracle.operators import assemble_q1, gershgorin_max
 from oracle.training import (adam_step, loss_and_grads, loss_only, meta_output_map,
@@ -118,6 +118,52 @@ def test_fft_matches_explicit_dft_and_zero_symbol():
         c = (F.conj() @ (S * (F @ r @ F.T)) @ F.conj().T) / (n * n)
         np.testing.assert_allclose(fourier_correction(A, f, u, S), u + c.real.ravel(), atol=1e-12)
         np.testing.assert_array_equal(fourier_correction(A, f, u, np.zeros((n, n))), u)
+
+
+def _vjp_case(n, seed):
+    A = assemble_q1(n, [1e-2, 1e-4][n % 2], 0.7 + 0.2 * n)
+    f = synth.rhs_uniform(9, seed, n).ravel()
+    u = 0.3 * synth.rhs_uniform(8, seed, n).ravel()
+    S = synth.fourier_symbol(n, seed=seed)
+    g = synth.rhs_uniform(7, seed, n).ravel()
+    return A, f, u, S, g
+
+
+def test_fourier_vjp_matches_central_differences():
+    # <g, u'> is linear in S and affine in u, so central differences are exact up to
+    # rounding: a dropped conjugate, a transposed spectrum or a lost 1/n^2 fails here
+    for n in (5, 6):
+        A, f, u, S, g = _vjp_case(n, 11 + n)
+        dS, du = fourier_correction_vjp(A, f, u, S, g)
+        L = lambda uu, SS: g @ fourier_correction(A, f, uu, SS)
+        h = 1e-6
+        for k1 in range(n):
+            for k2 in range(n):
+                E = np.zeros((n, n))
+                E[k1, k2] = 1.0
+                re = (L(u, S + h * E) - L(u, S - h * E)) / (2 * h)
+                im = (L(u, S + 1j * h * E) - L(u, S - 1j * h * E)) / (2 * h)
+                assert abs(re + 1j * im - dS[k1, k2]) < 1e-8
+        fdu = np.array([(L(u + h * e, S) - L(u - h * e, S)) / (2 * h) for e in np.eye(n * n)])
+        np.testing.assert_allclose(du, fdu, atol=1e-8)
+
+
+def test_fourier_vjp_matches_autograd_and_is_hermitian():
+    import torch
+    n = 8
+    A, f, u, S, g = _vjp_case(n, 4)
+    dS, du = fourier_correction_vjp(A, f, u, S, g)
+    At = torch.tensor(A.toarray())
+    St = torch.tensor(S, requires_grad=True)
+    ut = torch.tensor(u, requires_grad=True)
+    r = (torch.tensor(f) - At @ ut).reshape(n, n)
+    up = ut + torch.fft.ifft2(St * torch.fft.fft2(r)).real.reshape(-1)
+    (torch.tensor(g) * up).sum().backward()
+    np.testing.assert_allclose(dS, St.grad.numpy(), atol=1e-13)
+    np.testing.assert_allclose(du, ut.grad.numpy(), atol=1e-13)
+    # real r and g: dS(-k) = conj(dS(k))
+    idx = (-np.arange(n)) % n
+    np.testing.assert_allclose(dS[np.ix_(idx, idx)], np.conj(dS), atol=1e-13)
 
 
 def test_two_level_exact_inverse_symbol_on_periodic_free_case():
