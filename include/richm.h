@@ -341,7 +341,9 @@ richm_status richm_checkpoint_elems(const richm_operator* op, int K, int ckpt_ev
  * checkpoints; xK receives x_K (padded). Same coefficient conventions as
  * richm_apply_sweeps: precond 0 none, 1 Jacobi, 2 SSOR with relaxation factor relax
  * in (0, 2) (ignored otherwise). Requires K % ckpt_every == 0. work: at least
- * richm_adjoint_workspace bytes (four padded buffers suffice). */
+ * richm_adjoint_workspace bytes (four padded buffers suffice). Only the interior rows
+ * (and their padding columns) of the slots after slot 0 are written, and xK is a copy
+ * of the last slot: pass a zeroed store for xK to be a padded buffer with zero halos. */
 richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, const void* x0, const void* b,
                                         const void* w, const void* alpha, const void* alpha_t, int m, int K,
                                         int ckpt_every, int precond, double relax, void* ckpts, void* xK,
@@ -423,6 +425,25 @@ richm_status richm_fourier_workspace(const richm_operator* op, size_t* bytes);
  * [n][n] shared by the batch. x, b: padded. */
 richm_status richm_fourier_correction(richm_operator* op, richm_dtype dtype, void* x, const void* b,
                                       const void* symbol, void* work, size_t work_bytes, void* stream);
+
+/* Workspace bytes for richm_fourier_correction_vjp: two real n x n fields and two half
+ * spectra per instance, and the cuFFT work area. */
+richm_status richm_fourier_vjp_workspace(const richm_operator* op, size_t* bytes);
+
+/* Reverse mode of richm_fourier_correction, for learning the symbol of the FNS neural
+ * iteration (Sec. 3.1, eq. 20 with T = I; the Meta-Lambda step of Algorithm 2). With
+ * x, b the forward call's inputs (x before the correction), g = dL/dx' for its output
+ * x' = x + Re(IFFT2(S .* FFT2(b - A x))), R and G the spectra of b - A x and of g:
+ *   dsymbol[k] = sum over the batch of conj(R(k)) G(k) / n^2
+ *              = dL/dRe S(k) + i dL/dIm S(k)   (complex64 [n][n], written), or NULL;
+ *   g_x = g - A Re(IFFT2(conj(S) .* G)) = dL/dx   (padded, may alias g), or NULL.
+ * x and b may be NULL when dsymbol is. Same instance rules as the forward call; dtype
+ * RICHM_F32 (FP32 transforms and arithmetic). work: at least richm_fourier_vjp_workspace
+ * bytes. Errors: RICHM_ERR_ARG for a null g, symbol or work, or a symbol gradient
+ * without x and b; RICHM_ERR_NOMEM for a short workspace. */
+richm_status richm_fourier_correction_vjp(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
+                                          const void* g, const void* symbol, void* dsymbol, void* g_x, void* work,
+                                          size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------ misc */
 

@@ -108,6 +108,8 @@ _SIGS = {
     "richm_adam_step": (_I, [_P, _P, _P, _P, _I, _I, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
     "richm_fourier_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_fourier_correction": (_I, [_P, _I, _P, _P, _P, _P, _SZ, _P]),
+    "richm_fourier_vjp_workspace": (_I, [_P, C.POINTER(_SZ)]),
+    "richm_fourier_correction_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_selftest_conversions": (_I, [C.POINTER(C.c_longlong)]),
     "richm_last_error": (C.c_char_p, []),
     "richm_version": (C.c_char_p, []),
@@ -397,6 +399,15 @@ class Operator:
             work = self.workspace(self._ws("richm_fourier_workspace"))
         _check(load().richm_fourier_correction(self.handle, F32, _ptr(x), _ptr(b), _ptr(symbol), _ptr(work),
                                                work.numel(), _stream(stream)), "richm_fourier_correction")
+
+    def fourier_correction_vjp(self, x, b, g, symbol, dsymbol=None, g_x=None, work=None, stream=None):
+        """richm_fourier_correction_vjp: dsymbol = sum_b conj(R) G / n^2 (complex64 [n][n]),
+        g_x = g - A Re(IFFT2(conj(S) * G)) (padded F32; may be g itself)."""
+        if work is None:
+            work = self.workspace(self._ws("richm_fourier_vjp_workspace"))
+        _check(load().richm_fourier_correction_vjp(self.handle, F32, _ptr(x), _ptr(b), _ptr(g), _ptr(symbol),
+                                                   _ptr(dsymbol), _ptr(g_x), _ptr(work), work.numel(),
+                                                   _stream(stream)), "richm_fourier_correction_vjp")
 
 
 class Solver:
