@@ -114,8 +114,8 @@ def test_fp32_block_matches_oracle(variant):
 
 
 def test_fp32_block_mild_weights_within_1e5():
-    # weights with |1 - w lambda| <= 1 on the spectrum: the per-block bound is the
-    # spec 1e-5 relative
+    # weights with |1 - w lambda| <= 1 on the spectrum: no mode is amplified, so the
+    # FP32 block stays within 1e-5 of max|x| (the FP32 sweep tolerance)
     insts = _instances(sizes=[31, 63, 127, 130])
     op = make_op(insts)
     As = [assemble_q1(t.n, t.eps, t.theta) for t in insts]
