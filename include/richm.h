@@ -447,6 +447,15 @@ richm_status richm_fourier_correction_vjp(richm_operator* op, richm_dtype dtype,
 
 /* ------------------------------------------------------------------ misc */
 
+/* FMA throughput microbenchmark for the arithmetic ceilings of the roofline (no
+ * counterpart in the paper): kind 0 = FP32 FMA, 1 = packed FP32 pairs (two FMAs per
+ * instruction), 2 = FP64 FMA. Eight independent multiply-add chains in every thread of
+ * 8 blocks of 256 threads per SM, one warm-up and five timed launches on the legacy
+ * default stream of the current device (synchronous); *tflops = 2 flops per FMA over
+ * the timed launches. Allocates and frees a small output buffer. Errors: RICHM_ERR_ARG
+ * for another kind or a null output, RICHM_ERR_CUDA for a failed launch. */
+richm_status richm_fma_peak(int kind, double* tflops);
+
 /* Self-test of the library's own FP32 <-> FP64 conversions (no counterpart in the
  * paper: GB300 runs conversions to and from FP64 on its reduced-rate FP64 pipe, so
  * the refinement residual and update move the IEEE 754 fields with integer

@@ -111,6 +111,7 @@ _SIGS = {
     "richm_fourier_vjp_workspace": (_I, [_P, C.POINTER(_SZ)]),
     "richm_fourier_correction_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_selftest_conversions": (_I, [C.POINTER(C.c_longlong)]),
+    "richm_fma_peak": (_I, [_I, C.POINTER(_D)]),
     "richm_last_error": (C.c_char_p, []),
     "richm_version": (C.c_char_p, []),
 }
@@ -159,6 +160,16 @@ def _stream(stream=None) -> int | None:
 
 def version() -> str:
     return load().richm_version().decode()
+
+
+FMA_F32, FMA_F32X2, FMA_F64 = 0, 1, 2
+
+
+def fma_peak(kind: int) -> float:
+    """richm_fma_peak: measured FMA throughput in TFLOP/s (kind FMA_F32, FMA_F32X2 or FMA_F64)."""
+    out = C.c_double()
+    _check(load().richm_fma_peak(kind, C.byref(out)), "richm_fma_peak")
+    return out.value
 
 
 def selftest_conversions() -> tuple[int, int]:
