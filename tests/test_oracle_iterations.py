@@ -29,6 +29,31 @@ def _theta0_modes(n, eps):
     return lam, mode
 
 
+def test_richardson_period_is_the_printed_polynomial_form():
+    # eqs. 3-5: one outer iteration of m sweeps maps u to T_m u + g with
+    # T_m = (I - w_m A) ... (I - w_1 A) and g = (w_m + sum_j prod_{i>j} (I - w_i A) w_j) f,
+    # formed here as dense matrix products, independently of the sweep loop
+    rng = np.random.default_rng(5)
+    for n, eps, theta, m in [(4, 1e-2, 0.7, 3), (5, 1.0, 2.0, 4), (3, 1e-4, 0.1, 5)]:
+        A = assemble_q1(n, eps, theta).toarray()
+        N = n * n
+        w = rng.uniform(0.05, 0.4, m)
+        u0 = rng.standard_normal(N)
+        f = rng.standard_normal(N)
+        I = np.eye(N)
+        T = I.copy()
+        for i in range(m):
+            T = (I - w[i] * A) @ T
+        G = w[m - 1] * I
+        for j in range(m - 1):
+            P = I.copy()
+            for i in range(j + 1, m):
+                P = (I - w[i] * A) @ P
+            G = G + P * w[j]
+        u, _ = inner_steps(assemble_q1(n, eps, theta), f, u0, None, w, K=m)
+        np.testing.assert_allclose(u, T @ u0 + G @ f, rtol=1e-12, atol=1e-12)
+
+
 @pytest.mark.parametrize("eps", [1.0, 1e-2, 1e-5])
 def test_sine_mode_contraction(eps):
     # b = 0, x0 = sine mode: x_K = prod_s (1 - w_{s mod m} lam) x0 (eqs. 3-5)
