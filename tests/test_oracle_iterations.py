@@ -85,6 +85,100 @@ def test_nag_mode_recurrence():
         np.testing.assert_allclose(x, s * x0, rtol=1e-11, atol=1e-13)
 
 
+def _mode_transfer(w, a, at, lam, K, k_start=0):
+    """State-space form of Table 1's MOM / NAG / NAGex rows on an eigenvector of A with
+    eigenvalue lam (f = 0): the pair (u, v) of coefficients maps linearly per step,
+        u~ = u + at_i v,  v' = a_i v - w_i lam u~,  u' = u + v'
+    i.e. (u', v') = M_i (u, v) with M_i = [[1 - w_i lam, a_i - w_i lam at_i],
+                                           [  - w_i lam, a_i - w_i lam at_i]].
+    Returns the product M_{K-1} ... M_0 (a 2x2 matrix)."""
+    m = len(w)
+    P = np.eye(2)
+    for s in range(K):
+        i = (k_start + s) % m
+        g = w[i] * lam
+        c = a[i] - g * at[i]
+        P = np.array([[1.0 - g, c], [-g, c]]) @ P
+    return P
+
+
+@pytest.mark.parametrize("kind", ["mom", "nagex"])
+def test_lookahead_mode_transfer(kind):
+    # Table 1's MOM (at = 0) and NAGex (at != a) rows on theta = 0 sine modes, with a
+    # non-zero initial velocity: the oracle's (u, v) after K steps equal the product of
+    # the per-step 2x2 transfer matrices applied to the mode's (u0, v0) coefficients.
+    # Distinct a_i and at_i: a swapped pair (or a sign error in the look-ahead) moves the
+    # result far outside the tolerance (checked below).
+    n, m, K, k0 = 11, 5, 17, 3
+    eps = 1e-2
+    A = assemble_q1(n, eps, 0.0)
+    lam, mode = _theta0_modes(n, eps)
+    rng = np.random.default_rng(21)
+    G = lam.max()
+    w = rng.uniform(0.2, 1.2, m) / G
+    a = rng.uniform(0.05, 0.6, m)
+    at = np.zeros(m) if kind == "mom" else rng.uniform(0.3, 0.9, m)
+    c_u, c_v = 1.0, -0.4
+    for p, q in [(1, 2), (6, 6), (11, 3), (9, 10)]:
+        L = lam[p - 1, q - 1]
+        e = mode(p, q)
+        u, v = inner_steps(A, np.zeros_like(e), c_u * e, c_v * e, w, a, at, K=K, k_start=k0)
+        su, sv = _mode_transfer(w, a, at, L, K, k0) @ np.array([c_u, c_v])
+        np.testing.assert_allclose(u, su * e, rtol=1e-11, atol=1e-13)
+        np.testing.assert_allclose(v, sv * e, rtol=1e-11, atol=1e-13)
+        # the pin discriminates: swapping a and at, or dropping the look-ahead, changes
+        # the coefficient by far more than the tolerance
+        if kind == "nagex":
+            su_swap = (_mode_transfer(w, at, a, L, K, k0) @ np.array([c_u, c_v]))[0]
+            su_nag = (_mode_transfer(w, a, a, L, K, k0) @ np.array([c_u, c_v]))[0]
+            assert abs(su_swap - su) > 1e-6 * max(1.0, abs(su))
+            assert abs(su_nag - su) > 1e-6 * max(1.0, abs(su))
+        else:
+            su_nag = (_mode_transfer(w, a, a, L, K, k0) @ np.array([c_u, c_v]))[0]
+            assert abs(su_nag - su) > 1e-6 * max(1.0, abs(su))
+
+
+def test_mom_is_heavy_ball_three_term_recurrence():
+    # MOM-Richardson (Table 1, at = 0) on an eigenvector is Polyak's heavy-ball recurrence
+    # x_{k+1} = (1 + a - w lam) x_k - a x_{k-1}, written here for the coefficient alone
+    n, m, K = 9, 3, 14
+    eps = 1.0
+    A = assemble_q1(n, eps, 0.0)
+    lam, mode = _theta0_modes(n, eps)
+    w = np.array([0.21, 0.35, 0.5]) / lam.max() * 2
+    a = np.array([0.4, 0.15, 0.3])
+    for p, q in [(1, 1), (4, 8), (9, 9)]:
+        L = lam[p - 1, q - 1]
+        e = mode(p, q)
+        x, _ = inner_steps(A, np.zeros_like(e), e, None, w, a, np.zeros(m), K=K)
+        xm1, xk = 1.0, 1.0
+        for k in range(K):
+            i = k % m
+            xm1, xk = xk, (1 + a[i] - w[i] * L) * xk - a[i] * xm1
+        np.testing.assert_allclose(x, xk * e, rtol=1e-11, atol=1e-13)
+
+
+def test_torch_unroll_lookahead_mode_transfer():
+    # the training oracle's torch unroll (zero initial velocity) on the same modes
+    import torch
+    from oracle.training import to_torch_sparse, unrolled_nag
+    n, m, K = 7, 4, 13
+    eps = 1e-1
+    A = assemble_q1(n, eps, 0.0)
+    lam, mode = _theta0_modes(n, eps)
+    rng = np.random.default_rng(8)
+    w = rng.uniform(0.3, 1.4, m) / lam.max()
+    a = rng.uniform(0.1, 0.5, m)
+    for at in (np.zeros(m), rng.uniform(0.4, 0.8, m)):
+        for p, q in [(2, 5), (7, 1)]:
+            L = lam[p - 1, q - 1]
+            e = mode(p, q)
+            u = unrolled_nag(to_torch_sparse(A), torch.zeros(n * n, dtype=torch.float64), torch.from_numpy(e),
+                             torch.from_numpy(w), torch.from_numpy(a), K, at=torch.from_numpy(at)).numpy()
+            su = (_mode_transfer(w, a, at, L, K) @ np.array([1.0, 0.0]))[0]
+            np.testing.assert_allclose(u, su * e, rtol=1e-11, atol=1e-13)
+
+
 def test_momentum_zero_is_richardson_and_nagex_reductions():
     n = 9
     A = assemble_q1(n, 0.05, 0.7)

@@ -87,6 +87,17 @@ def test_gershgorin_bounds_spectrum():
         assert np.linalg.eigvalsh(A.toarray()).max() <= gershgorin_max(A) + 1e-12
 
 
+def test_gershgorin_hand_value():
+    # eps = 1e-2, theta = pi/6: c11 = 0.7525, c22 = 0.2575, c12 = 0.99 sin(pi/6) cos(pi/6);
+    # Q1 row (Sec. 2.4, eq. 18): centre 1.3466667, x-neighbours -0.4158333, y-neighbours
+    # 0.0791667, corners -0.3826746 and 0.0460080, so an interior row's absolute sum is
+    # 1.3466667 + 2 (0.4158333 + 0.0791667 + 0.3826746 + 0.0460080) = 3.1940319 (hand value)
+    A = assemble_q1(15, 1e-2, math.pi / 6)
+    assert abs(gershgorin_max(A) - 3.1940319) < 3e-7
+    # theta = 0, eps = 1: the textbook stencil (8, -1 x 8) / 3 sums to 16/3
+    assert abs(gershgorin_max(assemble_q1(6, 1.0, 0.0)) - 16.0 / 3.0) < 1e-13
+
+
 def test_window_is_submatrix():
     n = 11
     A = assemble_q1(n, 1e-2, 0.8).toarray()
