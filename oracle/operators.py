@@ -134,6 +134,39 @@ def assemble_helmholtz(n: int, k: float, absorbing: bool = True, window=None) ->
     return A.tocsr()
 
 
+def sponge_gamma(n: int, omega: float, c: float = 1.0, window=None) -> np.ndarray:
+    """The damping mask gamma of eq. 21 at the interior nodes (row-major over the window).
+
+    Readings: gamma rises linearly from 0 at depth L to omega on the boundary,
+    gamma(x) = omega * max(0, 1 - d(x) / L), with d(x) the distance from node x to the
+    boundary of the unit square and L = 2 pi c / omega one wavelength (the paper gives
+    the layer's thickness, one wavelength, and the end values, not the profile); the
+    wave speed c is constant. Pinned by: hand values (tests).
+    """
+    h = 1.0 / (n + 1)
+    if window is None:
+        i0, i1, j0, j1 = 0, n, 0, n
+    else:
+        i0, i1, j0, j1 = window
+    I, J = np.meshgrid(np.arange(i0, i1), np.arange(j0, j1), indexing="ij")
+    d = h * np.minimum(np.minimum(I + 1, n - I), np.minimum(J + 1, n - J))
+    L = 2.0 * math.pi * c / omega
+    return (omega * np.maximum(0.0, 1.0 - d / L)).ravel()
+
+
+def assemble_helmholtz_sponge(n: int, omega: float, c: float = 1.0, window=None) -> sp.csr_matrix:
+    """Eq. 21: -Lap(u) - k^2 u + i gamma omega / c^2 u = f, u = 0 on the boundary,
+    k = omega / c, with the 5-point stencil of eq. 22 (h = 1/(n+1)) and the damping
+    mask of `sponge_gamma` on the diagonal. Pinned by: Im(x^H A x) equals the
+    mask-weighted energy sum over the nodes, computed node by node (tests); the
+    Hermitian part is the Dirichlet Helmholtz operator.
+    """
+    k = omega / c
+    A = assemble_helmholtz(n, k, absorbing=False, window=window)
+    g = sponge_gamma(n, omega, c, window)
+    return (A + sp.diags(1j * g * omega / c ** 2)).tocsr()
+
+
 def gershgorin_max(A: sp.spmatrix) -> float:
     """max_i sum_j |a_ij|: an upper bound on the spectrum of symmetric A (used for lmax)."""
     return float(np.abs(A).sum(axis=1).max())

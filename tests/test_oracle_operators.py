@@ -178,3 +178,43 @@ def test_sampled_sweeps_equal_full_grid():
         s = sampled_sweeps(op, n, X0.astype(A.dtype), V0.astype(A.dtype), F.astype(A.dtype),
                            ww, a, None, K, pts, k_start=2)
         np.testing.assert_allclose(s, [x.reshape(n, n)[p] for p in pts], rtol=1e-13, atol=1e-13)
+
+
+def test_sponge_gamma_hand_values():
+    # N = 128 (n = 127, h = 1/128), omega = 2 pi 10 (Table 9's first column), c = 1:
+    # one wavelength L = 0.1 = 12.8 h, so gamma / omega = 1 - d / 12.8 with d the node's
+    # distance to the boundary in grid spacings
+    from oracle.operators import sponge_gamma
+    n, om = 127, 2 * math.pi * 10
+    g = sponge_gamma(n, om).reshape(n, n) / om
+    assert abs(g[0, 0] - (1 - 1 / 12.8)) < 1e-14          # d = 1
+    assert abs(g[0, 60] - (1 - 1 / 12.8)) < 1e-14         # an edge row, d = 1
+    assert abs(g[11, 40] - (1 - 12 / 12.8)) < 1e-14       # d = 12: 0.0625
+    assert g[12, 40] == 0.0 and g[63, 63] == 0.0          # d = 13 and the centre
+    assert abs(g[126, 5] - (1 - 1 / 12.8)) < 1e-14        # last row, d = 1
+    assert abs(g[5, 120] - (1 - 6 / 12.8)) < 1e-14        # d = min(6, 7) = 6
+
+
+def test_sponge_operator_energy_identity():
+    # the Laplacian and -k^2 parts are real symmetric, so Im(x^H A x) is the damping
+    # energy sum_x gamma(x) omega / c^2 |x|^2, here summed node by node with the
+    # distance taken from the node's coordinates
+    from oracle.operators import assemble_helmholtz_sponge
+    rng = np.random.default_rng(2)
+    for n, om, c in [(15, 40.0, 1.0), (20, 25.0, 1.3), (7, 30.0, 1.0)]:
+        A = assemble_helmholtz_sponge(n, om, c)
+        h = 1.0 / (n + 1)
+        x = rng.standard_normal(n * n) + 1j * rng.standard_normal(n * n)
+        E = 0.0
+        for i in range(n):
+            for j in range(n):
+                yy, xx = (i + 1) * h, (j + 1) * h
+                d = min(xx, 1 - xx, yy, 1 - yy)
+                gam = om * max(0.0, 1.0 - d / (2 * math.pi * c / om))
+                E += gam * om / c ** 2 * abs(x[i * n + j]) ** 2
+        q = np.vdot(x, A @ x)
+        assert abs(q.imag - E) <= 1e-10 * E
+        Ah = (A + A.conj().T) / 2
+        D = assemble_helmholtz(n, om / c, absorbing=False)
+        assert abs(Ah - D).max() < 1e-9
+        assert abs(A - A.T).max() < 1e-9  # complex symmetric
