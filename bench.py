@@ -1,11 +1,12 @@
 """Benchmark: batched NAG-Richardson(m) with FP64 refinement on synthetic anisotropic Q1 instances.
 
-Workload (one step = one refinement cycle over the whole batch): 256 instances of
--div(C grad u) = f (bilinear elements), eps = 10^U[-3, 0], theta ~ U[0, pi), n drawn
-from {127, 255, 511}, right-hand sides U[-1, 1]; NAG-Richardson(16) whose 16 weights
-and momentum come from the meta network; 64 FP32 sweeps, then the FP64 update,
-FP64 residual and per-instance convergence test. The full solve to 1e-10 is timed
-once after the steps (time to tolerance).
+Workload (the batched NAG configuration): 256 instances of -div(C grad u) = f (bilinear
+elements), eps = 10^U[-3, 0], theta ~ U[0, pi), n drawn from {127, 255, 511},
+right-hand sides U[-1, 1]; NAG-Richardson(16) with beta = 0.3 and the 16 weights of each
+instance from the meta network; FP32 sweeps (fused passes of 8), FP64 refinement every 64
+sweeps. One step = the whole hot path over the batch: the meta network's weight supply
+and the solve of every instance from x = 0 to relative residual 1e-10. value = the
+dof-sweeps performed / the time of the timed steps; ms_per_step = the time to 1e-10.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0). Under torchrun each rank solves its own batch of the
@@ -29,12 +30,10 @@ if ROOT not in sys.path:
 
 METRIC = "batched Richardson(m) Gdof-sweeps/s, time to 1e-10 rel residual, % HBM peak"
 UNIT = "Gdof-sweeps/s"
-# FP64 refinement every 256 sweeps: the momentum is carried across refinements, so the
-# interval changes only where FP32 rounding is corrected. On this batch 64, 128, 192 and
-# 256 sweeps per refinement gave 2.36, 2.02, 1.96 and 1.86 s to 1e-10 with the same
-# sweep counts (+0.5 %), the refinement being a quarter of a 64-sweep cycle on GB300's
-# reduced-rate FP64 pipe.
-M, BETA, REFINE, TOL = 16, 0.3, 256, 1e-10
+M, BETA, REFINE, TOL = 16, 0.3, 64, 1e-10
+# A longer refinement interval (measured beside the headline): the momentum is carried
+# across refinements, so the interval changes only where FP32 rounding is corrected.
+REFINE_LONG = 256
 # The solver stops at FP64 residual <= TOL * (1 - 1e-3): two independent FP64
 # evaluations of ||b - A x|| / ||b|| near 1e-10 (the library's stencil and the
 # oracle's assembled matrix) differ by ~1e-5 relative, so the margin makes the
@@ -42,18 +41,21 @@ M, BETA, REFINE, TOL = 16, 0.3, 256, 1e-10
 SOLVE_TOL = TOL * (1.0 - 1e-3)
 SIZES = (127, 255, 511)
 BATCH = 256
+# the meta network trained with its momentum held at BETA (meta.trained_path variant)
+META_VARIANT = "beta03"
 
 
 def workload_config(batch=BATCH):
     return {
         "workload": f"{batch} anisotropic Q1 (bilinear FEM) instances, n in {{127,255,511}}, "
-                    "eps=10^U[-3,0], theta~U[0,pi), b~U[-1,1]; NAG-Richardson(16), weights and momentum "
-                    f"from the meta MLP 2-64-64-17; FP32 sweeps, FP64 refinement every {REFINE} sweeps, tol 1e-10",
+                    "eps=10^U[-3,0], theta~U[0,pi), b~U[-1,1]; NAG-Richardson(16), beta=0.3, weights from the "
+                    f"meta MLP 2-64-64-17; FP32 sweeps, FP64 refinement every {REFINE} sweeps; "
+                    "one step = weight supply + solve of every instance from x=0 to rel. residual 1e-10",
         "instances": batch,
         "m": M,
+        "beta": BETA,
         "refine_every": REFINE,
-        "sweeps_per_step": REFINE,
-        "l2": "inputs larger than L2 (state ~0.47 GB FP32 + 0.47 GB FP64 > 129 MB): no flush",
+        "l2": "inputs larger than L2 (state ~0.47 GB FP32 + 0.71 GB FP64 > 129 MB): no flush",
     }
 
 
@@ -501,6 +503,75 @@ def meta_inputs(op, insts, params):
     return X, G, P
 
 
+def _timed(stream, fn):
+    """(result, ms) of fn() bracketed by CUDA events on `stream`."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1)
+
+
+def oracle_check(op, X, insts, rhs, per_size=4):
+    """Relative residuals of a sample of solutions (per_size of each grid size),
+    recomputed by the FP64 oracle from its own assembled matrices."""
+    import numpy as np
+
+    from oracle.operators import assemble_q1
+    from paper_2412_08076_gb300 import richm
+    xs_h = op.unpack(X, richm.F64).cpu().numpy()
+    offs = np.cumsum([0] + [t.n * t.n for t in insts])
+    checked, worst, per_n = 0, 0.0, {}
+    for i, t in enumerate(insts):
+        if per_n.get(t.n, 0) >= per_size:
+            continue
+        per_n[t.n] = per_n.get(t.n, 0) + 1
+        A = assemble_q1(t.n, t.eps, t.theta)
+        r = np.linalg.norm(rhs[i].ravel() - A @ xs_h[offs[i]:offs[i + 1]]) / np.linalg.norm(rhs[i])
+        worst = max(worst, float(r))
+        checked += 1
+    return checked, worst
+
+
+def plain_fp64_baseline(op, insts, rhs, w, a, sweeps, dev):
+    """The plain single-instance FP64 GPU sweep (one instance per call, one sweep per
+    launch, no graph, same weights, momentum and tolerance): one full solve to 1e-10 of
+    one instance of each grid size, timed; the batch's time is those solves plus the
+    other instances extrapolated from the measured time per sweep of their size."""
+    import torch
+
+    from paper_2412_08076_gb300 import richm
+    solved, per_sweep = {}, {}
+    for i, t in enumerate(insts):
+        if t.n in solved:
+            continue
+        op1 = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0)])
+        b1 = op1.pack(torch.tensor(rhs[i].ravel(), device=dev), richm.F64)
+        x1 = op1.zeros(richm.F64)
+        w1 = w[i:i + 1].double().contiguous()
+        a1 = a[i:i + 1].double().contiguous()
+        o1 = op1.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10 ** 7, refine_every=REFINE, inner=richm.F64, use_graph=0,
+                            fuse=1)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        st1, info1 = op1.solve(b1, x1, w1, a1, None, o1)
+        el = time.perf_counter() - c0
+        solved[t.n] = {"instance": i, "seconds": el, "sweeps": int(info1[0][0]), "status": int(st1),
+                       "rel_res": float(info1[0][1])}
+        per_sweep[t.n] = el / max(1, info1[0][0])
+        op1.close()
+    total = sum(v["seconds"] for v in solved.values())
+    done = {v["instance"] for v in solved.values()}
+    total += sum(per_sweep[t.n] * s for i, (s, t) in enumerate(zip(sweeps, insts)) if i not in done)
+    return {"seconds_measured_plus_extrapolated": total, "measured_solves": {str(k): v for k, v in solved.items()},
+            "per_sweep_s": {str(k): v for k, v in per_sweep.items()},
+            "note": "one full FP64 solve per grid size measured; the other instances extrapolated from the "
+                    "measured time per sweep of their size"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -523,37 +594,37 @@ def run_ours(args):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     insts, op, rhs, dense_b = build_batch(shard_seed(rank))
     dofs = sum(t.n * t.n for t in insts)
-    params, psrc = meta_mod.load_params(M)
+    params, psrc = meta_mod.load_params(M, variant=META_VARIANT)
     X, G, P = meta_inputs(op, insts, params)
     B64 = op.pack(dense_b.to(dev), richm.F64)
-    X64 = op.zeros(richm.F64)
     w, a = richm.meta_forward(P, X, G, M)
+    torch.cuda.synchronize()
+    beta_seen = float(a.min().item()), float(a.max().item())
     fuse, tune_ms = op.autotune(M, momentum=True)
-    opts = op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10**8, refine_every=REFINE, inner=richm.F32, use_graph=1,
+    opts = op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10 ** 7, refine_every=REFINE, inner=richm.F32, use_graph=1,
                          fuse=fuse)
-    # throughput cycles: tolerance 0, so no instance converges and drops out inside the
-    # timed region; every step sweeps every instance (the solve to tolerance is timed
-    # separately below)
-    opts_tp = op.solve_opts(M, tol=0.0, max_sweeps=10**8, refine_every=REFINE, inner=richm.F32, use_graph=1,
-                            fuse=fuse)
-    S = richm.Solver(op, opts_tp, w, a)
-    S.start(B64, X64)
     stream = torch.cuda.current_stream()
+    lib = richm.load()
 
-    # the weight supply writes into the solver's weight buffers directly
     def weight_supply():
-        lib = richm.load()
         richm._check(lib.richm_meta_forward(richm._ptr(P), richm._ptr(X), richm._ptr(G), len(insts), M,
                                             richm.HEAD_NAG_SHARED, richm._ptr(w), richm._ptr(a), None, None,
-                                            richm._stream(stream)),
-                     "richm_meta_forward")
+                                            richm._stream(stream)), "richm_meta_forward")
+
+    # one step: the weight supply and the solve of the whole batch to tolerance
+    Xs = op.zeros(richm.F64)
+    wsolve = op.workspace(op._ws("richm_solve_workspace", richm.C.byref(opts)))
+
+    def step():
+        weight_supply()
+        return op.solve(B64, Xs, w, a, None, opts, work=wsolve)
 
     for _ in range(args.warmup):
-        weight_supply()
-        S.step(1, sync=False)
+        step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -563,26 +634,65 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
+    infos = []
     for _ in range(args.steps):
-        weight_supply()
-        S.step(1, sync=False)
+        infos.append(step())
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    active = S.step(0, sync=True)
-    if active != len(insts):  # value assumes every instance was swept every step
-        print(f"warning: {len(insts) - active} instances stopped inside the timed region", file=sys.stderr)
     clk = clocks.stop()
+    st, info = infos[-1]
+    sweeps = [sw for sw, _, _ in info]
+    step_dof_sweeps = float(sum(sw * t.n * t.n for sw, t in zip(sweeps, insts)))
     t_max_ms = max_over_ranks(ms, world, dev)
-    total_dofs = sum_over_ranks(float(dofs), world, dev)
-    value = total_dofs * REFINE * args.steps / (t_max_ms / 1e3) / 1e9
-    # meta forward, sweep passes, then either the fused refinement and the reduction
-    # (fused passes) or the update, the residual and the reduction (one sweep per launch)
-    launches_per_step = 1 + REFINE // fuse + (2 if fuse > 1 else 3)
+    total = sum_over_ranks(step_dof_sweeps * args.steps, world, dev)
+    value = total / (t_max_ms / 1e3) / 1e9
+    # launches per step: the meta forward, the solver's start (zero start, reduction) and
+    # per cycle refine_every / fuse fused passes, the refinement and the reduction
+    cycles = int(math.ceil(max(sweeps) / REFINE))
+    launches_per_step = 1 + 2 + cycles * (REFINE // fuse + 2)
+    checked, worst = oracle_check(op, Xs, insts, rhs)
+    ttt = {"seconds": t_max_ms / args.steps / 1e3, "status": int(st),
+           "converged": sum(1 for _, _, s_ in info if s_ == richm.OK), "instances": len(insts),
+           "max_sweeps": int(max(sweeps)), "mean_sweeps": float(np.mean(sweeps)), "dof_sweeps": step_dof_sweeps,
+           "oracle_checked": checked, "oracle_worst_rel_res": worst,
+           "beta_from_network": list(beta_seen), "meta_params": psrc}
 
-    # -- dominant kernel (the FP32 NAG sweep pass) and the one-sweep kernel: launch
+    # -- refinement cycles with every instance active (tol = 0), both intervals: the
+    #    throughput of whole cycles without the convergence tail
+    cycle_tp = {}
+    for refine in (REFINE, REFINE_LONG):
+        o_tp = op.solve_opts(M, tol=0.0, max_sweeps=10 ** 8, refine_every=refine, inner=richm.F32, use_graph=1,
+                             fuse=fuse)
+        S = richm.Solver(op, o_tp, w, a)
+        S.start(B64, op.zeros(richm.F64))
+        nc = max(4, 4096 // refine)
+        S.step(4, sync=True)
+        _, cms = _timed(stream, lambda: S.step(nc, sync=False))
+        cycle_tp[f"refine_every_{refine}"] = {"ms_per_cycle": cms / nc,
+                                              "gdof_sweeps_per_s": dofs * refine * nc / (cms / 1e3) / 1e9}
+        S.close()
+    # the earlier network (momentum output ~0.645, trained without the momentum held)
+    # with refinement every 256 sweeps, for comparison
+    alt = None
+    if not args.no_secondary:
+        p_alt, src_alt = meta_mod.load_params(M)
+        _, _, P_alt = meta_inputs(op, insts, p_alt)
+        w_alt, a_alt = richm.meta_forward(P_alt, X, G, M)
+        o_alt = op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10 ** 7, refine_every=REFINE_LONG, inner=richm.F32,
+                              use_graph=1, fuse=fuse)
+        Xa = op.zeros(richm.F64)
+        (st_a, info_a), ams = _timed(stream, lambda: op.solve(B64, Xa, w_alt, a_alt, None, o_alt))
+        sw_a = [s_ for s_, _, _ in info_a]
+        alt = {"seconds": ams / 1e3, "status": int(st_a), "max_sweeps": int(max(sw_a)),
+               "beta": float(a_alt[0, 0].item()), "refine_every": REFINE_LONG,
+               "gdof_sweeps_per_s": sum(s_ * t.n * t.n for s_, t in zip(sw_a, insts)) / (ams / 1e3) / 1e9,
+               "note": "meta network trained with its momentum free (it settles near 0.645), refinement every "
+                       f"{REFINE_LONG} sweeps: not the stated configuration"}
+
+    # -- dominant kernel (the fused FP32 NAG pass) and the one-sweep kernel: launch
     #    durations by CUDA events on the launching stream
     xs = op.zeros(richm.F32)
     xps = op.zeros(richm.F32)
@@ -593,54 +703,50 @@ def run_ours(args):
     def launch_ms(f, K=192, reps=3):
         op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=f, work=ws)
         torch.cuda.synchronize()
-        k0 = torch.cuda.Event(enable_timing=True)
-        k1 = torch.cuda.Event(enable_timing=True)
-        k0.record(stream)
-        for _ in range(reps):
-            op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=f, work=ws)
-        k1.record(stream)
-        torch.cuda.synchronize()
-        return k0.elapsed_time(k1) / (reps * K // f)
+
+        def run():
+            for _ in range(reps):
+                op.apply_sweeps(richm.F32, xs, xps, b32, w, a, None, K=K, m=M, fuse=f, work=ws)
+        _, t = _timed(stream, run)
+        return t / (reps * K // f)
 
     one_ms = launch_ms(1)
     one_gbs = 16.0 * dofs / (one_ms / 1e3) / 1e9  # read x_k, x_{k-1}, b; write x_{k+1}
     if fuse == 1:
-        kname = "sweep1_kernel<float,NAG> (one FP32 NAG sweep per launch)"
-        alg_bytes = 16.0 * dofs
-        achieved = one_gbs
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": kernel_traffic("sweep1", dofs), "kernel": kname, "alg_bytes_per_launch": alg_bytes,
-                "launch_ms": one_ms, "sweeps_per_launch": 1, "peak_source": f"{peak_src} hbm_gbs (of measured)"}
+        roof = {"bound": "hbm", "achieved": one_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": one_gbs / hbm_peak,
+                "traffic": kernel_traffic("sweep1", dofs), "kernel": "sweep1_kernel<float,NAG>",
+                "alg_bytes_per_launch": 16.0 * dofs, "launch_ms": one_ms, "sweeps_per_launch": 1,
+                "peak_source": f"{peak_src} hbm_gbs"}
     else:
         fused_ms = launch_ms(fuse)
-        kname = (f"sweepT8_kernel<NAG> (8 FP32 NAG sweeps per launch, temporal blocking, two warps per tile, skewed levels)"
+        kname = (f"sweepT8_kernel<NAG> (8 FP32 NAG sweeps per launch, temporal blocking)"
                  if fuse == 8 else f"sweepT_kernel<{fuse},NAG> ({fuse} FP32 NAG sweeps per launch, temporal blocking)")
-        # instruction-issue bound: algorithmic FP32 work per unknown and sweep of the NAG
-        # 9-point update is 19 flops (y: 3, A y: 13, b - A y: 1, y + w r: 2); the peak
-        # is 152 SMs x 128 FP32 lanes x 2 flops (FMA) x the clock sampled under load
+        # algorithmic bytes of a pass: read x_k, x_{k-1}, b, write x_{k+T}, x_{k+T-1}
+        # (20 B per unknown, 20/T B per dof-sweep); the binding roof at T = 8 is HBM's
+        # (HBM: 6768 / 2.5 = 2707 Gdof-sweeps/s; FP32 pipe: 80.5 TFLOP/s / 19 = 4237)
+        alg = 20.0 * dofs
+        gbs = alg / (fused_ms / 1e3) / 1e9
         sm_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
-        fp32_peak = 152 * 128 * 2 * sm_ghz / 1e3  # TFLOP/s
+        fp32_peak = sms * 128 * 2 * sm_ghz / 1e3  # TFLOP/s
         flops = 19.0 * dofs * fuse
-        achieved = flops / (fused_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": kernel_traffic(f"sweepT{fuse}", dofs),
-                "kernel": kname, "alg_flops_per_launch": flops, "launch_ms": fused_ms, "sweeps_per_launch": fuse,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_ghz:.3f} GHz (sampled)",
-                "hbm_view": {"alg_bytes_per_launch": 20.0 * dofs,
-                             "achieved_gbs": 20.0 * dofs / (fused_ms / 1e3) / 1e9,
-                             "frac_of_measured_hbm": 20.0 * dofs / (fused_ms / 1e3) / 1e9 / hbm_peak},
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": kernel_traffic(f"sweepT{fuse}", dofs), "kernel": kname, "alg_bytes_per_launch": alg,
+                "launch_ms": fused_ms, "sweeps_per_launch": fuse, "peak_source": f"{peak_src} hbm_gbs",
+                "gdof_sweeps_per_s": dofs * fuse / (fused_ms / 1e3) / 1e9,
+                "alu_view": {"alg_flops_per_launch": flops, "achieved_tflops": flops / (fused_ms / 1e3) / 1e12,
+                             "derived_fp32_peak_tflops": fp32_peak,
+                             "frac": flops / (fused_ms / 1e3) / 1e12 / fp32_peak,
+                             "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_ghz:.3f} GHz (sampled)"},
                 "one_sweep_kernel": {"kernel": "sweep1_kernel<float,NAG>", "launch_ms": one_ms,
                                      "achieved_gbs": one_gbs, "frac_of_measured_hbm": one_gbs / hbm_peak}}
-        # the same ceiling measured: independent FMA chains at full occupancy
-        # (richm_fma_peak), outside the timed region; reported beside the derived peak
         try:
             fma = {"fp32": richm.fma_peak(richm.FMA_F32), "fp32x2": richm.fma_peak(richm.FMA_F32X2),
                    "fp64": richm.fma_peak(richm.FMA_F64), "unit": "TFLOP/s"}
             best = max(fma["fp32"], fma["fp32x2"])
-            fma["frac_of_measured_fp32"] = achieved / best if best > 0 else None
-            roof["fma_microbenchmark"] = fma
+            fma["frac_of_measured_fp32"] = flops / (fused_ms / 1e3) / 1e12 / best if best > 0 else None
+            roof["alu_view"]["fma_microbenchmark"] = fma
         except Exception as exc:  # a diagnostic: never costs the bench line
-            roof["fma_microbenchmark"] = {"error": str(exc)[:200]}
+            roof["alu_view"]["fma_microbenchmark"] = {"error": str(exc)[:200]}
 
     # -- e2e: the call a user makes with host buffers: richm_solve_host copies b from
     #    pinned host memory, packs, solves every instance to tolerance from x = 0,
@@ -651,6 +757,7 @@ def run_ours(args):
     for rep in range(1 + max(1, args.e2e_runs)):
         torch.cuda.synchronize()
         c0 = time.perf_counter()
+        weight_supply()
         st_e, info_e = op.solve_host(hb, hx, w, a, None, opts)
         el = time.perf_counter() - c0
         if rep > 0:  # the first call warms the host path
@@ -658,68 +765,11 @@ def run_ours(args):
     e2e_s = sum(r[0] for r in e2e_runs) / len(e2e_runs)
     e2e_val = sum(r[1] for r in e2e_runs) / sum(r[0] for r in e2e_runs) / 1e9
 
-    # -- time to tolerance: full solve from x0 = 0 (timed once)
-    ttt = None
+    plain = None
     if not args.no_solve:
-        Xs = op.zeros(richm.F64)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        st, info = op.solve(B64, Xs, w, a, None, opts)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        solve_s = t0.elapsed_time(t1) / 1e3
-        sweeps = [s for s, _, _ in info]
-        ok = sum(1 for _, _, s in info if s == richm.OK)
-        # oracle verification of a sample of instances (4 of each size)
-        from oracle.operators import assemble_q1
-        xs_h = op.unpack(Xs, richm.F64).cpu().numpy()
-        offs = np.cumsum([0] + [t.n * t.n for t in insts])
-        checked, worst = 0, 0.0
-        per_n = {}
-        for i, t in enumerate(insts):
-            if per_n.get(t.n, 0) >= 4:
-                continue
-            per_n[t.n] = per_n.get(t.n, 0) + 1
-            A = assemble_q1(t.n, t.eps, t.theta)
-            u = xs_h[offs[i]:offs[i + 1]]
-            r = np.linalg.norm(rhs[i].ravel() - A @ u) / np.linalg.norm(rhs[i])
-            worst = max(worst, r)
-            checked += 1
-        ttt = {"seconds": solve_s, "status": int(st), "converged": ok, "instances": len(insts),
-               "max_sweeps": int(max(sweeps)), "total_dof_sweeps": float(sum(s * t.n * t.n for s, t in zip(sweeps, insts))),
-               "oracle_checked": checked, "oracle_worst_rel_res": worst}
-        ttt["gdof_sweeps_per_s"] = ttt["total_dof_sweeps"] / solve_s / 1e9
-        # plain FP64 GPU sweep (one instance per call, one sweep per launch, no graph):
-        # time per sweep on a running session for one instance of each size,
-        # extrapolated to the sweep counts above
-        per_sweep = {}
-        seen = {}
-        for i, t in enumerate(insts):
-            if t.n in seen:
-                continue
-            seen[t.n] = i
-            op1 = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0)])
-            b1 = op1.pack(torch.tensor(rhs[i].ravel(), device=dev), richm.F64)
-            x1 = op1.zeros(richm.F64)
-            w1 = w[i:i + 1].double().contiguous()
-            a1 = a[i:i + 1].double().contiguous()
-            o1 = op1.solve_opts(M, tol=0.0, max_sweeps=10**9, refine_every=64, inner=richm.F64, use_graph=0,
-                                fuse=1)
-            S1 = richm.Solver(op1, o1, w1, a1)
-            S1.start(b1, x1)
-            S1.step(1, sync=True)
-            c0 = time.perf_counter()
-            S1.step(6, sync=True)
-            per_sweep[t.n] = (time.perf_counter() - c0) / (6 * 64)
-            S1.close()
-            op1.close()
-        fp64_est = sum(per_sweep[t.n] * s for s, t in zip(sweeps, insts))
-        ttt["plain_fp64_seconds_extrapolated"] = fp64_est
-        ttt["plain_fp64_per_sweep_s"] = {str(k): v for k, v in per_sweep.items()}
-        ttt["speedup_vs_plain_fp64"] = fp64_est / solve_s
+        plain = plain_fp64_baseline(op, insts, rhs, w, a, sweeps, dev)
+        plain["speedup_of_the_batched_solve"] = plain["seconds_measured_plus_extrapolated"] / ttt["seconds"]
 
-    S.close()
     fuse_rows = op.tuned()[1]
     workloads = None if args.no_secondary else secondary_workloads(dev)
     # -- experiment: bfloat16 storage of the inner iterate (FP32 arithmetic, FP64 refinement)
@@ -730,37 +780,22 @@ def run_ours(args):
         wsb = op.workspace(op._ws("richm_sweeps_workspace", richm.BF16))
         op.apply_sweeps(richm.BF16, xb16, xpb16, b32, w, a, None, K=192, m=M, fuse=fuse, work=wsb)
         torch.cuda.synchronize()
-        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        q0.record(stream)
-        for _ in range(3):
-            op.apply_sweeps(richm.BF16, xb16, xpb16, b32, w, a, None, K=192, m=M, fuse=fuse, work=wsb)
-        q1.record(stream)
-        torch.cuda.synchronize()
-        bf_ms = q0.elapsed_time(q1) / (3 * 192 // fuse)
-        ob = op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10**8, refine_every=REFINE, inner=richm.BF16, use_graph=1,
+
+        def runb():
+            for _ in range(3):
+                op.apply_sweeps(richm.BF16, xb16, xpb16, b32, w, a, None, K=192, m=M, fuse=fuse, work=wsb)
+        _, bms = _timed(stream, runb)
+        bf_ms = bms / (3 * 192 // fuse)
+        ob = op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10 ** 6, refine_every=REFINE, inner=richm.BF16, use_graph=1,
                            fuse=fuse)
         Xb = op.zeros(richm.F64)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        st_b, info_b = op.solve(B64, Xb, w, a, None, ob)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        from oracle.operators import assemble_q1
-        xbh = op.unpack(Xb, richm.F64).cpu().numpy()
-        offs = np.cumsum([0] + [t.n * t.n for t in insts])
-        worst_b = 0.0
-        for i in range(0, len(insts), 64):
-            t = insts[i]
-            A = assemble_q1(t.n, t.eps, t.theta)
-            u = xbh[offs[i]:offs[i + 1]]
-            worst_b = max(worst_b, np.linalg.norm(rhs[i].ravel() - A @ u) / np.linalg.norm(rhs[i]))
+        (st_b, info_b), sbms = _timed(stream, lambda: op.solve(B64, Xb, w, a, None, ob))
+        nb_chk, worst_b = oracle_check(op, Xb, insts, rhs, per_size=1)
         bf16 = {"fused_launch_ms": bf_ms, "fused_gdof_sweeps_per_s": dofs * fuse / (bf_ms / 1e3) / 1e9,
-                "fp32_fused_gdof_sweeps_per_s": dofs * fuse / (roof["launch_ms"] / 1e3) / 1e9
-                if roof.get("sweeps_per_launch", 1) > 1 else None,
-                "solve_seconds": t0.elapsed_time(t1) / 1e3, "status": int(st_b),
+                "fp32_fused_gdof_sweeps_per_s": roof.get("gdof_sweeps_per_s"),
+                "solve_seconds": sbms / 1e3, "status": int(st_b),
                 "converged": sum(1 for _, _, s_ in info_b if s_ == richm.OK),
-                "max_sweeps": int(max(sw_ for sw_, _, _ in info_b)), "oracle_checked": 4,
+                "max_sweeps": int(max(sw_ for sw_, _, _ in info_b)), "oracle_checked": nb_chk,
                 "oracle_worst_rel_res": worst_b,
                 "note": "bfloat16 inner state (x_k, x_{k-1} and the correction stored as bf16), FP32 arithmetic "
                         f"and rhs, FP64 refinement every {REFINE} sweeps; an experiment, not the headline"}
@@ -773,10 +808,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(), dofs_per_rank=dofs, meta_params=psrc,
-                           active_after_steps=active, timed_tol=0.0, sweeps_per_pass=fuse, fused_tile_rows=fuse_rows,
-                           autotune_ms_per_sweep=tune_ms,
-                           solve_tol=SOLVE_TOL),
+            "config": dict(workload_config(), dofs_per_rank=dofs, meta_params=psrc, sweeps_per_pass=fuse,
+                           fused_tile_rows=fuse_rows, autotune_ms_per_sweep=tune_ms, solve_tol=SOLVE_TOL),
             "roofline": roof,
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc,
                              "host_cores": os.cpu_count()},
@@ -785,12 +818,15 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(dense_b.numel() * 8),
                     "d2h_bytes_per_step": int(hx.numel() * 8), "seconds_per_call": e2e_s,
                     "statuses": [r[2] for r in e2e_runs],
-                    "note": "one step = one richm_solve_host call: pinned H2D of b, pack, solve every instance "
-                            "to 1e-10 from x = 0 (FP32 sweeps + FP64 refinement), unpack, D2H of x; "
-                            "value = dof-sweeps performed / wall time"},
+                    "note": "one step = the weight supply and one richm_solve_host call: pinned H2D of b, pack, "
+                            "solve every instance to 1e-10 from x = 0 (FP32 sweeps + FP64 refinement), unpack, "
+                            "D2H of x; value = dof-sweeps performed / wall time"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "time_to_tol": ttt,
+            "cycle_throughput_all_active": cycle_tp,
+            "plain_fp64_gpu_sweep": plain,
+            "network_free_momentum_refine256": alt,
             "workloads": workloads,
             "bf16_state_experiment": bf16,
         }
@@ -802,17 +838,137 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- profiling cases
+
+# the sources a kernel is compiled from (its translation unit and the shared device
+# header; kernels.cuh only declares host launchers)
+TRAFFIC_SOURCES = {
+    "sweep1": ["paper_2412_08076_gb300/csrc/sweep.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
+    "sweepT4": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
+    "sweepT8": ["paper_2412_08076_gb300/csrc/sweep_fused.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
+    "refine": ["paper_2412_08076_gb300/csrc/solve.cu", "paper_2412_08076_gb300/csrc/common.cuh"],
+}
+
+
+def record_traffic(report: str, kind: str, unknowns: int) -> float:
+    """Read dram__bytes_read/write.sum of the captured launch from an ncu report and
+    store DRAM bytes per unknown in profiles/traffic.txt with a hash of the kernel's
+    sources (the bench reports traffic only while the hash still matches)."""
+    import csv
+    import hashlib
+    out = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], capture_output=True, text=True,
+                         check=True).stdout
+    rows = list(csv.reader(out.splitlines()))
+    hdr, units, data = rows[0], rows[1], rows[2]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    tot = 0.0
+    for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        i = hdr.index(name)
+        tot += float(data[i].replace(",", "")) * scale[units[i]]
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[kind]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    lines = []
+    if os.path.exists(path):
+        lines = [ln for ln in open(path).read().splitlines() if ln and not ln.startswith(kind + " ")]
+    per = tot / unknowns
+    lines.append(f"{kind} {h.hexdigest()} {per:.6f} {' '.join(TRAFFIC_SOURCES[kind])}")
+    with open(path, "w") as fh:
+        fh.write("\n".join(sorted(lines)) + "\n")
+    return per
+
+
+def run_profile_case(args):
+    """A small fixed workload for capturing one kernel family with ncu: a few FP32 NAG
+    sweeps (or solver cycles, adjoint steps, complex Helmholtz or SSOR sweeps) on a batch
+    of identical-size anisotropic instances, large enough that the state exceeds L2 and
+    small enough (a few hundred MB) for a short capture."""
+    import numpy as np
+    import torch
+
+    import richm_synth as synth
+    from paper_2412_08076_gb300 import richm
+    m = 16
+    what = args.profile
+    insts = synth.batched_aniso(args.batch, sizes=(args.n,), param_seed=1)
+    if what == "helmholtz":
+        k = 2 * math.pi * (args.n + 1) / 10
+        op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, args.n, 1.0, 0.0, k)] * args.batch)
+        dt = richm.C64
+        w = torch.full((args.batch, 8), 1.0 / (8 * (args.n + 1) ** 2), device="cuda")
+        a = torch.full((args.batch, 8), 0.3, device="cuda")
+        x, xp, b = op.zeros(dt), op.zeros(dt), op.zeros(dt)
+        b.fill_(1.0)
+        op.apply_sweeps(dt, x, xp, b, w, a, None, K=args.sweeps, m=8, fuse=args.fuse)
+        torch.cuda.synchronize()
+        return 0
+    op = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0) for t in insts])
+    G = np.array(op.gershgorin())
+    unit = np.array(richm.chebyshev_weights(1.6, 1.6 / 30.0, m))
+    w = torch.tensor(unit[None, :] / G[:, None], dtype=torch.float32, device="cuda")
+    a = torch.full_like(w, 0.3)
+    dense = torch.tensor(np.concatenate([synth.rhs_uniform(2, i, t.n).ravel() for i, t in enumerate(insts)]),
+                         device="cuda")
+    if what == "sweep":
+        b = op.pack(dense.float(), richm.F32)
+        x, xp = op.zeros(richm.F32), op.zeros(richm.F32)
+        op.apply_sweeps(richm.F32, x, xp, b, w, a, None, K=args.sweeps, m=m, fuse=args.fuse)
+    elif what == "ssor":
+        # SSOR-preconditioned NAG sweeps (B^{-1} A has its spectrum in (0, 1])
+        b = op.pack(dense.float(), richm.F32)
+        x, xp = op.zeros(richm.F32), op.zeros(richm.F32)
+        ws_ = torch.tensor(np.tile(unit, (args.batch, 1)), dtype=torch.float32, device="cuda")
+        op.apply_sweeps(richm.F32, x, xp, b, ws_, a, None, K=args.sweeps, m=m, precond=2, relax=1.5)
+    elif what == "cycle":
+        b = op.pack(dense, richm.F64)
+        x = op.zeros(richm.F64)
+        S = richm.Solver(op, op.solve_opts(m, tol=1e-10, max_sweeps=10 ** 8, fuse=args.fuse), w, a)
+        S.start(b, x)
+        S.step(max(1, args.sweeps // 64), sync=True)
+        S.close()
+    else:  # adjoint
+        b = op.pack(dense.float(), richm.F32)
+        K, every = 16, 8
+        ck = torch.empty(op.checkpoint_elems(K, every), dtype=torch.float32, device="cuda")
+        xK, g = op.zeros(richm.F32), op.zeros(richm.F32)
+        x0 = op.zeros(richm.F32)
+        op.forward_checkpointed(richm.F32, x0, b, w, a, None, m, K, every, 0, ck, xK)
+        op.loss_log_residual(richm.F32, xK, b, g)
+        gw, ga = torch.zeros_like(w), torch.zeros_like(a)
+        op.sweeps_adjoint(richm.F32, ck, every, b, g, w, a, None, m, K, 0, gw, ga, None, None)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-tolerance solve")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--e2e-runs", type=int, default=2, help="timed richm_solve_host calls")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", choices=["sweep", "cycle", "adjoint", "helmholtz", "ssor"], default=None,
+                    help="run a small fixed workload of one kernel family for an ncu capture instead of the bench")
+    ap.add_argument("--batch", type=int, default=32, help="--profile: instances")
+    ap.add_argument("--n", type=int, default=511, help="--profile: grid size")
+    ap.add_argument("--sweeps", type=int, default=6, help="--profile: sweeps")
+    ap.add_argument("--fuse", type=int, default=1, help="--profile: sweeps per pass")
+    ap.add_argument("--record-traffic", metavar="NCU_REPORT", default=None,
+                    help="store the report's DRAM bytes per unknown (--kind, --batch x --n^2 unknowns) in "
+                         "profiles/traffic.txt and exit")
+    ap.add_argument("--kind", default="sweepT8", choices=sorted(TRAFFIC_SOURCES))
     args = ap.parse_args(argv)
+    if args.record_traffic:
+        per = record_traffic(args.record_traffic, args.kind, args.batch * args.n * args.n)
+        print(f"{args.kind}: {per:.3f} DRAM bytes per unknown per launch")
+        return 0
+    if args.profile:
+        return run_profile_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -66,7 +66,12 @@ typedef enum {
 typedef enum {
   RICHM_ANISO_Q1 = 0,              /* eq. 18, bilinear elements, Dirichlet eliminated (Sec. 2.4) */
   RICHM_HELMHOLTZ_FD5_ABC = 1,     /* eq. 22 interior rows; first-order absorbing boundary */
-  RICHM_HELMHOLTZ_FD5_DIRICHLET = 2/* eq. 22 interior rows; u = 0 on the boundary */
+  RICHM_HELMHOLTZ_FD5_DIRICHLET = 2,/* eq. 22 interior rows; u = 0 on the boundary */
+  RICHM_HELMHOLTZ_FD5_SPONGE = 3   /* eq. 21: eq. 22's stencil, u = 0 on the boundary, and the damping
+                                      term i gamma(x) omega / c^2 on the diagonal, with c = 1 (omega = k),
+                                      gamma = k max(0, 1 - d(x)/L), d(x) the distance to the boundary and
+                                      L = 2 pi / k one wavelength (a linear ramp: the paper gives the layer's
+                                      thickness and end values only) */
 } richm_problem;
 
 typedef enum {
@@ -122,8 +127,17 @@ richm_status richm_operator_batch(const richm_operator* op, int* batch);
 /* Host FP64 stencil coefficients of one instance.
  * Q1: coef[0..4] = centre, x-neighbour, y-neighbour, corner(+1,+1), corner(+1,-1).
  * Helmholtz: coef[0] = centre, coef[1] = neighbour, coef[2..3] = (re, im) added to the
- * diagonal per missing neighbour (0 for Dirichlet). coef: host [8]. */
+ * diagonal per missing neighbour (0 for Dirichlet and the sponge layer); sponge layer:
+ * coef[4] = the imaginary diagonal term on the boundary (k^2) and coef[5] = the layer's
+ * width L/h in grid spacings, so that a node at distance d h from the boundary gains
+ * i coef[4] max(0, 1 - d / coef[5]). coef: host [8]. */
 richm_status richm_stencil(const richm_operator* op, int instance, double* coef);
+
+/* The Q1 stencil of richm_operator_create for one (eps, theta) without an operator
+ * (host only, no device memory): coef[0..4] = centre, x-neighbour, y-neighbour,
+ * corner(+1,+1), corner(+1,-1); coef[5] = the Gershgorin bound |c| + 2 sum |off|.
+ * coef: host [6]. Errors: RICHM_ERR_ARG unless 0 < eps <= 1 and theta is finite. */
+richm_status richm_q1_stencil(double eps, double theta, double* coef);
 
 /* Gershgorin bound max_i sum_j |a_ij| per instance (the lmax estimate used with
  * eqs. 8-9 in the Chebyshev semi-iteration, Sec. 2.1). lmax: host [batch]. */
@@ -133,6 +147,27 @@ richm_status richm_gershgorin(const richm_operator* op, double* lmax);
  * x_i = cos((2i-1) pi / 2m), i = 1..m, returned in index order. w: host [m].
  * Errors: RICHM_ERR_ARG unless 0 < lmin < lmax and m >= 1. */
 richm_status richm_chebyshev_weights(double lmax, double lmin, int m, double* w);
+
+/* Order of the steps inside a period. Eqs. 8-9 fix the set of weights of a period,
+ * not the order of its steps; in FP32 the order decides how much the rounding made at
+ * one step is amplified by the later (long) steps of the same period. This reorders
+ * them by a Leja ordering of the nodes z_i = 1/w_i (the roots of the period's residual
+ * polynomial): first the node of largest |z|, then repeatedly the node maximising the
+ * product (FP64, in the order taken) of its distances to the nodes already taken, ties
+ * to the smaller index (Reichel 1990). The paper has no counterpart; it is an option
+ * of this library.
+ * richm_leja_order (host): w: host [m] (nonzero, finite), perm: host [m] receives the
+ * permutation, perm[s] = index of the step that runs at position s; 1 <= m <= 64.
+ * richm_leja_permute (device, stream-ordered): for every instance b of the operator,
+ * w_out[b][s] = w[b][perm_b[s]] with perm_b the Leja order of w[b][:], and alpha_out,
+ * alpha_t_out the same permutation of alpha, alpha_t (a step's coefficients move
+ * together); arrays [batch][m] in the real type of dtype (float for RICHM_F32,
+ * RICHM_C64, RICHM_BF16; double for RICHM_F64, RICHM_C128). alpha / alpha_t and their
+ * outputs are both given or both NULL. Not in place. Errors: RICHM_ERR_ARG. */
+richm_status richm_leja_order(const double* w, int m, int* perm);
+richm_status richm_leja_permute(const richm_operator* op, richm_dtype dtype, const void* w, const void* alpha,
+                                const void* alpha_t, int m, void* w_out, void* alpha_out, void* alpha_t_out,
+                                void* stream);
 
 /* Padded layout of one instance (see the header comment): element offset of its
  * row 0, row pitch in elements, and number of rows (n + 2). Host outputs. */
@@ -158,8 +193,8 @@ typedef struct {
                    numbering of each instance's unknowns (Q1, RICHM_F32 or RICHM_F64, one sweep per
                    pass) */
   int fuse;     /* sweeps per pass over HBM (temporal blocking): 0 = library choice, else 1, 2, 4 or 8
-                   (RICHM_F32 / RICHM_BF16 Q1: 4 or 8; RICHM_C64 Helmholtz without preconditioner: 4;
-                   other cases run one sweep per pass) */
+                   (RICHM_F32 / RICHM_BF16 Q1: 4 or 8; RICHM_C64 Helmholtz without preconditioner and
+                   without a sponge layer: 4; other cases run one sweep per pass) */
   double relax; /* SSOR relaxation factor, 0 < relax < 2 (precond = 2 only) */
 } richm_sweep_opts;
 
@@ -226,11 +261,14 @@ richm_status richm_residual_norm(richm_operator* op, richm_dtype dtype, const vo
  * convenience. The scratch (per-tile partial sums and per-instance tile offsets)
  * lives in file-scope device arrays of the library, present on every GPU that loads
  * it until the process exits (1 MiB + 256 KiB); the call allocates nothing.
- * Limits: at most 65536 warp tiles (tiles of 16 rows x 32 lanes x one 16-byte vector,
- * e.g. about 33 M FP64 unknowns) and 65536 instances; larger batches return
- * RICHM_ERR_NOMEM before any work is queued. The first call on a device looks up the
- * arrays' device addresses (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture. Every call shares the arrays and rewrites all
+ * Limits: at most 65536 warp tiles (tiles of 16 rows x 32 lanes x one 16-byte vector:
+ * about 134 M FP32, 67 M FP64 or complex64 and 33 M complex128 unknowns, less the
+ * padding of each row to its 32-element pitch) and 65536 instances; larger batches
+ * return RICHM_ERR_NOMEM before any work is queued. Every call looks up the arrays'
+ * device addresses on the current device (cudaGetSymbolAddress, host-side; no address
+ * is kept between calls, so a context that is destroyed and made again is safe); the
+ * first call on a device may load the library's module there, so make it before any
+ * stream capture. Every call shares the arrays and rewrites all
  * the entries it reads, so nothing needs clearing, but calls that overlap on the GPU
  * (different streams, threads or devices' contexts racing on one array) race: order
  * them. Outputs and error behaviour are those of richm_residual_norm. */
@@ -261,7 +299,14 @@ typedef struct {
 /* Workspace bytes of richm_solve / richm_solver_create: four inner-state buffers, the
  * inner right-hand side, per-tile partial sums, per-instance arrays and, for an FP32 or
  * bfloat16 inner state, a second padded FP64 solution buffer (fused cycles alternate
- * between it and x). */
+ * between it and x). Layout, for inspecting a session between steps (with
+ * E = elems x the inner state's element size rounded up to 256 bytes): inner-state
+ * buffer j (padded, inner dtype) at byte j*E, j = 0..3; the inner right-hand side
+ * (padded, FP64 for an FP64 inner state, else FP32) at 4*E; the second FP64 solution
+ * buffer in the last elems*8 bytes rounded up to 256. After cycle c of a fused session
+ * (refine_every/fuse passes per cycle) the cycle's final pair (e_k, e_{k-1}) is in
+ * buffers (0, 1) when (c + 1) * refine_every/fuse is even, else (2, 3), and the
+ * refinement has written x + e_k to the second buffer for even c, to x for odd c. */
 richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_opts* opts, size_t* bytes);
 
 /* Solve every instance of a Q1 batch to tolerance ("iterate until a tolerance or the
@@ -329,6 +374,48 @@ richm_status richm_solve_host(richm_operator* op, const double* b_host, double* 
  * work: at least richm_residual_workspace bytes. */
 richm_status richm_refine(richm_operator* op, double* x, const double* b, void* e, void* e_prev, int inner,
                           void* rhs_out, double* rel, void* work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------ Krylov outer solver */
+
+/* Restarted flexible GMRES with the Table 1 sweeps as its preconditioner (Sec. 3.2: the
+ * single-level solvers as smoothers of a preconditioner for FGMRES restarted every 20
+ * iterations, Table 9; FGMRES after Saad, SIAM J. Sci. Comput. 14 (1993) 461-469). */
+typedef struct {
+  int restart;    /* Arnoldi steps per cycle, 1..64 (the paper's 20) */
+  double tol;     /* an instance stops once its residual estimate reaches tol * ||b|| */
+  int max_iters;  /* Arnoldi steps per instance at most */
+  int m;          /* period of the smoother's coefficients ([batch][m] arrays) */
+  int sweeps;     /* smoother sweeps per preconditioner application (0: no preconditioner) */
+  int inner;      /* the smoother's state: RICHM_C64 (mixed precision) or RICHM_C128 */
+  int precond;    /* the smoother's B^{-1}: 0 none, 1 Jacobi (D^{-1}) */
+} richm_fgmres_opts;
+
+typedef struct {
+  int iters;       /* Arnoldi steps taken (the iteration count of Table 9) */
+  double rel_res;  /* final ||b - A x|| / ||b|| (FP64, recomputed) */
+  int status;      /* RICHM_OK, RICHM_ERR_NOT_CONVERGED or RICHM_ERR_DIVERGED */
+} richm_fgmres_info;
+
+/* Workspace bytes of richm_fgmres: restart + 1 complex128 basis vectors, restart
+ * preconditioned vectors of the inner type, the smoother's state and workspace, and the
+ * per-instance Hessenberg systems. */
+richm_status richm_fgmres_workspace(const richm_operator* op, const richm_fgmres_opts* opts, size_t* bytes);
+
+/* Solve A x = b for every (Helmholtz) instance of the batch: each cycle starts from
+ * r = b - A x, builds an orthonormal basis v_1..v_j of complex128 vectors with
+ * z_i = M(v_i), A z_i = sum_k h_ki v_k (classical Gram-Schmidt applied twice), reduces
+ * the Hessenberg system by complex Givens rotations, stops an instance once the
+ * least-squares residual reaches tol * ||b||, and updates x += sum_i y_i z_i. M(v) is
+ * opts->sweeps sweeps of the Table 1 iteration on A z = v from z = 0 (coefficients w,
+ * alpha, alpha_t as in richm_apply_sweeps, in the real type of opts->inner), run in
+ * opts->inner precision; the z_i are kept in that type. b, x: padded complex128
+ * buffers (x: initial guess in, solution out). info: host [batch]. Synchronises
+ * `stream` (the host reads the number of instances still iterating after every step).
+ * Returns RICHM_OK if every instance converged, else RICHM_ERR_DIVERGED if any
+ * diverged, else RICHM_ERR_NOT_CONVERGED; RICHM_ERR_UNSUPPORTED for Q1 instances. */
+richm_status richm_fgmres(richm_operator* op, const void* b, void* x, const void* w, const void* alpha,
+                          const void* alpha_t, const richm_fgmres_opts* opts, richm_fgmres_info* info, void* work,
+                          size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------ differentiation */
 

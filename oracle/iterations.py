@@ -35,6 +35,41 @@ def semi_iteration_weights(lmax: float, m: int, alpha: float = 1.0 / 30.0) -> np
     return chebyshev_weights(lmax, alpha * lmax, m)
 
 
+def leja_order(w) -> np.ndarray:
+    """A Leja ordering of the steps of one period (reading: eqs. 8-9 fix the set of
+    weights, not the order in which the m steps run; the order changes only how FP32
+    rounding is amplified inside a period).
+
+    The steps are ordered by their nodes z_i = 1/w_i, the roots of the period's residual
+    polynomial prod_i (1 - w_i z): first the node of largest |z|, then repeatedly the
+    node that maximises the product of its distances to the nodes already taken
+    (Leja points of a discrete set, after Reichel, BIT 30 (1990) 332-346). Ties go to
+    the smaller index. Returns the permutation: step s of the period uses original
+    index perm[s].
+    Pinned by: brute force over every choice on small sets, and the product bound of
+    Leja points (tests).
+    """
+    z = 1.0 / np.asarray(w, dtype=np.float64)
+    m = z.size
+    left = list(range(m))
+    first = max(left, key=lambda i: (abs(z[i]), -i))
+    perm = [first]
+    left.remove(first)
+    while left:
+        def score(i):
+            p = 1.0
+            for j in perm:  # in the order the nodes were taken (FP64)
+                p *= abs(z[i] - z[j])
+            return p
+        best = left[0]
+        for i in left[1:]:
+            if score(i) > score(best):
+                best = i
+        perm.append(best)
+        left.remove(best)
+    return np.array(perm, dtype=np.int64)
+
+
 def inner_steps(A, f, u, v, w, a=None, at=None, K=1, k_start=0, Binv=None):
     """K inner steps of the Table 1 iteration (NAGex form covers all rows).
 

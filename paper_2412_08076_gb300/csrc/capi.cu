@@ -28,6 +28,21 @@ void clear_error() { g_last_error.clear(); }
 
 static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+// Closed form of the element-assembled Q1 row (Sec. 2.4, eq. 18): q[0..4] = centre,
+// x-neighbour, y-neighbour, corner (+1,+1), corner (+1,-1); q[5] = Gershgorin bound.
+static void q1_stencil(double eps, double theta, double* q) {
+  const double cs = std::cos(theta), sn = std::sin(theta);
+  const double c11 = cs * cs + eps * sn * sn;
+  const double c22 = sn * sn + eps * cs * cs;
+  const double c12 = (1.0 - eps) * sn * cs;
+  q[0] = 4.0 * (c11 + c22) / 3.0;
+  q[1] = (c22 - 2.0 * c11) / 3.0;
+  q[2] = (c11 - 2.0 * c22) / 3.0;
+  q[3] = -(c11 + c22) / 6.0 - 0.5 * c12;
+  q[4] = -(c11 + c22) / 6.0 + 0.5 * c12;
+  q[5] = std::fabs(q[0]) + 2.0 * (std::fabs(q[1]) + std::fabs(q[2]) + std::fabs(q[3]) + std::fabs(q[4]));
+}
+
 richm_status get_tiles(richm_operator* op, int tw, int rows, const TileMap** out) {
   long long key = (long long)tw * 1000003LL + rows;
   auto it = op->tiles.find(key);
@@ -195,18 +210,17 @@ richm_status richm_operator_create(const richm_pde* pdes, int batch, richm_opera
         delete op;
         return set_error(RICHM_ERR_ARG, "instance %d: need 0 < eps <= 1 and finite theta", b);
       }
-      double cs = std::cos(p.theta), sn = std::sin(p.theta);
-      double c11 = cs * cs + p.eps * sn * sn;
-      double c22 = sn * sn + p.eps * cs * cs;
-      double c12 = (1.0 - p.eps) * sn * cs;
-      I.c = 4.0 * (c11 + c22) / 3.0;
-      I.ax = (c22 - 2.0 * c11) / 3.0;
-      I.ay = (c11 - 2.0 * c22) / 3.0;
-      I.d1 = -(c11 + c22) / 6.0 - 0.5 * c12;
-      I.d2 = -(c11 + c22) / 6.0 + 0.5 * c12;
+      double q[6];
+      q1_stencil(p.eps, p.theta, q);
+      I.c = q[0];
+      I.ax = q[1];
+      I.ay = q[2];
+      I.d1 = q[3];
+      I.d2 = q[4];
       I.dinv = 1.0 / I.c;
-      I.G = std::fabs(I.c) + 2.0 * (std::fabs(I.ax) + std::fabs(I.ay) + std::fabs(I.d1) + std::fabs(I.d2));
-    } else if (p.kind == RICHM_HELMHOLTZ_FD5_ABC || p.kind == RICHM_HELMHOLTZ_FD5_DIRICHLET) {
+      I.G = q[5];
+    } else if (p.kind == RICHM_HELMHOLTZ_FD5_ABC || p.kind == RICHM_HELMHOLTZ_FD5_DIRICHLET ||
+               p.kind == RICHM_HELMHOLTZ_FD5_SPONGE) {
       if (!(p.k >= 0.0) || !std::isfinite(p.k)) {
         delete op;
         return set_error(RICHM_ERR_ARG, "instance %d: need finite k >= 0", b);
@@ -222,18 +236,27 @@ richm_status richm_operator_create(const richm_pde* pdes, int batch, richm_opera
         I.abc_re = -(1.0 / den) / (h * h);
         I.abc_im = -(kh / den) / (h * h);
       }
-      // Gershgorin: largest row sum over the row types that exist for this n
+      if (p.kind == RICHM_HELMHOLTZ_FD5_SPONGE && p.k > 0.0) {
+        // eq. 21 with c = 1: i gamma omega on the diagonal, gamma = k max(0, 1 - d / L),
+        // L = 2 pi / k one wavelength, d the distance to the boundary
+        I.sp_im = p.k * p.k;
+        I.sp_iw = h * p.k / (2.0 * 3.14159265358979323846);  // h / L
+      }
+      // Gershgorin: largest row sum over the row types that exist for this n (a node at
+      // distance d >= 2 from the boundary has four neighbours, and its sponge term is at
+      // most that of d = 2)
       double off1 = 1.0 / (h * h);
-      auto rowsum = [&](int missing) {
-        double dr = I.c + missing * I.abc_re, di = missing * I.abc_im;
+      auto rowsum = [&](int missing, int d) {
+        double dr = I.c + missing * I.abc_re;
+        double di = missing * I.abc_im + I.sp_im * std::max(0.0, 1.0 - d * I.sp_iw);
         return std::sqrt(dr * dr + di * di) + (4 - missing) * off1;
       };
       double G = 0.0;
-      if (p.n == 1) G = rowsum(4);
+      if (p.n == 1) G = rowsum(4, 1);
       else {
-        G = std::max(G, rowsum(2));
-        G = std::max(G, rowsum(p.n >= 3 ? 1 : 2));
-        if (p.n >= 3) G = std::max(G, rowsum(0));
+        G = std::max(G, rowsum(2, 1));
+        G = std::max(G, rowsum(p.n >= 3 ? 1 : 2, 1));
+        if (p.n >= 3) G = std::max(G, rowsum(0, 2));
       }
       I.G = G;
       I.dinv = 0.0;
@@ -246,6 +269,7 @@ richm_status richm_operator_create(const richm_pde* pdes, int batch, richm_opera
   }
   op->elems = (size_t)off;
   cudaError_t e = cudaGetDevice(&op->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&op->sms, cudaDevAttrMultiProcessorCount, op->device);
   if (e == cudaSuccess) {
     // kernel attributes, once per device (a stream capture may follow later calls)
     static std::mutex mu;
@@ -295,7 +319,16 @@ richm_status richm_stencil(const richm_operator* op, int instance, double* coef)
     coef[0] = I.c; coef[1] = I.ax; coef[2] = I.ay; coef[3] = I.d1; coef[4] = I.d2;
   } else {
     coef[0] = I.c; coef[1] = I.ax; coef[2] = I.abc_re; coef[3] = I.abc_im;
+    coef[4] = I.sp_im; coef[5] = I.sp_iw > 0.0 ? 1.0 / I.sp_iw : 0.0;
   }
+  return RICHM_OK;
+}
+
+richm_status richm_q1_stencil(double eps, double theta, double* coef) {
+  clear_error();
+  RICHM_ARG(coef != nullptr, "null output");
+  RICHM_ARG(eps > 0.0 && eps <= 1.0 && std::isfinite(theta), "need 0 < eps <= 1 and finite theta");
+  q1_stencil(eps, theta, coef);
   return RICHM_OK;
 }
 

@@ -75,7 +75,9 @@ struct Inst {
   double dinv;    // Q1: 1 / centre
   double G;       // Gershgorin bound
   long long dense_off;  // element offset of the instance in a dense concatenation (n*n each)
-  double pad1[3];
+  double sp_im;   // sponge layer (eq. 21): imaginary diagonal term on the boundary (0: none)
+  double sp_iw;   // 1 / (layer width in grid spacings)
+  double pad1;
 };
 static_assert(sizeof(Inst) == 128, "Inst layout");
 
@@ -100,6 +102,7 @@ struct TileMap {
 
 struct richm_operator {
   int device = 0;
+  int sms = 152;  // multiprocessors of the device (queried at creation)
   int batch = 0;
   std::vector<richm_pde> pdes;
   std::vector<richm::Inst> h_inst;
@@ -314,10 +317,17 @@ __device__ inline void resid_q1(const RowT<double, VW>& U, const RowT<double, VW
 
 // A y of the 5-point Helmholtz stencil (complex E) at the VW points of the centre
 // row; i = interior row index, c0 = first column. The diagonal gains `abc` per
-// neighbour that lies outside the domain (absorbing boundary, ghost eliminated).
+// neighbour that lies outside the domain (absorbing boundary, ghost eliminated) and,
+// in a sponge layer (eq. 21), i sp_im max(0, 1 - d sp_iw) at distance d (in grid
+// spacings) from the boundary.
+template <typename S>
+__device__ __forceinline__ S sponge_im(int i, int col, int n, S sp_im, S sp_iw) {
+  const int d = min(min(i + 1, n - i), min(col + 1, n - col));
+  return sp_im * max((S)0, (S)1 - (S)d * sp_iw);
+}
 template <typename E, int VW, typename S>
 __device__ inline void apply_fd5(const RowT<E, VW>& U, const RowT<E, VW>& C, const RowT<E, VW>& D, int i, int c0,
-                                 int n, S c, S off, S abc_re, S abc_im, E* out) {
+                                 int n, S c, S off, S abc_re, S abc_im, S sp_im, S sp_iw, E* out) {
   int rmiss = (i == 0) + (i == n - 1);
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
@@ -326,7 +336,7 @@ __device__ inline void apply_fd5(const RowT<E, VW>& U, const RowT<E, VW>& C, con
     E cw = (e == 0) ? C.yl : C.y[e - 1];
     E ce = (e == VW - 1) ? C.yr : C.y[e + 1];
     E sum = (cw + ce) + (U.y[e] + D.y[e]);
-    E diag = {c + (S)miss * abc_re, (S)miss * abc_im};
+    E diag = {c + (S)miss * abc_re, (S)miss * abc_im + sponge_im<S>(i, col, n, sp_im, sp_iw)};
     out[e] = cmul(diag, C.y[e]) + off * sum;
   }
 }

@@ -77,6 +77,11 @@ template <typename E, typename RO>
 richm_status launch_residual_to(richm_operator* op, const E* x, const E* b, RO* r_out, double2* partials,
                                 const int* active, cudaStream_t s, bool refinement);
 
+// out = A x in FP64 (written in RO) over rows 1..n of every instance (columns >= n
+// written as zero); the halo rows of out are not touched.
+template <typename E, typename RO>
+richm_status launch_apply_to(richm_operator* op, const E* x, RO* out, cudaStream_t s);
+
 // Bytes of the loss workspace (residual buffer, partials, three per-instance arrays).
 size_t loss_workspace_bytes(richm_operator* op, size_t elem_size, int ntiles);
 

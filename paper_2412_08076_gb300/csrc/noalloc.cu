@@ -7,11 +7,11 @@
 // partial sums; this variant keeps that scratch in file-scope device arrays instead,
 // so the caller passes only inputs and outputs. The arrays live in every GPU that
 // loads this library until the process exits: 1 MiB of FP64 partial sums (at most
-// kMaxTiles warp tiles) and 256 KiB of per-instance tile offsets (at most
+// kMaxTiles warp tiles of 16 rows x one 16-byte vector per lane, i.e. about 134 M FP32,
+// 67 M FP64 or complex64 and 33 M complex128 unknowns, less the padding of each row to
+// the 32-element pitch) and 256 KiB of per-instance tile offsets (at most
 // kMaxInstances instances). The entry point computes the same quantities, with the
 // same kernels' arithmetic and summation order, as richm_residual_norm.
-#include <mutex>
-
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -19,48 +19,69 @@ namespace richm {
 
 constexpr int kMaxTiles = 65536;      // warp tiles (16 rows x 32 lanes x one 16-byte vector)
 constexpr int kMaxInstances = 65536;  // instances per operator
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double2 g_static_partials[kMaxTiles];
 static __device__ __align__(256) int g_static_tile_begin[kMaxInstances + 1];
 
-namespace {
-std::mutex g_symbol_mutex;
-double2* g_partials_ptr[kMaxDevices] = {};
-int* g_begin_ptr[kMaxDevices] = {};
-}  // namespace
-
-// Device addresses of the static arrays on the current device (looked up once per device).
+// Device addresses of the static arrays on the current device, looked up on every call
+// (a host-side query, cheap once the module is loaded): an address kept across calls
+// would go stale if the context were destroyed and made again (cudaDeviceReset), and a
+// kernel given a stale address would fault.
 static richm_status static_scratch(double2** partials, int** begin) {
-  int dev = 0;
-  RICHM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(RICHM_ERR_UNSUPPORTED, "device index %d >= %d", dev, kMaxDevices);
-  std::lock_guard<std::mutex> lock(g_symbol_mutex);
-  if (!g_partials_ptr[dev]) {
-    void* p = nullptr;
-    void* q = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_static_tile_begin);
-    if (e != cudaSuccess)
-      return set_error(RICHM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-    g_partials_ptr[dev] = reinterpret_cast<double2*>(p);
-    g_begin_ptr[dev] = reinterpret_cast<int*>(q);
-  }
-  *partials = g_partials_ptr[dev];
-  *begin = g_begin_ptr[dev];
+  void* p = nullptr;
+  void* q = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_static_tile_begin);
+  if (e != cudaSuccess)
+    return set_error(RICHM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+  *partials = reinterpret_cast<double2*>(p);
+  *begin = reinterpret_cast<int*>(q);
   return RICHM_OK;
 }
 
-// begin[b] = first warp tile of instance b for tiles of `tw` columns x kRows rows.
-__global__ void tile_prefix_kernel(const Inst* insts, int batch, int tw, int* begin) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int acc = 0;
-  for (int b = 0; b < batch; ++b) {
-    begin[b] = acc;
-    const Inst& I = insts[b];
-    acc += ((I.pitch + tw - 1) / tw) * ((I.n + kRows - 1) / kRows);
+constexpr int kPrefixThreads = 1024;
+
+__device__ __forceinline__ int inst_tiles(const Inst& I, int tw) {
+  return ((I.pitch + tw - 1) / tw) * ((I.n + kRows - 1) / kRows);
+}
+
+// begin[b] = first warp tile of instance b for tiles of `tw` columns x kRows rows, and
+// begin[batch] = the total: one block of kPrefixThreads threads, each summing a run of
+// consecutive instances, then a block-wide exclusive scan of the run sums (the total
+// fits an int: the host checks it against kMaxTiles before the launch).
+__global__ void __launch_bounds__(kPrefixThreads) tile_prefix_kernel(const Inst* insts, int batch, int tw,
+                                                                     int* begin) {
+  __shared__ int warp_excl[kPrefixThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int per = (batch + kPrefixThreads - 1) / kPrefixThreads;
+  const int lo = min(t * per, batch), hi = min(lo + per, batch);
+  int own = 0;
+  for (int b = lo; b < hi; ++b) own += inst_tiles(insts[b], tw);
+  int inc = own;  // inclusive scan within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
   }
-  begin[batch] = acc;
+  if (lane == 31) warp_excl[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int tot = warp_excl[lane];  // kPrefixThreads / 32 == 32 warp totals
+    int wi = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    warp_excl[lane] = wi - tot;
+  }
+  __syncthreads();
+  int acc = warp_excl[warp] + inc - own;
+  for (int b = lo; b < hi; ++b) {
+    begin[b] = acc;
+    acc += inst_tiles(insts[b], tw);
+  }
+  if (t == kPrefixThreads - 1) begin[batch] = acc;  // the last run ends at the batch's end
 }
 
 template <typename E> struct WideT { using type = double; };
@@ -134,7 +155,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     load(r + 1, D);
     ED Ax[VW];
     if constexpr (CPLX) {
-      apply_fd5<ED, VW, double>(U, C, D, r - 1, c0, n, I.c, I.ax, I.abc_re, I.abc_im, Ax);
+      apply_fd5<ED, VW, double>(U, C, D, r - 1, c0, n, I.c, I.ax, I.abc_re, I.abc_im, I.sp_im, I.sp_iw, Ax);
     } else {
       apply_q1<ED, VW, double>(U, C, D, I.c, I.ax, I.ay, I.d1, I.d2, Ax);
     }
@@ -200,7 +221,7 @@ static richm_status residual_static_t(richm_operator* op, const E* x, const E* b
   double2* partials = nullptr;
   int* begin = nullptr;
   RICHM_TRY(static_scratch(&partials, &begin));
-  tile_prefix_kernel<<<1, 32, 0, s>>>(op->d_inst, op->batch, tw, begin);
+  tile_prefix_kernel<<<1, kPrefixThreads, 0, s>>>(op->d_inst, op->batch, tw, begin);
   RICHM_LAUNCH_CHECK("tile prefix");
   const int blocks = (int)((nt + kWarpsPerBlock - 1) / kWarpsPerBlock);
   resid_static_kernel<E><<<blocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, op->batch, begin, (int)nt, x, b, r_out,

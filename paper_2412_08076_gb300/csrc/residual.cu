@@ -31,6 +31,7 @@ template <> __device__ inline cplx<double> narrow<cplx<double>, cplx<double>>(cp
 
 // MODE 0: residual (+ optional r_out) and partial sums (|r|^2, |b|^2).
 // MODE 1: out = scale_b * (A x) (used for the loss gradient), no partials.
+// MODE 3: out = A x, no partials (the Krylov solver's products).
 // MODE 2: the solver's refinement residual (real FP64 x and b): b folded into the
 //         stencil's multiply-adds and partial sums (|r|^2, 0), since |b| is known.
 template <typename E, int MODE, typename RO>
@@ -53,9 +54,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int r0 = t.ty * kRows + 1;
   const int r1 = min(r0 + kRows - 1, n);
   const E* xb = x + I.off;
-  const E* bb = (MODE != 1) ? b + I.off : nullptr;
+  const E* bb = (MODE == 0 || MODE == 2) ? b + I.off : nullptr;
   RO* ob = r_out ? r_out + I.off : nullptr;
-  const double sc = (MODE == 1) ? scale[t.inst] : 0.0;
+  const double sc = (MODE == 1) ? scale[t.inst] : 1.0;
 
   auto load = [&](int pr, RowT<ED, VW>& Y) {
     const bool in = (pr >= 1) && (pr <= n);
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     load(r + 1, D);
     ED Ax[VW];
     if constexpr (CPLX) {
-      apply_fd5<ED, VW, double>(U, C, D, r - 1, c0, n, I.c, I.ax, I.abc_re, I.abc_im, Ax);
+      apply_fd5<ED, VW, double>(U, C, D, r - 1, c0, n, I.c, I.ax, I.abc_re, I.abc_im, I.sp_im, I.sp_iw, Ax);
     } else {
       apply_q1<ED, VW, double>(U, C, D, I.c, I.ax, I.ay, I.d1, I.d2, Ax);
     }
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     U = C;
     C = D;
   }
-  if (MODE != 1) {
+  if (MODE == 0 || MODE == 2) {
     sr = warp_sum(sr);
     sb = warp_sum(sb);
     if (lane == 0) partials[wt] = make_double2(sr, sb);
@@ -213,6 +214,21 @@ static richm_status launch_scaled_apply(richm_operator* op, const E* x, E* out, 
   RICHM_LAUNCH_CHECK("scaled stencil");
   return RICHM_OK;
 }
+
+template <typename E, typename RO>
+richm_status launch_apply_to(richm_operator* op, const E* x, RO* out, cudaStream_t s) {
+  const TileMap* tm = nullptr;
+  RICHM_TRY(get_tiles(op, 32 * VecWidth<E>::value, kRows, &tm));
+  const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  resid_kernel<E, 3, RO><<<blocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, x, nullptr,
+                                                                out, nullptr, nullptr, nullptr);
+  RICHM_LAUNCH_CHECK("stencil product");
+  return RICHM_OK;
+}
+template richm_status launch_apply_to<cplx<float>, cplx<double>>(richm_operator*, const cplx<float>*, cplx<double>*,
+                                                                 cudaStream_t);
+template richm_status launch_apply_to<cplx<double>, cplx<double>>(richm_operator*, const cplx<double>*,
+                                                                  cplx<double>*, cudaStream_t);
 
 richm_status launch_norm_reduce(richm_operator* op, int residual_vw, const double2* partials, double* rnorm,
                                 double* bnorm, double* rel, cudaStream_t s) {

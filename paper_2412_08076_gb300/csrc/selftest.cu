@@ -57,10 +57,14 @@ richm_status richm_selftest_conversions(long long* mismatches) {
   RICHM_ARG(mismatches != nullptr, "null output");
   unsigned long long* d = nullptr;
   RICHM_CUDA_TRY(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+  int dev = 0, sms = 0;
   cudaError_t e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    widen_check_kernel<<<152 * 8, 256>>>(d);
-    narrow_check_kernel<<<152 * 8, 256>>>(d + 1);
+    // grid-stride loops: eight blocks per multiprocessor
+    widen_check_kernel<<<sms * 8, 256>>>(d);
+    narrow_check_kernel<<<sms * 8, 256>>>(d + 1);
     e = cudaGetLastError();
   }
   unsigned long long h[2] = {0, 0};

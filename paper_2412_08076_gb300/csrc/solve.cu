@@ -417,7 +417,7 @@ static richm_status cycle_t(richm_solver* S, long long k0, long long cycle) {
 // Fused tile height (the tuned height halved down to 16 rows) for the instances
 // still iterating, from a wave model of the
 // fused pass: its tiles form blocks (4 one-warp tiles at 4 sweeps per pass, 2 two-warp
-// tiles at 8), which run in waves of 152 SMs x K resident blocks (K = 4 and 3, set by
+// tiles at 8), which run in waves of (SM count) x K resident blocks (K = 4 and 3, set by
 // the registers); a wave takes rows + 2 TL row steps, and a row step takes 1 + 0.65 (k - 1) times its
 // single-block time when k blocks share an SM (fitted to GB300 timings of both pass
 // lengths over 1..77 instances of 511^2 and the 256-instance mix, where it picks
@@ -438,11 +438,12 @@ static double fused_pass_cost(const richm_solver* S, int rows) {
     nmax = std::max(nmax, n);
   }
   const long long blocks = (warps + per_block - 1) / per_block;
-  const long long wave = 152LL * K;
+  const long long sms = op->sms;
+  const long long wave = sms * K;
   const long long full = blocks / wave, rem = blocks % wave;
   const double per_wave = 1.0 + 0.65 * (K - 1);
   double cost = (double)full * per_wave;
-  if (rem > 0) cost += 1.0 + 0.65 * (double)((rem + 151) / 152 - 1);
+  if (rem > 0) cost += 1.0 + 0.65 * (double)((rem + sms - 1) / sms - 1);
   const int steps = (std::min(rows, nmax) + 2 * TL + 3) / 3 * 3;
   return cost * steps;
 }

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) sweep1_kernel(const Sw
   }
   const S sc = (S)I.c, sax = (S)I.ax, say = (S)I.ay, sd1 = (S)I.d1, sd2 = (S)I.d2;
   const S sabr = (S)I.abc_re, sabi = (S)I.abc_im, sdinv = (S)I.dinv;
+  const S sspi = (S)I.sp_im, sspw = (S)I.sp_iw;
   const int c0 = t.tx * 32 * VW + lane * VW;
   const bool live = c0 < pitch;
   const int r0 = t.ty * kRows + 1;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) sweep1_kernel(const Sw
     *reinterpret_cast<uint4*>(&Bv) = br[((r + 1) & (kS1Slots - 1)) * BC + lane];
     E Ay[VW];
     if constexpr (CPLX) {
-      apply_fd5<E, VW, S>(U, C, D, r - 1, c0, n, sc, sax, sabr, sabi, Ay);
+      apply_fd5<E, VW, S>(U, C, D, r - 1, c0, n, sc, sax, sabr, sabi, sspi, sspw, Ay);
     } else {
       apply_q1<E, VW, S>(U, C, D, sc, sax, say, sd1, sd2, Ay);
     }
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) sweep1_kernel(const Sw
       if (PRE) {
         if constexpr (CPLX) {
           int miss = (r == 1) + (r == n) + (col == 0) + (col == n - 1);
-          E diag = {sc + (S)miss * sabr, (S)miss * sabi};
+          E diag = {sc + (S)miss * sabr, (S)miss * sabi + sponge_im<S>(r - 1, col, n, sspi, sspw)};
           res = cdiv(res, diag);
         } else {
           res = sdinv * res;
@@ -483,6 +484,12 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
     else o.fuse = 1;
   }
   if (o.precond == 2) o.fuse = 1;  // the triangular solves cannot be fused in time
+  if (dtype == RICHM_C64 || dtype == RICHM_C128) {
+    // the fused complex kernel covers the absorbing and Dirichlet boundaries; a sponge
+    // layer's per-node diagonal runs one sweep per pass
+    for (int b = 0; b < op->batch; ++b)
+      if (op->h_inst[b].kind == RICHM_HELMHOLTZ_FD5_SPONGE) o.fuse = 1;
+  }
   opts = &o;
   switch (dtype) {
     case RICHM_BF16: {

@@ -28,11 +28,10 @@ PARAM_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "params")
 
 
 def chebyshev_unit_weights(m: int, stretch: float = STABLE_STRETCH, alpha: float = SEMI_ALPHA) -> np.ndarray:
-    """G * w_i for eqs. 8-9 on [alpha s G, s G] (independent of G)."""
-    i = np.arange(1, m + 1)
-    x = np.cos((2 * i - 1) * math.pi / (2 * m))
-    lmax, lmin = stretch, alpha * stretch
-    return 2.0 / (lmax + lmin + (lmax - lmin) * x)
+    """G * w_i for eqs. 8-9 on [alpha s G, s G] (independent of G), from the library's
+    richm_chebyshev_weights with G = 1."""
+    from . import richm
+    return np.array(richm.chebyshev_weights(stretch, alpha * stretch, m))
 
 
 HEAD_NAG_SHARED, HEAD_RICHARDSON, HEAD_MOM, HEAD_NAG, HEAD_NAGEX = 0, 1, 2, 3, 4
@@ -56,15 +55,28 @@ def stable_stretch(m: int, beta: float, lookahead: bool, step: float = 0.05, top
 
 
 def init_params(m: int = 16, beta: float = 0.3, seed: int = 7, out_scale: float = 0.01,
-                head: int = HEAD_NAG_SHARED) -> np.ndarray:
-    """Flat FP32 parameter vector in the library's order (W1, b1, W2, b2, W3, b3)."""
+                head: int = HEAD_NAG_SHARED, stretch: float = STABLE_STRETCH, leja: bool = False,
+                fixed_beta: bool = False) -> np.ndarray:
+    """Flat FP32 parameter vector in the library's order (W1, b1, W2, b2, W3, b3).
+
+    Shared-momentum head options: `stretch` of the Chebyshev interval, `leja` to start the
+    weights in the library's Leja step order (richm_leja_order) instead of index order,
+    and `fixed_beta` to make the momentum output the constant `beta` (its weight row
+    zero; training then leaves it untouched, see train.Trainer)."""
     import richm_synth as synth  # seeded generator shared by every consumer
     layers = synth.mlp_init((2, HIDDEN, HIDDEN, head_outputs(head, m)), seed=seed)
     W3, b3 = layers[2]
     W3 = W3 * out_scale
     logit = math.log(beta / (1.0 - beta))
     if head == HEAD_NAG_SHARED:
-        b3 = np.concatenate([np.log(chebyshev_unit_weights(m)), [logit]])
+        unit = chebyshev_unit_weights(m, stretch)
+        if leja:
+            from . import richm
+            unit = unit[richm.leja_order(unit)]
+        b3 = np.concatenate([np.log(unit), [logit]])
+        if fixed_beta:
+            W3 = np.array(W3, copy=True)
+            W3[m, :] = 0.0
     elif head == HEAD_RICHARDSON:
         b3 = np.log(chebyshev_unit_weights(m, 1.0))
     else:
@@ -79,35 +91,30 @@ def init_params(m: int = 16, beta: float = 0.3, seed: int = 7, out_scale: float 
     return np.concatenate(flat).astype(np.float32)
 
 
-def trained_path(m: int, head: int = HEAD_NAG_SHARED, precond: int = 0) -> str:
+def trained_path(m: int, head: int = HEAD_NAG_SHARED, precond: int = 0, variant: str = "") -> str:
+    """Where the trained network of a head is kept; variant "beta03" is the m = 16 network
+    trained with its momentum held at 0.3."""
     if head == HEAD_NAG_SHARED and precond == 0:
-        return os.path.join(PARAM_DIR, f"meta_m{m}.npy")
+        return os.path.join(PARAM_DIR, f"meta_m{m}{'_' + variant if variant else ''}.npy")
     return os.path.join(PARAM_DIR, f"meta_m{m}_head{head}_precond{precond}.npy")
 
 
 def load_params(m: int = 16, prefer_trained: bool = True, head: int = HEAD_NAG_SHARED,
-                precond: int = 0) -> tuple[np.ndarray, str]:
+                precond: int = 0, variant: str = "") -> tuple[np.ndarray, str]:
     """(params, source): the trained network if one was saved, else the initial one."""
-    p = trained_path(m, head, precond)
+    p = trained_path(m, head, precond, variant)
     if prefer_trained and os.path.exists(p):
         return np.load(p).astype(np.float32), "trained"
     return init_params(m, head=head), "initial"
 
 
 def symbol_max(eps: float, theta: float, grid: int = 513) -> float:
-    """Upper bound on the Q1 operator's spectrum: the maximum of the stencil's Fourier
-    symbol c + 2 ax cos x + 2 ay cos y + 2 d1 cos(x + y) + 2 d2 cos(x - y) over
+    """Upper bound on the Q1 operator's spectrum: the maximum of the library's stencil's
+    Fourier symbol c + 2 ax cos x + 2 ay cos y + 2 d1 cos(x + y) + 2 d2 cos(x - y) over
     x in [0, pi], y in [-pi, pi] (a symmetric Toeplitz-block-Toeplitz matrix's
     eigenvalues lie within the range of its symbol)."""
-    c, s = math.cos(theta), math.sin(theta)
-    c11 = c * c + eps * s * s
-    c22 = s * s + eps * c * c
-    c12 = (1.0 - eps) * s * c
-    cen = 4.0 * (c11 + c22) / 3.0
-    ax = (c22 - 2.0 * c11) / 3.0
-    ay = (c11 - 2.0 * c22) / 3.0
-    d1 = -(c11 + c22) / 6.0 - 0.5 * c12
-    d2 = -(c11 + c22) / 6.0 + 0.5 * c12
+    from . import richm
+    cen, ax, ay, d1, d2, _ = richm.q1_stencil(eps, theta)  # the library's stencil (host)
     x = np.linspace(0.0, math.pi, grid)
     y = np.linspace(-math.pi, math.pi, 2 * grid - 1)
     X, Y = np.meshgrid(x, y, indexing="ij")

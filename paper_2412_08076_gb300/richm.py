@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "librichm.so")
 # richm_status
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_UNSUPPORTED = range(7)
 # richm_problem
-ANISO_Q1, HELMHOLTZ_FD5_ABC, HELMHOLTZ_FD5_DIRICHLET = 0, 1, 2
+ANISO_Q1, HELMHOLTZ_FD5_ABC, HELMHOLTZ_FD5_DIRICHLET, HELMHOLTZ_FD5_SPONGE = 0, 1, 2, 3
 # richm_dtype
 F64, F32, C64, C128, BF16 = 0, 1, 2, 3, 4
 HEAD_NAG_SHARED, HEAD_RICHARDSON, HEAD_MOM, HEAD_NAG, HEAD_NAGEX = 0, 1, 2, 3, 4
@@ -58,6 +58,15 @@ class richm_solve_info(C.Structure):
     _fields_ = [("sweeps", C.c_longlong), ("rel_res", C.c_double), ("status", C.c_int)]
 
 
+class richm_fgmres_opts(C.Structure):
+    _fields_ = [("restart", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int), ("m", C.c_int),
+                ("sweeps", C.c_int), ("inner", C.c_int), ("precond", C.c_int)]
+
+
+class richm_fgmres_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_res", C.c_double), ("status", C.c_int)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -69,6 +78,12 @@ _SIGS = {
     "richm_stencil": (_I, [_P, _I, C.POINTER(_D)]),
     "richm_gershgorin": (_I, [_P, C.POINTER(_D)]),
     "richm_chebyshev_weights": (_I, [_D, _D, _I, C.POINTER(_D)]),
+    "richm_q1_stencil": (_I, [_D, _D, C.POINTER(_D)]),
+    "richm_fgmres_workspace": (_I, [_P, C.POINTER(richm_fgmres_opts), C.POINTER(_SZ)]),
+    "richm_fgmres": (_I, [_P, _P, _P, _P, _P, _P, C.POINTER(richm_fgmres_opts), C.POINTER(richm_fgmres_info), _P,
+                          _SZ, _P]),
+    "richm_leja_order": (_I, [C.POINTER(_D), _I, C.POINTER(_I)]),
+    "richm_leja_permute": (_I, [_P, _I, _P, _P, _P, _I, _P, _P, _P, _P]),
     "richm_layout": (_I, [_P, _I, C.POINTER(_SZ), C.POINTER(_I), C.POINTER(_I)]),
     "richm_buffer_elems": (_I, [_P, C.POINTER(_SZ)]),
     "richm_pack": (_I, [_P, _I, _P, _P, _P]),
@@ -187,6 +202,22 @@ def chebyshev_weights(lmax: float, lmin: float, m: int) -> list[float]:
     return list(out)
 
 
+def q1_stencil(eps: float, theta: float) -> list[float]:
+    """richm_q1_stencil (Sec. 2.4), host: [centre, x-nbr, y-nbr, corner(+1,+1), corner(+1,-1), Gershgorin]."""
+    out = (C.c_double * 6)()
+    _check(load().richm_q1_stencil(eps, theta, out), "richm_q1_stencil")
+    return list(out)
+
+
+def leja_order(w) -> list[int]:
+    """richm_leja_order, host: perm[s] = the step that runs at position s of the period."""
+    m = len(w)
+    wa = (C.c_double * m)(*[float(v) for v in w])
+    out = (C.c_int * m)()
+    _check(load().richm_leja_order(wa, m, out), "richm_leja_order")
+    return list(out)
+
+
 def meta_param_count(m: int, head: int = HEAD_NAG_SHARED) -> int:
     c = C.c_int()
     _check(load().richm_meta_param_count(m, head, C.byref(c)), "richm_meta_param_count")
@@ -294,6 +325,36 @@ class Operator:
         _check(load().richm_apply_sweeps(self.handle, dtype, _ptr(x), _ptr(x_prev), _ptr(b), _ptr(w), _ptr(alpha),
                                          _ptr(alpha_t), K, C.byref(o), _ptr(work), work.numel(), _stream(stream)),
                "richm_apply_sweeps")
+
+    def fgmres(self, b, x, w=None, alpha=None, alpha_t=None, restart=20, tol=1e-6, max_iters=1000, m=None,
+               sweeps=None, inner=C64, precond=0, work=None, stream=None):
+        """richm_fgmres (Sec. 3.2, Table 9): b, x padded complex128 (x: guess in, solution
+        out); the preconditioner is `sweeps` Table 1 sweeps with coefficients w, alpha,
+        alpha_t ([batch][m], real type of `inner`); returns (status, [(iters, rel_res, status)])."""
+        if m is None:
+            m = w.numel() // self.batch if w is not None else 1
+        if sweeps is None:
+            sweeps = m if w is not None else 0
+        o = richm_fgmres_opts(restart, tol, max_iters, m, sweeps, inner, precond)
+        need = C.c_size_t()
+        _check(load().richm_fgmres_workspace(self.handle, C.byref(o), C.byref(need)), "richm_fgmres_workspace")
+        if work is None:
+            work = self.workspace(need.value)
+        info = (richm_fgmres_info * self.batch)()
+        st = load().richm_fgmres(self.handle, _ptr(b), _ptr(x), _ptr(w), _ptr(alpha), _ptr(alpha_t), C.byref(o), info,
+                                 _ptr(work), work.numel(), _stream(stream))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+            _check(st, "richm_fgmres")
+        return st, [(info[i].iters, info[i].rel_res, info[i].status) for i in range(self.batch)]
+
+    def leja_permute(self, dtype, w, alpha=None, alpha_t=None, stream=None):
+        """richm_leja_permute: per-instance Leja reordering of the coefficient arrays
+        [batch][m] (device); returns new tensors (w, alpha, alpha_t), None where not given."""
+        m = w.numel() // self.batch
+        outs = [None if t is None else torch.empty_like(t) for t in (w, alpha, alpha_t)]
+        _check(load().richm_leja_permute(self.handle, dtype, _ptr(w), _ptr(alpha), _ptr(alpha_t), m, _ptr(outs[0]),
+                                         _ptr(outs[1]), _ptr(outs[2]), _stream(stream)), "richm_leja_permute")
+        return tuple(outs)
 
     def autotune(self, m=16, momentum=True, stream=None):
         """richm_autotune: pick sweeps per pass for FP32 sweeps; returns (fuse, ms per sweep)."""
@@ -428,12 +489,32 @@ class Solver:
         need = C.c_size_t()
         _check(load().richm_solve_workspace(op.handle, C.byref(opts), C.byref(need)), "richm_solve_workspace")
         self.work = work if work is not None else op.workspace(need.value)
+        self.need = need.value
+        self.opts = opts
         self.keep = (w, alpha, alpha_t)
         self.op = op
         h = C.c_void_p()
         _check(load().richm_solver_create(op.handle, C.byref(opts), _ptr(w), _ptr(alpha), _ptr(alpha_t),
                                           _ptr(self.work), self.work.numel(), C.byref(h)), "richm_solver_create")
         self.handle = h
+
+    def views(self):
+        """Views into the session's workspace (the layout richm_solve_workspace documents):
+        (inner-state buffers [4], inner right-hand side, second FP64 solution buffer or None)."""
+        o = self.opts
+        el = self.op.elems
+        es = {F64: 8, F32: 4, BF16: 2}[o.inner]
+        E = (el * es + 255) // 256 * 256
+        st = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}[o.inner]
+        bufs = [self.work[j * E: j * E + el * es].view(st) for j in range(4)]
+        rs = 8 if o.inner == F64 else 4
+        rhs = self.work[4 * E: 4 * E + el * rs].view(torch.float64 if rs == 8 else torch.float32)
+        x2 = None
+        if o.inner != F64:
+            X2 = (el * 8 + 255) // 256 * 256
+            need = self.need
+            x2 = self.work[need - X2: need - X2 + el * 8].view(torch.float64)
+        return bufs, rhs, x2
 
     def start(self, b, x, stream=None, zero=False):
         self.bx = (b, x)

@@ -5,10 +5,13 @@ checkpoints (library forward), loss = mean log relative residual and its gradien
 (library), adjoint sweeps (library), network backward and Adam (library). Python only
 sequences the calls. The network's head selects the Table 1 method (Richardson, MOM,
 NAG, NAGex; shared or per-step momenta) and --precond 2 the SSOR preconditioner. The
-committed m = 16 network comes from two stages:
+committed m = 16 networks come from two stages each (the first stage's output is not kept):
   python -m paper_2412_08076_gb300.train --steps 1500 --out stage1.npy
   python -m paper_2412_08076_gb300.train --finetune-from stage1.npy --out paper_2412_08076_gb300/params/meta_m16.npy
-(stage 1 is kept as params/meta_m16_stage1.npy).
+and, with the momentum held at 0.3 and Leja-ordered initial weights (the benchmark's network),
+  python -m paper_2412_08076_gb300.train --steps 1500 --fixed-beta 0.3 --stretch 1.2 --leja --out stage1.npy
+  python -m paper_2412_08076_gb300.train --finetune-from stage1.npy --fixed-beta 0.3 --stop 750 \
+      --out paper_2412_08076_gb300/params/meta_m16_beta03.npy
 """
 from __future__ import annotations
 
@@ -46,8 +49,9 @@ class Trainer:
     since the spectrum of B^{-1} A lies in (0, 1]."""
 
     def __init__(self, params: np.ndarray, m=16, K=64, every=8, lr=2e-3, precond=0, relax=1.0,
-                 head=richm.HEAD_NAG_SHARED):
+                 head=richm.HEAD_NAG_SHARED, fixed_beta=False):
         self.m, self.K, self.every, self.lr = m, K, every, lr
+        self.fixed_beta = fixed_beta  # the momentum output gets no gradient (held at its initial value)
         self.precond, self.relax, self.head = precond, relax, head
         self.P = torch.tensor(params, dtype=torch.float32, device="cuda")
         self.m1 = torch.zeros_like(self.P)
@@ -85,6 +89,8 @@ class Trainer:
         gat = W["gat"] if self.head == richm.HEAD_NAGEX else None
         op.sweeps_adjoint(richm.F32, W["ck"], self.every, batch.b, W["g"], w, a, at, self.m, self.K, self.precond,
                           W["gw"], W["ga"] if a is not None else None, gat, None, work=W["work"], relax=self.relax)
+        if self.fixed_beta and a is not None:
+            W["ga"].zero_()
         gP = richm.meta_backward(self.P, batch.X, G, W["acts"], self.m, W["gw"], W["ga"], W["gP"], W["mwork"],
                                  head=self.head, g_alpha_t=gat)
         return loss, gP
@@ -112,12 +118,19 @@ def make_batches(nbatches=8, B=64, n=255, seed=1000, log_eps=(-3.0, 0.0), normal
     return out
 
 
-def train(steps=1000, lr=2e-3, nbatches=8, n=255, log_every=100, verbose=True, K=64):
+def train(steps=1000, lr=2e-3, nbatches=8, n=255, log_every=100, verbose=True, K=64, fixed_beta=None,
+          stretch=meta_mod.STABLE_STRETCH, leja=False):
     """Algorithm 1 with the config-3 workload (64 instances of n x n per batch, K = 64,
     checkpoints every 8) from the initial network; cosine-decayed Adam step size.
+    fixed_beta: hold the momentum at this value (the network's momentum output is the
+    constant, untrained). stretch, leja: the initial weights (meta.init_params).
     Deterministic: seeded data, fixed-order kernels. Returns (params, loss history)."""
-    params, _ = meta_mod.load_params(16, prefer_trained=False)
-    tr = Trainer(params, K=K, lr=lr)
+    if fixed_beta is None and stretch == meta_mod.STABLE_STRETCH and not leja:
+        params, _ = meta_mod.load_params(16, prefer_trained=False)
+    else:
+        params = meta_mod.init_params(16, beta=0.3 if fixed_beta is None else fixed_beta, stretch=stretch,
+                                      leja=leja, fixed_beta=fixed_beta is not None)
+    tr = Trainer(params, K=K, lr=lr, fixed_beta=fixed_beta is not None)
     batches = make_batches(nbatches, n=n)
     hist = []
     t0 = time.time()
@@ -131,7 +144,8 @@ def train(steps=1000, lr=2e-3, nbatches=8, n=255, log_every=100, verbose=True, K
     return tr.params(), hist
 
 
-def finetune(params, steps=2000, stop=1250, K=128, lr=1e-3, log_every=250, verbose=True):
+def finetune(params, steps=2000, stop=1250, K=128, lr=1e-3, log_every=250, verbose=True, fixed_beta=False,
+             save_every=0, save_prefix=None):
     """Second training stage of the committed m = 16 network: from `params`, alternate
     batches of 64 x 255^2 and 32 x 511^2 instances (seeds 7000 and 7100, four of each),
     K = 128 unrolled sweeps, checkpoints every 8, Adam with a cosine step size over
@@ -141,7 +155,7 @@ def finetune(params, steps=2000, stop=1250, K=128, lr=1e-3, log_every=250, verbo
     checks of tests/test_meta_stability_cpu.py) and that converged on every instance of
     four 256-instance batches; later checkpoints of this run lowered the loss further but
     left a few (eps, theta) with a transfer radius above 1 and a diverging instance."""
-    tr = Trainer(params, K=K, every=8, lr=lr)
+    tr = Trainer(params, K=K, every=8, lr=lr, fixed_beta=fixed_beta)
     b255 = make_batches(4, B=64, n=255, seed=7000)
     b511 = make_batches(4, B=32, n=511, seed=7100)
     hist = []
@@ -152,6 +166,8 @@ def finetune(params, steps=2000, stop=1250, K=128, lr=1e-3, log_every=250, verbo
             hist.append((s + 1, float(loss.item())))
             if verbose:
                 print(f"step {s + 1:5d} loss {hist[-1][1]:.4f}", flush=True)
+        if save_every and save_prefix and (s + 1) % save_every == 0:
+            np.save(f"{save_prefix}_{s + 1}.npy", tr.params())
     return tr.params(), hist
 
 
@@ -165,11 +181,19 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="where to save the parameters (.npy)")
     ap.add_argument("--finetune-from", default=None,
                     help="run the second stage (finetune) from these parameters instead of training from scratch")
+    ap.add_argument("--fixed-beta", type=float, default=None, help="hold the momentum at this value")
+    ap.add_argument("--stretch", type=float, default=meta_mod.STABLE_STRETCH, help="initial Chebyshev stretch")
+    ap.add_argument("--leja", action="store_true", help="initial weights in Leja step order")
+    ap.add_argument("--stop", type=int, default=1250, help="finetune: stop after this many steps")
+    ap.add_argument("--save-every", type=int, default=0, help="finetune: save parameters every this many steps")
     args = ap.parse_args(argv)
     if args.finetune_from:
-        params, hist = finetune(np.load(args.finetune_from).astype(np.float32))
+        params, hist = finetune(np.load(args.finetune_from).astype(np.float32), stop=args.stop,
+                                fixed_beta=args.fixed_beta is not None, save_every=args.save_every,
+                                save_prefix=args.out[:-4] if args.out and args.save_every else None)
     else:
-        params, hist = train(args.steps, args.lr, args.batches, args.n, K=args.K)
+        params, hist = train(args.steps, args.lr, args.batches, args.n, K=args.K, fixed_beta=args.fixed_beta,
+                             stretch=args.stretch, leja=args.leja)
     if args.out:
         os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
         np.save(args.out, params)

@@ -21,3 +21,11 @@ def lib():
         pytest.skip("no CUDA device")
     from paper_2412_08076_gb300 import richm
     return richm
+
+
+@pytest.fixture(scope="session")
+def built_lib():
+    """Build librichm.so (nvcc cross-compiles without a GPU) for tests that call its
+    host-only entry points."""
+    from paper_2412_08076_gb300.build import build
+    return build()

@@ -72,11 +72,11 @@ def period_amplification(w, a, at, G, k_start, K, npts=4001):
     return amps
 
 
-def fp32_bound(w, a, at, G, k_start, K, xmax, bmax):
-    """Rounding bound for K FP32 sweeps started from the same state as an FP64 run:
+def fp32_bound(w, a, at, G, k_start, K, xmax, bmax, u=2.0 ** -24):
+    """Rounding bound for K sweeps in a precision of unit roundoff u (FP32 by default)
+    started from the same state as an exact run:
     16 u sum_k amp_k ((1+|a|+|at|) |x| + |w| (|b| + G (1+2|at|) |x|)), with amp_k the
     largest per-mode transfer norm from sweep k+1 to the end."""
-    u = 2.0 ** -24
     amps = period_amplification(w, a, at, G, k_start, K)
     tot = 0.0
     for k in range(K):

@@ -50,10 +50,12 @@ def test_max_and_sum_over_two_gloo_ranks(tmp_path):
 
 
 def test_weak_scaling_value_arithmetic():
-    # value = (all ranks' dof-sweeps) / (max over ranks of the time)
+    # value = (all ranks' dof-sweeps) / (max over ranks of the time); one step solves a
+    # rank's batch to tolerance, so its dof-sweeps are sum_b sweeps_b n_b^2
     sys.path.insert(0, ROOT)
     import bench
-    dofs, steps, ms = 1.0e7, 10, 250.0
-    assert bench.REFINE == 256  # sweeps per step (one refinement cycle)
-    v = dofs * 2 * bench.REFINE * steps / (ms / 1e3) / 1e9
-    assert abs(v - 2 * dofs * 256 * 10 / 0.25 / 1e9) < 1e-9
+    assert (bench.M, bench.BETA, bench.REFINE, bench.TOL) == (16, 0.3, 64, 1e-10)  # the stated configuration
+    per_step = [3.0e9, 2.0e9]  # two ranks' dof-sweeps per solve
+    steps, ms_max = 10, 4000.0
+    v = sum(per_step) * steps / (ms_max / 1e3) / 1e9
+    assert abs(v - 12.5) < 1e-12

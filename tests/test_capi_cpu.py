@@ -95,3 +95,29 @@ def test_argument_errors_before_any_device_work(clib):
     assert lib.richm_operator_create(arr, 1, ctypes.byref(h)) == richm.ERR_ARG
     assert lib.richm_operator_create(arr, 0, ctypes.byref(h)) == richm.ERR_ARG
     assert h.value is None
+
+
+def test_leja_order_matches_oracle_and_q1_stencil(clib):
+    # host-only entries: the Leja permutation (bit-exact integers) and the Q1 stencil
+    from oracle.iterations import chebyshev_weights, leja_order
+    from oracle.operators import assemble_q1, gershgorin_max
+    rng = np.random.default_rng(12)
+    for m in (1, 3, 8, 16, 64):
+        for w in (chebyshev_weights(3.0, 0.1, m), 1.0 / rng.uniform(0.05, 4.0, m),
+                  rng.uniform(0.1, 1.0, m).astype(np.float32).astype(np.float64)):
+            wa = (ctypes.c_double * m)(*w)
+            perm = (ctypes.c_int * m)()
+            assert clib.richm_leja_order(wa, m, perm) == 0
+            assert list(perm) == list(leja_order(w))
+    bad = (ctypes.c_double * 2)(1.0, 0.0)
+    assert clib.richm_leja_order(bad, 2, (ctypes.c_int * 2)()) == 1
+    clib.richm_q1_stencil.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    for eps, th in [(1e-2, math.pi / 6), (1.0, 0.0), (0.3, 2.2)]:
+        q = (ctypes.c_double * 6)()
+        assert clib.richm_q1_stencil(eps, th, q) == 0
+        A = assemble_q1(5, eps, th).toarray()
+        row = A[12].reshape(5, 5)  # interior unknown (2, 2): rows are y, columns x
+        np.testing.assert_allclose([q[0], q[1], q[2], q[3], q[4]],
+                                   [row[2, 2], row[2, 3], row[3, 2], row[3, 3], row[1, 3]], rtol=1e-13, atol=1e-15)
+        assert abs(q[5] - gershgorin_max(assemble_q1(7, eps, th))) <= 1e-13 * q[5]
+    assert clib.richm_q1_stencil(0.0, 0.0, (ctypes.c_double * 6)()) == 1

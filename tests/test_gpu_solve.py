@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import richm_synth as synth
-from gpu_util import coef, from_dev, make_op, nag_weights, to_dev
+from gpu_util import coef, fp32_bound, from_dev, make_op, nag_weights, to_dev
 from oracle.iterations import inner_steps, refined_steps
 from oracle.operators import assemble_helmholtz, assemble_q1, gershgorin_max, helmholtz_wavenumber
 from paper_2412_08076_gb300 import richm
@@ -139,21 +139,37 @@ def test_solve_graph_and_plain_launches_agree_bitwise():
 
 def test_fp64_inner_solver_follows_the_oracle_iteration():
     # tol = 0: every instance runs exactly max_sweeps; FP64 inner sweeps with FP64
-    # refinement are the same iteration as the oracle's plain sweeps
+    # refinement are the same iteration as the oracle's plain sweeps.
+    # (a) Steps that damp every mode (w lambda in (0, 1.5], momentum 0.3): FP64 rounding is
+    # not amplified, and the solver matches the oracle to 1e-12 after 160 sweeps.
+    # (b) The momentum-aware Chebyshev weights (w lambda up to ~24): the rounding made at a
+    # sweep is carried by the long later steps of its period (per-mode factors up to ~1e4),
+    # so two FP64 evaluation orders of the same iteration differ by more than 1e-12; the
+    # oracle's own split and unsplit runs do too. There the state is held to the rounding
+    # bound derived from the arithmetic with the FP64 unit roundoff.
     insts, op, As, w, a, bs = _solve_setup([9, 31, 70])
+    G = np.array([gershgorin_max(A) for A in As])
+    rng = np.random.default_rng(17)
+    mild = rng.uniform(0.3, 1.5, w.shape) / G[:, None]
     B = to_dev(op, bs, richm.F64)
-    X = op.zeros(richm.F64)
-    opts = op.solve_opts(16, tol=0.0, max_sweeps=160, refine_every=32, inner=richm.F64)
-    st, info = op.solve(B, X, coef(w, richm.F64), coef(a, richm.F64), None, opts)
-    assert st == richm.ERR_NOT_CONVERGED
-    xs = from_dev(op, X, richm.F64)
-    for i, t in enumerate(insts):
-        ref, _ = inner_steps(As[i], bs[i].ravel(), np.zeros(t.n * t.n), None, w[i], a[i], K=160)
-        split = refined_steps(As[i], bs[i].ravel(), np.zeros(t.n * t.n), 160, w[i], a[i], refine_every=32)
-        assert info[i][0] == 160
-        assert np.linalg.norm(xs[i].ravel() - ref) <= 1e-11 * np.linalg.norm(ref)
-        # FP64 rounding inside a period is amplified by the large Chebyshev steps
-        assert np.linalg.norm(split - ref) <= 1e-11 * np.linalg.norm(ref)
+    for case, wc in (("mild", mild), ("chebyshev", w)):
+        X = op.zeros(richm.F64)
+        opts = op.solve_opts(16, tol=0.0, max_sweeps=160, refine_every=32, inner=richm.F64)
+        st, info = op.solve(B, X, coef(wc, richm.F64), coef(a, richm.F64), None, opts)
+        assert st == richm.ERR_NOT_CONVERGED
+        xs = from_dev(op, X, richm.F64)
+        for i, t in enumerate(insts):
+            ref, _ = inner_steps(As[i], bs[i].ravel(), np.zeros(t.n * t.n), None, wc[i], a[i], K=160)
+            assert info[i][0] == 160
+            err = np.abs(xs[i].ravel() - ref).max() / np.abs(ref).max()
+            if case == "mild":
+                assert err <= 1e-12, (t.n, err)
+            else:
+                bound = fp32_bound(wc[i], a[i], None, G[i], 0, 160, np.abs(ref).max(), np.abs(bs[i]).max(),
+                                   u=2.0 ** -53) / np.abs(ref).max()
+                split = refined_steps(As[i], bs[i].ravel(), np.zeros(t.n * t.n), 160, wc[i], a[i], refine_every=32)
+                assert err <= bound, (t.n, err, bound)
+                assert np.abs(split - ref).max() / np.abs(ref).max() <= bound
 
 
 @pytest.mark.parametrize("fuse", [1, 8])

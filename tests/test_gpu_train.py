@@ -363,3 +363,52 @@ def test_head_training_lowers_the_loss(head, precond, drop):
         tr.step(batches[s % 2])
     last = float(tr.loss_and_grad(batches[0])[0].item())
     assert np.isfinite(last) and last < first - drop, (first, last)
+
+
+def test_config3_adjoint_matches_central_differences_at_full_size():
+    # The training step's workload: 64 instances of 255^2, K = 64 NAG sweeps from x0 with
+    # checkpoints every 8, FP64, with the 16 weights and the momentum the meta network
+    # gives (Algorithm 1, "backpropagate"). The adjoint's gradient with respect to some
+    # w_i, the momentum beta of an instance (shared by its 16 steps) and entries of x0
+    # against central differences (h = 1e-4) of the oracle's FP64 loss. The loss is the
+    # mean over the batch, L = (1/B) sum_b ln(||f_b - A_b u_b^K|| / ||f_b||), so the
+    # differences need only the perturbed instance's term.
+    from oracle.iterations import inner_steps
+    from paper_2412_08076_gb300 import meta
+    m, K, every, B, n = 16, 64, 8, 64, 255
+    insts = synth.batched_aniso(B, sizes=(n,), param_seed=1000)
+    op = make_op(insts)
+    G = torch.tensor(op.gershgorin(), dtype=torch.float32, device="cuda")
+    params, _ = meta.load_params(m)
+    X = torch.tensor(synth.meta_inputs(insts), dtype=torch.float32, device="cuda")
+    w32, a32 = richm.meta_forward(torch.tensor(params, device="cuda"), X, G, m)
+    w = w32.double().cpu().numpy()
+    a = a32.double().cpu().numpy()
+    fs = [synth.rhs_uniform(1500, i, n) for i in range(B)]
+    x0 = [0.1 * synth.rhs_uniform(1501, i, n) for i in range(B)]
+    L, gw, ga, _, gx0, _ = _gpu_grads(op, richm.F64, x0, fs, w, a, None, m, K, every)
+    gbeta = ga.sum(axis=1)
+
+    def term(b, w_b, a_b, x0_b):
+        t = insts[b]
+        A = assemble_q1(t.n, t.eps, t.theta)
+        u, _ = inner_steps(A, fs[b].ravel(), x0_b.ravel(), None, w_b, a_b, K=K)
+        return math.log(np.linalg.norm(fs[b].ravel() - A @ u) / np.linalg.norm(fs[b])) / B
+
+    for b in (0, 37):
+        for i in (0, 7, 15):
+            def loss_at(d, b=b, i=i):
+                p = w[b].copy()
+                p[i] += d
+                return term(b, p, a[b], x0[b])
+            _fd_check(gw[b, i], loss_at)
+
+        def loss_beta(d, b=b):
+            return term(b, w[b], a[b] + d, x0[b])
+        _fd_check(gbeta[b], loss_beta)
+        for (r, c) in ((0, 0), (127, 128), (254, 3)):
+            def loss_x0(d, b=b, r=r, c=c):
+                xp = x0[b].copy()
+                xp[r, c] += d
+                return term(b, w[b], a[b], xp)
+            _fd_check(gx0[b][r, c], loss_x0)

@@ -15,6 +15,8 @@ from oracle.operators import assemble_q1
 from oracle.training import meta_output_map, mlp_forward
 from paper_2412_08076_gb300 import meta
 
+pytestmark = pytest.mark.usefixtures("built_lib")
+
 
 def _layers(p, m=16):
     sizes = [(64, 2), (64,), (64, 64), (64,), (m + 1, 64), (m + 1,)]
@@ -60,6 +62,21 @@ def _certify(params, grid=6):
 
 def test_initial_network_is_stable_on_every_spectrum():
     assert _certify(meta.init_params(16)) <= 1.0 + 1e-9
+
+
+def test_fixed_momentum_network_outputs_beta_and_is_stable():
+    # the benchmark's network: momentum held at 0.3 (its output row is constant), the
+    # 16 weights trained from Leja-ordered Chebyshev weights on [1.2 G/30, 1.2 G]
+    p0 = meta.init_params(16, beta=0.3, stretch=1.2, leja=True, fixed_beta=True)
+    assert _certify(p0) <= 1.0 + 1e-9
+    p, src = meta.load_params(16, variant="beta03")
+    assert src == "trained"
+    rng = np.random.default_rng(4)
+    X = np.stack([rng.uniform(-3, 0, 50), rng.uniform(0, math.pi, 50)], axis=1)
+    o = mlp_forward(_layers(p), X)
+    beta = 1.0 / (1.0 + np.exp(-o[:, 16]))
+    assert np.abs(beta - 0.3).max() <= 1e-6
+    assert _certify(p) <= 1.0 + 1e-9
 
 
 @pytest.mark.skipif(not os.path.exists(meta.trained_path(16)), reason="no trained parameters saved")

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import richm_synth as synth
-from oracle.iterations import (chebyshev_weights, inner_steps, jacobi_binv,
+from oracle.iterations import (chebyshev_weights, inner_steps, jacobi_binv, leja_order,
                                outer_iterations_to_tol, refined_steps, rel_residual,
                                semi_iteration_weights, ssor_binv)
 from oracle.operators import assemble_q1, diffusion_tensor
@@ -337,3 +337,58 @@ def test_table2_chebyshev_rows(row):
         k, u = outer_iterations_to_tol(A, f, w, tol=1e-6)
         assert rel_residual(A, f, u) < 1e-6
         assert abs(k - paper_it) <= band * paper_it, (meth, eps, seed, k, paper_it)
+
+
+def _lex_best_order(z):
+    """Brute force over all permutations: the first node of largest |z| (smallest index
+    on ties), then the lexicographically largest sequence of distance products."""
+    import itertools
+    m = len(z)
+    best, best_key = None, None
+    for perm in itertools.permutations(range(m)):
+        key = [abs(z[perm[0]])]
+        for s in range(1, m):
+            p = 1.0
+            for j in perm[:s]:
+                p *= abs(z[perm[s]] - z[j])
+            key.append(p)
+        if best_key is None or key > best_key:
+            best, best_key = perm, key
+    return list(best)
+
+
+def test_leja_order_brute_force():
+    rng = np.random.default_rng(4)
+    for m in (1, 2, 3, 5, 6):
+        for _ in range(4):
+            w = 1.0 / rng.uniform(0.1, 3.0, m)
+            assert list(leja_order(w)) == _lex_best_order(1.0 / w)
+    # two nodes: the larger node first
+    assert list(leja_order(np.array([1.0, 0.5]))) == [1, 0]
+
+
+def test_leja_order_tames_partial_products():
+    # The rounding made at step s of a period is carried by the product of the later
+    # factors (1 - w_k lam). Chebyshev weights of eqs. 8-9 in index order (increasing w)
+    # put the long steps last, so those suffix products reach ~5e5 on [0, G]; in Leja
+    # order both the prefix and the suffix products stay below 10, and the period (the
+    # whole product) is the same.
+    G, m = 1.0, 16
+    w = chebyshev_weights(G, G / 30.0, m)
+    lam = np.linspace(0.0, G, 4001)
+
+    def worst(order):
+        order = list(order)
+        out = []
+        for seq in (order, order[::-1]):  # prefix, suffix products
+            P = np.ones_like(lam)
+            wst = 1.0
+            for i in seq:
+                P = P * (1.0 - w[i] * lam)
+                wst = max(wst, np.abs(P).max())
+            out.append(wst)
+        return out, P
+    (npre, nsuf), Pn = worst(range(m))
+    (lpre, lsuf), Pl = worst(leja_order(w))
+    np.testing.assert_allclose(Pl, Pn, rtol=1e-9, atol=1e-12)
+    assert nsuf > 1e5 and max(lpre, lsuf) < 10.0, (npre, nsuf, lpre, lsuf)

@@ -2,9 +2,12 @@
 import math
 
 import numpy as np
+import pytest
 
 from oracle.training import meta_output_map, mlp_forward
 from paper_2412_08076_gb300 import meta
+
+pytestmark = pytest.mark.usefixtures("built_lib")
 
 
 def _period_radius(w, beta, lam):

@@ -53,8 +53,49 @@ def test_static_scratch_residual_matches_workspace_version_twice(dtype):
         np.testing.assert_allclose(R1.cpu().numpy(), R.cpu().numpy(), rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("dtype", [richm.C64, richm.C128])
+def test_static_scratch_complex_helmholtz_matches_workspace_version_twice(dtype):
+    # the complex branch: 5-point Helmholtz stencil with the absorbing boundary's diagonal
+    from oracle.operators import helmholtz_wavenumber
+    ns = (1, 17, 64, 100)
+    op = richm.Operator([(richm.HELMHOLTZ_FD5_ABC, n, 1.0, 0.0, helmholtz_wavenumber(n)) for n in ns])
+    td = richm.TORCH_DTYPE[dtype]
+    for call in range(2):
+        xs = np.concatenate([(synth.rhs_uniform(60 + call, i, n) + 1j * synth.rhs_uniform(70 + call, i, n)).ravel()
+                             for i, n in enumerate(ns)])
+        bs = np.concatenate([(synth.rhs_uniform(80 + call, i, n) - 0.5j * synth.rhs_uniform(85 + call, i, n)).ravel()
+                             for i, n in enumerate(ns)])
+        X = op.pack(torch.tensor(xs, dtype=td, device="cuda"), dtype)
+        B = op.pack(torch.tensor(bs, dtype=td, device="cuda"), dtype)
+        R = op.zeros(dtype)
+        rn0, bn0, rel0 = op.residual_norm(dtype, X, B, r_out=R)
+        rn1, bn1, rel1, R1 = _static(op, dtype, X, B)
+        torch.cuda.synchronize()
+        for u, v in ((rn0, rn1), (bn0, bn1), (rel0, rel1)):
+            np.testing.assert_allclose(v.cpu().numpy(), u.cpu().numpy(), rtol=1e-14, atol=0)
+        np.testing.assert_allclose(R1.cpu().numpy(), R.cpu().numpy(), rtol=1e-14, atol=0)
+
+
+def test_static_scratch_many_instances():
+    # 3000 instances: the tile offsets come from a block-wide scan in which every thread
+    # sums a run of three consecutive instances
+    ns = [1 + (i * 7) % 40 for i in range(3000)]
+    op = richm.Operator([(richm.ANISO_Q1, n, 0.1 + 0.0003 * i, 0.001 * i, 0.0) for i, n in enumerate(ns)])
+    xs = np.concatenate([synth.rhs_uniform(40, i, n).ravel() for i, n in enumerate(ns)])
+    bs = np.concatenate([synth.rhs_uniform(41, i, n).ravel() for i, n in enumerate(ns)])
+    X = op.pack(torch.tensor(xs, dtype=torch.float64, device="cuda"), richm.F64)
+    B = op.pack(torch.tensor(bs, dtype=torch.float64, device="cuda"), richm.F64)
+    rn0, bn0, rel0 = op.residual_norm(richm.F64, X, B)
+    for _ in range(2):
+        rn1, bn1, rel1, _r = _static(op, richm.F64, X, B)
+        torch.cuda.synchronize()
+        for u, v in ((rn0, rn1), (bn0, bn1), (rel0, rel1)):
+            np.testing.assert_allclose(v.cpu().numpy(), u.cpu().numpy(), rtol=1e-14, atol=0)
+
+
 def test_static_scratch_rejects_batches_beyond_its_limit():
-    # 256 instances of 2047^2 need more warp tiles than the static scratch holds
+    # 32 instances of 2047^2 in FP64: 64-column tiles, 32 x 128 = 4096 warp tiles each,
+    # 131072 in all, twice what the static scratch holds (65536)
     op = richm.Operator([(richm.ANISO_Q1, 2047, 0.5, 0.3, 0.0)] * 32)
     lib = richm.load()
     fn = lib.richm_residual_norm_static
