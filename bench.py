@@ -621,6 +621,7 @@ def run_ours(args):
 
     def step():
         weight_supply()
+        Xs.zero_()  # every step solves from x = 0
         return op.solve(B64, Xs, w, a, None, opts, work=wsolve)
 
     for _ in range(args.warmup):

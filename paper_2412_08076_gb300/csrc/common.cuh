@@ -364,11 +364,15 @@ __device__ inline VecN<T, N> ldv(const T* p) {
 }
 template <typename T, int N>
 __device__ inline void stv(T* p, const VecN<T, N>& r) {
-  if constexpr (sizeof(VecN<T, N>) == 16) {
+  if constexpr (sizeof(VecN<T, N>) == 32) {  // e.g. two complex128 values
+    reinterpret_cast<uint4*>(p)[0] = reinterpret_cast<const uint4*>(&r)[0];
+    reinterpret_cast<uint4*>(p)[1] = reinterpret_cast<const uint4*>(&r)[1];
+  } else if constexpr (sizeof(VecN<T, N>) == 16) {
     *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(&r);
   } else if constexpr (sizeof(VecN<T, N>) == 8) {
     *reinterpret_cast<uint2*>(p) = *reinterpret_cast<const uint2*>(&r);
   } else {
+    static_assert(sizeof(VecN<T, N>) == 4, "vector size");
     *reinterpret_cast<unsigned*>(p) = *reinterpret_cast<const unsigned*>(&r);
   }
 }

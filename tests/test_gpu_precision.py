@@ -46,13 +46,14 @@ def batch():
 
 def _weights(kind, op, insts, G):
     """(w, a) [256][16] FP32 device tensors in natural order: the momentum-aware Chebyshev
-    weights from the library (eqs. 8-9 on [1.6 G/30, 1.6 G], beta 0.3) or the meta network's."""
+    weights from the library (eqs. 8-9 on [1.6 G/30, 1.6 G], beta 0.3) or a meta network's
+    (the one trained with free momentum, or the benchmark's, with the momentum held at 0.3)."""
     if kind == "chebyshev":
         unit = np.array(richm.chebyshev_weights(meta_mod.STABLE_STRETCH, meta_mod.STABLE_STRETCH * meta_mod.SEMI_ALPHA,
                                                 M))
         w = (unit[None, :] / G[:, None]).astype(np.float32)
         return coef(w, richm.F32), coef(np.full_like(w, 0.3), richm.F32)
-    params, _ = meta_mod.load_params(M)
+    params, _ = meta_mod.load_params(M, variant="beta03" if kind == "meta_beta03" else "")
     X = torch.tensor(synth.meta_inputs(insts), dtype=torch.float32, device="cuda")
     Gt = torch.tensor(G, dtype=torch.float32, device="cuda")
     return richm.meta_forward(torch.tensor(params, device="cuda"), X, Gt, M)
@@ -82,7 +83,7 @@ def test_leja_permute_matches_oracle(dtype):
 
 @pytest.mark.parametrize("kidx0", [0, 8])
 @pytest.mark.parametrize("order", ["natural", "leja"])
-@pytest.mark.parametrize("kind", ["chebyshev", "meta"])
+@pytest.mark.parametrize("kind", ["chebyshev", "meta", "meta_beta03"])
 def test_fused_block_fp32_relative_error(batch, kind, order, kidx0):
     # one 8-sweep fused pass (the benchmark's) from the same FP32 state on both sides;
     # the error relative to the instance's max |x| is reported. The rounding made at a
