@@ -434,13 +434,65 @@ def secondary_workloads(dev):
     e1.record()
     torch.cuda.synchronize()
     _, _, relh = op.residual_norm(richm.C64, Xc, Bc)
+    out["table9_analogue_fgmres20_sponge"] = table9_analogue(dev)
     out["helmholtz_16x2047sq_c64"] = {"ms_128_sweeps": e0.elapsed_time(e1),
                                       "gdof_sweeps_per_s": nb * n * n * 128 / (e0.elapsed_time(e1) / 1e3) / 1e9,
                                       "rel_res_after_128_max": float(relh.max().item()),
                                       "rel_res_after_128_min": float(relh.min().item()),
                                       "note": "fused passes of 4 complex sweeps (64-column tiles); oracle residual "
-                                              "check in tests"}
+                                              "check in tests. The seeded weights (h^2/8) U[0.5, 1.5) with momentum "
+                                              "0.3 do not converge on this indefinite operator: the residual grows "
+                                              "over the 128 sweeps (a throughput workload, as the configuration "
+                                              "states)"}
     op.close()
+    return out
+
+
+def table9_analogue(dev, sizes=(128, 256, 512), batch=4, tol=1e-6, max_iters=3000):
+    """FGMRES(20) on the sponge-layer Helmholtz problem of eq. 21 at Table 9's grids
+    (h = 1/N, omega/2pi = 10 N/128, c = 1), preconditioned by 5 sweeps of Richardson(5) or
+    NAG-Richardson(5) (Chebyshev weights of eqs. 8-9 on the upper spectrum [G/4, G], G the
+    Gershgorin bound; NAG with beta = 0.3 on the interval stretched by 1.6), or by nothing.
+    The WANS multigrid and ADR parts are not built (their networks and data are not
+    available), so the counts are for the smoother alone as the preconditioner. Right-hand
+    sides: unit point sources at seeded interior points."""
+    import numpy as np
+    import torch
+
+    import richm_synth as synth
+    from paper_2412_08076_gb300 import richm
+    out = {}
+    for N in sizes:
+        n = N - 1
+        om = 2 * math.pi * 10 * N / 128
+        op = richm.Operator([(richm.HELMHOLTZ_FD5_SPONGE, n, 1.0, 0.0, om)] * batch)
+        G = op.gershgorin()[0]
+        src = np.zeros((batch, n * n), np.complex128)
+        for s_, (i, j) in enumerate(synth.point_sources(n, batch, seed=6)):
+            src[s_, i * n + j] = 1.0
+        B = op.pack(torch.tensor(src.ravel(), device=dev), richm.C128)
+        row = {"omega_over_2pi": om / (2 * math.pi)}
+        for name, beta, stretch in (("none", None, 1.0), ("richardson5", None, 1.0), ("nag_richardson5", 0.3, 1.6)):
+            X = op.zeros(richm.C128)
+            if name == "none":
+                w = a = None
+                sweeps = 0
+            else:
+                wv = np.array(richm.chebyshev_weights(stretch * G, stretch * G / 4.0, 5))
+                w = torch.tensor(np.tile(wv, (batch, 1)), dtype=torch.float32, device=dev)
+                a = torch.full_like(w, beta) if beta is not None else None
+                sweeps = 5
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, info = op.fgmres(B, X, w, a, None, restart=20, tol=tol, max_iters=max_iters, m=5, sweeps=sweeps,
+                                 inner=richm.C64)
+            el = time.perf_counter() - t0
+            its = [i_ for i_, _, _ in info]
+            row[name] = {"iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+                         "converged": sum(1 for *_, s_ in info if s_ == richm.OK), "seconds": el,
+                         "worst_rel_res": max(r for _, r, _ in info)}
+        out[f"N{N}"] = row
+        op.close()
     return out
 
 
@@ -893,6 +945,23 @@ def run_profile_case(args):
     from paper_2412_08076_gb300 import richm
     m = 16
     what = args.profile
+    if what == "bench_cycles":
+        # the benchmark's batch, network and settings: the weight supply, the solver's start
+        # and `sweeps` / 64 refinement cycles (plain launches, no graph)
+        from paper_2412_08076_gb300 import meta as meta_mod
+        insts, op, rhs, dense_b = build_batch(1)
+        params, _ = meta_mod.load_params(M, variant=META_VARIANT)
+        X, G, P = meta_inputs(op, insts, params)
+        w, a = richm.meta_forward(P, X, G, M)
+        op.set_tuning(8, 128)
+        B64 = op.pack(dense_b.cuda(), richm.F64)
+        S = richm.Solver(op, op.solve_opts(M, tol=SOLVE_TOL, max_sweeps=10 ** 7, refine_every=REFINE,
+                                           inner=richm.F32, use_graph=0, fuse=8), w, a)
+        S.start(B64, op.zeros(richm.F64))
+        S.step(max(1, args.sweeps // REFINE), sync=True)
+        S.close()
+        torch.cuda.synchronize()
+        return 0
     insts = synth.batched_aniso(args.batch, sizes=(args.n,), param_seed=1)
     if what == "helmholtz":
         k = 2 * math.pi * (args.n + 1) / 10
@@ -953,7 +1022,7 @@ def main(argv=None):
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--e2e-runs", type=int, default=2, help="timed richm_solve_host calls")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["sweep", "cycle", "adjoint", "helmholtz", "ssor"], default=None,
+    ap.add_argument("--profile", choices=["sweep", "cycle", "adjoint", "helmholtz", "ssor", "bench_cycles"], default=None,
                     help="run a small fixed workload of one kernel family for an ncu capture instead of the bench")
     ap.add_argument("--batch", type=int, default=32, help="--profile: instances")
     ap.add_argument("--n", type=int, default=511, help="--profile: grid size")

@@ -90,7 +90,10 @@ typedef enum {
   RICHM_HEAD_RICHARDSON = 1, /* m: w_i only (Richardson(m)) */
   RICHM_HEAD_MOM = 2,        /* 2m: w_i, a_i; at_i = 0 (MOM) */
   RICHM_HEAD_NAG = 3,        /* 2m: w_i, a_i; at_i = a_i (NAG) */
-  RICHM_HEAD_NAGEX = 4       /* 3m: w_i, a_i, at_i (NAGex) */
+  RICHM_HEAD_NAGEX = 4,      /* 3m: w_i, a_i, at_i (NAGex) */
+  RICHM_HEAD_RAW = 5         /* m outputs o_i written as they are (w_out[b][i] = o_i; G unused): the
+                                parameters of the FNS symbol and transition maps (richm_symbol_from_stencil,
+                                richm_transition_from_band) */
 } richm_meta_head;
 
 /* One PDE instance. eps, theta: anisotropy strength (0 < eps <= 1) and angle for
@@ -531,6 +534,62 @@ richm_status richm_fourier_vjp_workspace(const richm_operator* op, size_t* bytes
 richm_status richm_fourier_correction_vjp(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
                                           const void* g, const void* symbol, void* dsymbol, void* g_x, void* work,
                                           size_t work_bytes, void* stream);
+
+/* The FNS correction with a transition (Sec. 3.1, eq. 20, H = F T Lambda T^* F^{-1}): T
+ * mixes every frequency with its neighbours in a band by one kernel tau, which is the
+ * same as multiplying by the field t(x) = sum_d tau_d exp(2 pi i d.x / n) on the grid; the
+ * library takes t directly, real (tau Hermitian-symmetric), [n][n] FP32 device, shared
+ * by the batch:
+ *   x += t .* Re(IFFT2(S .* FFT2(t .* (b - A x)))).
+ * transition NULL is T = I (richm_fourier_correction). Same instance rules, dtype and
+ * workspace as richm_fourier_correction. */
+richm_status richm_fourier_correction_t(richm_operator* op, richm_dtype dtype, void* x, const void* b,
+                                        const void* symbol, const void* transition, void* work, size_t work_bytes,
+                                        void* stream);
+
+/* Workspace bytes for richm_fourier_correction_t_vjp: three real n x n fields and three
+ * half spectra per instance, and the cuFFT work area. */
+richm_status richm_fourier_t_vjp_workspace(const richm_operator* op, size_t* bytes);
+
+/* Reverse mode of richm_fourier_correction_t (the Meta-Lambda and Meta-T steps of
+ * Algorithm 2). With r = b - A x, q = t r, Q = FFT2(q), p = Re(IFFT2(S Q)) (so
+ * x' = x + t p), g = dL/dx', G^ = FFT2(t g) and h = Re(IFFT2(conj(S) G^)):
+ *   dsymbol     = sum over the batch of conj(Q) G^ / n^2   (complex64 [n][n]) or NULL,
+ *   dtransition = sum over the batch of g p + r h           (FP32 [n][n]) or NULL,
+ *   g_x         = g - A (t h) = dL/dx                       (padded, may alias g) or NULL.
+ * x, b are needed for either parameter gradient; transition NULL is t = 1 (and then
+ * dtransition must be NULL). work: at least richm_fourier_t_vjp_workspace bytes. */
+richm_status richm_fourier_correction_t_vjp(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
+                                            const void* g, const void* symbol, const void* transition,
+                                            void* dsymbol, void* dtransition, void* g_x, void* work,
+                                            size_t work_bytes, void* stream);
+
+/* Parameter maps of the FNS neural iteration (Sec. 3.1: Meta-Lambda produces the diagonal
+ * Lambda approximating the inverses of A's eigenvalues, Meta-T the transition's kernel;
+ * their architectures are not given, so the library maps a few network outputs, o,
+ * to the symbol and the transition field, and the meta network with the RICHM_HEAD_RAW
+ * head produces o).
+ * Symbol: p_m = q_m exp(o_m) (m < 5) with q the instance's Q1 stencil (centre,
+ * x-neighbour, y-neighbour, corner(+1,+1), corner(+1,-1)), delta = q_5 exp(o_5), and
+ *   sigma(k) = p0 + 2 p1 cos t2 + 2 p2 cos t1 + 2 p3 cos(t1 + t2) + 2 p4 cos(t1 - t2),
+ *   S(k) = sigma / (sigma^2 + delta^2),  t = 2 pi k / n  (k = (row, column) frequency),
+ * the regularised inverse of the periodic symbol (o = 0: the instance's own stencil).
+ * q: host double [6]; o: device FP32 [6]; symbol: device complex64 [n][n] (imaginary 0).
+ * Transition: tau = device FP32 [9] = (tau_0, then (re, im) of the band offsets (0,1),
+ * (1,0), (1,1), (1,-1)) of a Hermitian-symmetric kernel; the field is
+ *   t(i, j) = tau_0 + 2 sum_d (re_d cos(2 pi d.x / n) - im_d sin(2 pi d.x / n)),
+ * written to transition: device FP32 [n][n] (the input of richm_fourier_correction_t).
+ * Reverse modes: d_o[m] = dL/do_m from dsymbol (the complex gradient
+ * richm_fourier_correction_t_vjp gives; S is real, so its real part), dtau[q] = dL/dtau_q
+ * from dtransition; outputs device FP32, written; summed in FP64 in a fixed order.
+ * work: at least richm_fns_map_workspace bytes. Errors: RICHM_ERR_ARG, RICHM_ERR_NOMEM. */
+richm_status richm_fns_map_workspace(size_t* bytes);
+richm_status richm_symbol_from_stencil(int n, const double* q, const float* o, void* symbol, void* stream);
+richm_status richm_symbol_from_stencil_vjp(int n, const double* q, const float* o, const void* dsymbol, float* d_o,
+                                           void* work, size_t work_bytes, void* stream);
+richm_status richm_transition_from_band(int n, const float* tau, float* transition, void* stream);
+richm_status richm_transition_from_band_vjp(int n, const float* dtransition, float* dtau, void* work,
+                                            size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------ misc */
 

@@ -53,6 +53,88 @@ def fourier_correction_vjp(A, f, u, S, g):
     return dS, du
 
 
+def transition_field(tau, n):
+    """The real field t(x) of a banded transition T (reading: T mixes each frequency
+    with its neighbours within a band, with the same kernel tau[d] for every frequency;
+    tau is a (2w+1, 2w+1) array indexed by the offset d + w, Hermitian-symmetric,
+    tau[-d] = conj(tau[d]), so that t is real): t(x) = sum_d tau[d] exp(2 pi i d.x / n)
+    on the n x n grid (x = (row, column) indices)."""
+    tau = np.asarray(tau, dtype=np.complex128)
+    w = (tau.shape[0] - 1) // 2
+    i = np.arange(n)
+    t = np.zeros((n, n), dtype=np.complex128)
+    for a in range(-w, w + 1):
+        for c in range(-w, w + 1):
+            t += tau[a + w, c + w] * np.exp(2j * np.pi * (a * i[:, None] + c * i[None, :]) / n)
+    return t.real
+
+
+def fourier_correction_t(A, f, u, S, t):
+    """u + t * Re(ifft2(S * fft2(t * (f - A u)))): the correction H (f - A u) with
+    H = F T S T* F^{-1} (eqs. 19-20) for a banded transition T given by its real field t
+    (`transition_field`; a kernel convolving the spectrum is a pointwise product on the
+    grid). Pinned by: equality with the explicit matrix product F T S T^H F^{-1} built from
+    DFT matrices and the band matrix T for small n; t = 1 gives ``fourier_correction``
+    (tests)."""
+    n = S.shape[0]
+    r = (f - A @ u).reshape(n, n)
+    c = np.fft.ifft2(S * np.fft.fft2(t * r)).real
+    return u + (t * c).ravel()
+
+
+def fourier_correction_t_vjp(A, f, u, S, t, g):
+    """Reverse mode of ``fourier_correction_t``: (dS, dt, du) for g = dL/du' (real).
+    With q = t r, Q = fft2(q), p = Re(ifft2(S Q)) (so u' = u + t p), gh = t g and
+    Gh = fft2(gh): dS = conj(Q) Gh / n^2, h = Re(ifft2(conj(S) Gh)) (the transpose of
+    q -> p applied to gh), dt = g p + r h, du = g - A^T (t h).
+    Pinned by: central finite differences in Re S, Im S, t and u (tests)."""
+    n = S.shape[0]
+    r = (f - A @ u).reshape(n, n)
+    g = np.asarray(g, dtype=np.float64).reshape(n, n)
+    Q = np.fft.fft2(t * r)
+    p = np.fft.ifft2(S * Q).real
+    Gh = np.fft.fft2(t * g)
+    dS = np.conj(Q) * Gh / (n * n)
+    h = np.fft.ifft2(np.conj(S) * Gh).real
+    dt = g * p + r * h
+    du = g.ravel() - A.T @ (t * h).ravel()
+    return dS, dt, du
+
+
+def symbol_from_stencil(q, o, n):
+    """The FNS symbol of a few network outputs (reading: Meta-Lambda's architecture is not
+    given; its output Lambda approximates the inverses of A's eigenvalues, here as the
+    regularised inverse of a periodic 9-point symbol): p_m = q_m exp(o_m) (m < 5),
+    delta = q_5 exp(o_5), sigma(k) = p0 + 2 p1 cos t2 + 2 p2 cos t1 + 2 p3 cos(t1 + t2)
+    + 2 p4 cos(t1 - t2) with t = 2 pi k / n, and S = sigma / (sigma^2 + delta^2).
+    Pinned by: for a Q1 stencil q and o = 0, sigma is the exact spectrum of the periodic
+    extension of A (eigenvalues of the circulant matrix, tests); central differences of
+    the reverse mode."""
+    q = np.asarray(q, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    p = q[:5] * np.exp(o[:5])
+    d = q[5] * np.exp(o[5])
+    t = 2.0 * np.pi * np.arange(n) / n
+    t1, t2 = np.meshgrid(t, t, indexing="ij")
+    sig = p[0] + 2 * p[1] * np.cos(t2) + 2 * p[2] * np.cos(t1) + 2 * p[3] * np.cos(t1 + t2) \
+        + 2 * p[4] * np.cos(t1 - t2)
+    return (sig / (sig * sig + d * d)).astype(np.complex128)
+
+
+def transition_band(tau9, n):
+    """The transition field of the library's band parametrisation: tau9 = (tau_0, then
+    (re, im) of the offsets (0,1), (1,0), (1,1), (1,-1)), the other half of the 3 x 3
+    kernel by Hermitian symmetry; the field of `transition_field`."""
+    t = np.asarray(tau9, dtype=np.float64)
+    tau = np.zeros((3, 3), dtype=np.complex128)
+    tau[1, 1] = t[0]
+    for q, (a, c) in enumerate([(0, 1), (1, 0), (1, 1), (1, -1)]):
+        v = t[1 + 2 * q] + 1j * t[2 + 2 * q]
+        tau[a + 1, c + 1] = v
+        tau[-a + 1, -c + 1] = np.conj(v)
+    return transition_field(tau, n)
+
+
 def two_level_cycle(A, f, u, w, S, Binv=None):
     """One cycle: len(w) Richardson(m) smoothing steps then one Fourier correction."""
     u, _ = inner_steps(A, f, u, None, w, K=len(w), Binv=Binv)

@@ -1,5 +1,8 @@
-// Fourier-domain correction of the FNS iteration (eqs. 19-20 with T = I):
-//   x += Re( IFFT2( S .* FFT2(b - A x) ) )
+// Fourier-domain correction of the FNS iteration (eqs. 19-20):
+//   x += t .* Re( IFFT2( S .* FFT2(t .* (b - A x)) ) ),
+// the correction H (b - A x), H = F T S T^H F^{-1}, for a banded transition T applied as
+// the real field t on the grid (a band kernel convolving the spectrum is a pointwise
+// product in space; t = 1 is T = I).
 // The residual is real, so its spectrum R is Hermitian (R(-k) = conj(R(k))), and the
 // real part of IFFT2(S .* R) is the inverse transform of the Hermitian part of S .* R,
 // which is R(k) (S(k) + conj(S(-k))) / 2. The correction is therefore computed with a
@@ -66,9 +69,11 @@ static richm_status ensure_plan(richm_operator* op, FftState** out) {
   return RICHM_OK;
 }
 
-// res[b][i][j] = (b - A x)(i, j) (dense n x n per instance, FP32).
+// res[b][i][j] = t(i, j) (b - A x)(i, j) (dense n x n per instance, FP32); t: the
+// transition field [n][n] shared by the batch, or NULL for t = 1.
 __global__ void fourier_resid_kernel(const Inst* insts, int n, const float* __restrict__ x,
-                                     const float* __restrict__ rhs, float* __restrict__ res) {
+                                     const float* __restrict__ rhs, float* __restrict__ res,
+                                     const float* __restrict__ t = nullptr) {
   const int b = blockIdx.z;
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,7 +91,8 @@ __global__ void fourier_resid_kernel(const Inst* insts, int n, const float* __re
   const float xsw = (west && south) ? x[o + p - 1] : 0.f, xse = (east && south) ? x[o + p + 1] : 0.f;
   const float ax = (float)I.c * xc + (float)I.ax * (xw + xe) + (float)I.ay * (xn + xs) +
                    (float)I.d1 * (xse + xnw) + (float)I.d2 * (xne + xsw);
-  res[((long long)b * n + i) * n + j] = rhs[o] - ax;
+  const float r = rhs[o] - ax;
+  res[((long long)b * n + i) * n + j] = t ? t[(long long)i * n + j] * r : r;
 }
 
 // half[b][k1][k2] *= (S(k1, k2) + conj(S(-k1, -k2))) / (2 n^2), k2 = 0 .. n/2 (symbol
@@ -108,16 +114,17 @@ __global__ void fourier_symbol_kernel(float2* __restrict__ half, const float2* _
   half[k] = make_float2(sr * v.x - si * v.y, sr * v.y + si * v.x);
 }
 
-// x += res on the interior.
+// x += t res on the interior (t NULL: t = 1).
 __global__ void fourier_update_kernel(const Inst* insts, int n, float* __restrict__ x,
-                                      const float* __restrict__ res) {
+                                      const float* __restrict__ res, const float* __restrict__ t = nullptr) {
   const int b = blockIdx.z;
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const Inst& I = insts[b];
   const long long o = I.off + (long long)(i + 1) * I.pitch + j;
-  x[o] += res[((long long)b * n + i) * n + j];
+  const float c = res[((long long)b * n + i) * n + j];
+  x[o] += t ? t[(long long)i * n + j] * c : c;
 }
 
 // ---------------------------------------------------------------- reverse mode
@@ -128,15 +135,44 @@ __global__ void fourier_update_kernel(const Inst* insts, int n, float* __restric
 // Both spectra are real-to-complex transforms; the symbol gradient's columns beyond n/2
 // follow from conj(R(-k)) G(-k) = conj(conj(R(k)) G(k)).
 
-// dense[b][i][j] = g(i, j) (the interior of a padded buffer).
+// dense[b][i][j] = t(i, j) g(i, j) (the interior of a padded buffer; t NULL: t = 1).
 __global__ void fourier_gather_kernel(const Inst* insts, int n, const float* __restrict__ g,
-                                      float* __restrict__ dense) {
+                                      float* __restrict__ dense, const float* __restrict__ t = nullptr) {
   const int b = blockIdx.z;
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const Inst& I = insts[b];
-  dense[((long long)b * n + i) * n + j] = g[I.off + (long long)(i + 1) * I.pitch + j];
+  const float v = g[I.off + (long long)(i + 1) * I.pitch + j];
+  dense[((long long)b * n + i) * n + j] = t ? t[(long long)i * n + j] * v : v;
+}
+
+// dt[i][j] = sum over the batch of g p + r h at (i, j), with r = b - A x recomputed,
+// p = Re(IFFT2(S Q)) and h = Re(IFFT2(conj(S) G^)) dense (the transition's gradient;
+// the batch is summed in a fixed order).
+__global__ void fourier_transition_grad_kernel(const Inst* insts, int n, int batch, const float* __restrict__ x,
+                                               const float* __restrict__ rhs, const float* __restrict__ g,
+                                               const float* __restrict__ p, const float* __restrict__ h,
+                                               float* __restrict__ dt) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float acc = 0.f;
+  for (int b = 0; b < batch; ++b) {
+    const Inst& I = insts[b];
+    const long long o = I.off + (long long)(i + 1) * I.pitch + j;
+    const long long pp = I.pitch;
+    const bool west = j > 0, east = j < n - 1, north = i > 0, south = i < n - 1;
+    const float xc = x[o], xw = west ? x[o - 1] : 0.f, xe = east ? x[o + 1] : 0.f;
+    const float xn = north ? x[o - pp] : 0.f, xs = south ? x[o + pp] : 0.f;
+    const float xnw = (west && north) ? x[o - pp - 1] : 0.f, xne = (east && north) ? x[o - pp + 1] : 0.f;
+    const float xsw = (west && south) ? x[o + pp - 1] : 0.f, xse = (east && south) ? x[o + pp + 1] : 0.f;
+    const float ax = (float)I.c * xc + (float)I.ax * (xw + xe) + (float)I.ay * (xn + xs) +
+                     (float)I.d1 * (xse + xnw) + (float)I.d2 * (xne + xsw);
+    const long long d = ((long long)b * n + i) * n + j;
+    acc += g[o] * p[d] + (rhs[o] - ax) * h[d];
+  }
+  dt[(long long)i * n + j] = acc;
 }
 
 // dS[k1][k2] = scale * sum_b conj(R_b(k)) G_b(k) over the full n x n spectrum.
@@ -158,16 +194,19 @@ __global__ void fourier_symbol_grad_kernel(const float2* __restrict__ R, const f
   dS[k] = make_float2(scale * re, (mirror ? -scale : scale) * im);
 }
 
-// gout = g - A h on the interior (h dense, zero outside the grid); gout may alias g.
+// gout = g - A (t h) on the interior (h dense, zero outside the grid; t NULL: t = 1);
+// gout may alias g.
 __global__ void fourier_adjoint_kernel(const Inst* insts, int n, const float* g, const float* __restrict__ h,
-                                       float* gout) {
+                                       float* gout, const float* __restrict__ t = nullptr) {
   const int b = blockIdx.z;
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const Inst& I = insts[b];
   const float* hb = h + (long long)b * n * n;
-  auto hv = [&](int ii, int jj) { return (ii >= 0 && ii < n && jj >= 0 && jj < n) ? hb[ii * n + jj] : 0.f; };
+  auto hv = [&](int ii, int jj) {
+    return (ii >= 0 && ii < n && jj >= 0 && jj < n) ? (t ? t[ii * n + jj] : 1.f) * hb[ii * n + jj] : 0.f;
+  };
   const float ax = (float)I.c * hv(i, j) + (float)I.ax * (hv(i, j - 1) + hv(i, j + 1)) +
                    (float)I.ay * (hv(i - 1, j) + hv(i + 1, j)) + (float)I.d1 * (hv(i + 1, j + 1) + hv(i - 1, j - 1)) +
                    (float)I.d2 * (hv(i - 1, j + 1) + hv(i + 1, j - 1));
@@ -201,6 +240,89 @@ richm_status richm_fourier_vjp_workspace(const richm_operator* op, size_t* bytes
   return RICHM_OK;
 }
 
+richm_status richm_fourier_t_vjp_workspace(const richm_operator* op, size_t* bytes) {
+  clear_error();
+  RICHM_ARG(op && bytes, "null argument");
+  FftState* st = nullptr;
+  RICHM_TRY(ensure_plan(const_cast<richm_operator*>(op), &st));
+  const size_t nn = (size_t)st->n * st->n, nh = (size_t)st->n * (st->n / 2 + 1);
+  *bytes = 3 * a256(sizeof(float) * nn * st->batch) + 3 * a256(sizeof(float2) * nh * st->batch) + a256(st->work);
+  return RICHM_OK;
+}
+
+static richm_status bind_work(FftState* st, void* fwork, cudaStream_t s) {
+  for (cufftHandle h : {st->fwd, st->inv}) {
+    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return set_error(RICHM_ERR_CUDA, "cufftSetStream failed");
+    if (cufftSetWorkArea(h, fwork) != CUFFT_SUCCESS) return set_error(RICHM_ERR_CUDA, "cufftSetWorkArea failed");
+  }
+  return RICHM_OK;
+}
+
+// Reverse mode with an optional transition field t (NULL: t = 1) and its gradient dt.
+static richm_status fourier_vjp_impl(richm_operator* op, const float* x, const float* b, const float* g,
+                                     const float2* symbol, const float* t, float2* dsymbol, float* dt, float* g_x,
+                                     void* work, size_t work_bytes, cudaStream_t s, bool three) {
+  FftState* st = nullptr;
+  RICHM_TRY(ensure_plan(op, &st));
+  const int n = st->n;
+  const size_t nn = (size_t)n * n, nh = (size_t)n * (n / 2 + 1);
+  const size_t dense_bytes = a256(sizeof(float) * nn * st->batch);
+  const size_t half_bytes = a256(sizeof(float2) * nh * st->batch);
+  const int nb = three ? 3 : 2;
+  const size_t need = nb * dense_bytes + nb * half_bytes + a256(st->work);
+  if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  char* wp = reinterpret_cast<char*>(work);
+  float* dres = reinterpret_cast<float*>(wp);
+  float* dg = reinterpret_cast<float*>(wp + dense_bytes);
+  float* dp = three ? reinterpret_cast<float*>(wp + 2 * dense_bytes) : nullptr;
+  float2* hres = reinterpret_cast<float2*>(wp + nb * dense_bytes);
+  float2* hg = reinterpret_cast<float2*>(wp + nb * dense_bytes + half_bytes);
+  float2* hq2 = three ? reinterpret_cast<float2*>(wp + nb * dense_bytes + 2 * half_bytes) : nullptr;
+  RICHM_TRY(bind_work(st, wp + nb * dense_bytes + nb * half_bytes, s));
+  const dim3 grid((n + 127) / 128, n, op->batch);
+  const float inv_nn = (float)(1.0 / (double)nn);
+  const long long tot = (long long)nh * op->batch;
+  fourier_gather_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, g, dg, t);
+  RICHM_LAUNCH_CHECK("fourier gather");
+  if (cufftExecR2C(st->fwd, dg, (cufftComplex*)hg) != CUFFT_SUCCESS)
+    return set_error(RICHM_ERR_CUDA, "forward FFT failed");
+  if (dsymbol || dt) {
+    fourier_resid_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, x, b, dres, t);
+    RICHM_LAUNCH_CHECK("fourier residual");
+    if (cufftExecR2C(st->fwd, dres, (cufftComplex*)hres) != CUFFT_SUCCESS)
+      return set_error(RICHM_ERR_CUDA, "forward FFT failed");
+  }
+  if (dsymbol) {
+    fourier_symbol_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(hres, hg, n, op->batch, inv_nn, dsymbol);
+    RICHM_LAUNCH_CHECK("fourier symbol gradient");
+  }
+  if (dt) {
+    // p = Re(IFFT2(S Q)), the correction before its product with t
+    RICHM_CUDA_TRY(cudaMemcpyAsync(hq2, hres, sizeof(float2) * nh * op->batch, cudaMemcpyDeviceToDevice, s));
+    fourier_symbol_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(hq2, symbol, n, op->batch, inv_nn, 1.f);
+    RICHM_LAUNCH_CHECK("fourier symbol");
+    if (cufftExecC2R(st->inv, (cufftComplex*)hq2, dp) != CUFFT_SUCCESS)
+      return set_error(RICHM_ERR_CUDA, "inverse FFT failed");
+  }
+  if (g_x || dt) {
+    // h = Re(IFFT2(conj(S) G^)), the transpose of the correction's inner map applied to t g
+    fourier_symbol_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(hg, symbol, n, op->batch, inv_nn, -1.f);
+    RICHM_LAUNCH_CHECK("fourier symbol");
+    if (cufftExecC2R(st->inv, (cufftComplex*)hg, dg) != CUFFT_SUCCESS)
+      return set_error(RICHM_ERR_CUDA, "inverse FFT failed");
+  }
+  if (dt) {
+    fourier_transition_grad_kernel<<<dim3((n + 127) / 128, n), 128, 0, s>>>(op->d_inst, n, op->batch, x, b, g, dp,
+                                                                             dg, dt);
+    RICHM_LAUNCH_CHECK("fourier transition gradient");
+  }
+  if (g_x) {
+    fourier_adjoint_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, g, dg, g_x, t);
+    RICHM_LAUNCH_CHECK("fourier adjoint");
+  }
+  return RICHM_OK;
+}
+
 richm_status richm_fourier_correction_vjp(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
                                           const void* g, const void* symbol, void* dsymbol, void* g_x, void* work,
                                           size_t work_bytes, void* stream) {
@@ -209,59 +331,27 @@ richm_status richm_fourier_correction_vjp(richm_operator* op, richm_dtype dtype,
   RICHM_ARG(dtype == RICHM_F32, "the Fourier correction takes RICHM_F32 state");
   RICHM_ARG(g && symbol && work, "null argument");
   RICHM_ARG(!dsymbol || (x && b), "the symbol gradient needs x and b");
-  FftState* st = nullptr;
-  RICHM_TRY(ensure_plan(op, &st));
-  const int n = st->n;
-  const size_t nn = (size_t)n * n, nh = (size_t)n * (n / 2 + 1);
-  const size_t dense_bytes = a256(sizeof(float) * nn * st->batch);
-  const size_t half_bytes = a256(sizeof(float2) * nh * st->batch);
-  const size_t need = 2 * dense_bytes + 2 * half_bytes + a256(st->work);
-  if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
-  cudaStream_t s = (cudaStream_t)stream;
-  char* wp = reinterpret_cast<char*>(work);
-  float* dres = reinterpret_cast<float*>(wp);
-  float* dg = reinterpret_cast<float*>(wp + dense_bytes);
-  float2* hres = reinterpret_cast<float2*>(wp + 2 * dense_bytes);
-  float2* hg = reinterpret_cast<float2*>(wp + 2 * dense_bytes + half_bytes);
-  void* fwork = wp + 2 * dense_bytes + 2 * half_bytes;
-  for (cufftHandle h : {st->fwd, st->inv}) {
-    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return set_error(RICHM_ERR_CUDA, "cufftSetStream failed");
-    if (cufftSetWorkArea(h, fwork) != CUFFT_SUCCESS) return set_error(RICHM_ERR_CUDA, "cufftSetWorkArea failed");
-  }
-  const dim3 grid((n + 127) / 128, n, op->batch);
-  const float inv_nn = (float)(1.0 / (double)nn);
-  fourier_gather_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, (const float*)g, dg);
-  RICHM_LAUNCH_CHECK("fourier gather");
-  if (cufftExecR2C(st->fwd, dg, (cufftComplex*)hg) != CUFFT_SUCCESS)
-    return set_error(RICHM_ERR_CUDA, "forward FFT failed");
-  if (dsymbol) {
-    fourier_resid_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, (const float*)x, (const float*)b, dres);
-    RICHM_LAUNCH_CHECK("fourier residual");
-    if (cufftExecR2C(st->fwd, dres, (cufftComplex*)hres) != CUFFT_SUCCESS)
-      return set_error(RICHM_ERR_CUDA, "forward FFT failed");
-    fourier_symbol_grad_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(hres, hg, n, op->batch, inv_nn,
-                                                                             (float2*)dsymbol);
-    RICHM_LAUNCH_CHECK("fourier symbol gradient");
-  }
-  if (g_x) {
-    const long long tot = (long long)nh * op->batch;
-    fourier_symbol_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(hg, (const float2*)symbol, n, op->batch,
-                                                                          inv_nn, -1.f);
-    RICHM_LAUNCH_CHECK("fourier symbol");
-    if (cufftExecC2R(st->inv, (cufftComplex*)hg, dg) != CUFFT_SUCCESS)
-      return set_error(RICHM_ERR_CUDA, "inverse FFT failed");
-    fourier_adjoint_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, (const float*)g, dg, (float*)g_x);
-    RICHM_LAUNCH_CHECK("fourier adjoint");
-  }
-  return RICHM_OK;
+  return fourier_vjp_impl(op, (const float*)x, (const float*)b, (const float*)g, (const float2*)symbol, nullptr,
+                          (float2*)dsymbol, nullptr, (float*)g_x, work, work_bytes, (cudaStream_t)stream, false);
 }
 
-richm_status richm_fourier_correction(richm_operator* op, richm_dtype dtype, void* x, const void* b,
-                                      const void* symbol, void* work, size_t work_bytes, void* stream) {
+richm_status richm_fourier_correction_t_vjp(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
+                                            const void* g, const void* symbol, const void* transition,
+                                            void* dsymbol, void* dtransition, void* g_x, void* work,
+                                            size_t work_bytes, void* stream) {
   clear_error();
   RICHM_ARG(op != nullptr, "null operator");
   RICHM_ARG(dtype == RICHM_F32, "the Fourier correction takes RICHM_F32 state");
-  RICHM_ARG(x && b && symbol && work, "null argument");
+  RICHM_ARG(g && symbol && work, "null argument");
+  RICHM_ARG(!(dsymbol || dtransition) || (x && b), "the parameter gradients need x and b");
+  RICHM_ARG(!dtransition || transition, "the transition gradient needs the transition");
+  return fourier_vjp_impl(op, (const float*)x, (const float*)b, (const float*)g, (const float2*)symbol,
+                          (const float*)transition, (float2*)dsymbol, (float*)dtransition, (float*)g_x, work,
+                          work_bytes, (cudaStream_t)stream, true);
+}
+
+static richm_status fourier_correction_impl(richm_operator* op, float* x, const float* b, const float2* symbol,
+                                            const float* t, void* work, size_t work_bytes, cudaStream_t s) {
   FftState* st = nullptr;
   RICHM_TRY(ensure_plan(op, &st));
   const int n = st->n;
@@ -271,28 +361,44 @@ richm_status richm_fourier_correction(richm_operator* op, richm_dtype dtype, voi
   if (work_bytes < res_bytes + half_bytes + a256(st->work))
     return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes,
                      res_bytes + half_bytes + a256(st->work));
-  cudaStream_t s = (cudaStream_t)stream;
   float* res = reinterpret_cast<float*>(work);
   float2* half = reinterpret_cast<float2*>(reinterpret_cast<char*>(work) + res_bytes);
-  void* fwork = reinterpret_cast<char*>(work) + res_bytes + half_bytes;
-  for (cufftHandle h : {st->fwd, st->inv}) {
-    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return set_error(RICHM_ERR_CUDA, "cufftSetStream failed");
-    if (cufftSetWorkArea(h, fwork) != CUFFT_SUCCESS) return set_error(RICHM_ERR_CUDA, "cufftSetWorkArea failed");
-  }
+  RICHM_TRY(bind_work(st, reinterpret_cast<char*>(work) + res_bytes + half_bytes, s));
   dim3 grid((n + 127) / 128, n, op->batch);
-  fourier_resid_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, (const float*)x, (const float*)b, res);
+  fourier_resid_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, x, b, res, t);
   RICHM_LAUNCH_CHECK("fourier residual");
   if (cufftExecR2C(st->fwd, res, (cufftComplex*)half) != CUFFT_SUCCESS)
     return set_error(RICHM_ERR_CUDA, "forward FFT failed");
   const long long tot = (long long)nh * op->batch;
-  fourier_symbol_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(half, (const float2*)symbol, n, op->batch,
+  fourier_symbol_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(half, symbol, n, op->batch,
                                                                         (float)(1.0 / (double)nn), 1.f);
   RICHM_LAUNCH_CHECK("fourier symbol");
   if (cufftExecC2R(st->inv, (cufftComplex*)half, res) != CUFFT_SUCCESS)
     return set_error(RICHM_ERR_CUDA, "inverse FFT failed");
-  fourier_update_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, (float*)x, res);
+  fourier_update_kernel<<<grid, 128, 0, s>>>(op->d_inst, n, x, res, t);
   RICHM_LAUNCH_CHECK("fourier update");
   return RICHM_OK;
+}
+
+richm_status richm_fourier_correction(richm_operator* op, richm_dtype dtype, void* x, const void* b,
+                                      const void* symbol, void* work, size_t work_bytes, void* stream) {
+  clear_error();
+  RICHM_ARG(op != nullptr, "null operator");
+  RICHM_ARG(dtype == RICHM_F32, "the Fourier correction takes RICHM_F32 state");
+  RICHM_ARG(x && b && symbol && work, "null argument");
+  return fourier_correction_impl(op, (float*)x, (const float*)b, (const float2*)symbol, nullptr, work, work_bytes,
+                                 (cudaStream_t)stream);
+}
+
+richm_status richm_fourier_correction_t(richm_operator* op, richm_dtype dtype, void* x, const void* b,
+                                        const void* symbol, const void* transition, void* work, size_t work_bytes,
+                                        void* stream) {
+  clear_error();
+  RICHM_ARG(op != nullptr, "null operator");
+  RICHM_ARG(dtype == RICHM_F32, "the Fourier correction takes RICHM_F32 state");
+  RICHM_ARG(x && b && symbol && work, "null argument");
+  return fourier_correction_impl(op, (float*)x, (const float*)b, (const float2*)symbol, (const float*)transition,
+                                 work, work_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

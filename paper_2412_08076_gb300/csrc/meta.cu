@@ -25,6 +25,7 @@ __host__ __device__ inline int head_outputs(int head, int m) {
     case RICHM_HEAD_MOM:
     case RICHM_HEAD_NAG: return 2 * m;
     case RICHM_HEAD_NAGEX: return 3 * m;
+    case RICHM_HEAD_RAW: return m;
     default: return -1;
   }
 }
@@ -74,7 +75,9 @@ __global__ void __launch_bounds__(kHid) meta_forward_kernel(const float* __restr
     acts[(long long)b * na + kHid + j] = z2;
     if (j < nout) acts[(long long)b * na + 2 * kHid + j] = o[j];
   }
-  if (j < m) {
+  if (j < m && head == RICHM_HEAD_RAW) {
+    w_out[(long long)b * m + j] = o[j];
+  } else if (j < m) {
     const long long i = (long long)b * m + j;
     w_out[i] = expf(o[j]) / G[b];
     switch (head) {
@@ -107,7 +110,9 @@ __global__ void __launch_bounds__(kHid) meta_backward_kernel(const float* __rest
   h1[j] = fmaxf(z1, 0.f);
   h2[j] = fmaxf(z2, 0.f);
   const long long row = (long long)b * m;
-  if (j < m) {
+  if (j < m && head == RICHM_HEAD_RAW) {
+    go[j] = g_w[row + j];
+  } else if (j < m) {
     const float wj = expf(A[2 * kHid + j]) / G[b];
     go[j] = g_w[row + j] * wj;  // dw/do = w
   } else if (j < nout) {
@@ -180,7 +185,7 @@ using namespace richm;
 extern "C" {
 
 static richm_status check_head(int m, int head) {
-  RICHM_ARG(head >= RICHM_HEAD_NAG_SHARED && head <= RICHM_HEAD_NAGEX, "unknown meta head %d", head);
+  RICHM_ARG(head >= RICHM_HEAD_NAG_SHARED && head <= RICHM_HEAD_RAW, "unknown meta head %d", head);
   const int nout = head_outputs(head, m);
   RICHM_ARG(m >= 1 && nout <= kHid, "m = %d out of range for head %d (at most %d outputs)", m, head, kHid);
   return RICHM_OK;
@@ -199,7 +204,7 @@ richm_status richm_meta_forward(const float* params, const float* inputs, const 
   clear_error();
   RICHM_TRY(check_head(m, head));
   RICHM_ARG(params && inputs && G && w_out, "null argument");
-  RICHM_ARG(head == RICHM_HEAD_RICHARDSON || alpha_out, "null alpha_out");
+  RICHM_ARG(head == RICHM_HEAD_RICHARDSON || head == RICHM_HEAD_RAW || alpha_out, "null alpha_out");
   RICHM_ARG(head != RICHM_HEAD_NAGEX || alpha_t_out, "null alpha_t_out (NAGex head)");
   RICHM_ARG(B >= 1, "B < 1");
   meta_forward_kernel<<<B, kHid, 0, (cudaStream_t)stream>>>(params, inputs, G, m, head, w_out, alpha_out,
@@ -215,7 +220,7 @@ richm_status richm_meta_backward(const float* params, const float* inputs, const
   clear_error();
   RICHM_TRY(check_head(m, head));
   RICHM_ARG(params && inputs && G && acts && g_w && g_params && work, "null argument");
-  RICHM_ARG(head == RICHM_HEAD_RICHARDSON || g_alpha, "null g_alpha");
+  RICHM_ARG(head == RICHM_HEAD_RICHARDSON || head == RICHM_HEAD_RAW || g_alpha, "null g_alpha");
   RICHM_ARG(head != RICHM_HEAD_NAGEX || g_alpha_t, "null g_alpha_t (NAGex head)");
   RICHM_ARG(B >= 1, "B < 1");
   const int cnt = meta_count(head_outputs(head, m));

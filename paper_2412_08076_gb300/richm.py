@@ -23,9 +23,9 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_UNSUPPORT
 ANISO_Q1, HELMHOLTZ_FD5_ABC, HELMHOLTZ_FD5_DIRICHLET, HELMHOLTZ_FD5_SPONGE = 0, 1, 2, 3
 # richm_dtype
 F64, F32, C64, C128, BF16 = 0, 1, 2, 3, 4
-HEAD_NAG_SHARED, HEAD_RICHARDSON, HEAD_MOM, HEAD_NAG, HEAD_NAGEX = 0, 1, 2, 3, 4
+HEAD_NAG_SHARED, HEAD_RICHARDSON, HEAD_MOM, HEAD_NAG, HEAD_NAGEX, HEAD_RAW = 0, 1, 2, 3, 4, 5
 HEAD_OUTPUTS = {HEAD_NAG_SHARED: lambda m: m + 1, HEAD_RICHARDSON: lambda m: m, HEAD_MOM: lambda m: 2 * m,
-                HEAD_NAG: lambda m: 2 * m, HEAD_NAGEX: lambda m: 3 * m}
+                HEAD_NAG: lambda m: 2 * m, HEAD_NAGEX: lambda m: 3 * m, HEAD_RAW: lambda m: m}
 
 TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, C64: torch.complex64, C128: torch.complex128,
                BF16: torch.bfloat16}
@@ -79,6 +79,14 @@ _SIGS = {
     "richm_gershgorin": (_I, [_P, C.POINTER(_D)]),
     "richm_chebyshev_weights": (_I, [_D, _D, _I, C.POINTER(_D)]),
     "richm_q1_stencil": (_I, [_D, _D, C.POINTER(_D)]),
+    "richm_fns_map_workspace": (_I, [C.POINTER(_SZ)]),
+    "richm_symbol_from_stencil": (_I, [_I, C.POINTER(_D), _P, _P, _P]),
+    "richm_symbol_from_stencil_vjp": (_I, [_I, C.POINTER(_D), _P, _P, _P, _P, _SZ, _P]),
+    "richm_transition_from_band": (_I, [_I, _P, _P, _P]),
+    "richm_transition_from_band_vjp": (_I, [_I, _P, _P, _P, _SZ, _P]),
+    "richm_fourier_correction_t": (_I, [_P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "richm_fourier_t_vjp_workspace": (_I, [_P, C.POINTER(_SZ)]),
+    "richm_fourier_correction_t_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "richm_fgmres_workspace": (_I, [_P, C.POINTER(richm_fgmres_opts), C.POINTER(_SZ)]),
     "richm_fgmres": (_I, [_P, _P, _P, _P, _P, _P, C.POINTER(richm_fgmres_opts), C.POINTER(richm_fgmres_info), _P,
                           _SZ, _P]),
@@ -216,6 +224,51 @@ def leja_order(w) -> list[int]:
     out = (C.c_int * m)()
     _check(load().richm_leja_order(wa, m, out), "richm_leja_order")
     return list(out)
+
+
+def _map_work():
+    b = C.c_size_t()
+    _check(load().richm_fns_map_workspace(C.byref(b)), "richm_fns_map_workspace")
+    return torch.empty(b.value, dtype=torch.uint8, device="cuda")
+
+
+def symbol_from_stencil(n: int, q, o, out=None, stream=None):
+    """richm_symbol_from_stencil: the FNS symbol (complex64 [n][n]) from the base stencil q
+    (6 values: the Q1 stencil and delta's base) and the network outputs o (FP32 [6] device)."""
+    qa = (C.c_double * 6)(*[float(v) for v in q])
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    _check(load().richm_symbol_from_stencil(n, qa, _ptr(o), _ptr(out), _stream(stream)), "richm_symbol_from_stencil")
+    return out
+
+
+def symbol_from_stencil_vjp(n: int, q, o, dsymbol, d_o=None, stream=None):
+    """richm_symbol_from_stencil_vjp: dL/do (FP32 [6] device) from dL/dS."""
+    qa = (C.c_double * 6)(*[float(v) for v in q])
+    if d_o is None:
+        d_o = torch.empty(6, dtype=torch.float32, device="cuda")
+    w = _map_work()
+    _check(load().richm_symbol_from_stencil_vjp(n, qa, _ptr(o), _ptr(dsymbol), _ptr(d_o), _ptr(w), w.numel(),
+                                                _stream(stream)), "richm_symbol_from_stencil_vjp")
+    return d_o
+
+
+def transition_from_band(n: int, tau, out=None, stream=None):
+    """richm_transition_from_band: the transition field (FP32 [n][n]) of the band kernel tau (FP32 [9])."""
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    _check(load().richm_transition_from_band(n, _ptr(tau), _ptr(out), _stream(stream)), "richm_transition_from_band")
+    return out
+
+
+def transition_from_band_vjp(n: int, dtransition, dtau=None, stream=None):
+    """richm_transition_from_band_vjp: dL/dtau (FP32 [9] device) from dL/dt."""
+    if dtau is None:
+        dtau = torch.empty(9, dtype=torch.float32, device="cuda")
+    w = _map_work()
+    _check(load().richm_transition_from_band_vjp(n, _ptr(dtransition), _ptr(dtau), _ptr(w), w.numel(),
+                                                 _stream(stream)), "richm_transition_from_band_vjp")
+    return dtau
 
 
 def meta_param_count(m: int, head: int = HEAD_NAG_SHARED) -> int:
@@ -465,12 +518,29 @@ class Operator:
                                            _ptr(g_alpha_t), _ptr(g_x0), _ptr(work), work.numel(), _stream(stream)),
                "richm_sweeps_adjoint")
 
-    def fourier_correction(self, x, b, symbol, work=None, stream=None):
-        """richm_fourier_correction: x += Re(IFFT2(S * FFT2(b - A x))) (F32 state)."""
+    def fourier_correction(self, x, b, symbol, work=None, stream=None, transition=None):
+        """richm_fourier_correction(_t): x += t Re(IFFT2(S * FFT2(t (b - A x)))) (F32 state;
+        transition t real [n][n], None for T = I)."""
         if work is None:
             work = self.workspace(self._ws("richm_fourier_workspace"))
-        _check(load().richm_fourier_correction(self.handle, F32, _ptr(x), _ptr(b), _ptr(symbol), _ptr(work),
-                                               work.numel(), _stream(stream)), "richm_fourier_correction")
+        if transition is None:
+            _check(load().richm_fourier_correction(self.handle, F32, _ptr(x), _ptr(b), _ptr(symbol), _ptr(work),
+                                                   work.numel(), _stream(stream)), "richm_fourier_correction")
+        else:
+            _check(load().richm_fourier_correction_t(self.handle, F32, _ptr(x), _ptr(b), _ptr(symbol),
+                                                     _ptr(transition), _ptr(work), work.numel(), _stream(stream)),
+                   "richm_fourier_correction_t")
+
+    def fourier_correction_t_vjp(self, x, b, g, symbol, transition, dsymbol=None, dtransition=None, g_x=None,
+                                 work=None, stream=None):
+        """richm_fourier_correction_t_vjp: dsymbol (complex64 [n][n]), dtransition (F32 [n][n]),
+        g_x = g - A (t h) (padded F32; may be g itself); each output may be None."""
+        if work is None:
+            work = self.workspace(self._ws("richm_fourier_t_vjp_workspace"))
+        _check(load().richm_fourier_correction_t_vjp(self.handle, F32, _ptr(x), _ptr(b), _ptr(g), _ptr(symbol),
+                                                     _ptr(transition), _ptr(dsymbol), _ptr(dtransition), _ptr(g_x),
+                                                     _ptr(work), work.numel(), _stream(stream)),
+               "richm_fourier_correction_t_vjp")
 
     def fourier_correction_vjp(self, x, b, g, symbol, dsymbol=None, g_x=None, work=None, stream=None):
         """richm_fourier_correction_vjp: dsymbol = sum_b conj(R) G / n^2 (complex64 [n][n]),
@@ -561,7 +631,7 @@ def meta_forward_head(params, inputs, G, m, head, acts=None, stream=None):
     alpha_t None where at = alpha (NAG heads), zeros for MOM."""
     B = inputs.shape[0]
     w = torch.empty(B, m, dtype=torch.float32, device="cuda")
-    a = None if head == HEAD_RICHARDSON else torch.empty(B, m, dtype=torch.float32, device="cuda")
+    a = None if head in (HEAD_RICHARDSON, HEAD_RAW) else torch.empty(B, m, dtype=torch.float32, device="cuda")
     at = torch.empty(B, m, dtype=torch.float32, device="cuda") if head in (HEAD_MOM, HEAD_NAGEX) else None
     _check(load().richm_meta_forward(_ptr(params), _ptr(inputs), _ptr(G), B, m, head, _ptr(w), _ptr(a), _ptr(at),
                                      _ptr(acts), _stream(stream)), "richm_meta_forward")

@@ -283,3 +283,135 @@ def test_head_training_gradients_match_central_differences():
                 vals.append(mlp_loss_and_grads(P, X, G, m, As, fs, K, head=head, Binvs=Bm)[0])
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - grads[li][0][r, c]) <= 1e-6 * max(1.0, abs(fd)), (head, ssor, li, fd)
+
+
+def _band_kernel(w, seed):
+    """A Hermitian-symmetric (2w+1)^2 band kernel: tau[-d] = conj(tau[d])."""
+    rng = np.random.default_rng(seed)
+    k = 2 * w + 1
+    tau = rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))
+    tau = 0.5 * (tau + np.conj(tau[::-1, ::-1]))
+    tau[w, w] = 1.0 + 0.0j
+    return 0.3 * tau
+
+
+def test_transition_correction_equals_the_matrix_product():
+    # H = F T S T^H F^{-1} written out: DFT matrices for the transforms, T the banded
+    # matrix T[k, k'] = tau[k - k'] (indices mod n) acting on the spectrum, S diagonal
+    from oracle.fourier import fourier_correction, fourier_correction_t, transition_field
+    from oracle.operators import assemble_q1
+    for n, w in [(6, 1), (7, 2), (5, 1)]:
+        A = assemble_q1(n, 0.1, 0.6)
+        rng = np.random.default_rng(n)
+        f, u = rng.standard_normal(n * n), rng.standard_normal(n * n)
+        S = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        tau = _band_kernel(w, n)
+        j = np.arange(n)
+        D1 = np.exp(-2j * np.pi * np.outer(j, j) / n)
+        Fwd = np.kron(D1, D1)                    # fft2 on row-major flattening
+        Inv = np.conj(Fwd) / (n * n)             # ifft2
+        T = np.zeros((n * n, n * n), complex)
+        for k1 in range(n):
+            for k2 in range(n):
+                for a in range(-w, w + 1):
+                    for c in range(-w, w + 1):
+                        T[k1 * n + k2, ((k1 - a) % n) * n + (k2 - c) % n] += tau[a + w, c + w]
+        H = Inv @ T @ np.diag(S.ravel()) @ T.conj().T @ Fwd
+        ref = u + (H @ (f - A @ u)).real
+        got = fourier_correction_t(A, f, u, S, transition_field(tau, n))
+        np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11)
+        # the identity transition is the plain correction
+        np.testing.assert_allclose(fourier_correction_t(A, f, u, S, np.ones((n, n))),
+                                   fourier_correction(A, f, u, S), rtol=1e-13, atol=1e-13)
+
+
+def test_transition_vjp_matches_central_differences():
+    from oracle.fourier import fourier_correction_t, fourier_correction_t_vjp, transition_field
+    from oracle.operators import assemble_q1
+    n = 6
+    A = assemble_q1(n, 0.05, 1.1)
+    rng = np.random.default_rng(9)
+    f, u, g = rng.standard_normal(n * n), rng.standard_normal(n * n), rng.standard_normal(n * n)
+    S = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    t = transition_field(_band_kernel(1, 3), n)
+    dS, dt, du = fourier_correction_t_vjp(A, f, u, S, t, g)
+
+    def L(S_, t_, u_):
+        return float(np.dot(g, fourier_correction_t(A, f, u_, S_, t_)))
+    h = 1e-6
+    for (a, c) in [(0, 0), (2, 5), (4, 1)]:
+        E = np.zeros((n, n))
+        E[a, c] = h
+        assert abs((L(S + E, t, u) - L(S - E, t, u)) / (2 * h) - dS[a, c].real) < 1e-7
+        assert abs((L(S + 1j * E, t, u) - L(S - 1j * E, t, u)) / (2 * h) - dS[a, c].imag) < 1e-7
+        assert abs((L(S, t + E, u) - L(S, t - E, u)) / (2 * h) - dt[a, c]) < 1e-7
+        e = E.ravel()
+        assert abs((L(S, t, u + e) - L(S, t, u - e)) / (2 * h) - du[a * n + c]) < 1e-7
+
+
+def test_symbol_map_is_the_periodic_spectrum_and_has_its_gradient():
+    # o = 0 and no regularisation: 1/S is the spectrum of the periodic extension of the Q1
+    # operator (a block-circulant matrix built from the stencil), in DFT order
+    from oracle.fourier import symbol_from_stencil
+    import math
+    n = 6
+    eps, th = 0.1, 0.7
+    c, s = math.cos(th), math.sin(th)
+    c11, c22, c12 = c * c + eps * s * s, s * s + eps * c * c, (1 - eps) * s * c
+    q = [4 * (c11 + c22) / 3, (c22 - 2 * c11) / 3, (c11 - 2 * c22) / 3,
+         -(c11 + c22) / 6 - c12 / 2, -(c11 + c22) / 6 + c12 / 2, 1e-9]
+    P = np.zeros((n * n, n * n))
+    for i in range(n):
+        for j in range(n):
+            for (di, dj, v) in [(0, 0, q[0]), (0, -1, q[1]), (0, 1, q[1]), (-1, 0, q[2]), (1, 0, q[2]),
+                                (1, 1, q[3]), (-1, -1, q[3]), (-1, 1, q[4]), (1, -1, q[4])]:
+                P[i * n + j, ((i + di) % n) * n + (j + dj) % n] += v
+    S = symbol_from_stencil(q, np.zeros(6), n)
+    # every DFT mode is an eigenvector of the circulant operator with eigenvalue sigma(k),
+    # and S = 1/sigma there (the k = 0 mode: sigma = 0, S bounded by 1/(2 delta))
+    for k1 in range(n):
+        for k2 in range(n):
+            v = np.exp(2j * np.pi * (k1 * np.arange(n)[:, None] + k2 * np.arange(n)[None, :]) / n).ravel()
+            Pv = P @ v
+            if k1 == 0 and k2 == 0:
+                assert np.abs(Pv).max() < 1e-12 and abs(S[0, 0]) <= 0.5 / 1e-9  # at most 1/(2 delta)
+            else:
+                np.testing.assert_allclose(Pv, v / S[k1, k2].real, rtol=1e-9, atol=1e-12)
+    # the reverse mode: dL/do for L = Re sum conj(G) S, against central differences
+    from oracle.fourier import symbol_from_stencil as sym
+    rng = np.random.default_rng(1)
+    G = rng.standard_normal((n, n))
+    o = 0.1 * rng.standard_normal(6)
+    q2 = list(q[:5]) + [0.2]
+    h = 1e-6
+    for m in range(6):
+        e = np.zeros(6)
+        e[m] = h
+        fd = (np.sum(G * sym(q2, o + e, n).real) - np.sum(G * sym(q2, o - e, n).real)) / (2 * h)
+        t = 2.0 * np.pi * np.arange(n) / n
+        t1, t2 = np.meshgrid(t, t, indexing="ij")
+        p = np.array(q2[:5]) * np.exp(o[:5])
+        d = q2[5] * np.exp(o[5])
+        basis = [np.ones_like(t1), 2 * np.cos(t2), 2 * np.cos(t1), 2 * np.cos(t1 + t2), 2 * np.cos(t1 - t2)]
+        sig = sum(pm * bm for pm, bm in zip(p, basis))
+        den = sig ** 2 + d ** 2
+        if m < 5:
+            an = np.sum(G * (d * d - sig ** 2) / den ** 2 * basis[m] * p[m])
+        else:
+            an = np.sum(G * (-2 * sig * d) / den ** 2 * d)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+def test_transition_band_parametrisation():
+    from oracle.fourier import transition_band, transition_field
+    n = 7
+    tau9 = np.array([1.0, 0.1, -0.2, 0.05, 0.3, -0.15, 0.02, 0.07, -0.01])
+    t = transition_band(tau9, n)
+    # written out term by term
+    i, j = np.arange(n)[:, None], np.arange(n)[None, :]
+    ref = tau9[0] + 0 * i * j
+    for q, (a, c) in enumerate([(0, 1), (1, 0), (1, 1), (1, -1)]):
+        ang = 2 * np.pi * (a * i + c * j) / n
+        ref = ref + 2 * (tau9[1 + 2 * q] * np.cos(ang) - tau9[2 + 2 * q] * np.sin(ang))
+    np.testing.assert_allclose(t, ref, atol=1e-12)
+    assert np.isrealobj(t)
