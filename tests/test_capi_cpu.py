@@ -71,13 +71,14 @@ def test_meta_param_count_and_version(clib):
     assert clib.richm_meta_param_count(16, 0, ctypes.byref(c)) == 0
     assert c.value == 2 * 64 + 64 + 64 * 64 + 64 + 17 * 64 + 17 == 5457
     base = 2 * 64 + 64 + 64 * 64 + 64
-    for head, nout in ((1, 16), (2, 32), (3, 32), (4, 48)):
+    for head, nout in ((1, 16), (2, 32), (3, 32), (4, 48), (5, 16)):
         assert clib.richm_meta_param_count(16, head, ctypes.byref(c)) == 0
         assert c.value == base + 65 * nout
     assert clib.richm_meta_param_count(0, 0, ctypes.byref(c)) == 1
     assert clib.richm_meta_param_count(22, 4, ctypes.byref(c)) == 1  # 66 outputs > 64
     assert clib.richm_meta_param_count(21, 4, ctypes.byref(c)) == 0
-    assert clib.richm_meta_param_count(3, 5, ctypes.byref(c)) == 1   # unknown head
+    assert clib.richm_meta_param_count(64, 5, ctypes.byref(c)) == 0  # raw head: m outputs
+    assert clib.richm_meta_param_count(3, 6, ctypes.byref(c)) == 1   # unknown head
     clib.richm_version.restype = ctypes.c_char_p
     assert b"richm" in clib.richm_version()
 
