@@ -915,9 +915,17 @@ def record_traffic(report: str, kind: str, unknowns: int) -> float:
     hdr, units, data = rows[0], rows[1], rows[2]
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
     tot = 0.0
-    for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-        i = hdr.index(name)
-        tot += float(data[i].replace(",", "")) * scale[units[i]]
+    if "dram__bytes_read.sum" in hdr:
+        for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            i = hdr.index(name)
+            tot += float(data[i].replace(",", "")) * scale[units[i]]
+    else:  # a capture by sections: the DRAM byte rate times the launch's duration
+        i = hdr.index("dram__bytes.sum.per_second")
+        rate = float(data[i].replace(",", "")) * {"byte/s": 1.0, "Kbyte/s": 1e3, "Mbyte/s": 1e6,
+                                                   "Gbyte/s": 1e9, "Tbyte/s": 1e12}[units[i]]
+        j = hdr.index("gpu__time_duration.sum")
+        dur = float(data[j].replace(",", "")) * {"nsecond": 1e-9, "ns": 1e-9, "usecond": 1e-6, "us": 1e-6, "msecond": 1e-3, "ms": 1e-3}[units[j]]
+        tot = rate * dur
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES[kind]:
         with open(os.path.join(ROOT, f), "rb") as fh:
