@@ -357,6 +357,29 @@ richm_status richm_solver_step(richm_solver* s, int cycles, int* active_out, voi
 richm_status richm_solver_finish(richm_solver* s, richm_solve_info* info, void* stream);
 void richm_solver_destroy(richm_solver* s);
 
+/* Checkpoint and resume of a solver session between steps (no counterpart in the
+ * paper; the solve of eq. 15's iteration to tolerance run in several processes).
+ * richm_solver_state_bytes gives the size of the session's image; richm_solver_save
+ * waits for `stream` and the session's own stream and copies the image into `host`
+ * (bytes at least that size; pageable or pinned host memory, owned by the caller): a
+ * 128-byte header (magic "RICHMSV1", version 1, batch, elems, opts->inner, the resolved
+ * fuse, m, refine_every, precond, tol, max_sweeps, the cycle count, an FNV-1a hash of
+ * every instance's kind, sizes and stencil, an FNV-1a hash of the weights' bytes), then
+ * the current x (FP64, padded), the second FP64 buffer (inner RICHM_F32 / RICHM_BF16),
+ * the four inner-state buffers, the inner right-hand side and the per-instance norms,
+ * sweep counts, statuses and active flags. The caller may write it to a file.
+ * richm_solver_resume binds b and x like richm_solver_start and restores the image into
+ * a session created (in this process or another) for the same instances, options and
+ * weights; it returns RICHM_ERR_ARG, restoring nothing, if the header does not match.
+ * richm_solver_step then continues with the saved cycle count, and the cycles give the
+ * same bits as in the uninterrupted session. Both calls are synchronous and must not run
+ * during stream capture. Errors: RICHM_ERR_ARG (null, not started, mismatch),
+ * RICHM_ERR_NOMEM (host buffer too small), RICHM_ERR_CUDA. */
+richm_status richm_solver_state_bytes(const richm_solver* s, size_t* bytes);
+richm_status richm_solver_save(richm_solver* s, void* host, size_t bytes, void* stream);
+richm_status richm_solver_resume(richm_solver* s, const double* b, double* x, const void* host, size_t bytes,
+                                 void* stream);
+
 /* richm_solve from host memory, from the initial guess 0: copies b_host (dense,
  * instances concatenated, n_b*n_b row-major, FP64; pinned memory makes the copy
  * asynchronous and fast) to the device, packs it, solves as richm_solve, unpacks the

@@ -905,3 +905,180 @@ richm_status richm_solve(richm_operator* op, const double* b, double* x, const v
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- checkpoint / resume
+// A solver session's state between steps, as one host byte image: a fixed header, then
+// the iterate x, the second FP64 buffer (fused cycles), the four inner-state buffers,
+// the inner right-hand side and the per-instance records. The header carries what a
+// resumed session must share with the saved one (batch layout, options, a hash of the
+// instances' stencils and of the weights) and the cycle count; the per-cycle norm
+// partials are scratch and not saved. Resuming in another process continues the same
+// arithmetic: the cycles that follow give the same bits as an uninterrupted session.
+
+namespace {
+
+struct SolverImageHeader {
+  char magic[8];  // "RICHMSV1"
+  unsigned version, header_bytes;
+  int batch, inner, fuse, m, refine_every, precond;
+  long long elems, cycles_run, max_sweeps, total_bytes;
+  double tol;
+  unsigned long long op_hash, weights_hash;
+  char pad[32];
+};
+static_assert(sizeof(SolverImageHeader) == 128, "image header layout");
+
+unsigned long long fnv1a(const void* p, size_t n, unsigned long long h = 1469598103934665603ull) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  return h;
+}
+
+unsigned long long operator_hash(const richm_operator* op) {
+  unsigned long long h = fnv1a(&op->batch, sizeof(int));
+  for (int b = 0; b < op->batch; ++b) {
+    const Inst& I = op->h_inst[b];
+    const double v[9] = {I.c, I.ax, I.ay, I.d1, I.d2, I.abc_re, I.abc_im, I.sp_im, I.sp_iw};
+    const int k[3] = {I.n, I.pitch, I.kind};
+    h = fnv1a(k, sizeof(k), h);
+    h = fnv1a(v, sizeof(v), h);
+  }
+  return h;
+}
+
+richm_status weights_hash(const richm_solver* S, unsigned long long* out) {
+  const size_t n = (size_t)S->op->batch * S->o.m * (S->o.inner == RICHM_F64 ? 8 : 4);
+  std::vector<unsigned char> h(n);
+  unsigned long long v = 1469598103934665603ull;
+  for (const void* p : {S->w, S->a, S->at}) {
+    const unsigned char tag = p ? 1 : 0;
+    v = fnv1a(&tag, 1, v);
+    if (!p) continue;
+    RICHM_CUDA_TRY(cudaMemcpy(h.data(), p, n, cudaMemcpyDeviceToHost));
+    v = fnv1a(h.data(), n, v);
+  }
+  *out = v;
+  return RICHM_OK;
+}
+
+// (device pointer, bytes) of every saved part, in image order.
+std::vector<std::pair<void*, size_t>> image_parts(const richm_solver* S, double* x) {
+  const richm_operator* op = S->op;
+  const size_t el = (size_t)op->elems, B = (size_t)op->batch;
+  const size_t es = S->o.inner == RICHM_F64 ? 8 : (S->o.inner == RICHM_F32 ? 4 : 2);
+  const size_t rs = S->o.inner == RICHM_F64 ? 8 : 4;
+  std::vector<std::pair<void*, size_t>> v;
+  v.push_back({x, el * sizeof(double)});
+  if (S->x2) v.push_back({S->x2, el * sizeof(double)});
+  for (int i = 0; i < 4; ++i) v.push_back({S->E[i], el * es});
+  v.push_back({S->rhs, el * rs});
+  v.push_back({S->bnorm, B * sizeof(double)});
+  v.push_back({S->rel, B * sizeof(double)});
+  v.push_back({S->sweeps, B * sizeof(long long)});
+  v.push_back({S->status, B * sizeof(int)});
+  v.push_back({S->active, B * sizeof(int)});
+  v.push_back({S->xloc, B * sizeof(int)});
+  v.push_back({S->count, sizeof(int)});
+  return v;
+}
+
+size_t image_bytes(const richm_solver* S) {
+  size_t n = sizeof(SolverImageHeader);
+  for (const auto& p : image_parts(S, nullptr)) n += p.second;
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+richm_status richm_solver_state_bytes(const richm_solver* S, size_t* bytes) {
+  clear_error();
+  RICHM_ARG(S != nullptr && bytes != nullptr, "null argument");
+  *bytes = image_bytes(S);
+  return RICHM_OK;
+}
+
+richm_status richm_solver_save(richm_solver* S, void* host, size_t bytes, void* stream) {
+  clear_error();
+  RICHM_ARG(S != nullptr && host != nullptr, "null argument");
+  RICHM_ARG(S->started, "richm_solver_start has not been called");
+  const size_t need = image_bytes(S);
+  if (bytes < need) return set_error(RICHM_ERR_NOMEM, "image buffer %zu < %zu bytes", bytes, need);
+  RICHM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
+  SolverImageHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "RICHMSV1", 8);
+  h.version = 1;
+  h.header_bytes = sizeof(h);
+  h.batch = S->op->batch;
+  h.inner = S->o.inner;
+  h.fuse = S->o.fuse;
+  h.m = S->o.m;
+  h.refine_every = S->o.refine_every;
+  h.precond = S->o.precond;
+  h.elems = S->op->elems;
+  h.cycles_run = S->cycles_run;
+  h.max_sweeps = S->o.max_sweeps;
+  h.total_bytes = (long long)need;
+  h.tol = S->o.tol;
+  h.op_hash = operator_hash(S->op);
+  RICHM_TRY(weights_hash(S, &h.weights_hash));
+  unsigned char* p = static_cast<unsigned char*>(host);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  for (const auto& part : image_parts(S, S->x)) {
+    RICHM_CUDA_TRY(cudaMemcpy(p, part.first, part.second, cudaMemcpyDeviceToHost));
+    p += part.second;
+  }
+  return RICHM_OK;
+}
+
+richm_status richm_solver_resume(richm_solver* S, const double* b, double* x, const void* host, size_t bytes,
+                                 void* stream) {
+  clear_error();
+  RICHM_ARG(S != nullptr && b != nullptr && x != nullptr && host != nullptr, "null argument");
+  RICHM_ARG(bytes >= sizeof(SolverImageHeader), "image of %zu bytes is shorter than its header", bytes);
+  SolverImageHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  RICHM_ARG(std::memcmp(h.magic, "RICHMSV1", 8) == 0 && h.version == 1 && h.header_bytes == sizeof(h),
+            "not a solver image of this version");
+  const size_t need = image_bytes(S);
+  RICHM_ARG(h.total_bytes == (long long)need && bytes >= need, "image of %lld bytes, this session needs %zu",
+            h.total_bytes, need);
+  RICHM_ARG(h.batch == S->op->batch && h.elems == S->op->elems && h.op_hash == operator_hash(S->op),
+            "the image was saved for other instances");
+  RICHM_ARG(h.inner == S->o.inner && h.fuse == S->o.fuse && h.m == S->o.m && h.refine_every == S->o.refine_every &&
+                h.precond == S->o.precond && h.tol == S->o.tol && h.max_sweeps == S->o.max_sweeps,
+            "the image was saved with other solve options (inner %d, fuse %d, m %d, refine_every %d)", h.inner,
+            h.fuse, h.m, h.refine_every);
+  unsigned long long wh = 0;
+  RICHM_TRY(weights_hash(S, &wh));
+  RICHM_ARG(wh == h.weights_hash, "the image was saved with other weights");
+  RICHM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
+  if (S->b != b || S->x != x) {
+    for (auto& kv : S->execs) cudaGraphExecDestroy(kv.second);
+    S->execs.clear();
+  }
+  S->b = b;
+  S->x = x;
+  const unsigned char* p = static_cast<const unsigned char*>(host) + sizeof(h);
+  for (const auto& part : image_parts(S, x)) {
+    RICHM_CUDA_TRY(cudaMemcpy(part.first, p, part.second, cudaMemcpyHostToDevice));
+    p += part.second;
+  }
+  S->cycles_run = h.cycles_run;
+  S->rows_now = S->rows_max;
+  if (S->o.fuse > 1) {
+    RICHM_CUDA_TRY(cudaMemcpy(S->h_count + 1, S->active, sizeof(int) * S->op->batch, cudaMemcpyDeviceToHost));
+    int act = 0;
+    for (int i = 0; i < S->op->batch; ++i) act += S->h_count[1 + i] != 0;
+    if (act > 0) S->rows_now = choose_rows(S);
+  }
+  S->started = true;
+  return RICHM_OK;
+}
+
+}  // extern "C"

@@ -116,6 +116,9 @@ _SIGS = {
                               _SZ, _P]),
     "richm_solver_step": (_I, [_P, _I, C.POINTER(_I), _P]),
     "richm_solver_finish": (_I, [_P, C.POINTER(richm_solve_info), _P]),
+    "richm_solver_state_bytes": (_I, [_P, C.POINTER(C.c_size_t)]),
+    "richm_solver_save": (_I, [_P, _P, C.c_size_t, _P]),
+    "richm_solver_resume": (_I, [_P, _P, _P, _P, C.c_size_t, _P]),
     "richm_solver_destroy": (None, [_P]),
     "richm_refine": (_I, [_P, _P, _P, _P, _P, _I, _P, _P, _P, _SZ, _P]),
     "richm_checkpoint_elems": (_I, [_P, _I, _I, C.POINTER(_SZ)]),
@@ -603,6 +606,21 @@ class Solver:
         if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
             _check(st, "richm_solver_finish")
         return st, [(info[i].sweeps, info[i].rel_res, info[i].status) for i in range(self.op.batch)]
+
+    def save(self, stream=None) -> bytes:
+        """richm_solver_save: the session's image (between steps) as bytes."""
+        n = C.c_size_t()
+        _check(load().richm_solver_state_bytes(self.handle, C.byref(n)), "richm_solver_state_bytes")
+        buf = (C.c_ubyte * n.value)()
+        _check(load().richm_solver_save(self.handle, C.addressof(buf), n.value, _stream(stream)), "richm_solver_save")
+        return bytes(buf)
+
+    def resume(self, b, x, image: bytes, stream=None):
+        """richm_solver_resume: bind b and x and restore a saved image."""
+        self.bx = (b, x)
+        buf = (C.c_ubyte * len(image)).from_buffer_copy(image)
+        _check(load().richm_solver_resume(self.handle, _ptr(b), _ptr(x), C.addressof(buf), len(image),
+                                          _stream(stream)), "richm_solver_resume")
 
     def close(self):
         if getattr(self, "handle", None):
