@@ -451,8 +451,9 @@ richm_status richm_fgmres(richm_operator* op, const void* b, void* x, const void
 richm_status richm_checkpoint_elems(const richm_operator* op, int K, int ckpt_every, size_t* elems);
 
 /* Forward K sweeps from x0 with zero initial velocity (x_{-1} = x0), storing the
- * checkpoints; xK receives x_K (padded). Same coefficient conventions as
- * richm_apply_sweeps: precond 0 none, 1 Jacobi, 2 SSOR with relaxation factor relax
+ * checkpoints; xK receives x_K (padded). dtype: RICHM_F32 / RICHM_F64 (Q1) or
+ * RICHM_C64 / RICHM_C128 (Helmholtz, precond 0 only; the weights in the real type).
+ * Same coefficient conventions as richm_apply_sweeps: precond 0 none, 1 Jacobi, 2 SSOR with relaxation factor relax
  * in (0, 2) (ignored otherwise). Requires K % ckpt_every == 0. work: at least
  * richm_adjoint_workspace bytes (four padded buffers suffice). Only the interior rows
  * (and their padding columns) of the slots after slot 0 are written, and xK is a copy
@@ -467,14 +468,19 @@ richm_status richm_adjoint_workspace(const richm_operator* op, richm_dtype dtype
 
 /* Training loss (the log form of eq. 15, the L2 loss of Algorithm 1):
  *   L = (1/B) sum_b ln(||b_b - A_b x_b|| / ||b_b||),
- * and its gradient g = dL/dx = -(1/B) A r / ||r||^2 (A symmetric), r = b - A x.
- * loss: device scalar (FP64); g: padded buffer (dtype of x) or NULL. */
+ * and its gradient g = dL/dx = -(1/B) A^H r / ||r||^2, r = b - A x (A^H = A for Q1; for
+ * the complex Helmholtz dtypes g = dL/dRe x + i dL/dIm x and A^H = conj(A), the 5-point
+ * matrix being complex symmetric). loss: device scalar (FP64); g: padded buffer (dtype
+ * of x) or NULL. */
 richm_status richm_loss_log_residual(richm_operator* op, richm_dtype dtype, const void* x, const void* b,
                                      double* loss, void* g, void* work, size_t work_bytes, void* stream);
 
 /* Reverse-mode sweep ("backpropagate", Algorithm 1) over the K sweeps recorded by
  * richm_forward_checkpointed (same precond and relax), with A and B^{-1} symmetric so
- * the adjoint applies the same stencil and preconditioner: for k = K-1 .. 0
+ * the adjoint applies the same stencil and preconditioner. Complex (Helmholtz) dtypes
+ * (precond 0, real weights) use A^H = conj(A) in place of A for q and the real parts
+ * of the complex inner products <u, v> = sum conj(u) v; lam and the gradients with
+ * respect to x0 are dL/dRe + i dL/dIm. For k = K-1 .. 0
  * (i = k mod m), with lam_{k+1} = dL/dx_{k+1}, u = B^{-1} lam_{k+1} (for SSOR one
  * forward and one backward triangular solve per step) and q = w_i A u,
  *   dL/dw_i   += <lam_{k+1}, B^{-1}(b - A y_k)> = <u, b - A y_k>

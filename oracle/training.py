@@ -107,6 +107,44 @@ def loss_only(As, fs, u0s, ws, alphas, K, Binvs=None):
     return tot / len(As)
 
 
+def loss_and_grads_general(As, fs, u0s, ws, alphas, alpha_ts, K):
+    """The mean log relative residual after K steps of Table 1's NAGex form (at = None:
+    NAG; alphas = None: Richardson(m)) for real or complex states (the Helmholtz
+    operators: As complex scipy matrices, fs and u0s complex arrays, real weights), and
+    its gradients (dL/dw, dL/dalpha, dL/dalpha_t (B, m) each or None, [dL/du0_b]). For a
+    complex u0 the gradient is dL/dRe u0 + i dL/dIm u0, PyTorch's convention for a real
+    function of complex leaves. Pinned by: central finite differences of the same
+    forward in every weight and in the real and imaginary parts of u0 (tests)."""
+    B = len(As)
+    w_t = torch.tensor(np.asarray(ws, dtype=np.float64), requires_grad=True)
+    a_t = None if alphas is None else torch.tensor(np.asarray(alphas, dtype=np.float64), requires_grad=True)
+    at_t = None if alpha_ts is None else torch.tensor(np.asarray(alpha_ts, dtype=np.float64), requires_grad=True)
+    u0_t = [torch.tensor(np.asarray(u), requires_grad=True) for u in u0s]
+    total = 0.0
+    for b in range(B):
+        At = to_torch_sparse(As[b])
+        f = torch.from_numpy(np.asarray(fs[b]))
+        a_b = torch.zeros_like(w_t[b]) if a_t is None else a_t[b]
+        uK = unrolled_nag(At, f, u0_t[b], w_t[b], a_b, K, at=None if at_t is None else at_t[b])
+        total = total + log_rel_residual(At, f, uK)
+    L = total / B
+    L.backward()
+    return (float(L.detach()), w_t.grad.numpy(), None if a_t is None else a_t.grad.numpy(),
+            None if at_t is None else at_t.grad.numpy(), [u.grad.numpy() for u in u0_t])
+
+
+def loss_general(As, fs, u0s, ws, alphas, alpha_ts, K):
+    """The loss of ``loss_and_grads_general`` by the numpy iteration of
+    ``oracle.iterations.inner_steps`` (no autograd; for finite differences)."""
+    from oracle.iterations import inner_steps
+    tot = 0.0
+    for b in range(len(As)):
+        u, _ = inner_steps(As[b], fs[b], u0s[b], None, ws[b], None if alphas is None else alphas[b],
+                           None if alpha_ts is None else alpha_ts[b], K=K)
+        tot += np.log(np.linalg.norm(fs[b] - As[b] @ u) / np.linalg.norm(fs[b]))
+    return tot / len(As)
+
+
 # ---------------------------------------------------------------- meta network
 
 def mlp_forward(params, X):

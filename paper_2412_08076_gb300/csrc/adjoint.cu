@@ -14,6 +14,13 @@
 // With the SSOR preconditioner (d replaced by the symmetric matrix B^{-1}) the step
 // first forms u = B^{-1} lam_{k+1} with the SSOR solves; then q = w_i A u and, because
 // <lam, B^{-1} r> = <B^{-1} lam, r>, dL/dw_i += <u, b - A y> with no second solve.
+//
+// Complex states (the Helmholtz operators of eqs. 21-22, real weights): with the
+// gradient of a real loss written g = dL/dRe x + i dL/dIm x, so that dL = Re<g, dx>
+// with <u, v> = sum conj(u) v, the same recursion holds with A^T replaced by A^H. The
+// 5-point Helmholtz matrix is complex symmetric (its absorbing and sponge terms sit on
+// the diagonal), so A^H = conj(A): the stencil with the imaginary parts of its diagonal
+// negated; the weight gradients are the real parts of the inner products above.
 #include <type_traits>
 
 #include "common.cuh"
@@ -246,6 +253,151 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
+
+// One adjoint step for complex states (no preconditioner): rows walk down a warp tile
+// of 32 * VW columns with plain vector loads (the state of a complex tile row is 16
+// bytes per lane), the stencils of y (for b - A y) and of lam (for A^H lam) kept as
+// three-row windows.
+template <typename C, bool MOM>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    adjoint_cx_kernel(const Inst* insts, const Tile* tiles, int ntiles, const C* __restrict__ lam,
+                      const C* __restrict__ carry, const C* __restrict__ x, const C* __restrict__ xp,
+                      const C* __restrict__ b, C* __restrict__ lam_out, C* __restrict__ carry_out,
+                      const typename RealOf<C>::type* __restrict__ w, const typename RealOf<C>::type* __restrict__ a,
+                      const typename RealOf<C>::type* __restrict__ at, int m, int kidx, int final_step,
+                      Dot3* __restrict__ partials) {
+  using R = typename RealOf<C>::type;
+  constexpr int VW = VecWidth<C>::value;
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile t = tiles[wt];
+  const Inst& I = insts[t.inst];
+  const int n = I.n, pitch = I.pitch;
+  const int cidx = t.inst * m + kidx;
+  const R wi = w[cidx];
+  R ai = 0, ati = 0;
+  if (MOM) {
+    ai = a[cidx];
+    ati = at ? at[cidx] : ai;
+  }
+  const R sc = (R)I.c, soff = (R)I.ax, abr = (R)I.abc_re, abi = (R)I.abc_im, spi = (R)I.sp_im, spw = (R)I.sp_iw;
+  const int c0 = t.tx * 32 * VW + lane * VW;
+  const bool live = c0 < pitch;
+  const int r0 = t.ty * kRows + 1;
+  const int r1 = min(r0 + kRows - 1, n);
+  const long long off = I.off;
+  const bool has_carry = MOM && carry != nullptr;
+  const C z{};
+  // row pr of y = x + at (x - x_prev) with its neighbours; x, x_prev of the row kept
+  auto load_y = [&](int pr, RowT<C, VW>& Y, C* xs, C* xps) {
+    const bool in = (pr >= 1) && (pr <= n);
+    const long long ro = off + (long long)pr * pitch;
+    VecN<C, VW> X{}, XP{};
+    if (in && live) {
+      X = ldv<C, VW>(x + ro + c0);
+      if (MOM) XP = ldv<C, VW>(xp + ro + c0);
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      Y.y[e] = MOM ? X.v[e] + ati * (X.v[e] - XP.v[e]) : X.v[e];
+      xs[e] = X.v[e];
+      xps[e] = XP.v[e];
+    }
+    C le = z, re = z;
+    if (in) {
+      if (lane == 0 && c0 > 0) {
+        le = x[ro + c0 - 1];
+        if (MOM) le = le + ati * (le - xp[ro + c0 - 1]);
+      }
+      if (lane == 31 && c0 + VW < pitch) {
+        re = x[ro + c0 + VW];
+        if (MOM) re = re + ati * (re - xp[ro + c0 + VW]);
+      }
+    }
+    row_neighbours<C, VW>(Y, lane, le, re);
+  };
+  auto load_l = [&](int pr, RowT<C, VW>& L) {
+    const bool in = (pr >= 1) && (pr <= n);
+    const long long ro = off + (long long)pr * pitch;
+    VecN<C, VW> Lv{};
+    if (in && live) Lv = ldv<C, VW>(lam + ro + c0);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) L.y[e] = Lv.v[e];
+    C le = z, re = z;
+    if (in) {
+      if (lane == 0 && c0 > 0) le = lam[ro + c0 - 1];
+      if (lane == 31 && c0 + VW < pitch) re = lam[ro + c0 + VW];
+    }
+    row_neighbours<C, VW>(L, lane, le, re);
+  };
+  double s_w = 0.0, s_a = 0.0, s_at = 0.0;
+  RowT<C, VW> YU, YC, YD, LU, LC, LD;
+  C xC[VW], xpC[VW], xD[VW], xpD[VW], t0[VW], t1[VW];
+  load_y(r0 - 1, YU, t0, t1);
+  load_y(r0, YC, xC, xpC);
+  load_l(r0 - 1, LU);
+  load_l(r0, LC);
+  for (int r = r0; r <= r1; ++r) {
+    load_y(r + 1, YD, xD, xpD);
+    load_l(r + 1, LD);
+    const long long ro = off + (long long)r * pitch + c0;
+    VecN<C, VW> Bv{}, Cv{};
+    if (live) {
+      Bv = ldv<C, VW>(b + ro);
+      if (has_carry) Cv = ldv<C, VW>(carry + ro);
+    }
+    C Ay[VW], Al[VW];
+    apply_fd5<C, VW, R>(YU, YC, YD, r - 1, c0, n, sc, soff, abr, abi, spi, spw, Ay);
+    apply_fd5<C, VW, R>(LU, LC, LD, r - 1, c0, n, sc, soff, abr, -abi, -spi, spw, Al);  // conj(A) lam
+    VecN<C, VW> Lo, Co;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const bool ok = (c0 + e) < n;
+      const C l = LC.y[e];
+      const C q = wi * Al[e];
+      const C dr = Bv.v[e] - Ay[e];
+      const C v = MOM ? xC[e] - xpC[e] : z;
+      C ln = MOM ? ((R(1) + ai) * l - (R(1) + ati) * q) + Cv.v[e] : l - q;
+      const C cn = MOM ? (-ai) * l + ati * q : z;
+      if (ok) {
+        s_w += (double)l.re * (double)dr.re + (double)l.im * (double)dr.im;
+        if (MOM) {
+          s_a += (double)l.re * (double)v.re + (double)l.im * (double)v.im;
+          s_at += (double)q.re * (double)v.re + (double)q.im * (double)v.im;
+        }
+      }
+      if (final_step) ln = ln + cn;
+      Lo.v[e] = ok ? ln : z;
+      Co.v[e] = ok ? cn : z;
+    }
+    if (live) {
+      stv<C, VW>(lam_out + ro, Lo);
+      if (MOM && !final_step) stv<C, VW>(carry_out + ro, Co);
+    }
+    YU = YC;
+    YC = YD;
+    LU = LC;
+    LC = LD;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      xC[e] = xD[e];
+      xpC[e] = xpD[e];
+    }
+  }
+  s_w = warp_sum(s_w);
+  s_a = warp_sum(s_a);
+  s_at = warp_sum(s_at);
+  if (lane == 0) {
+    Dot3 d;
+    d.v[0] = s_w;
+    d.v[1] = s_a;
+    d.v[2] = s_at;
+    d.v[3] = 0.0;
+    partials[wt] = d;
+  }
+}
+
 // The adjoint kernels' rings exceed the default 48 KB of dynamic shared memory.
 template <typename T>
 static cudaError_t adjoint_attributes_t() {
@@ -296,7 +448,7 @@ __global__ void adjoint_reduce_kernel(const Dot3* __restrict__ partials, const i
 
 template <typename T>
 __global__ void adjoint_finish_kernel(const double* __restrict__ acc, int count, T* g_w, T* g_a, T* g_at,
-                                      int nag) {
+                                      int nag) {  // T: the weights' real type
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const double dw = acc[3 * i], da = acc[3 * i + 1], dat = -acc[3 * i + 2];
@@ -338,18 +490,46 @@ static richm_status launch_adjoint(richm_operator* op, const T* lam, const T* ub
   return RICHM_OK;
 }
 
-// One forward sweep with any preconditioner (z: SSOR scratch).
+template <typename C>
+static richm_status launch_adjoint_cx(richm_operator* op, const C* lam, const C* carry, const C* x, const C* xp,
+                                      const C* b, C* lam_out, C* carry_out, const typename RealOf<C>::type* w,
+                                      const typename RealOf<C>::type* a, const typename RealOf<C>::type* at, int m,
+                                      int kidx, int final_step, Dot3* partials, double* acc, cudaStream_t s) {
+  constexpr int VW = VecWidth<C>::value;
+  const TileMap* tm = nullptr;
+  RICHM_TRY(get_tiles(op, 32 * VW, kRows, &tm));
+  const int blocks = (tm->ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int thr = kWarpsPerBlock * 32;
+  if (a != nullptr)
+    adjoint_cx_kernel<C, true><<<blocks, thr, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, lam, carry, x, xp, b,
+                                                      lam_out, carry_out, w, a, at, m, kidx, final_step, partials);
+  else
+    adjoint_cx_kernel<C, false><<<blocks, thr, 0, s>>>(op->d_inst, tm->d_tiles, tm->ntiles, lam, carry, x, xp, b,
+                                                       lam_out, carry_out, w, a, at, m, kidx, final_step, partials);
+  RICHM_LAUNCH_CHECK("complex adjoint sweep");
+  const int wpb = 8;
+  adjoint_reduce_kernel<<<(op->batch + wpb - 1) / wpb, wpb * 32, 0, s>>>(partials, tm->d_inst_begin, op->batch, m,
+                                                                         kidx, acc);
+  RICHM_LAUNCH_CHECK("adjoint reduce");
+  return RICHM_OK;
+}
+
+// One forward sweep with any preconditioner (z: SSOR scratch; real states only).
 template <typename T>
-static richm_status sweep_any(richm_operator* op, const T* x, const T* xp, const T* b, T* out, const T* w,
-                              const T* a, const T* at, int m, int kidx, int precond, double relax, T* z,
+static richm_status sweep_any(richm_operator* op, const T* x, const T* xp, const T* b, T* out,
+                              const typename RealOf<T>::type* w, const typename RealOf<T>::type* a,
+                              const typename RealOf<T>::type* at, int m, int kidx, int precond, double relax, T* z,
                               cudaStream_t s) {
-  if (precond == 2) return launch_ssor_sweep<T>(op, x, xp, b, z, out, nullptr, w, a, at, m, kidx, relax, nullptr, s);
+  if constexpr (!IsCplx<T>::value) {
+    if (precond == 2)
+      return launch_ssor_sweep<T>(op, x, xp, b, z, out, nullptr, w, a, at, m, kidx, relax, nullptr, s);
+  }
   return launch_sweep<T>(op, x, xp, b, out, w, a, at, m, kidx, precond, nullptr, s);
 }
 
-template <typename T>
-static richm_status forward_ckpt_t(richm_operator* op, const T* x0, const T* b, const T* w, const T* a,
-                                   const T* at, int m, int K, int s_every, int precond, double relax, T* ckpts,
+template <typename T, typename WT = typename RealOf<T>::type>
+static richm_status forward_ckpt_t(richm_operator* op, const T* x0, const T* b, const WT* w, const WT* a,
+                                   const WT* at, int m, int K, int s_every, int precond, double relax, T* ckpts,
                                    T* xK, void* work, cudaStream_t s) {
   const size_t es = op->elems;
   const size_t bytes = es * sizeof(T);
@@ -413,10 +593,10 @@ static size_t adjoint_ws(richm_operator* op, int s_every) {
   return adj > loss ? adj : loss;
 }
 
-template <typename T>
-static richm_status adjoint_t(richm_operator* op, const T* ckpts, int s_every, const T* b, const T* gK, const T* w,
-                              const T* a, const T* at, int m, int K, int precond, double relax, T* g_w, T* g_a,
-                              T* g_at, T* g_x0, void* work, size_t work_bytes, cudaStream_t s) {
+template <typename T, typename W = typename RealOf<T>::type>
+static richm_status adjoint_t(richm_operator* op, const T* ckpts, int s_every, const T* b, const T* gK, const W* w,
+                              const W* a, const W* at, int m, int K, int precond, double relax, W* g_w, W* g_a,
+                              W* g_at, T* g_x0, void* work, size_t work_bytes, cudaStream_t s) {
   if (work_bytes < adjoint_ws<T>(op, s_every)) return set_error(RICHM_ERR_NOMEM, "adjoint workspace too small");
   const size_t es = op->elems;
   const size_t buf = a256(es * sizeof(T));
@@ -464,16 +644,21 @@ static richm_status adjoint_t(richm_operator* op, const T* ckpts, int s_every, c
       const int k = j * s_every + t;
       const int fin = (k == 0) ? 1 : 0;
       T* lo = (fin && g_x0) ? g_x0 : LB[pi];
-      if (precond == 2) RICHM_TRY(launch_ssor_apply<T>(op, lam, Z, U, relax, s));
-      RICHM_TRY(launch_adjoint<T>(op, lam, U, carry, seg[t + 1], seg[t], b, lo, CB[pi], w, a, at, m, k % m,
-                                  precond, fin, partials, acc, s));
+      if constexpr (IsCplx<T>::value) {
+        RICHM_TRY(launch_adjoint_cx<T>(op, lam, carry, seg[t + 1], seg[t], b, lo, CB[pi], w, a, at, m, k % m, fin,
+                                       partials, acc, s));
+      } else {
+        if (precond == 2) RICHM_TRY(launch_ssor_apply<T>(op, lam, Z, U, relax, s));
+        RICHM_TRY(launch_adjoint<T>(op, lam, U, carry, seg[t + 1], seg[t], b, lo, CB[pi], w, a, at, m, k % m,
+                                    precond, fin, partials, acc, s));
+      }
       lam = LB[pi];
       carry = CB[pi];
       pi ^= 1;
     }
   }
   const int cnt = op->batch * m;
-  adjoint_finish_kernel<T><<<(cnt + 255) / 256, 256, 0, s>>>(acc, cnt, g_w, g_a, g_at, at == nullptr ? 1 : 0);
+  adjoint_finish_kernel<W><<<(cnt + 255) / 256, 256, 0, s>>>(acc, cnt, g_w, g_a, g_at, at == nullptr ? 1 : 0);
   RICHM_LAUNCH_CHECK("adjoint finish");
   return RICHM_OK;
 }
@@ -492,6 +677,14 @@ richm_status richm_checkpoint_elems(const richm_operator* op, int K, int ckpt_ev
   return RICHM_OK;
 }
 
+// Real (Q1) states take every preconditioner; complex (Helmholtz) states none.
+static richm_status check_adjoint_dtype(richm_dtype dtype, int precond) {
+  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64 || dtype == RICHM_C64 || dtype == RICHM_C128,
+            "invalid dtype %d", (int)dtype);
+  RICHM_ARG(!dtype_complex(dtype) || precond == 0, "complex (Helmholtz) differentiation takes no preconditioner");
+  return RICHM_OK;
+}
+
 static richm_status check_precond(int precond, double relax) {
   RICHM_ARG(precond >= 0 && precond <= 2, "precond must be 0, 1 or 2");
   RICHM_ARG(precond != 2 || (relax > 0.0 && relax < 2.0), "SSOR relaxation factor must lie in (0, 2)");
@@ -505,7 +698,7 @@ richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, c
   clear_error();
   RICHM_ARG(op != nullptr, "null operator");
   RICHM_TRY(check_dtype_for_op(op, dtype));
-  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "differentiation is implemented for real (Q1) problems");
+  RICHM_TRY(check_adjoint_dtype(dtype, precond));
   RICHM_ARG(x0 && b && w && ckpts, "null argument");
   RICHM_ARG(m >= 1 && m <= 64, "m out of range");
   RICHM_ARG(ckpt_every >= 1 && K >= 0 && K % ckpt_every == 0, "K must be a multiple of ckpt_every >= 1");
@@ -515,23 +708,37 @@ richm_status richm_forward_checkpointed(richm_operator* op, richm_dtype dtype, c
   RICHM_ARG(work != nullptr, "null workspace");
   if (work_bytes < need) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == RICHM_F32)
-    return forward_ckpt_t<float>(op, (const float*)x0, (const float*)b, (const float*)w, (const float*)alpha,
-                                 (const float*)alpha_t, m, K, ckpt_every, precond, relax, (float*)ckpts, (float*)xK,
-                                 work, s);
-  return forward_ckpt_t<double>(op, (const double*)x0, (const double*)b, (const double*)w, (const double*)alpha,
-                                (const double*)alpha_t, m, K, ckpt_every, precond, relax, (double*)ckpts,
-                                (double*)xK, work, s);
+  switch (dtype) {
+    case RICHM_F32:
+      return forward_ckpt_t<float>(op, (const float*)x0, (const float*)b, (const float*)w, (const float*)alpha,
+                                   (const float*)alpha_t, m, K, ckpt_every, precond, relax, (float*)ckpts,
+                                   (float*)xK, work, s);
+    case RICHM_F64:
+      return forward_ckpt_t<double>(op, (const double*)x0, (const double*)b, (const double*)w, (const double*)alpha,
+                                    (const double*)alpha_t, m, K, ckpt_every, precond, relax, (double*)ckpts,
+                                    (double*)xK, work, s);
+    case RICHM_C64:
+      return forward_ckpt_t<cplx<float>>(op, (const cplx<float>*)x0, (const cplx<float>*)b, (const float*)w,
+                                         (const float*)alpha, (const float*)alpha_t, m, K, ckpt_every, precond,
+                                         relax, (cplx<float>*)ckpts, (cplx<float>*)xK, work, s);
+    default:
+      return forward_ckpt_t<cplx<double>>(op, (const cplx<double>*)x0, (const cplx<double>*)b, (const double*)w,
+                                          (const double*)alpha, (const double*)alpha_t, m, K, ckpt_every, precond,
+                                          relax, (cplx<double>*)ckpts, (cplx<double>*)xK, work, s);
+  }
 }
 
 richm_status richm_adjoint_workspace(const richm_operator* op, richm_dtype dtype, int ckpt_every, size_t* bytes) {
   clear_error();
   RICHM_ARG(op && bytes, "null argument");
-  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "real dtype required");
+  RICHM_TRY(check_adjoint_dtype(dtype, 0));
   RICHM_ARG(ckpt_every >= 1, "ckpt_every < 1");
   auto* o = const_cast<richm_operator*>(op);
   const size_t fwd = 4 * a256(op->elems * dtype_size(dtype));
-  const size_t adj = dtype == RICHM_F32 ? adjoint_ws<float>(o, ckpt_every) : adjoint_ws<double>(o, ckpt_every);
+  const size_t adj = dtype == RICHM_F32   ? adjoint_ws<float>(o, ckpt_every)
+                     : dtype == RICHM_F64 ? adjoint_ws<double>(o, ckpt_every)
+                     : dtype == RICHM_C64 ? adjoint_ws<cplx<float>>(o, ckpt_every)
+                                          : adjoint_ws<cplx<double>>(o, ckpt_every);
   *bytes = adj > fwd ? adj : fwd;
   return RICHM_OK;
 }
@@ -544,20 +751,34 @@ richm_status richm_sweeps_adjoint(richm_operator* op, richm_dtype dtype, const v
   clear_error();
   RICHM_ARG(op != nullptr, "null operator");
   RICHM_TRY(check_dtype_for_op(op, dtype));
-  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "differentiation is implemented for real (Q1) problems");
+  RICHM_TRY(check_adjoint_dtype(dtype, precond));
   RICHM_ARG(ckpts && b && gK && w && work, "null argument");
   RICHM_ARG(m >= 1 && m <= 64, "m out of range");
   RICHM_ARG(ckpt_every >= 1 && K >= 1 && K % ckpt_every == 0, "K must be a positive multiple of ckpt_every");
   RICHM_ARG(alpha != nullptr || alpha_t == nullptr, "alpha_t given without alpha");
   RICHM_TRY(check_precond(precond, relax));
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == RICHM_F32)
-    return adjoint_t<float>(op, (const float*)ckpts, ckpt_every, (const float*)b, (const float*)gK, (const float*)w,
-                            (const float*)alpha, (const float*)alpha_t, m, K, precond, relax, (float*)g_w,
-                            (float*)g_alpha, (float*)g_alpha_t, (float*)g_x0, work, work_bytes, s);
-  return adjoint_t<double>(op, (const double*)ckpts, ckpt_every, (const double*)b, (const double*)gK,
-                           (const double*)w, (const double*)alpha, (const double*)alpha_t, m, K, precond, relax,
-                           (double*)g_w, (double*)g_alpha, (double*)g_alpha_t, (double*)g_x0, work, work_bytes, s);
+  switch (dtype) {
+    case RICHM_F32:
+      return adjoint_t<float>(op, (const float*)ckpts, ckpt_every, (const float*)b, (const float*)gK,
+                              (const float*)w, (const float*)alpha, (const float*)alpha_t, m, K, precond, relax,
+                              (float*)g_w, (float*)g_alpha, (float*)g_alpha_t, (float*)g_x0, work, work_bytes, s);
+    case RICHM_F64:
+      return adjoint_t<double>(op, (const double*)ckpts, ckpt_every, (const double*)b, (const double*)gK,
+                               (const double*)w, (const double*)alpha, (const double*)alpha_t, m, K, precond, relax,
+                               (double*)g_w, (double*)g_alpha, (double*)g_alpha_t, (double*)g_x0, work, work_bytes,
+                               s);
+    case RICHM_C64:
+      return adjoint_t<cplx<float>>(op, (const cplx<float>*)ckpts, ckpt_every, (const cplx<float>*)b,
+                                    (const cplx<float>*)gK, (const float*)w, (const float*)alpha,
+                                    (const float*)alpha_t, m, K, precond, relax, (float*)g_w, (float*)g_alpha,
+                                    (float*)g_alpha_t, (cplx<float>*)g_x0, work, work_bytes, s);
+    default:
+      return adjoint_t<cplx<double>>(op, (const cplx<double>*)ckpts, ckpt_every, (const cplx<double>*)b,
+                                     (const cplx<double>*)gK, (const double*)w, (const double*)alpha,
+                                     (const double*)alpha_t, m, K, precond, relax, (double*)g_w, (double*)g_alpha,
+                                     (double*)g_alpha_t, (cplx<double>*)g_x0, work, work_bytes, s);
+  }
 }
 
 }  // extern "C"

@@ -30,7 +30,8 @@ template <> __device__ inline cplx<float> narrow<cplx<float>, cplx<double>>(cplx
 template <> __device__ inline cplx<double> narrow<cplx<double>, cplx<double>>(cplx<double> v) { return v; }
 
 // MODE 0: residual (+ optional r_out) and partial sums (|r|^2, |b|^2).
-// MODE 1: out = scale_b * (A x) (used for the loss gradient), no partials.
+// MODE 1: out = scale_b * (A^H x) (the loss gradient; A^H = A for the real Q1 stencil,
+//         conj(A) for the complex symmetric Helmholtz stencil), no partials.
 // MODE 3: out = A x, no partials (the Krylov solver's products).
 // MODE 2: the solver's refinement residual (real FP64 x and b): b folded into the
 //         stencil's multiply-adds and partial sums (|r|^2, 0), since |b| is known.
@@ -81,7 +82,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     load(r + 1, D);
     ED Ax[VW];
     if constexpr (CPLX) {
-      apply_fd5<ED, VW, double>(U, C, D, r - 1, c0, n, I.c, I.ax, I.abc_re, I.abc_im, I.sp_im, I.sp_iw, Ax);
+      const double sg = MODE == 1 ? -1.0 : 1.0;  // conj(A) for the loss gradient
+      apply_fd5<ED, VW, double>(U, C, D, r - 1, c0, n, I.c, I.ax, I.abc_re, sg * I.abc_im, sg * I.sp_im, I.sp_iw, Ax);
     } else {
       apply_q1<ED, VW, double>(U, C, D, I.c, I.ax, I.ay, I.d1, I.d2, Ax);
     }
@@ -341,12 +343,21 @@ richm_status richm_loss_log_residual(richm_operator* op, richm_dtype dtype, cons
   clear_error();
   RICHM_ARG(op != nullptr, "null operator");
   RICHM_TRY(check_dtype_for_op(op, dtype));
-  RICHM_ARG(dtype == RICHM_F32 || dtype == RICHM_F64, "the loss is defined for real (Q1) problems");
   RICHM_ARG(x && b && loss && work, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
-  if (dtype == RICHM_F32)
-    return loss_t<float>(op, (const float*)x, (const float*)b, loss, (float*)g, work, work_bytes, s);
-  return loss_t<double>(op, (const double*)x, (const double*)b, loss, (double*)g, work, work_bytes, s);
+  switch (dtype) {
+    case RICHM_F32:
+      return loss_t<float>(op, (const float*)x, (const float*)b, loss, (float*)g, work, work_bytes, s);
+    case RICHM_F64:
+      return loss_t<double>(op, (const double*)x, (const double*)b, loss, (double*)g, work, work_bytes, s);
+    case RICHM_C64:
+      return loss_t<cplx<float>>(op, (const cplx<float>*)x, (const cplx<float>*)b, loss, (cplx<float>*)g, work,
+                                 work_bytes, s);
+    case RICHM_C128:
+      return loss_t<cplx<double>>(op, (const cplx<double>*)x, (const cplx<double>*)b, loss, (cplx<double>*)g, work,
+                                  work_bytes, s);
+  }
+  return set_error(RICHM_ERR_ARG, "invalid dtype");
 }
 
 }  // extern "C"

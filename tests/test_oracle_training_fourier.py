@@ -415,3 +415,70 @@ def test_transition_band_parametrisation():
         ref = ref + 2 * (tau9[1 + 2 * q] * np.cos(ang) - tau9[2 + 2 * q] * np.sin(ang))
     np.testing.assert_allclose(t, ref, atol=1e-12)
     assert np.isrealobj(t)
+
+
+def _helmholtz_problem(B=2, n=7, K=10, m=4):
+    from oracle.operators import assemble_helmholtz, assemble_helmholtz_sponge, helmholtz_wavenumber
+    As, fs, u0s = [], [], []
+    for b in range(B):
+        if b % 2 == 0:
+            A = assemble_helmholtz_sponge(n, 2 * math.pi * 1.5)
+        else:
+            A = assemble_helmholtz(n, helmholtz_wavenumber(n, 6.0), absorbing=True)
+        As.append(A.tocsr())
+        fs.append(synth.rhs_uniform(31, b, n).ravel() + 1j * synth.rhs_uniform(32, b, n).ravel())
+        u0s.append(0.1 * (synth.rhs_uniform(33, b, n).ravel() - 0.5j * synth.rhs_uniform(34, b, n).ravel()))
+    G = np.array([abs(A).sum(axis=1).max() for A in As])
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.3, 1.2, (B, m)) / G[:, None]
+    a = rng.uniform(0.1, 0.4, (B, m))
+    at = rng.uniform(0.0, 0.5, (B, m))
+    return As, fs, u0s, w, a, at, K
+
+
+def test_complex_lookahead_gradient_matches_central_differences():
+    # complex states (Helmholtz with a sponge layer and with an absorbing boundary),
+    # real weights, distinct a and at: every weight and the real and imaginary parts of
+    # x0 against central differences of the numpy iteration
+    from oracle.training import loss_and_grads_general, loss_general
+    As, fs, u0s, w, a, at, K = _helmholtz_problem()
+    L, gw, ga, gat, gu = loss_and_grads_general(As, fs, u0s, w, a, at, K)
+    assert abs(L - loss_general(As, fs, u0s, w, a, at, K)) < 1e-12
+    h = 1e-6
+    for name, arr, g in (("w", w, gw), ("a", a, ga), ("at", at, gat)):
+        for b in range(2):
+            for i in range(w.shape[1]):
+                hp = h * max(1.0, abs(arr[b, i]))
+                P, M = arr.copy(), arr.copy()
+                P[b, i] += hp
+                M[b, i] -= hp
+                args_p = {"w": (P, a, at), "a": (w, P, at), "at": (w, a, P)}[name]
+                args_m = {"w": (M, a, at), "a": (w, M, at), "at": (w, a, M)}[name]
+                fd = (loss_general(As, fs, u0s, *args_p, K) - loss_general(As, fs, u0s, *args_m, K)) / (2 * hp)
+                scale = max(abs(fd), 1e-3 * np.abs(g).max())
+                assert abs(fd - g[b, i]) <= 1e-5 * scale, (name, b, i, fd, g[b, i])
+    for b in range(2):
+        for idx in (0, 10, 24, 48):
+            for unit in (1.0, 1j):
+                up = [u.copy() for u in u0s]
+                um = [u.copy() for u in u0s]
+                up[b][idx] += h * unit
+                um[b][idx] -= h * unit
+                fd = (loss_general(As, fs, up, w, a, at, K) - loss_general(As, fs, um, w, a, at, K)) / (2 * h)
+                comp = gu[b][idx].real if unit == 1.0 else gu[b][idx].imag
+                assert abs(fd - comp) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gu[b]).max()), (b, idx, unit, fd, comp)
+
+
+def test_general_loss_reduces_to_the_real_nag_and_richardson_forms():
+    from oracle.training import loss_and_grads_general
+    As, fs, u0s, w, a, K = _problem()
+    L, gw, ga, gu = loss_and_grads(As, fs, u0s, w, a, K)
+    L2, gw2, ga2, gat2, gu2 = loss_and_grads_general(As, fs, u0s, w, a, None, K)
+    assert gat2 is None and abs(L - L2) < 1e-13
+    np.testing.assert_allclose(gw2, gw, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(ga2, ga, rtol=1e-11, atol=1e-13)
+    # Richardson(m): alphas None equals zero momentum
+    L3, gw3, ga3, _, _ = loss_and_grads_general(As, fs, u0s, w, None, None, K)
+    L4, gw4, _, _ = loss_and_grads(As, fs, u0s, w, np.zeros_like(a), K)
+    assert ga3 is None and abs(L3 - L4) < 1e-13
+    np.testing.assert_allclose(gw3, gw4, rtol=1e-11, atol=1e-13)
