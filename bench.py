@@ -452,7 +452,9 @@ def table9_analogue(dev, sizes=(128, 256, 512), batch=4, tol=1e-6, max_iters=300
     """FGMRES(20) on the sponge-layer Helmholtz problem of eq. 21 at Table 9's grids
     (h = 1/N, omega/2pi = 10 N/128, c = 1), preconditioned by 5 sweeps of Richardson(5) or
     NAG-Richardson(5) (Chebyshev weights of eqs. 8-9 on the upper spectrum [G/4, G], G the
-    Gershgorin bound; NAG with beta = 0.3 on the interval stretched by 1.6), or by nothing.
+    Gershgorin bound; NAG with beta = 0.3 on the interval stretched by 1.6), by 5 sweeps of
+    NAG-Richardson(5) with log-weights and momentum from a Meta-omega network trained here
+    (paper_2412_08076_gb300.helmholtz), or by nothing.
     The WANS multigrid and ADR parts are not built (their networks and data are not
     available), so the counts are for the smoother alone as the preconditioner. Right-hand
     sides: unit point sources at seeded interior points."""
@@ -461,7 +463,19 @@ def table9_analogue(dev, sizes=(128, 256, 512), batch=4, tol=1e-6, max_iters=300
 
     import richm_synth as synth
     from paper_2412_08076_gb300 import richm
+    from paper_2412_08076_gb300 import helmholtz as hz
     out = {}
+    # Meta-omega: one network for the three grids, trained on random right-hand sides
+    specs = [(richm.HELMHOLTZ_FD5_SPONGE, N - 1, 2 * math.pi * 10 * N / 128) for N in sizes for _ in range(2)]
+    net = hz.SmootherNet(m=5, K=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = hz.train(net, specs, steps=300, lr=3e-3)
+    torch.cuda.synchronize()
+    out["meta_omega_training"] = {"steps": 300, "seconds": time.perf_counter() - t0, "loss_first": hist[0],
+                                  "loss_last": hist[-1], "instances": len(specs),
+                                  "note": "log-weights and momentum of NAG-Richardson(5) from the meta MLP, "
+                                          "complex64 sweeps, complex adjoint, Adam 3e-3"}
     for N in sizes:
         n = N - 1
         om = 2 * math.pi * 10 * N / 128
@@ -472,11 +486,17 @@ def table9_analogue(dev, sizes=(128, 256, 512), batch=4, tol=1e-6, max_iters=300
             src[s_, i * n + j] = 1.0
         B = op.pack(torch.tensor(src.ravel(), device=dev), richm.C128)
         row = {"omega_over_2pi": om / (2 * math.pi)}
-        for name, beta, stretch in (("none", None, 1.0), ("richardson5", None, 1.0), ("nag_richardson5", 0.3, 1.6)):
+        for name, beta, stretch in (("none", None, 1.0), ("richardson5", None, 1.0), ("nag_richardson5", 0.3, 1.6),
+                                    ("meta_omega_nag5", None, 1.0)):
             X = op.zeros(richm.C128)
             if name == "none":
                 w = a = None
                 sweeps = 0
+            elif name == "meta_omega_nag5":
+                Xin = torch.tensor(hz.instance_inputs([(richm.HELMHOLTZ_FD5_SPONGE, n, om)] * batch), device=dev)
+                Gt = torch.full((batch,), G, dtype=torch.float32, device=dev)
+                w, a, _ = net.coefficients(Xin, Gt)
+                sweeps = 5
             else:
                 wv = np.array(richm.chebyshev_weights(stretch * G, stretch * G / 4.0, 5))
                 w = torch.tensor(np.tile(wv, (batch, 1)), dtype=torch.float32, device=dev)
