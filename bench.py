@@ -990,6 +990,27 @@ def run_profile_case(args):
         S.close()
         torch.cuda.synchronize()
         return 0
+    if what in ("fgmres", "adjoint_cx"):
+        # Table 9's largest grid (N = 512, sponge layer): FGMRES(20) preconditioned by 5 NAG
+        # sweeps (`sweeps` bounds the iterations), or one Meta-omega training step (forward
+        # and complex adjoint of 5 complex64 sweeps on random right-hand sides)
+        from paper_2412_08076_gb300 import helmholtz as hz
+        N = args.n + 1
+        spec = (richm.HELMHOLTZ_FD5_SPONGE, args.n, 2 * math.pi * 10 * N / 128)
+        op = richm.Operator([(kind, n_, 1.0, 0.0, k) for kind, n_, k in [spec] * args.batch])
+        net = hz.SmootherNet(m=5, K=5)
+        X = torch.tensor(hz.instance_inputs([spec] * args.batch), device="cuda")
+        G = torch.tensor(np.array(op.gershgorin()), dtype=torch.float32, device="cuda")
+        B = hz.random_rhs(op, [spec] * args.batch, 77)
+        if what == "adjoint_cx":
+            net.loss_and_grads(op, X, G, B)
+        else:
+            w, a, _ = net.coefficients(X, G)
+            B128 = op.pack(op.unpack(B, richm.C64).to(torch.complex128), richm.C128)
+            op.fgmres(B128, op.zeros(richm.C128), w, a, None, restart=20, tol=1e-6, max_iters=args.sweeps, m=5,
+                      sweeps=5, inner=richm.C64)
+        torch.cuda.synchronize()
+        return 0
     insts = synth.batched_aniso(args.batch, sizes=(args.n,), param_seed=1)
     if what == "helmholtz":
         k = 2 * math.pi * (args.n + 1) / 10
@@ -1050,7 +1071,8 @@ def main(argv=None):
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--e2e-runs", type=int, default=2, help="timed richm_solve_host calls")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["sweep", "cycle", "adjoint", "helmholtz", "ssor", "bench_cycles"], default=None,
+    ap.add_argument("--profile", choices=["sweep", "cycle", "adjoint", "helmholtz", "ssor", "bench_cycles", "fgmres",
+                                          "adjoint_cx"], default=None,
                     help="run a small fixed workload of one kernel family for an ncu capture instead of the bench")
     ap.add_argument("--batch", type=int, default=32, help="--profile: instances")
     ap.add_argument("--n", type=int, default=511, help="--profile: grid size")

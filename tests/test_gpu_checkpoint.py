@@ -140,3 +140,31 @@ def test_mismatched_images_are_refused():
     np.testing.assert_array_equal(X.cpu().numpy(), x_before)
     for s in (S, S2, S3, S4, S5):
         s.close()
+
+
+def test_resume_at_the_benchmark_size():
+    # the benchmark's batch (256 instances, 27 M unknowns), network and settings: an image
+    # saved after 20 refinement cycles and resumed in a new session continues with the
+    # same bits as the uninterrupted session after 20 more
+    import bench
+    from paper_2412_08076_gb300 import meta as meta_mod
+    insts, op, rhs, dense_b = bench.build_batch(1)
+    params, _ = meta_mod.load_params(bench.M, variant=bench.META_VARIANT)
+    X, G, P = bench.meta_inputs(op, insts, params)
+    w, a = richm.meta_forward(P, X, G, bench.M)
+    B = op.pack(dense_b.cuda(), richm.F64)
+    opts = op.solve_opts(bench.M, tol=bench.SOLVE_TOL, max_sweeps=10 ** 7, refine_every=bench.REFINE,
+                         inner=richm.F32, use_graph=1, fuse=8)
+    X1 = op.zeros(richm.F64)
+    S1 = richm.Solver(op, opts, w, a)
+    img, x1, info1 = _run_to(S1, B, X1, 20, 20)
+    S1.close()
+    X2 = torch.full_like(X1, 1.0)
+    S2 = richm.Solver(op, opts, w, a)
+    S2.resume(B, X2, img)
+    del img
+    S2.step(20)
+    st2, info2 = S2.finish()
+    assert info2 == info1
+    assert torch.equal(X2, torch.tensor(x1, device="cuda"))
+    S2.close()
