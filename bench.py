@@ -454,7 +454,8 @@ def table9_analogue(dev, sizes=(128, 256, 512), batch=4, tol=1e-6, max_iters=300
     NAG-Richardson(5) (Chebyshev weights of eqs. 8-9 on the upper spectrum [G/4, G], G the
     Gershgorin bound; NAG with beta = 0.3 on the interval stretched by 1.6), by 5 sweeps of
     NAG-Richardson(5) with log-weights and momentum from a Meta-omega network trained here
-    (paper_2412_08076_gb300.helmholtz), or by nothing.
+    (paper_2412_08076_gb300.helmholtz), or by nothing; each with the complex128 Arnoldi basis
+    and with the complex64 one (`complex64_basis`).
     The WANS multigrid and ADR parts are not built (their networks and data are not
     available), so the counts are for the smoother alone as the preconditioner. Right-hand
     sides: unit point sources at seeded interior points."""
@@ -502,15 +503,19 @@ def table9_analogue(dev, sizes=(128, 256, 512), batch=4, tol=1e-6, max_iters=300
                 w = torch.tensor(np.tile(wv, (batch, 1)), dtype=torch.float32, device=dev)
                 a = torch.full_like(w, beta) if beta is not None else None
                 sweeps = 5
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st, info = op.fgmres(B, X, w, a, None, restart=20, tol=tol, max_iters=max_iters, m=5, sweeps=sweeps,
-                                 inner=richm.C64)
-            el = time.perf_counter() - t0
-            its = [i_ for i_, _, _ in info]
-            row[name] = {"iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
-                         "converged": sum(1 for *_, s_ in info if s_ == richm.OK), "seconds": el,
-                         "worst_rel_res": max(r for _, r, _ in info)}
+            res = {}
+            for basis in (richm.C128, richm.C64):
+                X = op.zeros(richm.C128)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, info = op.fgmres(B, X, w, a, None, restart=20, tol=tol, max_iters=max_iters, m=5, sweeps=sweeps,
+                                     inner=richm.C64, basis=basis)
+                el = time.perf_counter() - t0
+                its = [i_ for i_, _, _ in info]
+                res[basis] = {"iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+                              "converged": sum(1 for *_, s_ in info if s_ == richm.OK), "seconds": el,
+                              "worst_rel_res": max(r for _, r, _ in info)}
+            row[name] = dict(res[richm.C128], complex64_basis=res[richm.C64])
         out[f"N{N}"] = row
         op.close()
     return out
@@ -1008,7 +1013,7 @@ def run_profile_case(args):
             w, a, _ = net.coefficients(X, G)
             B128 = op.pack(op.unpack(B, richm.C64).to(torch.complex128), richm.C128)
             op.fgmres(B128, op.zeros(richm.C128), w, a, None, restart=20, tol=1e-6, max_iters=args.sweeps, m=5,
-                      sweeps=5, inner=richm.C64)
+                      sweeps=5, inner=richm.C64, basis=richm.C64 if args.basis == "c64" else richm.C128)
         torch.cuda.synchronize()
         return 0
     insts = synth.batched_aniso(args.batch, sizes=(args.n,), param_seed=1)
@@ -1075,6 +1080,7 @@ def main(argv=None):
                                           "adjoint_cx"], default=None,
                     help="run a small fixed workload of one kernel family for an ncu capture instead of the bench")
     ap.add_argument("--batch", type=int, default=32, help="--profile: instances")
+    ap.add_argument("--basis", choices=["c128", "c64"], default="c128", help="--profile fgmres: the Arnoldi basis")
     ap.add_argument("--n", type=int, default=511, help="--profile: grid size")
     ap.add_argument("--sweeps", type=int, default=6, help="--profile: sweeps")
     ap.add_argument("--fuse", type=int, default=1, help="--profile: sweeps per pass")

@@ -414,6 +414,10 @@ typedef struct {
   int sweeps;     /* smoother sweeps per preconditioner application (0: no preconditioner) */
   int inner;      /* the smoother's state: RICHM_C64 (mixed precision) or RICHM_C128 */
   int precond;    /* the smoother's B^{-1}: 0 none, 1 Jacobi (D^{-1}) */
+  int basis;      /* the Arnoldi basis: 0 or RICHM_C128 (complex128), or RICHM_C64 (with inner
+                     RICHM_C64: the cycle's vectors, products and Gram-Schmidt passes in
+                     complex64, dots and norms summed over tiles in FP64; every cycle
+                     still starts from b - A x in FP64) */
 } richm_fgmres_opts;
 
 typedef struct {
@@ -422,7 +426,7 @@ typedef struct {
   int status;      /* RICHM_OK, RICHM_ERR_NOT_CONVERGED or RICHM_ERR_DIVERGED */
 } richm_fgmres_info;
 
-/* Workspace bytes of richm_fgmres: restart + 1 complex128 basis vectors, restart
+/* Workspace bytes of richm_fgmres: restart + 1 basis vectors (opts->basis), restart
  * preconditioned vectors of the inner type, the smoother's state and workspace, and the
  * per-instance Hessenberg systems. */
 richm_status richm_fgmres_workspace(const richm_operator* op, const richm_fgmres_opts* opts, size_t* bytes);

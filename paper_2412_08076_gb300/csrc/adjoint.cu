@@ -351,6 +351,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     apply_fd5<C, VW, R>(YU, YC, YD, r - 1, c0, n, sc, soff, abr, abi, spi, spw, Ay);
     apply_fd5<C, VW, R>(LU, LC, LD, r - 1, c0, n, sc, soff, abr, -abi, -spi, spw, Al);  // conj(A) lam
     VecN<C, VW> Lo, Co;
+    // complex64: the row's products summed in FP32, the row sums in FP64 (GB300's FP64
+    // pipe would otherwise bound the kernel); complex128 sums in FP64
+    R rw = R(0), ra = R(0), rat = R(0);
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       const bool ok = (c0 + e) < n;
@@ -361,15 +364,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       C ln = MOM ? ((R(1) + ai) * l - (R(1) + ati) * q) + Cv.v[e] : l - q;
       const C cn = MOM ? (-ai) * l + ati * q : z;
       if (ok) {
-        s_w += (double)l.re * (double)dr.re + (double)l.im * (double)dr.im;
+        rw = fma(l.re, dr.re, fma(l.im, dr.im, rw));
         if (MOM) {
-          s_a += (double)l.re * (double)v.re + (double)l.im * (double)v.im;
-          s_at += (double)q.re * (double)v.re + (double)q.im * (double)v.im;
+          ra = fma(l.re, v.re, fma(l.im, v.im, ra));
+          rat = fma(q.re, v.re, fma(q.im, v.im, rat));
         }
       }
       if (final_step) ln = ln + cn;
       Lo.v[e] = ok ? ln : z;
       Co.v[e] = ok ? cn : z;
+    }
+    if constexpr (std::is_same<R, float>::value) {
+      s_w += f32_to_f64_exact(rw);
+      if (MOM) {
+        s_a += f32_to_f64_exact(ra);
+        s_at += f32_to_f64_exact(rat);
+      }
+    } else {
+      s_w += rw;
+      if (MOM) {
+        s_a += ra;
+        s_at += rat;
+      }
     }
     if (live) {
       stv<C, VW>(lam_out + ro, Lo);

@@ -18,7 +18,16 @@
 // would, with the same stability. Dots and norms are summed in FP64 per warp tile and
 // then per instance in a fixed order. The small Hessenberg problems are reduced by
 // complex Givens rotations, one thread per instance.
+//
+// With a complex64 basis (opts->basis) the cycle's vectors, A z_j, the Gram-Schmidt
+// products and updates are complex64 on the FP32 pipe (GB300 runs FP64 at 1/64 of the
+// FP32 rate, and the complex128 passes are bound by it); the dots and norms are summed
+// over a warp tile's rows in FP32 and over the tiles in FP64. The residual that starts
+// every cycle stays b - A x in FP64 with x in complex128, so each restart refines the
+// solution against the exact residual (the cycles of 20 steps reduce it by far less
+// than the complex64 rounding).
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -28,43 +37,52 @@ namespace richm {
 
 using C128 = cplx<double>;
 using C64 = cplx<float>;
+constexpr int kMaxRestart = 64;
 
-__device__ __forceinline__ C128 conj_mul(C128 a, C128 b) {  // conj(a) * b
+// the basis type of the options: complex128 unless opts->basis is RICHM_C64
+static bool narrow_basis(const richm_fgmres_opts* o) { return o->basis == RICHM_C64; }
+
+template <typename T>
+__device__ __forceinline__ cplx<T> conj_mul(cplx<T> a, cplx<T> b) {  // conj(a) * b
   return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
 }
+__device__ __forceinline__ double widen_d(float v) { return f32_to_f64_exact(v); }
+__device__ __forceinline__ double widen_d(double v) { return v; }
 __device__ __forceinline__ double2 c2d(C128 v) { return make_double2(v.re, v.im); }
 __device__ __forceinline__ C128 d2c(double2 v) { return {v.x, v.y}; }
 
 // partials[i * ntiles + t] = sum over warp tile t of conj(V_i) w (32 columns x kRows
 // rows of complex128; the padding columns and halo rows are zero in both)
+template <typename VB>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    kry_dot_kernel(const Inst* insts, const Tile* tiles, int ntiles, const C128* __restrict__ V, size_t vstride,
-                   const C128* __restrict__ w, double2* __restrict__ partials, const int* __restrict__ active) {
+    kry_dot_kernel(const Inst* insts, const Tile* tiles, int ntiles, const VB* __restrict__ V, size_t vstride,
+                   const VB* __restrict__ w, double2* __restrict__ partials, const int* __restrict__ active) {
+  using T = typename RealOf<VB>::type;
   const int lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (wt >= ntiles) return;
   const int i = blockIdx.y;
   const Tile t = tiles[wt];
-  double sre = 0.0, sim = 0.0;
+  T sre = T(0), sim = T(0);  // this lane's column of the tile (at most kRows terms)
   if (!active || active[t.inst]) {
     const Inst& I = insts[t.inst];
     const int c0 = t.tx * 32 + lane;
     if (c0 < I.n) {
       const int r0 = t.ty * kRows + 1;
       const int r1 = min(r0 + kRows - 1, I.n);
-      const C128* vi = V + (size_t)i * vstride + I.off;
-      const C128* wb = w + I.off;
+      const VB* vi = V + (size_t)i * vstride + I.off;
+      const VB* wb = w + I.off;
       for (int r = r0; r <= r1; ++r) {
         const long long o = (long long)r * I.pitch + c0;
-        const C128 p = conj_mul(vi[o], wb[o]);
+        const VB p = conj_mul(vi[o], wb[o]);
         sre += p.re;
         sim += p.im;
       }
     }
   }
-  sre = warp_sum(sre);
-  sim = warp_sum(sim);
-  if (lane == 0) partials[(size_t)i * ntiles + wt] = make_double2(sre, sim);
+  const double dre = warp_sum(widen_d(sre));
+  const double dim = warp_sum(widen_d(sim));
+  if (lane == 0) partials[(size_t)i * ntiles + wt] = make_double2(dre, dim);
 }
 
 // h[b * ldh + i] = sum over instance b's tiles of partials[i * ntiles + t] (fixed order)
@@ -86,44 +104,105 @@ __global__ void kry_reduce_kernel(const double2* __restrict__ partials, const in
 
 // w -= sum_{i < nv} h[b][i] V_i over the tile; optionally the tile's sum |w|^2 in
 // partials (as (|w|^2, 0), the layout of the residual norm partials)
+// (complex64 basis: the coefficients narrowed once per warp into shared memory)
+template <typename VB>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    kry_update_kernel(const Inst* insts, const Tile* tiles, int ntiles, const C128* __restrict__ V, size_t vstride,
-                      int nv, const double2* __restrict__ h, int ldh, C128* __restrict__ w,
+    kry_update_kernel(const Inst* insts, const Tile* tiles, int ntiles, const VB* __restrict__ V, size_t vstride,
+                      int nv, const double2* __restrict__ h, int ldh, VB* __restrict__ w,
                       double2* __restrict__ partials, const int* __restrict__ active) {
-  const int lane = threadIdx.x & 31;
-  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  using T = typename RealOf<VB>::type;
+  constexpr bool NARROW = std::is_same<T, float>::value;
+  __shared__ C64 hs[kWarpsPerBlock][kMaxRestart + 1];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int wt = blockIdx.x * kWarpsPerBlock + wi;
   if (wt >= ntiles) return;
   const Tile t = tiles[wt];
-  double s2 = 0.0;
+  T s2 = T(0);
   if (!active || active[t.inst]) {
     const Inst& I = insts[t.inst];
+    const double2* hb = h + (size_t)t.inst * ldh;
+    if constexpr (NARROW) {
+      for (int i = lane; i < nv; i += 32) hs[wi][i] = C64{f64_to_f32_rn(hb[i].x), f64_to_f32_rn(hb[i].y)};
+      __syncwarp();
+    }
     const int c0 = t.tx * 32 + lane;
     if (c0 < I.n) {
       const int r0 = t.ty * kRows + 1;
       const int r1 = min(r0 + kRows - 1, I.n);
-      const double2* hb = h + (size_t)t.inst * ldh;
-      C128* wb = w + I.off;
+      VB* wb = w + I.off;
       for (int r = r0; r <= r1; ++r) {
         const long long o = (long long)r * I.pitch + c0;
-        C128 acc = wb[o];
-        for (int i = 0; i < nv; ++i) acc = acc - cmul(d2c(hb[i]), V[(size_t)i * vstride + I.off + o]);
+        VB acc = wb[o];
+        for (int i = 0; i < nv; ++i) {
+          VB hi;
+          if constexpr (NARROW) hi = hs[wi][i];
+          else hi = d2c(hb[i]);
+          acc = acc - cmul(hi, V[(size_t)i * vstride + I.off + o]);
+        }
         wb[o] = acc;
         s2 += acc.re * acc.re + acc.im * acc.im;
       }
     }
   }
   if (partials) {
-    s2 = warp_sum(s2);
-    if (lane == 0) partials[wt] = make_double2(s2, 0.0);
+    const double d2 = warp_sum(widen_d(s2));
+    if (lane == 0) partials[wt] = make_double2(d2, 0.0);
+  }
+}
+
+// w = A z in complex64 arithmetic over rows 1..n (columns >= n written as zero), one
+// column per lane (the complex128 geometry), for the complex64 basis.
+template <typename EZ>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    kry_apply_kernel(const Inst* insts, const Tile* tiles, int ntiles, const EZ* __restrict__ z,
+                     C64* __restrict__ out, const int* __restrict__ active) {
+  const int lane = threadIdx.x & 31;
+  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (wt >= ntiles) return;
+  const Tile t = tiles[wt];
+  if (active && !active[t.inst]) return;
+  const Inst& I = insts[t.inst];
+  const int n = I.n, pitch = I.pitch;
+  const int c0 = t.tx * 32 + lane;
+  const bool live = c0 < pitch;
+  const int r0 = t.ty * kRows + 1;
+  const int r1 = min(r0 + kRows - 1, n);
+  const EZ* zb = z + I.off;
+  auto load = [&](int pr, RowT<C64, 1>& Y) {
+    const bool in = (pr >= 1) && (pr <= n);
+    const long long ro = (long long)pr * pitch;
+    C64 v{0.f, 0.f};
+    if (in && live) v = C64{(float)zb[ro + c0].re, (float)zb[ro + c0].im};
+    Y.y[0] = v;
+    C64 le{0.f, 0.f}, re{0.f, 0.f};
+    if (in) {
+      if (lane == 0 && c0 > 0) le = C64{(float)zb[ro + c0 - 1].re, (float)zb[ro + c0 - 1].im};
+      if (lane == 31 && c0 + 1 < pitch) re = C64{(float)zb[ro + c0 + 1].re, (float)zb[ro + c0 + 1].im};
+    }
+    row_neighbours<C64, 1>(Y, lane, le, re);
+  };
+  RowT<C64, 1> U, C, D;
+  load(r0 - 1, U);
+  load(r0, C);
+  for (int r = r0; r <= r1; ++r) {
+    load(r + 1, D);
+    C64 Ax[1];
+    apply_fd5<C64, 1, float>(U, C, D, r - 1, c0, n, (float)I.c, (float)I.ax, (float)I.abc_re, (float)I.abc_im,
+                             (float)I.sp_im, (float)I.sp_iw, Ax);
+    if (live) out[I.off + (long long)r * pitch + c0] = c0 < n ? Ax[0] : C64{0.f, 0.f};
+    U = C;
+    C = D;
   }
 }
 
 // v = w / nrm[b] over rows 1..n (columns >= n stay zero), and the same narrowed to
 // complex64 in vn when given
+template <typename VB>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    kry_scale_kernel(const Inst* insts, const Tile* tiles, int ntiles, const C128* __restrict__ w,
-                     const double* __restrict__ nrm, C128* __restrict__ v, C64* __restrict__ vn,
+    kry_scale_kernel(const Inst* insts, const Tile* tiles, int ntiles, const VB* __restrict__ w,
+                     const double* __restrict__ nrm, VB* __restrict__ v, C64* __restrict__ vn,
                      const int* __restrict__ active) {
+  using T = typename RealOf<VB>::type;
   const int lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (wt >= ntiles) return;
@@ -132,12 +211,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const Inst& I = insts[t.inst];
   const int c0 = t.tx * 32 + lane;
   if (c0 >= I.pitch) return;
-  const double s = nrm[t.inst] > 0.0 ? 1.0 / nrm[t.inst] : 0.0;
+  const double sd = nrm[t.inst] > 0.0 ? 1.0 / nrm[t.inst] : 0.0;
+  T s;
+  if constexpr (std::is_same<T, float>::value) s = f64_to_f32_rn(sd);
+  else s = sd;
   const int r0 = t.ty * kRows + 1;
   const int r1 = min(r0 + kRows - 1, I.n);
   for (int r = r0; r <= r1; ++r) {
     const long long o = I.off + (long long)r * I.pitch + c0;
-    const C128 q = c0 < I.n ? s * w[o] : C128{0.0, 0.0};
+    const VB q = c0 < I.n ? s * w[o] : VB{T(0), T(0)};
     v[o] = q;
     if (vn) vn[o] = C64{(float)q.re, (float)q.im};
   }
@@ -289,6 +371,7 @@ struct KryLayout {
 static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, KryLayout* L) {
   const size_t el = op->elems;
   const size_t es = o->inner == RICHM_C64 ? 8 : 16;
+  const size_t vs = narrow_basis(o) ? 8 : 16;  // basis element
   const size_t R = (size_t)o->restart, B = (size_t)op->batch;
   int nt = 0;
   RICHM_TRY(residual_tiles<C128>(op, &nt));
@@ -300,10 +383,10 @@ static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, K
     p += a256(bytes);
     return at;
   };
-  L->V = take((R + 1) * a256(el * 16));
+  L->V = take((R + 1) * a256(el * vs));
   L->Z = take(R * a256(el * es));
-  L->W = take(el * 16);
-  L->vin = take(o->inner == RICHM_C64 ? el * 8 : 0);
+  L->W = take(el * vs);
+  L->vin = take(o->inner == RICHM_C64 && !narrow_basis(o) ? el * 8 : 0);
   L->zp = take(el * es);
   L->sw = take(sw);
   L->dots = take((R + 1) * (size_t)nt * sizeof(double2));
@@ -330,31 +413,35 @@ static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, K
 
 static richm_status check_fgmres(const richm_operator* op, const richm_fgmres_opts* o) {
   RICHM_ARG(op != nullptr && o != nullptr, "null operator or options");
-  RICHM_ARG(o->restart >= 1 && o->restart <= 64, "restart = %d out of range [1, 64]", o->restart);
+  RICHM_ARG(o->restart >= 1 && o->restart <= kMaxRestart, "restart = %d out of range [1, 64]", o->restart);
   RICHM_ARG(o->tol >= 0.0, "tol < 0");
   RICHM_ARG(o->max_iters >= 0, "max_iters < 0");
   RICHM_ARG(o->m >= 1 && o->m <= 64, "m = %d out of range [1, 64]", o->m);
   RICHM_ARG(o->sweeps >= 0, "sweeps < 0");
   RICHM_ARG(o->inner == RICHM_C64 || o->inner == RICHM_C128, "inner must be RICHM_C64 or RICHM_C128");
   RICHM_ARG(o->precond == 0 || o->precond == 1, "precond must be 0 or 1");
+  RICHM_ARG(o->basis == 0 || o->basis == RICHM_C128 || o->basis == RICHM_C64,
+            "basis must be 0 (complex128), RICHM_C128 or RICHM_C64");
+  RICHM_ARG(!narrow_basis(o) || o->inner == RICHM_C64, "a complex64 basis needs inner RICHM_C64");
   for (int b = 0; b < op->batch; ++b)
     if (op->h_inst[b].kind == RICHM_ANISO_Q1)
       return set_error(RICHM_ERR_UNSUPPORTED, "richm_fgmres takes Helmholtz instances (instance %d is Q1)", b);
   return RICHM_OK;
 }
 
-template <typename EZ>
+template <typename EZ, typename VB>
 static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const void* w, const void* alpha,
                              const void* alpha_t, const richm_fgmres_opts* o, richm_fgmres_info* info, char* work,
                              const KryLayout& L, cudaStream_t s) {
+  constexpr bool NB = std::is_same<VB, C64>::value;  // complex64 basis
   const int R = o->restart, B = op->batch;
   const size_t el = op->elems;
   const size_t es = sizeof(EZ);
-  const size_t vstride = a256(el * 16) / 16, zstride = a256(el * es) / es;
-  C128* V = reinterpret_cast<C128*>(work + L.V);
+  const size_t vstride = a256(el * sizeof(VB)) / sizeof(VB), zstride = a256(el * es) / es;
+  VB* V = reinterpret_cast<VB*>(work + L.V);
   EZ* Z = reinterpret_cast<EZ*>(work + L.Z);
-  C128* W = reinterpret_cast<C128*>(work + L.W);
-  C64* vin = o->inner == RICHM_C64 ? reinterpret_cast<C64*>(work + L.vin) : nullptr;
+  VB* W = reinterpret_cast<VB*>(work + L.W);
+  C64* vin = (o->inner == RICHM_C64 && !NB) ? reinterpret_cast<C64*>(work + L.vin) : nullptr;
   EZ* zp = reinterpret_cast<EZ*>(work + L.zp);
   void* sw = work + L.sw;
   size_t swb = 0;
@@ -385,15 +472,16 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
   richm_sweep_opts so{o->m, 0, o->precond, 0, 1.0};
   for (int cycle = 0;; ++cycle) {
     // r = b - A x, beta = |r| (and |b| at the first cycle from the same pass)
-    RICHM_TRY(launch_residual<C128>(op, x, b, W, norms, s));
+    if constexpr (NB) RICHM_TRY((launch_residual_to<C128, C64>(op, x, b, W, norms, nullptr, s, false)));
+    else RICHM_TRY(launch_residual<C128>(op, x, b, W, norms, s));
     RICHM_TRY(launch_norm_reduce(op, 1, norms, S.beta, cycle == 0 ? S.bnorm : nullptr, nullptr, s));
     RICHM_CUDA_TRY(cudaMemsetAsync(S.count, 0, sizeof(int), s));
     kry_cycle_start_kernel<<<iblocks, ithr, 0, s>>>(S, B, R, o->tol, o->max_iters);
     RICHM_LAUNCH_CHECK("FGMRES cycle start");
     RICHM_TRY(read_count());
     if (h_count == 0) break;
-    kry_scale_kernel<<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, W, S.beta, V, vin,
-                                                             S.in_cycle);
+    kry_scale_kernel<VB><<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, W, S.beta, V, vin,
+                                                                 S.in_cycle);
     RICHM_LAUNCH_CHECK("FGMRES scale");
     for (int j = 0; j < R; ++j) {
       // z_j = M(v_j): K smoother sweeps on A z = v_j from z = 0
@@ -407,17 +495,22 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
       else
         RICHM_CUDA_TRY(cudaMemcpyAsync(zj, rhs, el * es, cudaMemcpyDeviceToDevice, s));
       // w = A z_j, then two Gram-Schmidt passes against v_0..v_j
-      RICHM_TRY((launch_apply_to<EZ, C128>(op, zj, W, s)));
+      if constexpr (NB) {
+        kry_apply_kernel<EZ><<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, zj, W, S.in_cycle);
+        RICHM_LAUNCH_CHECK("FGMRES stencil");
+      } else {
+        RICHM_TRY((launch_apply_to<EZ, C128>(op, zj, W, s)));
+      }
       for (int pass = 0; pass < 2; ++pass) {
-        kry_dot_kernel<<<dim3(tblocks, j + 1), kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, V, vstride,
-                                                                           W, dots, S.in_cycle);
+        kry_dot_kernel<VB><<<dim3(tblocks, j + 1), kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, V,
+                                                                               vstride, W, dots, S.in_cycle);
         RICHM_LAUNCH_CHECK("FGMRES dots");
         double2* hc = pass == 0 ? S.hcol : S.hcol2;
         kry_reduce_kernel<<<dim3(B, j + 1), 32, 0, s>>>(dots, tm->d_inst_begin, nt, B, hc, R + 1);
         RICHM_LAUNCH_CHECK("FGMRES dot reduction");
-        kry_update_kernel<<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, V, vstride, j + 1,
-                                                                  hc, R + 1, W, pass == 1 ? norms : nullptr,
-                                                                  S.in_cycle);
+        kry_update_kernel<VB><<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, V, vstride,
+                                                                      j + 1, hc, R + 1, W,
+                                                                      pass == 1 ? norms : nullptr, S.in_cycle);
         RICHM_LAUNCH_CHECK("FGMRES update");
       }
       RICHM_TRY(launch_norm_reduce(op, 1, norms, S.wnorm, nullptr, nullptr, s));
@@ -425,8 +518,9 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
       kry_givens_kernel<<<iblocks, ithr, 0, s>>>(S, B, R, j, o->tol, o->max_iters);
       RICHM_LAUNCH_CHECK("FGMRES rotations");
       if (j + 1 < R) {
-        kry_scale_kernel<<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, W, S.wnorm,
-                                                                 V + (size_t)(j + 1) * vstride, vin, S.in_cycle);
+        kry_scale_kernel<VB><<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, W, S.wnorm,
+                                                                     V + (size_t)(j + 1) * vstride, vin,
+                                                                     S.in_cycle);
         RICHM_LAUNCH_CHECK("FGMRES scale");
       }
       RICHM_TRY(read_count());
@@ -438,7 +532,8 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
     RICHM_LAUNCH_CHECK("FGMRES solution update");
   }
   // the final true residual of every instance
-  RICHM_TRY(launch_residual<C128>(op, x, b, W, norms, s));
+  if constexpr (NB) RICHM_TRY((launch_residual_to<C128, C64>(op, x, b, W, norms, nullptr, s, false)));
+  else RICHM_TRY(launch_residual<C128>(op, x, b, W, norms, s));
   RICHM_TRY(launch_norm_reduce(op, 1, norms, S.rnorm, nullptr, nullptr, s));
   std::vector<double> hr(B), hb(B);
   std::vector<int> hi(B), hd(B);
@@ -494,9 +589,11 @@ richm_status richm_fgmres(richm_operator* op, const void* b, void* x, const void
   if (work_bytes < L.total) return set_error(RICHM_ERR_NOMEM, "workspace %zu < %zu bytes", work_bytes, L.total);
   cudaStream_t s = (cudaStream_t)stream;
   char* wk = reinterpret_cast<char*>(work);
+  if (narrow_basis(o))
+    return fgmres_t<C64, C64>(op, (const C128*)b, (C128*)x, w, alpha, alpha_t, o, info, wk, L, s);
   if (o->inner == RICHM_C64)
-    return fgmres_t<C64>(op, (const C128*)b, (C128*)x, w, alpha, alpha_t, o, info, wk, L, s);
-  return fgmres_t<C128>(op, (const C128*)b, (C128*)x, w, alpha, alpha_t, o, info, wk, L, s);
+    return fgmres_t<C64, C128>(op, (const C128*)b, (C128*)x, w, alpha, alpha_t, o, info, wk, L, s);
+  return fgmres_t<C128, C128>(op, (const C128*)b, (C128*)x, w, alpha, alpha_t, o, info, wk, L, s);
 }
 
 }  // extern "C"

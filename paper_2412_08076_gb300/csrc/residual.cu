@@ -204,6 +204,9 @@ template richm_status launch_residual_to<double, float>(richm_operator*, const d
                                                         double2*, const int*, cudaStream_t, bool);
 template richm_status launch_residual_to<double, double>(richm_operator*, const double*, const double*, double*,
                                                          double2*, const int*, cudaStream_t, bool);
+template richm_status launch_residual_to<cplx<double>, cplx<float>>(richm_operator*, const cplx<double>*,
+                                                                    const cplx<double>*, cplx<float>*, double2*,
+                                                                    const int*, cudaStream_t, bool);
 
 template <typename E>
 static richm_status launch_scaled_apply(richm_operator* op, const E* x, E* out, const double* scale,

@@ -60,7 +60,7 @@ class richm_solve_info(C.Structure):
 
 class richm_fgmres_opts(C.Structure):
     _fields_ = [("restart", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int), ("m", C.c_int),
-                ("sweeps", C.c_int), ("inner", C.c_int), ("precond", C.c_int)]
+                ("sweeps", C.c_int), ("inner", C.c_int), ("precond", C.c_int), ("basis", C.c_int)]
 
 
 class richm_fgmres_info(C.Structure):
@@ -383,7 +383,7 @@ class Operator:
                "richm_apply_sweeps")
 
     def fgmres(self, b, x, w=None, alpha=None, alpha_t=None, restart=20, tol=1e-6, max_iters=1000, m=None,
-               sweeps=None, inner=C64, precond=0, work=None, stream=None):
+               sweeps=None, inner=C64, precond=0, work=None, stream=None, basis=C128):
         """richm_fgmres (Sec. 3.2, Table 9): b, x padded complex128 (x: guess in, solution
         out); the preconditioner is `sweeps` Table 1 sweeps with coefficients w, alpha,
         alpha_t ([batch][m], real type of `inner`); returns (status, [(iters, rel_res, status)])."""
@@ -391,7 +391,7 @@ class Operator:
             m = w.numel() // self.batch if w is not None else 1
         if sweeps is None:
             sweeps = m if w is not None else 0
-        o = richm_fgmres_opts(restart, tol, max_iters, m, sweeps, inner, precond)
+        o = richm_fgmres_opts(restart, tol, max_iters, m, sweeps, inner, precond, basis)
         need = C.c_size_t()
         _check(load().richm_fgmres_workspace(self.handle, C.byref(o), C.byref(need)), "richm_fgmres_workspace")
         if work is None:

@@ -137,3 +137,39 @@ def test_fgmres_without_preconditioner_is_gmres():
     for i, A in enumerate(mats):
         ref, its, est = fgmres(A, bs[i].ravel(), None, None, m=7, tol=0.0, max_iters=14)
         assert np.abs(got[i].ravel() - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_fgmres_complex64_basis_solves_to_tolerance():
+    # complex64 smoother and Arnoldi basis (the cycles on the FP32 pipe), complex128
+    # iterate and restart residual: every instance to 1e-9 against the oracle's
+    # recomputed residual, in about as many steps as with the complex128 basis
+    op, mats = _batch(SPECS)
+    bs = _rhs(SPECS, 30)
+    G = np.array(op.gershgorin())
+    w, a = _smoother(G)
+    B = to_dev(op, bs, richm.C128)
+    its = {}
+    for basis in (richm.C128, richm.C64):
+        X = op.zeros(richm.C128)
+        st, info = op.fgmres(B, X, coef(w, richm.C64), coef(a, richm.C64), None, restart=20, tol=1e-9,
+                             max_iters=5000, sweeps=5, inner=richm.C64, basis=basis)
+        assert st == richm.OK, info
+        got = from_dev(op, X, richm.C128)
+        for i, A in enumerate(mats):
+            rel = np.linalg.norm(bs[i].ravel() - A @ got[i].ravel()) / np.linalg.norm(bs[i])
+            assert rel <= 1e-9 * (1 + 1e-6), (basis, i, rel)
+            assert abs(info[i][1] - rel) <= 1e-6 * rel
+        its[basis] = [i_ for i_, _, _ in info]
+    print(f"\nFGMRES(20) to 1e-9, Arnoldi steps: complex128 basis {its[richm.C128]}, complex64 basis {its[richm.C64]}")
+    for i128, i64 in zip(its[richm.C128], its[richm.C64]):
+        assert i64 <= 1.15 * i128 + 20, (i128, i64)
+
+
+def test_fgmres_basis_option_is_checked():
+    op, mats = _batch(SPECS[:2])
+    B, X = op.zeros(richm.C128), op.zeros(richm.C128)
+    w = coef(np.full((2, 5), 1e-4), richm.C128)
+    with pytest.raises(richm.RichmError):  # a complex64 basis needs the complex64 smoother
+        op.fgmres(B, X, w, None, None, sweeps=5, m=5, inner=richm.C128, basis=richm.C64)
+    with pytest.raises(richm.RichmError):
+        op.fgmres(B, X, w, None, None, sweeps=5, m=5, inner=richm.C128, basis=richm.F32)
