@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const int r1 = min(r0 + kRows - 1, I.n);
       const VB* vi = V + (size_t)i * vstride + I.off;
       const VB* wb = w + I.off;
+#pragma unroll 4
       for (int r = r0; r <= r1; ++r) {
         const long long o = (long long)r * I.pitch + c0;
         const VB p = conj_mul(vi[o], wb[o]);
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       for (int r = r0; r <= r1; ++r) {
         const long long o = (long long)r * I.pitch + c0;
         VB acc = wb[o];
+#pragma unroll 4
         for (int i = 0; i < nv; ++i) {
           VB hi;
           if constexpr (NARROW) hi = hs[wi][i];
@@ -333,31 +335,49 @@ __global__ void kry_backsolve_kernel(KryState S, int batch, int R) {
   }
 }
 
-// x += sum_{i < jend[b]} y[b][i] Z_i (Z in the preconditioner's type)
-template <typename EZ>
+// x += sum_{i < jend[b]} y[b][i] Z_i (Z in the preconditioner's type). NARROW (the
+// complex64 basis): the sum formed in complex64 with y narrowed once per warp, then
+// added to x in FP64; the next cycle's FP64 residual corrects its rounding.
+template <typename EZ, bool NARROW>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     kry_xupdate_kernel(const Inst* insts, const Tile* tiles, int ntiles, const EZ* __restrict__ Z, size_t zstride,
                        KryState S, int R, C128* __restrict__ x) {
-  const int lane = threadIdx.x & 31;
-  const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  __shared__ C64 ys[kWarpsPerBlock][kMaxRestart];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int wt = blockIdx.x * kWarpsPerBlock + wi;
   if (wt >= ntiles) return;
   const Tile t = tiles[wt];
   const int J = S.jend[t.inst];
   if (J == 0) return;
   const Inst& I = insts[t.inst];
+  const double2* yb = S.y + (size_t)t.inst * R;
+  if constexpr (NARROW) {
+    for (int i = lane; i < J; i += 32) ys[wi][i] = C64{f64_to_f32_rn(yb[i].x), f64_to_f32_rn(yb[i].y)};
+    __syncwarp();
+  }
   const int c0 = t.tx * 32 + lane;
   if (c0 >= I.n) return;
   const int r0 = t.ty * kRows + 1;
   const int r1 = min(r0 + kRows - 1, I.n);
-  const double2* yb = S.y + (size_t)t.inst * R;
   for (int r = r0; r <= r1; ++r) {
     const long long o = I.off + (long long)r * I.pitch + c0;
-    C128 acc = x[o];
-    for (int i = 0; i < J; ++i) {
-      const EZ z = Z[(size_t)i * zstride + o];
-      acc = acc + cmul(d2c(yb[i]), C128{(double)z.re, (double)z.im});
+    if constexpr (NARROW) {
+      C64 acc{0.f, 0.f};
+#pragma unroll 4
+      for (int i = 0; i < J; ++i) {
+        const EZ z = Z[(size_t)i * zstride + o];
+        acc = acc + cmul(ys[wi][i], C64{(float)z.re, (float)z.im});
+      }
+      const C128 xo = x[o];
+      x[o] = C128{xo.re + f32_to_f64_exact(acc.re), xo.im + f32_to_f64_exact(acc.im)};
+    } else {
+      C128 acc = x[o];
+      for (int i = 0; i < J; ++i) {
+        const EZ z = Z[(size_t)i * zstride + o];
+        acc = acc + cmul(d2c(yb[i]), C128{(double)z.re, (double)z.im});
+      }
+      x[o] = acc;
     }
-    x[o] = acc;
   }
 }
 
@@ -528,7 +548,8 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
     }
     kry_backsolve_kernel<<<iblocks, ithr, 0, s>>>(S, B, R);
     RICHM_LAUNCH_CHECK("FGMRES back substitution");
-    kry_xupdate_kernel<EZ><<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, Z, zstride, S, R, x);
+    kry_xupdate_kernel<EZ, NB><<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, Z, zstride, S, R,
+                                                                       x);
     RICHM_LAUNCH_CHECK("FGMRES solution update");
   }
   // the final true residual of every instance
