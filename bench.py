@@ -189,6 +189,42 @@ def oracle_sample_rate(instances, seconds: float = 12.0, sweeps_per_chunk: int =
     return dofs / el / 1e9, desc
 
 
+def oracle_other_configs():
+    """The oracle (one host thread, as it stands) on the other configurations' shapes:
+    400 FP64 Richardson(8) sweeps on the 63^2 instance (eps 1e-2, theta pi/6) and 8
+    complex NAG-Richardson(8) sweeps on one 2047^2 Helmholtz instance with the absorbing
+    boundary (k for 10 points per wavelength)."""
+    import numpy as np
+
+    import richm_synth as synth
+    from oracle.iterations import chebyshev_weights, inner_steps
+    from oracle.operators import assemble_helmholtz, assemble_q1, gershgorin_max, helmholtz_wavenumber
+    out = {}
+    A = assemble_q1(63, 1e-2, math.pi / 6)
+    G = gershgorin_max(A)
+    w = chebyshev_weights(G, G / 30.0, 8)
+    f = synth.rhs_uniform(0, 0, 63).ravel()
+    t0 = time.perf_counter()
+    inner_steps(A, f, np.zeros_like(f), None, w, K=400)
+    el = time.perf_counter() - t0
+    out["fp64_63sq_richardson8_400_sweeps"] = {"seconds": el, "us_per_sweep": 1e6 * el / 400,
+                                                "gdof_sweeps_per_s": 63 * 63 * 400 / el / 1e9}
+    n = 2047
+    t0 = time.perf_counter()
+    H = assemble_helmholtz(n, helmholtz_wavenumber(n, 10.0), absorbing=True).tocsr()
+    t_asm = time.perf_counter() - t0
+    h2 = 1.0 / (n + 1) ** 2
+    wv = (h2 / 8.0) * np.linspace(0.5, 1.5, 8)
+    b = np.zeros(n * n, np.complex128)
+    b[(n // 2) * n + n // 3] = 1.0
+    t0 = time.perf_counter()
+    inner_steps(H, b, np.zeros_like(b), None, wv, np.full(8, 0.3), K=8)
+    el = time.perf_counter() - t0
+    out["helmholtz_2047sq_c128_8_sweeps"] = {"seconds": el, "assembly_seconds": t_asm,
+                                              "gdof_sweeps_per_s": n * n * 8 / el / 1e9}
+    return out
+
+
 def _oracle_worker_init():
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
@@ -882,6 +918,7 @@ def run_ours(args):
     if rank == 0:
         cpu_rate, cpu_desc = oracle_sample_rate(insts, seconds=args.cpu_seconds)
         all_rate, all_procs, all_desc = oracle_all_cores_rate(insts, seconds=min(8.0, args.cpu_seconds))
+        other_cpu = oracle_other_configs() if args.cpu_seconds >= 5 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
@@ -893,6 +930,7 @@ def run_ours(args):
                              "host_cores": os.cpu_count()},
             "cpu_baseline_all_cores": {"value": all_rate, "unit": UNIT, "cores": all_procs, "kind": "oracle",
                                        "sample": all_desc},
+            "cpu_oracle_other_configs": other_cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(dense_b.numel() * 8),
                     "d2h_bytes_per_step": int(hx.numel() * 8), "seconds_per_call": e2e_s,
                     "statuses": [r[2] for r in e2e_runs],
