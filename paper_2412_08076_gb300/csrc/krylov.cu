@@ -26,6 +26,7 @@
 // every cycle stays b - A x in FP64 with x in complex128, so each restart refines the
 // solution against the exact residual (the cycles of 20 steps reduce it by far less
 // than the complex64 rounding).
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -38,6 +39,10 @@ namespace richm {
 using C128 = cplx<double>;
 using C64 = cplx<float>;
 constexpr int kMaxRestart = 64;
+// Rows of a Krylov warp tile: short tiles give the streaming kernels (dots, updates,
+// products) four times the warps of the residual geometry, enough loads in flight
+// per SM to stream at HBM rate.
+constexpr int kKryRows = 4;
 
 // the basis type of the options: complex128 unless opts->basis is RICHM_C64
 static bool narrow_basis(const richm_fgmres_opts* o) { return o->basis == RICHM_C64; }
@@ -51,7 +56,7 @@ __device__ __forceinline__ double widen_d(double v) { return v; }
 __device__ __forceinline__ double2 c2d(C128 v) { return make_double2(v.re, v.im); }
 __device__ __forceinline__ C128 d2c(double2 v) { return {v.x, v.y}; }
 
-// partials[i * ntiles + t] = sum over warp tile t of conj(V_i) w (32 columns x kRows
+// partials[i * ntiles + t] = sum over warp tile t of conj(V_i) w (32 columns x kKryRows
 // rows of complex128; the padding columns and halo rows are zero in both)
 template <typename VB>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -63,13 +68,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   if (wt >= ntiles) return;
   const int i = blockIdx.y;
   const Tile t = tiles[wt];
-  T sre = T(0), sim = T(0);  // this lane's column of the tile (at most kRows terms)
+  T sre = T(0), sim = T(0);  // this lane's column of the tile (at most kKryRows terms)
   if (!active || active[t.inst]) {
     const Inst& I = insts[t.inst];
     const int c0 = t.tx * 32 + lane;
     if (c0 < I.n) {
-      const int r0 = t.ty * kRows + 1;
-      const int r1 = min(r0 + kRows - 1, I.n);
+      const int r0 = t.ty * kKryRows + 1;
+      const int r1 = min(r0 + kKryRows - 1, I.n);
       const VB* vi = V + (size_t)i * vstride + I.off;
       const VB* wb = w + I.off;
 #pragma unroll 4
@@ -128,8 +133,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
     const int c0 = t.tx * 32 + lane;
     if (c0 < I.n) {
-      const int r0 = t.ty * kRows + 1;
-      const int r1 = min(r0 + kRows - 1, I.n);
+      const int r0 = t.ty * kKryRows + 1;
+      const int r1 = min(r0 + kKryRows - 1, I.n);
       VB* wb = w + I.off;
       for (int r = r0; r <= r1; ++r) {
         const long long o = (long long)r * I.pitch + c0;
@@ -167,8 +172,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int n = I.n, pitch = I.pitch;
   const int c0 = t.tx * 32 + lane;
   const bool live = c0 < pitch;
-  const int r0 = t.ty * kRows + 1;
-  const int r1 = min(r0 + kRows - 1, n);
+  const int r0 = t.ty * kKryRows + 1;
+  const int r1 = min(r0 + kKryRows - 1, n);
   const EZ* zb = z + I.off;
   auto load = [&](int pr, RowT<C64, 1>& Y) {
     const bool in = (pr >= 1) && (pr <= n);
@@ -217,8 +222,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   T s;
   if constexpr (std::is_same<T, float>::value) s = f64_to_f32_rn(sd);
   else s = sd;
-  const int r0 = t.ty * kRows + 1;
-  const int r1 = min(r0 + kRows - 1, I.n);
+  const int r0 = t.ty * kKryRows + 1;
+  const int r1 = min(r0 + kKryRows - 1, I.n);
   for (int r = r0; r <= r1; ++r) {
     const long long o = I.off + (long long)r * I.pitch + c0;
     const VB q = c0 < I.n ? s * w[o] : VB{T(0), T(0)};
@@ -239,6 +244,7 @@ struct KryState {
   double* beta;     // [batch] residual norm at the cycle's start
   double* bnorm;    // [batch]
   double* wnorm;    // [batch]
+  double2* wn2;     // [batch]: (|w|^2, 0) after the second Gram-Schmidt pass
   double* rnorm;    // [batch] true residual norm
   int* iters;       // [batch] Arnoldi steps taken
   int* jend;        // [batch] steps of the current cycle
@@ -275,7 +281,8 @@ __global__ void kry_givens_kernel(KryState S, int batch, int R, int j, double to
     const double2 p = S.hcol[b * ld + i], q = S.hcol2[b * ld + i];
     Hc[i] = make_double2(p.x + q.x, p.y + q.y);
   }
-  const double hn = S.wnorm[b];
+  const double hn = sqrt(S.wn2[b].x);
+  S.wnorm[b] = hn;
   Hc[j + 1] = make_double2(hn, 0.0);
   for (int i = 0; i < j; ++i) {  // earlier rotations
     const double c = S.cs[(size_t)b * R + i];
@@ -357,8 +364,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
   const int c0 = t.tx * 32 + lane;
   if (c0 >= I.n) return;
-  const int r0 = t.ty * kRows + 1;
-  const int r1 = min(r0 + kRows - 1, I.n);
+  const int r0 = t.ty * kKryRows + 1;
+  const int r1 = min(r0 + kKryRows - 1, I.n);
   for (int r = r0; r <= r1; ++r) {
     const long long o = I.off + (long long)r * I.pitch + c0;
     if constexpr (NARROW) {
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 static size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct KryLayout {
-  size_t V, Z, W, vin, zp, sw, dots, norms, H, hcol, hcol2, cs, sn, g, y, beta, bnorm, wnorm, rnorm, iters, jend,
+  size_t V, Z, W, vin, zp, sw, dots, norms, H, hcol, hcol2, cs, sn, g, y, beta, bnorm, wnorm, wn2, rnorm, iters, jend,
       in_cycle, done, count, total;
 };
 
@@ -393,8 +400,11 @@ static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, K
   const size_t es = o->inner == RICHM_C64 ? 8 : 16;
   const size_t vs = narrow_basis(o) ? 8 : 16;  // basis element
   const size_t R = (size_t)o->restart, B = (size_t)op->batch;
-  int nt = 0;
-  RICHM_TRY(residual_tiles<C128>(op, &nt));
+  int nt_res = 0;
+  RICHM_TRY(residual_tiles<C128>(op, &nt_res));
+  const TileMap* tm = nullptr;
+  RICHM_TRY(get_tiles(op, 32, kKryRows, &tm));
+  const size_t nt = (size_t)tm->ntiles;
   size_t sw = 0;
   RICHM_TRY(richm_sweeps_workspace(op, (richm_dtype)o->inner, &sw));
   size_t p = 0;
@@ -409,8 +419,9 @@ static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, K
   L->vin = take(o->inner == RICHM_C64 && !narrow_basis(o) ? el * 8 : 0);
   L->zp = take(el * es);
   L->sw = take(sw);
-  L->dots = take((R + 1) * (size_t)nt * sizeof(double2));
-  L->norms = take((size_t)nt * sizeof(double2));
+  L->dots = take((R + 1) * nt * sizeof(double2));
+  L->norms = take(std::max(nt, (size_t)nt_res) * sizeof(double2));  // the residual's partials or the Krylov tiles'
+
   L->H = take(B * R * (R + 1) * sizeof(double2));
   L->hcol = take(B * (R + 1) * sizeof(double2));
   L->hcol2 = take(B * (R + 1) * sizeof(double2));
@@ -421,6 +432,7 @@ static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, K
   L->beta = take(B * sizeof(double));
   L->bnorm = take(B * sizeof(double));
   L->wnorm = take(B * sizeof(double));
+  L->wn2 = take(B * sizeof(double2));
   L->rnorm = take(B * sizeof(double));
   L->iters = take(B * sizeof(int));
   L->jend = take(B * sizeof(int));
@@ -473,11 +485,11 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
              reinterpret_cast<double2*>(work + L.sn),    reinterpret_cast<double2*>(work + L.g),
              reinterpret_cast<double2*>(work + L.y),     reinterpret_cast<double*>(work + L.beta),
              reinterpret_cast<double*>(work + L.bnorm),  reinterpret_cast<double*>(work + L.wnorm),
-             reinterpret_cast<double*>(work + L.rnorm),  reinterpret_cast<int*>(work + L.iters),
+             reinterpret_cast<double2*>(work + L.wn2),   reinterpret_cast<double*>(work + L.rnorm),  reinterpret_cast<int*>(work + L.iters),
              reinterpret_cast<int*>(work + L.jend),      reinterpret_cast<int*>(work + L.in_cycle),
              reinterpret_cast<int*>(work + L.done),      reinterpret_cast<int*>(work + L.count)};
   const TileMap* tm = nullptr;
-  RICHM_TRY(get_tiles(op, 32, kRows, &tm));  // complex128 geometry
+  RICHM_TRY(get_tiles(op, 32, kKryRows, &tm));  // 32 columns (one per lane) x kKryRows rows
   const int nt = tm->ntiles;
   const int tblocks = (nt + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int ithr = 128, iblocks = (B + ithr - 1) / ithr;
@@ -533,7 +545,8 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
                                                                       pass == 1 ? norms : nullptr, S.in_cycle);
         RICHM_LAUNCH_CHECK("FGMRES update");
       }
-      RICHM_TRY(launch_norm_reduce(op, 1, norms, S.wnorm, nullptr, nullptr, s));
+      kry_reduce_kernel<<<dim3(B, 1), 32, 0, s>>>(norms, tm->d_inst_begin, nt, B, S.wn2, 1);
+      RICHM_LAUNCH_CHECK("FGMRES norm reduction");
       RICHM_CUDA_TRY(cudaMemsetAsync(S.count, 0, sizeof(int), s));
       kry_givens_kernel<<<iblocks, ithr, 0, s>>>(S, B, R, j, o->tol, o->max_iters);
       RICHM_LAUNCH_CHECK("FGMRES rotations");
