@@ -43,6 +43,9 @@ constexpr int kMaxRestart = 64;
 // products) four times the warps of the residual geometry, enough loads in flight
 // per SM to stream at HBM rate.
 constexpr int kKryRows = 4;
+// the dots keep the residual's 16-row tiles: one block row per basis vector already
+// gives them enough warps, and fewer partial sums to reduce
+constexpr int kDotRows = 16;
 
 // the basis type of the options: complex128 unless opts->basis is RICHM_C64
 static bool narrow_basis(const richm_fgmres_opts* o) { return o->basis == RICHM_C64; }
@@ -56,7 +59,7 @@ __device__ __forceinline__ double widen_d(double v) { return v; }
 __device__ __forceinline__ double2 c2d(C128 v) { return make_double2(v.re, v.im); }
 __device__ __forceinline__ C128 d2c(double2 v) { return {v.x, v.y}; }
 
-// partials[i * ntiles + t] = sum over warp tile t of conj(V_i) w (32 columns x kKryRows
+// partials[i * ntiles + t] = sum over warp tile t of conj(V_i) w (32 columns x kDotRows
 // rows of complex128; the padding columns and halo rows are zero in both)
 template <typename VB>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -68,13 +71,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   if (wt >= ntiles) return;
   const int i = blockIdx.y;
   const Tile t = tiles[wt];
-  T sre = T(0), sim = T(0);  // this lane's column of the tile (at most kKryRows terms)
+  T sre = T(0), sim = T(0);  // this lane's column of the tile (at most kDotRows terms)
   if (!active || active[t.inst]) {
     const Inst& I = insts[t.inst];
     const int c0 = t.tx * 32 + lane;
     if (c0 < I.n) {
-      const int r0 = t.ty * kKryRows + 1;
-      const int r1 = min(r0 + kKryRows - 1, I.n);
+      const int r0 = t.ty * kDotRows + 1;
+      const int r1 = min(r0 + kDotRows - 1, I.n);
       const VB* vi = V + (size_t)i * vstride + I.off;
       const VB* wb = w + I.off;
 #pragma unroll 4
@@ -92,20 +95,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 // h[b * ldh + i] = sum over instance b's tiles of partials[i * ntiles + t] (fixed order)
-__global__ void kry_reduce_kernel(const double2* __restrict__ partials, const int* __restrict__ inst_begin,
-                                  int ntiles, int batch, double2* __restrict__ h, int ldh) {
-  const int lane = threadIdx.x;
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads)
+    kry_reduce_kernel(const double2* __restrict__ partials, const int* __restrict__ inst_begin, int ntiles,
+                      int batch, double2* __restrict__ h, int ldh) {
+  __shared__ double2 part[kReduceThreads / 32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int b = blockIdx.x, i = blockIdx.y;
   if (b >= batch) return;
   double sre = 0.0, sim = 0.0;
-  for (int t = inst_begin[b] + lane; t < inst_begin[b + 1]; t += 32) {
+  for (int t = inst_begin[b] + threadIdx.x; t < inst_begin[b + 1]; t += kReduceThreads) {
     const double2 p = partials[(size_t)i * ntiles + t];
     sre += p.x;
     sim += p.y;
   }
   sre = warp_sum(sre);
   sim = warp_sum(sim);
-  if (lane == 0) h[(size_t)b * ldh + i] = make_double2(sre, sim);
+  if (lane == 0) part[wi] = make_double2(sre, sim);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int q = 0; q < kReduceThreads / 32; ++q) {
+      acc.x += part[q].x;
+      acc.y += part[q].y;
+    }
+    h[(size_t)b * ldh + i] = acc;
+  }
 }
 
 // w -= sum_{i < nv} h[b][i] V_i over the tile; optionally the tile's sum |w|^2 in
@@ -405,6 +420,8 @@ static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, K
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 32, kKryRows, &tm));
   const size_t nt = (size_t)tm->ntiles;
+  RICHM_TRY(get_tiles(op, 32, kDotRows, &tm));
+  const size_t nt_dot = (size_t)tm->ntiles;
   size_t sw = 0;
   RICHM_TRY(richm_sweeps_workspace(op, (richm_dtype)o->inner, &sw));
   size_t p = 0;
@@ -419,7 +436,7 @@ static richm_status kry_layout(richm_operator* op, const richm_fgmres_opts* o, K
   L->vin = take(o->inner == RICHM_C64 && !narrow_basis(o) ? el * 8 : 0);
   L->zp = take(el * es);
   L->sw = take(sw);
-  L->dots = take((R + 1) * nt * sizeof(double2));
+  L->dots = take((R + 1) * nt_dot * sizeof(double2));
   L->norms = take(std::max(nt, (size_t)nt_res) * sizeof(double2));  // the residual's partials or the Krylov tiles'
 
   L->H = take(B * R * (R + 1) * sizeof(double2));
@@ -491,6 +508,10 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
   const TileMap* tm = nullptr;
   RICHM_TRY(get_tiles(op, 32, kKryRows, &tm));  // 32 columns (one per lane) x kKryRows rows
   const int nt = tm->ntiles;
+  const TileMap* td = nullptr;  // the dots' 16-row tiles
+  RICHM_TRY(get_tiles(op, 32, kDotRows, &td));
+  const int ntd = td->ntiles;
+  const int dblocks = (ntd + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int tblocks = (nt + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int ithr = 128, iblocks = (B + ithr - 1) / ithr;
   // the buffers' halo rows and padding must be zero: clear everything the kernels read
@@ -534,18 +555,18 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
         RICHM_TRY((launch_apply_to<EZ, C128>(op, zj, W, s)));
       }
       for (int pass = 0; pass < 2; ++pass) {
-        kry_dot_kernel<VB><<<dim3(tblocks, j + 1), kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, V,
+        kry_dot_kernel<VB><<<dim3(dblocks, j + 1), kWarpsPerBlock * 32, 0, s>>>(op->d_inst, td->d_tiles, ntd, V,
                                                                                vstride, W, dots, S.in_cycle);
         RICHM_LAUNCH_CHECK("FGMRES dots");
         double2* hc = pass == 0 ? S.hcol : S.hcol2;
-        kry_reduce_kernel<<<dim3(B, j + 1), 32, 0, s>>>(dots, tm->d_inst_begin, nt, B, hc, R + 1);
+        kry_reduce_kernel<<<dim3(B, j + 1), kReduceThreads, 0, s>>>(dots, td->d_inst_begin, ntd, B, hc, R + 1);
         RICHM_LAUNCH_CHECK("FGMRES dot reduction");
         kry_update_kernel<VB><<<tblocks, kWarpsPerBlock * 32, 0, s>>>(op->d_inst, tm->d_tiles, nt, V, vstride,
                                                                       j + 1, hc, R + 1, W,
                                                                       pass == 1 ? norms : nullptr, S.in_cycle);
         RICHM_LAUNCH_CHECK("FGMRES update");
       }
-      kry_reduce_kernel<<<dim3(B, 1), 32, 0, s>>>(norms, tm->d_inst_begin, nt, B, S.wn2, 1);
+      kry_reduce_kernel<<<dim3(B, 1), kReduceThreads, 0, s>>>(norms, tm->d_inst_begin, nt, B, S.wn2, 1);
       RICHM_LAUNCH_CHECK("FGMRES norm reduction");
       RICHM_CUDA_TRY(cudaMemsetAsync(S.count, 0, sizeof(int), s));
       kry_givens_kernel<<<iblocks, ithr, 0, s>>>(S, B, R, j, o->tol, o->max_iters);
