@@ -196,8 +196,8 @@ typedef struct {
                    numbering of each instance's unknowns (Q1, RICHM_F32 or RICHM_F64, one sweep per
                    pass) */
   int fuse;     /* sweeps per pass over HBM (temporal blocking): 0 = library choice, else 1, 2, 4 or 8
-                   (RICHM_F32 / RICHM_BF16 Q1: 4 or 8; RICHM_C64 Helmholtz without preconditioner and
-                   without a sponge layer: 4; other cases run one sweep per pass) */
+                   (RICHM_F32 / RICHM_BF16 Q1: 4 or 8; RICHM_C64 Helmholtz without preconditioner,
+                   absorbing, Dirichlet or sponge boundary: 4; other cases run one sweep per pass) */
   double relax; /* SSOR relaxation factor, 0 < relax < 2 (precond = 2 only) */
 } richm_sweep_opts;
 

@@ -484,12 +484,6 @@ richm_status richm_apply_sweeps(richm_operator* op, richm_dtype dtype, void* x, 
     else o.fuse = 1;
   }
   if (o.precond == 2) o.fuse = 1;  // the triangular solves cannot be fused in time
-  if (dtype == RICHM_C64 || dtype == RICHM_C128) {
-    // the fused complex kernel covers the absorbing and Dirichlet boundaries; a sponge
-    // layer's per-node diagonal runs one sweep per pass
-    for (int b = 0; b < op->batch; ++b)
-      if (op->h_inst[b].kind == RICHM_HELMHOLTZ_FD5_SPONGE) o.fuse = 1;
-  }
   opts = &o;
   switch (dtype) {
     case RICHM_BF16: {

@@ -681,9 +681,11 @@ struct CxCoef {
   float nb[2];        // neighbour coefficient per column of this lane (0 from column n on)
   float dre[2], dim[2];  // diagonal of an interior row per column (with the column terms)
   float abre, abim;   // added to the diagonal per missing row neighbour
+  float spim, spiw;   // sponge layer (eq. 21): i spim max(0, 1 - d spiw) at distance d
+  float dcol[2];      // distance of this lane's columns from the left / right boundary
 };
 
-template <int TL, bool MOM, bool NAGF, int PH, int PW>
+template <int TL, bool MOM, bool NAGF, bool SP, int PH, int PW>
 __device__ __forceinline__ void fused_step_cx(int rr, const FusedCtx<float>& c, const CxCoef& k,
                                               FusedState<TL>& st, const float* wl, const float* al,
                                               const float* atl) {
@@ -709,6 +711,8 @@ __device__ __forceinline__ void fused_step_cx(int rr, const FusedCtx<float>& c, 
     const float Bv[4] = {B4.x, B4.y, B4.z, B4.w};
     const float ws = ((unsigned)(row - c.rlo) < (unsigned)c.n) ? wl[s] : 0.f;
     const float rm = (float)((row == c.rlo) + (row == c.rlo + c.n - 1));  // missing row neighbours
+    // the row's distance from the top / bottom boundary (sponge layer)
+    const float drow = SP ? (float)min(row - c.rlo + 1, c.n - (row - c.rlo)) : 0.f;
     float* Yn = st.Y[s][SD];
     float vn[4];
 #pragma unroll
@@ -733,7 +737,9 @@ __device__ __forceinline__ void fused_step_cx(int rr, const FusedCtx<float>& c, 
       const float ere = e == 1 ? rre : YC[2], eim = e == 1 ? rim : YC[3];
       const float sre = (wre + ere) + (YU[2 * e] + Yn[2 * e]);
       const float sim = (wim + eim) + (YU[2 * e + 1] + Yn[2 * e + 1]);
-      const float dre = fmaf(rm, k.abre, k.dre[e]), dim = fmaf(rm, k.abim, k.dim[e]);
+      const float dre = fmaf(rm, k.abre, k.dre[e]);
+      float dim = fmaf(rm, k.abim, k.dim[e]);
+      if constexpr (SP) dim = fmaf(k.spim, fmaxf(0.f, fmaf(-fminf(drow, k.dcol[e]), k.spiw, 1.f)), dim);
       ry[2 * e] = fmaf(-k.nb[e], sre, fmaf(dim, yim, fmaf(-dre, yre, Bv[2 * e])));
       ry[2 * e + 1] = fmaf(-k.nb[e], sim, fmaf(-dim, yre, fmaf(-dre, yim, Bv[2 * e + 1])));
     }
@@ -761,7 +767,7 @@ __device__ __forceinline__ void fused_step_cx(int rr, const FusedCtx<float>& c, 
   }
 }
 
-template <int TL, bool MOM, bool NAGF>
+template <int TL, bool MOM, bool NAGF, bool SP>
 __global__ void __launch_bounds__(kFuseWarps * 32, 3) sweepT_cx_kernel(const SweepTArgs A) {
   constexpr int STRIDE = 64 - 2 * TL;
   extern __shared__ __align__(16) unsigned char fused_smem[];
@@ -803,9 +809,12 @@ __global__ void __launch_bounds__(kFuseWarps * 32, 3) sweepT_cx_kernel(const Swe
     k.nb[e] = col < n ? (float)I.ax : 0.f;
     k.dre[e] = (float)I.c + cm * (float)I.abc_re;
     k.dim[e] = cm * (float)I.abc_im;
+    k.dcol[e] = (float)min(col + 1, n - col);
   }
   k.abre = (float)I.abc_re;
   k.abim = (float)I.abc_im;
+  k.spim = (float)I.sp_im;
+  k.spiw = (float)I.sp_iw;
   const bool last_tile = tail || (cs + 64 >= n);
   const int clo = cs + (t.tx > 0 ? TL : 0);
   const int chi = last_tile ? I.pitch : cs + 64 - TL;
@@ -843,9 +852,9 @@ __global__ void __launch_bounds__(kFuseWarps * 32, 3) sweepT_cx_kernel(const Swe
 #pragma unroll
   for (int d = 0; d < kPrefetch; ++d) issue_row<float, TL, MOM>(c, rstart + d);
   for (int rr = rstart; rr <= rend; rr += 3) {
-    fused_step_cx<TL, MOM, NAGF, 0, 0>(rr, c, k, st, wl, al, atl);
-    fused_step_cx<TL, MOM, NAGF, 1, 1>(rr + 1, c, k, st, wl, al, atl);
-    fused_step_cx<TL, MOM, NAGF, 2, 0>(rr + 2, c, k, st, wl, al, atl);
+    fused_step_cx<TL, MOM, NAGF, SP, 0, 0>(rr, c, k, st, wl, al, atl);
+    fused_step_cx<TL, MOM, NAGF, SP, 1, 1>(rr + 1, c, k, st, wl, al, atl);
+    fused_step_cx<TL, MOM, NAGF, SP, 2, 0>(rr + 2, c, k, st, wl, al, atl);
     if (MOM) {
 #pragma unroll
       for (int s = 0; s + 2 <= TL; ++s)
@@ -907,13 +916,17 @@ static cudaError_t fused_attributes_tl() {
 // The fused kernels' rings can exceed the default 48 KB of dynamic shared memory.
 cudaError_t init_fused_attributes() {
   const int cx_bytes = FusedRings<float, 4>::BYTES * kFuseWarps;
-  cudaError_t e = cudaFuncSetAttribute(sweepT_cx_kernel<4, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       cx_bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sweepT_cx_kernel<4, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cx_bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sweepT_cx_kernel<4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             cx_bytes);
+  cudaError_t e = cudaSuccess;
+#define RICHM_CX_ATTR(M, N, SP)                                                                                 \
+  if (e == cudaSuccess)                                                                                         \
+    e = cudaFuncSetAttribute(sweepT_cx_kernel<4, M, N, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, cx_bytes);
+  RICHM_CX_ATTR(true, true, false)
+  RICHM_CX_ATTR(true, false, false)
+  RICHM_CX_ATTR(false, false, false)
+  RICHM_CX_ATTR(true, true, true)
+  RICHM_CX_ATTR(true, false, true)
+  RICHM_CX_ATTR(false, false, true)
+#undef RICHM_CX_ATTR
   if (e == cudaSuccess) e = fused_attributes_tl<float, 4>();
   if (e == cudaSuccess) e = skew_attributes<float>();
   if (e == cudaSuccess) e = fused_attributes_tl<__nv_bfloat16, 4>();
@@ -993,9 +1006,18 @@ richm_status launch_sweep_fused_cx(richm_operator* op, int TL, const cplx<float>
   const size_t smem = (size_t)FusedRings<float, 4>::BYTES * kFuseWarps;
   const bool mom = a != nullptr;
   const bool nag = mom && at == nullptr;
-  if (nag) sweepT_cx_kernel<4, true, true><<<blocks, kFuseWarps * 32, smem, s>>>(A);
-  else if (mom) sweepT_cx_kernel<4, true, false><<<blocks, kFuseWarps * 32, smem, s>>>(A);
-  else sweepT_cx_kernel<4, false, false><<<blocks, kFuseWarps * 32, smem, s>>>(A);
+  bool sp = false;  // a sponge layer in the batch: the per-node diagonal term
+  for (const Inst& I : op->h_inst) sp = sp || I.sp_im != 0.0;
+#define RICHM_CX(SP)                                                                          \
+  if (nag) sweepT_cx_kernel<4, true, true, SP><<<blocks, kFuseWarps * 32, smem, s>>>(A);      \
+  else if (mom) sweepT_cx_kernel<4, true, false, SP><<<blocks, kFuseWarps * 32, smem, s>>>(A); \
+  else sweepT_cx_kernel<4, false, false, SP><<<blocks, kFuseWarps * 32, smem, s>>>(A);
+  if (sp) {
+    RICHM_CX(true)
+  } else {
+    RICHM_CX(false)
+  }
+#undef RICHM_CX
   RICHM_LAUNCH_CHECK("complex fused sweep");
   return RICHM_OK;
 }

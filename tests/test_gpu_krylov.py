@@ -173,3 +173,28 @@ def test_fgmres_basis_option_is_checked():
         op.fgmres(B, X, w, None, None, sweeps=5, m=5, inner=richm.C128, basis=richm.C64)
     with pytest.raises(richm.RichmError):
         op.fgmres(B, X, w, None, None, sweeps=5, m=5, inner=richm.C128, basis=richm.F32)
+
+
+@pytest.mark.parametrize("K", [8, 6])
+def test_sponge_fused_complex64_sweeps_match_oracle(K):
+    # the fused complex64 kernel with the sponge layer's per-node diagonal: passes of four
+    # sweeps (K = 6: one pass and two single sweeps), no preconditioner, against the
+    # oracle's eq. 21 matrix; the one-sweep kernel agrees with it to FP32 rounding
+    op, mats = _batch(SPECS)
+    bs = _rhs(SPECS, 14)
+    B = to_dev(op, bs, richm.C64)
+    G = np.array(op.gershgorin())
+    w = np.stack([np.array([0.3, 0.7, 0.5, 0.9]) / g for g in G])
+    a = np.full_like(w, 0.3)
+    out = {}
+    for fuse in (4, 1):
+        X, XP = op.zeros(richm.C64), op.zeros(richm.C64)
+        op.apply_sweeps(richm.C64, X, XP, B, coef(w, richm.C64), coef(a, richm.C64), None, K=K, m=4, fuse=fuse)
+        out[fuse] = from_dev(op, X, richm.C64)
+    for i, A in enumerate(mats):
+        bi = bs[i].ravel().astype(np.complex64).astype(np.complex128)
+        ref, _ = inner_steps(A, bi, np.zeros_like(bi), None, w[i].astype(np.float32).astype(np.float64),
+                             a[i].astype(np.float32).astype(np.float64), K=K)
+        scale = np.abs(ref).max()
+        assert np.abs(out[4][i].ravel() - ref).max() <= 1e-5 * scale, (i, np.abs(out[4][i].ravel() - ref).max())
+        assert np.abs(out[4][i] - out[1][i]).max() <= 1e-5 * scale
