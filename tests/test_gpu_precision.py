@@ -120,6 +120,9 @@ def test_fused_block_fp32_relative_error(batch, kind, order, kidx0):
           f"{worst:.3e} (derived bound {worst_bound:.3e})")
     if kind == "chebyshev" and (order == "leja" or kidx0 == 0):
         assert worst_bound <= 2e-4 and worst <= 1e-5, (worst, worst_bound)
+    if kind == "meta_beta03":
+        # the benchmark's own weights, in either order: within 1e-5 per block (observed ~1e-6)
+        assert worst <= 1e-5, worst
 
 
 def test_refinement_of_a_fused_cycle_is_exact(batch):
