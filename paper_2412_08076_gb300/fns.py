@@ -265,3 +265,60 @@ def train_algorithm2(net: MetaFNS, batches, C=2, cycles=2, steps=40, lr=2e-3, lo
         run("w")
         run("lam_t")
     return hist
+
+
+def table5_analogue(n: int = 63, classes=((1.0, 0.0), (1e-2, 0.0), (1e-4, 0.0), (1e-2, math.pi / 6), (1e-4, math.pi / 3)),
+                    B: int = 8, m: int = 4, M: int = 10, C: int = 2, cycles: int = 2, steps: int = 150,
+                    lr: float = 2e-3, tol: float = 1e-6, max_outer: int = 3000, log=None):
+    """Outer iterations of Richardson(m)-FNS to `tol` (the count of Tables 5-7) on classes
+    of (eps, theta) at n x n, Jacobi-preconditioned smoother with M sweeps per outer
+    iteration, for: the smoother alone (weights 0.5, no correction); the initial networks
+    (the stencil's periodic inverse, T = I); the networks trained by Algorithm 2 with
+    T = I; and trained with the banded transition. Training: B right-hand sides N(0, I)
+    per class, the classes taken in turn; counting: B others. Returns {row: {class: mean
+    count (None where some instance did not reach tol)}}."""
+    import richm_synth as synth
+    batches, evals = [], []
+    for k, (eps, th) in enumerate(classes):
+        insts = [synth.AnisoInstance(eps, th, n)] * B
+        op = richm.Operator([(richm.ANISO_Q1, t.n, t.eps, t.theta, 0.0) for t in insts])
+        mk = lambda seed: op.pack(torch.tensor(np.concatenate(
+            [synth.rhs_normal(seed, i, n).ravel() for i in range(B)]), dtype=torch.float32, device="cuda"), richm.F32)
+        X = torch.tensor(synth.meta_inputs(insts), dtype=torch.float32, device="cuda")
+        batches.append((op, mk(300 + k), X[:1].contiguous(), X))
+        evals.append((op, mk(400 + k), X[:1].contiguous(), X))
+
+    def mean_count(counts):
+        return None if any(c is None for c in counts) else float(np.mean(counts))
+
+    out = {}
+    row = {}
+    for (eps, th), (op, b, X1, XB) in zip(classes, evals):
+        S0 = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+        f = FNS(op, torch.full((op.batch, m), 0.5, device="cuda"), m, M, S0, precond=1)
+        row[f"{eps:g},{th:.3f}"] = mean_count(f.iterations(b, tol=tol, max_outer=max_outer))
+    out["smoother_alone"] = row
+    for name, use_t, train in (("initial_networks", False, False), ("trained_T_identity", False, True),
+                               ("trained_with_T", True, True)):
+        net = MetaFNS(m=m, M=M, use_t=use_t)
+        if train:
+            hist = train_algorithm2(net, batches, C=C, cycles=cycles, steps=steps, lr=lr)
+            if log:
+                log(f"{name}: loss {np.mean(hist[:len(classes)]):.3f} -> {np.mean(hist[-len(classes):]):.3f}")
+        row = {}
+        for (eps, th), (op, b, X1, XB) in zip(classes, evals):
+            row[f"{eps:g},{th:.3f}"] = mean_count(net.iterations(op, b, X1, XB, tol=tol, max_outer=max_outer))
+        out[name] = row
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="Richardson(m)-FNS outer-iteration counts (Tables 5-7 analogue)")
+    ap.add_argument("--n", type=int, default=63)
+    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--cycles", type=int, default=2)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    args = ap.parse_args()
+    print(json.dumps(table5_analogue(n=args.n, steps=args.steps, cycles=args.cycles, tol=args.tol, log=print)))
