@@ -8,8 +8,8 @@
 // space; the batch moves in lockstep and an instance whose residual estimate reached
 // the tolerance stops taking Arnoldi steps.
 //
-// GB300 form: the Arnoldi basis V and the iterate are complex128 in the padded
-// layout; the preconditioner (K smoother sweeps on A z = v from z = 0) runs in
+// GB300 form: the Arnoldi basis V (complex128 by default) and the iterate (complex128)
+// are in the padded layout; the preconditioner (K smoother sweeps on A z = v from z = 0) runs in
 // complex64 (or complex128), and the z_j are kept in that type: the flexible variant
 // only needs w = A z_j for the z_j it keeps, so storing them narrow is exact. The
 // orthogonalisation is classical Gram-Schmidt applied twice (two passes of one
@@ -39,9 +39,9 @@ namespace richm {
 using C128 = cplx<double>;
 using C64 = cplx<float>;
 constexpr int kMaxRestart = 64;
-// Rows of a Krylov warp tile: short tiles give the streaming kernels (dots, updates,
-// products) four times the warps of the residual geometry, enough loads in flight
-// per SM to stream at HBM rate.
+// Rows of a Krylov warp tile: short tiles give the streaming kernels (updates, products,
+// scaling, the solution update) four times the warps of the residual geometry, more
+// loads in flight per SM.
 constexpr int kKryRows = 4;
 // the dots keep the residual's 16-row tiles: one block row per basis vector already
 // gives them enough warps, and fewer partial sums to reduce
