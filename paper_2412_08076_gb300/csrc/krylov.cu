@@ -78,14 +78,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     if (c0 < I.n) {
       const int r0 = t.ty * kDotRows + 1;
       const int r1 = min(r0 + kDotRows - 1, I.n);
-      const VB* vi = V + (size_t)i * vstride + I.off;
-      const VB* wb = w + I.off;
-#pragma unroll 4
-      for (int r = r0; r <= r1; ++r) {
-        const long long o = (long long)r * I.pitch + c0;
-        const VB p = conj_mul(vi[o], wb[o]);
-        sre += p.re;
-        sim += p.im;
+      const VB* vi = V + (size_t)i * vstride + I.off + c0;
+      const VB* wb = w + I.off + c0;
+      // eight rows' loads issued together at a time (the tile's rows are independent)
+      constexpr int kBatch = 8;
+#pragma unroll
+      for (int h = 0; h < kDotRows; h += kBatch) {
+        VB va[kBatch], wa[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+          const long long o = (long long)(r0 + h + q) * I.pitch;
+          const bool ok = r0 + h + q <= r1;
+          va[q] = ok ? vi[o] : VB{T(0), T(0)};
+          wa[q] = ok ? wb[o] : VB{T(0), T(0)};
+        }
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+          const VB p = conj_mul(va[q], wa[q]);
+          sre += p.re;
+          sim += p.im;
+        }
       }
     }
   }
