@@ -165,14 +165,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       VB* wb = w + I.off;
       for (int r = r0; r <= r1; ++r) {
         const long long o = (long long)r * I.pitch + c0;
-        VB acc = wb[o];
-#pragma unroll 4
-        for (int i = 0; i < nv; ++i) {
-          VB hi;
-          if constexpr (NARROW) hi = hs[wi][i];
-          else hi = d2c(hb[i]);
-          acc = acc - cmul(hi, V[(size_t)i * vstride + I.off + o]);
+        // two independent sums (even and odd vectors) halve the dependent chain
+        VB acc = wb[o], acc2{T(0), T(0)};
+        int i = 0;
+#pragma unroll 2
+        for (; i + 1 < nv; i += 2) {
+          VB h0, h1;
+          if constexpr (NARROW) {
+            h0 = hs[wi][i];
+            h1 = hs[wi][i + 1];
+          } else {
+            h0 = d2c(hb[i]);
+            h1 = d2c(hb[i + 1]);
+          }
+          const VB v0 = V[(size_t)i * vstride + I.off + o], v1 = V[(size_t)(i + 1) * vstride + I.off + o];
+          acc = acc - cmul(h0, v0);
+          acc2 = acc2 + cmul(h1, v1);
         }
+        if (i < nv) {
+          VB h0;
+          if constexpr (NARROW) h0 = hs[wi][i];
+          else h0 = d2c(hb[i]);
+          acc = acc - cmul(h0, V[(size_t)i * vstride + I.off + o]);
+        }
+        acc = acc - acc2;
         wb[o] = acc;
         s2 += acc.re * acc.re + acc.im * acc.im;
       }
