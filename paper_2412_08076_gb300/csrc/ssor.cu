@@ -410,20 +410,21 @@ __device__ __forceinline__ void scaled_rhs(const RowVW<E, VW>& U, const RowVW<E,
   }
 }
 
-// FP32 rows of 16 columns per lane: the same on packed pairs of columns (sm_100's FFMA2
+// FP32 rows of VW columns per lane: the same on packed pairs of columns (sm_100's FFMA2
 // and friends: one issue slot for two columns), with the horizontal couplings written
 // per column as west / east terms W_j = axr C_j + d1r U_j + d2r D_j and
 // E_j = axr C_j + d2r U_j + d1r D_j formed on pairs, so that only their shifted sum
 // W_{e-1} + E_{e+1} needs per-column adds.
-template <>
-__device__ __forceinline__ void scaled_rhs<float, 16>(const RowVW<float, 16>& U, const RowVW<float, 16>& C,
-                                                      const RowVW<float, 16>& D, const float* bv, float rc, float axr,
-                                                      float ayr, float d1r, float d2r, float* rp) {
+template <int VW>
+__device__ __forceinline__ void scaled_rhs_f32(const RowVW<float, VW>& U, const RowVW<float, VW>& C,
+                                               const RowVW<float, VW>& D, const float* bv, float rc, float axr,
+                                               float ayr, float d1r, float d2r, float* rp) {
+  constexpr int NP = VW / 2;
   const float2 ax2 = make_float2(axr, axr), d12 = make_float2(d1r, d1r), d22 = make_float2(d2r, d2r);
   const float2 nay2 = make_float2(-ayr, -ayr), rc2 = make_float2(rc, rc), m1 = make_float2(-1.f, -1.f);
-  float W[16], E[16];
+  float W[VW], E[VW];
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
+  for (int p = 0; p < NP; ++p) {
     const float2 c2 = make_float2(C.v[2 * p], C.v[2 * p + 1]);
     const float2 u2 = make_float2(U.v[2 * p], U.v[2 * p + 1]);
     const float2 d2 = make_float2(D.v[2 * p], D.v[2 * p + 1]);
@@ -438,13 +439,13 @@ __device__ __forceinline__ void scaled_rhs<float, 16>(const RowVW<float, 16>& U,
   const float wl = fmaf(d2r, D.l, fmaf(d1r, U.l, axr * C.l));  // W of the column left of this lane
   const float er = fmaf(d1r, D.r, fmaf(d2r, U.r, axr * C.r));  // E of the column right of this lane
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
+  for (int p = 0; p < NP; ++p) {
     const float2 c2 = make_float2(C.v[2 * p], C.v[2 * p + 1]);
     const float2 u2 = make_float2(U.v[2 * p], U.v[2 * p + 1]);
     const float2 d2 = make_float2(D.v[2 * p], D.v[2 * p + 1]);
     const float2 b2 = make_float2(bv[2 * p], bv[2 * p + 1]);
     const float2 s2 = make_float2((p == 0 ? wl : W[2 * p - 1]) + E[2 * p + 1],
-                                  W[2 * p] + (p == 7 ? er : E[2 * p + 2]));
+                                  W[2 * p] + (p == NP - 1 ? er : E[2 * p + 2]));
     float2 t = __ffma2_rn(m1, c2, __fmul2_rn(b2, rc2));
     t = __ffma2_rn(nay2, __fadd2_rn(u2, d2), t);
     t = __ffma2_rn(m1, s2, t);
@@ -454,19 +455,53 @@ __device__ __forceinline__ void scaled_rhs<float, 16>(const RowVW<float, 16>& U,
 }
 
 template <>
-__device__ __forceinline__ void y_from<float, 16>(const float* xv, const float* xpv, float at, bool mom,
-                                                  RowVW<float, 16>& Y) {
+__device__ __forceinline__ void scaled_rhs<float, 16>(const RowVW<float, 16>& U, const RowVW<float, 16>& C,
+                                                      const RowVW<float, 16>& D, const float* bv, float rc, float axr,
+                                                      float ayr, float d1r, float d2r, float* rp) {
+  scaled_rhs_f32<16>(U, C, D, bv, rc, axr, ayr, d1r, d2r, rp);
+}
+template <>
+__device__ __forceinline__ void scaled_rhs<float, 8>(const RowVW<float, 8>& U, const RowVW<float, 8>& C,
+                                                     const RowVW<float, 8>& D, const float* bv, float rc, float axr,
+                                                     float ayr, float d1r, float d2r, float* rp) {
+  scaled_rhs_f32<8>(U, C, D, bv, rc, axr, ayr, d1r, d2r, rp);
+}
+template <>
+__device__ __forceinline__ void scaled_rhs<float, 4>(const RowVW<float, 4>& U, const RowVW<float, 4>& C,
+                                                     const RowVW<float, 4>& D, const float* bv, float rc, float axr,
+                                                     float ayr, float d1r, float d2r, float* rp) {
+  scaled_rhs_f32<4>(U, C, D, bv, rc, axr, ayr, d1r, d2r, rp);
+}
+
+template <int VW>
+__device__ __forceinline__ void y_from_f32(const float* xv, const float* xpv, float at, bool mom,
+                                           RowVW<float, VW>& Y) {
   const float2 at2 = make_float2(at, at), m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
+  for (int p = 0; p < VW / 2; ++p) {
     const float2 x2 = make_float2(xv[2 * p], xv[2 * p + 1]);
     float2 y2 = x2;
     if (mom) y2 = __ffma2_rn(at2, __ffma2_rn(m1, make_float2(xpv[2 * p], xpv[2 * p + 1]), x2), x2);
     Y.v[2 * p] = y2.x;
     Y.v[2 * p + 1] = y2.y;
   }
-  Y.l = __shfl_up_sync(0xffffffffu, Y.v[15], 1);
+  Y.l = __shfl_up_sync(0xffffffffu, Y.v[VW - 1], 1);
   Y.r = __shfl_down_sync(0xffffffffu, Y.v[0], 1);
+}
+template <>
+__device__ __forceinline__ void y_from<float, 16>(const float* xv, const float* xpv, float at, bool mom,
+                                                  RowVW<float, 16>& Y) {
+  y_from_f32<16>(xv, xpv, at, mom, Y);
+}
+template <>
+__device__ __forceinline__ void y_from<float, 8>(const float* xv, const float* xpv, float at, bool mom,
+                                                 RowVW<float, 8>& Y) {
+  y_from_f32<8>(xv, xpv, at, mom, Y);
+}
+template <>
+__device__ __forceinline__ void y_from<float, 4>(const float* xv, const float* xpv, float at, bool mom,
+                                                 RowVW<float, 4>& Y) {
+  y_from_f32<4>(xv, xpv, at, mom, Y);
 }
 
 // ---------------------------------------------------------------- two-warp row pipelines
@@ -857,9 +892,8 @@ __global__ void __launch_bounds__(64) ssor_backward_pipe_kernel(const SsorArgs<E
 }
 
 // The row kernels' rings exceed the default 48 KB of dynamic shared memory per block.
-template <typename E>
+template <typename E, int VW>
 static cudaError_t ssor_row_attributes() {
-  constexpr int VW = SsorVW<E>::v;
   cudaError_t e = cudaFuncSetAttribute(ssor_forward_pipe_kernel<E, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        PipeSizes<E, VW>::FWD);
   if (e == cudaSuccess)
@@ -869,9 +903,22 @@ static cudaError_t ssor_row_attributes() {
 }
 
 cudaError_t init_ssor_attributes() {
-  cudaError_t e = ssor_row_attributes<float>();
-  if (e == cudaSuccess) e = ssor_row_attributes<double>();
+  cudaError_t e = ssor_row_attributes<float, 16>();
+  if (e == cudaSuccess) e = ssor_row_attributes<float, 8>();
+  if (e == cudaSuccess) e = ssor_row_attributes<float, 4>();
+  if (e == cudaSuccess) e = ssor_row_attributes<double, 8>();
+  if (e == cudaSuccess) e = ssor_row_attributes<double, 4>();
   return e;
+}
+
+// The two-warp row pipelines with VW columns per lane (rows of at most 32 VW columns).
+template <typename E, int VW>
+static richm_status launch_ssor_pipes(richm_operator* op, const SsorArgs<E>& A, cudaStream_t s) {
+  ssor_forward_pipe_kernel<E, VW><<<op->batch, 64, PipeSizes<E, VW>::FWD, s>>>(A);
+  RICHM_LAUNCH_CHECK("SSOR forward solve");
+  ssor_backward_pipe_kernel<E, VW><<<op->batch, 64, PipeSizes<E, VW>::BWD, s>>>(A);
+  RICHM_LAUNCH_CHECK("SSOR backward solve");
+  return RICHM_OK;
 }
 
 template <typename E>
@@ -885,12 +932,12 @@ richm_status launch_ssor_sweep(richm_operator* op, const E* x, const E* xp, cons
   const int blocks = (op->batch + kSsorWarps - 1) / kSsorWarps;
   int max_pitch = 0;
   for (const Inst& I : op->h_inst) max_pitch = std::max(max_pitch, I.pitch);
-  if (max_pitch <= 32 * VW) {  // every row is one chunk: two-warp row pipelines, one block per instance
-    ssor_forward_pipe_kernel<E, VW><<<op->batch, 64, PipeSizes<E, VW>::FWD, s>>>(A);
-    RICHM_LAUNCH_CHECK("SSOR forward solve");
-    ssor_backward_pipe_kernel<E, VW><<<op->batch, 64, PipeSizes<E, VW>::BWD, s>>>(A);
-    RICHM_LAUNCH_CHECK("SSOR backward solve");
-    return RICHM_OK;
+  // every row is one chunk: two-warp row pipelines, one block per instance, with the
+  // fewest columns per lane that cover the widest row (shorter lane chains per row)
+  if (max_pitch <= 128) return launch_ssor_pipes<E, 4>(op, A, s);
+  if (max_pitch <= 256) return launch_ssor_pipes<E, 8>(op, A, s);
+  if constexpr (VW == 16) {
+    if (max_pitch <= 512) return launch_ssor_pipes<E, 16>(op, A, s);
   }
   ssor_forward_kernel<E, VW><<<blocks, kSsorWarps * 32, 0, s>>>(A);
   RICHM_LAUNCH_CHECK("SSOR forward solve");
