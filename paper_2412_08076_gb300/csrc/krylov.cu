@@ -607,8 +607,14 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
                                                                      S.in_cycle);
         RICHM_LAUNCH_CHECK("FGMRES scale");
       }
-      RICHM_TRY(read_count());
-      if (h_count == 0) break;
+      // the host looks at the count of instances still in the cycle every fourth step
+      // (each look is a round trip that idles the GPU); steps taken after every instance
+      // left the cycle change nothing, since every kernel but the preconditioner's skips
+      // the instances outside it
+      if ((j & 3) == 3 || j + 1 == R) {
+        RICHM_TRY(read_count());
+        if (h_count == 0) break;
+      }
     }
     kry_backsolve_kernel<<<iblocks, ithr, 0, s>>>(S, B, R);
     RICHM_LAUNCH_CHECK("FGMRES back substitution");
