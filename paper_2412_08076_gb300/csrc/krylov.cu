@@ -550,9 +550,9 @@ static richm_status fgmres_t(richm_operator* op, const C128* b, C128* x, const v
     RICHM_CUDA_TRY(cudaStreamSynchronize(s));
     return RICHM_OK;
   };
-  // one sweep per launch: a preconditioner application is a handful of sweeps on a
-  // small batch, where the fused passes' tall tiles would occupy few SMs
-  richm_sweep_opts so{o->m, 0, o->precond, 1, 1.0};
+  // the library's choice of pass length (complex64 without preconditioner: fused passes
+  // of four sweeps, on tiles short enough to spread a small batch over the GPU)
+  richm_sweep_opts so{o->m, 0, o->precond, 0, 1.0};
   for (int cycle = 0;; ++cycle) {
     // r = b - A x, beta = |r| (and |b| at the first cycle from the same pass)
     if constexpr (NB) RICHM_TRY((launch_residual_to<C128, C64>(op, x, b, W, norms, nullptr, s, false)));

@@ -997,9 +997,20 @@ richm_status launch_sweep_fused_cx(richm_operator* op, int TL, const cplx<float>
                                    const float* a, const float* at, int m, int kidx0, const int* active,
                                    cudaStream_t s, int rows) {
   if (TL != 4) return set_error(RICHM_ERR_ARG, "complex fused sweeps take 4 sweeps per pass");
-  if (rows <= 0) rows = op->best_rows;
   const TileMap* tm = nullptr;
-  RICHM_TRY(get_tiles(op, -100 - TL, rows, &tm));
+  if (rows <= 0) {
+    // the operator's tile height, halved (down to 16 rows) while the batch has fewer
+    // warp tiles than two blocks per SM take: a small batch then still spreads over the
+    // GPU (4 x 511^2: 5 sweeps in 49 instead of 112 us)
+    rows = op->best_rows;
+    RICHM_TRY(get_tiles(op, -100 - TL, rows, &tm));
+    while (rows > 16 && tm->ntiles < 2 * kFuseWarps * op->sms) {
+      rows /= 2;
+      RICHM_TRY(get_tiles(op, -100 - TL, rows, &tm));
+    }
+  } else {
+    RICHM_TRY(get_tiles(op, -100 - TL, rows, &tm));
+  }
   SweepTArgs A{op->d_inst, tm->d_tiles, tm->ntiles, x, xp, reinterpret_cast<const float*>(b), out_x, out_xp,
                w, a, at, m, kidx0, active, rows};
   const int blocks = (tm->ntiles + kFuseWarps - 1) / kFuseWarps;
