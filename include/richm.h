@@ -321,7 +321,13 @@ richm_status richm_solve_workspace(const richm_operator* op, const richm_solve_o
  * w / alpha / alpha_t: [batch][m] in the real type of opts->inner (alpha, alpha_t as in
  * richm_apply_sweeps). info: host [batch]. Synchronises `stream` before returning.
  * Returns RICHM_OK if every instance converged, else RICHM_ERR_DIVERGED if any
- * diverged, else RICHM_ERR_NOT_CONVERGED. */
+ * diverged, else RICHM_ERR_NOT_CONVERGED. The operator keeps the call's session (the
+ * richm_solver below: its stream, events, pinned words and captured cycle graphs) for
+ * the next richm_solve or richm_solve_host with the same options, the same weight and
+ * workspace pointers and the same tuned fused settings, so repeated solves skip that
+ * setup; it is released with the operator or replaced by the next call that differs.
+ * One-call solves on one operator must therefore not run from several host threads
+ * at once. */
 richm_status richm_solve(richm_operator* op, const double* b, double* x, const void* w, const void* alpha,
                          const void* alpha_t, const richm_solve_opts* opts, richm_solve_info* info,
                          void* work, size_t work_bytes, void* stream);

@@ -299,6 +299,7 @@ void richm_operator_destroy(richm_operator* op) {
     cudaFree(kv.second.d_tiles);
     cudaFree(kv.second.d_inst_begin);
   }
+  richm::solver_release_oneshot(op);
   if (op->d_inst) cudaFree(op->d_inst);
   richm::fourier_release(op);
   delete op;

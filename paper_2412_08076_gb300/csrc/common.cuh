@@ -114,6 +114,14 @@ struct richm_operator {
   int best_rows = 256;  // rows of a fused-sweep warp tile (set by richm_autotune)
   // cuFFT state for richm_fourier_correction (created on first use)
   void* fft_state = nullptr;
+  // The session richm_solve / richm_solve_host keep for the next call with the same
+  // options, weights, workspace and tuned settings: its stream, events, pinned words and
+  // captured cycle graphs are reused instead of being set up again for every solve.
+  richm_solver* oneshot = nullptr;
+  richm_solve_opts oneshot_opts{};
+  const void* oneshot_ptrs[4] = {nullptr, nullptr, nullptr, nullptr};  // w, alpha, alpha_t, work
+  size_t oneshot_bytes = 0;
+  int oneshot_tuned[2] = {0, 0};  // best_fuse, best_rows when it was created
 };
 
 namespace richm {
@@ -379,5 +387,8 @@ __device__ inline void stv(T* p, const VecN<T, N>& r) {
 
 // Releases the cuFFT state of an operator (defined with the Fourier correction).
 void fourier_release(richm_operator* op);
+
+// Destroys the session richm_solve keeps between calls (defined with the solver).
+void solver_release_oneshot(richm_operator* op);
 
 }  // namespace richm

@@ -857,6 +857,47 @@ richm_status richm_solve_host_workspace(const richm_operator* op, const richm_so
   return RICHM_OK;
 }
 
+}  // extern "C"
+
+namespace richm {
+
+void solver_release_oneshot(richm_operator* op) {
+  richm_solver_destroy(op->oneshot);
+  op->oneshot = nullptr;
+}
+
+// The session of a one-call solve: the operator's kept session when the options, the
+// weight and workspace pointers and the tuned fused settings are those it was created
+// with, else a new one (replacing it). A session is only pointers and launch plans, so
+// reuse changes no arithmetic; its graphs are captured again when b or x move.
+static richm_status oneshot_solver(richm_operator* op, const richm_solve_opts* o, const void* w, const void* alpha,
+                                   const void* alpha_t, void* work, size_t work_bytes, richm_solver** out) {
+  const void* ptrs[4] = {w, alpha, alpha_t, work};
+  const int tuned[2] = {op->best_fuse, op->best_rows};
+  if (op->oneshot && memcmp(&op->oneshot_opts, o, sizeof(*o)) == 0 && memcmp(op->oneshot_ptrs, ptrs, sizeof(ptrs)) == 0 &&
+      op->oneshot_bytes == work_bytes && memcmp(op->oneshot_tuned, tuned, sizeof(tuned)) == 0) {
+    *out = op->oneshot;
+    return RICHM_OK;
+  }
+  solver_release_oneshot(op);
+  RICHM_TRY(richm_solver_create(op, o, w, alpha, alpha_t, work, work_bytes, out));
+  op->oneshot = *out;
+  op->oneshot_opts = *o;
+  memcpy(op->oneshot_ptrs, ptrs, sizeof(ptrs));
+  op->oneshot_bytes = work_bytes;
+  memcpy(op->oneshot_tuned, tuned, sizeof(tuned));
+  return RICHM_OK;
+}
+
+// Ends a one-call solve: a session that met a CUDA or argument error is not kept.
+static void oneshot_done(richm_operator* op, richm_status st) {
+  if (st != RICHM_OK && st != RICHM_ERR_NOT_CONVERGED && st != RICHM_ERR_DIVERGED) solver_release_oneshot(op);
+}
+
+}  // namespace richm
+
+extern "C" {
+
 richm_status richm_solve_host(richm_operator* op, const double* b_host, double* x_host, const void* w,
                               const void* alpha, const void* alpha_t, const richm_solve_opts* o,
                               richm_solve_info* info, void* work, size_t work_bytes, void* stream) {
@@ -877,11 +918,11 @@ richm_status richm_solve_host(richm_operator* op, const double* b_host, double* 
   RICHM_CUDA_TRY(cudaMemcpyAsync(stage, b_host, dense * sizeof(double), cudaMemcpyHostToDevice, s));
   RICHM_TRY(richm_pack(op, RICHM_F64, stage, bd, stream));
   richm_solver* S = nullptr;
-  RICHM_TRY(richm_solver_create(op, o, w, alpha, alpha_t, work, sw, &S));
+  RICHM_TRY(oneshot_solver(op, o, w, alpha, alpha_t, work, sw, &S));
   richm_status st = richm_solver_start_zero(S, bd, xd, stream);
   if (st == RICHM_OK) st = run_to_completion(S, o->max_sweeps / o->refine_every + 2, s);
   if (st == RICHM_OK) st = richm_solver_finish(S, info, stream);
-  richm_solver_destroy(S);
+  oneshot_done(op, st);
   if (st != RICHM_OK && st != RICHM_ERR_NOT_CONVERGED && st != RICHM_ERR_DIVERGED) return st;
   const richm_status solve_st = st;
   RICHM_TRY(richm_unpack(op, RICHM_F64, xd, stage, stream));
@@ -896,11 +937,11 @@ richm_status richm_solve(richm_operator* op, const double* b, double* x, const v
   clear_error();
   RICHM_ARG(info != nullptr, "null info");
   richm_solver* S = nullptr;
-  RICHM_TRY(richm_solver_create(op, o, w, alpha, alpha_t, work, work_bytes, &S));
+  RICHM_TRY(oneshot_solver(op, o, w, alpha, alpha_t, work, work_bytes, &S));
   richm_status st = richm_solver_start(S, b, x, stream);
   if (st == RICHM_OK) st = run_to_completion(S, o->max_sweeps / o->refine_every + 2, (cudaStream_t)stream);
   if (st == RICHM_OK) st = richm_solver_finish(S, info, stream);
-  richm_solver_destroy(S);
+  oneshot_done(op, st);
   return st;
 }
 

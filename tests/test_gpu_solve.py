@@ -280,6 +280,67 @@ def test_solve_host_matches_device_solve():
         assert np.linalg.norm(bs[i].ravel() - As[i] @ u) / np.linalg.norm(bs[i]) <= 1e-10
 
 
+def test_kept_session_repeats_and_rebinds():
+    # richm_solve keeps its session in the operator for the next call with the same
+    # options, weights and workspace: repeated solves (graphs reused), new weight values
+    # behind the same pointers, another x buffer, other options and an interleaved host
+    # solve each give the bits of a solve on a fresh operator
+    sizes = [15, 40, 63, 130]
+
+    def fresh(bs_, w_, a_, opts_kw):
+        insts, op, As, w, a, bs = _solve_setup(sizes)
+        X = op.zeros(richm.F64)
+        st, info = op.solve(to_dev(op, bs_, richm.F64), X, coef(w_, richm.F32), coef(a_, richm.F32), None,
+                            op.solve_opts(16, **opts_kw))
+        x = X.cpu().numpy()
+        op.close()
+        return st, info, x
+
+    kw1 = dict(tol=1e-10, max_sweeps=400000, refine_every=64, use_graph=1, fuse=8)
+    kw2 = dict(tol=1e-9, max_sweeps=400000, refine_every=32, use_graph=1, fuse=4)
+    insts, op, As, w, a, bs = _solve_setup(sizes)
+    wt, at = coef(w, richm.F32), coef(a, richm.F32)
+    B = to_dev(op, bs, richm.F64)
+    work = op.workspace(op._ws("richm_solve_workspace", richm.C.byref(op.solve_opts(16, **kw1))))
+    ref1 = fresh(bs, w, a, kw1)
+    X = op.zeros(richm.F64)
+    for _ in range(3):
+        X.zero_()
+        st, info = op.solve(B, X, wt, at, None, op.solve_opts(16, **kw1), work=work)
+        assert (st, info) == ref1[:2]
+        np.testing.assert_array_equal(X.cpu().numpy(), ref1[2])
+    # new weights written into the same device arrays
+    w2 = w * 0.97
+    wt.copy_(coef(w2, richm.F32))
+    ref2 = fresh(bs, w2, a, kw1)
+    X.zero_()
+    st, info = op.solve(B, X, wt, at, None, op.solve_opts(16, **kw1), work=work)
+    assert (st, info) == ref2[:2]
+    np.testing.assert_array_equal(X.cpu().numpy(), ref2[2])
+    # another x buffer (the kept graphs are captured again)
+    X2 = op.zeros(richm.F64)
+    st, info = op.solve(B, X2, wt, at, None, op.solve_opts(16, **kw1), work=work)
+    np.testing.assert_array_equal(X2.cpu().numpy(), ref2[2])
+    # other options
+    ref3 = fresh(bs, w2, a, kw2)
+    X2.zero_()
+    st, info = op.solve(B, X2, wt, at, None, op.solve_opts(16, **kw2), work=work)
+    assert (st, info) == ref3[:2]
+    np.testing.assert_array_equal(X2.cpu().numpy(), ref3[2])
+    # a host solve in between, then the device solve again
+    hb = torch.tensor(np.concatenate([v.ravel() for v in bs])).pin_memory()
+    hx = torch.empty(op.dense_elems(), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        st_h, info_h = op.solve_host(hb, hx, wt, at, None, op.solve_opts(16, **kw1))
+        assert info_h == ref2[1]
+        dense = op.unpack(torch.tensor(ref2[2], device="cuda"), richm.F64).cpu().numpy()
+        np.testing.assert_array_equal(hx.numpy(), dense)
+    X.zero_()
+    st, info = op.solve(B, X, wt, at, None, op.solve_opts(16, **kw1), work=work)
+    np.testing.assert_array_equal(X.cpu().numpy(), ref2[2])
+    op.close()
+
+
 def test_bf16_inner_state_converges_with_mild_steps_and_reports_divergence_otherwise():
     # bfloat16 inner iterate (FP32 arithmetic), FP64 refinement. With steps that damp
     # every mode (|1 - w lam| <= 1) the refinement removes the storage rounding and the
