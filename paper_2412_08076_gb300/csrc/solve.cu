@@ -126,10 +126,47 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
+// hi = the binary64 value d rounded to binary32 (as f64_to_f32_rn) and lo = d - hi to
+// binary32 precision, from the fields of d: the remainder is the 29 dropped fraction
+// bits (less one unit of the kept fraction when hi was rounded up), converted and
+// scaled by d's exponent. Outside the range where that scale is a normal binary32
+// (|d| < 2^-74 or hi not finite) lo is 0.
+__device__ __forceinline__ float f64_split_f32(double d, float& lo) {
+  const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+  const unsigned ex = (hw >> 20) & 0x7ffu;
+  const float hi = f64_to_f32_rn(d);
+  lo = 0.f;
+  if (ex - 949u < 254u && ex - 897u < 254u) {
+    const int rest = (int)(lw & 0x1fffffffu);
+    const int up = (rest > 0x10000000 || (rest == 0x10000000 && ((lw >> 29) & 1u))) ? 1 : 0;
+    const float scale = __uint_as_float((ex - 948u) << 23);  // 2^(exponent of d - 52)
+    const float mag = (float)(rest - (up << 29)) * scale;
+    lo = (hw & 0x80000000u) ? -mag : mag;
+  }
+  return hi;
+}
+
+// (s_hi, s_lo) += (hi + lo)^2 with the square of hi exact as a pair (FMA remainder),
+// the cross term 2 hi lo added to the remainder, lo^2 dropped (below 2^-46 of the
+// square), and the sum kept as an unevaluated pair (two-sum).
+__device__ __forceinline__ void sq_acc(float hi, float lo, float& s_hi, float& s_lo) {
+  const float p = hi * hi;
+  const float q = fmaf(2.f * hi, lo, fmaf(hi, hi, -p));
+  const float s = s_hi + p;
+  const float bp = s - s_hi;
+  const float err = (s_hi - (s - bp)) + (p - bp);
+  s_hi = s;
+  s_lo += err + q;
+}
+
 // Refinement after a fused cycle: for the tile's rows, x_out = x_in + e (FP64; e is
 // the cycle's final correction, read here and left in place) and
 // rhs = b - A (x_in + e) in FP64 (b folded into the multiply-adds, the sum formed on
-// the fly for the halo rows too), with the tile's partial sum (|r|^2, 0).
+// the fly for the halo rows too), with the tile's partial sum (|r|^2, 0). GB300's FP64
+// pipe bounds this kernel (its cost is per active lane), so |r|^2 is summed on the FP32
+// pipe: r split into its binary32 rounding and remainder, each square exact as a pair,
+// the lane's sum a two-sum pair (relative error ~2^-43 over a tile's 32 terms), and
+// only the lanes' sums widened to FP64.
 template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     refine_fused_kernel(const Inst* insts, const Tile* tiles, int ntiles, const double* __restrict__ x_in,
@@ -167,7 +204,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
     row_neighbours<double, 2>(Y, lane, le, re);
   };
-  double sr = 0.0;
+  float s_hi = 0.f, s_lo = 0.f;  // the lane's |r|^2 as an unevaluated FP32 pair
   RowT<double, 2> U, C, D;
   load(r0 - 1, U);
   load(r0, C);
@@ -179,12 +216,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const double bb[2] = {bv.x, bv.y};
     double rv[2];
     resid_q1<2>(U, C, D, bb, I.c, I.ax, I.ay, I.d1, I.d2, rv);
-    float2 out;
+    float2 out, lo;
     const bool ok0 = c0 < n, ok1 = c0 + 1 < n;
-    if (ok0) sr = fma(rv[0], rv[0], sr);
-    if (ok1) sr = fma(rv[1], rv[1], sr);
-    out.x = ok0 ? f64_to_f32_rn(rv[0]) : 0.f;
-    out.y = ok1 ? f64_to_f32_rn(rv[1]) : 0.f;
+    out.x = ok0 ? f64_split_f32(rv[0], lo.x) : 0.f;
+    out.y = ok1 ? f64_split_f32(rv[1], lo.y) : 0.f;
+    if (!ok0) lo.x = 0.f;
+    if (!ok1) lo.y = 0.f;
+    sq_acc(out.x, lo.x, s_hi, s_lo);
+    sq_acc(out.y, lo.y, s_hi, s_lo);
     if (live) {
       *reinterpret_cast<float2*>(rhs + o) = out;
       *reinterpret_cast<double2*>(x_out + o) = make_double2(C.y[0], C.y[1]);
@@ -192,6 +231,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     U = C;
     C = D;
   }
+  double sr = f32_to_f64_exact(s_hi) + f32_to_f64_exact(s_lo);
   sr = warp_sum(sr);
   if (lane == 0) partials[wt] = make_double2(sr, 0.0);
 }

@@ -120,6 +120,25 @@ def test_refinement_residual_norm_matches_oracle(inner):
         assert abs(info[i][1] - r) <= 1e-12 * r + 1e-13, (t, info[i][1], r)
 
 
+def test_fused_refinement_norm_over_a_wide_range():
+    # the fused refinement sums |r|^2 as FP32 pairs from r's binary32 split; right-hand
+    # sides whose entries span 1e-30 .. 1e6 (residual entries below 2^-74 take the
+    # unsplit path) give the FP64 relative residual to 1e-12
+    insts, op, As, w, a, bs = _solve_setup([33, 64, 130])
+    rng = np.random.default_rng(17)
+    bs = [v * 10.0 ** rng.uniform(-30, 6, v.shape) for v in bs]
+    B = to_dev(op, bs, richm.F64)
+    for sweeps in (64, 192):
+        X = op.zeros(richm.F64)
+        opts = op.solve_opts(16, tol=0.0, max_sweeps=sweeps, refine_every=64, inner=richm.F32, fuse=8)
+        st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None, opts)
+        xs = from_dev(op, X, richm.F64)
+        for i, t in enumerate(insts):
+            r = np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i])
+            assert info[i][0] == sweeps
+            assert abs(info[i][1] - r) <= 1e-12 * r + 1e-15, (t, info[i][1], r)
+
+
 def test_integer_field_conversions_match_hardware():
     assert richm.selftest_conversions() == (0, 0)
 
