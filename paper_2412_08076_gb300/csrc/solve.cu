@@ -33,6 +33,11 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+// Readbacks of the active count in flight in richm_solve's loop: the host acts on the
+// count of the cycle kSolveReadDepth - 1 cycles before the newest one queued, so that a
+// late host thread (a preempted wait on a shared machine) finds cycles still queued.
+static constexpr int kSolveReadDepth = 4;
+
 struct richm_solver {
   richm_operator* op = nullptr;
   richm_solve_opts o{};
@@ -61,8 +66,8 @@ struct richm_solver {
   int graph_cycles = 1;      // cycles captured in one graph replay
   long long cycles_run = 0;  // cycles since start
   int* h_count = nullptr;    // pinned: [0] active count, [1 .. batch] per-instance active flags
-  int* h_stage = nullptr;    // pinned: two more such records for readbacks still in flight
-  cudaEvent_t ev_read[2] = {nullptr, nullptr};
+  int* h_stage = nullptr;    // pinned: kSolveReadDepth more such records for readbacks in flight
+  cudaEvent_t ev_read[kSolveReadDepth] = {};
   int rows_now = 256;        // fused tile height used by the next cycles
   int rows_max = 256;        // the operator's tuned tile height
   bool started = false;
@@ -626,9 +631,9 @@ richm_status richm_solver_create(richm_operator* op, const richm_solve_opts* o, 
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&S->h_count, sizeof(int) * (op->batch + 1), cudaHostAllocDefault);
   if (e == cudaSuccess)
-    e = cudaHostAlloc((void**)&S->h_stage, sizeof(int) * 2 * (op->batch + 1), cudaHostAllocDefault);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_read[0], cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_read[1], cudaEventDisableTiming);
+    e = cudaHostAlloc((void**)&S->h_stage, sizeof(int) * kSolveReadDepth * (op->batch + 1), cudaHostAllocDefault);
+  for (int i = 0; i < kSolveReadDepth && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&S->ev_read[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     richm_solver_destroy(S);
     return set_error(RICHM_ERR_CUDA, "solver setup failed: %s", cudaGetErrorString(e));
@@ -777,10 +782,11 @@ static richm_status enqueue_readback(richm_solver* S, int* rec) {
 }
 
 // The loop of richm_solve: cycles until no instance is active or max_cycles ran. The
-// readback of a cycle's active count is not waited for before the next cycle is
-// queued, so the GPU does not idle on the host round trip; the tile height and the
-// stopping decision use the count of the cycle before (one cycle may run with every
-// instance already converged; its kernels skip inactive instances).
+// readback of a cycle's active count is not waited for until kSolveReadDepth - 1 more
+// cycles are queued behind it, so the GPU does not idle on the host round trip or on a
+// late host thread; the tile height and the stopping decision use that older count (up
+// to kSolveReadDepth - 1 cycles may run with every instance already converged; their
+// kernels skip inactive instances).
 static richm_status run_to_completion(richm_solver* S, long long max_cycles, cudaStream_t stream) {
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_in, stream));
   RICHM_CUDA_TRY(cudaStreamWaitEvent(S->s, S->ev_in, 0));
@@ -789,21 +795,22 @@ static richm_status run_to_completion(richm_solver* S, long long max_cycles, cud
   int active = *S->h_count;
   if (S->o.fuse > 1 && active > 0) S->rows_now = choose_rows(S);
   const size_t rec = (size_t)S->op->batch + 1;
-  long long c = 0;
-  int pending = -1;  // slot of the readback in flight
+  long long c = 0, issued = 0, consumed = 0;  // cycles queued; readbacks queued and read
   while (active > 0 && c < max_cycles) {
     RICHM_TRY(launch_cycles(S, S->graph_cycles));
     c += S->graph_cycles;
-    if (pending >= 0) {
-      RICHM_CUDA_TRY(cudaEventSynchronize(S->ev_read[pending]));
-      memcpy(S->h_count, S->h_stage + pending * rec, sizeof(int) * rec);
+    const int slot = (int)(issued % kSolveReadDepth);
+    RICHM_TRY(enqueue_readback(S, S->h_stage + slot * rec));
+    RICHM_CUDA_TRY(cudaEventRecord(S->ev_read[slot], S->s));
+    ++issued;
+    if (issued - consumed == kSolveReadDepth) {  // every slot in flight: read the oldest
+      const int old = (int)(consumed % kSolveReadDepth);
+      RICHM_CUDA_TRY(cudaEventSynchronize(S->ev_read[old]));
+      memcpy(S->h_count, S->h_stage + old * rec, sizeof(int) * rec);
+      ++consumed;
       active = *S->h_count;
       if (S->o.fuse > 1 && active > 0) S->rows_now = choose_rows(S);
     }
-    const int slot = pending < 0 ? 0 : 1 - pending;
-    RICHM_TRY(enqueue_readback(S, S->h_stage + slot * rec));
-    RICHM_CUDA_TRY(cudaEventRecord(S->ev_read[slot], S->s));
-    pending = slot;
   }
   RICHM_CUDA_TRY(cudaStreamSynchronize(S->s));
   RICHM_CUDA_TRY(cudaEventRecord(S->ev_out, S->s));
