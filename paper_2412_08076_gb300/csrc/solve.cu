@@ -131,26 +131,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
-// hi = the binary64 value d rounded to binary32 (as f64_to_f32_rn) and lo = d - hi to
-// binary32 precision, from the fields of d: the remainder is the 29 dropped fraction
-// bits (less one unit of the kept fraction when hi was rounded up), converted and
-// scaled by d's exponent. Outside the range where that scale is a normal binary32
-// (|d| < 2^-74 or hi not finite) lo is 0.
-__device__ __forceinline__ float f64_split_f32(double d, float& lo) {
-  const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
-  const unsigned ex = (hw >> 20) & 0x7ffu;
-  const float hi = f64_to_f32_rn(d);
-  lo = 0.f;
-  if (ex - 949u < 254u && ex - 897u < 254u) {
-    const int rest = (int)(lw & 0x1fffffffu);
-    const int up = (rest > 0x10000000 || (rest == 0x10000000 && ((lw >> 29) & 1u))) ? 1 : 0;
-    const float scale = __uint_as_float((ex - 948u) << 23);  // 2^(exponent of d - 52)
-    const float mag = (float)(rest - (up << 29)) * scale;
-    lo = (hw & 0x80000000u) ? -mag : mag;
-  }
-  return hi;
-}
-
 // (s_hi, s_lo) += (hi + lo)^2 with the square of hi exact as a pair (FMA remainder),
 // the cross term 2 hi lo added to the remainder, lo^2 dropped (below 2^-46 of the
 // square), and the sum kept as an unevaluated pair (two-sum).
@@ -164,14 +144,45 @@ __device__ __forceinline__ void sq_acc(float hi, float lo, float& s_hi, float& s
   s_lo += err + q;
 }
 
+// Exponent bounds: the smallest E with |v| < 2^E for a finite nonzero v (infinite and
+// NaN inputs give a bound above every range used here), -4096 for zero and subnormals.
+__device__ __forceinline__ int ebound_f64(double v) {
+  const unsigned ex = ((unsigned)__double2hiint(v) >> 20) & 0x7ffu;
+  return ex == 0u ? -4096 : (int)ex - 1022;
+}
+__device__ __forceinline__ int ebound_f32(float v) {
+  const unsigned ex = (__float_as_uint(v) >> 23) & 0xffu;
+  return ex == 0u ? -4096 : (int)ex - 126;
+}
+__device__ __forceinline__ int ebound_e(float v) { return ebound_f32(v); }
+__device__ __forceinline__ int ebound_e(__nv_bfloat16 v) { return ebound_f32(__bfloat162float(v)); }
+
+// trunc(v 2^s) as a 64-bit integer, from the fields of v (subnormal v gives 0); the
+// caller guarantees |v| 2^s < 2^63.
+__device__ __forceinline__ long long fixed_from_f64(double v, int s) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((u >> 52) & 0x7ffull);
+  if (ex == 0) return 0;
+  const unsigned long long m = (u & 0xfffffffffffffull) | 0x10000000000000ull;
+  const int sh = ex - 1075 + s;  // |v| 2^s = m 2^sh
+  const unsigned long long q = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+  return (u >> 63) ? -(long long)q : (long long)q;
+}
+
 // Refinement after a fused cycle: for the tile's rows, x_out = x_in + e (FP64; e is
-// the cycle's final correction, read here and left in place) and
-// rhs = b - A (x_in + e) in FP64 (b folded into the multiply-adds, the sum formed on
-// the fly for the halo rows too), with the tile's partial sum (|r|^2, 0). GB300's FP64
-// pipe bounds this kernel (its cost is per active lane), so |r|^2 is summed on the FP32
-// pipe: r split into its binary32 rounding and remainder, each square exact as a pair,
-// the lane's sum a two-sum pair (relative error ~2^-43 over a tile's 32 terms), and
-// only the lanes' sums widened to FP64.
+// the cycle's final correction, read here and left in place), rhs = b - A (x_in + e)
+// rounded to FP32, and the tile's partial sum (|r|^2, 0). GB300 runs FP64 arithmetic at
+// 1/64 of its FP32 rate (charged per active lane), which bound the FP64 form of this
+// kernel, so the residual is formed in 64-bit fixed point on the integer pipes instead:
+// one power-of-two scale per tile from the exponents of x, e, b and the stencil, the
+// neighbour pairs summed exactly, the top 64 bits of each coefficient product, b at the
+// same unit. That stays within a few units of 2^-57 of the tile's largest product,
+// below the FP64 evaluation's rounding of the same sum; tiles whose scale falls outside
+// the range the conversions allow (all-zero, extreme or non-finite values) take the
+// FP64 form. On the fixed-point path |r|^2 is summed on the FP32 pipe: each residual
+// as its binary32 rounding and remainder at the tile's scale, each square exact as a
+// pair, the lane's sum a two-sum pair (relative error ~2^-43 over a tile's 32 terms),
+// only the lanes' sums widened to FP64 and scaled back.
 template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     refine_fused_kernel(const Inst* insts, const Tile* tiles, int ntiles, const double* __restrict__ x_in,
@@ -190,7 +201,44 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int r1 = min(r0 + kRows - 1, n);
   const double* xb = x_in + I.off;
   const T* eb = e + I.off;
-  auto load = [&](int pr, RowT<double, 2>& Y) {
+  const bool has_l = lane == 0 && c0 > 0, has_r = lane == 31 && c0 + 2 < pitch;
+  const int hc = lane == 0 ? c0 - 1 : c0 + 2;
+
+  // The tile's scale: bounds of |x|, |e| over its rows with the halo and of |b| over its
+  // output rows, and of the stencil's coefficients.
+  int ey = -4096, ebb = -4096;
+  for (int pr = max(r0 - 1, 1); pr <= min(r1 + 1, n); ++pr) {
+    const long long ro = (long long)pr * pitch;
+    if (live) {
+      const double2 xv = *reinterpret_cast<const double2*>(xb + ro + c0);
+      const VecN<T, 2> ev = *reinterpret_cast<const VecN<T, 2>*>(eb + ro + c0);
+      ey = max(ey, max(max(ebound_f64(xv.x), ebound_f64(xv.y)), max(ebound_e(ev.v[0]), ebound_e(ev.v[1]))));
+      if (pr >= r0 && pr <= r1) {
+        const double2 bv = *reinterpret_cast<const double2*>(b + I.off + ro + c0);
+        ebb = max(ebb, max(ebound_f64(bv.x), ebound_f64(bv.y)));
+      }
+    }
+    if (has_l || has_r) ey = max(ey, max(ebound_f64(xb[ro + hc]), ebound_e(eb[ro + hc])));
+  }
+  ey = __reduce_max_sync(0xffffffffu, ey);
+  ebb = __reduce_max_sync(0xffffffffu, ebb);
+  const int ea = max(max(ebound_f64(I.c), ebound_f64(I.ax)),
+                     max(ebound_f64(I.ay), max(ebound_f64(I.d1), ebound_f64(I.d2))));
+  // |x + e| < 2^(ey + 1); b enters at no more than 2^(ea + eyp + 4)
+  const int eyp = max(ey + 1, ebb - ea - 4);
+  const int k = ea + eyp - 57;  // the residual's unit is 2^k
+  const bool fixed = k >= -120 && k <= 60;
+
+  // the right-hand side and x + e of an output row
+  auto emit = [&](int r, float r0v, float r1v, double x0, double x1) {
+    if (live) {
+      const long long o = I.off + (long long)r * pitch + c0;
+      *reinterpret_cast<float2*>(rhs + o) = make_float2(c0 < n ? r0v : 0.f, c0 + 1 < n ? r1v : 0.f);
+      *reinterpret_cast<double2*>(x_out + o) = make_double2(x0, x1);
+    }
+  };
+  // x + e of a row (FP64) and of the edge lanes' outer neighbours
+  auto row_sum = [&](int pr, double* y, double& h) {
     const bool in = (pr >= 1) && (pr <= n);
     const long long ro = (long long)pr * pitch;
     double2 xv = make_double2(0.0, 0.0);
@@ -200,43 +248,94 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       xv = *reinterpret_cast<const double2*>(xb + ro + c0);
       ev = *reinterpret_cast<const VecN<T, 2>*>(eb + ro + c0);
     }
-    Y.y[0] = xv.x + to_d(ev.v[0]);
-    Y.y[1] = xv.y + to_d(ev.v[1]);
-    double le = 0.0, re = 0.0;
-    if (in) {
-      if (lane == 0 && c0 > 0) le = xb[ro + c0 - 1] + to_d(eb[ro + c0 - 1]);
-      if (lane == 31 && c0 + 2 < pitch) re = xb[ro + c0 + 2] + to_d(eb[ro + c0 + 2]);
-    }
-    row_neighbours<double, 2>(Y, lane, le, re);
+    y[0] = xv.x + to_d(ev.v[0]);
+    y[1] = xv.y + to_d(ev.v[1]);
+    h = 0.0;
+    if (in && has_l) h = xb[ro + hc] + to_d(eb[ro + hc]);
+    if (in && has_r) h = xb[ro + hc] + to_d(eb[ro + hc]);
   };
-  float s_hi = 0.f, s_lo = 0.f;  // the lane's |r|^2 as an unevaluated FP32 pair
-  RowT<double, 2> U, C, D;
-  load(r0 - 1, U);
-  load(r0, C);
-  for (int r = r0; r <= r1; ++r) {
-    load(r + 1, D);
-    const long long o = I.off + (long long)r * pitch + c0;
-    double2 bv = make_double2(0.0, 0.0);
-    if (live) bv = *reinterpret_cast<const double2*>(b + o);
-    const double bb[2] = {bv.x, bv.y};
-    double rv[2];
-    resid_q1<2>(U, C, D, bb, I.c, I.ax, I.ay, I.d1, I.d2, rv);
-    float2 out, lo;
-    const bool ok0 = c0 < n, ok1 = c0 + 1 < n;
-    out.x = ok0 ? f64_split_f32(rv[0], lo.x) : 0.f;
-    out.y = ok1 ? f64_split_f32(rv[1], lo.y) : 0.f;
-    if (!ok0) lo.x = 0.f;
-    if (!ok1) lo.y = 0.f;
-    sq_acc(out.x, lo.x, s_hi, s_lo);
-    sq_acc(out.y, lo.y, s_hi, s_lo);
-    if (live) {
-      *reinterpret_cast<float2*>(rhs + o) = out;
-      *reinterpret_cast<double2*>(x_out + o) = make_double2(C.y[0], C.y[1]);
+
+  double sr;  // the lane's |r|^2
+  if (fixed) {
+    // r = b - A (x + e) in 64-bit fixed point: x + e at unit 2^(eyp - 59) (|Y| <= 2^59),
+    // the coefficients at 2^(ea - 62) (|A| < 2^62), neighbour pairs summed exactly, each
+    // product's top 64 bits (unit 2^k), b at 2^k; |acc| < 2^62. The error per point is
+    // a few units of 2^k, below the FP64 evaluation's rounding of the same sum. |r|^2
+    // is summed as (acc 2^-40)^2 (every square a normal binary32) and scaled back.
+    const long long Ac = fixed_from_f64(I.c, 62 - ea), Aax = fixed_from_f64(I.ax, 62 - ea),
+                    Aay = fixed_from_f64(I.ay, 62 - ea), Ad1 = fixed_from_f64(I.d1, 62 - ea),
+                    Ad2 = fixed_from_f64(I.d2, 62 - ea);
+    const int sy = 59 - eyp, sb = 57 - ea - eyp;
+    const float scale = __uint_as_float((unsigned)(k + 127) << 23);  // 2^k
+    const float down = 0x1p-40f;
+    auto load = [&](int pr, RowT<long long, 2>& Y, double* xn) {
+      double h;
+      row_sum(pr, xn, h);
+      Y.y[0] = fixed_from_f64(xn[0], sy);
+      Y.y[1] = fixed_from_f64(xn[1], sy);
+      const long long hf = fixed_from_f64(h, sy);
+      row_neighbours<long long, 2>(Y, lane, hf, hf);
+    };
+    float s_hi = 0.f, s_lo = 0.f;  // the lane's sum of (acc 2^-40)^2 as an unevaluated pair
+    RowT<long long, 2> U, C, D;
+    double xu[2], xc[2], xd[2];
+    load(r0 - 1, U, xu);
+    load(r0, C, xc);
+    for (int r = r0; r <= r1; ++r) {
+      load(r + 1, D, xd);
+      double2 bv = make_double2(0.0, 0.0);
+      if (live) bv = *reinterpret_cast<const double2*>(b + I.off + (long long)r * pitch + c0);
+      const double bb[2] = {bv.x, bv.y};
+      float out[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const long long cw = q == 0 ? C.yl : C.y[0], ce = q == 1 ? C.yr : C.y[1];
+        const long long uw = q == 0 ? U.yl : U.y[0], ue = q == 1 ? U.yr : U.y[1];
+        const long long dw = q == 0 ? D.yl : D.y[0], de = q == 1 ? D.yr : D.y[1];
+        long long acc = fixed_from_f64(bb[q], sb);
+        acc -= __mul64hi(Ac, C.y[q]);
+        acc -= __mul64hi(Aax, cw + ce);
+        acc -= __mul64hi(Aay, U.y[q] + D.y[q]);
+        acc -= __mul64hi(Ad1, de + uw);
+        acc -= __mul64hi(Ad2, ue + dw);
+        const float hf = __ll2float_rn(acc);                       // RN(acc), integer valued
+        const float lf = __ll2float_rn(acc - __float2ll_rn(hf));  // the remainder
+        out[q] = hf * scale;
+        if (c0 + q < n) sq_acc(hf * down, lf * down, s_hi, s_lo);
+      }
+      emit(r, out[0], out[1], xc[0], xc[1]);
+      U = C;
+      C = D;
+      xc[0] = xd[0];
+      xc[1] = xd[1];
     }
-    U = C;
-    C = D;
+    // (s_hi + s_lo) 2^(2k + 80) in FP64, the power of two exact
+    sr = (f32_to_f64_exact(s_hi) + f32_to_f64_exact(s_lo)) * __hiloint2double((2 * k + 80 + 1023) << 20, 0);
+  } else {
+    // outside that range (all-zero tiles, extreme or non-finite values): FP64 arithmetic
+    auto load = [&](int pr, RowT<double, 2>& Y) {
+      double h;
+      row_sum(pr, Y.y, h);
+      row_neighbours<double, 2>(Y, lane, h, h);
+    };
+    sr = 0.0;
+    RowT<double, 2> U, C, D;
+    load(r0 - 1, U);
+    load(r0, C);
+    for (int r = r0; r <= r1; ++r) {
+      load(r + 1, D);
+      double2 bv = make_double2(0.0, 0.0);
+      if (live) bv = *reinterpret_cast<const double2*>(b + I.off + (long long)r * pitch + c0);
+      const double bb[2] = {bv.x, bv.y};
+      double rv[2];
+      resid_q1<2>(U, C, D, bb, I.c, I.ax, I.ay, I.d1, I.d2, rv);
+      if (c0 < n) sr = fma(rv[0], rv[0], sr);
+      if (c0 + 1 < n) sr = fma(rv[1], rv[1], sr);
+      emit(r, f64_to_f32_rn(rv[0]), f64_to_f32_rn(rv[1]), C.y[0], C.y[1]);
+      U = C;
+      C = D;
+    }
   }
-  double sr = f32_to_f64_exact(s_hi) + f32_to_f64_exact(s_lo);
   sr = warp_sum(sr);
   if (lane == 0) partials[wt] = make_double2(sr, 0.0);
 }

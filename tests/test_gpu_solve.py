@@ -139,6 +139,40 @@ def test_fused_refinement_norm_over_a_wide_range():
             assert abs(info[i][1] - r) <= 1e-12 * r + 1e-15, (t, info[i][1], r)
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e-28, 1e33])
+def test_fused_refinement_right_hand_side_matches_the_oracle(scale):
+    # the refinement after fused cycles forms r = b - A x in 64-bit fixed point per tile
+    # (scale 1), or in FP64 where the tile's values fall outside that form's range
+    # (1e-28, 1e33); either way its FP32 right-hand side is the oracle's FP64 residual of
+    # the x it wrote, rounded to FP32: within one unit in the last place plus a few FP64
+    # units of |b| + |A||x| (the oracle's own rounding where the sum cancels)
+    insts, op, As, w, a, bs = _solve_setup([33, 64, 130])
+    bs = [v * scale for v in bs]
+    B = to_dev(op, bs, richm.F64)
+    X = op.zeros(richm.F64)
+    opts = op.solve_opts(16, tol=0.0, max_sweeps=10 ** 6, refine_every=64, inner=richm.F32, fuse=8)
+    S = richm.Solver(op, opts, coef(w, richm.F32), coef(a, richm.F32))
+    S.start(B, X)
+    for cycles in (1, 2):
+        S.step(1)
+        _, rhs, _ = S.views()
+        rhs = from_dev(op, rhs.clone(), richm.F32)
+        st, info = S.finish()
+        xs = from_dev(op, X, richm.F64)
+        for i, t in enumerate(insts):
+            x = xs[i].ravel()
+            r = bs[i].ravel() - As[i] @ x
+            mag = np.abs(bs[i].ravel()) + abs(As[i]) @ np.abs(x)
+            got = rhs[i].ravel().astype(np.float64)
+            tol = np.spacing(np.abs(r).astype(np.float32)).astype(np.float64) + 2.0 ** -50 * mag
+            bad = np.abs(got - r) > tol
+            assert not bad.any(), (t, cycles, got[bad][:4], r[bad][:4])
+            assert info[i][0] == 64 * cycles
+            rel = np.linalg.norm(r) / np.linalg.norm(bs[i])
+            assert abs(info[i][1] - rel) <= 1e-12 * rel, (t, info[i][1], rel)
+    S.close()
+
+
 def test_integer_field_conversions_match_hardware():
     assert richm.selftest_conversions() == (0, 0)
 
