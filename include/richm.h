@@ -295,8 +295,9 @@ typedef struct {
 
 typedef struct {
   long long sweeps;  /* sweeps applied to this instance */
-  double rel_res;    /* final relative residual ||b - A x|| / ||b||: r = b - A x in FP64; with fused
-                        FP32 cycles |r|^2 is summed as FP32 pairs (relative error below 1e-12) */
+  double rel_res;    /* final relative residual ||b - A x|| / ||b||: r = b - A x in FP64, or, after
+                        fused FP32 cycles, in 64-bit fixed point per tile (error below FP64
+                        evaluation's) with |r|^2 summed as FP32 pairs (relative error below 1e-12) */
   int status;        /* RICHM_OK, RICHM_ERR_NOT_CONVERGED or RICHM_ERR_DIVERGED */
 } richm_solve_info;
 

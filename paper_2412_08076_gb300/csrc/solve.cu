@@ -144,18 +144,12 @@ __device__ __forceinline__ void sq_acc(float hi, float lo, float& s_hi, float& s
   s_lo += err + q;
 }
 
-// Exponent bounds: the smallest E with |v| < 2^E for a finite nonzero v (infinite and
+// Exponent bound: the smallest E with |v| < 2^E for a finite nonzero v (infinite and
 // NaN inputs give a bound above every range used here), -4096 for zero and subnormals.
 __device__ __forceinline__ int ebound_f64(double v) {
   const unsigned ex = ((unsigned)__double2hiint(v) >> 20) & 0x7ffu;
   return ex == 0u ? -4096 : (int)ex - 1022;
 }
-__device__ __forceinline__ int ebound_f32(float v) {
-  const unsigned ex = (__float_as_uint(v) >> 23) & 0xffu;
-  return ex == 0u ? -4096 : (int)ex - 126;
-}
-__device__ __forceinline__ int ebound_e(float v) { return ebound_f32(v); }
-__device__ __forceinline__ int ebound_e(__nv_bfloat16 v) { return ebound_f32(__bfloat162float(v)); }
 
 // trunc(v 2^s) as a 64-bit integer, from the fields of v (subnormal v gives 0); the
 // caller guarantees |v| 2^s < 2^63.
@@ -169,11 +163,32 @@ __device__ __forceinline__ long long fixed_from_f64(double v, int s) {
   return (u >> 63) ? -(long long)q : (long long)q;
 }
 
+// acc (|acc| < 2^62) as hi + lo, hi a faithful binary32 rounding of acc and lo the rest
+// to 2^-24 of itself, with FP32 additions only: acc = a2 2^46 + a1 2^23 + a0 with
+// 0 <= a1, a0 < 2^23, each chunk exact in binary32 through the 2^23 bias (its bits
+// placed in the significand of 2^23), the three summed by two-sums.
+__device__ __forceinline__ void fixed_to_pair(long long acc, float& hi, float& lo) {
+  const int a2 = (int)(acc >> 46);  // |a2| < 2^16
+  const unsigned a1 = (unsigned)(acc >> 23) & 0x7fffffu, a0 = (unsigned)acc & 0x7fffffu;
+  const float f2 = __uint_as_float(0x4b000000u | (unsigned)(a2 + 0x400000)) - 12582912.f;  // 2^23 + 2^22
+  const float f1 = __uint_as_float(0x4b000000u | a1) - 8388608.f;
+  const float f0 = __uint_as_float(0x4b000000u | a0) - 8388608.f;
+  const float p = f2 * 0x1p46f, q = f1 * 0x1p23f;
+  const float s = p + q;
+  const float sv = s - p;
+  const float e1 = (p - (s - sv)) + (q - sv);
+  hi = s + f0;
+  const float hv = hi - s;
+  const float e2 = (s - (hi - hv)) + (f0 - hv);
+  lo = e1 + e2;
+}
+
 // Refinement after a fused cycle: for the tile's rows, x_out = x_in + e (FP64; e is
 // the cycle's final correction, read here and left in place), rhs = b - A (x_in + e)
-// rounded to FP32, and the tile's partial sum (|r|^2, 0). GB300 runs FP64 arithmetic at
-// 1/64 of its FP32 rate (charged per active lane), which bound the FP64 form of this
-// kernel, so the residual is formed in 64-bit fixed point on the integer pipes instead:
+// rounded to FP32 (faithfully: within one unit in the last place), and the tile's
+// partial sum (|r|^2, 0). GB300 runs FP64 arithmetic at about 1/70 of its FP32 rate
+// (charged per active lane), which bound the FP64 form of this kernel, so the
+// residual is formed in 64-bit fixed point on the integer pipes instead:
 // one power-of-two scale per tile from the exponents of x, e, b and the stencil, the
 // neighbour pairs summed exactly, the top 64 bits of each coefficient product, b at the
 // same unit. That stays within a few units of 2^-57 of the tile's largest product,
@@ -206,22 +221,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 
   // The tile's scale: bounds of |x|, |e| over its rows with the halo and of |b| over its
   // output rows, and of the stencil's coefficients.
-  int ey = -4096, ebb = -4096;
+  // (maxima of the magnitudes' bit patterns: their exponent fields order them)
+  unsigned mx = 0u, me = 0u, mb = 0u;
+  auto mag64 = [](double v) { return (unsigned)__double2hiint(v) & 0x7fffffffu; };
+  auto mag_e = [](T v) { return __float_as_uint(to_f(v)) & 0x7fffffffu; };
   for (int pr = max(r0 - 1, 1); pr <= min(r1 + 1, n); ++pr) {
     const long long ro = (long long)pr * pitch;
     if (live) {
       const double2 xv = *reinterpret_cast<const double2*>(xb + ro + c0);
       const VecN<T, 2> ev = *reinterpret_cast<const VecN<T, 2>*>(eb + ro + c0);
-      ey = max(ey, max(max(ebound_f64(xv.x), ebound_f64(xv.y)), max(ebound_e(ev.v[0]), ebound_e(ev.v[1]))));
+      mx = max(mx, max(mag64(xv.x), mag64(xv.y)));
+      me = max(me, max(mag_e(ev.v[0]), mag_e(ev.v[1])));
       if (pr >= r0 && pr <= r1) {
         const double2 bv = *reinterpret_cast<const double2*>(b + I.off + ro + c0);
-        ebb = max(ebb, max(ebound_f64(bv.x), ebound_f64(bv.y)));
+        mb = max(mb, max(mag64(bv.x), mag64(bv.y)));
       }
     }
-    if (has_l || has_r) ey = max(ey, max(ebound_f64(xb[ro + hc]), ebound_e(eb[ro + hc])));
+    if (has_l || has_r) {
+      mx = max(mx, mag64(xb[ro + hc]));
+      me = max(me, mag_e(eb[ro + hc]));
+    }
   }
-  ey = __reduce_max_sync(0xffffffffu, ey);
-  ebb = __reduce_max_sync(0xffffffffu, ebb);
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  me = __reduce_max_sync(0xffffffffu, me);
+  mb = __reduce_max_sync(0xffffffffu, mb);
+  const int ey = max(mx >> 20 ? (int)(mx >> 20) - 1022 : -4096, me >> 23 ? (int)(me >> 23) - 126 : -4096);
+  const int ebb = mb >> 20 ? (int)(mb >> 20) - 1022 : -4096;
   const int ea = max(max(ebound_f64(I.c), ebound_f64(I.ax)),
                      max(ebound_f64(I.ay), max(ebound_f64(I.d1), ebound_f64(I.d2))));
   // |x + e| < 2^(ey + 1); b enters at no more than 2^(ea + eyp + 4)
@@ -298,8 +323,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         acc -= __mul64hi(Aay, U.y[q] + D.y[q]);
         acc -= __mul64hi(Ad1, de + uw);
         acc -= __mul64hi(Ad2, ue + dw);
-        const float hf = __ll2float_rn(acc);                       // RN(acc), integer valued
-        const float lf = __ll2float_rn(acc - __float2ll_rn(hf));  // the remainder
+        float hf, lf;
+        fixed_to_pair(acc, hf, lf);
         out[q] = hf * scale;
         if (c0 + q < n) sq_acc(hf * down, lf * down, s_hi, s_lo);
       }
