@@ -198,8 +198,10 @@ __device__ __forceinline__ void fixed_to_pair(long long acc, float& hi, float& l
 // as its binary32 rounding and remainder at the tile's scale, each square exact as a
 // pair, the lane's sum a two-sum pair (relative error ~2^-43 over a tile's 32 terms),
 // only the lanes' sums widened to FP64 and scaled back.
+// (three blocks per SM: the one-row prefetch below costs a few spilled registers,
+// which measured faster than two blocks per SM without spills)
 template <typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3)
     refine_fused_kernel(const Inst* insts, const Tile* tiles, int ntiles, const double* __restrict__ x_in,
                         const T* __restrict__ e, const double* __restrict__ b, float* __restrict__ rhs,
                         double* __restrict__ x_out, double2* __restrict__ partials, const int* __restrict__ active) {
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   unsigned mx = 0u, me = 0u, mb = 0u;
   auto mag64 = [](double v) { return (unsigned)__double2hiint(v) & 0x7fffffffu; };
   auto mag_e = [](T v) { return __float_as_uint(to_f(v)) & 0x7fffffffu; };
+#pragma unroll 6
   for (int pr = max(r0 - 1, 1); pr <= min(r1 + 1, n); ++pr) {
     const long long ro = (long long)pr * pitch;
     if (live) {
@@ -293,9 +296,39 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int sy = 59 - eyp, sb = 57 - ea - eyp;
     const float scale = __uint_as_float((unsigned)(k + 127) << 23);  // 2^k
     const float down = 0x1p-40f;
-    auto load = [&](int pr, RowT<long long, 2>& Y, double* xn) {
-      double h;
-      row_sum(pr, xn, h);
+    // a row's raw inputs, fetched one row step before they are used
+    struct Raw {
+      double2 x;
+      VecN<T, 2> e;
+      double hx;
+      T he;
+    };
+    auto fetch = [&](int pr, Raw& w) {
+      const bool in = (pr >= 1) && (pr <= n);
+      const long long ro = (long long)pr * pitch;
+      w.x = make_double2(0.0, 0.0);
+      w.e.v[0] = w.e.v[1] = from_f<T>(0.f);
+      w.hx = 0.0;
+      w.he = from_f<T>(0.f);
+      if (in && live) {
+        w.x = *reinterpret_cast<const double2*>(xb + ro + c0);
+        w.e = *reinterpret_cast<const VecN<T, 2>*>(eb + ro + c0);
+      }
+      if (in && (has_l || has_r)) {
+        w.hx = xb[ro + hc];
+        w.he = eb[ro + hc];
+      }
+    };
+    auto fetch_b = [&](int r) {
+      double2 bv = make_double2(0.0, 0.0);
+      if (live && r <= r1) bv = *reinterpret_cast<const double2*>(b + I.off + (long long)r * pitch + c0);
+      return bv;
+    };
+    // x + e (FP64) of a fetched row and its fixed-point form with the edge neighbours
+    auto convert = [&](const Raw& w, RowT<long long, 2>& Y, double* xn) {
+      xn[0] = w.x.x + to_d(w.e.v[0]);
+      xn[1] = w.x.y + to_d(w.e.v[1]);
+      const double h = w.hx + to_d(w.he);
       Y.y[0] = fixed_from_f64(xn[0], sy);
       Y.y[1] = fixed_from_f64(xn[1], sy);
       const long long hf = fixed_from_f64(h, sy);
@@ -304,13 +337,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     float s_hi = 0.f, s_lo = 0.f;  // the lane's sum of (acc 2^-40)^2 as an unevaluated pair
     RowT<long long, 2> U, C, D;
     double xu[2], xc[2], xd[2];
-    load(r0 - 1, U, xu);
-    load(r0, C, xc);
+    Raw w;
+    fetch(r0 - 1, w);
+    convert(w, U, xu);
+    fetch(r0, w);
+    convert(w, C, xc);
+    fetch(r0 + 1, w);
+    double2 bv = fetch_b(r0);
     for (int r = r0; r <= r1; ++r) {
-      load(r + 1, D, xd);
-      double2 bv = make_double2(0.0, 0.0);
-      if (live) bv = *reinterpret_cast<const double2*>(b + I.off + (long long)r * pitch + c0);
-      const double bb[2] = {bv.x, bv.y};
+      const Raw cur = w;
+      const double2 bcur = bv;
+      if (r < r1) {
+        fetch(r + 2, w);
+        bv = fetch_b(r + 1);
+      }
+      convert(cur, D, xd);
+      const double bb[2] = {bcur.x, bcur.y};
       float out[2];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
