@@ -163,30 +163,32 @@ __device__ __forceinline__ long long fixed_from_f64(double v, int s) {
   return (u >> 63) ? -(long long)q : (long long)q;
 }
 
-// acc (|acc| < 2^62) as hi + lo, hi a faithful binary32 rounding of acc and lo the rest
-// to 2^-24 of itself, with FP32 additions only: acc = a2 2^46 + a1 2^23 + a0 with
-// 0 <= a1, a0 < 2^23, each chunk exact in binary32 through the 2^23 bias (its bits
-// placed in the significand of 2^23), the three summed by two-sums.
+// acc (|acc| < 2^62) as hi + lo with hi = RN(acc) in binary32 and lo the remainder to
+// within 2^-45 of |hi|, from integer operations: |acc| normalised by its leading zeros,
+// the top 24 bits rounded to nearest (ties to even; a carry steps the exponent), the
+// next 23 bits of the signed remainder made exact in binary32 through the 2^23 bias.
 __device__ __forceinline__ void fixed_to_pair(long long acc, float& hi, float& lo) {
-  const int a2 = (int)(acc >> 46);  // |a2| < 2^16
-  const unsigned a1 = (unsigned)(acc >> 23) & 0x7fffffu, a0 = (unsigned)acc & 0x7fffffu;
-  const float f2 = __uint_as_float(0x4b000000u | (unsigned)(a2 + 0x400000)) - 12582912.f;  // 2^23 + 2^22
-  const float f1 = __uint_as_float(0x4b000000u | a1) - 8388608.f;
-  const float f0 = __uint_as_float(0x4b000000u | a0) - 8388608.f;
-  const float p = f2 * 0x1p46f, q = f1 * 0x1p23f;
-  const float s = p + q;
-  const float sv = s - p;
-  const float e1 = (p - (s - sv)) + (q - sv);
-  hi = s + f0;
-  const float hv = hi - s;
-  const float e2 = (s - (hi - hv)) + (f0 - hv);
-  lo = e1 + e2;
+  const unsigned long long ua = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+  if (ua == 0ull) {
+    hi = lo = 0.f;
+    return;
+  }
+  const int lz = __clzll((long long)ua);  // >= 2
+  const unsigned long long m = ua << lz;  // leading one at bit 63
+  const unsigned top = (unsigned)(m >> 40);
+  const unsigned long long rest = m & 0xffffffffffull;
+  const unsigned up = (rest > 0x8000000000ull || (rest == 0x8000000000ull && (top & 1u))) ? 1u : 0u;
+  const unsigned sign = acc < 0 ? 0x80000000u : 0u;
+  hi = __uint_as_float((((unsigned)(63 - lz + 127) << 23) + (top - 0x800000u) + up) | sign);
+  const int r23 = (int)(((long long)rest - (long long)((unsigned long long)up << 40)) >> 17);  // |r23| <= 2^22
+  const float fr = __uint_as_float(0x4b000000u | (unsigned)(r23 + 0x400000)) - 12582912.f;  // 2^23 + 2^22
+  const float l = fr * __uint_as_float((unsigned)(17 - lz + 127) << 23);                     // 2^(17 - lz)
+  lo = sign ? -l : l;
 }
 
 // Refinement after a fused cycle: for the tile's rows, x_out = x_in + e (FP64; e is
 // the cycle's final correction, read here and left in place), rhs = b - A (x_in + e)
-// rounded to FP32 (faithfully: within one unit in the last place), and the tile's
-// partial sum (|r|^2, 0). GB300 runs FP64 arithmetic at about 1/70 of its FP32 rate
+// rounded to FP32, and the tile's partial sum (|r|^2, 0). GB300 runs FP64 arithmetic at about 1/70 of its FP32 rate
 // (charged per active lane), which bound the FP64 form of this kernel, so the
 // residual is formed in 64-bit fixed point on the integer pipes instead:
 // one power-of-two scale per tile from the exponents of x, e, b and the stencil, the
