@@ -309,11 +309,22 @@ class Operator:
         _check(lib.richm_buffer_elems(h, C.byref(el)), "richm_buffer_elems")
         self.elems = el.value
         self.layouts = [self.layout(i) for i in range(self.batch)]
+        self._solve_ws = None  # workspace of solve / solve_host calls that pass none
+
+    def _solve_workspace(self, nbytes: int) -> torch.Tensor:
+        """A workspace kept for solve / solve_host calls without one (both synchronise
+        before they return): the library keeps a one-call solve's session, graphs
+        included, for the next call with the same workspace pointer."""
+        if self._solve_ws is None or self._solve_ws.numel() < nbytes:
+            self._solve_ws = None
+            self._solve_ws = self.workspace(nbytes)
+        return self._solve_ws
 
     def close(self):
         if getattr(self, "handle", None):
             load().richm_operator_destroy(self.handle)
             self.handle = None
+        self._solve_ws = None
 
     def __del__(self):
         try:
@@ -460,7 +471,7 @@ class Operator:
         need = C.c_size_t()
         _check(load().richm_solve_workspace(self.handle, C.byref(opts), C.byref(need)), "richm_solve_workspace")
         if work is None:
-            work = self.workspace(need.value)
+            work = self._solve_workspace(need.value)
         info = (richm_solve_info * self.batch)()
         st = load().richm_solve(self.handle, _ptr(b), _ptr(x), _ptr(w), _ptr(alpha), _ptr(alpha_t), C.byref(opts),
                                 info, _ptr(work), work.numel(), _stream(stream))
@@ -477,7 +488,7 @@ class Operator:
         _check(load().richm_solve_host_workspace(self.handle, C.byref(opts), C.byref(need)),
                "richm_solve_host_workspace")
         if work is None:
-            work = self.workspace(need.value)
+            work = self._solve_workspace(need.value)
         info = (richm_solve_info * self.batch)()
         st = load().richm_solve_host(self.handle, b_host.data_ptr(), x_host.data_ptr(), _ptr(w), _ptr(alpha),
                                      _ptr(alpha_t), C.byref(opts), info, _ptr(work), work.numel(), _stream(stream))
