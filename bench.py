@@ -937,6 +937,7 @@ def run_ours(args):
             "cpu_oracle_other_configs": other_cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(dense_b.numel() * 8),
                     "d2h_bytes_per_step": int(hx.numel() * 8), "seconds_per_call": e2e_s,
+                    "seconds_each": [round(r[0], 4) for r in e2e_runs],
                     "statuses": [r[2] for r in e2e_runs], "clocks": e2e_clk,
                     "note": "one step = the weight supply and one richm_solve_host call: pinned H2D of b, pack, "
                             "solve every instance to 1e-10 from x = 0 (FP32 sweeps + FP64 refinement), unpack, "
@@ -1116,7 +1117,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-tolerance solve")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--e2e-runs", type=int, default=2, help="timed richm_solve_host calls")
+    ap.add_argument("--e2e-runs", type=int, default=4, help="timed richm_solve_host calls")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile", choices=["sweep", "cycle", "adjoint", "helmholtz", "ssor", "bench_cycles", "fgmres",
                                           "adjoint_cx"], default=None,
