@@ -188,12 +188,12 @@ __device__ __forceinline__ void fixed_to_pair(long long acc, float& hi, float& l
 
 // Refinement after a fused cycle: for the tile's rows, x_out = x_in + e (FP64; e is
 // the cycle's final correction, read here and left in place), rhs = b - A (x_in + e)
-// rounded to FP32, and the tile's partial sum (|r|^2, 0). GB300 runs FP64 arithmetic at about 1/70 of its FP32 rate
-// (charged per active lane), which bound the FP64 form of this kernel, so the
-// residual is formed in 64-bit fixed point on the integer pipes instead:
-// one power-of-two scale per tile from the exponents of x, e, b and the stencil, the
-// neighbour pairs summed exactly, the top 64 bits of each coefficient product, b at the
-// same unit. That stays within a few units of 2^-57 of the tile's largest product,
+// rounded to FP32, and the tile's partial sum (|r|^2, 0). GB300 runs FP64 arithmetic
+// at about 1/70 of its FP32 rate (charged per active lane), which bound the FP64 form
+// of this kernel, so the residual is formed in 64-bit fixed point on the integer
+// pipes instead: one power-of-two scale per tile from the exponents of x, e, b and
+// the stencil, the neighbour pairs summed exactly, the top 64 bits of each
+// coefficient product, b at the same unit. That stays within a few units of 2^-57 of the tile's largest product,
 // below the FP64 evaluation's rounding of the same sum; tiles whose scale falls outside
 // the range the conversions allow (all-zero, extreme or non-finite values) take the
 // FP64 form. On the fixed-point path |r|^2 is summed on the FP32 pipe: each residual
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3)
   const int ebb = mb >> 20 ? (int)(mb >> 20) - 1022 : -4096;
   const int ea = max(max(ebound_f64(I.c), ebound_f64(I.ax)),
                      max(ebound_f64(I.ay), max(ebound_f64(I.d1), ebound_f64(I.d2))));
-  // |x + e| < 2^(ey + 1); b enters at no more than 2^(ea + eyp + 4)
+  // |x + e| <= 2^(ey + 1) (the FP64 sum may round up to it); |b| < 2^(ea + eyp + 4)
   const int eyp = max(ey + 1, ebb - ea - 4);
   const int k = ea + eyp - 57;  // the residual's unit is 2^k
   const bool fixed = k >= -120 && k <= 60;
