@@ -291,6 +291,9 @@ typedef struct {
   int fuse;              /* as in richm_sweep_opts */
   int use_graph;         /* 1: replay the refinement cycle as a CUDA graph */
   double relax;          /* as in richm_sweep_opts */
+  int fp64_residual;     /* fused FP32 / BF16 cycles: 0 (default) forms each refinement's r = b - A x in
+                            64-bit fixed point (error below the FP64 evaluation's, see rel_res), 1 in
+                            FP64 arithmetic (slower on GB300); other solves always use FP64 */
 } richm_solve_opts;
 
 typedef struct {

@@ -206,7 +206,8 @@ template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3)
     refine_fused_kernel(const Inst* insts, const Tile* tiles, int ntiles, const double* __restrict__ x_in,
                         const T* __restrict__ e, const double* __restrict__ b, float* __restrict__ rhs,
-                        double* __restrict__ x_out, double2* __restrict__ partials, const int* __restrict__ active) {
+                        double* __restrict__ x_out, double2* __restrict__ partials, const int* __restrict__ active,
+                        int fp64_residual) {
   const int lane = threadIdx.x & 31;
   const int wt = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (wt >= ntiles) return;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3)
   // |x + e| <= 2^(ey + 1) (the FP64 sum may round up to it); |b| < 2^(ea + eyp + 4)
   const int eyp = max(ey + 1, ebb - ea - 4);
   const int k = ea + eyp - 57;  // the residual's unit is 2^k
-  const bool fixed = k >= -120 && k <= 60;
+  const bool fixed = !fp64_residual && k >= -120 && k <= 60;
 
   // the right-hand side and x + e of an output row
   auto emit = [&](int r, float r0v, float r1v, double x0, double x1) {
@@ -543,7 +544,8 @@ static richm_status refine_t(richm_solver* S, bool init, int cur = 0, int prv = 
       double* xout = xpar ? S->x2 : S->x;
       refine_fused_kernel<T><<<blocks, kWarpsPerBlock * 32, 0, S->s>>>(op->d_inst, tm->d_tiles, tm->ntiles, xin,
                                                                         (const T*)S->E[cur], S->b, (float*)S->rhs,
-                                                                        xout, S->partials, S->active);
+                                                                        xout, S->partials, S->active,
+                                                                        S->o.fp64_residual);
       RICHM_LAUNCH_CHECK("fused refinement");
     }
   }
@@ -704,6 +706,7 @@ static richm_status check_solve_opts(const richm_operator* op, const richm_solve
   RICHM_ARG(o->inner == RICHM_F32 || o->inner == RICHM_F64 || o->inner == RICHM_BF16,
             "inner dtype must be RICHM_F32, RICHM_F64 or RICHM_BF16");
   RICHM_ARG(o->precond == 0 || o->precond == 1 || o->precond == 2, "precond must be 0, 1 or 2");
+  RICHM_ARG(o->fp64_residual == 0 || o->fp64_residual == 1, "fp64_residual must be 0 or 1");
   if (o->precond == 2) {
     RICHM_ARG(o->relax > 0.0 && o->relax < 2.0, "SSOR relaxation factor %g outside (0, 2)", o->relax);
     RICHM_ARG(o->fuse == 0 || o->fuse == 1, "SSOR sweeps run one per launch (fuse 0 or 1)");
@@ -1180,7 +1183,8 @@ struct SolverImageHeader {
   long long elems, cycles_run, max_sweeps, total_bytes;
   double tol;
   unsigned long long op_hash, weights_hash;
-  char pad[32];
+  int fp64_residual;
+  char pad[28];
 };
 static_assert(sizeof(SolverImageHeader) == 128, "image header layout");
 
@@ -1274,6 +1278,7 @@ richm_status richm_solver_save(richm_solver* S, void* host, size_t bytes, void* 
   h.m = S->o.m;
   h.refine_every = S->o.refine_every;
   h.precond = S->o.precond;
+  h.fp64_residual = S->o.fp64_residual;
   h.elems = S->op->elems;
   h.cycles_run = S->cycles_run;
   h.max_sweeps = S->o.max_sweeps;
@@ -1306,7 +1311,8 @@ richm_status richm_solver_resume(richm_solver* S, const double* b, double* x, co
   RICHM_ARG(h.batch == S->op->batch && h.elems == S->op->elems && h.op_hash == operator_hash(S->op),
             "the image was saved for other instances");
   RICHM_ARG(h.inner == S->o.inner && h.fuse == S->o.fuse && h.m == S->o.m && h.refine_every == S->o.refine_every &&
-                h.precond == S->o.precond && h.tol == S->o.tol && h.max_sweeps == S->o.max_sweeps,
+                h.precond == S->o.precond && h.tol == S->o.tol && h.max_sweeps == S->o.max_sweeps &&
+                h.fp64_residual == S->o.fp64_residual,
             "the image was saved with other solve options (inner %d, fuse %d, m %d, refine_every %d)", h.inner,
             h.fuse, h.m, h.refine_every);
   unsigned long long wh = 0;

@@ -51,7 +51,7 @@ class richm_sweep_opts(C.Structure):
 class richm_solve_opts(C.Structure):
     _fields_ = [("m", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_longlong), ("refine_every", C.c_int),
                 ("inner", C.c_int), ("precond", C.c_int), ("fuse", C.c_int), ("use_graph", C.c_int),
-                ("relax", C.c_double)]
+                ("relax", C.c_double), ("fp64_residual", C.c_int)]
 
 
 class richm_solve_info(C.Structure):
@@ -463,8 +463,9 @@ class Operator:
         return rel
 
     def solve_opts(self, m, tol=1e-10, max_sweeps=10**7, refine_every=64, inner=F32, precond=0, fuse=0, use_graph=1,
-                   relax=1.0):
-        return richm_solve_opts(m, tol, max_sweeps, refine_every, inner, precond, fuse, use_graph, relax)
+                   relax=1.0, fp64_residual=0):
+        return richm_solve_opts(m, tol, max_sweeps, refine_every, inner, precond, fuse, use_graph, relax,
+                                fp64_residual)
 
     def solve(self, b, x, w, alpha=None, alpha_t=None, opts=None, work=None, stream=None):
         """richm_solve; returns (status, list of (sweeps, rel_res, status))."""

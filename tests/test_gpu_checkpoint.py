@@ -124,6 +124,13 @@ def test_mismatched_images_are_refused():
     S3 = richm.Solver(op, opts3, W, A)
     with pytest.raises(richm.RichmError, match="options"):
         S3.resume(B, op.zeros(richm.F64), img)
+    # the other refinement residual form
+    opts3b = op.solve_opts(16, tol=1e-10, max_sweeps=10 ** 6, use_graph=1, refine_every=64, inner=richm.F32, fuse=8,
+                           fp64_residual=1)
+    S3b = richm.Solver(op, opts3b, W, A)
+    with pytest.raises(richm.RichmError, match="options"):
+        S3b.resume(B, op.zeros(richm.F64), img)
+    S3b.close()
     # other instances
     op4, W4, A4, B4, opts4 = _setup("fused", sizes=[17, 40, 63, 129])
     S4 = richm.Solver(op4, opts4, W4, A4)

@@ -139,18 +139,20 @@ def test_fused_refinement_norm_over_a_wide_range():
             assert abs(info[i][1] - r) <= 1e-12 * r + 1e-15, (t, info[i][1], r)
 
 
-@pytest.mark.parametrize("scale", [1.0, 1e-28, 1e33])
-def test_fused_refinement_right_hand_side_matches_the_oracle(scale):
+@pytest.mark.parametrize("scale,fp64", [(1.0, 0), (1e-28, 0), (1e33, 0), (1.0, 1)])
+def test_fused_refinement_right_hand_side_matches_the_oracle(scale, fp64):
     # the refinement after fused cycles forms r = b - A x in 64-bit fixed point per tile
     # (scale 1), or in FP64 where the tile's values fall outside that form's range
-    # (1e-28, 1e33); either way its FP32 right-hand side is the oracle's FP64 residual of
-    # the x it wrote, rounded to FP32: within one unit in the last place plus a few FP64
-    # units of |b| + |A||x| (the oracle's own rounding where the sum cancels)
+    # (1e-28, 1e33) or when the options ask for it (fp64_residual); either way its FP32
+    # right-hand side is the oracle's FP64 residual of the x it wrote, rounded to FP32:
+    # within one unit in the last place plus a few FP64 units of |b| + |A||x| (the
+    # oracle's own rounding where the sum cancels)
     insts, op, As, w, a, bs = _solve_setup([33, 64, 130])
     bs = [v * scale for v in bs]
     B = to_dev(op, bs, richm.F64)
     X = op.zeros(richm.F64)
-    opts = op.solve_opts(16, tol=0.0, max_sweeps=10 ** 6, refine_every=64, inner=richm.F32, fuse=8)
+    opts = op.solve_opts(16, tol=0.0, max_sweeps=10 ** 6, refine_every=64, inner=richm.F32, fuse=8,
+                         fp64_residual=fp64)
     S = richm.Solver(op, opts, coef(w, richm.F32), coef(a, richm.F32))
     S.start(B, X)
     for cycles in (1, 2):
@@ -171,6 +173,29 @@ def test_fused_refinement_right_hand_side_matches_the_oracle(scale):
             rel = np.linalg.norm(r) / np.linalg.norm(bs[i])
             assert abs(info[i][1] - rel) <= 1e-12 * rel, (t, info[i][1], rel)
     S.close()
+
+
+def test_solve_with_either_refinement_residual_reaches_1e10():
+    # the fixed-point and the FP64-arithmetic refinement residual both take every instance
+    # to 1e-10 (oracle-recomputed), and the options check refuses other values
+    insts, op, As, w, a, bs = _solve_setup([15, 63, 130, 255])
+    B = to_dev(op, bs, richm.F64)
+    res = []
+    for fp64 in (0, 1):
+        X = op.zeros(richm.F64)
+        opts = op.solve_opts(16, tol=1e-10, max_sweeps=400000, refine_every=64, inner=richm.F32, fuse=8,
+                             fp64_residual=fp64)
+        st, info = op.solve(B, X, coef(w, richm.F32), coef(a, richm.F32), None, opts)
+        assert st == richm.OK
+        xs = from_dev(op, X, richm.F64)
+        for i, t in enumerate(insts):
+            r = np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i])
+            assert r <= 1e-10 and abs(info[i][1] - r) <= 1e-12 * r + 1e-15, (fp64, t, r, info[i])
+        res.append([i_[0] for i_ in info])
+    print(f"\nsweeps to 1e-10, fixed-point / FP64 refinement residual: {res[0]} / {res[1]}")
+    with pytest.raises(richm.RichmError):
+        op.solve(B, op.zeros(richm.F64), coef(w, richm.F32), coef(a, richm.F32), None,
+                 op.solve_opts(16, fp64_residual=2))
 
 
 def test_integer_field_conversions_match_hardware():
