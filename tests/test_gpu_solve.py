@@ -190,7 +190,9 @@ def test_solve_with_either_refinement_residual_reaches_1e10():
         xs = from_dev(op, X, richm.F64)
         for i, t in enumerate(insts):
             r = np.linalg.norm(bs[i].ravel() - As[i] @ xs[i].ravel()) / np.linalg.norm(bs[i])
-            assert r <= 1e-10 and abs(info[i][1] - r) <= 1e-12 * r + 1e-15, (fp64, t, r, info[i])
+            # near 1e-10 the two FP64-level evaluations of |b - A x| / |b| differ by their
+            # rounding, a few 1e-16 of |A||x| / |b|
+            assert r <= 1e-10 and abs(info[i][1] - r) <= 1e-12 * r + 2e-14, (fp64, t, r, info[i])
         res.append([i_[0] for i_ in info])
     print(f"\nsweeps to 1e-10, fixed-point / FP64 refinement residual: {res[0]} / {res[1]}")
     with pytest.raises(richm.RichmError):
