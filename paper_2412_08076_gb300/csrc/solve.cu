@@ -230,8 +230,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3)
   unsigned mx = 0u, me = 0u, mb = 0u;
   auto mag64 = [](double v) { return (unsigned)__double2hiint(v) & 0x7fffffffu; };
   auto mag_e = [](T v) { return __float_as_uint(to_f(v)) & 0x7fffffffu; };
+  const int pre_hi = fp64_residual ? 0 : min(r1 + 1, n);  // no prepass for the FP64 form
 #pragma unroll 6
-  for (int pr = max(r0 - 1, 1); pr <= min(r1 + 1, n); ++pr) {
+  for (int pr = max(r0 - 1, 1); pr <= pre_hi; ++pr) {
     const long long ro = (long long)pr * pitch;
     if (live) {
       const double2 xv = *reinterpret_cast<const double2*>(xb + ro + c0);
