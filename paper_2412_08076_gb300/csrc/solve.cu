@@ -1089,11 +1089,17 @@ void solver_release_oneshot(richm_operator* op) {
 // weight and workspace pointers and the tuned fused settings are those it was created
 // with, else a new one (replacing it). A session is only pointers and launch plans, so
 // reuse changes no arithmetic; its graphs are captured again when b or x move.
+static bool same_solve_opts(const richm_solve_opts& a, const richm_solve_opts& b) {
+  return a.m == b.m && a.tol == b.tol && a.max_sweeps == b.max_sweeps && a.refine_every == b.refine_every &&
+         a.inner == b.inner && a.precond == b.precond && a.fuse == b.fuse && a.use_graph == b.use_graph &&
+         a.relax == b.relax && a.fp64_residual == b.fp64_residual;
+}
+
 static richm_status oneshot_solver(richm_operator* op, const richm_solve_opts* o, const void* w, const void* alpha,
                                    const void* alpha_t, void* work, size_t work_bytes, richm_solver** out) {
   const void* ptrs[4] = {w, alpha, alpha_t, work};
   const int tuned[2] = {op->best_fuse, op->best_rows};
-  if (op->oneshot && memcmp(&op->oneshot_opts, o, sizeof(*o)) == 0 && memcmp(op->oneshot_ptrs, ptrs, sizeof(ptrs)) == 0 &&
+  if (op->oneshot && same_solve_opts(op->oneshot_opts, *o) && memcmp(op->oneshot_ptrs, ptrs, sizeof(ptrs)) == 0 &&
       op->oneshot_bytes == work_bytes && memcmp(op->oneshot_tuned, tuned, sizeof(tuned)) == 0) {
     *out = op->oneshot;
     return RICHM_OK;
